@@ -1,0 +1,348 @@
+"""Benchmark: repeated-pattern multivector FETI solves on one GB300.
+
+Workload (default): 2D heat, two square patterns of 32x32 Q1 elements with conductivity 1 and 1000 in a
+seeded checkerboard over an 8x8 occurrence grid, u = 0 on x = 0, f ~ U(0,1) (n_lambda = 3904).
+A step is one pass of the whole method on that structure: FP64 pattern factorisation (both patterns),
+coarse problem and d, block ORTHODIR to ||r|| / ||r0|| <= 1e-8 (mixed forms: FP32 local products inside FP64
+refinement), and the recovery of lambda and u.  Inputs (pattern stiffness, links, loads) are resident on the
+device when the timed region starts; the L2 cache is flushed between steps (a 256 MB write) because the
+whole working set fits in L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision fp64|fp32]
+                    [--k K] [--workload c2|c1]
+
+Under torchrun (N > 1) every rank solves its own independently seeded structure (weak scaling, no collective
+on the data path); rank 0 prints the JSON line with the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FETI solves/s to 1e-8 rel. residual"
+WORKLOADS = {
+    "c2": "2D heat, two 32x32 Q1 patterns (conductivity 1 / 1000, seeded checkerboard) on 8x8 occurrences, "
+          "u=0 on x=0, f~U(0,1), n_lambda=3904",
+    "c1": "2D heat, one 8x8 Q1 pattern on 2x2 occurrences, u=0 on x=0, f~U(0,1), n_lambda=52",
+}
+PHASE_BOUND = {  # roofline resource of each phase's kernels
+    "factor": "alu", "coarse": "alu", "local": "alu", "gather": "hbm", "scatter": "hbm", "project": "hbm",
+    "gram": "alu", "reorth": "alu", "update": "alu", "recover": "alu",
+}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 / FP32 SIMT peaks of GB300 derived from the unit counts and clock: 152 SMs x 2070 MHz x
+# (FP32: 128 FMA lanes/SM -> 80.5 TFLOP/s; FP64: nominal 1.25 TFLOP/s, i.e. ~2 FMA/clk/SM).
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 2070e6 * 128 * 2 / 1e12
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, gpu_index=0):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9 or p[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def h2d_bytes(prob):
+    b = 0
+    for pat in prob.patterns:
+        K = pat.K
+        b += K.indptr.size * 8 + K.indices.size * 4 + K.data.size * 8 + pat.bnd_nodes.size * 4
+    for o in prob.occs:
+        b += o.n_links * (4 + 1 + 4 + 1) + o.f_global.size * 8 + 9 * 8
+    b += prob.n_lambda * 8 + prob.n_occ * 4
+    return b
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_1208_6387_gb300.fetirp as F
+    from fetirp_gen import config
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    prob = config(args.workload, seed=args.seed + rank, k=args.k)
+    stream = torch.cuda.Stream(device=dev)
+    opts = F.fetirp_default_options(precision=args.precision, tol=1e-8, inner_tol=args.inner_tol,
+                                    device=local, timing=1)
+    opts.cuda_stream = stream.cuda_stream
+    ctx = F.fetirp_create(opts)
+    F.load_problem(ctx, prob)
+    nu = F.n_u(prob)
+    c_d = torch.tensor(prob.c, dtype=torch.float64, device=dev)
+    lam_d = torch.empty(prob.n_lambda, dtype=torch.float64, device=dev)
+    u_d = torch.empty(nu, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        F.fetirp_factorize(ctx)
+        return F.fetirp_solve_device(ctx, prob.n_lambda, c_d.data_ptr(), lam_d.data_ptr(), u_d.data_ptr())
+
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
+    torch.cuda.synchronize()
+    with clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[i][0].record(stream)
+            stats.append(step())
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    # check the last result against the definition (residual reported by the library, FP64)
+    rel_res = max(s["rel_residual"] for s in stats)
+
+    # roofline: dominant phase over the timed steps (CUDA events on the library's stream)
+    ph_ms = np.sum([s["phase_ms"] for s in stats], axis=0)
+    ph_fl = np.sum([s["phase_flops"] for s in stats], axis=0)
+    ph_by = np.sum([s["phase_bytes"] for s in stats], axis=0)
+    ph_ln = np.sum([s["phase_launches"] for s in stats], axis=0)
+    dom = int(np.argmax(ph_ms))
+    name = F.PHASES[dom]
+    bound = PHASE_BOUND[name]
+    peaks, src = load_peaks()
+    per_launch_ms = ph_ms[dom] / max(ph_ln[dom], 1)
+    if bound == "hbm":
+        achieved = ph_by[dom] / (ph_ms[dom] / 1e3) / 1e9
+        peak, unit = peaks["hbm_gbs"], "GB/s"
+        peak_note = f"hbm_gbs of {src}"
+    else:
+        achieved = ph_fl[dom] / (ph_ms[dom] / 1e3) / 1e12
+        fp32 = (name == "local" and args.precision != "fp64")
+        peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+        unit = "TFLOP/s"
+        peak_note = ("FP32 SIMT peak derived from 152 SMs x 128 lanes x 2070 MHz" if fp32 else
+                     "FP64 nominal 1.25 TFLOP/s (152 SMs x 2070 MHz; DFMA probe measured 1.19)")
+    roof = {"kernel": f"phase:{name}", "bound": bound, "achieved": round(achieved, 4), "peak": peak, "unit": unit,
+            "frac": round(achieved / peak, 5), "traffic": None, "peak_source": peak_note,
+            "launches_per_step": float(ph_ln[dom]) / args.steps, "ms_per_launch": round(per_launch_ms, 5),
+            "share_of_step": round(float(ph_ms[dom]) / total_ms, 4) if world == 1 else None,
+            "phases_ms_per_step": {F.PHASES[i]: round(float(ph_ms[i]) / args.steps, 4) for i in range(10)}}
+
+    # block F-applies/s: the block operator alone, device resident, k columns
+    k = prob.k
+    V = torch.randn(prob.n_lambda, k, dtype=torch.float64, device=dev)
+    Qo = torch.empty_like(V)
+    F.fetirp_prepare(ctx, prob.n_lambda, prob.c)
+    prec = F.PRECISIONS[args.precision if args.precision != "tf32x3" else "fp32"]
+    for _ in range(5):
+        F.fetirp_apply_block_device(ctx, k, V.data_ptr(), Qo.data_ptr(), prec)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_app = 50
+    a.record(stream)
+    for _ in range(n_app):
+        F.fetirp_apply_block_device(ctx, k, V.data_ptr(), Qo.data_ptr(), prec)
+    b.record(stream)
+    torch.cuda.synchronize()
+    fapply_per_s = n_app / (a.elapsed_time(b) / 1e3)
+
+    # e2e: the public API from host buffers (create, patterns, occurrences, solve, outputs to host, destroy)
+    e2e_times = []
+    for i in range(max(2, min(args.steps, 5)) + 1):
+        t = time.perf_counter()
+        c2 = F.fetirp_create(F.fetirp_default_options(precision=args.precision, tol=1e-8, inner_tol=args.inner_tol,
+                                                       device=local))
+        F.load_problem(c2, prob)
+        F.fetirp_solve(c2, prob.n_lambda, prob.c, nu)
+        F.fetirp_destroy(c2)
+        if i > 0:
+            e2e_times.append(time.perf_counter() - t)
+    e2e_s = statistics.median(e2e_times)
+    F.fetirp_destroy(ctx)
+    launches = int(np.mean([s["launches"] for s in stats]))
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "data": "synthetic (seeded Q1 meshes, loads; no datasets)",
+        "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "precision": args.precision,
+                   "block_k": prob.k, "n_lambda": prob.n_lambda, "n_occ": prob.n_occ,
+                   "l2": "flushed between steps (256 MB write)", "tol": 1e-8,
+                   "step": "factorise patterns + coarse + d + block ORTHODIR + recovery"},
+        "time_to_solution_ms": round(ms_per_step, 4),
+        "iterations": stats[-1]["iterations"], "outer_steps": stats[-1]["outer_steps"],
+        "rel_residual": rel_res,
+        "block_f_applies_per_s": round(fapply_per_s, 2),
+        "gpu_launches": launches * args.steps,
+        "e2e": {"value": round(world / e2e_s, 4), "unit": "solves/s", "h2d_bytes_per_step": h2d_bytes(prob),
+                "d2h_bytes_per_step": (prob.n_lambda + nu) * 8},
+        "roofline": roof,
+        "clocks": clk.summary(local),
+        "wall_s": round(wall, 4),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, prob)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def oracle_step(prob):
+    from oracle.feti import FetiOracle
+    o = FetiOracle(prob)
+    lam, it, _ = o.multivector(tol=1e-8, max_it=2000)
+    o.recover(lam)
+    return it
+
+
+def cpu_baseline(args, prob):
+    """The oracle as it stands (numpy/scipy FP64 multivector FETI), one full solve of the same workload."""
+    t = time.perf_counter()
+    it = oracle_step(prob)
+    dt = time.perf_counter() - t
+    return {"value": round(1.0 / dt, 5), "unit": "solves/s", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle", "sample": f"one full solve of the same workload ({it} block iterations, "
+                                        f"{dt:.1f} s; numpy/scipy default BLAS threads)"}
+
+
+def run_reference(args, rank, world):
+    """The oracle timed on the host cores (rank 0 only), same workload/metric; each step one full solve."""
+    from fetirp_gen import config
+    if rank != 0:
+        return None
+    prob = config(args.workload, seed=args.seed, k=args.k)
+    for _ in range(args.warmup):
+        oracle_step(prob)
+    times = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle_step(prob)
+        times.append(time.perf_counter() - t)
+    wall = time.perf_counter() - t0
+    value = args.steps / sum(times)
+    cores = len(os.sched_getaffinity(0))
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Q1 meshes, loads; no datasets)",
+        "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "block_k": prob.k,
+                   "n_lambda": prob.n_lambda, "n_occ": prob.n_occ, "tol": 1e-8},
+        "cpu_baseline": {"value": round(value, 5), "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": "each step one full oracle solve of the workload"},
+        "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": round(wall, 3),
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--k", type=int, default=None)
+    ap.add_argument("--inner-tol", type=float, default=1e-6)
+    ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

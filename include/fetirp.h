@@ -1,0 +1,219 @@
+/*
+ * fetirp.h -- repeated-pattern FETI on one GB300 (sm_103a): C ABI.
+ *
+ * Method: Gosselet, Rixen & Rey, "A domain decomposition strategy to efficiently solve structures
+ * containing repeated patterns" (arXiv 1208.6387).  A structure is a set of occurrences of a few meshed
+ * patterns.  Each occurrence s carries its pattern's stiffness K(s) in the pattern frame, a rigid rotation
+ * and a signed Boolean assembly B(s) = A(s) t(s) (Eq. 2).  The library solves the dual interface problem
+ *     [F G; G^T 0] [lambda; alpha] = [d; e],   F = sum_s B(s) K(s)^+ B(s)^T   (Eq. 3)
+ * with multivector (block) FETI (Table 1, right column; full reorthogonalisation and F-normalisation of
+ * the numerical-issues subsection), every occurrence of a pattern sharing that pattern's one factorisation
+ * (the multi-right-hand-side product of the efficient-implementation subsection).  Dirichlet data enter
+ * as total-FETI multiplier rows (Dirichlet-conditions subsection), so every occurrence is floating.
+ *
+ * Conventions shared by every entry point
+ *  - Status: every call returns a fetirp_status and never throws; on error fetirp_last_error(ctx) holds
+ *    a message owned by the context, and no output buffer has been written.
+ *  - Ownership: every input array is copied (to host and device memory owned by the context) before the
+ *    call returns; the caller may free or reuse it.  Outputs go to caller-allocated buffers whose sizes
+ *    follow from the arguments.  "_device" entry points take device pointers allocated by the caller and
+ *    run on the context's stream; they return once the work is enqueued unless stated otherwise.
+ *  - Threading: a context is used by one host thread at a time.
+ *  - Indices are 0-based.  dof = node * dofs_per_node + component.
+ *  - Sizes that overflow int32 where an int32 is taken, negative sizes, NULL required pointers, non-finite
+ *    values, or indices out of range return FETIRP_EINVAL.
+ */
+#ifndef FETIRP_H
+#define FETIRP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fetirp_ctx_s* fetirp_ctx;
+
+typedef enum {
+  FETIRP_OK = 0,
+  FETIRP_EINVAL = 1,     /* bad argument */
+  FETIRP_ENOMEM = 2,     /* device or host allocation failed */
+  FETIRP_ESINGULAR = 3,  /* detected kernel dimension differs from the expected one, or G^T G singular */
+  FETIRP_ENOCONV = 4,    /* tolerance not reached within the iteration caps (outputs hold the last iterate) */
+  FETIRP_ECUDA = 5,      /* a CUDA call failed */
+  FETIRP_ESTATE = 6,     /* call out of order (e.g. solve before any occurrence) */
+  FETIRP_ETIMEOUT = 7    /* a bounded device-side wait gave up */
+} fetirp_status;
+
+/* Arithmetic of the local multi-right-hand-side products S^+ Y (the hot contraction). */
+enum {
+  FETIRP_PREC_FP64 = 0, /* plain FP64 form */
+  FETIRP_PREC_FP32 = 1, /* FP32 products wrapped in FP64 outer refinement (defect correction) */
+  FETIRP_PREC_TF32X3 = 2 /* tensor cores (tcgen05 kind::tf32), operands split hi+lo, 3 products, FP32
+                            accumulation in TMEM; wrapped in FP64 outer refinement */
+};
+
+typedef struct {
+  int32_t precision;   /* FETIRP_PREC_*, default FP64 */
+  double tol;          /* target ||r_j|| / ||r_0||, r = P^T (d - F lambda) (Table 1 line 3); default 1e-8 */
+  int32_t max_iter;    /* cap on block iterations over the whole solve; default 2000 */
+  int32_t block_k;     /* multivector width k; 1 = classical FETI-CG; default 32 (clamped to the number
+                          of occurrences; fetirp_set_groups overrides) */
+  int32_t max_outer;   /* cap on FP64 refinement steps of the mixed forms; default 12 */
+  double inner_tol;    /* relative tolerance of each inner (low-precision) solve; default 1e-6 */
+  double pivot_tol;    /* zero pivot when pivot <= pivot_tol * original diagonal; default 1e-9 */
+  double eig_trunc;    /* a direction is dropped when its normalisation pivot <= eig_trunc * largest;
+                          default 1e-12 */
+  void* cuda_stream;   /* cudaStream_t used for all device work; NULL = the legacy default stream */
+  int32_t device;      /* CUDA device ordinal; default 0 */
+  int32_t check_every; /* convergence is read back every check_every block iterations; default 1 */
+  int32_t timing;      /* 1: bracket every phase with CUDA events and fill the phase_* statistics; default 0 */
+  double eig_trunc_inner; /* truncation threshold of the low-precision inner solves of the mixed forms, where
+                             the operator is only accurate to ~1e-7; default 1e-6 */
+} fetirp_options;
+
+/* Phases of a solve, for the per-phase statistics. */
+enum {
+  FETIRP_PHASE_FACTOR = 0,   /* pattern factorisation (fetirp_factorize / fetirp_create_pattern) */
+  FETIRP_PHASE_COARSE = 1,   /* G^T G, its inverse, e, lambda_0, d */
+  FETIRP_PHASE_LOCAL = 2,    /* local multi-RHS products S^+ Y (the hot contraction) */
+  FETIRP_PHASE_GATHER = 3,   /* signed gather B(s)^T V into pattern-frame traces */
+  FETIRP_PHASE_SCATTER = 4,  /* signed scatter-add of the local solutions */
+  FETIRP_PHASE_PROJECT = 5,  /* projector P = I - G (G^T G)^{-1} G^T */
+  FETIRP_PHASE_GRAM = 6,     /* block Gram products (reorthogonalisation coefficients, eta, W^T r) */
+  FETIRP_PHASE_REORTH = 7,   /* W -= W_hist C */
+  FETIRP_PHASE_UPDATE = 8,   /* normalisation, W T, P~ T, lambda and residual updates, norms */
+  FETIRP_PHASE_RECOVER = 9,  /* alpha and u(s) */
+  FETIRP_NPHASE = 10
+};
+
+typedef struct {
+  int32_t iterations;         /* block iterations (all outer steps) */
+  int32_t outer_steps;        /* FP64 residual evaluations after the first (0 for the plain FP64 form) */
+  int32_t f_applies;          /* block F-applies P^T F P W */
+  int32_t dropped_directions; /* directions removed by the normalisation (redundant information) */
+  int32_t kernel_dim_total;   /* columns of G */
+  double rel_residual;        /* final ||P^T (d - F lambda)|| / ||r_0|| evaluated in FP64 */
+  double setup_ms;            /* host wall time of the structure set-up (tables, coarse problem, d, lambda_0) */
+  double solve_ms;            /* device time of iterations + recovery (CUDA events on the context stream) */
+  int64_t launches;           /* kernels launched by the call */
+  /* with options.timing = 1: per phase (FETIRP_PHASE_*) device time, launches, and the algorithmic work
+     counted from the sizes (flops and compulsory bytes, not hardware counters) */
+  double phase_ms[10];
+  int64_t phase_launches[10];
+  double phase_flops[10];
+  double phase_bytes[10];
+} fetirp_stats;
+
+/* Fill *opt with the defaults listed above. */
+void fetirp_default_options(fetirp_options* opt);
+
+/* Human-readable name of a status code (static storage). */
+const char* fetirp_status_string(fetirp_status s);
+
+/* Create a context on opt->device (opt may be NULL for defaults).  *out receives the handle. */
+fetirp_status fetirp_create(const fetirp_options* opt, fetirp_ctx* out);
+
+/* Message of the last failed call on ctx (owned by ctx, valid until the next call); "" if none. */
+const char* fetirp_last_error(fetirp_ctx ctx);
+
+/* Release every host and device resource of ctx.  NULL is a no-op. */
+void fetirp_destroy(fetirp_ctx ctx);
+
+/*
+ * Register a pattern and factorise it on the device in FP64 (Sec. 2: K(s)^+ with K K^+ y = y on range(K),
+ * kernel N; Schur complement S = K_bb - K_bi K_ii^{-1} K_ib and S^+ = t K^+ t^T, stated after Eq. 3).
+ *  n_nodes, dofs_per_node: mesh size; dofs_per_node is 1 (heat) or 2..3 (elasticity).
+ *  rowptr[n+1], col[nnz], val[nnz]: the FULL symmetric CSR of the free (unconstrained) pattern stiffness,
+ *     n = n_nodes * dofs_per_node, pattern frame.  Symmetry is assumed, not checked.
+ *  n_bnd, bnd_nodes[n_bnd]: the trace t: distinct nodes that may carry multipliers.  Their dofs are
+ *     ordered last (boundary-last), in the order given, so the trailing factor block is chol(S).
+ *  expected_kernel_dim: -1 to accept the detected kernel dimension; otherwise FETIRP_ESINGULAR when the
+ *     number of zero pivots differs.
+ *  *pattern_id receives the id (0, 1, ...).
+ * Device memory: a dense FP64 factor of (n rounded up to 64)^2 doubles plus S^+ in FP64 and FP32.
+ */
+fetirp_status fetirp_create_pattern(fetirp_ctx ctx, int32_t n_nodes, int32_t dofs_per_node,
+                                    const int64_t* rowptr, const int32_t* col, const double* val,
+                                    int32_t n_bnd, const int32_t* bnd_nodes, int32_t expected_kernel_dim,
+                                    int32_t* pattern_id);
+
+/*
+ * Add an occurrence of a pattern (Eq. 2 with the rotation of the elasticity subsection).
+ *  rot[9]: row-major R with global = R * local, or NULL for the identity.  Only signed permutation
+ *     matrices with determinant +1 (the 24 rotations of the cube) are accepted; the rotation is folded into
+ *     the links, so the hot path stays a signed gather/scatter.
+ *  n_links and the four link arrays: the rows of B(s) in the GLOBAL frame: entry sign[i] (+1 or -1) in
+ *     multiplier row lambda_row[i] on component global_comp[i] of pattern node local_node[i], which must
+ *     be one of the pattern's boundary nodes.  Every multiplier row must end up with one or two entries in
+ *     total over all occurrences (a Dirichlet row or a pairwise gluing row).
+ *  f_global[n_nodes * dofs_per_node]: the occurrence's load, pattern node order, global-frame components.
+ *  *occ_id receives the occurrence id (0, 1, ... in call order).
+ */
+fetirp_status fetirp_add_occurrence(fetirp_ctx ctx, int32_t pattern_id, const double* rot, int32_t n_links,
+                                    const int32_t* local_node, const int8_t* global_comp,
+                                    const int32_t* lambda_row, const int8_t* sign, const double* f_global,
+                                    int32_t* occ_id);
+
+/*
+ * Multivector columns (the block of search directions of Table 1, right): occurrence s contributes its
+ * share Delta(s) z of the preconditioned residual z to column group_of_occ[s] in [0, k), where
+ * Delta(s) = 1/(number of occurrences in the row) on the multiplier rows s appears in (sum_s Delta(s) = I).
+ * Without this call the occurrences are split into min(block_k, n_occ) contiguous groups by id.
+ */
+fetirp_status fetirp_set_groups(fetirp_ctx ctx, int32_t k, const int32_t* group_of_occ);
+
+/*
+ * Solve for lambda and the displacements (Table 1 and the recovery u(s) = K^+ (f - B^T lambda) + N alpha).
+ *  n_lambda: number of multiplier rows (max lambda_row + 1 over all occurrences).
+ *  c[n_lambda]: right-hand side of B u = c (Dirichlet values on Dirichlet rows, 0 on gluing rows), or NULL
+ *     for zero.
+ *  lambda_out[n_lambda]; u_out[sum_s n_nodes(s) * dofs_per_node]: occurrences concatenated in id order,
+ *     pattern node order, global-frame components.  Host memory.
+ *  stats: may be NULL.
+ * Blocks until done.  FETIRP_ENOCONV still writes the last iterate.
+ */
+fetirp_status fetirp_solve(fetirp_ctx ctx, int64_t n_lambda, const double* c, double* lambda_out,
+                           double* u_out, fetirp_stats* stats);
+
+/* As fetirp_solve with caller-allocated DEVICE buffers (c may be NULL); blocks until done. */
+fetirp_status fetirp_solve_device(fetirp_ctx ctx, int64_t n_lambda, const double* d_c, double* d_lambda,
+                                  double* d_u, fetirp_stats* stats);
+
+/*
+ * The block interface operator Q = P^T F P V on a block of k directions (Table 1 line 5.1), with
+ * P = I - G (G^T G)^{-1} G^T.  V and Q are n_lambda x k, row-major (k contiguous), FP64, host memory.
+ * precision: FETIRP_PREC_* for the local products.  Blocks until done.  Requires n_lambda to have been
+ * fixed by a previous fetirp_solve or fetirp_prepare.
+ */
+fetirp_status fetirp_apply_block(fetirp_ctx ctx, int32_t k, const double* V, double* Q, int32_t precision);
+
+/* As fetirp_apply_block on DEVICE buffers; enqueued on the context's stream, returns without waiting. */
+fetirp_status fetirp_apply_block_device(fetirp_ctx ctx, int32_t k, const double* d_V, double* d_Q,
+                                        int32_t precision);
+
+/*
+ * Build the coarse problem (G, G^T G and its inverse, e, lambda_0) and d for n_lambda rows and the given
+ * c (host, may be NULL) without iterating.  fetirp_solve calls it itself.
+ */
+fetirp_status fetirp_prepare(fetirp_ctx ctx, int64_t n_lambda, const double* c);
+
+/* Re-run the FP64 factorisation of every pattern from its resident stiffness (the setup of the method);
+ * blocks until done. */
+fetirp_status fetirp_factorize(fetirp_ctx ctx);
+
+/*
+ * Read back a pattern's operators (test hook).  Any output may be NULL.
+ *  n_b_out, kernel_dim_out: boundary dof count (n_bnd * dofs_per_node) and detected kernel dimension.
+ *  splus[n_b * n_b]: S^+ (row-major, boundary dofs in bnd_nodes order, dof-major within a node).
+ *  kernel[n * kernel_dim]: N (row-major over the pattern's ORIGINAL dof numbering), K N = 0.
+ * Call once with splus = kernel = NULL to learn the sizes.
+ */
+fetirp_status fetirp_get_pattern(fetirp_ctx ctx, int32_t pattern_id, int32_t* n_b_out, int32_t* kernel_dim_out,
+                                 double* splus, double* kernel);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FETIRP_H */

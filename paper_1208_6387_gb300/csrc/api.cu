@@ -1,0 +1,1246 @@
+// C ABI of the library (include/fetirp.h): patterns, occurrences, the coarse problem, the block interface
+// operator and the multivector FETI solver driver.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+
+#include "../../include/fetirp.h"
+#include "common.cuh"
+#include "dense.cuh"
+#include "ops.cuh"
+#include "tc.cuh"
+
+using namespace fetirp;
+
+namespace fetirp {
+unsigned long long g_launch_count = 0;
+}
+
+namespace {
+
+// ------------------------------------------------------------------------------------------- small kernels
+__global__ void k_csr_to_dense(int n, int npad, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                               const double* __restrict__ val, const int* __restrict__ newidx, double* A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  if (i >= n) { A[(size_t)i * npad + i] = 1.0; return; }
+  const int ri = newidx[i];
+  for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) A[(size_t)newidx[col[e]] * npad + ri] = val[e];
+}
+
+__global__ void k_set_diag(double* A, int ld, int from, int to, double v) {
+  const int i = from + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < to) A[(size_t)i * ld + i] = v;
+}
+
+__global__ void k_to_f32(size_t n, const double* __restrict__ x, float* __restrict__ y) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (float)x[i];
+}
+
+// Boundary rows of K^+ y (pattern frame, new ordering) minus, or the full local solution back to the
+// original dof order and the global frame: u_g[node][c] = sum_c' R[c][c'] u_l[node][c'].
+__global__ void k_unpermute_rotate(int n_dofs, int dpn, int npad, const double* __restrict__ U,
+                                   const int* __restrict__ newidx, const int* __restrict__ occ_list,
+                                   const int* __restrict__ rot, const long long* __restrict__ uoff, int n_occ_p,
+                                   double* __restrict__ out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n_dofs * n_occ_p) return;
+  const int q = (int)(idx / n_dofs), d = (int)(idx % n_dofs);
+  const int s = occ_list[q];
+  const int node = d / dpn, c = d % dpn;
+  const int* R = rot + 9 * s;
+  double v = 0.0;
+  for (int c2 = 0; c2 < dpn; ++c2) {
+    const int r = R[3 * c + c2];
+    if (r != 0) v += r * U[(size_t)q * npad + newidx[node * dpn + c2]];
+  }
+  out[uoff[s] + d] = v;
+}
+
+// ------------------------------------------------------------------------------------------- host data
+struct PatternData {
+  int n_nodes = 0, dpn = 1, n = 0, n_b = 0, n_i = 0, npad = 0, nbpad = 0, expected = -1, kdim = 0;
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  std::vector<int> bnd_nodes, bpos, newidx, oldidx, zpiv;
+  TilePlan plan, planS;
+  DBuf<int64_t> d_rowptr;
+  DBuf<int> d_col, d_newidx, zp;
+  DBuf<double> d_val, L, diag0, S64, N, Nb;
+  DBuf<float> S32, S_hi, S_lo;   // FP32 S^+ and its tf32 pair (leading dimension lds)
+  long long lds = 0;
+  std::vector<int> occs;       // occurrences of this pattern (ids), q = position
+  DBuf<int> d_occs;
+  DBuf<double> F;              // npad x n_occ loads (pattern frame, new ordering)
+  DBuf<double> U;              // npad x n_occ work (local solves)
+  long long ld_y = 0;          // Y/Z leading dimension
+};
+
+struct OccData {
+  int pattern = 0;
+  int R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  std::vector<double> f_local;  // pattern frame, original dof order
+  std::vector<int> link_j, link_row;
+  std::vector<int8_t> link_sign;
+};
+
+
+}  // namespace
+
+struct fetirp_ctx_s {
+  fetirp_options opt{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  std::vector<std::unique_ptr<PatternData>> pats;
+  std::vector<OccData> occs;
+  int k_user = 0;
+  std::vector<int> groups_user;
+
+  // structure state (prepare)
+  bool prepared = false;
+  int64_t n_lambda = -1;
+  int k = 1, n_G = 0, n_Gpad = 0;
+  Layout L{};
+  DBuf<int> d_slot_ptr, d_slot_row, d_row_slot, d_slot_occ, d_occ_obase, d_occ_pat, d_occ_q, d_occ_gofs,
+      d_occ_group, d_pair_s, d_pair_t, d_rot;
+  DBuf<int8_t> d_slot_sign, d_row_sign;
+  DBuf<long long> d_uoff;
+  int n_pairs = 0;
+  std::vector<int> pofs;               // first coarse column of every pattern
+  std::vector<long long> uoff;         // offset of every occurrence in u_out
+  long long n_u = 0;
+  DBuf<double> GtG, Ginv, e, d, lambda0, c;
+  TilePlan planG;
+  DBuf<int> zpG;
+
+  // work
+  DBuf<double> lam, r, t1, W, Q, Zr, Whist, Qhist, C, eta, wr, T, alpha, rr_part, Xc, Ac, gram_part, V1, V2;
+  DBuf<int> n_kept;
+  DBuf<double> Y64, Z64;
+  DBuf<float> Y32, Z32, Ylo32;
+  DBuf<int> tc_error;
+  long long hist_cap = 0;
+  int rr_blocks = 0;
+  fetirp_stats last{};
+
+  // per-phase accounting (CUDA events when opt.timing = 1)
+  struct PhaseRec { int phase; int e0, e1; };
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<PhaseRec> recs;
+  double phase_flops[FETIRP_NPHASE] = {}, phase_bytes[FETIRP_NPHASE] = {};
+  long long phase_launches[FETIRP_NPHASE] = {};
+  bool phases_pending = false;          // a fetirp_factorize call's phases belong to the next solve
+  long long pending_launches = 0;
+  ~fetirp_ctx_s() {
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+void set_err(fetirp_ctx ctx, const std::string& m) {
+  if (ctx) ctx->err = m;
+}
+
+template <typename F>
+fetirp_status guarded(fetirp_ctx ctx, F&& f) {
+  if (!ctx) return FETIRP_EINVAL;
+  try {
+    ctx->err.clear();
+    FETIRP_CUDA(cudaSetDevice(ctx->opt.device));
+    return f();
+  } catch (const Error& e) {
+    set_err(ctx, e.what());
+    return (fetirp_status)e.status;
+  } catch (const std::bad_alloc&) {
+    set_err(ctx, "host allocation failed");
+    return FETIRP_ENOMEM;
+  } catch (const std::exception& e) {
+    set_err(ctx, e.what());
+    return FETIRP_EINVAL;
+  }
+}
+
+// Brackets one phase of work: counts its launches and algorithmic work, and with opt.timing records a pair
+// of CUDA events on the context stream.
+struct PhaseScope {
+  fetirp_ctx ctx;
+  int phase;
+  unsigned long long l0;
+  int e0 = -1;
+  PhaseScope(fetirp_ctx c, int ph, double flops, double bytes) : ctx(c), phase(ph), l0(g_launch_count) {
+    ctx->phase_flops[ph] += flops;
+    ctx->phase_bytes[ph] += bytes;
+    if (ctx->opt.timing) e0 = record();
+  }
+  int record() {
+    if (ctx->ev_used == ctx->ev_pool.size()) {
+      cudaEvent_t e;
+      FETIRP_CUDA(cudaEventCreate(&e));
+      ctx->ev_pool.push_back(e);
+    }
+    const int id = (int)ctx->ev_used++;
+    FETIRP_CUDA(cudaEventRecord(ctx->ev_pool[id], ctx->stream));
+    return id;
+  }
+  ~PhaseScope() {
+    ctx->phase_launches[phase] += (long long)(g_launch_count - l0);
+    if (e0 >= 0) {
+      try {
+        const int e1 = record();
+        ctx->recs.push_back({phase, e0, e1});
+      } catch (...) {
+      }
+    }
+  }
+};
+
+void reset_phases(fetirp_ctx ctx) {
+  ctx->ev_used = 0;
+  ctx->recs.clear();
+  for (int i = 0; i < FETIRP_NPHASE; ++i) {
+    ctx->phase_flops[i] = ctx->phase_bytes[i] = 0.0;
+    ctx->phase_launches[i] = 0;
+  }
+}
+
+// Call after the stream is synchronised.
+void collect_phases(fetirp_ctx ctx, fetirp_stats& st) {
+  for (int i = 0; i < FETIRP_NPHASE; ++i) {
+    st.phase_ms[i] = 0.0;
+    st.phase_flops[i] = ctx->phase_flops[i];
+    st.phase_bytes[i] = ctx->phase_bytes[i];
+    st.phase_launches[i] = ctx->phase_launches[i];
+  }
+  for (auto& r : ctx->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev_pool[r.e0], ctx->ev_pool[r.e1]) == cudaSuccess) st.phase_ms[r.phase] += ms;
+  }
+}
+
+#define REQUIRE(cond, msg) \
+  do {                     \
+    if (!(cond)) throw Error(FETIRP_EINVAL, msg); \
+  } while (0)
+
+// ----------------------------------------------------------------------------------------- pattern set-up
+// FP64 factorisation on the device: dense factor of K in interior-first/boundary-last order with zero-pivot
+// detection (Sec. 2), kernel N, Schur complement pseudo-inverse S^+ = L_S^{-T} L_S^{-1} (stated after Eq. 3).
+void factorize_pattern(fetirp_ctx ctx, PatternData& P) {
+  cudaStream_t s = ctx->stream;
+  const int n = P.n, npad = P.npad;
+  PhaseScope ph(ctx, FETIRP_PHASE_FACTOR, 0.0, 0.0);
+  P.L.alloc((size_t)npad * npad);
+  P.L.zero(s);
+  k_csr_to_dense<<<ceil_div(npad, 128), 128, 0, s>>>(n, npad, P.d_rowptr.p, P.d_col.p, P.d_val.p, P.d_newidx.p,
+                                                      P.L.p);
+  FETIRP_LAUNCH_CHECK();
+  P.diag0.alloc(npad);
+  P.zp.alloc(npad);
+  copy_diag(P.L.p, npad, P.diag0.p, s);
+  chol_tiles(P.L.p, npad, P.plan, P.diag0.p, P.zp.p, ctx->opt.pivot_tol, s);
+  std::vector<int> zp(npad);
+  FETIRP_CUDA(cudaMemcpyAsync(zp.data(), P.zp.p, sizeof(int) * npad, cudaMemcpyDeviceToHost, s));
+  FETIRP_CUDA(cudaStreamSynchronize(s));
+  P.zpiv.clear();
+  for (int i = 0; i < npad; ++i)
+    if (zp[i]) P.zpiv.push_back(i);
+  for (int z : P.zpiv)
+    if (z < P.n_i || z >= n)
+      throw Error(FETIRP_ESINGULAR, "zero pivot outside the boundary block: interior stiffness is singular");
+  P.kdim = (int)P.zpiv.size();
+  if (P.kdim > 6)
+    throw Error(FETIRP_ESINGULAR, "kernel dimension " + std::to_string(P.kdim) + " > 6 (disconnected pattern?)");
+  if (P.expected >= 0 && P.kdim != P.expected)
+    throw Error(FETIRP_ESINGULAR, "detected kernel dimension " + std::to_string(P.kdim) + " != expected " +
+                                      std::to_string(P.expected));
+  const int kd = P.kdim;
+  // kernel: N_r = -K_rr^{-1} K_rz, N_z = I
+  P.N.alloc((size_t)npad * std::max(kd, 1));
+  P.N.zero(s);
+  if (kd > 0) {
+    std::vector<double> rhs((size_t)npad * kd, 0.0);
+    for (int m = 0; m < kd; ++m) {
+      const int old = P.oldidx[P.zpiv[m]];
+      for (int64_t e = P.rowptr[old]; e < P.rowptr[old + 1]; ++e)
+        rhs[(size_t)m * npad + P.newidx[P.col[e]]] = -P.val[e];
+      for (int z : P.zpiv) rhs[(size_t)m * npad + z] = 0.0;
+    }
+    P.N.upload(rhs, s);
+    tri_solve(P.L.p, npad, P.plan, P.zp.p, P.N.p, npad, kd, false, s);
+    tri_solve(P.L.p, npad, P.plan, P.zp.p, P.N.p, npad, kd, true, s);
+    const double one = 1.0;
+    for (int m = 0; m < kd; ++m)
+      FETIRP_CUDA(cudaMemcpyAsync(P.N.p + (size_t)m * npad + P.zpiv[m], &one, sizeof(double),
+                                  cudaMemcpyHostToDevice, s));
+    FETIRP_CUDA(cudaStreamSynchronize(s));   // `one` lives on this stack frame
+  }
+  P.Nb.alloc((size_t)P.n_b * std::max(kd, 1));
+  for (int m = 0; m < kd; ++m)
+    FETIRP_CUDA(cudaMemcpy2DAsync(P.Nb.p + m, sizeof(double) * kd, P.N.p + (size_t)m * npad + P.n_i,
+                                  sizeof(double), sizeof(double), P.n_b, cudaMemcpyDeviceToDevice, s));
+  // S^+ from the trailing block L_S
+  const int nbp = P.nbpad;
+  DBuf<double> LS((size_t)nbp * nbp), X((size_t)nbp * nbp);
+  DBuf<int> zpS(nbp);
+  LS.zero(s);
+  X.zero(s);
+  zpS.zero(s);
+  FETIRP_CUDA(cudaMemcpy2DAsync(LS.p, sizeof(double) * nbp, P.L.p + (size_t)P.n_i * npad + P.n_i,
+                                sizeof(double) * npad, sizeof(double) * P.n_b, P.n_b, cudaMemcpyDeviceToDevice, s));
+  FETIRP_CUDA(cudaMemcpyAsync(zpS.p, P.zp.p + P.n_i, sizeof(int) * P.n_b, cudaMemcpyDeviceToDevice, s));
+  if (nbp > P.n_b) {
+    k_set_diag<<<ceil_div(nbp - P.n_b, 128), 128, 0, s>>>(LS.p, nbp, P.n_b, nbp, 1.0);
+    FETIRP_LAUNCH_CHECK();
+  }
+  k_set_diag<<<ceil_div(nbp, 128), 128, 0, s>>>(X.p, nbp, 0, nbp, 1.0);
+  FETIRP_LAUNCH_CHECK();
+  tri_solve(LS.p, nbp, P.planS, zpS.p, X.p, nbp, nbp, false, s);   // X = L_S^{-1}
+  P.S64.alloc((size_t)P.n_b * P.n_b);
+  gemm_f64(P.n_b, P.n_b, nbp, 1.0, X.p, nbp, 1, X.p, 1, nbp, 0.0, P.S64.p, P.n_b, 1, s);
+  P.S32.alloc((size_t)P.n_b * P.n_b);
+  const size_t nn = (size_t)P.n_b * P.n_b;
+  k_to_f32<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(nn, P.S64.p, P.S32.p);
+  FETIRP_LAUNCH_CHECK();
+  P.lds = round_up(P.n_b, 4);
+  P.S_hi.alloc((size_t)P.n_b * P.lds);
+  P.S_lo.alloc((size_t)P.n_b * P.lds);
+  split_tf32(P.S64.p, P.n_b, P.n_b, P.n_b, P.S_hi.p, P.S_lo.p, P.lds, s);
+  FETIRP_CUDA(cudaStreamSynchronize(s));
+}
+
+// Dense SPD inverse in FP64 (coarse matrix G^T G): tile Cholesky, X = L^{-1}, A^{-1} = X^T X.
+void spd_inverse(fetirp_ctx ctx, const double* A_rowmajor, int n, int npad, TilePlan& plan, DBuf<int>& zp,
+                 double* out_rowmajor) {
+  cudaStream_t s = ctx->stream;
+  DBuf<double> A((size_t)npad * npad), X((size_t)npad * npad), diag(npad);
+  A.zero(s);
+  X.zero(s);
+  FETIRP_CUDA(cudaMemcpy2DAsync(A.p, sizeof(double) * npad, A_rowmajor, sizeof(double) * n, sizeof(double) * n, n,
+                                cudaMemcpyDeviceToDevice, s));   // symmetric: row-major == column-major
+  if (npad > n) {
+    k_set_diag<<<ceil_div(npad - n, 128), 128, 0, s>>>(A.p, npad, n, npad, 1.0);
+    FETIRP_LAUNCH_CHECK();
+  }
+  zp.alloc(npad);
+  copy_diag(A.p, npad, diag.p, s);
+  chol_tiles(A.p, npad, plan, diag.p, zp.p, 1e-13, s);
+  std::vector<int> h(npad);
+  FETIRP_CUDA(cudaMemcpyAsync(h.data(), zp.p, sizeof(int) * npad, cudaMemcpyDeviceToHost, s));
+  FETIRP_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < n; ++i)
+    if (h[i]) throw Error(FETIRP_ESINGULAR, "coarse matrix G^T G is singular (an occurrence is not constrained)");
+  k_set_diag<<<ceil_div(npad, 128), 128, 0, s>>>(X.p, npad, 0, npad, 1.0);
+  FETIRP_LAUNCH_CHECK();
+  tri_solve(A.p, npad, plan, zp.p, X.p, npad, npad, false, s);
+  gemm_f64(n, n, npad, 1.0, X.p, npad, 1, X.p, 1, npad, 0.0, out_rowmajor, n, 1, s);
+  FETIRP_CUDA(cudaStreamSynchronize(s));
+}
+
+TilePlan dense_plan(int nt) {
+  TilePlan p;
+  std::vector<uint8_t> nz((size_t)nt * nt, 0);
+  for (int I = 0; I < nt; ++I)
+    for (int J = 0; J <= I; ++J) nz[(size_t)I * nt + J] = 1;
+  p.build(nt, nz);
+  return p;
+}
+
+// ----------------------------------------------------------------------------------------- structure
+void invalidate(fetirp_ctx ctx) { ctx->prepared = false; }
+
+void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, const double* c_dev) {
+  cudaStream_t s = ctx->stream;
+  const int n_occ = (int)ctx->occs.size();
+  if (n_occ == 0) throw Error(FETIRP_ESTATE, "no occurrence has been added");
+  REQUIRE(n_lambda > 0 && n_lambda < (1LL << 31), "n_lambda out of range");
+  const int nl = (int)n_lambda;
+  const int n_pat = (int)ctx->pats.size();
+  if (n_pat > MAXP) throw Error(FETIRP_EINVAL, "more than 16 patterns in one structure");
+  // occurrence tables
+  std::vector<int> obase(n_occ + 1, 0), occ_pat(n_occ), occ_q(n_occ), occ_gofs(n_occ), group(n_occ);
+  for (auto& P : ctx->pats) P->occs.clear();
+  for (int o = 0; o < n_occ; ++o) {
+    PatternData& P = *ctx->pats[ctx->occs[o].pattern];
+    occ_pat[o] = ctx->occs[o].pattern;
+    occ_q[o] = (int)P.occs.size();
+    P.occs.push_back(o);
+    obase[o + 1] = obase[o] + P.n_b;
+  }
+  ctx->pofs.assign(n_pat + 1, 0);
+  for (int p = 0; p < n_pat; ++p) ctx->pofs[p + 1] = ctx->pofs[p] + ctx->pats[p]->kdim * (int)ctx->pats[p]->occs.size();
+  for (int o = 0; o < n_occ; ++o) occ_gofs[o] = ctx->pofs[occ_pat[o]] + occ_q[o] * ctx->pats[occ_pat[o]]->kdim;
+  ctx->n_G = ctx->pofs[n_pat];
+  // multivector groups
+  int k;
+  if (ctx->k_user > 0) {
+    k = ctx->k_user;
+    group = ctx->groups_user;
+  } else {
+    k = std::max(1, std::min(ctx->opt.block_k, n_occ));
+    for (int o = 0; o < n_occ; ++o) group[o] = (int)((long long)o * k / n_occ);
+  }
+  REQUIRE((int)group.size() == n_occ, "groups do not match the number of occurrences");
+  if (k > 64) throw Error(FETIRP_EINVAL, "block width k > 64 is not supported");
+  ctx->k = k;
+  // links -> gather CSR by slot, scatter lists by row
+  const int n_slots = obase[n_occ];
+  std::vector<int> cnt_slot(n_slots, 0);
+  std::vector<int> row_cnt(nl, 0), row_slot(2 * (size_t)nl, 0);
+  std::vector<int8_t> row_sign(2 * (size_t)nl, 0);
+  for (int o = 0; o < n_occ; ++o) {
+    const OccData& O = ctx->occs[o];
+    for (size_t i = 0; i < O.link_row.size(); ++i) {
+      const int row = O.link_row[i];
+      if (row >= nl) throw Error(FETIRP_EINVAL, "lambda_row >= n_lambda");
+      const int slot = obase[o] + O.link_j[i];
+      cnt_slot[slot]++;
+      if (row_cnt[row] >= 2) throw Error(FETIRP_EINVAL, "multiplier row " + std::to_string(row) + " has more than two entries");
+      row_slot[2 * (size_t)row + row_cnt[row]] = slot;
+      row_sign[2 * (size_t)row + row_cnt[row]] = O.link_sign[i];
+      row_cnt[row]++;
+    }
+  }
+  for (int r = 0; r < nl; ++r) {
+    if (row_cnt[r] == 0) throw Error(FETIRP_EINVAL, "multiplier row " + std::to_string(r) + " has no entry");
+    if (row_cnt[r] == 2 && row_slot[2 * (size_t)r] > row_slot[2 * (size_t)r + 1]) {
+      std::swap(row_slot[2 * (size_t)r], row_slot[2 * (size_t)r + 1]);
+      std::swap(row_sign[2 * (size_t)r], row_sign[2 * (size_t)r + 1]);
+    }
+  }
+  std::vector<int> slot_ptr(n_slots + 1, 0);
+  for (int i = 0; i < n_slots; ++i) slot_ptr[i + 1] = slot_ptr[i] + cnt_slot[i];
+  std::vector<int> slot_row(slot_ptr[n_slots]), fill(slot_ptr.begin(), slot_ptr.end() - 1);
+  std::vector<int8_t> slot_sign(slot_ptr[n_slots]);
+  for (int r = 0; r < nl; ++r)   // rows in increasing order inside every slot
+    for (int e = 0; e < row_cnt[r]; ++e) {
+      const int slot = row_slot[2 * (size_t)r + e];
+      slot_row[fill[slot]] = r;
+      slot_sign[fill[slot]] = row_sign[2 * (size_t)r + e];
+      fill[slot]++;
+    }
+  std::vector<int> slot_occ(n_slots);
+  for (int o = 0; o < n_occ; ++o)
+    for (int j = obase[o]; j < obase[o + 1]; ++j) slot_occ[j] = o;
+  // neighbour pairs (s, t) sharing a row, plus (s, s)
+  std::vector<std::vector<int>> nbr(n_occ);
+  for (int o = 0; o < n_occ; ++o) nbr[o].push_back(o);
+  for (int r = 0; r < nl; ++r)
+    if (row_cnt[r] == 2) {
+      const int a = slot_occ[row_slot[2 * (size_t)r]], b = slot_occ[row_slot[2 * (size_t)r + 1]];
+      nbr[a].push_back(b);
+      nbr[b].push_back(a);
+    }
+  std::vector<int> pair_s, pair_t;
+  for (int o = 0; o < n_occ; ++o) {
+    std::sort(nbr[o].begin(), nbr[o].end());
+    nbr[o].erase(std::unique(nbr[o].begin(), nbr[o].end()), nbr[o].end());
+    for (int t : nbr[o]) { pair_s.push_back(o); pair_t.push_back(t); }
+  }
+  // upload
+  ctx->d_slot_ptr.upload(slot_ptr, s);
+  ctx->d_slot_row.upload(slot_row, s);
+  ctx->d_slot_sign.upload(slot_sign, s);
+  ctx->d_row_slot.upload(row_slot, s);
+  ctx->d_row_sign.upload(row_sign, s);
+  ctx->d_slot_occ.upload(slot_occ, s);
+  ctx->d_occ_obase.upload(obase, s);
+  ctx->d_occ_pat.upload(occ_pat, s);
+  ctx->d_occ_q.upload(occ_q, s);
+  ctx->d_occ_gofs.upload(occ_gofs, s);
+  ctx->d_occ_group.upload(group, s);
+  ctx->d_pair_s.upload(pair_s, s);
+  ctx->d_pair_t.upload(pair_t, s);
+  ctx->n_pairs = (int)pair_s.size();
+  std::vector<int> rot(9 * (size_t)n_occ);
+  for (int o = 0; o < n_occ; ++o) std::memcpy(&rot[9 * (size_t)o], ctx->occs[o].R, sizeof(int) * 9);
+  ctx->d_rot.upload(rot, s);
+  ctx->uoff.assign(n_occ + 1, 0);
+  for (int o = 0; o < n_occ; ++o) ctx->uoff[o + 1] = ctx->uoff[o] + ctx->pats[occ_pat[o]]->n;
+  ctx->n_u = ctx->uoff[n_occ];
+  ctx->d_uoff.upload(ctx->uoff, s);
+
+  Layout& L = ctx->L;
+  L = Layout{};
+  L.n_lambda = nl; L.n_occ = n_occ; L.n_slots = n_slots; L.n_G = ctx->n_G; L.n_pat = n_pat; L.k = k;
+  L.slot_ptr = ctx->d_slot_ptr.p; L.slot_row = ctx->d_slot_row.p; L.slot_sign = ctx->d_slot_sign.p;
+  L.row_slot = ctx->d_row_slot.p; L.row_sign = ctx->d_row_sign.p; L.slot_occ = ctx->d_slot_occ.p;
+  L.occ_obase = ctx->d_occ_obase.p; L.occ_pat = ctx->d_occ_pat.p; L.occ_q = ctx->d_occ_q.p;
+  L.occ_gofs = ctx->d_occ_gofs.p; L.occ_group = ctx->d_occ_group.p;
+  for (int p = 0; p < n_pat; ++p) {
+    L.Nb[p] = ctx->pats[p]->Nb.p;
+    L.n_b[p] = ctx->pats[p]->n_b;
+    L.kdim[p] = ctx->pats[p]->kdim;
+  }
+  // per-pattern loads (pattern frame, new ordering) and work
+  for (int p = 0; p < n_pat; ++p) {
+    PatternData& P = *ctx->pats[p];
+    const int no = (int)P.occs.size();
+    std::vector<double> F((size_t)P.npad * std::max(no, 1), 0.0);
+    for (int q = 0; q < no; ++q) {
+      const OccData& O = ctx->occs[P.occs[q]];
+      for (int d = 0; d < P.n; ++d) F[(size_t)q * P.npad + P.newidx[d]] = O.f_local[d];
+    }
+    P.F.upload(F, s);
+    P.U.ensure((size_t)P.npad * std::max(no, 1));
+    P.d_occs.upload(P.occs, s);
+    P.ld_y = round_up(P.n_b, 4);
+  }
+  // coarse problem: G^T G (FP64), its inverse, e, lambda_0 (projector paragraph)
+  PhaseScope ph(ctx, FETIRP_PHASE_COARSE, 0.0, 0.0);
+  ctx->n_Gpad = (int)round_up(std::max(ctx->n_G, 1), TILE);
+  ctx->GtG.alloc((size_t)std::max(ctx->n_G, 1) * std::max(ctx->n_G, 1));
+  ctx->Ginv.alloc((size_t)std::max(ctx->n_G, 1) * std::max(ctx->n_G, 1));
+  ctx->e.alloc(std::max(ctx->n_G, 1));
+  ctx->d.alloc(nl);
+  ctx->lambda0.alloc(nl);
+  ctx->c.alloc(nl);
+  if (c_host) ctx->c.upload(c_host, nl, s);
+  else if (c_dev) FETIRP_CUDA(cudaMemcpyAsync(ctx->c.p, c_dev, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
+  else ctx->c.zero(s);
+  ctx->Xc.ensure((size_t)std::max(ctx->n_G, 1) * 64);
+  ctx->Ac.ensure((size_t)std::max(ctx->n_G, 1) * 64);
+  if (ctx->n_G > 0) {
+    gtg_dense(L, nullptr, nullptr, ctx->n_pairs, ctx->d_pair_s.p, ctx->d_pair_t.p, ctx->GtG.p, s);
+    ctx->planG = dense_plan(ctx->n_Gpad / TILE);
+    ctx->planG.upload(s);
+    spd_inverse(ctx, ctx->GtG.p, ctx->n_G, ctx->n_Gpad, ctx->planG, ctx->zpG, ctx->Ginv.p);
+    // e_s = N^T f_s
+    for (int p = 0; p < n_pat; ++p) {
+      PatternData& P = *ctx->pats[p];
+      const int no = (int)P.occs.size();
+      if (no == 0 || P.kdim == 0) continue;
+      gemm_f64(P.kdim, no, P.npad, 1.0, P.N.p, P.npad, 1, P.F.p, 1, P.npad, 0.0, ctx->e.p + ctx->pofs[p], 1, P.kdim,
+               s);
+    }
+    gemm_f64(ctx->n_G, 1, ctx->n_G, 1.0, ctx->Ginv.p, ctx->n_G, 1, ctx->e.p, 1, 1, 0.0, ctx->Ac.p, 1, 1, s);
+    g_apply(L, ctx->Ac.p, 1, 1.0, 0.0, ctx->lambda0.p, s);
+  } else {
+    ctx->lambda0.zero(s);
+  }
+  // d = sum_s B(s) K(s)^+ f(s) - c (Eq. 3)
+  PatView<double> V{};
+  for (int p = 0; p < n_pat; ++p) {
+    PatternData& P = *ctx->pats[p];
+    const int no = (int)P.occs.size();
+    if (no > 0) {
+      FETIRP_CUDA(cudaMemcpyAsync(P.U.p, P.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, s));
+      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, false, s);
+      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, true, s);
+    }
+    V.base[p] = P.U.p; V.ld[p] = P.npad; V.off[p] = P.n_i;
+  }
+  scatter<double>(L, V, 1, 0.0, ctx->d.p, s);
+  axpy_f64(nl, -1.0, ctx->c.p, ctx->d.p, s);
+  // work buffers
+  ctx->rr_blocks = std::max(1, std::min(304, ceil_div(nl, 64)));
+  ctx->rr_part.ensure(ctx->rr_blocks);
+  ctx->lam.ensure(nl); ctx->r.ensure(nl); ctx->t1.ensure(nl);
+  ctx->W.ensure((size_t)nl * k); ctx->Q.ensure((size_t)nl * k); ctx->Zr.ensure((size_t)nl * k);
+  ctx->V1.ensure((size_t)nl * 64); ctx->V2.ensure((size_t)nl * 64);
+  ctx->eta.ensure((size_t)k * k); ctx->wr.ensure(k); ctx->T.ensure((size_t)k * k); ctx->alpha.ensure(k);
+  ctx->n_kept.ensure(1);
+  ctx->n_lambda = n_lambda;
+  ctx->prepared = true;
+  FETIRP_CUDA(cudaStreamSynchronize(s));
+}
+
+// ----------------------------------------------------------------------------------------- operators
+void project(fetirp_ctx ctx, double* V, int k) {
+  if (ctx->n_G == 0) return;
+  cudaStream_t s = ctx->stream;
+  const double nl = ctx->L.n_lambda, nG = ctx->n_G;
+  PhaseScope ph(ctx, FETIRP_PHASE_PROJECT, 2.0 * nG * nG * k + 4.0 * nl * k * 6.0, 16.0 * nl * k + 8.0 * nG * nG);
+  ctx->Xc.ensure((size_t)ctx->n_G * k);
+  ctx->Ac.ensure((size_t)ctx->n_G * k);
+  gt_v(ctx->L, V, k, ctx->Xc.p, s);
+  gemm_f64(ctx->n_G, k, ctx->n_G, 1.0, ctx->Ginv.p, ctx->n_G, 1, ctx->Xc.p, k, 1, 0.0, ctx->Ac.p, k, 1, s);
+  g_apply(ctx->L, ctx->Ac.p, k, -1.0, 1.0, V, s);
+}
+
+// gather -> local products -> scatter, each bracketed as its own phase
+template <typename T>
+void run_local(fetirp_ctx ctx, const Layout& L, const double* src, double* out, int k, const PatView<T>& Yv,
+               const PatView<T>& Zv, const LocalProblem& LP, double es) {
+  cudaStream_t s = ctx->stream;
+  double flops = 0, sbytes = 0, rhs_elems = 0;
+  for (int p = 0; p < LP.n_pat; ++p) {
+    flops += 2.0 * LP.n_b[p] * (double)LP.n_b[p] * LP.n_rhs[p];
+    sbytes += (double)LP.n_b[p] * LP.n_b[p] * es;
+    rhs_elems += (double)LP.n_b[p] * LP.n_rhs[p];
+  }
+  const double vbytes = 8.0 * L.n_lambda * k;
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_GATHER, 0.0, vbytes + rhs_elems * es);
+    gather<T>(L, src, k, Yv, s);
+  }
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_LOCAL, flops, sbytes + 2.0 * rhs_elems * es);
+    if (es == 8.0) local_gemm_f64(LP, s);
+    else local_gemm_f32(LP, s);
+  }
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_SCATTER, 0.0, vbytes + rhs_elems * es);
+    scatter<T>(L, Zv, k, 0.0, out, s);
+  }
+}
+
+// out = F in (F = sum_s B K^+ B^T through S^+), block of k columns; optional projections around it.
+void apply_F(fetirp_ctx ctx, const double* in, double* out, int k, int prec, bool project_in, bool project_out) {
+  cudaStream_t s = ctx->stream;
+  const Layout& L = ctx->L;
+  const double* src = in;
+  if (project_in && ctx->n_G > 0) {
+    ctx->V2.ensure((size_t)L.n_lambda * k);
+    FETIRP_CUDA(cudaMemcpyAsync(ctx->V2.p, in, sizeof(double) * (size_t)L.n_lambda * k, cudaMemcpyDeviceToDevice, s));
+    project(ctx, ctx->V2.p, k);
+    src = ctx->V2.p;
+  }
+  const int n_pat = (int)ctx->pats.size();
+  long long total = 0;
+  std::vector<long long> base(n_pat);
+  for (int p = 0; p < n_pat; ++p) {
+    base[p] = total;
+    total += (long long)ctx->pats[p]->occs.size() * k * ctx->pats[p]->ld_y;
+  }
+  LocalProblem LP{};
+  LP.n_pat = n_pat;
+  if (prec == FETIRP_PREC_FP64) {
+    ctx->Y64.ensure(total); ctx->Z64.ensure(total);
+    PatView<double> Yv{}, Zv{};
+    for (int p = 0; p < n_pat; ++p) {
+      PatternData& P = *ctx->pats[p];
+      Yv.base[p] = ctx->Y64.p + base[p]; Yv.ld[p] = P.ld_y; Yv.off[p] = 0;
+      Zv.base[p] = ctx->Z64.p + base[p]; Zv.ld[p] = P.ld_y; Zv.off[p] = 0;
+      LP.S[p] = P.S64.p; LP.n_b[p] = P.n_b; LP.n_rhs[p] = (int)P.occs.size() * k; LP.ld[p] = P.ld_y;
+      LP.Y[p] = Yv.base[p]; LP.Z[p] = Zv.base[p];
+    }
+    run_local<double>(ctx, L, src, out, k, Yv, Zv, LP, 8.0);
+  } else if (prec == FETIRP_PREC_FP32) {
+    ctx->Y32.ensure(total); ctx->Z32.ensure(total);
+    PatView<float> Yv{}, Zv{};
+    for (int p = 0; p < n_pat; ++p) {
+      PatternData& P = *ctx->pats[p];
+      Yv.base[p] = ctx->Y32.p + base[p]; Yv.ld[p] = P.ld_y; Yv.off[p] = 0;
+      Zv.base[p] = ctx->Z32.p + base[p]; Zv.ld[p] = P.ld_y; Zv.off[p] = 0;
+      LP.S[p] = P.S32.p; LP.n_b[p] = P.n_b; LP.n_rhs[p] = (int)P.occs.size() * k; LP.ld[p] = P.ld_y;
+      LP.Y[p] = Yv.base[p]; LP.Z[p] = Zv.base[p];
+    }
+    run_local<float>(ctx, L, src, out, k, Yv, Zv, LP, 4.0);
+  } else if (prec == FETIRP_PREC_TF32X3) {
+    ctx->Y32.ensure(total); ctx->Ylo32.ensure(total); ctx->Z32.ensure(total);
+    if (!ctx->tc_error.p) { ctx->tc_error.alloc(1); ctx->tc_error.zero(s); }
+    PatView<float> Yh{}, Yl{}, Zv{};
+    TcProblem T;
+    T.n_pat = n_pat;
+    double flops = 0, bytes = 0, rhs_elems = 0;
+    for (int p = 0; p < n_pat; ++p) {
+      PatternData& P = *ctx->pats[p];
+      Yh.base[p] = ctx->Y32.p + base[p]; Yh.ld[p] = P.ld_y; Yh.off[p] = 0;
+      Yl.base[p] = ctx->Ylo32.p + base[p]; Yl.ld[p] = P.ld_y; Yl.off[p] = 0;
+      Zv.base[p] = ctx->Z32.p + base[p]; Zv.ld[p] = P.ld_y; Zv.off[p] = 0;
+      T.S_hi[p] = P.S_hi.p; T.S_lo[p] = P.S_lo.p; T.lds[p] = P.lds;
+      T.Y_hi[p] = Yh.base[p]; T.Y_lo[p] = Yl.base[p]; T.Z[p] = Zv.base[p]; T.ldy[p] = P.ld_y;
+      T.n_b[p] = P.n_b; T.n_rhs[p] = (int)P.occs.size() * k;
+      flops += 2.0 * P.n_b * (double)P.n_b * T.n_rhs[p];
+      bytes += 2.0 * P.n_b * (double)P.n_b * 4 + 3.0 * P.n_b * (double)T.n_rhs[p] * 4;
+      rhs_elems += (double)P.n_b * T.n_rhs[p];
+    }
+    const double vbytes = 8.0 * L.n_lambda * k;
+    {
+      PhaseScope ph(ctx, FETIRP_PHASE_GATHER, 0.0, vbytes + 2.0 * rhs_elems * 4);
+      gather_split(L, src, k, Yh, Yl, s);
+    }
+    {
+      PhaseScope ph(ctx, FETIRP_PHASE_LOCAL, flops, bytes);
+      tc_gemm_tf32x3(T, ctx->tc_error.p, s);
+    }
+    {
+      PhaseScope ph(ctx, FETIRP_PHASE_SCATTER, 0.0, vbytes + rhs_elems * 4);
+      scatter<float>(L, Zv, k, 0.0, out, s);
+    }
+  } else {
+    throw Error(FETIRP_EINVAL, "unsupported precision");
+  }
+  if (project_out) project(ctx, out, k);
+}
+
+double norm2(fetirp_ctx ctx, const double* x, int n) {
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_UPDATE, 2.0 * n, 8.0 * n);
+    sum_sq(n, x, ctx->rr_part.p, ctx->rr_blocks, ctx->stream);
+  }
+  std::vector<double> h(ctx->rr_blocks);
+  FETIRP_CUDA(cudaMemcpyAsync(h.data(), ctx->rr_part.p, sizeof(double) * ctx->rr_blocks, cudaMemcpyDeviceToHost,
+                              ctx->stream));
+  FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
+  double acc = 0.0;
+  for (double v : h) acc += v;
+  return std::sqrt(acc);
+}
+
+// Residual r = P^T (d - F lambda) in FP64 (Table 1 line 3).
+void residual(fetirp_ctx ctx) {
+  const int nl = ctx->L.n_lambda;
+  apply_F(ctx, ctx->lam.p, ctx->r.p, 1, FETIRP_PREC_FP64, false, false);
+  // r = d - F lambda
+  cudaStream_t s = ctx->stream;
+  ctx->t1.ensure(nl);
+  FETIRP_CUDA(cudaMemcpyAsync(ctx->t1.p, ctx->d.p, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
+  axpy_f64(nl, -1.0, ctx->r.p, ctx->t1.p, s);
+  FETIRP_CUDA(cudaMemcpyAsync(ctx->r.p, ctx->t1.p, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
+  project(ctx, ctx->r.p, 1);
+}
+
+struct Hist {
+  long long cols = 0;   // columns stored
+};
+
+// Block ORTHODIR iterations on P^T F_prec P (Table 1 right with full reorthogonalisation and
+// F-normalisation).  Updates lam and r in place until ||r|| <= target or the caps are hit.  Directions kept in
+// the history stay F_prec-orthonormal, so a later call with the same precision reuses them.
+double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, Hist& H, fetirp_stats& st,
+                      int& it_budget) {
+  cudaStream_t s = ctx->stream;
+  const int nl = ctx->L.n_lambda, k = ctx->k;
+  const long long cap = ctx->hist_cap;
+  std::vector<double> rrh(ctx->rr_blocks);
+  // Galerkin start on the stored directions: lam += W_h (W_h^T r), r -= Q_h (W_h^T r)
+  if (H.cols > 0) {
+    const int a = (int)H.cols;
+    {
+      PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 2.0 * nl * a, 8.0 * nl * (a + 1.0));
+      gram_f64(nl, a, 1, ctx->Whist.p, (int)cap, ctx->r.p, 1, ctx->C.p, ctx->gram_part, s);
+    }
+    {
+      PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 4.0 * nl * a, 16.0 * nl * a);
+      gemm_f64(nl, 1, a, 1.0, ctx->Whist.p, cap, 1, ctx->C.p, 1, 1, 1.0, ctx->lam.p, 1, 1, s);
+      gemm_f64(nl, 1, a, -1.0, ctx->Qhist.p, cap, 1, ctx->C.p, 1, 1, 1.0, ctx->r.p, 1, 1, s);
+    }
+    rnorm = norm2(ctx, ctx->r.p, nl);
+  }
+  int check = std::max(1, ctx->opt.check_every);
+  int since = 0;
+  while (rnorm > target && it_budget > 0) {
+    if (H.cols + k > cap) H.cols = 0;   // history full: restart
+    double* Wn = ctx->Whist.p + H.cols;
+    double* Qn = ctx->Qhist.p + H.cols;
+    // multivector from the (projected) residual, then P
+    {
+      PhaseScope ph(ctx, FETIRP_PHASE_UPDATE, 0.0, 8.0 * nl * (k + 1.0));
+      split(ctx->L, ctx->r.p, k, ctx->Zr.p, s);
+    }
+    project(ctx, ctx->Zr.p, k);
+    // full reorthogonalisation against the stored F-orthonormal directions
+    if (H.cols > 0) {
+      const int a = (int)H.cols;
+      {
+        PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 2.0 * nl * a * k, 8.0 * nl * (a + k));
+        gram_f64(nl, a, k, ctx->Qhist.p, (int)cap, ctx->Zr.p, k, ctx->C.p, ctx->gram_part, s);
+      }
+      {
+        PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 2.0 * nl * a * k, 8.0 * nl * (a + 2.0 * k));
+        gemm_f64(nl, k, a, -1.0, ctx->Whist.p, cap, 1, ctx->C.p, k, 1, 1.0, ctx->Zr.p, k, 1, s);
+      }
+    }
+    // P~ = P^T F W (Table 1 line 5.1)
+    apply_F(ctx, ctx->Zr.p, ctx->Q.p, k, prec, false, true);
+    st.f_applies++;
+    {
+      PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 2.0 * nl * k * (k + 1.0), 8.0 * nl * (2.0 * k + 1.0));
+      gram_f64(nl, k, k, ctx->Zr.p, k, ctx->Q.p, k, ctx->eta.p, ctx->gram_part, s);
+      gram_f64(nl, k, 1, ctx->Zr.p, k, ctx->r.p, 1, ctx->wr.p, ctx->gram_part, s);
+    }
+    {
+      PhaseScope ph(ctx, FETIRP_PHASE_UPDATE, 4.0 * nl * k * k + 4.0 * nl * k, 8.0 * nl * (4.0 * k + 4.0));
+      normalise(k, ctx->eta.p, ctx->wr.p, prec == FETIRP_PREC_FP64 ? ctx->opt.eig_trunc : ctx->opt.eig_trunc_inner,
+                ctx->T.p, ctx->alpha.p, ctx->n_kept.p, s);
+      update(nl, k, ctx->Zr.p, ctx->Q.p, ctx->T.p, ctx->alpha.p, Wn, Qn, cap, ctx->lam.p, ctx->r.p, ctx->rr_part.p,
+             ctx->rr_blocks, s);
+    }
+    H.cols += k;
+    st.iterations++;
+    it_budget--;
+    if (++since >= check || it_budget == 0) {
+      since = 0;
+      int kept = 0;
+      FETIRP_CUDA(cudaMemcpyAsync(rrh.data(), ctx->rr_part.p, sizeof(double) * ctx->rr_blocks,
+                                  cudaMemcpyDeviceToHost, s));
+      FETIRP_CUDA(cudaMemcpyAsync(&kept, ctx->n_kept.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+      FETIRP_CUDA(cudaStreamSynchronize(s));
+      double acc = 0.0;
+      for (double v : rrh) acc += v;
+      rnorm = std::sqrt(acc);
+      st.dropped_directions += k - kept;
+      if (kept == 0) break;   // no new information: stagnation
+    }
+  }
+  return rnorm;
+}
+
+void recover(fetirp_ctx ctx, double* d_u_out) {
+  cudaStream_t s = ctx->stream;
+  PhaseScope ph(ctx, FETIRP_PHASE_RECOVER, 0.0, 0.0);
+  const Layout& L = ctx->L;
+  const int nl = L.n_lambda;
+  const int n_pat = (int)ctx->pats.size();
+  // alpha = (G^T G)^{-1} G^T (d - F lambda)   (first row of Eq. 3)
+  if (ctx->n_G > 0) {
+    apply_F(ctx, ctx->lam.p, ctx->t1.p, 1, FETIRP_PREC_FP64, false, false);
+    ctx->V1.ensure(nl);
+    FETIRP_CUDA(cudaMemcpyAsync(ctx->V1.p, ctx->d.p, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
+    axpy_f64(nl, -1.0, ctx->t1.p, ctx->V1.p, s);
+    gt_v(L, ctx->V1.p, 1, ctx->Xc.p, s);
+    gemm_f64(ctx->n_G, 1, ctx->n_G, 1.0, ctx->Ginv.p, ctx->n_G, 1, ctx->Xc.p, 1, 1, 0.0, ctx->Ac.p, 1, 1, s);
+  }
+  // u(s) = K^+ (f(s) - B(s)^T lambda) - N(s) alpha(s)
+  PatView<double> V{};
+  for (int p = 0; p < n_pat; ++p) {
+    PatternData& P = *ctx->pats[p];
+    const int no = (int)P.occs.size();
+    if (no > 0)
+      FETIRP_CUDA(cudaMemcpyAsync(P.U.p, P.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, s));
+    V.base[p] = P.U.p; V.ld[p] = P.npad; V.off[p] = P.n_i;
+  }
+  gather<double>(L, ctx->lam.p, 1, V, s, -1.0, 1.0);
+  for (int p = 0; p < n_pat; ++p) {
+    PatternData& P = *ctx->pats[p];
+    const int no = (int)P.occs.size();
+    if (no == 0) continue;
+    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, false, s);
+    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, true, s);
+    if (P.kdim > 0 && ctx->n_G > 0)
+      gemm_f64(P.npad, no, P.kdim, -1.0, P.N.p, 1, P.npad, ctx->Ac.p + ctx->pofs[p], 1, P.kdim, 1.0, P.U.p, 1,
+               P.npad, s);
+    const long long tot = (long long)P.n * no;
+    k_unpermute_rotate<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.n, P.dpn, P.npad, P.U.p, P.d_newidx.p,
+                                                                     P.d_occs.p, ctx->d_rot.p, ctx->d_uoff.p, no,
+                                                                     d_u_out);
+    FETIRP_LAUNCH_CHECK();
+  }
+}
+
+void ensure_history(fetirp_ctx ctx) {
+  const int nl = ctx->L.n_lambda, k = ctx->k;
+  // History: at most n_lambda directions can be F-orthogonal, and at most max_iter blocks are made; the two
+  // arrays are also kept under 8 GB.  A full history restarts the recurrence.
+  long long want = std::min<long long>((long long)std::max(1, ctx->opt.max_iter) * k, round_up(nl, k));
+  long long limit = (8LL << 30) / (2LL * 8 * std::max(nl, 1));
+  long long cap = std::max<long long>(k, std::min(want, limit));
+  cap = cap / k * k;
+  if (cap != ctx->hist_cap || (long long)ctx->Whist.n < (long long)nl * cap) {
+    ctx->Whist.alloc((size_t)nl * cap);
+    ctx->Qhist.alloc((size_t)nl * cap);
+    ctx->hist_cap = cap;
+  }
+  ctx->C.ensure((size_t)cap * k);
+  // gram partials: the largest product is (cap x k) over nl rows
+  const int ta = ceil_div(cap, 64), tb = ceil_div(k, 64);
+  const int chunks = std::max(1, std::min(ceil_div(nl, 64), 304 / std::max(1, ta * tb)));
+  // any product a x b with a <= cap, b <= k uses at most max(chunks * cap * k, 304 * 64 * 64) partials
+  ctx->gram_part.ensure(std::max<size_t>((size_t)(chunks + 1) * cap * k, (size_t)304 * 64 * 64));
+}
+
+// A bounded wait inside the tensor-core kernel that expired leaves a nonzero code in tc_error.
+void check_tc_error(fetirp_ctx ctx) {
+  if (!ctx->tc_error.p) return;
+  int code = 0;
+  FETIRP_CUDA(cudaMemcpyAsync(&code, ctx->tc_error.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (code != 0) {
+    ctx->tc_error.zero(ctx->stream);
+    throw Error(FETIRP_ETIMEOUT, "tensor-core pipeline wait expired (code " + std::to_string(code) + ")");
+  }
+}
+
+fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_stats* stats) {
+  cudaStream_t s = ctx->stream;
+  const int nl = ctx->L.n_lambda;
+  fetirp_stats st{};
+  st.kernel_dim_total = ctx->n_G;
+  const unsigned long long l0 = g_launch_count;
+  cudaEvent_t e0, e1;
+  FETIRP_CUDA(cudaEventCreate(&e0));
+  FETIRP_CUDA(cudaEventCreate(&e1));
+  FETIRP_CUDA(cudaEventRecord(e0, s));
+  ensure_history(ctx);
+  FETIRP_CUDA(cudaMemcpyAsync(ctx->lam.p, ctx->lambda0.p, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
+  residual(ctx);
+  const double r0 = norm2(ctx, ctx->r.p, nl);
+  double rn = r0;
+  const double target = ctx->opt.tol * r0;
+  int budget = ctx->opt.max_iter;
+  Hist H;
+  const int prec = ctx->opt.precision;
+  if (r0 > 0.0) {
+    if (prec == FETIRP_PREC_FP64) {
+      rn = block_orthodir(ctx, FETIRP_PREC_FP64, target, rn, H, st, budget);
+      residual(ctx);   // report the FP64 residual of the final iterate
+      rn = norm2(ctx, ctx->r.p, nl);
+    } else {
+      // outer FP64 defect correction: inner solves on the low-precision operator reuse their directions
+      for (int outer = 0; outer < ctx->opt.max_outer && rn > target && budget > 0; ++outer) {
+        const double inner_target = std::max(ctx->opt.inner_tol * rn, 0.5 * target);
+        block_orthodir(ctx, prec, inner_target, rn, H, st, budget);
+        residual(ctx);
+        rn = norm2(ctx, ctx->r.p, nl);
+        st.outer_steps++;
+      }
+    }
+  }
+  st.rel_residual = r0 > 0.0 ? rn / r0 : 0.0;
+  check_tc_error(ctx);
+  if (d_lambda)
+    FETIRP_CUDA(cudaMemcpyAsync(d_lambda, ctx->lam.p, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
+  if (d_u) recover(ctx, d_u);
+  FETIRP_CUDA(cudaEventRecord(e1, s));
+  FETIRP_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  FETIRP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  st.solve_ms = ms;
+  st.setup_ms = ctx->last.setup_ms;
+  st.launches = (int64_t)(g_launch_count - l0) + ctx->last.launches;
+  collect_phases(ctx, st);
+  ctx->last = st;
+  if (stats) *stats = st;
+  if (!(st.rel_residual <= ctx->opt.tol)) {
+    set_err(ctx, "tolerance not reached: relative residual " + std::to_string(st.rel_residual));
+    return FETIRP_ENOCONV;
+  }
+  return FETIRP_OK;
+}
+
+// Resets the per-phase accounting (unless keep_phases: a factorisation just ran and belongs to the call).
+void prepare_timed(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, const double* c_dev,
+                   bool keep_phases = false) {
+  if (!keep_phases && !ctx->phases_pending) reset_phases(ctx);
+  ctx->phases_pending = false;
+  const unsigned long long l0 = g_launch_count;
+  auto t0 = std::chrono::steady_clock::now();
+  build_structure(ctx, n_lambda, c_host, c_dev);
+  ctx->last.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  ctx->last.launches = (int64_t)(g_launch_count - l0) + ctx->pending_launches;
+  ctx->pending_launches = 0;
+}
+
+}  // namespace
+
+// =========================================================================================== C ABI
+extern "C" {
+
+void fetirp_default_options(fetirp_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = FETIRP_PREC_FP64;
+  o->tol = 1e-8;
+  o->max_iter = 2000;
+  o->block_k = 32;
+  o->max_outer = 12;
+  o->inner_tol = 1e-6;
+  o->pivot_tol = 1e-9;
+  o->eig_trunc = 1e-12;
+  o->cuda_stream = nullptr;
+  o->device = 0;
+  o->check_every = 1;
+  o->timing = 0;
+  o->eig_trunc_inner = 1e-6;
+}
+
+const char* fetirp_status_string(fetirp_status s) {
+  switch (s) {
+    case FETIRP_OK: return "FETIRP_OK";
+    case FETIRP_EINVAL: return "FETIRP_EINVAL";
+    case FETIRP_ENOMEM: return "FETIRP_ENOMEM";
+    case FETIRP_ESINGULAR: return "FETIRP_ESINGULAR";
+    case FETIRP_ENOCONV: return "FETIRP_ENOCONV";
+    case FETIRP_ECUDA: return "FETIRP_ECUDA";
+    case FETIRP_ESTATE: return "FETIRP_ESTATE";
+    case FETIRP_ETIMEOUT: return "FETIRP_ETIMEOUT";
+  }
+  return "unknown status";
+}
+
+fetirp_status fetirp_create(const fetirp_options* opt, fetirp_ctx* out) {
+  if (!out) return FETIRP_EINVAL;
+  *out = nullptr;
+  std::unique_ptr<fetirp_ctx_s> ctx(new (std::nothrow) fetirp_ctx_s());
+  if (!ctx) return FETIRP_ENOMEM;
+  if (opt) ctx->opt = *opt;
+  else fetirp_default_options(&ctx->opt);
+  const fetirp_options& o = ctx->opt;
+  if (!(o.tol > 0) || o.max_iter < 1 || o.block_k < 1 || o.max_outer < 1 || !(o.inner_tol > 0) ||
+      !(o.pivot_tol > 0) || !(o.eig_trunc > 0) || !(o.eig_trunc_inner > 0) || o.check_every < 0 ||
+      (o.precision != FETIRP_PREC_FP64 && o.precision != FETIRP_PREC_FP32 && o.precision != FETIRP_PREC_TF32X3))
+    return FETIRP_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) return FETIRP_ECUDA;
+  if (cudaSetDevice(o.device) != cudaSuccess) return FETIRP_ECUDA;
+  ctx->stream = (cudaStream_t)o.cuda_stream;
+  *out = ctx.release();
+  return FETIRP_OK;
+}
+
+const char* fetirp_last_error(fetirp_ctx ctx) { return ctx ? ctx->err.c_str() : "invalid context"; }
+
+void fetirp_destroy(fetirp_ctx ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->opt.device);
+  cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+}
+
+fetirp_status fetirp_create_pattern(fetirp_ctx ctx, int32_t n_nodes, int32_t dpn, const int64_t* rowptr,
+                                    const int32_t* col, const double* val, int32_t n_bnd, const int32_t* bnd_nodes,
+                                    int32_t expected_kernel_dim, int32_t* pattern_id) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    REQUIRE(n_nodes > 0 && dpn >= 1 && dpn <= 3, "n_nodes must be > 0 and dofs_per_node in 1..3");
+    REQUIRE(rowptr && col && val && bnd_nodes && pattern_id, "NULL argument");
+    REQUIRE((long long)n_nodes * dpn < (1LL << 30), "pattern too large");
+    REQUIRE(n_bnd > 0 && n_bnd <= n_nodes, "n_bnd out of range");
+    REQUIRE(expected_kernel_dim >= -1, "expected_kernel_dim must be >= -1");
+    if ((int)ctx->pats.size() >= MAXP) throw Error(FETIRP_EINVAL, "at most 16 patterns per context");
+    auto P = std::make_unique<PatternData>();
+    P->n_nodes = n_nodes; P->dpn = dpn; P->n = n_nodes * dpn; P->expected = expected_kernel_dim;
+    const int n = P->n;
+    REQUIRE(rowptr[0] == 0, "rowptr[0] must be 0");
+    for (int i = 0; i < n; ++i) REQUIRE(rowptr[i + 1] >= rowptr[i], "rowptr must be non-decreasing");
+    const int64_t nnz = rowptr[n];
+    P->rowptr.assign(rowptr, rowptr + n + 1);
+    P->col.assign(col, col + nnz);
+    P->val.assign(val, val + nnz);
+    for (int64_t e = 0; e < nnz; ++e) {
+      REQUIRE(col[e] >= 0 && col[e] < n, "column index out of range");
+      REQUIRE(std::isfinite(val[e]), "non-finite stiffness value");
+    }
+    P->bpos.assign(n_nodes, -1);
+    for (int b = 0; b < n_bnd; ++b) {
+      REQUIRE(bnd_nodes[b] >= 0 && bnd_nodes[b] < n_nodes, "boundary node out of range");
+      REQUIRE(P->bpos[bnd_nodes[b]] < 0, "duplicate boundary node");
+      P->bpos[bnd_nodes[b]] = b;
+    }
+    P->bnd_nodes.assign(bnd_nodes, bnd_nodes + n_bnd);
+    P->n_b = n_bnd * dpn;
+    P->n_i = n - P->n_b;
+    P->newidx.assign(n, -1);
+    P->oldidx.assign(n, -1);
+    int next = 0;
+    for (int node = 0; node < n_nodes; ++node)
+      if (P->bpos[node] < 0)
+        for (int c = 0; c < dpn; ++c) { P->newidx[node * dpn + c] = next; P->oldidx[next] = node * dpn + c; ++next; }
+    for (int b = 0; b < n_bnd; ++b)
+      for (int c = 0; c < dpn; ++c) {
+        const int old = bnd_nodes[b] * dpn + c;
+        P->newidx[old] = next; P->oldidx[next] = old; ++next;
+      }
+    P->npad = (int)round_up(n, TILE);
+    P->nbpad = (int)round_up(P->n_b, TILE);
+    const int nt = P->npad / TILE;
+    std::vector<uint8_t> nz((size_t)nt * nt, 0);
+    for (int i = 0; i < n; ++i)
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        int a = P->newidx[i] / TILE, b = P->newidx[col[e]] / TILE;
+        nz[(size_t)std::max(a, b) * nt + std::min(a, b)] = 1;
+      }
+    P->plan.build(nt, nz);
+    P->plan.upload(ctx->stream);
+    P->planS = dense_plan(P->nbpad / TILE);
+    P->planS.upload(ctx->stream);
+    P->d_rowptr.upload(P->rowptr, ctx->stream);
+    P->d_col.upload(P->col, ctx->stream);
+    P->d_val.upload(P->val, ctx->stream);
+    P->d_newidx.upload(P->newidx, ctx->stream);
+    factorize_pattern(ctx, *P);
+    *pattern_id = (int)ctx->pats.size();
+    ctx->pats.push_back(std::move(P));
+    invalidate(ctx);
+    return FETIRP_OK;
+  });
+}
+
+fetirp_status fetirp_add_occurrence(fetirp_ctx ctx, int32_t pattern_id, const double* rot, int32_t n_links,
+                                    const int32_t* local_node, const int8_t* global_comp, const int32_t* lambda_row,
+                                    const int8_t* sign, const double* f_global, int32_t* occ_id) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    REQUIRE(pattern_id >= 0 && pattern_id < (int)ctx->pats.size(), "unknown pattern id");
+    REQUIRE(n_links >= 0, "n_links < 0");
+    REQUIRE(occ_id && f_global, "NULL argument");
+    REQUIRE(n_links == 0 || (local_node && global_comp && lambda_row && sign), "NULL link array");
+    const PatternData& P = *ctx->pats[pattern_id];
+    OccData O;
+    O.pattern = pattern_id;
+    if (rot) {
+      int det = 0;
+      for (int r = 0; r < 3; ++r) {
+        int nzc = 0;
+        for (int c = 0; c < 3; ++c) {
+          const double v = rot[3 * r + c];
+          REQUIRE(v == 0.0 || v == 1.0 || v == -1.0, "rotation must be a signed permutation (90-degree steps)");
+          if (v != 0.0) ++nzc;
+          O.R[3 * r + c] = (int)v;
+        }
+        REQUIRE(nzc == 1, "rotation must be a signed permutation (90-degree steps)");
+      }
+      const int* R = O.R;
+      det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) + R[2] * (R[3] * R[7] - R[4] * R[6]);
+      REQUIRE(det == 1, "rotation must have determinant +1");
+      if (P.dpn > 1)
+        for (int c = 0; c < P.dpn; ++c)
+          for (int c2 = P.dpn; c2 < 3; ++c2)
+            REQUIRE(O.R[3 * c + c2] == 0, "rotation mixes a modelled component with an absent one");
+    }
+    if (P.dpn == 1) { const int I[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}; std::memcpy(O.R, I, sizeof(I)); }
+    O.link_j.resize(n_links);
+    O.link_row.resize(n_links);
+    O.link_sign.resize(n_links);
+    for (int i = 0; i < n_links; ++i) {
+      REQUIRE(local_node[i] >= 0 && local_node[i] < P.n_nodes, "link node out of range");
+      REQUIRE(P.bpos[local_node[i]] >= 0, "link on a node that is not a boundary node of the pattern");
+      REQUIRE(global_comp[i] >= 0 && global_comp[i] < P.dpn, "link component out of range");
+      REQUIRE(sign[i] == 1 || sign[i] == -1, "link sign must be +1 or -1");
+      REQUIRE(lambda_row[i] >= 0, "negative lambda_row");
+      const int c = global_comp[i];
+      int c2 = 0, rs = 1;
+      if (P.dpn > 1)
+        for (int cc = 0; cc < P.dpn; ++cc)
+          if (O.R[3 * c + cc] != 0) { c2 = cc; rs = O.R[3 * c + cc]; }
+      O.link_j[i] = P.bpos[local_node[i]] * P.dpn + c2;
+      O.link_row[i] = lambda_row[i];
+      O.link_sign[i] = (int8_t)(sign[i] * rs);
+    }
+    // f in the pattern frame: f_l = R^T f_g per node
+    O.f_local.assign(P.n, 0.0);
+    for (int node = 0; node < P.n_nodes; ++node)
+      for (int c2 = 0; c2 < P.dpn; ++c2) {
+        double v = 0.0;
+        for (int c = 0; c < P.dpn; ++c) {
+          const double fg = f_global[node * P.dpn + c];
+          REQUIRE(std::isfinite(fg), "non-finite load");
+          v += (P.dpn > 1 ? O.R[3 * c + c2] : (c == c2 ? 1 : 0)) * fg;
+        }
+        O.f_local[node * P.dpn + c2] = v;
+      }
+    *occ_id = (int)ctx->occs.size();
+    ctx->occs.push_back(std::move(O));
+    invalidate(ctx);
+    return FETIRP_OK;
+  });
+}
+
+fetirp_status fetirp_set_groups(fetirp_ctx ctx, int32_t k, const int32_t* group_of_occ) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    REQUIRE(k >= 1 && k <= 64, "k must be in 1..64");
+    REQUIRE(group_of_occ, "NULL groups");
+    const int n = (int)ctx->occs.size();
+    for (int o = 0; o < n; ++o) REQUIRE(group_of_occ[o] >= 0 && group_of_occ[o] < k, "group id out of range");
+    ctx->k_user = k;
+    ctx->groups_user.assign(group_of_occ, group_of_occ + n);
+    invalidate(ctx);
+    return FETIRP_OK;
+  });
+}
+
+fetirp_status fetirp_prepare(fetirp_ctx ctx, int64_t n_lambda, const double* c) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    if (c)
+      for (int64_t i = 0; i < n_lambda; ++i) REQUIRE(std::isfinite(c[i]), "non-finite c");
+    prepare_timed(ctx, n_lambda, c, nullptr);
+    return FETIRP_OK;
+  });
+}
+
+fetirp_status fetirp_solve(fetirp_ctx ctx, int64_t n_lambda, const double* c, double* lambda_out, double* u_out,
+                           fetirp_stats* stats) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    REQUIRE(lambda_out && u_out, "NULL output");
+    if (c)
+      for (int64_t i = 0; i < n_lambda; ++i) REQUIRE(std::isfinite(c[i]), "non-finite c");
+    prepare_timed(ctx, n_lambda, c, nullptr);
+    DBuf<double> dl(n_lambda), du(ctx->n_u);
+    fetirp_status st = run_solve(ctx, dl.p, du.p, stats);
+    FETIRP_CUDA(cudaMemcpyAsync(lambda_out, dl.p, sizeof(double) * n_lambda, cudaMemcpyDeviceToHost, ctx->stream));
+    FETIRP_CUDA(cudaMemcpyAsync(u_out, du.p, sizeof(double) * ctx->n_u, cudaMemcpyDeviceToHost, ctx->stream));
+    FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
+    return st;
+  });
+}
+
+fetirp_status fetirp_solve_device(fetirp_ctx ctx, int64_t n_lambda, const double* d_c, double* d_lambda,
+                                  double* d_u, fetirp_stats* stats) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    REQUIRE(d_lambda && d_u, "NULL output");
+    prepare_timed(ctx, n_lambda, nullptr, d_c);
+    return run_solve(ctx, d_lambda, d_u, stats);
+  });
+}
+
+fetirp_status fetirp_apply_block_device(fetirp_ctx ctx, int32_t k, const double* d_V, double* d_Q, int32_t precision) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    if (!ctx->prepared) throw Error(FETIRP_ESTATE, "call fetirp_prepare or fetirp_solve first");
+    REQUIRE(k >= 1 && k <= 64, "k must be in 1..64");
+    REQUIRE(d_V && d_Q, "NULL buffer");
+    REQUIRE(precision >= FETIRP_PREC_FP64 && precision <= FETIRP_PREC_TF32X3, "unsupported precision");
+    apply_F(ctx, d_V, d_Q, k, precision, true, true);
+    return FETIRP_OK;
+  });
+}
+
+fetirp_status fetirp_apply_block(fetirp_ctx ctx, int32_t k, const double* V, double* Q, int32_t precision) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    if (!ctx->prepared) throw Error(FETIRP_ESTATE, "call fetirp_prepare or fetirp_solve first");
+    REQUIRE(k >= 1 && k <= 64, "k must be in 1..64");
+    REQUIRE(V && Q, "NULL buffer");
+    REQUIRE(precision >= FETIRP_PREC_FP64 && precision <= FETIRP_PREC_TF32X3, "unsupported precision");
+    const size_t n = (size_t)ctx->L.n_lambda * k;
+    DBuf<double> dv(n), dq(n);
+    dv.upload(V, n, ctx->stream);
+    apply_F(ctx, dv.p, dq.p, k, precision, true, true);
+    check_tc_error(ctx);
+    FETIRP_CUDA(cudaMemcpyAsync(Q, dq.p, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
+    return FETIRP_OK;
+  });
+}
+
+fetirp_status fetirp_factorize(fetirp_ctx ctx) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    reset_phases(ctx);
+    const unsigned long long l0 = g_launch_count;
+    for (auto& P : ctx->pats) factorize_pattern(ctx, *P);
+    ctx->phases_pending = true;
+    ctx->pending_launches = (long long)(g_launch_count - l0);
+    invalidate(ctx);
+    return FETIRP_OK;
+  });
+}
+
+fetirp_status fetirp_get_pattern(fetirp_ctx ctx, int32_t pid, int32_t* n_b_out, int32_t* kdim_out, double* splus,
+                                 double* kernel) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    REQUIRE(pid >= 0 && pid < (int)ctx->pats.size(), "unknown pattern id");
+    PatternData& P = *ctx->pats[pid];
+    if (n_b_out) *n_b_out = P.n_b;
+    if (kdim_out) *kdim_out = P.kdim;
+    if (splus)
+      FETIRP_CUDA(cudaMemcpyAsync(splus, P.S64.p, sizeof(double) * (size_t)P.n_b * P.n_b, cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    if (kernel && P.kdim > 0) {
+      std::vector<double> N((size_t)P.npad * P.kdim);
+      FETIRP_CUDA(cudaMemcpyAsync(N.data(), P.N.p, sizeof(double) * N.size(), cudaMemcpyDeviceToHost, ctx->stream));
+      FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
+      for (int d = 0; d < P.n; ++d)
+        for (int m = 0; m < P.kdim; ++m) kernel[(size_t)d * P.kdim + m] = N[(size_t)m * P.npad + P.newidx[d]];
+    }
+    FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
+    return FETIRP_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// Dense FP64 building blocks of the pattern set-up (once per pattern; not the per-iteration hot path).
+#pragma once
+#include "common.cuh"
+
+namespace fetirp {
+
+constexpr int TILE = 64;
+
+// Tile-level structure of a lower-triangular factor stored densely (column-major, ld = npad = nt * TILE).
+// nz[I * nt + J] (I >= J) says whether tile (I, J) of L can be nonzero after fill-in.  The per-step work lists
+// of the right-looking factorisation are kept on the device so that refactorisation needs no host work.
+struct TilePlan {
+  int nt = 0;
+  std::vector<uint8_t> nz;            // nt * nt
+  std::vector<int> col_rows;          // for column J: rows I > J with nz(I, J), concatenated
+  std::vector<int> col_off;           // nt + 1
+  std::vector<int> row_cols;          // for row I: columns J < I with nz(I, J) (backward-solve lists)
+  std::vector<int> row_off;           // nt + 1
+  std::vector<int2> pairs;            // for step k: (I, J) with I >= J > k, nz(I,k) && nz(J,k)
+  std::vector<int> pair_off;          // nt + 1
+  DBuf<int> d_col_rows, d_row_cols;
+  DBuf<int2> d_pairs;
+  void build(int nt_, const std::vector<uint8_t>& nz0);   // symbolic factorisation (fill) + lists
+  void upload(cudaStream_t s);
+};
+
+// A <- L (lower, in place) with zero-pivot detection: a pivot p_j <= tol * diag0[j] (or not finite) marks
+// dof j as a zero pivot: zp[j] = 1 and column j of L is set to 0.  diag0 holds the diagonal before
+// factorisation.  Rows of zero-pivot dofs are zeroed at the end, so L is the Cholesky factor of the
+// nonsingular block K_rr embedded with zeros (the generalized inverse of Sec. 2).
+void chol_tiles(double* A, int npad, const TilePlan& plan, const double* diag0, int* zp, double tol,
+                cudaStream_t s);
+
+// X <- L^{-1} X (trans = false) or X <- L^{-T} X (trans = true), X column-major npad x nrhs (ld = ldx),
+// zero-pivot rows of the result set to 0.  Right-looking over tile columns, skipping zero tiles.
+void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, double* X, int ldx, int nrhs,
+               bool trans, cudaStream_t s);
+
+// C(m, n) = alpha * sum_k A(m, k) B(k, n) + beta * C(m, n) with arbitrary element strides:
+// A(m, k) = A[m * sAm + k * sAk], B(k, n) = B[k * sBk + n * sBn], C(m, n) = C[m * sCm + n * sCn].
+// FP64 arithmetic.  Generic (set-up and small coarse products).
+void gemm_f64(int M, int N, int K, double alpha, const double* A, long long sAm, long long sAk,
+              const double* B, long long sBk, long long sBn, double beta, double* C, long long sCm,
+              long long sCn, cudaStream_t s);
+
+void copy_diag(const double* A, int npad, double* diag, cudaStream_t s);
+void zero_zp_rows(double* A, int npad, const int* zp, cudaStream_t s);
+
+}  // namespace fetirp

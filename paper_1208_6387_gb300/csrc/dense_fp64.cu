@@ -1,0 +1,368 @@
+// Dense FP64 tile kernels of the pattern set-up: Cholesky with zero-pivot detection (Sec. 2, floating
+// subdomains), right-looking multi-right-hand-side triangular solves and a strided generic GEMM.
+#include "dense.cuh"
+
+namespace fetirp {
+
+// ------------------------------------------------------------------------------------------------ plan
+void TilePlan::build(int nt_, const std::vector<uint8_t>& nz0) {
+  nt = nt_;
+  nz = nz0;
+  col_rows.clear(); col_off.assign(nt + 1, 0);
+  pairs.clear(); pair_off.assign(nt + 1, 0);
+  for (int k = 0; k < nt; ++k) {
+    nz[(size_t)k * nt + k] = 1;
+    col_off[k] = (int)col_rows.size();
+    std::vector<int> rows;
+    for (int I = k + 1; I < nt; ++I)
+      if (nz[(size_t)I * nt + k]) rows.push_back(I);
+    for (int I : rows) col_rows.push_back(I);
+    pair_off[k] = (int)pairs.size();
+    // fill-in: (I, J) becomes nonzero when both (I, k) and (J, k) are
+    for (size_t a = 0; a < rows.size(); ++a)
+      for (size_t b = 0; b <= a; ++b) {
+        int I = rows[a], J = rows[b];
+        nz[(size_t)I * nt + J] = 1;
+        pairs.push_back(make_int2(I, J));
+      }
+  }
+  col_off[nt] = (int)col_rows.size();
+  pair_off[nt] = (int)pairs.size();
+  row_cols.clear(); row_off.assign(nt + 1, 0);
+  for (int I = 0; I < nt; ++I) {
+    row_off[I] = (int)row_cols.size();
+    for (int J = 0; J < I; ++J)
+      if (nz[(size_t)I * nt + J]) row_cols.push_back(J);
+  }
+  row_off[nt] = (int)row_cols.size();
+}
+
+void TilePlan::upload(cudaStream_t s) {
+  d_col_rows.upload(col_rows, s);
+  d_row_cols.upload(row_cols, s);
+  d_pairs.upload(pairs, s);
+}
+
+// ------------------------------------------------------------------------------------------------ kernels
+__global__ void k_copy_diag(const double* A, int npad, double* diag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < npad) diag[i] = A[(size_t)i * npad + i];
+}
+
+__global__ void k_zero_zp_rows(double* A, int npad, const int* zp) {
+  int j = blockIdx.x;                 // row
+  if (!zp[j]) return;
+  for (int c = threadIdx.x; c < npad; c += blockDim.x) A[(size_t)c * npad + j] = 0.0;
+}
+
+// Factor the diagonal tile k in place (one CTA, 256 threads).
+__global__ void __launch_bounds__(256) k_potrf_tile(double* A, int npad, int k, const double* diag0, int* zp,
+                                                    double tol) {
+  __shared__ double a[TILE][TILE + 1];   // a[row][col]
+  const int tid = threadIdx.x;
+  double* T = A + (size_t)k * TILE * npad + (size_t)k * TILE;
+  for (int idx = tid; idx < TILE * TILE; idx += 256) {
+    int r = idx % TILE, c = idx / TILE;
+    a[r][c] = T[(size_t)c * npad + r];
+  }
+  __syncthreads();
+  for (int j = 0; j < TILE; ++j) {
+    const int gj = k * TILE + j;
+    const double d = a[j][j];
+    const bool zero = !(d > tol * diag0[gj]);   // also catches NaN and negative roundoff
+    __syncthreads();
+    if (zero) {
+      for (int r = j + tid; r < TILE; r += 256) a[r][j] = 0.0;
+      if (tid == 0) zp[gj] = 1;
+    } else {
+      const double l = sqrt(d);
+      const double inv = 1.0 / l;
+      for (int r = j + tid; r < TILE; r += 256) a[r][j] = (r == j) ? l : a[r][j] * inv;
+      if (tid == 0) zp[gj] = 0;
+    }
+    __syncthreads();
+    const int w = TILE - 1 - j;        // trailing columns j+1 .. TILE-1, rows >= column
+    for (int idx = tid; idx < w * TILE; idx += 256) {
+      int c = j + 1 + idx / TILE, r = idx % TILE;
+      if (r >= c) a[r][c] -= a[r][j] * a[c][j];
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < TILE * TILE; idx += 256) {
+    int r = idx % TILE, c = idx / TILE;
+    T[(size_t)c * npad + r] = (r >= c) ? a[r][c] : 0.0;
+  }
+}
+
+// For step k: tiles (I, k), I in rows[0..cnt): L_Ik = A_Ik L_kk^{-T} (zero-pivot columns -> 0).
+__global__ void __launch_bounds__(256) k_trsm_tiles(double* A, int npad, int k, const int* rows, const int* zp) {
+  __shared__ double l[TILE][TILE + 1];
+  __shared__ double x[TILE][TILE + 1];
+  const int tid = threadIdx.x;
+  const int I = rows[blockIdx.x];
+  const double* D = A + (size_t)k * TILE * npad + (size_t)k * TILE;
+  double* X = A + (size_t)k * TILE * npad + (size_t)I * TILE;
+  for (int idx = tid; idx < TILE * TILE; idx += 256) {
+    int r = idx % TILE, c = idx / TILE;
+    l[r][c] = D[(size_t)c * npad + r];
+    x[r][c] = X[(size_t)c * npad + r];
+  }
+  __syncthreads();
+  for (int j = 0; j < TILE; ++j) {
+    const bool zero = zp[k * TILE + j] != 0;
+    if (tid < TILE) x[tid][j] = zero ? 0.0 : x[tid][j] / l[j][j];
+    __syncthreads();
+    const int w = TILE - 1 - j;
+    for (int idx = tid; idx < w * TILE; idx += 256) {
+      int c = j + 1 + idx / TILE, r = idx % TILE;
+      x[r][c] -= x[r][j] * l[c][j];
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < TILE * TILE; idx += 256) {
+    int r = idx % TILE, c = idx / TILE;
+    X[(size_t)c * npad + r] = x[r][c];
+  }
+}
+
+// For step k: A_IJ -= L_Ik L_Jk^T for each pair (I, J).  64x64 output per CTA, 4x4 per thread.
+__global__ void __launch_bounds__(256) k_update_pairs(double* A, int npad, int k, const int2* pairs) {
+  __shared__ double sa[16][TILE + 1];   // [kk][row]
+  __shared__ double sb[16][TILE + 1];
+  const int tid = threadIdx.x;
+  const int2 pr = pairs[blockIdx.x];
+  const int I = pr.x, J = pr.y;
+  const double* LI = A + (size_t)k * TILE * npad + (size_t)I * TILE;
+  const double* LJ = A + (size_t)k * TILE * npad + (size_t)J * TILE;
+  const int tx = tid % 16, ty = tid / 16;     // rows ty*4.., cols tx*4..
+  double acc[4][4] = {};
+  for (int kk0 = 0; kk0 < TILE; kk0 += 16) {
+    for (int idx = tid; idx < 16 * TILE; idx += 256) {
+      int r = idx % TILE, kk = idx / TILE;
+      sa[kk][r] = LI[(size_t)(kk0 + kk) * npad + r];
+      sb[kk][r] = LJ[(size_t)(kk0 + kk) * npad + r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { av[q] = sa[kk][ty * 4 + q]; bv[q] = sb[kk][tx * 4 + q]; }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(av[p], bv[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+  double* C = A + (size_t)J * TILE * npad + (size_t)I * TILE;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) C[(size_t)(tx * 4 + q) * npad + ty * 4 + p] -= acc[p][q];
+}
+
+// Triangular solve on one diagonal tile J for a chunk of 64 right-hand sides (blockIdx.x).
+__global__ void __launch_bounds__(256) k_tri_diag(const double* L, int npad, int J, const int* zp, double* X,
+                                                  int ldx, int nrhs, int trans) {
+  __shared__ double l[TILE][TILE + 1];
+  __shared__ double x[TILE][TILE + 1];   // x[row][rhs]
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * TILE;
+  const double* D = L + (size_t)J * TILE * npad + (size_t)J * TILE;
+  for (int idx = tid; idx < TILE * TILE; idx += 256) {
+    int r = idx % TILE, c = idx / TILE;
+    l[r][c] = D[(size_t)c * npad + r];
+    x[r][c] = (c0 + c < nrhs) ? X[(size_t)(c0 + c) * ldx + (size_t)J * TILE + r] : 0.0;
+  }
+  __syncthreads();
+  if (!trans) {
+    for (int j = 0; j < TILE; ++j) {
+      const bool zero = zp[J * TILE + j] != 0;
+      if (tid < TILE) x[j][tid] = zero ? 0.0 : x[j][tid] / l[j][j];
+      __syncthreads();
+      for (int idx = tid; idx < (TILE - 1 - j) * TILE; idx += 256) {
+        int r = j + 1 + idx / TILE, c = idx % TILE;
+        x[r][c] -= l[r][j] * x[j][c];
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int j = TILE - 1; j >= 0; --j) {
+      const bool zero = zp[J * TILE + j] != 0;
+      if (tid < TILE) x[j][tid] = zero ? 0.0 : x[j][tid] / l[j][j];
+      __syncthreads();
+      for (int idx = tid; idx < j * TILE; idx += 256) {
+        int r = idx / TILE, c = idx % TILE;   // rows r < j
+        x[r][c] -= l[j][r] * x[j][c];
+      }
+      __syncthreads();
+    }
+  }
+  for (int idx = tid; idx < TILE * TILE; idx += 256) {
+    int r = idx % TILE, c = idx / TILE;
+    if (c0 + c < nrhs) X[(size_t)(c0 + c) * ldx + (size_t)J * TILE + r] = x[r][c];
+  }
+}
+
+// After solving tile J: X_I -= L_IJ X_J (forward, I in list) or X_I -= L_JI^T X_J (backward, I in list).
+// grid (list count, rhs chunks).
+__global__ void __launch_bounds__(256) k_tri_update(const double* L, int npad, int J, const int* list, double* X,
+                                                    int ldx, int nrhs, int trans) {
+  __shared__ double sa[16][TILE + 1];   // [kk][row of output]
+  __shared__ double sb[16][TILE + 1];   // [kk][rhs]
+  const int tid = threadIdx.x;
+  const int I = list[blockIdx.x];
+  const int c0 = blockIdx.y * TILE;
+  const int tx = tid % 16, ty = tid / 16;
+  double acc[4][4] = {};
+  for (int kk0 = 0; kk0 < TILE; kk0 += 16) {
+    for (int idx = tid; idx < 16 * TILE; idx += 256) {
+      int r = idx % TILE, kk = idx / TILE;
+      // A(r, kk) = L_IJ(r, kk) or L_JI(kk, r)
+      if (!trans) sa[kk][r] = L[(size_t)(J * TILE + kk0 + kk) * npad + I * TILE + r];
+      else sa[kk][r] = L[(size_t)(I * TILE + r) * npad + J * TILE + kk0 + kk];
+      int c = idx % TILE, k2 = idx / TILE;
+      sb[k2][c] = (c0 + c < nrhs) ? X[(size_t)(c0 + c) * ldx + (size_t)J * TILE + kk0 + k2] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { av[q] = sa[kk][ty * 4 + q]; bv[q] = sb[kk][tx * 4 + q]; }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(av[p], bv[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int c = c0 + tx * 4 + q;
+    if (c < nrhs) {
+#pragma unroll
+      for (int p = 0; p < 4; ++p) X[(size_t)c * ldx + (size_t)I * TILE + ty * 4 + p] -= acc[p][q];
+    }
+  }
+}
+
+// Generic strided GEMM, 64x64 output tile per CTA, 4x4 per thread, FP64.
+__global__ void __launch_bounds__(256) k_gemm_f64(int M, int N, int K, double alpha, const double* __restrict__ A,
+                                                  long long sAm, long long sAk, const double* __restrict__ B,
+                                                  long long sBk, long long sBn, double beta, double* C,
+                                                  long long sCm, long long sCn) {
+  __shared__ double sa[16][TILE + 1];
+  __shared__ double sb[16][TILE + 1];
+  const int tid = threadIdx.x;
+  const int m0 = blockIdx.x * TILE, n0 = blockIdx.y * TILE;
+  const int tx = tid % 16, ty = tid / 16;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int idx = tid; idx < 16 * TILE; idx += 256) {
+      int r, kk;
+      if (sAk == 1) { kk = idx % 16; r = idx / 16; } else { r = idx % TILE; kk = idx / TILE; }
+      int m = m0 + r, k = k0 + kk;
+      sa[kk][r] = (m < M && k < K) ? A[m * sAm + k * sAk] : 0.0;
+      int c, k2;
+      if (sBk == 1) { k2 = idx % 16; c = idx / 16; } else { c = idx % TILE; k2 = idx / TILE; }
+      int n = n0 + c, kb = k0 + k2;
+      sb[k2][c] = (n < N && kb < K) ? B[kb * sBk + n * sBn] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { av[q] = sa[kk][ty * 4 + q]; bv[q] = sb[kk][tx * 4 + q]; }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(av[p], bv[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    int m = m0 + ty * 4 + p;
+    if (m >= M) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int n = n0 + tx * 4 + q;
+      if (n >= N) continue;
+      double* c = C + m * sCm + n * sCn;
+      *c = alpha * acc[p][q] + (beta == 0.0 ? 0.0 : beta * *c);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------ host
+void copy_diag(const double* A, int npad, double* diag, cudaStream_t s) {
+  k_copy_diag<<<ceil_div(npad, 256), 256, 0, s>>>(A, npad, diag);
+  FETIRP_LAUNCH_CHECK();
+}
+
+void zero_zp_rows(double* A, int npad, const int* zp, cudaStream_t s) {
+  k_zero_zp_rows<<<npad, 256, 0, s>>>(A, npad, zp);
+  FETIRP_LAUNCH_CHECK();
+}
+
+void chol_tiles(double* A, int npad, const TilePlan& plan, const double* diag0, int* zp, double tol,
+                cudaStream_t s) {
+  for (int k = 0; k < plan.nt; ++k) {
+    k_potrf_tile<<<1, 256, 0, s>>>(A, npad, k, diag0, zp, tol);
+    FETIRP_LAUNCH_CHECK();
+    int nr = plan.col_off[k + 1] - plan.col_off[k];
+    if (nr > 0) {
+      k_trsm_tiles<<<nr, 256, 0, s>>>(A, npad, k, plan.d_col_rows.p + plan.col_off[k], zp);
+      FETIRP_LAUNCH_CHECK();
+    }
+    int np = plan.pair_off[k + 1] - plan.pair_off[k];
+    if (np > 0) {
+      k_update_pairs<<<np, 256, 0, s>>>(A, npad, k, plan.d_pairs.p + plan.pair_off[k]);
+      FETIRP_LAUNCH_CHECK();
+    }
+  }
+  zero_zp_rows(A, npad, zp, s);
+}
+
+void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, double* X, int ldx, int nrhs,
+               bool trans, cudaStream_t s) {
+  if (nrhs <= 0) return;
+  const int chunks = ceil_div(nrhs, TILE);
+  if (!trans) {
+    for (int J = 0; J < plan.nt; ++J) {
+      k_tri_diag<<<chunks, 256, 0, s>>>(L, npad, J, zp, X, ldx, nrhs, 0);
+      FETIRP_LAUNCH_CHECK();
+      int nr = plan.col_off[J + 1] - plan.col_off[J];
+      if (nr > 0) {
+        k_tri_update<<<dim3(nr, chunks), 256, 0, s>>>(L, npad, J, plan.d_col_rows.p + plan.col_off[J], X, ldx,
+                                                      nrhs, 0);
+        FETIRP_LAUNCH_CHECK();
+      }
+    }
+  } else {
+    for (int J = plan.nt - 1; J >= 0; --J) {
+      k_tri_diag<<<chunks, 256, 0, s>>>(L, npad, J, zp, X, ldx, nrhs, 1);
+      FETIRP_LAUNCH_CHECK();
+      int nr = plan.row_off[J + 1] - plan.row_off[J];
+      if (nr > 0) {
+        k_tri_update<<<dim3(nr, chunks), 256, 0, s>>>(L, npad, J, plan.d_row_cols.p + plan.row_off[J], X, ldx,
+                                                      nrhs, 1);
+        FETIRP_LAUNCH_CHECK();
+      }
+    }
+  }
+}
+
+void gemm_f64(int M, int N, int K, double alpha, const double* A, long long sAm, long long sAk, const double* B,
+              long long sBk, long long sBn, double beta, double* C, long long sCm, long long sCn,
+              cudaStream_t s) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid(ceil_div(M, TILE), ceil_div(N, TILE));
+  k_gemm_f64<<<grid, 256, 0, s>>>(M, N, K, alpha, A, sAm, sAk, B, sBk, sBn, beta, C, sCm, sCn);
+  FETIRP_LAUNCH_CHECK();
+}
+
+}  // namespace fetirp

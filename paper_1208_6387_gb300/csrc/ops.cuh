@@ -1,0 +1,101 @@
+// Device layout of one structure and the interface operators of the hot path.
+#pragma once
+#include "common.cuh"
+
+namespace fetirp {
+
+constexpr int MAXP = 16;   // patterns per structure handled by one launch
+
+// Per-pattern view of a block of local vectors: element (occurrence q of the pattern, column g, boundary
+// dof j) lives at base[(q * k + g) * ld + off + j].  Used for Y (gathered traces) and Z (local solutions).
+template <typename T>
+struct PatView {
+  T* base[MAXP];
+  long long ld[MAXP];
+  long long off[MAXP];
+};
+
+// Structure layout on the device (built once per structure).  "Slot" = (occurrence s, boundary dof j),
+// slot = obase[s] + j.  Links are folded into the pattern frame (rotation sign included).
+struct Layout {
+  int n_lambda = 0, n_occ = 0, n_slots = 0, n_G = 0, n_pat = 0, k = 1;
+  // gather CSR by slot: entries (row, sign)
+  const int* slot_ptr;
+  const int* slot_row;
+  const int8_t* slot_sign;
+  // scatter by row: up to two (slot, sign); sign 0 = empty
+  const int* row_slot;
+  const int8_t* row_sign;
+  const int* slot_occ;   // slot -> occurrence
+  // occurrence tables
+  const int* occ_obase;  // n_occ + 1
+  const int* occ_pat;
+  const int* occ_q;      // index among the pattern's occurrences
+  const int* occ_gofs;   // first coarse column of the occurrence
+  const int* occ_group;  // multivector column
+  // pattern tables (indexed by pattern)
+  const double* Nb[MAXP];   // n_b x kdim row-major: kernel restricted to the boundary (pattern frame)
+  int n_b[MAXP];
+  int kdim[MAXP];
+};
+
+// ---- coarse space G = [ ... B(s) N(s) ... ] (Eq. 3) ------------------------------------------------
+// X[gofs(s) + m][g] = sum over links (row, sign) of s: sign * Nb[j][m] * V[row][g]   (X = G^T V)
+void gt_v(const Layout& L, const double* V, int k, double* X, cudaStream_t s);
+// out[row][g] = beta * out[row][g] + alpha * (G A)[row][g]
+void g_apply(const Layout& L, const double* A, int k, double alpha, double beta, double* out, cudaStream_t s);
+// dense G^T G (n_G x n_G, row-major), nb_ptr/nb_list: neighbour occurrences of every occurrence
+void gtg_dense(const Layout& L, const int* nb_ptr, const int* nb_list, int n_pairs, const int* pair_s,
+               const int* pair_t, double* GtG, cudaStream_t s);
+
+// ---- gather / scatter (Eq. 7 blocked storage, signed Boolean assembly) -------------------------------
+// Y[(q * k + g) * ld + off + j] = beta * Y[...] + alpha * sum over links of slot (s, j): sign * V[row][g]
+template <typename TO>
+void gather(const Layout& L, const double* V, int k, const PatView<TO>& Y, cudaStream_t s, double alpha = 1.0,
+            double beta = 0.0);
+// As gather, FP32 result split into a tf32 pair (hi = tf32(y), lo = y - hi) for the tensor-core product.
+// Yh and Yl share leading dimensions and offsets.
+void gather_split(const Layout& L, const double* V, int k, const PatView<float>& Yh, const PatView<float>& Yl,
+                  cudaStream_t s);
+// out[row][g] = beta * out[row][g] + sum over the row's slots: sign * Z(slot, g)
+template <typename TI>
+void scatter(const Layout& L, const PatView<TI>& Z, int k, double beta, double* out, cudaStream_t s);
+
+// ---- multivector split (occurrence share of the residual) ------------------------------------------
+// Z[row][g] = sum over the row's occurrences s with group(s) = g: r[row] / (number of occurrences in row)
+void split(const Layout& L, const double* r, int k, double* Z, cudaStream_t s);
+
+// ---- local products Z_p = S_p^+ Y_p ----------------------------------------------------------------
+// FP64 (DFMA) and FP32 (FFMA) SIMT forms; one launch for every pattern.
+struct LocalProblem {
+  const void* S[MAXP];    // n_b x n_b row-major (symmetric)
+  int n_b[MAXP];
+  int n_rhs[MAXP];        // n_occ_p * k
+  long long ld[MAXP];     // leading dimension of Y_p / Z_p (>= n_b)
+  const void* Y[MAXP];
+  void* Z[MAXP];
+  int n_pat;
+};
+void local_gemm_f64(const LocalProblem& P, cudaStream_t s);
+void local_gemm_f32(const LocalProblem& P, cudaStream_t s);
+
+// ---- block Gram products and the F-normalised update (numerical-issues subsection) -----------------
+// C (a x b, row-major) = A^T B, A n x a (ld lda), B n x b (ld ldb), FP64 accumulation over n in a fixed
+// order (two passes: per-chunk partials, then an ordered sum).
+void gram_f64(int n, int a, int b, const double* A, int lda, const double* B, int ldb, double* C,
+              DBuf<double>& partial, cudaStream_t s);
+// Normalisation of eta = W^T P~ (k x k row-major) so that T^T eta T = I on the kept directions: pivoted
+// Cholesky eta = Pi M M^T Pi^T, stopping when the largest remaining pivot <= trunc * (largest diagonal);
+// T = Pi M^{-T} on the kept columns (zero columns for dropped ones); alpha = T^T wr with wr = W^T r.
+// One CTA, k <= 64.
+void normalise(int k, const double* eta, const double* wr, double trunc, double* T, double* alpha, int* n_kept,
+               cudaStream_t s);
+// Wn = W T, Qn = Q T (n x k each, written to history), lambda += Wn alpha, r -= Qn alpha, and
+// rr_partial[block] = partial sums of r^2 after the update.
+void update(int n, int k, const double* W, const double* Q, const double* T, const double* alpha,
+            double* Wn, double* Qn, long long ldn, double* lam, double* r, double* rr_partial, int rr_blocks,
+            cudaStream_t s);
+void sum_sq(int n, const double* x, double* out_partial, int blocks, cudaStream_t s);
+void axpy_f64(int n, double a, const double* x, double* y, cudaStream_t s);
+
+}  // namespace fetirp

@@ -1,0 +1,359 @@
+// Tensor-core local products Z_p = S_p^+ Y_p on sm_103a: tcgen05.mma kind::tf32 with the accumulator in
+// TMEM, operands staged by TMA (128-byte swizzle) through a 3-stage mbarrier pipeline.
+//
+// Precision: both operands are split into tf32 pairs, x = hi + lo with hi = tf32(x) and lo = x - hi, and
+// the product is taken as hi*hi + hi*lo + lo*hi (three MMAs into one FP32 accumulator).  The dropped lo*lo
+// term and the truncation of lo to tf32 leave a relative error near 2^-21 per product, close to FP32 local
+// products, which the FP64 outer refinement of the solver then removes.
+//
+// One CTA computes a 128 (rows of S^+) x 128 (right-hand sides) tile of one pattern.  Warp roles: warp 0
+// lane 0 issues TMA loads, warp 1 lane 0 issues the MMAs, all four warps drain TMEM in the epilogue.  Every
+// wait on an mbarrier is bounded: on expiry the CTA records an error code, stops issuing work, waits (again
+// bounded) for its own MMAs to retire, frees TMEM and returns.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "ops.cuh"
+#include "tc.cuh"
+
+namespace fetirp {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 32;        // BK fp32 = 128 bytes = one swizzle row
+constexpr int STAGES = 3;
+constexpr int TILE_BYTES = BM * BK * 4;           // 16 KB (A or B tile, BM == BN)
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;       // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // a bounded wait gives up after 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait; returns false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  while (now_ns() - t0 < WAIT_NS)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+  const uint64_t addr = smem_u32(p);
+  uint64_t d = 0;
+  d |= (addr >> 4) & 0x3FFFull;                 // start address
+  d |= (uint64_t)(16 >> 4) << 16;               // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                       // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                       // layout: SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: D f32, A/B tf32, both K-major, N = BN, M = BM.
+__device__ __forceinline__ uint32_t instr_desc() {
+  uint32_t d = 0;
+  d |= 1u << 4;                    // D format f32
+  d |= 2u << 7;                    // A format tf32
+  d |= 2u << 10;                   // B format tf32
+  d |= (uint32_t)(BN >> 3) << 17;  // N / 8
+  d |= (uint32_t)(BM >> 4) << 24;  // M / 16
+  return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+struct TcParams {
+  CUtensorMap a_hi[TC_MAXP], a_lo[TC_MAXP], b_hi[TC_MAXP], b_lo[TC_MAXP];
+  float* Z[TC_MAXP];
+  long long ldz[TC_MAXP];
+  int n_b[TC_MAXP];
+  int n_rhs[TC_MAXP];
+  int tiles_m[TC_MAXP];
+  int tile_off[TC_MAXP + 1];
+  int n_pat;
+  int* error;   // device flag: first failing CTA writes its code
+};
+
+}  // namespace
+
+__global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcParams P) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* n_loaded = abort_flag + 1;     // stages whose TMA loads were issued
+  volatile int* n_consumed = abort_flag + 2;   // stages whose full barrier the MMA thread observed
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int p = 0;
+  while (p + 1 < P.n_pat && (int)blockIdx.x >= P.tile_off[p + 1]) ++p;
+  const int t = blockIdx.x - P.tile_off[p];
+  const int m0 = (t % P.tiles_m[p]) * BM, n0 = (t / P.tiles_m[p]) * BN;
+  const int nk = (P.n_b[p] + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    *n_loaded = 0;
+    *n_consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {   // TMEM allocation: BN fp32 columns, by one full warp
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (kb >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) {
+        atomicCAS(P.error, 0, 1);
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      uint8_t* st = smem + s * STAGE_BYTES;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      const int kx = kb * BK;
+      tma_load_2d(&P.a_hi[p], &full[s], st, kx, m0);
+      tma_load_2d(&P.a_lo[p], &full[s], st + TILE_BYTES, kx, m0);
+      tma_load_2d(&P.b_hi[p], &full[s], st + 2 * TILE_BYTES, kx, n0);
+      tma_load_2d(&P.b_lo[p], &full[s], st + 3 * TILE_BYTES, kx, n0);
+      *n_loaded = kb + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t idesc = instr_desc();
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(&full[s], ph)) {
+        atomicCAS(P.error, 0, 2);
+        *abort_flag = 1;
+        break;
+      }
+      *n_consumed = kb + 1;
+      if (*abort_flag) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint8_t* st = smem + s * STAGE_BYTES;
+      const uint64_t ahi = smem_desc(st), alo = smem_desc(st + TILE_BYTES);
+      const uint64_t bhi = smem_desc(st + 2 * TILE_BYTES), blo = smem_desc(st + 3 * TILE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BK / 8; ++kk) {
+        const uint64_t koff = (uint64_t)((kk * 8 * 4) >> 4);   // 32 bytes per K step of 8 tf32
+        mma_tf32(tmem, ahi + koff, bhi + koff, idesc, (kb | kk) ? 1u : 0u);
+        mma_tf32(tmem, ahi + koff, blo + koff, idesc, 1u);
+        mma_tf32(tmem, alo + koff, bhi + koff, idesc, 1u);
+      }
+      mma_commit(&empty[s]);   // frees the stage once these MMAs have read it
+      ++issued;
+    }
+    mma_commit(done);          // fires when every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // epilogue: every warp waits for the accumulator, then drains its 32 TMEM lanes
+  const bool ok = mbar_wait(done, 0);
+  if (!ok) atomicCAS(P.error, 0, 3);
+  // the TMEM loads below are warp-collective: take the decision for the whole CTA
+  const bool drain = __syncthreads_and(ok && !*abort_flag) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (drain) {
+    const int row = m0 + warp * 32 + lane;
+    float* Z = P.Z[p];
+    const long long ldz = P.ldz[p];
+    const int nr = P.n_rhs[p];
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < P.n_b[p]) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int c = n0 + c0 + j;
+          if (c < nr) Z[(long long)c * ldz + row] = __uint_as_float(v[j]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  // after an abort: wait (bounded) for TMA loads that were issued but never consumed, so no copy is still
+  // writing this CTA's shared memory when it exits
+  if (threadIdx.x == 0 && *abort_flag) {
+    for (int kb = *n_consumed; kb < *n_loaded; ++kb) mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1);
+  }
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+}
+
+__global__ void k_split_tf32(const double* __restrict__ x, long long rows, long long cols, long long ld_in,
+                             float* __restrict__ hi, float* __restrict__ lo, long long ld_out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * ld_out) return;
+  const long long r = idx / ld_out, c = idx % ld_out;
+  float h = 0.f, l = 0.f;
+  if (c < cols) {
+    const float v = (float)x[r * ld_in + c];
+    uint32_t t;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
+    h = __uint_as_float(t);
+    l = v - h;
+  }
+  hi[idx] = h;
+  lo[idx] = l;
+}
+
+// ------------------------------------------------------------------------------------------------ host
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    FETIRP_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) throw Error(5, "cuTensorMapEncodeTiled unavailable");
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2D fp32 map over a row-major (rows x cols, leading dimension ld) array; box 32 (cols) x 128 (rows).
+void make_map(CUtensorMap* m, const float* base, long long rows, long long cols, long long ld) {
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 4) % 16)
+    throw Error(1, "tensor-core operand not 16-byte aligned");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {BK, 128};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(5, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+}
+
+}  // namespace
+
+void split_tf32(const double* x, long long rows, long long cols, long long ld_in, float* hi, float* lo,
+                long long ld_out, cudaStream_t s) {
+  const long long n = rows * ld_out;
+  if (n == 0) return;
+  k_split_tf32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, rows, cols, ld_in, hi, lo, ld_out);
+  FETIRP_LAUNCH_CHECK();
+}
+
+void tc_gemm_tf32x3(const TcProblem& T, int* d_error, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    FETIRP_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr = true;
+  }
+  for (int base = 0; base < T.n_pat; base += TC_MAXP) {
+    TcParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.n_pat = std::min(TC_MAXP, T.n_pat - base);
+    P.error = d_error;
+    int total = 0;
+    for (int i = 0; i < P.n_pat; ++i) {
+      const int p = base + i;
+      make_map(&P.a_hi[i], T.S_hi[p], T.n_b[p], T.n_b[p], T.lds[p]);
+      make_map(&P.a_lo[i], T.S_lo[p], T.n_b[p], T.n_b[p], T.lds[p]);
+      make_map(&P.b_hi[i], T.Y_hi[p], T.n_rhs[p], T.n_b[p], T.ldy[p]);
+      make_map(&P.b_lo[i], T.Y_lo[p], T.n_rhs[p], T.n_b[p], T.ldy[p]);
+      P.Z[i] = T.Z[p];
+      P.ldz[i] = T.ldy[p];
+      P.n_b[i] = T.n_b[p];
+      P.n_rhs[i] = T.n_rhs[p];
+      P.tiles_m[i] = ceil_div(T.n_b[p], BM);
+      P.tile_off[i] = total;
+      total += P.tiles_m[i] * ceil_div(T.n_rhs[p], BN);
+    }
+    P.tile_off[P.n_pat] = total;
+    if (total == 0) continue;
+    k_tc_gemm<<<total, 128, SMEM_BYTES, s>>>(P);
+    FETIRP_LAUNCH_CHECK();
+  }
+}
+
+}  // namespace fetirp

@@ -1,0 +1,243 @@
+"""Thin Python binding of include/fetirp.h (ctypes): the same entry points, argument marshalling only.
+
+Every step of the method runs in libfetirp.so on the GPU.  There is no CPU fallback: importing works without
+a GPU (so the exported symbols can be checked), but every call needs the compiled library and a CUDA device,
+and fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libfetirp.so")
+
+FETIRP_OK, FETIRP_EINVAL, FETIRP_ENOMEM, FETIRP_ESINGULAR, FETIRP_ENOCONV, FETIRP_ECUDA, FETIRP_ESTATE, \
+    FETIRP_ETIMEOUT = range(8)
+FETIRP_PREC_FP64, FETIRP_PREC_FP32, FETIRP_PREC_TF32X3 = 0, 1, 2
+PRECISIONS = {"fp64": FETIRP_PREC_FP64, "fp32": FETIRP_PREC_FP32, "tf32x3": FETIRP_PREC_TF32X3}
+
+
+class fetirp_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32), ("block_k", C.c_int32),
+                ("max_outer", C.c_int32), ("inner_tol", C.c_double), ("pivot_tol", C.c_double),
+                ("eig_trunc", C.c_double), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
+                ("check_every", C.c_int32), ("timing", C.c_int32), ("eig_trunc_inner", C.c_double)]
+
+
+PHASES = ["factor", "coarse", "local", "gather", "scatter", "project", "gram", "reorth", "update", "recover"]
+
+
+class fetirp_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("outer_steps", C.c_int32), ("f_applies", C.c_int32),
+                ("dropped_directions", C.c_int32), ("kernel_dim_total", C.c_int32), ("rel_residual", C.c_double),
+                ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("launches", C.c_int64),
+                ("phase_ms", C.c_double * 10), ("phase_launches", C.c_int64 * 10),
+                ("phase_flops", C.c_double * 10), ("phase_bytes", C.c_double * 10)]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if name.startswith("phase_") else v
+        return d
+
+
+class FetirpError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_STATUS = {0: "FETIRP_OK", 1: "FETIRP_EINVAL", 2: "FETIRP_ENOMEM", 3: "FETIRP_ESINGULAR", 4: "FETIRP_ENOCONV",
+           5: "FETIRP_ECUDA", 6: "FETIRP_ESTATE", 7: "FETIRP_ETIMEOUT"}
+
+_lib = None
+P = C.c_void_p
+_SIGS = {
+    "fetirp_default_options": (None, [C.POINTER(fetirp_options)]),
+    "fetirp_status_string": (C.c_char_p, [C.c_int]),
+    "fetirp_create": (C.c_int, [C.POINTER(fetirp_options), C.POINTER(P)]),
+    "fetirp_last_error": (C.c_char_p, [P]),
+    "fetirp_destroy": (None, [P]),
+    "fetirp_create_pattern": (C.c_int, [P, C.c_int32, C.c_int32, P, P, P, C.c_int32, P, C.c_int32,
+                                        C.POINTER(C.c_int32)]),
+    "fetirp_add_occurrence": (C.c_int, [P, C.c_int32, P, C.c_int32, P, P, P, P, P, C.POINTER(C.c_int32)]),
+    "fetirp_set_groups": (C.c_int, [P, C.c_int32, P]),
+    "fetirp_solve": (C.c_int, [P, C.c_int64, P, P, P, C.POINTER(fetirp_stats)]),
+    "fetirp_solve_device": (C.c_int, [P, C.c_int64, P, P, P, C.POINTER(fetirp_stats)]),
+    "fetirp_apply_block": (C.c_int, [P, C.c_int32, P, P, C.c_int32]),
+    "fetirp_apply_block_device": (C.c_int, [P, C.c_int32, P, P, C.c_int32]),
+    "fetirp_prepare": (C.c_int, [P, C.c_int64, P]),
+    "fetirp_factorize": (C.c_int, [P]),
+    "fetirp_get_pattern": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), P, P]),
+}
+
+
+def lib():
+    """The loaded libfetirp.so (built by __graft_entry__.build() / paper_1208_6387_gb300._build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfetirp.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(ctx, st):
+    if st != FETIRP_OK:
+        msg = lib().fetirp_last_error(ctx).decode() if ctx else ""
+        raise FetirpError(st, msg)
+
+
+def fetirp_default_options(**kw) -> fetirp_options:
+    o = fetirp_options()
+    lib().fetirp_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(o, k, v)
+    return o
+
+
+def fetirp_create(opts: fetirp_options | None = None):
+    h = C.c_void_p()
+    st = lib().fetirp_create(C.byref(opts) if opts is not None else None, C.byref(h))
+    if st != FETIRP_OK:
+        raise FetirpError(st, "fetirp_create failed (no CUDA device or bad options)")
+    return h
+
+
+def fetirp_status_string(status: int) -> str:
+    return lib().fetirp_status_string(int(status)).decode()
+
+
+def fetirp_destroy(ctx):
+    lib().fetirp_destroy(ctx)
+
+
+def fetirp_last_error(ctx) -> str:
+    return lib().fetirp_last_error(ctx).decode()
+
+
+def fetirp_create_pattern(ctx, n_nodes, dofs_per_node, rowptr, col, val, bnd_nodes, expected_kernel_dim=-1) -> int:
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    bnd = np.ascontiguousarray(bnd_nodes, dtype=np.int32)
+    pid = C.c_int32()
+    _check(ctx, lib().fetirp_create_pattern(ctx, int(n_nodes), int(dofs_per_node), _ptr(rowptr), _ptr(col), _ptr(val),
+                                            len(bnd), _ptr(bnd), int(expected_kernel_dim), C.byref(pid)))
+    return pid.value
+
+
+def fetirp_add_occurrence(ctx, pattern_id, rot, local_node, global_comp, lambda_row, sign, f_global) -> int:
+    rot = None if rot is None else np.ascontiguousarray(rot, dtype=np.float64).reshape(9)
+    ln = np.ascontiguousarray(local_node, dtype=np.int32)
+    gc = np.ascontiguousarray(global_comp, dtype=np.int8)
+    lr = np.ascontiguousarray(lambda_row, dtype=np.int32)
+    sg = np.ascontiguousarray(sign, dtype=np.int8)
+    f = np.ascontiguousarray(f_global, dtype=np.float64)
+    oid = C.c_int32()
+    _check(ctx, lib().fetirp_add_occurrence(ctx, int(pattern_id), _ptr(rot), len(lr), _ptr(ln), _ptr(gc), _ptr(lr),
+                                            _ptr(sg), _ptr(f), C.byref(oid)))
+    return oid.value
+
+
+def fetirp_set_groups(ctx, k, group_of_occ):
+    g = np.ascontiguousarray(group_of_occ, dtype=np.int32)
+    _check(ctx, lib().fetirp_set_groups(ctx, int(k), _ptr(g)))
+
+
+def fetirp_prepare(ctx, n_lambda, c=None):
+    c = None if c is None else np.ascontiguousarray(c, dtype=np.float64)
+    _check(ctx, lib().fetirp_prepare(ctx, int(n_lambda), _ptr(c)))
+
+
+def fetirp_solve(ctx, n_lambda, c, n_u, allow_noconv=False):
+    """Returns (lambda, u, stats dict); u concatenates the occurrences (global frame)."""
+    c = None if c is None else np.ascontiguousarray(c, dtype=np.float64)
+    lam = np.zeros(int(n_lambda))
+    u = np.zeros(int(n_u))
+    st = fetirp_stats()
+    s = lib().fetirp_solve(ctx, int(n_lambda), _ptr(c), _ptr(lam), _ptr(u), C.byref(st))
+    if not (allow_noconv and s == FETIRP_ENOCONV):
+        _check(ctx, s)
+    return lam, u, st.as_dict()
+
+
+def fetirp_solve_device(ctx, n_lambda, c_ptr, lambda_ptr, u_ptr, allow_noconv=False):
+    """Device pointers (ints, e.g. torch tensor .data_ptr()); c_ptr may be 0 / None."""
+    st = fetirp_stats()
+    s = lib().fetirp_solve_device(ctx, int(n_lambda), C.c_void_p(c_ptr) if c_ptr else None, C.c_void_p(lambda_ptr),
+                                  C.c_void_p(u_ptr), C.byref(st))
+    if not (allow_noconv and s == FETIRP_ENOCONV):
+        _check(ctx, s)
+    return st.as_dict()
+
+
+def fetirp_apply_block(ctx, V, precision=FETIRP_PREC_FP64):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    Q = np.zeros_like(V)
+    _check(ctx, lib().fetirp_apply_block(ctx, V.shape[1], _ptr(V), _ptr(Q), int(precision)))
+    return Q
+
+
+def fetirp_apply_block_device(ctx, k, V_ptr, Q_ptr, precision=FETIRP_PREC_FP64):
+    _check(ctx, lib().fetirp_apply_block_device(ctx, int(k), C.c_void_p(V_ptr), C.c_void_p(Q_ptr), int(precision)))
+
+
+def fetirp_factorize(ctx):
+    _check(ctx, lib().fetirp_factorize(ctx))
+
+
+def fetirp_get_pattern(ctx, pattern_id, n_dofs=None):
+    """Returns (n_b, kernel_dim, S^+ (n_b x n_b), N (n_dofs x kernel_dim) or None)."""
+    nb, kd = C.c_int32(), C.c_int32()
+    _check(ctx, lib().fetirp_get_pattern(ctx, int(pattern_id), C.byref(nb), C.byref(kd), None, None))
+    S = np.zeros((nb.value, nb.value))
+    N = np.zeros((n_dofs, kd.value)) if n_dofs is not None else None
+    _check(ctx, lib().fetirp_get_pattern(ctx, int(pattern_id), None, None, _ptr(S), _ptr(N)))
+    return nb.value, kd.value, S, N
+
+
+# ------------------------------------------------------------------------------------------------ marshalling
+def load_problem(ctx, prob, expected_kernel=True, groups=True):
+    """Register every pattern and occurrence of a fetirp_gen.Problem (argument marshalling only)."""
+    pids = []
+    for pat in prob.patterns:
+        K = pat.K.tocsr()
+        pids.append(fetirp_create_pattern(ctx, pat.n_nodes, pat.dpn, K.indptr, K.indices, K.data, pat.bnd_nodes,
+                                          pat.kernel_dim if expected_kernel else -1))
+    for occ in prob.occs:
+        fetirp_add_occurrence(ctx, pids[occ.pattern], occ.rot.astype(float), occ.link_local_node,
+                              occ.link_global_comp, occ.link_lambda_row, occ.link_sign, occ.f_global)
+    if groups:
+        fetirp_set_groups(ctx, prob.k, prob.groups)
+    return pids
+
+
+def n_u(prob):
+    return sum(prob.patterns[o.pattern].n_dofs for o in prob.occs)
+
+
+def split_u(prob, u):
+    out, off = [], 0
+    for o in prob.occs:
+        n = prob.patterns[o.pattern].n_dofs
+        out.append(u[off:off + n])
+        off += n
+    return out

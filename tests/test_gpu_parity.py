@@ -1,0 +1,153 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element, on seeded inputs
+that span several tiles and ragged tails.  Tolerances: FP64 paths 1e-10 relative (operator) and 1e-8
+(solve, the target of the method).  FP32 local products: 2e-4 relative on the projected operator.  The FP32
+rounding of S^+ and of the traces is ~6e-8 per entry, but S^+ of a floating pattern carries large
+near-rigid components that the projector P removes again, so the relative error of P^T F P V is the FP32
+unit roundoff times that cancellation ratio (measured ~3e-5 for the elastic cases).  Solves reach 1e-8
+after the FP64 refinement in every precision."""
+import numpy as np
+import pytest
+
+from fetirp_gen import config, heat_grid, elastic_grid
+from oracle.direct import direct
+from oracle.feti import FetiOracle
+
+pytestmark = pytest.mark.gpu
+
+F = pytest.importorskip("paper_1208_6387_gb300.fetirp")
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+def make_ctx(prob, **kw):
+    ctx = F.fetirp_create(F.fetirp_default_options(**kw))
+    F.load_problem(ctx, prob)
+    return ctx
+
+
+CASES = {
+    "c1": lambda: config("c1"),
+    "heat_rot_ragged": lambda: heat_grid(5, (3, 2), kappas=(1.0, 30.0), checker=True, rotate=True, k=4, seed=7),
+    "elastic_2x2x1": lambda: elastic_grid(3, (2, 2, 1), n_patterns=2, k=4, seed=1),
+    "c3r": lambda: config("c3r"),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_pattern_operators(name):
+    """S^+ is a generalized inverse of S = K_bb - K_bi K_ii^{-1} K_ib (S S^+ S = S), the kernel satisfies
+    K N = 0 with the expected dimension."""
+    prob = CASES[name]()
+    ctx = make_ctx(prob)
+    try:
+        for pid, pat in enumerate(prob.patterns):
+            nb, kd, S_plus, N = F.fetirp_get_pattern(ctx, pid, pat.n_dofs)
+            assert kd == pat.kernel_dim and nb == pat.n_b
+            K = pat.K.toarray()
+            bd = (pat.bnd_nodes[:, None] * pat.dpn + np.arange(pat.dpn)).ravel()
+            it = np.setdiff1d(np.arange(pat.n_dofs), bd)
+            S = K[np.ix_(bd, bd)] - K[np.ix_(bd, it)] @ np.linalg.solve(K[np.ix_(it, it)], K[np.ix_(it, bd)])
+            assert rel(S @ S_plus @ S, S) < 1e-10
+            assert np.allclose(S_plus, S_plus.T, atol=1e-12 * np.abs(S_plus).max())
+            assert np.abs(K @ N).max() < 1e-9 * np.abs(K).max() * np.abs(N).max()
+            assert np.linalg.matrix_rank(N) == kd
+    finally:
+        F.fetirp_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", list(CASES) + ["c2"])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-4)])
+def test_apply_block_matches_oracle(name, prec, tol):
+    prob = config("c2") if name == "c2" else CASES[name]()
+    orc = FetiOracle(prob)
+    ctx = make_ctx(prob)
+    try:
+        F.fetirp_prepare(ctx, prob.n_lambda, prob.c)
+        rng = np.random.default_rng(11)
+        for k in (1, 3, prob.k):
+            V = rng.standard_normal((prob.n_lambda, k))
+            Q = F.fetirp_apply_block(ctx, V, F.PRECISIONS[prec])
+            Qo = orc.PtFP(V)
+            assert rel(Q, Qo) < tol, (k, rel(Q, Qo))
+            assert np.abs(Q - Qo).max() < 10 * tol * np.abs(Qo).max()
+    finally:
+        F.fetirp_destroy(ctx)
+
+
+@pytest.mark.parametrize("name", list(CASES) + ["c2"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_solve_matches_direct(name, prec):
+    prob = config("c2") if name == "c2" else CASES[name]()
+    us_ref, lam_ref, _, _ = direct(prob)
+    ctx = make_ctx(prob, precision=prec, tol=1e-12, inner_tol=1e-5)
+    try:
+        lam, u, st = F.fetirp_solve(ctx, prob.n_lambda, prob.c, F.n_u(prob))
+    finally:
+        F.fetirp_destroy(ctx)
+    assert st["rel_residual"] <= 1e-12
+    assert rel(lam, lam_ref) < 1e-8, st
+    for a, b in zip(F.split_u(prob, u), us_ref):
+        assert rel(a, b) < 1e-8
+    if prec == "fp32":
+        assert st["outer_steps"] >= 1
+
+
+def test_classical_k1_and_block_agree():
+    """k = 1 is classical FETI-CG; block k = n_occ converges in no more iterations (convergence cannot be
+    deteriorated) and both reach the same lambda."""
+    prob = config("c1")
+    out = {}
+    for k in (1, 4):
+        ctx = F.fetirp_create(F.fetirp_default_options(tol=1e-12))
+        F.load_problem(ctx, prob, groups=False)
+        F.fetirp_set_groups(ctx, k, np.arange(prob.n_occ) * k // prob.n_occ)
+        out[k] = F.fetirp_solve(ctx, prob.n_lambda, prob.c, F.n_u(prob))
+        F.fetirp_destroy(ctx)
+    assert rel(out[1][0], out[4][0]) < 1e-9
+    assert out[4][2]["iterations"] <= out[1][2]["iterations"]
+
+
+def test_iterates_match_oracle_multivector():
+    """Same multivector iterates as the oracle's Table 1 (right) loop after a fixed number of steps."""
+    prob = config("c1")
+    orc = FetiOracle(prob)
+    for its in (1, 2, 4):
+        lam_o, _, _ = orc.multivector(tol=0.0, max_it=its)
+        ctx = F.fetirp_create(F.fetirp_default_options(tol=1e-300, max_iter=its))
+        F.load_problem(ctx, prob)
+        lam, _, st = F.fetirp_solve(ctx, prob.n_lambda, prob.c, F.n_u(prob), allow_noconv=True)
+        F.fetirp_destroy(ctx)
+        assert st["iterations"] == its
+        assert rel(lam, lam_o) < 1e-9, (its, rel(lam, lam_o))
+
+
+def test_deterministic():
+    prob = config("c3r")
+    res = []
+    for _ in range(2):
+        ctx = make_ctx(prob, tol=1e-10)
+        res.append(F.fetirp_solve(ctx, prob.n_lambda, prob.c, F.n_u(prob)))
+        F.fetirp_destroy(ctx)
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+def test_single_occurrence_and_invalid_inputs():
+    prob = heat_grid(3, (1, 1), k=1)
+    us_ref, lam_ref, _, _ = direct(prob)
+    ctx = make_ctx(prob, tol=1e-12)
+    lam, u, st = F.fetirp_solve(ctx, prob.n_lambda, prob.c, F.n_u(prob))
+    assert rel(lam, lam_ref) < 1e-9 and rel(u, us_ref[0]) < 1e-9
+    pat = prob.patterns[0]
+    K = pat.K.tocsr()
+    with pytest.raises(F.FetirpError) as e:   # link on an interior node
+        F.fetirp_add_occurrence(ctx, 0, None, [5], [0], [0], [1], np.zeros(pat.n_dofs))
+    assert e.value.status == F.FETIRP_EINVAL
+    with pytest.raises(F.FetirpError) as e:   # not a rotation of the cube
+        F.fetirp_add_occurrence(ctx, 0, np.eye(3) * 0.5, [0], [0], [0], [1], np.zeros(pat.n_dofs))
+    assert e.value.status == F.FETIRP_EINVAL
+    with pytest.raises(F.FetirpError) as e:   # wrong expected kernel dimension
+        F.fetirp_create_pattern(ctx, pat.n_nodes, 1, K.indptr, K.indices, K.data, pat.bnd_nodes, 2)
+    assert e.value.status == F.FETIRP_ESINGULAR
+    F.fetirp_destroy(ctx)
