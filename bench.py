@@ -62,6 +62,18 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(base_seed, rank):
+    """Every rank solves its own, independently seeded structure of the same shape (weak scaling)."""
+    return base_seed + 1000003 * rank
+
+
+def job_throughput(local_total_ms, steps, world, reduce_max=None):
+    """Whole-job solves/s: every rank ran `steps` solves; the job time is the slowest rank's (max over ranks).
+    reduce_max: callable taking a float and returning the max over ranks (None for one rank)."""
+    total_ms = reduce_max(local_total_ms) if (reduce_max and world > 1) else local_total_ms
+    return world * steps / (total_ms / 1e3), total_ms / steps
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -132,7 +144,7 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    prob = config(args.workload, seed=args.seed + rank, k=args.k)
+    prob = config(args.workload, seed=rank_seed(args.seed, rank), k=args.k)
     stream = torch.cuda.Stream(device=dev)
     opts = F.fetirp_default_options(precision=args.precision, tol=1e-8, inner_tol=args.inner_tol,
                                     device=local, timing=1)
@@ -175,13 +187,14 @@ def run_ours(args, rank, world, local):
     if world > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+
+    def reduce_max(x):
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
+        return float(t.item())
+
+    value, ms_per_step = job_throughput(sum(step_ms), args.steps, world, reduce_max)
+    total_ms = ms_per_step * args.steps
 
     # check the last result against the definition (residual reported by the library, FP64)
     rel_res = max(s["rel_residual"] for s in stats)

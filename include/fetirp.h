@@ -65,12 +65,15 @@ typedef struct {
   double pivot_tol;    /* zero pivot when pivot <= pivot_tol * original diagonal; default 1e-9 */
   double eig_trunc;    /* a direction is dropped when its normalisation pivot <= eig_trunc * largest;
                           default 1e-12 */
-  void* cuda_stream;   /* cudaStream_t used for all device work; NULL = the legacy default stream */
+  void* cuda_stream;   /* cudaStream_t used for all device work; NULL = a stream created and owned by the
+                          context (the legacy default stream cannot be captured into CUDA graphs) */
   int32_t device;      /* CUDA device ordinal; default 0 */
-  int32_t check_every; /* convergence is read back every check_every block iterations; default 1 */
+  int32_t check_every; /* block iterations per convergence read-back (and per captured graph); default 4 */
   int32_t timing;      /* 1: bracket every phase with CUDA events and fill the phase_* statistics; default 0 */
   double eig_trunc_inner; /* truncation threshold of the low-precision inner solves of the mixed forms, where
                              the operator is only accurate to ~1e-7; default 1e-6 */
+  int32_t use_graphs;  /* 1: the check_every iterations between read-backs are captured once as a CUDA graph
+                          and replayed; 0: launched one by one; default 1 */
 } fetirp_options;
 
 /* Phases of a solve, for the per-phase statistics. */

@@ -36,6 +36,12 @@ __global__ void k_set_diag(double* A, int ld, int from, int to, double v) {
   if (i < to) A[(size_t)i * ld + i] = v;
 }
 
+// N[z_m][m] = 1 for the zero-pivot dofs z_m (identity block of the kernel basis).
+__global__ void k_set_entries(double* N, int npad, const int* zpiv, int kd) {
+  const int m = threadIdx.x;
+  if (m < kd) N[(size_t)m * npad + zpiv[m]] = 1.0;
+}
+
 __global__ void k_to_f32(size_t n, const double* __restrict__ x, float* __restrict__ y) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = (float)x[i];
@@ -71,7 +77,16 @@ struct PatternData {
   TilePlan plan, planS;
   DBuf<int64_t> d_rowptr;
   DBuf<int> d_col, d_newidx, zp;
-  DBuf<double> d_val, L, diag0, S64, N, Nb;
+  DBuf<double> d_val, L, diag0, S64, N, Nb, Dinv, LS, XS, DinvS;
+  DBuf<int> zpS, d_zpiv;
+  std::vector<int> h_zp;
+  int* h_zp_pinned = nullptr;
+  std::vector<double> h_nrhs;
+  const int* d_zpiv_list(int) const { return d_zpiv.p; }
+  void upload_zpiv(cudaStream_t s) { if (!zpiv.empty()) d_zpiv.upload(zpiv, s); }
+  ~PatternData() {
+    if (h_zp_pinned) cudaFreeHost(h_zp_pinned);
+  }
   DBuf<float> S32, S_hi, S_lo;   // FP32 S^+ and its tf32 pair (leading dimension lds)
   long long lds = 0;
   std::vector<int> occs;       // occurrences of this pattern (ids), q = position
@@ -107,10 +122,13 @@ struct fetirp_ctx_s {
   int k = 1, n_G = 0, n_Gpad = 0;
   Layout L{};
   DBuf<int> d_slot_ptr, d_slot_row, d_row_slot, d_slot_occ, d_occ_obase, d_occ_pat, d_occ_q, d_occ_gofs,
-      d_occ_group, d_pair_s, d_pair_t, d_rot;
+      d_occ_group, d_pair_s, d_pair_t, d_rot, d_grp_ptr, d_grp_row, d_ell_row;
+  DBuf<int8_t> d_ell_sign;
+  DBuf<double> d_grp_w;
   DBuf<int8_t> d_slot_sign, d_row_sign;
   DBuf<long long> d_uoff;
   int n_pairs = 0;
+  int max_group_rows = 0;
   std::vector<int> pofs;               // first coarse column of every pattern
   std::vector<long long> uoff;         // offset of every occurrence in u_out
   long long n_u = 0;
@@ -120,6 +138,9 @@ struct fetirp_ctx_s {
 
   // work
   DBuf<double> lam, r, t1, W, Q, Zr, Whist, Qhist, C, eta, wr, T, alpha, rr_part, Xc, Ac, gram_part, V1, V2;
+  DBuf<float> Whist32, Qhist32;   // direction history of the low-precision inner solves
+  DBuf<double> tu_part;           // split partials of the history update
+  DBuf<double> eta_part;          // row-chunk partials of eta and W^T r
   DBuf<int> n_kept;
   DBuf<double> Y64, Z64;
   DBuf<float> Y32, Z32, Ylo32;
@@ -132,13 +153,39 @@ struct fetirp_ctx_s {
   struct PhaseRec { int phase; int e0, e1; };
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
+  size_t ev_reserved = 0;
   std::vector<PhaseRec> recs;
   double phase_flops[FETIRP_NPHASE] = {}, phase_bytes[FETIRP_NPHASE] = {};
   long long phase_launches[FETIRP_NPHASE] = {};
+  double graph_phase_ms[FETIRP_NPHASE] = {};
   bool phases_pending = false;          // a fetirp_factorize call's phases belong to the next solve
+  // device-resident iteration state and the captured iteration graph
+  DBuf<int> d_state;                    // [0] stored directions, [1] dropped directions, [2] iterations
+  int* h_state = nullptr;               // pinned mirror for read-back
+  double* h_rr = nullptr;               // pinned read-back of the residual partials
+  bool owns_stream = false;
+  bool capturing = false;
+  std::vector<cudaStream_t> fstreams;   // one per concurrently factorised pattern
+  cudaEvent_t fork_ev = nullptr;
+  std::vector<cudaEvent_t> join_ev;
+  struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int prec = -1, k = 0, G = 0, th = 0, timing = 0;
+    long long cap = 0;
+    std::vector<PhaseRec> recs;
+    long long launches[FETIRP_NPHASE] = {};
+    long long total_launches = 0;
+  } gc;
   long long pending_launches = 0;
   ~fetirp_ctx_s() {
+    if (gc.exec) cudaGraphExecDestroy(gc.exec);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    if (h_state) cudaFreeHost(h_state);
+    if (h_rr) cudaFreeHost(h_rr);
+    for (cudaStream_t st : fstreams) cudaStreamDestroy(st);
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    for (cudaEvent_t e : join_ev) cudaEventDestroy(e);
+    if (owns_stream && stream) cudaStreamDestroy(stream);
   }
 };
 
@@ -175,8 +222,10 @@ struct PhaseScope {
   unsigned long long l0;
   int e0 = -1;
   PhaseScope(fetirp_ctx c, int ph, double flops, double bytes) : ctx(c), phase(ph), l0(g_launch_count) {
-    ctx->phase_flops[ph] += flops;
-    ctx->phase_bytes[ph] += bytes;
+    if (!ctx->capturing) {   // inside a captured graph the work is accounted per replay instead
+      ctx->phase_flops[ph] += flops;
+      ctx->phase_bytes[ph] += bytes;
+    }
     if (ctx->opt.timing) e0 = record();
   }
   int record() {
@@ -186,15 +235,20 @@ struct PhaseScope {
       ctx->ev_pool.push_back(e);
     }
     const int id = (int)ctx->ev_used++;
-    FETIRP_CUDA(cudaEventRecord(ctx->ev_pool[id], ctx->stream));
+    if (ctx->capturing)   // an event node inside the captured graph, re-recorded at every replay
+      FETIRP_CUDA(cudaEventRecordWithFlags(ctx->ev_pool[id], ctx->stream, cudaEventRecordExternal));
+    else
+      FETIRP_CUDA(cudaEventRecord(ctx->ev_pool[id], ctx->stream));
     return id;
   }
   ~PhaseScope() {
-    ctx->phase_launches[phase] += (long long)(g_launch_count - l0);
+    const long long n = (long long)(g_launch_count - l0);
+    if (ctx->capturing) ctx->gc.launches[phase] += n;
+    else ctx->phase_launches[phase] += n;
     if (e0 >= 0) {
       try {
         const int e1 = record();
-        ctx->recs.push_back({phase, e0, e1});
+        (ctx->capturing ? ctx->gc.recs : ctx->recs).push_back({phase, e0, e1});
       } catch (...) {
       }
     }
@@ -202,10 +256,10 @@ struct PhaseScope {
 };
 
 void reset_phases(fetirp_ctx ctx) {
-  ctx->ev_used = 0;
+  ctx->ev_used = ctx->ev_reserved;   // events owned by the captured graph stay reserved
   ctx->recs.clear();
   for (int i = 0; i < FETIRP_NPHASE; ++i) {
-    ctx->phase_flops[i] = ctx->phase_bytes[i] = 0.0;
+    ctx->phase_flops[i] = ctx->phase_bytes[i] = ctx->graph_phase_ms[i] = 0.0;
     ctx->phase_launches[i] = 0;
   }
 }
@@ -213,7 +267,7 @@ void reset_phases(fetirp_ctx ctx) {
 // Call after the stream is synchronised.
 void collect_phases(fetirp_ctx ctx, fetirp_stats& st) {
   for (int i = 0; i < FETIRP_NPHASE; ++i) {
-    st.phase_ms[i] = 0.0;
+    st.phase_ms[i] = ctx->graph_phase_ms[i];
     st.phase_flops[i] = ctx->phase_flops[i];
     st.phase_bytes[i] = ctx->phase_bytes[i];
     st.phase_launches[i] = ctx->phase_launches[i];
@@ -232,27 +286,32 @@ void collect_phases(fetirp_ctx ctx, fetirp_stats& st) {
 // ----------------------------------------------------------------------------------------- pattern set-up
 // FP64 factorisation on the device: dense factor of K in interior-first/boundary-last order with zero-pivot
 // detection (Sec. 2), kernel N, Schur complement pseudo-inverse S^+ = L_S^{-T} L_S^{-1} (stated after Eq. 3).
-void factorize_pattern(fetirp_ctx ctx, PatternData& P) {
-  cudaStream_t s = ctx->stream;
+// Several patterns are factorised concurrently, each on its own stream forked from the context stream;
+// work buffers stay resident so that a refactorisation allocates nothing.
+void factor_stage_a(PatternData& P, double pivot_tol, cudaStream_t s) {
   const int n = P.n, npad = P.npad;
-  PhaseScope ph(ctx, FETIRP_PHASE_FACTOR, 0.0, 0.0);
-  P.L.alloc((size_t)npad * npad);
-  P.L.zero(s);
+  P.L.ensure((size_t)npad * npad);
+  FETIRP_CUDA(cudaMemsetAsync(P.L.p, 0, sizeof(double) * (size_t)npad * npad, s));
   k_csr_to_dense<<<ceil_div(npad, 128), 128, 0, s>>>(n, npad, P.d_rowptr.p, P.d_col.p, P.d_val.p, P.d_newidx.p,
                                                       P.L.p);
   FETIRP_LAUNCH_CHECK();
-  P.diag0.alloc(npad);
-  P.zp.alloc(npad);
+  P.diag0.ensure(npad);
+  P.zp.ensure(npad);
   copy_diag(P.L.p, npad, P.diag0.p, s);
-  chol_tiles(P.L.p, npad, P.plan, P.diag0.p, P.zp.p, ctx->opt.pivot_tol, s);
-  std::vector<int> zp(npad);
-  FETIRP_CUDA(cudaMemcpyAsync(zp.data(), P.zp.p, sizeof(int) * npad, cudaMemcpyDeviceToHost, s));
-  FETIRP_CUDA(cudaStreamSynchronize(s));
+  chol_tiles(P.L.p, npad, P.plan, P.diag0.p, P.zp.p, pivot_tol, s);
+  P.Dinv.ensure((size_t)npad * TILE);
+  tile_inverses(P.L.p, npad, P.zp.p, P.Dinv.p, s);
+  P.h_zp.resize(npad);
+  if (!P.h_zp_pinned) FETIRP_CUDA(cudaMallocHost(&P.h_zp_pinned, sizeof(int) * npad));
+  FETIRP_CUDA(cudaMemcpyAsync(P.h_zp_pinned, P.zp.p, sizeof(int) * npad, cudaMemcpyDeviceToHost, s));
+}
+
+void factor_check(PatternData& P) {
   P.zpiv.clear();
-  for (int i = 0; i < npad; ++i)
-    if (zp[i]) P.zpiv.push_back(i);
+  for (int i = 0; i < P.npad; ++i)
+    if (P.h_zp_pinned[i]) P.zpiv.push_back(i);
   for (int z : P.zpiv)
-    if (z < P.n_i || z >= n)
+    if (z < P.n_i || z >= P.n)
       throw Error(FETIRP_ESINGULAR, "zero pivot outside the boundary block: interior stiffness is singular");
   P.kdim = (int)P.zpiv.size();
   if (P.kdim > 6)
@@ -260,59 +319,92 @@ void factorize_pattern(fetirp_ctx ctx, PatternData& P) {
   if (P.expected >= 0 && P.kdim != P.expected)
     throw Error(FETIRP_ESINGULAR, "detected kernel dimension " + std::to_string(P.kdim) + " != expected " +
                                       std::to_string(P.expected));
-  const int kd = P.kdim;
-  // kernel: N_r = -K_rr^{-1} K_rz, N_z = I
-  P.N.alloc((size_t)npad * std::max(kd, 1));
-  P.N.zero(s);
+}
+
+void factor_stage_b(PatternData& P, cudaStream_t s) {
+  const int npad = P.npad, kd = P.kdim;
+  // kernel: N_r = -K_rr^{-1} K_rz, N_z = I (right-hand side built on the host from the CSR)
+  P.N.ensure((size_t)npad * std::max(kd, 1));
   if (kd > 0) {
-    std::vector<double> rhs((size_t)npad * kd, 0.0);
+    P.h_nrhs.assign((size_t)npad * kd, 0.0);
     for (int m = 0; m < kd; ++m) {
       const int old = P.oldidx[P.zpiv[m]];
       for (int64_t e = P.rowptr[old]; e < P.rowptr[old + 1]; ++e)
-        rhs[(size_t)m * npad + P.newidx[P.col[e]]] = -P.val[e];
-      for (int z : P.zpiv) rhs[(size_t)m * npad + z] = 0.0;
+        P.h_nrhs[(size_t)m * npad + P.newidx[P.col[e]]] = -P.val[e];
+      for (int z : P.zpiv) P.h_nrhs[(size_t)m * npad + z] = 0.0;
     }
-    P.N.upload(rhs, s);
-    tri_solve(P.L.p, npad, P.plan, P.zp.p, P.N.p, npad, kd, false, s);
-    tri_solve(P.L.p, npad, P.plan, P.zp.p, P.N.p, npad, kd, true, s);
-    const double one = 1.0;
-    for (int m = 0; m < kd; ++m)
-      FETIRP_CUDA(cudaMemcpyAsync(P.N.p + (size_t)m * npad + P.zpiv[m], &one, sizeof(double),
-                                  cudaMemcpyHostToDevice, s));
-    FETIRP_CUDA(cudaStreamSynchronize(s));   // `one` lives on this stack frame
+    FETIRP_CUDA(cudaMemcpyAsync(P.N.p, P.h_nrhs.data(), sizeof(double) * P.h_nrhs.size(), cudaMemcpyHostToDevice, s));
+    tri_solve(P.L.p, npad, P.plan, P.zp.p, P.N.p, npad, kd, false, s, P.Dinv.p);
+    tri_solve(P.L.p, npad, P.plan, P.zp.p, P.N.p, npad, kd, true, s, P.Dinv.p);
+    k_set_entries<<<1, 32, 0, s>>>(P.N.p, npad, P.d_zpiv_list(kd), kd);
+    FETIRP_LAUNCH_CHECK();
   }
-  P.Nb.alloc((size_t)P.n_b * std::max(kd, 1));
+  P.Nb.ensure((size_t)P.n_b * std::max(kd, 1));
   for (int m = 0; m < kd; ++m)
     FETIRP_CUDA(cudaMemcpy2DAsync(P.Nb.p + m, sizeof(double) * kd, P.N.p + (size_t)m * npad + P.n_i,
                                   sizeof(double), sizeof(double), P.n_b, cudaMemcpyDeviceToDevice, s));
   // S^+ from the trailing block L_S
   const int nbp = P.nbpad;
-  DBuf<double> LS((size_t)nbp * nbp), X((size_t)nbp * nbp);
-  DBuf<int> zpS(nbp);
-  LS.zero(s);
-  X.zero(s);
-  zpS.zero(s);
-  FETIRP_CUDA(cudaMemcpy2DAsync(LS.p, sizeof(double) * nbp, P.L.p + (size_t)P.n_i * npad + P.n_i,
+  P.LS.ensure((size_t)nbp * nbp);
+  P.XS.ensure((size_t)nbp * nbp);
+  P.zpS.ensure(nbp);
+  P.DinvS.ensure((size_t)nbp * TILE);
+  FETIRP_CUDA(cudaMemsetAsync(P.LS.p, 0, sizeof(double) * (size_t)nbp * nbp, s));
+  FETIRP_CUDA(cudaMemsetAsync(P.XS.p, 0, sizeof(double) * (size_t)nbp * nbp, s));
+  FETIRP_CUDA(cudaMemsetAsync(P.zpS.p, 0, sizeof(int) * nbp, s));
+  FETIRP_CUDA(cudaMemcpy2DAsync(P.LS.p, sizeof(double) * nbp, P.L.p + (size_t)P.n_i * npad + P.n_i,
                                 sizeof(double) * npad, sizeof(double) * P.n_b, P.n_b, cudaMemcpyDeviceToDevice, s));
-  FETIRP_CUDA(cudaMemcpyAsync(zpS.p, P.zp.p + P.n_i, sizeof(int) * P.n_b, cudaMemcpyDeviceToDevice, s));
+  FETIRP_CUDA(cudaMemcpyAsync(P.zpS.p, P.zp.p + P.n_i, sizeof(int) * P.n_b, cudaMemcpyDeviceToDevice, s));
   if (nbp > P.n_b) {
-    k_set_diag<<<ceil_div(nbp - P.n_b, 128), 128, 0, s>>>(LS.p, nbp, P.n_b, nbp, 1.0);
+    k_set_diag<<<ceil_div(nbp - P.n_b, 128), 128, 0, s>>>(P.LS.p, nbp, P.n_b, nbp, 1.0);
     FETIRP_LAUNCH_CHECK();
   }
-  k_set_diag<<<ceil_div(nbp, 128), 128, 0, s>>>(X.p, nbp, 0, nbp, 1.0);
+  k_set_diag<<<ceil_div(nbp, 128), 128, 0, s>>>(P.XS.p, nbp, 0, nbp, 1.0);
   FETIRP_LAUNCH_CHECK();
-  tri_solve(LS.p, nbp, P.planS, zpS.p, X.p, nbp, nbp, false, s);   // X = L_S^{-1}
-  P.S64.alloc((size_t)P.n_b * P.n_b);
-  gemm_f64(P.n_b, P.n_b, nbp, 1.0, X.p, nbp, 1, X.p, 1, nbp, 0.0, P.S64.p, P.n_b, 1, s);
-  P.S32.alloc((size_t)P.n_b * P.n_b);
+  tile_inverses(P.LS.p, nbp, P.zpS.p, P.DinvS.p, s);
+  tri_solve(P.LS.p, nbp, P.planS, P.zpS.p, P.XS.p, nbp, nbp, false, s, P.DinvS.p);   // X = L_S^{-1}
+  P.S64.ensure((size_t)P.n_b * P.n_b);
+  gemm_f64(P.n_b, P.n_b, nbp, 1.0, P.XS.p, nbp, 1, P.XS.p, 1, nbp, 0.0, P.S64.p, P.n_b, 1, s);
+  P.S32.ensure((size_t)P.n_b * P.n_b);
   const size_t nn = (size_t)P.n_b * P.n_b;
   k_to_f32<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(nn, P.S64.p, P.S32.p);
   FETIRP_LAUNCH_CHECK();
   P.lds = round_up(P.n_b, 4);
-  P.S_hi.alloc((size_t)P.n_b * P.lds);
-  P.S_lo.alloc((size_t)P.n_b * P.lds);
+  P.S_hi.ensure((size_t)P.n_b * P.lds);
+  P.S_lo.ensure((size_t)P.n_b * P.lds);
   split_tf32(P.S64.p, P.n_b, P.n_b, P.n_b, P.S_hi.p, P.S_lo.p, P.lds, s);
-  FETIRP_CUDA(cudaStreamSynchronize(s));
+}
+
+void factorize_patterns(fetirp_ctx ctx, const std::vector<PatternData*>& pats) {
+  PhaseScope ph(ctx, FETIRP_PHASE_FACTOR, 0.0, 0.0);
+  const size_t np = pats.size();
+  while (ctx->fstreams.size() < np) {
+    cudaStream_t st;
+    FETIRP_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    ctx->fstreams.push_back(st);
+  }
+  if (!ctx->fork_ev) FETIRP_CUDA(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+  FETIRP_CUDA(cudaEventRecord(ctx->fork_ev, ctx->stream));
+  for (size_t i = 0; i < np; ++i) {
+    FETIRP_CUDA(cudaStreamWaitEvent(ctx->fstreams[i], ctx->fork_ev, 0));
+    factor_stage_a(*pats[i], ctx->opt.pivot_tol, ctx->fstreams[i]);
+  }
+  for (size_t i = 0; i < np; ++i) FETIRP_CUDA(cudaStreamSynchronize(ctx->fstreams[i]));
+  for (size_t i = 0; i < np; ++i) {
+    factor_check(*pats[i]);
+    pats[i]->upload_zpiv(ctx->fstreams[i]);
+  }
+  for (size_t i = 0; i < np; ++i) factor_stage_b(*pats[i], ctx->fstreams[i]);
+  for (size_t i = 0; i < np; ++i) {
+    if (ctx->join_ev.size() <= i) {
+      cudaEvent_t e;
+      FETIRP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      ctx->join_ev.push_back(e);
+    }
+    FETIRP_CUDA(cudaEventRecord(ctx->join_ev[i], ctx->fstreams[i]));
+    FETIRP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->join_ev[i], 0));
+  }
+  FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 
 // Dense SPD inverse in FP64 (coarse matrix G^T G): tile Cholesky, X = L^{-1}, A^{-1} = X^T X.
@@ -354,6 +446,14 @@ TilePlan dense_plan(int nt) {
 
 // ----------------------------------------------------------------------------------------- structure
 void invalidate(fetirp_ctx ctx) { ctx->prepared = false; }
+
+// Local-product buffers for a block of k columns in every precision (allocated before any graph capture).
+void ensure_apply_buffers(fetirp_ctx ctx, int k) {
+  long long total = 0;
+  for (auto& P : ctx->pats) total += (long long)P->occs.size() * k * P->ld_y;
+  ctx->Y64.ensure(total); ctx->Z64.ensure(total);
+  ctx->Y32.ensure(total); ctx->Z32.ensure(total); ctx->Ylo32.ensure(total);
+}
 
 void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, const double* c_dev) {
   cudaStream_t s = ctx->stream;
@@ -428,6 +528,35 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   std::vector<int> slot_occ(n_slots);
   for (int o = 0; o < n_occ; ++o)
     for (int j = obase[o]; j < obase[o + 1]; ++j) slot_occ[j] = o;
+  int ell_w = 1;
+  for (int i = 0; i < n_slots; ++i) ell_w = std::max(ell_w, slot_ptr[i + 1] - slot_ptr[i]);
+  std::vector<int> ell_row((size_t)n_slots * ell_w, 0);
+  std::vector<int8_t> ell_sign((size_t)n_slots * ell_w, 0);
+  for (int i = 0; i < n_slots; ++i)
+    for (int e = slot_ptr[i]; e < slot_ptr[i + 1]; ++e) {
+      ell_row[(size_t)i * ell_w + (e - slot_ptr[i])] = slot_row[e];
+      ell_sign[(size_t)i * ell_w + (e - slot_ptr[i])] = slot_sign[e];
+    }
+  // rows of every multivector group with the multiplicity weight 1/(occurrences in the row): the split
+  // S(r)[row][g] = sum over the row's occurrences in group g of r[row] / count
+  std::vector<std::vector<std::pair<int, double>>> grp(k);
+  for (int r = 0; r < nl; ++r) {
+    const double w = 1.0 / row_cnt[r];
+    int g1 = group[slot_occ[row_slot[2 * (size_t)r]]];
+    if (row_cnt[r] == 2) {
+      int g2 = group[slot_occ[row_slot[2 * (size_t)r + 1]]];
+      if (g1 == g2) { grp[g1].push_back({r, 2.0 * w}); continue; }
+      grp[g2].push_back({r, w});
+    }
+    grp[g1].push_back({r, w});
+  }
+  std::vector<int> grp_ptr(k + 1, 0), grp_row;
+  std::vector<double> grp_w;
+  for (int g = 0; g < k; ++g) {
+    std::sort(grp[g].begin(), grp[g].end());
+    for (auto& e : grp[g]) { grp_row.push_back(e.first); grp_w.push_back(e.second); }
+    grp_ptr[g + 1] = (int)grp_row.size();
+  }
   // neighbour pairs (s, t) sharing a row, plus (s, s)
   std::vector<std::vector<int>> nbr(n_occ);
   for (int o = 0; o < n_occ; ++o) nbr[o].push_back(o);
@@ -455,6 +584,13 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   ctx->d_occ_q.upload(occ_q, s);
   ctx->d_occ_gofs.upload(occ_gofs, s);
   ctx->d_occ_group.upload(group, s);
+  ctx->max_group_rows = 0;
+  for (int g = 0; g < k; ++g) ctx->max_group_rows = std::max(ctx->max_group_rows, grp_ptr[g + 1] - grp_ptr[g]);
+  ctx->d_ell_row.upload(ell_row, s);
+  ctx->d_ell_sign.upload(ell_sign, s);
+  ctx->d_grp_ptr.upload(grp_ptr, s);
+  ctx->d_grp_row.upload(grp_row, s);
+  ctx->d_grp_w.upload(grp_w, s);
   ctx->d_pair_s.upload(pair_s, s);
   ctx->d_pair_t.upload(pair_t, s);
   ctx->n_pairs = (int)pair_s.size();
@@ -471,6 +607,7 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   L.n_lambda = nl; L.n_occ = n_occ; L.n_slots = n_slots; L.n_G = ctx->n_G; L.n_pat = n_pat; L.k = k;
   L.slot_ptr = ctx->d_slot_ptr.p; L.slot_row = ctx->d_slot_row.p; L.slot_sign = ctx->d_slot_sign.p;
   L.row_slot = ctx->d_row_slot.p; L.row_sign = ctx->d_row_sign.p; L.slot_occ = ctx->d_slot_occ.p;
+  L.ell_w = ell_w; L.ell_row = ctx->d_ell_row.p; L.ell_sign = ctx->d_ell_sign.p;
   L.occ_obase = ctx->d_occ_obase.p; L.occ_pat = ctx->d_occ_pat.p; L.occ_q = ctx->d_occ_q.p;
   L.occ_gofs = ctx->d_occ_gofs.p; L.occ_group = ctx->d_occ_group.p;
   for (int p = 0; p < n_pat; ++p) {
@@ -531,21 +668,27 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
     const int no = (int)P.occs.size();
     if (no > 0) {
       FETIRP_CUDA(cudaMemcpyAsync(P.U.p, P.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, s));
-      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, false, s);
-      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, true, s);
+      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, false, s, P.Dinv.p);
+      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, true, s, P.Dinv.p);
     }
     V.base[p] = P.U.p; V.ld[p] = P.npad; V.off[p] = P.n_i;
   }
   scatter<double>(L, V, 1, 0.0, ctx->d.p, s);
   axpy_f64(nl, -1.0, ctx->c.p, ctx->d.p, s);
   // work buffers
-  ctx->rr_blocks = std::max(1, std::min(304, ceil_div(nl, 64)));
+  ctx->rr_blocks = std::max(1, std::min(152, ceil_div(nl, 8)));
   ctx->rr_part.ensure(ctx->rr_blocks);
   ctx->lam.ensure(nl); ctx->r.ensure(nl); ctx->t1.ensure(nl);
   ctx->W.ensure((size_t)nl * k); ctx->Q.ensure((size_t)nl * k); ctx->Zr.ensure((size_t)nl * k);
   ctx->V1.ensure((size_t)nl * 64); ctx->V2.ensure((size_t)nl * 64);
-  ctx->eta.ensure((size_t)k * k); ctx->wr.ensure(k); ctx->T.ensure((size_t)k * k); ctx->alpha.ensure(k);
+  ctx->eta.ensure((size_t)k * k); ctx->wr.ensure(k);
+  ctx->eta_part.ensure((size_t)(std::min(152, ceil_div(nl, 16)) + 1) * k * (k + 1)); ctx->T.ensure((size_t)k * k); ctx->alpha.ensure(k);
   ctx->n_kept.ensure(1);
+  ctx->d_state.ensure(4);
+  if (!ctx->tc_error.p) { ctx->tc_error.alloc(1); ctx->tc_error.zero(s); }
+  tc_init();
+  ensure_apply_buffers(ctx, k);
+  if (ctx->gc.exec) { cudaGraphExecDestroy(ctx->gc.exec); ctx->gc.exec = nullptr; }   // buffers may have moved
   ctx->n_lambda = n_lambda;
   ctx->prepared = true;
   FETIRP_CUDA(cudaStreamSynchronize(s));
@@ -560,7 +703,7 @@ void project(fetirp_ctx ctx, double* V, int k) {
   ctx->Xc.ensure((size_t)ctx->n_G * k);
   ctx->Ac.ensure((size_t)ctx->n_G * k);
   gt_v(ctx->L, V, k, ctx->Xc.p, s);
-  gemm_f64(ctx->n_G, k, ctx->n_G, 1.0, ctx->Ginv.p, ctx->n_G, 1, ctx->Xc.p, k, 1, 0.0, ctx->Ac.p, k, 1, s);
+  small_gemm(ctx->n_G, k, ctx->Ginv.p, ctx->Xc.p, ctx->Ac.p, s);
   g_apply(ctx->L, ctx->Ac.p, k, -1.0, 1.0, V, s);
 }
 
@@ -698,89 +841,200 @@ void residual(fetirp_ctx ctx) {
   project(ctx, ctx->r.p, 1);
 }
 
+// lambda <- lambda_0 + P (lambda - lambda_0) in FP64: keeps G^T lambda = e exactly after corrections built
+// from directions that were stored in FP32 (their rounding leaves range(P) at the 1e-7 level).
+void reproject_lambda(fetirp_ctx ctx) {
+  if (ctx->n_G == 0) return;
+  const int nl = ctx->L.n_lambda;
+  cudaStream_t s = ctx->stream;
+  axpy_f64(nl, -1.0, ctx->lambda0.p, ctx->lam.p, s);
+  project(ctx, ctx->lam.p, 1);
+  axpy_f64(nl, 1.0, ctx->lambda0.p, ctx->lam.p, s);
+}
+
 struct Hist {
   long long cols = 0;   // columns stored
 };
 
+template <typename TH> TH* hist_w(fetirp_ctx ctx);
+template <typename TH> TH* hist_q(fetirp_ctx ctx);
+template <> double* hist_w<double>(fetirp_ctx ctx) { return ctx->Whist.p; }
+template <> double* hist_q<double>(fetirp_ctx ctx) { return ctx->Qhist.p; }
+template <> float* hist_w<float>(fetirp_ctx ctx) { return ctx->Whist32.p; }
+template <> float* hist_q<float>(fetirp_ctx ctx) { return ctx->Qhist32.p; }
+
+// One block iteration, enqueued only (no host read-back), so that it can be captured in a CUDA graph.  The
+// number of stored directions lives on the device (d_state[0]); every kernel that depends on it reads it there.
+// Reorthogonalisation coefficients C = Q_h^T W are FP64 sums; since Q_h lies in range(P) and W = P S(r),
+// C = Q_h^T S(r) is taken from the split structure of S(r) (at most two nonzero columns per row).
+template <typename TH>
+void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
+  cudaStream_t s = ctx->stream;
+  const int nl = ctx->L.n_lambda, k = ctx->k;
+  const long long cap = ctx->hist_cap;
+  int* d_cols = ctx->d_state.p;
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_UPDATE, 0.0, 0.0);
+    split(ctx->L, ctx->r.p, k, ctx->Zr.p, s);
+  }
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 0.0, 0.0);
+    gram_split<TH>((int)cap, d_cols, k, Qh, cap, ctx->r.p, ctx->d_grp_ptr.p, ctx->d_grp_row.p, ctx->d_grp_w.p,
+                   ctx->max_group_rows, ctx->C.p, ctx->gram_part, s);
+  }
+  project(ctx, ctx->Zr.p, k);
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 0.0, 0.0);
+    tall_update<TH>(nl, (int)cap, d_cols, k, Wh, cap, ctx->C.p, -1.0, ctx->Zr.p, ctx->tu_part, s);
+  }
+  apply_F(ctx, ctx->Zr.p, ctx->Q.p, k, prec, false, true);   // P~ = P^T F W (Table 1 line 5.1)
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 0.0, 0.0);
+    eta_and_wr(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta.p, ctx->wr.p, ctx->eta_part, s);
+  }
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_UPDATE, 0.0, 0.0);
+    normalise(k, ctx->eta.p, ctx->wr.p, prec == FETIRP_PREC_FP64 ? ctx->opt.eig_trunc : ctx->opt.eig_trunc_inner,
+              ctx->T.p, ctx->alpha.p, ctx->n_kept.p, s);
+    update<TH>(nl, k, ctx->Zr.p, ctx->Q.p, ctx->T.p, ctx->alpha.p, Wh, Qh, d_cols, cap, ctx->lam.p, ctx->r.p,
+               ctx->rr_part.p, ctx->rr_blocks, s);
+    advance(d_cols, k, cap, ctx->n_kept.p, ctx->d_state.p + 1, ctx->d_state.p + 2, s);
+  }
+}
+
+// Algorithmic work of one iteration with `a` stored directions (the per-phase flops and compulsory bytes).
+void account_iteration(fetirp_ctx ctx, int prec, long long a, double es) {
+  const double nl = ctx->L.n_lambda, k = ctx->k, nG = ctx->n_G;
+  double* F = ctx->phase_flops;
+  double* B = ctx->phase_bytes;
+  F[FETIRP_PHASE_GRAM] += 4.0 * nl * a + 2.0 * nl * k * (k + 1.0);
+  B[FETIRP_PHASE_GRAM] += es * nl * a + 24.0 * nl + 8.0 * nl * (2.0 * k + 1.0);
+  F[FETIRP_PHASE_REORTH] += 2.0 * nl * a * k;
+  B[FETIRP_PHASE_REORTH] += es * nl * a + 16.0 * nl * k;
+  F[FETIRP_PHASE_UPDATE] += 4.0 * nl * k * k + 4.0 * nl * k;
+  B[FETIRP_PHASE_UPDATE] += 8.0 * nl * (3.0 * k + 4.0) + 2.0 * es * nl * k;
+  F[FETIRP_PHASE_PROJECT] += 2.0 * (2.0 * nG * nG * k + 24.0 * nl * k);
+  B[FETIRP_PHASE_PROJECT] += 2.0 * (16.0 * nl * k + 8.0 * nG * nG);
+  const double e_loc = prec == FETIRP_PREC_FP64 ? 8.0 : 4.0;
+  double rhs = 0;
+  for (auto& P : ctx->pats) {
+    const double R = (double)P->occs.size() * k;
+    F[FETIRP_PHASE_LOCAL] += 2.0 * P->n_b * (double)P->n_b * R;
+    B[FETIRP_PHASE_LOCAL] += (prec == FETIRP_PREC_TF32X3 ? 2.0 : 1.0) * e_loc * P->n_b * (double)P->n_b +
+                             (prec == FETIRP_PREC_TF32X3 ? 3.0 : 2.0) * e_loc * P->n_b * R;
+    rhs += P->n_b * R;
+  }
+  B[FETIRP_PHASE_GATHER] += 8.0 * nl * k + (prec == FETIRP_PREC_TF32X3 ? 2.0 : 1.0) * e_loc * rhs;
+  B[FETIRP_PHASE_SCATTER] += 8.0 * nl * k + e_loc * rhs;
+}
+
+// Replay (or run) G iterations; returns the residual norm after the last one and the kept count.
+template <typename TH>
+void run_iterations(fetirp_ctx ctx, int prec, int G, bool use_graph, TH* Wh, TH* Qh) {
+  cudaStream_t s = ctx->stream;
+  auto& gc = ctx->gc;
+  const int th = (int)sizeof(TH);
+  if (use_graph) {
+    const bool valid = gc.exec && gc.prec == prec && gc.k == ctx->k && gc.G == G && gc.th == th &&
+                       gc.cap == ctx->hist_cap && gc.timing == ctx->opt.timing;
+    if (!valid) {
+      if (gc.exec) { cudaGraphExecDestroy(gc.exec); gc.exec = nullptr; }
+      gc.recs.clear();
+      for (auto& v : gc.launches) v = 0;
+      ctx->ev_used = ctx->ev_reserved = 0;
+      const unsigned long long l0 = g_launch_count;
+      cudaGraph_t graph = nullptr;
+      FETIRP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      ctx->capturing = true;
+      try {
+        for (int i = 0; i < G; ++i) enqueue_iteration<TH>(ctx, prec, Wh, Qh);
+      } catch (...) {
+        ctx->capturing = false;
+        cudaStreamEndCapture(s, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+      }
+      ctx->capturing = false;
+      FETIRP_CUDA(cudaStreamEndCapture(s, &graph));
+      cudaError_t e = cudaGraphInstantiate(&gc.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      FETIRP_CUDA(e);
+      gc.total_launches = (long long)(g_launch_count - l0);
+      g_launch_count = l0;   // captured, not launched
+      gc.prec = prec; gc.k = ctx->k; gc.G = G; gc.th = th; gc.cap = ctx->hist_cap; gc.timing = ctx->opt.timing;
+      ctx->ev_reserved = ctx->ev_used;
+    }
+    FETIRP_CUDA(cudaGraphLaunch(gc.exec, s));
+    g_launch_count += gc.total_launches;
+    for (int p = 0; p < FETIRP_NPHASE; ++p) ctx->phase_launches[p] += gc.launches[p];
+  } else {
+    for (int i = 0; i < G; ++i) enqueue_iteration<TH>(ctx, prec, Wh, Qh);
+  }
+}
+
 // Block ORTHODIR iterations on P^T F_prec P (Table 1 right with full reorthogonalisation and
 // F-normalisation).  Updates lam and r in place until ||r|| <= target or the caps are hit.  Directions kept in
-// the history stay F_prec-orthonormal, so a later call with the same precision reuses them.
+// the history stay F_prec-orthonormal, so a later call with the same precision reuses them (Galerkin start).
+// TH is the storage type of the direction history: FP64 for the plain form, FP32 inside the mixed forms.
+// Iterations run in groups of check_every, captured once as a CUDA graph and replayed; the residual is read
+// back after every group.
+template <typename TH>
 double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, Hist& H, fetirp_stats& st,
                       int& it_budget) {
   cudaStream_t s = ctx->stream;
   const int nl = ctx->L.n_lambda, k = ctx->k;
   const long long cap = ctx->hist_cap;
-  std::vector<double> rrh(ctx->rr_blocks);
+  TH* Wh = hist_w<TH>(ctx);
+  TH* Qh = hist_q<TH>(ctx);
+  const double es = sizeof(TH);
   // Galerkin start on the stored directions: lam += W_h (W_h^T r), r -= Q_h (W_h^T r)
   if (H.cols > 0) {
     const int a = (int)H.cols;
     {
-      PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 2.0 * nl * a, 8.0 * nl * (a + 1.0));
-      gram_f64(nl, a, 1, ctx->Whist.p, (int)cap, ctx->r.p, 1, ctx->C.p, ctx->gram_part, s);
+      PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 2.0 * nl * a, nl * (es * a + 8.0));
+      gram<TH, double>(nl, a, 1, Wh, (int)cap, ctx->r.p, 1, ctx->C.p, ctx->gram_part, s);
     }
     {
-      PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 4.0 * nl * a, 16.0 * nl * a);
-      gemm_f64(nl, 1, a, 1.0, ctx->Whist.p, cap, 1, ctx->C.p, 1, 1, 1.0, ctx->lam.p, 1, 1, s);
-      gemm_f64(nl, 1, a, -1.0, ctx->Qhist.p, cap, 1, ctx->C.p, 1, 1, 1.0, ctx->r.p, 1, 1, s);
+      PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 4.0 * nl * a, 2.0 * es * nl * a + 32.0 * nl);
+      tall_update<TH>(nl, a, nullptr, 1, Wh, cap, ctx->C.p, 1.0, ctx->lam.p, ctx->tu_part, s);
+      tall_update<TH>(nl, a, nullptr, 1, Qh, cap, ctx->C.p, -1.0, ctx->r.p, ctx->tu_part, s);
     }
     rnorm = norm2(ctx, ctx->r.p, nl);
   }
-  int check = std::max(1, ctx->opt.check_every);
-  int since = 0;
-  while (rnorm > target && it_budget > 0) {
-    if (H.cols + k > cap) H.cols = 0;   // history full: restart
-    double* Wn = ctx->Whist.p + H.cols;
-    double* Qn = ctx->Qhist.p + H.cols;
-    // multivector from the (projected) residual, then P
-    {
-      PhaseScope ph(ctx, FETIRP_PHASE_UPDATE, 0.0, 8.0 * nl * (k + 1.0));
-      split(ctx->L, ctx->r.p, k, ctx->Zr.p, s);
+  ctx->h_state[0] = (int)H.cols;
+  ctx->h_state[1] = 0;
+  ctx->h_state[2] = 0;
+  FETIRP_CUDA(cudaMemcpyAsync(ctx->d_state.p, ctx->h_state, 3 * sizeof(int), cudaMemcpyHostToDevice, s));
+  const int G = std::max(1, ctx->opt.check_every);
+  int kept = k;
+  while (rnorm > target && it_budget > 0 && kept > 0) {
+    const int g = std::min(G, it_budget);
+    run_iterations<TH>(ctx, prec, g, g == G && ctx->opt.use_graphs, Wh, Qh);
+    for (int i = 0; i < g; ++i) {   // host mirror of the device history count (same restart rule)
+      account_iteration(ctx, prec, H.cols, es);
+      H.cols += k;
+      if (H.cols + k > cap) H.cols = 0;
     }
-    project(ctx, ctx->Zr.p, k);
-    // full reorthogonalisation against the stored F-orthonormal directions
-    if (H.cols > 0) {
-      const int a = (int)H.cols;
-      {
-        PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 2.0 * nl * a * k, 8.0 * nl * (a + k));
-        gram_f64(nl, a, k, ctx->Qhist.p, (int)cap, ctx->Zr.p, k, ctx->C.p, ctx->gram_part, s);
+    FETIRP_CUDA(cudaMemcpyAsync(ctx->h_rr, ctx->rr_part.p, sizeof(double) * ctx->rr_blocks,
+                                cudaMemcpyDeviceToHost, s));
+    FETIRP_CUDA(cudaMemcpyAsync(ctx->h_state + 3, ctx->n_kept.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FETIRP_CUDA(cudaStreamSynchronize(s));
+    if (ctx->opt.timing && g == G && ctx->opt.use_graphs)
+      for (auto& r : ctx->gc.recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev_pool[r.e0], ctx->ev_pool[r.e1]) == cudaSuccess)
+          ctx->graph_phase_ms[r.phase] += ms;
       }
-      {
-        PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 2.0 * nl * a * k, 8.0 * nl * (a + 2.0 * k));
-        gemm_f64(nl, k, a, -1.0, ctx->Whist.p, cap, 1, ctx->C.p, k, 1, 1.0, ctx->Zr.p, k, 1, s);
-      }
-    }
-    // P~ = P^T F W (Table 1 line 5.1)
-    apply_F(ctx, ctx->Zr.p, ctx->Q.p, k, prec, false, true);
-    st.f_applies++;
-    {
-      PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 2.0 * nl * k * (k + 1.0), 8.0 * nl * (2.0 * k + 1.0));
-      gram_f64(nl, k, k, ctx->Zr.p, k, ctx->Q.p, k, ctx->eta.p, ctx->gram_part, s);
-      gram_f64(nl, k, 1, ctx->Zr.p, k, ctx->r.p, 1, ctx->wr.p, ctx->gram_part, s);
-    }
-    {
-      PhaseScope ph(ctx, FETIRP_PHASE_UPDATE, 4.0 * nl * k * k + 4.0 * nl * k, 8.0 * nl * (4.0 * k + 4.0));
-      normalise(k, ctx->eta.p, ctx->wr.p, prec == FETIRP_PREC_FP64 ? ctx->opt.eig_trunc : ctx->opt.eig_trunc_inner,
-                ctx->T.p, ctx->alpha.p, ctx->n_kept.p, s);
-      update(nl, k, ctx->Zr.p, ctx->Q.p, ctx->T.p, ctx->alpha.p, Wn, Qn, cap, ctx->lam.p, ctx->r.p, ctx->rr_part.p,
-             ctx->rr_blocks, s);
-    }
-    H.cols += k;
-    st.iterations++;
-    it_budget--;
-    if (++since >= check || it_budget == 0) {
-      since = 0;
-      int kept = 0;
-      FETIRP_CUDA(cudaMemcpyAsync(rrh.data(), ctx->rr_part.p, sizeof(double) * ctx->rr_blocks,
-                                  cudaMemcpyDeviceToHost, s));
-      FETIRP_CUDA(cudaMemcpyAsync(&kept, ctx->n_kept.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-      FETIRP_CUDA(cudaStreamSynchronize(s));
-      double acc = 0.0;
-      for (double v : rrh) acc += v;
-      rnorm = std::sqrt(acc);
-      st.dropped_directions += k - kept;
-      if (kept == 0) break;   // no new information: stagnation
-    }
+    double acc = 0.0;
+    for (int i = 0; i < ctx->rr_blocks; ++i) acc += ctx->h_rr[i];
+    rnorm = std::sqrt(acc);
+    kept = ctx->h_state[3];
+    st.iterations += g;
+    it_budget -= g;
   }
+  FETIRP_CUDA(cudaMemcpyAsync(ctx->h_state, ctx->d_state.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  FETIRP_CUDA(cudaStreamSynchronize(s));
+  st.dropped_directions += ctx->h_state[1];
   return rnorm;
 }
 
@@ -813,8 +1067,8 @@ void recover(fetirp_ctx ctx, double* d_u_out) {
     PatternData& P = *ctx->pats[p];
     const int no = (int)P.occs.size();
     if (no == 0) continue;
-    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, false, s);
-    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, true, s);
+    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, false, s, P.Dinv.p);
+    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, true, s, P.Dinv.p);
     if (P.kdim > 0 && ctx->n_G > 0)
       gemm_f64(P.npad, no, P.kdim, -1.0, P.N.p, 1, P.npad, ctx->Ac.p + ctx->pofs[p], 1, P.kdim, 1.0, P.U.p, 1,
                P.npad, s);
@@ -834,17 +1088,36 @@ void ensure_history(fetirp_ctx ctx) {
   long long limit = (8LL << 30) / (2LL * 8 * std::max(nl, 1));
   long long cap = std::max<long long>(k, std::min(want, limit));
   cap = cap / k * k;
-  if (cap != ctx->hist_cap || (long long)ctx->Whist.n < (long long)nl * cap) {
-    ctx->Whist.alloc((size_t)nl * cap);
-    ctx->Qhist.alloc((size_t)nl * cap);
-    ctx->hist_cap = cap;
+  if (ctx->opt.precision == FETIRP_PREC_FP64) {
+    if (cap != ctx->hist_cap || (long long)ctx->Whist.n < (long long)nl * cap) {
+      ctx->Whist.alloc((size_t)nl * cap);
+      ctx->Qhist.alloc((size_t)nl * cap);
+    }
+  } else if (cap != ctx->hist_cap || (long long)ctx->Whist32.n < (long long)nl * cap) {
+    ctx->Whist32.alloc((size_t)nl * cap);
+    ctx->Qhist32.alloc((size_t)nl * cap);
   }
+  if (cap != ctx->hist_cap && ctx->gc.exec) { cudaGraphExecDestroy(ctx->gc.exec); ctx->gc.exec = nullptr; }
+  ctx->hist_cap = cap;
+  const void* before[4] = {ctx->C.p, ctx->gram_part.p, ctx->Whist32.p, ctx->tu_part.p};
   ctx->C.ensure((size_t)cap * k);
   // gram partials: the largest product is (cap x k) over nl rows
   const int ta = ceil_div(cap, 64), tb = ceil_div(k, 64);
   const int chunks = std::max(1, std::min(ceil_div(nl, 64), 304 / std::max(1, ta * tb)));
   // any product a x b with a <= cap, b <= k uses at most max(chunks * cap * k, 304 * 64 * 64) partials
-  ctx->gram_part.ensure(std::max<size_t>((size_t)(chunks + 1) * cap * k, (size_t)304 * 64 * 64));
+  const int gs_chunks = std::max(1, ceil_div(ctx->max_group_rows, 128));
+  ctx->gram_part.ensure(std::max<size_t>(std::max<size_t>((size_t)(chunks + 1) * cap * k, (size_t)304 * 64 * 64),
+                                         (size_t)gs_chunks * cap * k));
+  {
+    const int tiles = ceil_div(nl, 64);
+    const int splits = std::max(1, std::min(std::max(1, 304 / tiles), ceil_div(cap, 32)));
+    ctx->tu_part.ensure((size_t)splits * nl * 64);
+  }
+  const void* after[4] = {ctx->C.p, ctx->gram_part.p, ctx->Whist32.p, ctx->tu_part.p};
+  if (ctx->gc.exec && std::memcmp(before, after, sizeof(before)) != 0) {
+    cudaGraphExecDestroy(ctx->gc.exec);
+    ctx->gc.exec = nullptr;
+  }
 }
 
 // A bounded wait inside the tensor-core kernel that expired leaves a nonzero code in tc_error.
@@ -880,14 +1153,15 @@ fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_st
   const int prec = ctx->opt.precision;
   if (r0 > 0.0) {
     if (prec == FETIRP_PREC_FP64) {
-      rn = block_orthodir(ctx, FETIRP_PREC_FP64, target, rn, H, st, budget);
+      rn = block_orthodir<double>(ctx, FETIRP_PREC_FP64, target, rn, H, st, budget);
       residual(ctx);   // report the FP64 residual of the final iterate
       rn = norm2(ctx, ctx->r.p, nl);
     } else {
       // outer FP64 defect correction: inner solves on the low-precision operator reuse their directions
       for (int outer = 0; outer < ctx->opt.max_outer && rn > target && budget > 0; ++outer) {
         const double inner_target = std::max(ctx->opt.inner_tol * rn, 0.5 * target);
-        block_orthodir(ctx, prec, inner_target, rn, H, st, budget);
+        block_orthodir<float>(ctx, prec, inner_target, rn, H, st, budget);
+        reproject_lambda(ctx);
         residual(ctx);
         rn = norm2(ctx, ctx->r.p, nl);
         st.outer_steps++;
@@ -949,9 +1223,10 @@ void fetirp_default_options(fetirp_options* o) {
   o->eig_trunc = 1e-12;
   o->cuda_stream = nullptr;
   o->device = 0;
-  o->check_every = 1;
+  o->check_every = 4;
   o->timing = 0;
   o->eig_trunc_inner = 1e-6;
+  o->use_graphs = 1;
 }
 
 const char* fetirp_status_string(fetirp_status s) {
@@ -984,6 +1259,12 @@ fetirp_status fetirp_create(const fetirp_options* opt, fetirp_ctx* out) {
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) return FETIRP_ECUDA;
   if (cudaSetDevice(o.device) != cudaSuccess) return FETIRP_ECUDA;
   ctx->stream = (cudaStream_t)o.cuda_stream;
+  if (!ctx->stream) {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return FETIRP_ECUDA;
+    ctx->owns_stream = true;
+  }
+  if (cudaMallocHost(&ctx->h_state, 8 * sizeof(int)) != cudaSuccess) return FETIRP_ENOMEM;
+  if (cudaMallocHost(&ctx->h_rr, 1024 * sizeof(double)) != cudaSuccess) return FETIRP_ENOMEM;
   *out = ctx.release();
   return FETIRP_OK;
 }
@@ -1057,7 +1338,7 @@ fetirp_status fetirp_create_pattern(fetirp_ctx ctx, int32_t n_nodes, int32_t dpn
     P->d_col.upload(P->col, ctx->stream);
     P->d_val.upload(P->val, ctx->stream);
     P->d_newidx.upload(P->newidx, ctx->stream);
-    factorize_pattern(ctx, *P);
+    factorize_patterns(ctx, {P.get()});
     *pattern_id = (int)ctx->pats.size();
     ctx->pats.push_back(std::move(P));
     invalidate(ctx);
@@ -1213,7 +1494,9 @@ fetirp_status fetirp_factorize(fetirp_ctx ctx) {
   return guarded(ctx, [&]() -> fetirp_status {
     reset_phases(ctx);
     const unsigned long long l0 = g_launch_count;
-    for (auto& P : ctx->pats) factorize_pattern(ctx, *P);
+    std::vector<PatternData*> all;
+    for (auto& P : ctx->pats) all.push_back(P.get());
+    factorize_patterns(ctx, all);
     ctx->phases_pending = true;
     ctx->pending_launches = (long long)(g_launch_count - l0);
     invalidate(ctx);

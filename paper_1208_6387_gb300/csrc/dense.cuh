@@ -33,8 +33,11 @@ void chol_tiles(double* A, int npad, const TilePlan& plan, const double* diag0, 
 
 // X <- L^{-1} X (trans = false) or X <- L^{-T} X (trans = true), X column-major npad x nrhs (ld = ldx),
 // zero-pivot rows of the result set to 0.  Right-looking over tile columns, skipping zero tiles.
+// Dinv (optional): inverted diagonal tiles from tile_inverses(); each diagonal step is then a parallel product.
 void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, double* X, int ldx, int nrhs,
-               bool trans, cudaStream_t s);
+               bool trans, cudaStream_t s, const double* Dinv = nullptr);
+// Dinv (npad/64 tiles of 64 x 64, column-major) = inverses of the diagonal tiles of L (zero pivots -> 0).
+void tile_inverses(const double* L, int npad, const int* zp, double* Dinv, cudaStream_t s);
 
 // C(m, n) = alpha * sum_k A(m, k) B(k, n) + beta * C(m, n) with arbitrary element strides:
 // A(m, k) = A[m * sAm + k * sAk], B(k, n) = B[k * sBk + n * sBn], C(m, n) = C[m * sCm + n * sCn].

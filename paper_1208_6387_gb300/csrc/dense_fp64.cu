@@ -162,6 +162,72 @@ __global__ void __launch_bounds__(256) k_update_pairs(double* A, int npad, int k
     for (int q = 0; q < 4; ++q) C[(size_t)(tx * 4 + q) * npad + ty * 4 + p] -= acc[p][q];
 }
 
+// Inverse of every diagonal tile, all tiles in parallel (one CTA per tile): Dinv_J = L_JJ^{-1} by forward
+// substitution on the identity, zero-pivot rows and columns left at 0 (the same linear map as solving with
+// the zero pivot skipped).  Stored column-major, 64 x 64 per tile.
+__global__ void __launch_bounds__(256) k_tile_inverse(const double* L, int npad, const int* zp, double* Dinv) {
+  __shared__ double l[TILE][TILE + 1];
+  __shared__ double x[TILE][TILE + 1];
+  const int tid = threadIdx.x;
+  const int J = blockIdx.x;
+  const double* D = L + (size_t)J * TILE * npad + (size_t)J * TILE;
+  for (int idx = tid; idx < TILE * TILE; idx += 256) {
+    int r = idx % TILE, c = idx / TILE;
+    l[r][c] = D[(size_t)c * npad + r];
+    x[r][c] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < TILE; ++j) {
+    const bool zero = zp[J * TILE + j] != 0;
+    if (tid < TILE) x[j][tid] = zero ? 0.0 : x[j][tid] / l[j][j];
+    __syncthreads();
+    for (int idx = tid; idx < (TILE - 1 - j) * TILE; idx += 256) {
+      int r = j + 1 + idx / TILE, c = idx % TILE;
+      x[r][c] -= l[r][j] * x[j][c];
+    }
+    __syncthreads();
+  }
+  double* out = Dinv + (size_t)J * TILE * TILE;
+  for (int idx = tid; idx < TILE * TILE; idx += 256) {
+    int r = idx % TILE, c = idx / TILE;
+    out[(size_t)c * TILE + r] = x[r][c];
+  }
+}
+
+// X_J <- Dinv_J X_J (forward) or Dinv_J^T X_J (backward) for a chunk of 16 right-hand sides (4 rows x 1 rhs
+// per thread), so that narrow solves spread over many SMs.
+__global__ void __launch_bounds__(256) k_tri_diag_inv(const double* __restrict__ Dinv, int J, double* X, int ldx,
+                                                      int nrhs, int trans) {
+  __shared__ double a[TILE][TILE + 1];   // a[r][c] = op(Dinv_J)(r, c)
+  __shared__ double x[TILE][17];         // x[row][rhs]
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * 16;
+  const double* D = Dinv + (size_t)J * TILE * TILE;
+  for (int idx = tid; idx < TILE * TILE; idx += 256) {
+    int r = idx % TILE, c = idx / TILE;
+    const double v = D[(size_t)c * TILE + r];   // Dinv(r, c)
+    if (trans) a[c][r] = v; else a[r][c] = v;
+  }
+  for (int idx = tid; idx < TILE * 16; idx += 256) {
+    int r = idx % TILE, c = idx / TILE;
+    x[r][c] = (c0 + c < nrhs) ? X[(size_t)(c0 + c) * ldx + (size_t)J * TILE + r] : 0.0;
+  }
+  __syncthreads();
+  const int tx = tid % 16, ty = tid / 16;   // rhs tx, rows ty*4 .. +3
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 8
+  for (int q = 0; q < TILE; ++q) {
+    const double b = x[q][tx];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = fma(a[ty * 4 + u][q], b, acc[u]);
+  }
+  const int c = c0 + tx;
+  if (c < nrhs) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) X[(size_t)c * ldx + (size_t)J * TILE + ty * 4 + u] = acc[u];
+  }
+}
+
 // Triangular solve on one diagonal tile J for a chunk of 64 right-hand sides (blockIdx.x).
 __global__ void __launch_bounds__(256) k_tri_diag(const double* L, int npad, int J, const int* zp, double* X,
                                                   int ldx, int nrhs, int trans) {
@@ -206,44 +272,88 @@ __global__ void __launch_bounds__(256) k_tri_diag(const double* L, int npad, int
 }
 
 // After solving tile J: X_I -= L_IJ X_J (forward, I in list) or X_I -= L_JI^T X_J (backward, I in list).
-// grid (list count, rhs chunks).
+// grid (list count, chunks of 16 right-hand sides): 64 rows x 16 rhs per CTA, 4 rows x 1 rhs per thread, so
+// that narrow solves (one column per occurrence) still spread their FP64 work over many SMs.
+constexpr int TU_RHS = 16;
 __global__ void __launch_bounds__(256) k_tri_update(const double* L, int npad, int J, const int* list, double* X,
                                                     int ldx, int nrhs, int trans) {
   __shared__ double sa[16][TILE + 1];   // [kk][row of output]
-  __shared__ double sb[16][TILE + 1];   // [kk][rhs]
+  __shared__ double sb[16][TU_RHS + 1]; // [kk][rhs]
   const int tid = threadIdx.x;
   const int I = list[blockIdx.x];
-  const int c0 = blockIdx.y * TILE;
-  const int tx = tid % 16, ty = tid / 16;
-  double acc[4][4] = {};
+  const int c0 = blockIdx.y * TU_RHS;
+  const int tx = tid % 16, ty = tid / 16;   // rhs tx, rows ty*4 .. +3
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int kk0 = 0; kk0 < TILE; kk0 += 16) {
     for (int idx = tid; idx < 16 * TILE; idx += 256) {
-      int r = idx % TILE, kk = idx / TILE;
-      // A(r, kk) = L_IJ(r, kk) or L_JI(kk, r)
+      const int r = idx % TILE, kk = idx / TILE;
       if (!trans) sa[kk][r] = L[(size_t)(J * TILE + kk0 + kk) * npad + I * TILE + r];
       else sa[kk][r] = L[(size_t)(I * TILE + r) * npad + J * TILE + kk0 + kk];
-      int c = idx % TILE, k2 = idx / TILE;
+    }
+    {
+      const int k2 = tid / 16, c = tid % 16;
       sb[k2][c] = (c0 + c < nrhs) ? X[(size_t)(c0 + c) * ldx + (size_t)J * TILE + kk0 + k2] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      double av[4], bv[4];
+      const double b = sb[kk][tx];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) { av[q] = sa[kk][ty * 4 + q]; bv[q] = sb[kk][tx * 4 + q]; }
+      for (int u = 0; u < 4; ++u) acc[u] = fma(sa[kk][ty * 4 + u], b, acc[u]);
+    }
+    __syncthreads();
+  }
+  const int c = c0 + tx;
+  if (c < nrhs) {
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = fma(av[p], bv[q], acc[p][q]);
+    for (int u = 0; u < 4; ++u) X[(size_t)c * ldx + (size_t)I * TILE + ty * 4 + u] -= acc[u];
+  }
+}
+
+// Generic strided GEMM, 32x32 output tile per CTA, 2x2 per thread (small FP64 products: more CTAs).
+__global__ void __launch_bounds__(256) k_gemm_f64_32(int M, int N, int K, double alpha, const double* __restrict__ A,
+                                                     long long sAm, long long sAk, const double* __restrict__ B,
+                                                     long long sBk, long long sBn, double beta, double* C,
+                                                     long long sCm, long long sCn) {
+  __shared__ double sa[32][33];
+  __shared__ double sb[32][33];
+  const int tid = threadIdx.x;
+  const int m0 = blockIdx.x * 32, n0 = blockIdx.y * 32;
+  const int tx = tid % 16, ty = tid / 16;
+  double acc[2][2] = {};
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int idx = tid; idx < 32 * 32; idx += 256) {
+      int r, kk;
+      if (sAk == 1) { kk = idx % 32; r = idx / 32; } else { r = idx % 32; kk = idx / 32; }
+      const int m = m0 + r, k = k0 + kk;
+      sa[kk][r] = (m < M && k < K) ? A[m * sAm + k * sAk] : 0.0;
+      int c, k2;
+      if (sBk == 1) { k2 = idx % 32; c = idx / 32; } else { c = idx % 32; k2 = idx / 32; }
+      const int n = n0 + c, kb = k0 + k2;
+      sb[k2][c] = (n < N && kb < K) ? B[kb * sBk + n * sBn] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const double a0 = sa[kk][ty * 2], a1 = sa[kk][ty * 2 + 1];
+      const double b0 = sb[kk][tx * 2], b1 = sb[kk][tx * 2 + 1];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    int c = c0 + tx * 4 + q;
-    if (c < nrhs) {
+  for (int p = 0; p < 2; ++p) {
+    const int m = m0 + ty * 2 + p;
+    if (m >= M) continue;
 #pragma unroll
-      for (int p = 0; p < 4; ++p) X[(size_t)c * ldx + (size_t)I * TILE + ty * 4 + p] -= acc[p][q];
+    for (int q = 0; q < 2; ++q) {
+      const int n = n0 + tx * 2 + q;
+      if (n >= N) continue;
+      double* c = C + m * sCm + n * sCn;
+      *c = alpha * acc[p][q] + (beta == 0.0 ? 0.0 : beta * *c);
     }
   }
 }
@@ -327,29 +437,38 @@ void chol_tiles(double* A, int npad, const TilePlan& plan, const double* diag0, 
   zero_zp_rows(A, npad, zp, s);
 }
 
+void tile_inverses(const double* L, int npad, const int* zp, double* Dinv, cudaStream_t s) {
+  k_tile_inverse<<<npad / TILE, 256, 0, s>>>(L, npad, zp, Dinv);
+  FETIRP_LAUNCH_CHECK();
+}
+
 void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, double* X, int ldx, int nrhs,
-               bool trans, cudaStream_t s) {
+               bool trans, cudaStream_t s, const double* Dinv) {
   if (nrhs <= 0) return;
   const int chunks = ceil_div(nrhs, TILE);
+  auto diag = [&](int J, int tr) {
+    if (Dinv) k_tri_diag_inv<<<ceil_div(nrhs, 16), 256, 0, s>>>(Dinv, J, X, ldx, nrhs, tr);
+    else k_tri_diag<<<chunks, 256, 0, s>>>(L, npad, J, zp, X, ldx, nrhs, tr);
+  };
   if (!trans) {
     for (int J = 0; J < plan.nt; ++J) {
-      k_tri_diag<<<chunks, 256, 0, s>>>(L, npad, J, zp, X, ldx, nrhs, 0);
+      diag(J, 0);
       FETIRP_LAUNCH_CHECK();
       int nr = plan.col_off[J + 1] - plan.col_off[J];
       if (nr > 0) {
-        k_tri_update<<<dim3(nr, chunks), 256, 0, s>>>(L, npad, J, plan.d_col_rows.p + plan.col_off[J], X, ldx,
-                                                      nrhs, 0);
+        k_tri_update<<<dim3(nr, ceil_div(nrhs, TU_RHS)), 256, 0, s>>>(L, npad, J, plan.d_col_rows.p + plan.col_off[J],
+                                                                      X, ldx, nrhs, 0);
         FETIRP_LAUNCH_CHECK();
       }
     }
   } else {
     for (int J = plan.nt - 1; J >= 0; --J) {
-      k_tri_diag<<<chunks, 256, 0, s>>>(L, npad, J, zp, X, ldx, nrhs, 1);
+      diag(J, 1);
       FETIRP_LAUNCH_CHECK();
       int nr = plan.row_off[J + 1] - plan.row_off[J];
       if (nr > 0) {
-        k_tri_update<<<dim3(nr, chunks), 256, 0, s>>>(L, npad, J, plan.d_row_cols.p + plan.row_off[J], X, ldx,
-                                                      nrhs, 1);
+        k_tri_update<<<dim3(nr, ceil_div(nrhs, TU_RHS)), 256, 0, s>>>(L, npad, J, plan.d_row_cols.p + plan.row_off[J],
+                                                                      X, ldx, nrhs, 1);
         FETIRP_LAUNCH_CHECK();
       }
     }
@@ -361,7 +480,12 @@ void gemm_f64(int M, int N, int K, double alpha, const double* A, long long sAm,
               cudaStream_t s) {
   if (M <= 0 || N <= 0) return;
   dim3 grid(ceil_div(M, TILE), ceil_div(N, TILE));
-  k_gemm_f64<<<grid, 256, 0, s>>>(M, N, K, alpha, A, sAm, sAk, B, sBk, sBn, beta, C, sCm, sCn);
+  if ((long long)grid.x * grid.y < 2 * 152) {   // too few 64x64 tiles to occupy the SMs' FP64 units
+    dim3 g32(ceil_div(M, 32), ceil_div(N, 32));
+    k_gemm_f64_32<<<g32, 256, 0, s>>>(M, N, K, alpha, A, sAm, sAk, B, sBk, sBn, beta, C, sCm, sCn);
+  } else {
+    k_gemm_f64<<<grid, 256, 0, s>>>(M, N, K, alpha, A, sAm, sAk, B, sBk, sBn, beta, C, sCm, sCn);
+  }
   FETIRP_LAUNCH_CHECK();
 }
 

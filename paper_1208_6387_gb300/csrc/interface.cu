@@ -4,10 +4,21 @@
 
 namespace fetirp {
 
+// y(slot, g) = sum over the slot's links: sign * V[row][g]   (ELL links, independent loads)
+__device__ __forceinline__ double trace_of(const Layout& L, const double* __restrict__ V, int k, int slot, int g) {
+  const int* er = L.ell_row + (size_t)slot * L.ell_w;
+  const int8_t* es = L.ell_sign + (size_t)slot * L.ell_w;
+  double y = 0.0;
+#pragma unroll 4
+  for (int e = 0; e < L.ell_w; ++e) y = fma((double)es[e], V[(size_t)er[e] * k + g], y);
+  return y;
+}
+
 // X[gofs(s)+m][g] = sum_{links of s} sign * Nb[j][m] * V[row][g]        (one CTA per occurrence)
 // Thread t takes column g = t % k and every (256/k)-th boundary dof; partial sums per kernel mode m live in
 // registers and are reduced over the threads of one column in a fixed order (deterministic).
 constexpr int GTV_THREADS = 256;
+constexpr int GTV_COLS = 8;     // columns per CTA (grid.y splits the block of k columns)
 constexpr int MAX_KDIM = 6;
 __global__ void __launch_bounds__(GTV_THREADS) k_gt_v(Layout L, const double* __restrict__ V, int k,
                                                        double* __restrict__ X) {
@@ -19,15 +30,15 @@ __global__ void __launch_bounds__(GTV_THREADS) k_gt_v(Layout L, const double* __
   const int b0 = L.occ_obase[s], nb = L.occ_obase[s + 1] - b0;
   const int g0 = L.occ_gofs[s];
   const int t = threadIdx.x;
-  const int lanes = GTV_THREADS / k;        // threads per column (k <= 64 -> >= 4)
-  const int g = t % k, sub = t / k;
+  const int gbase = blockIdx.y * GTV_COLS;
+  const int kk = min(GTV_COLS, k - gbase);
+  const int lanes = GTV_THREADS / kk;       // threads per column
+  const int g = gbase + t % kk, sub = t / kk;
   double acc[MAX_KDIM] = {};
   if (sub < lanes) {
+#pragma unroll 2
     for (int j = sub; j < nb; j += lanes) {
-      const int slot = b0 + j;
-      double y = 0.0;
-      for (int e = L.slot_ptr[slot]; e < L.slot_ptr[slot + 1]; ++e)
-        y = fma((double)L.slot_sign[e], V[(size_t)L.slot_row[e] * k + g], y);
+      const double y = trace_of(L, V, k, b0 + j, g);
 #pragma unroll
       for (int m = 0; m < MAX_KDIM; ++m)
         if (m < kd) acc[m] = fma(Nb[(size_t)j * kd + m], y, acc[m]);
@@ -36,11 +47,11 @@ __global__ void __launch_bounds__(GTV_THREADS) k_gt_v(Layout L, const double* __
 #pragma unroll
   for (int m = 0; m < MAX_KDIM; ++m) red[t][m] = acc[m];
   __syncthreads();
-  if (t < k) {
+  if (t < kk) {
     for (int m = 0; m < kd; ++m) {
       double v = 0.0;
-      for (int q = 0; q < lanes; ++q) v += red[q * k + t][m];
-      X[(size_t)(g0 + m) * k + t] = v;
+      for (int q = 0; q < lanes; ++q) v += red[q * kk + t][m];
+      X[(size_t)(g0 + m) * k + gbase + t] = v;
     }
   }
 }
@@ -116,12 +127,10 @@ __global__ void k_gather(Layout L, const double* __restrict__ V, int k, PatView<
   const int b0 = L.occ_obase[s], nb = L.occ_obase[s + 1] - b0;
   TO* base = Y.base[p];
   const long long ld = Y.ld[p], off = Y.off[p];
-  for (int idx = threadIdx.x; idx < nb * k; idx += blockDim.x) {
-    const int g = idx / nb, j = idx % nb;
-    const int slot = b0 + j;
-    double acc = 0.0;
-    for (int e = L.slot_ptr[slot]; e < L.slot_ptr[slot + 1]; ++e)
-      acc = fma((double)L.slot_sign[e], V[(size_t)L.slot_row[e] * k + g], acc);
+  const int gbase = blockIdx.y * GTV_COLS, kk = min(GTV_COLS, k - gbase);
+  for (int idx = threadIdx.x; idx < nb * kk; idx += blockDim.x) {
+    const int g = gbase + idx / nb, j = idx % nb;
+    const double acc = trace_of(L, V, k, b0 + j, g);
     TO* y = base + ((long long)q * k + g) * ld + off + j;
     *y = (TO)((beta == 0.0 ? 0.0 : beta * (double)*y) + alpha * acc);
   }
@@ -133,13 +142,10 @@ __global__ void k_gather_split(Layout L, const double* __restrict__ V, int k, Pa
   const int p = L.occ_pat[s];
   const int q = L.occ_q[s];
   const int b0 = L.occ_obase[s], nb = L.occ_obase[s + 1] - b0;
-  for (int idx = threadIdx.x; idx < nb * k; idx += blockDim.x) {
-    const int g = idx / nb, j = idx % nb;
-    const int slot = b0 + j;
-    double acc = 0.0;
-    for (int e = L.slot_ptr[slot]; e < L.slot_ptr[slot + 1]; ++e)
-      acc = fma((double)L.slot_sign[e], V[(size_t)L.slot_row[e] * k + g], acc);
-    const float v = (float)acc;
+  const int gbase = blockIdx.y * GTV_COLS, kk = min(GTV_COLS, k - gbase);
+  for (int idx = threadIdx.x; idx < nb * kk; idx += blockDim.x) {
+    const int g = gbase + idx / nb, j = idx % nb;
+    const float v = (float)trace_of(L, V, k, b0 + j, g);
     uint32_t t;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
     const float h = __uint_as_float(t);
@@ -189,7 +195,7 @@ __global__ void k_split(Layout L, const double* __restrict__ r, int k, double* _
 void gt_v(const Layout& L, const double* V, int k, double* X, cudaStream_t s) {
   if (L.n_occ == 0) return;
   if (k > 64) throw Error(1, "k > 64");
-  k_gt_v<<<L.n_occ, GTV_THREADS, 0, s>>>(L, V, k, X);
+  k_gt_v<<<dim3(L.n_occ, ceil_div(k, GTV_COLS)), GTV_THREADS, 0, s>>>(L, V, k, X);
   FETIRP_LAUNCH_CHECK();
 }
 
@@ -212,7 +218,7 @@ template <typename TO>
 void gather(const Layout& L, const double* V, int k, const PatView<TO>& Y, cudaStream_t s, double alpha,
             double beta) {
   if (L.n_occ == 0) return;
-  k_gather<TO><<<L.n_occ, 256, 0, s>>>(L, V, k, Y, alpha, beta);
+  k_gather<TO><<<dim3(L.n_occ, ceil_div(k, GTV_COLS)), 256, 0, s>>>(L, V, k, Y, alpha, beta);
   FETIRP_LAUNCH_CHECK();
 }
 
@@ -227,7 +233,7 @@ void scatter(const Layout& L, const PatView<TI>& Z, int k, double beta, double* 
 void gather_split(const Layout& L, const double* V, int k, const PatView<float>& Yh, const PatView<float>& Yl,
                   cudaStream_t s) {
   if (L.n_occ == 0) return;
-  k_gather_split<<<L.n_occ, 256, 0, s>>>(L, V, k, Yh, Yl);
+  k_gather_split<<<dim3(L.n_occ, ceil_div(k, GTV_COLS)), 256, 0, s>>>(L, V, k, Yh, Yl);
   FETIRP_LAUNCH_CHECK();
 }
 

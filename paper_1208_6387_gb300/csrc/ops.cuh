@@ -23,6 +23,10 @@ struct Layout {
   const int* slot_ptr;
   const int* slot_row;
   const int8_t* slot_sign;
+  // the same links in ELL form: ell_w entries per slot (sign 0 = padding, row 0)
+  int ell_w = 1;
+  const int* ell_row;
+  const int8_t* ell_sign;
   // scatter by row: up to two (slot, sign); sign 0 = empty
   const int* row_slot;
   const int8_t* row_sign;
@@ -84,6 +88,30 @@ void local_gemm_f32(const LocalProblem& P, cudaStream_t s);
 // order (two passes: per-chunk partials, then an ordered sum).
 void gram_f64(int n, int a, int b, const double* A, int lda, const double* B, int ldb, double* C,
               DBuf<double>& partial, cudaStream_t s);
+template <typename TA, typename TB>
+void gram(int n, int a, int b, const TA* A, int lda, const TB* B, int ldb, double* C, DBuf<double>& partial,
+          cudaStream_t s);
+// Reorthogonalisation coefficients C = Qh^T S(r) (a x k, row-major) of the split multivector S(r) without
+// forming it: group g's rows (grp_ptr/grp_row) with weights grp_w = 1/(occurrences of the row).  FP64 sums.
+// The number of stored directions a is read from d_a on the device when d_a != NULL (at most a_max), so one
+// captured launch serves every iteration.
+template <typename TH>
+void gram_split(int a_max, const int* d_a, int k, const TH* Qh, long long ldq, const double* r, const int* grp_ptr,
+                const int* grp_row, const double* grp_w, int max_group_rows, double* C, DBuf<double>& partial,
+                cudaStream_t s);
+// W (n x k, FP64) += alpha * Wh (n x a, history type TH, leading dimension ldh) * C (a x k, FP64), computed
+// in TH arithmetic.
+// scratch: split partials (grown here; callers that capture graphs size it first with the same arguments).
+template <typename TH>
+void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, long long ldh, const double* C, double alpha,
+                 double* W, DBuf<double>& scratch, cudaStream_t s);
+// history count += k with restart, dropped and iteration counters (one thread)
+void advance(int* cols, int k, long long cap, const int* n_kept, int* dropped, int* iters, cudaStream_t s);
+// eta = W^T Q (k x k, row-major) and wr = W^T r (k) in one pass over the rows (FP64 sums, fixed order).
+void eta_and_wr(int n, int k, const double* W, const double* Q, const double* r, double* eta, double* wr,
+                DBuf<double>& partial, cudaStream_t s);
+// C (m x k) = A (m x m) B (m x k), row-major, FP64, one warp per row (small coarse products).
+void small_gemm(int m, int k, const double* A, const double* B, double* C, cudaStream_t s);
 // Normalisation of eta = W^T P~ (k x k row-major) so that T^T eta T = I on the kept directions: pivoted
 // Cholesky eta = Pi M M^T Pi^T, stopping when the largest remaining pivot <= trunc * (largest diagonal);
 // T = Pi M^{-T} on the kept columns (zero columns for dropped ones); alpha = T^T wr with wr = W^T r.
@@ -92,8 +120,10 @@ void normalise(int k, const double* eta, const double* wr, double trunc, double*
                cudaStream_t s);
 // Wn = W T, Qn = Q T (n x k each, written to history), lambda += Wn alpha, r -= Qn alpha, and
 // rr_partial[block] = partial sums of r^2 after the update.
-void update(int n, int k, const double* W, const double* Q, const double* T, const double* alpha,
-            double* Wn, double* Qn, long long ldn, double* lam, double* r, double* rr_partial, int rr_blocks,
+// d_off (device, may be NULL): column offset added to Wn and Qn on the device.
+template <typename TH>
+void update(int n, int k, const double* W, const double* Q, const double* T, const double* alpha, TH* Wn, TH* Qn,
+            const int* d_off, long long ldn, double* lam, double* r, double* rr_partial, int rr_blocks,
             cudaStream_t s);
 void sum_sq(int n, const double* x, double* out_partial, int blocks, cudaStream_t s);
 void axpy_f64(int n, double a, const double* x, double* y, cudaStream_t s);

@@ -23,6 +23,9 @@ struct TcProblem {
 // that receives a nonzero code if a bounded wait inside the kernel expired (0 otherwise).
 void tc_gemm_tf32x3(const TcProblem& T, int* d_error, cudaStream_t s);
 
+// One-time kernel attribute set-up (large dynamic shared memory); call before any graph capture.
+void tc_init();
+
 // hi = tf32(x) (round to nearest), lo = x - hi; x is FP64, outputs FP32 with leading dimension ld_out.
 void split_tf32(const double* x, long long rows, long long cols, long long ld_in, float* hi, float* lo,
                 long long ld_out, cudaStream_t s);

@@ -323,12 +323,19 @@ void split_tf32(const double* x, long long rows, long long cols, long long ld_in
   FETIRP_LAUNCH_CHECK();
 }
 
-void tc_gemm_tf32x3(const TcProblem& T, int* d_error, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+void tc_init() {
+  static int attr_device = -1;
+  int dev = 0;
+  FETIRP_CUDA(cudaGetDevice(&dev));
+  if (attr_device != dev) {
     FETIRP_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr = true;
+    attr_device = dev;
   }
+  encode_fn();   // resolve the driver entry point outside any stream capture
+}
+
+void tc_gemm_tf32x3(const TcProblem& T, int* d_error, cudaStream_t s) {
+  tc_init();
   for (int base = 0; base < T.n_pat; base += TC_MAXP) {
     TcParams P;
     std::memset(&P, 0, sizeof(P));

@@ -24,7 +24,8 @@ class fetirp_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32), ("block_k", C.c_int32),
                 ("max_outer", C.c_int32), ("inner_tol", C.c_double), ("pivot_tol", C.c_double),
                 ("eig_trunc", C.c_double), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
-                ("check_every", C.c_int32), ("timing", C.c_int32), ("eig_trunc_inner", C.c_double)]
+                ("check_every", C.c_int32), ("timing", C.c_int32), ("eig_trunc_inner", C.c_double),
+                ("use_graphs", C.c_int32)]
 
 
 PHASES = ["factor", "coarse", "local", "gather", "scatter", "project", "gram", "reorth", "update", "recover"]
