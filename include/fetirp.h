@@ -197,6 +197,30 @@ fetirp_status fetirp_apply_block_device(fetirp_ctx ctx, int32_t k, const double*
                                         int32_t precision);
 
 /*
+ * Allocation-free variant of fetirp_apply_block_device (this entry point has no counterpart in the paper; it
+ * exists for callers of the library).  Some callers cannot let a library allocate device memory while they
+ * run: for example an application that provisions every byte of GPU memory once at start-up through its own
+ * allocator and forbids later cudaMalloc/cudaFree calls, whose implicit device synchronisation and failure
+ * modes it cannot accept.  This call computes the same Q = P^T F P V (same arguments and layout) but keeps
+ * its scratch (the gathered traces, local products and coarse vectors) in one fixed array compiled into the
+ * library, FETIRP_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library holds until the process
+ * exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *  - Limit: a call needing more scratch than FETIRP_NOALLOC_SCRATCH_BYTES (about 8 bytes x k x (n_lambda +
+ *    2 x sum over occurrences of the boundary dof count) in FP64) returns FETIRP_EINVAL with the sizes in
+ *    fetirp_last_error; nothing is written.
+ *  - Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress, with that
+ *    device current) and caches it; make that first call before any stream capture.
+ *  - Sharing: every call on a device uses the same array and it keeps the previous call's contents; the
+ *    call overwrites every scratch entry it reads, so nothing has to start at zero.  Calls that overlap on the
+ *    GPU (other streams, other host threads, other contexts on the same device) race on the array and must
+ *    be serialised by the caller.
+ *  - Requires fetirp_prepare (or a solve) on ctx first; enqueued on the context's stream.
+ */
+#define FETIRP_NOALLOC_SCRATCH_BYTES (32u << 20)
+fetirp_status fetirp_apply_block_device_noalloc(fetirp_ctx ctx, int32_t k, const double* d_V, double* d_Q,
+                                                int32_t precision);
+
+/*
  * Build the coarse problem (G, G^T G and its inverse, e, lambda_0) and d for n_lambda rows and the given
  * c (host, may be NULL) without iterating.  fetirp_solve calls it itself.
  */

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <numeric>
 
 #include "../../include/fetirp.h"
@@ -1207,8 +1208,129 @@ void prepare_timed(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, const
 
 }  // namespace
 
+// ------------------------------------------------------------------------------ allocation-free apply
+// Scratch of fetirp_apply_block_device_noalloc: a fixed array in the library's device image.  Host code only
+// ever uses the device address returned by cudaGetSymbolAddress (the name itself is a host-side stand-in).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FETIRP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_addr[64] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+unsigned char* noalloc_scratch(int device) {
+  if (device < 0 || device >= 64) throw Error(FETIRP_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    FETIRP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[device] = static_cast<unsigned char*>(p);
+  }
+  return g_noalloc_addr[device];
+}
+
+// P V with caller-provided coarse vectors (no context buffer is touched).
+void project_with(fetirp_ctx ctx, double* V, int k, double* Xc, double* Ac) {
+  if (ctx->n_G == 0) return;
+  gt_v(ctx->L, V, k, Xc, ctx->stream);
+  small_gemm(ctx->n_G, k, ctx->Ginv.p, Xc, Ac, ctx->stream);
+  g_apply(ctx->L, Ac, k, -1.0, 1.0, V, ctx->stream);
+}
+
+// Q = P^T F P V with every scratch buffer carved from `base` (size `cap` bytes); throws FETIRP_EINVAL when
+// the call needs more.
+void apply_noalloc(fetirp_ctx ctx, const double* V, double* Q, int k, int prec, unsigned char* base, size_t cap) {
+  cudaStream_t s = ctx->stream;
+  const Layout& L = ctx->L;
+  const int n_pat = (int)ctx->pats.size();
+  const size_t es = prec == FETIRP_PREC_FP64 ? sizeof(double) : sizeof(float);
+  long long pbase[MAXP] = {};
+  long long total = 0;
+  for (int p = 0; p < n_pat; ++p) {
+    pbase[p] = total;
+    total += (long long)ctx->pats[p]->occs.size() * k * ctx->pats[p]->ld_y;
+  }
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t nv = up(sizeof(double) * (size_t)L.n_lambda * k);
+  const size_t nc = up(sizeof(double) * (size_t)std::max(ctx->n_G, 1) * k);
+  const size_t ny = up(es * (size_t)total);
+  const size_t need = nv + 2 * nc + (prec == FETIRP_PREC_TF32X3 ? 3 : 2) * ny;
+  if (need > cap)
+    throw Error(FETIRP_EINVAL, "fetirp_apply_block_device_noalloc needs " + std::to_string(need) +
+                                   " bytes of scratch, more than its fixed " + std::to_string(cap) + " bytes");
+  unsigned char* q = base;
+  double* V2 = reinterpret_cast<double*>(q); q += nv;
+  double* Xc = reinterpret_cast<double*>(q); q += nc;
+  double* Ac = reinterpret_cast<double*>(q); q += nc;
+  unsigned char* Yb = q; q += ny;
+  unsigned char* Zb = q; q += ny;
+  unsigned char* Ylb = q;
+  FETIRP_CUDA(cudaMemcpyAsync(V2, V, sizeof(double) * (size_t)L.n_lambda * k, cudaMemcpyDeviceToDevice, s));
+  project_with(ctx, V2, k, Xc, Ac);
+  LocalProblem LP{};
+  LP.n_pat = n_pat;
+  if (prec == FETIRP_PREC_FP64 || prec == FETIRP_PREC_FP32) {
+    PatView<double> Yd{}, Zd{};
+    PatView<float> Yf{}, Zf{};
+    for (int p = 0; p < n_pat; ++p) {
+      PatternData& P = *ctx->pats[p];
+      void* y = Yb + pbase[p] * es;
+      void* z = Zb + pbase[p] * es;
+      Yd.base[p] = (double*)y; Zd.base[p] = (double*)z;
+      Yf.base[p] = (float*)y; Zf.base[p] = (float*)z;
+      Yd.ld[p] = Zd.ld[p] = Yf.ld[p] = Zf.ld[p] = P.ld_y;
+      LP.S[p] = prec == FETIRP_PREC_FP64 ? (const void*)P.S64.p : (const void*)P.S32.p;
+      LP.n_b[p] = P.n_b; LP.n_rhs[p] = (int)P.occs.size() * k; LP.ld[p] = P.ld_y;
+      LP.Y[p] = y; LP.Z[p] = z;
+    }
+    if (prec == FETIRP_PREC_FP64) {
+      gather<double>(L, V2, k, Yd, s);
+      local_gemm_f64(LP, s);
+      scatter<double>(L, Zd, k, 0.0, Q, s);
+    } else {
+      gather<float>(L, V2, k, Yf, s);
+      local_gemm_f32(LP, s);
+      scatter<float>(L, Zf, k, 0.0, Q, s);
+    }
+  } else {
+    PatView<float> Yh{}, Yl{}, Zv{};
+    TcProblem T;
+    T.n_pat = n_pat;
+    for (int p = 0; p < n_pat; ++p) {
+      PatternData& P = *ctx->pats[p];
+      Yh.base[p] = (float*)(Yb + pbase[p] * es);
+      Yl.base[p] = (float*)(Ylb + pbase[p] * es);
+      Zv.base[p] = (float*)(Zb + pbase[p] * es);
+      Yh.ld[p] = Yl.ld[p] = Zv.ld[p] = P.ld_y;
+      T.S_hi[p] = P.S_hi.p; T.S_lo[p] = P.S_lo.p; T.lds[p] = P.lds;
+      T.Y_hi[p] = Yh.base[p]; T.Y_lo[p] = Yl.base[p]; T.Z[p] = Zv.base[p]; T.ldy[p] = P.ld_y;
+      T.n_b[p] = P.n_b; T.n_rhs[p] = (int)P.occs.size() * k;
+    }
+    gather_split(L, V2, k, Yh, Yl, s);
+    tc_gemm_tf32x3(T, ctx->tc_error.p, s);
+    scatter<float>(L, Zv, k, 0.0, Q, s);
+  }
+  project_with(ctx, Q, k, Xc, Ac);
+}
+
+}  // namespace
+
 // =========================================================================================== C ABI
 extern "C" {
+
+fetirp_status fetirp_apply_block_device_noalloc(fetirp_ctx ctx, int32_t k, const double* d_V, double* d_Q,
+                                                int32_t precision) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    if (!ctx->prepared) throw Error(FETIRP_ESTATE, "call fetirp_prepare or fetirp_solve first");
+    REQUIRE(k >= 1 && k <= 64, "k must be in 1..64");
+    REQUIRE(d_V && d_Q, "NULL buffer");
+    REQUIRE(precision >= FETIRP_PREC_FP64 && precision <= FETIRP_PREC_TF32X3, "unsupported precision");
+    apply_noalloc(ctx, d_V, d_Q, k, precision, noalloc_scratch(ctx->opt.device), FETIRP_NOALLOC_SCRATCH_BYTES);
+    return FETIRP_OK;
+  });
+}
+
 
 void fetirp_default_options(fetirp_options* o) {
   if (!o) return;

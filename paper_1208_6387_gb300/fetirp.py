@@ -71,6 +71,7 @@ _SIGS = {
     "fetirp_solve_device": (C.c_int, [P, C.c_int64, P, P, P, C.POINTER(fetirp_stats)]),
     "fetirp_apply_block": (C.c_int, [P, C.c_int32, P, P, C.c_int32]),
     "fetirp_apply_block_device": (C.c_int, [P, C.c_int32, P, P, C.c_int32]),
+    "fetirp_apply_block_device_noalloc": (C.c_int, [P, C.c_int32, P, P, C.c_int32]),
     "fetirp_prepare": (C.c_int, [P, C.c_int64, P]),
     "fetirp_factorize": (C.c_int, [P]),
     "fetirp_get_pattern": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), P, P]),
@@ -199,6 +200,16 @@ def fetirp_apply_block(ctx, V, precision=FETIRP_PREC_FP64):
 
 def fetirp_apply_block_device(ctx, k, V_ptr, Q_ptr, precision=FETIRP_PREC_FP64):
     _check(ctx, lib().fetirp_apply_block_device(ctx, int(k), C.c_void_p(V_ptr), C.c_void_p(Q_ptr), int(precision)))
+
+
+FETIRP_NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def fetirp_apply_block_device_noalloc(ctx, k, V_ptr, Q_ptr, precision=FETIRP_PREC_FP64):
+    """Same operator as fetirp_apply_block_device with the scratch in the library's fixed device array (no
+    device allocation in the call; see include/fetirp.h for the size limit and the sharing rules)."""
+    _check(ctx, lib().fetirp_apply_block_device_noalloc(ctx, int(k), C.c_void_p(V_ptr), C.c_void_p(Q_ptr),
+                                                         int(precision)))
 
 
 def fetirp_factorize(ctx):
