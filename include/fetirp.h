@@ -74,6 +74,7 @@ typedef struct {
                              the operator is only accurate to ~1e-7; default 1e-6 */
   int32_t use_graphs;  /* 1: the check_every iterations between read-backs are captured once as a CUDA graph
                           and replayed; 0: launched one by one; default 1 */
+  int32_t timing_mask; /* with timing = 1: bit p set -> phase p is bracketed with events; 0 = every phase */
 } fetirp_options;
 
 /* Phases of a solve, for the per-phase statistics. */
@@ -86,9 +87,10 @@ enum {
   FETIRP_PHASE_PROJECT = 5,  /* projector P = I - G (G^T G)^{-1} G^T */
   FETIRP_PHASE_GRAM = 6,     /* block Gram products (reorthogonalisation coefficients, eta, W^T r) */
   FETIRP_PHASE_REORTH = 7,   /* W -= W_hist C */
-  FETIRP_PHASE_UPDATE = 8,   /* normalisation, W T, P~ T, lambda and residual updates, norms */
+  FETIRP_PHASE_UPDATE = 8,   /* split of r, W T, P~ T, lambda and residual updates, norms */
   FETIRP_PHASE_RECOVER = 9,  /* alpha and u(s) */
-  FETIRP_NPHASE = 10
+  FETIRP_PHASE_NORMALISE = 10, /* F-normalisation of eta (pivoted Cholesky, one CTA) */
+  FETIRP_NPHASE = 11
 };
 
 typedef struct {
@@ -103,10 +105,10 @@ typedef struct {
   int64_t launches;           /* kernels launched by the call */
   /* with options.timing = 1: per phase (FETIRP_PHASE_*) device time, launches, and the algorithmic work
      counted from the sizes (flops and compulsory bytes, not hardware counters) */
-  double phase_ms[10];
-  int64_t phase_launches[10];
-  double phase_flops[10];
-  double phase_bytes[10];
+  double phase_ms[11];
+  int64_t phase_launches[11];
+  double phase_flops[11];
+  double phase_bytes[11];
 } fetirp_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -43,6 +43,25 @@ __global__ void k_set_entries(double* N, int npad, const int* zpiv, int kd) {
   if (m < kd) N[(size_t)m * npad + zpiv[m]] = 1.0;
 }
 
+// In-place inverse of a small SPD matrix (dimension <= 6) by Gauss-Jordan, one thread (pattern set-up).
+__global__ void k_small_spd_inverse(double* C, int n) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a[6][12];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 2 * n; ++j) a[i][j] = j < n ? C[i * n + j] : (j - n == i ? 1.0 : 0.0);
+  for (int c = 0; c < n; ++c) {
+    const double inv = 1.0 / a[c][c];
+    for (int j = 0; j < 2 * n; ++j) a[c][j] *= inv;
+    for (int i = 0; i < n; ++i)
+      if (i != c) {
+        const double f = a[i][c];
+        for (int j = 0; j < 2 * n; ++j) a[i][j] -= f * a[c][j];
+      }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) C[i * n + j] = a[i][j + n];
+}
+
 __global__ void k_to_f32(size_t n, const double* __restrict__ x, float* __restrict__ y) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = (float)x[i];
@@ -78,7 +97,7 @@ struct PatternData {
   TilePlan plan, planS;
   DBuf<int64_t> d_rowptr;
   DBuf<int> d_col, d_newidx, zp;
-  DBuf<double> d_val, L, diag0, S64, N, Nb, Dinv, LS, XS, DinvS;
+  DBuf<double> d_val, L, diag0, S64, N, Nb, Dinv, LS, XS, DinvS, Sdag, Nwork;
   DBuf<int> zpS, d_zpiv;
   std::vector<int> h_zp;
   int* h_zp_pinned = nullptr;
@@ -227,7 +246,7 @@ struct PhaseScope {
       ctx->phase_flops[ph] += flops;
       ctx->phase_bytes[ph] += bytes;
     }
-    if (ctx->opt.timing) e0 = record();
+    if (ctx->opt.timing && (ctx->opt.timing_mask == 0 || ((ctx->opt.timing_mask >> ph) & 1))) e0 = record();
   }
   int record() {
     if (ctx->ev_used == ctx->ev_pool.size()) {
@@ -366,14 +385,40 @@ void factor_stage_b(PatternData& P, cudaStream_t s) {
   tri_solve(P.LS.p, nbp, P.planS, P.zpS.p, P.XS.p, nbp, nbp, false, s, P.DinvS.p);   // X = L_S^{-1}
   P.S64.ensure((size_t)P.n_b * P.n_b);
   gemm_f64(P.n_b, P.n_b, nbp, 1.0, P.XS.p, nbp, 1, P.XS.p, 1, nbp, 0.0, P.S64.p, P.n_b, 1, s);
-  P.S32.ensure((size_t)P.n_b * P.n_b);
-  const size_t nn = (size_t)P.n_b * P.n_b;
-  k_to_f32<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(nn, P.S64.p, P.S32.p);
+  // Moore-Penrose inverse S^dag = Pi S^+ Pi, Pi = I - N_b (N_b^T N_b)^{-1} N_b^T, for the low-precision local
+  // products: S^+ from zero pivots carries large components along the kernel (a body held at a few dofs)
+  // that the projector P removes again, so rounding them would survive that cancellation; S^dag has none.
+  // P^T F P is the same for every generalized inverse (Sec. 2), so the inner operator is unchanged.
+  const int nb = P.n_b;
+  const double* Sdag = P.S64.p;
+  if (kd > 0) {
+    P.Sdag.ensure((size_t)nb * nb);
+    P.Nwork.ensure((size_t)nb * kd * 2 + 2 * kd * kd);
+    double* A = P.Nwork.p;                  // S^+ N_b       (nb x kd, row-major)
+    double* E = A + (size_t)nb * kd;        // N_b C^{-1}    (nb x kd)
+    double* Cm = E + (size_t)nb * kd;       // N_b^T N_b, then its inverse (kd x kd)
+    double* D = Cm + kd * kd;               // N_b^T S^+ N_b (kd x kd)
+    gemm_f64(nb, kd, nb, 1.0, P.S64.p, nb, 1, P.Nb.p, kd, 1, 0.0, A, kd, 1, s);
+    gemm_f64(kd, kd, nb, 1.0, P.Nb.p, 1, kd, P.Nb.p, kd, 1, 0.0, Cm, kd, 1, s);
+    gemm_f64(kd, kd, nb, 1.0, P.Nb.p, 1, kd, A, kd, 1, 0.0, D, kd, 1, s);
+    k_small_spd_inverse<<<1, 32, 0, s>>>(Cm, kd);
+    FETIRP_LAUNCH_CHECK();
+    gemm_f64(nb, kd, kd, 1.0, P.Nb.p, kd, 1, Cm, kd, 1, 0.0, E, kd, 1, s);
+    FETIRP_CUDA(cudaMemcpyAsync(P.Sdag.p, P.S64.p, sizeof(double) * (size_t)nb * nb, cudaMemcpyDeviceToDevice, s));
+    gemm_f64(nb, nb, kd, -1.0, E, kd, 1, A, 1, kd, 1.0, P.Sdag.p, nb, 1, s);    // - E A^T
+    gemm_f64(nb, nb, kd, -1.0, A, kd, 1, E, 1, kd, 1.0, P.Sdag.p, nb, 1, s);    // - A E^T
+    gemm_f64(nb, kd, kd, 1.0, E, kd, 1, D, kd, 1, 0.0, A, kd, 1, s);            // A <- E D
+    gemm_f64(nb, nb, kd, 1.0, A, kd, 1, E, 1, kd, 1.0, P.Sdag.p, nb, 1, s);     // + E D E^T
+    Sdag = P.Sdag.p;
+  }
+  P.S32.ensure((size_t)nb * nb);
+  const size_t nn = (size_t)nb * nb;
+  k_to_f32<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(nn, Sdag, P.S32.p);
   FETIRP_LAUNCH_CHECK();
-  P.lds = round_up(P.n_b, 4);
-  P.S_hi.ensure((size_t)P.n_b * P.lds);
-  P.S_lo.ensure((size_t)P.n_b * P.lds);
-  split_tf32(P.S64.p, P.n_b, P.n_b, P.n_b, P.S_hi.p, P.S_lo.p, P.lds, s);
+  P.lds = round_up(nb, 4);
+  P.S_hi.ensure((size_t)nb * P.lds);
+  P.S_lo.ensure((size_t)nb * P.lds);
+  split_tf32(Sdag, nb, nb, nb, P.S_hi.p, P.S_lo.p, P.lds, s);
 }
 
 void factorize_patterns(fetirp_ctx ctx, const std::vector<PatternData*>& pats) {
@@ -894,9 +939,12 @@ void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
     eta_and_wr(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta.p, ctx->wr.p, ctx->eta_part, s);
   }
   {
-    PhaseScope ph(ctx, FETIRP_PHASE_UPDATE, 0.0, 0.0);
+    PhaseScope ph(ctx, FETIRP_PHASE_NORMALISE, 0.0, 0.0);
     normalise(k, ctx->eta.p, ctx->wr.p, prec == FETIRP_PREC_FP64 ? ctx->opt.eig_trunc : ctx->opt.eig_trunc_inner,
               ctx->T.p, ctx->alpha.p, ctx->n_kept.p, s);
+  }
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_UPDATE, 0.0, 0.0);
     update<TH>(nl, k, ctx->Zr.p, ctx->Q.p, ctx->T.p, ctx->alpha.p, Wh, Qh, d_cols, cap, ctx->lam.p, ctx->r.p,
                ctx->rr_part.p, ctx->rr_blocks, s);
     advance(d_cols, k, cap, ctx->n_kept.p, ctx->d_state.p + 1, ctx->d_state.p + 2, s);
@@ -913,6 +961,8 @@ void account_iteration(fetirp_ctx ctx, int prec, long long a, double es) {
   F[FETIRP_PHASE_REORTH] += 2.0 * nl * a * k;
   B[FETIRP_PHASE_REORTH] += es * nl * a + 16.0 * nl * k;
   F[FETIRP_PHASE_UPDATE] += 4.0 * nl * k * k + 4.0 * nl * k;
+  F[FETIRP_PHASE_NORMALISE] += (2.0 / 3.0) * k * k * k;   // pivoted Cholesky + triangular inverse, O(k^3)
+  B[FETIRP_PHASE_NORMALISE] += 8.0 * (2.0 * k * k + 2.0 * k);
   B[FETIRP_PHASE_UPDATE] += 8.0 * nl * (3.0 * k + 4.0) + 2.0 * es * nl * k;
   F[FETIRP_PHASE_PROJECT] += 2.0 * (2.0 * nG * nG * k + 24.0 * nl * k);
   B[FETIRP_PHASE_PROJECT] += 2.0 * (16.0 * nl * k + 8.0 * nG * nG);
@@ -936,8 +986,9 @@ void run_iterations(fetirp_ctx ctx, int prec, int G, bool use_graph, TH* Wh, TH*
   auto& gc = ctx->gc;
   const int th = (int)sizeof(TH);
   if (use_graph) {
+    const int tkey = ctx->opt.timing ? (1 + (ctx->opt.timing_mask & 0xFFFF) * 2) : 0;
     const bool valid = gc.exec && gc.prec == prec && gc.k == ctx->k && gc.G == G && gc.th == th &&
-                       gc.cap == ctx->hist_cap && gc.timing == ctx->opt.timing;
+                       gc.cap == ctx->hist_cap && gc.timing == tkey;
     if (!valid) {
       if (gc.exec) { cudaGraphExecDestroy(gc.exec); gc.exec = nullptr; }
       gc.recs.clear();
@@ -962,7 +1013,7 @@ void run_iterations(fetirp_ctx ctx, int prec, int G, bool use_graph, TH* Wh, TH*
       FETIRP_CUDA(e);
       gc.total_launches = (long long)(g_launch_count - l0);
       g_launch_count = l0;   // captured, not launched
-      gc.prec = prec; gc.k = ctx->k; gc.G = G; gc.th = th; gc.cap = ctx->hist_cap; gc.timing = ctx->opt.timing;
+      gc.prec = prec; gc.k = ctx->k; gc.G = G; gc.th = th; gc.cap = ctx->hist_cap; gc.timing = tkey;
       ctx->ev_reserved = ctx->ev_used;
     }
     FETIRP_CUDA(cudaGraphLaunch(gc.exec, s));
@@ -1086,7 +1137,13 @@ void ensure_history(fetirp_ctx ctx) {
   // History: at most n_lambda directions can be F-orthogonal, and at most max_iter blocks are made; the two
   // arrays are also kept under 8 GB.  A full history restarts the recurrence.
   long long want = std::min<long long>((long long)std::max(1, ctx->opt.max_iter) * k, round_up(nl, k));
-  long long limit = (8LL << 30) / (2LL * 8 * std::max(nl, 1));
+  // the two history arrays may take half of the device memory that is free (HBM is the limit, not a constant)
+  size_t free_b = 0, total_b = 0;
+  FETIRP_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const double es_h = ctx->opt.precision == FETIRP_PREC_FP64 ? 8.0 : 4.0;
+  const double held = ctx->opt.precision == FETIRP_PREC_FP64 ? 8.0 * (ctx->Whist.n + ctx->Qhist.n)
+                                                             : 4.0 * (ctx->Whist32.n + ctx->Qhist32.n);
+  long long limit = (long long)(0.5 * ((double)free_b + held) / (2.0 * es_h * std::max(nl, 1)));
   long long cap = std::max<long long>(k, std::min(want, limit));
   cap = cap / k * k;
   if (ctx->opt.precision == FETIRP_PREC_FP64) {
@@ -1187,7 +1244,10 @@ fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_st
   ctx->last = st;
   if (stats) *stats = st;
   if (!(st.rel_residual <= ctx->opt.tol)) {
-    set_err(ctx, "tolerance not reached: relative residual " + std::to_string(st.rel_residual));
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "tolerance not reached: relative residual %.3e after %d iterations, %d outer steps",
+                  st.rel_residual, st.iterations, st.outer_steps);
+    set_err(ctx, buf);
     return FETIRP_ENOCONV;
   }
   return FETIRP_OK;
@@ -1349,6 +1409,7 @@ void fetirp_default_options(fetirp_options* o) {
   o->timing = 0;
   o->eig_trunc_inner = 1e-6;
   o->use_graphs = 1;
+  o->timing_mask = 0;
 }
 
 const char* fetirp_status_string(fetirp_status s) {

@@ -354,46 +354,33 @@ void eta_and_wr(int n, int k, const double* W, const double* Q, const double* r,
   FETIRP_LAUNCH_CHECK();
 }
 
-// C (m x k, row-major) = A (m x m, row-major) B (m x k, row-major) in FP64.  16 rows of C per CTA; chunks of 64
-// rows of B and the matching 16 x 64 block of A are staged in shared memory; thread (row, column) sums in a
-// fixed order.  Spreads the small coarse products over many SMs.
-__global__ void __launch_bounds__(256) k_small_gemm(int m, int k, const double* __restrict__ A,
+// C (m x k, row-major) = A (m x m, row-major) B (m x k, row-major) in FP64.  One CTA per 4 rows of C, one warp
+// per row, lanes over (column, j-slice) pairs: lane = slice * k' + column with k' = k rounded up to a power of
+// two <= 32, so that every lane does useful FMAs; the slices of a column are added by a fixed shuffle tree.
+__global__ void __launch_bounds__(128) k_small_gemm(int m, int k, const double* __restrict__ A,
                                                     const double* __restrict__ B, double* __restrict__ C) {
-  __shared__ double sa[16][65];
-  __shared__ double sb[64][65];
-  const int r0 = blockIdx.x * 16;
-  const int tid = threadIdx.x;
-  const int row = tid / 16, cg = tid % 16;     // columns cg, cg+16, cg+32, cg+48
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int j0 = 0; j0 < m; j0 += 64) {
-    for (int idx = tid; idx < 16 * 64; idx += 256) {
-      const int rr = idx / 64, jj = idx % 64;
-      sa[rr][jj] = (r0 + rr < m && j0 + jj < m) ? A[(size_t)(r0 + rr) * m + j0 + jj] : 0.0;
-    }
-    for (int idx = tid; idx < 64 * 64; idx += 256) {
-      const int jj = idx / 64, g = idx % 64;
-      sb[jj][g] = (j0 + jj < m && g < k) ? B[(size_t)(j0 + jj) * k + g] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int jj = 0; jj < 64; ++jj) {
-      const double a = sa[row][jj];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u] = fma(a, sb[jj][cg + 16 * u], acc[u]);
-    }
-    __syncthreads();
-  }
-  if (r0 + row < m) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (cg + 16 * u < k) C[(size_t)(r0 + row) * k + cg + 16 * u] = acc[u];
+  const int row = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  const double* a = A + (size_t)row * m;
+  for (int g0 = 0; g0 < k; g0 += 32) {
+    const int kk = min(32, k - g0);
+    int kp = 1;
+    while (kp < kk) kp <<= 1;                // columns handled by this pass, power of two
+    const int slices = 32 / kp;
+    const int g = g0 + (lane % kp), sl = lane / kp;
+    double acc = 0.0;
+    if (g < k)
+      for (int j = sl; j < m; j += slices) acc = fma(a[j], B[(size_t)j * k + g], acc);
+    for (int off = kp; off < 32; off <<= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (sl == 0 && g < k) C[(size_t)row * k + g] = acc;
   }
 }
 
 void small_gemm(int m, int k, const double* A, const double* B, double* C, cudaStream_t s) {
   if (m <= 0 || k <= 0) return;
   if (k > 64) throw Error(1, "k > 64");
-  k_small_gemm<<<ceil_div(m, 16), 256, 0, s>>>(m, k, A, B, C);
+  k_small_gemm<<<ceil_div(m, 4), 128, 0, s>>>(m, k, A, B, C);
   FETIRP_LAUNCH_CHECK();
 }
 
@@ -442,20 +429,17 @@ __global__ void __launch_bounds__(128) k_gram_split(int a_max, const int* __rest
   }
   __syncthreads();
   if (c >= a) return;
-  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   int i = 0;
-  for (; i + 4 <= cnt; i += 4) {
-    const double q0 = (double)Qh[(size_t)srow[i] * ldq + c];
-    const double q1 = (double)Qh[(size_t)srow[i + 1] * ldq + c];
-    const double q2 = (double)Qh[(size_t)srow[i + 2] * ldq + c];
-    const double q3 = (double)Qh[(size_t)srow[i + 3] * ldq + c];
-    acc0 = fma(sw[i], q0, acc0);
-    acc1 = fma(sw[i + 1], q1, acc1);
-    acc2 = fma(sw[i + 2], q2, acc2);
-    acc3 = fma(sw[i + 3], q3, acc3);
+  for (; i + 8 <= cnt; i += 8) {
+    double q[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) q[u] = (double)Qh[(size_t)srow[i + u] * ldq + c];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = fma(sw[i + u], q[u], acc[u]);
   }
-  for (; i < cnt; ++i) acc0 = fma(sw[i], (double)Qh[(size_t)srow[i] * ldq + c], acc0);
-  partial[((size_t)ch * a + c) * k + g] = (acc0 + acc1) + (acc2 + acc3);
+  for (; i < cnt; ++i) acc[0] = fma(sw[i], (double)Qh[(size_t)srow[i] * ldq + c], acc[0]);
+  partial[((size_t)ch * a + c) * k + g] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 }
 
 __global__ void k_reduce_chunks_dyn(int a_max, const int* __restrict__ d_a, int k, int chunks,

@@ -11,11 +11,11 @@ struct LocalTiles {
   int tile_off[MAXP + 1];
 };
 
-template <typename T>
+template <typename T, int BM, int BN>
 __global__ void __launch_bounds__(256) k_local_gemm(LocalTiles LT) {
-  constexpr int BM = 64, BN = 64, BK = 16;
-  __shared__ T sa[BK][BM + 1];   // S(i, j): [j][i]
-  __shared__ T sb[BK][BN + 1];   // Y(j, rhs): [j][rhs]
+  constexpr int BK = 16, TM = BM / 16, TN = BN / 16;   // per thread: TM rows x TN right-hand sides
+  __shared__ T sa[16][BM + 1];   // S(i, j): [j][i]
+  __shared__ T sb[16][BN + 1];   // Y(j, rhs): [j][rhs]
   int p = 0;
   while (p + 1 < LT.P.n_pat && (int)blockIdx.x >= LT.tile_off[p + 1]) ++p;
   const int t = blockIdx.x - LT.tile_off[p];
@@ -25,54 +25,71 @@ __global__ void __launch_bounds__(256) k_local_gemm(LocalTiles LT) {
   const T* S = (const T*)LT.P.S[p];
   const T* Y = (const T*)LT.P.Y[p];
   T* Z = (T*)LT.P.Z[p];
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;   // rows tx*4.., rhs ty*4..
-  T acc[4][4] = {};
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;   // rows tx*TM.., rhs ty*TN..
+  T acc[TM][TN] = {};
   for (int k0 = 0; k0 < nb; k0 += BK) {
     for (int idx = tid; idx < BK * BM; idx += 256) {
       const int kk = idx % BK, r = idx / BK;
       const int i = m0 + r, j = k0 + kk;
       sa[kk][r] = (i < nb && j < nb) ? S[(size_t)i * nb + j] : T(0);
-      const int c = n0 + r;
+    }
+    for (int idx = tid; idx < BK * BN; idx += 256) {
+      const int kk = idx % BK, r = idx / BK;
+      const int c = n0 + r, j = k0 + kk;
       sb[kk][r] = (c < nr && j < nb) ? Y[(long long)c * ld + j] : T(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      T av[4], bv[4];
+      T av[TM], bv[TN];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) { av[q] = sa[kk][tx * 4 + q]; bv[q] = sb[kk][ty * 4 + q]; }
+      for (int q = 0; q < TM; ++q) av[q] = sa[kk][tx * TM + q];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int q = 0; q < TN; ++q) bv[q] = sb[kk][ty * TN + q];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+      for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const int c = n0 + ty * 4 + b;
+  for (int b = 0; b < TN; ++b) {
+    const int c = n0 + ty * TN + b;
     if (c >= nr) continue;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int i = m0 + tx * 4 + a;
+    for (int a = 0; a < TM; ++a) {
+      const int i = m0 + tx * TM + a;
       if (i < nb) Z[(long long)c * ld + i] = acc[a][b];
     }
   }
 }
 
-template <typename T>
-static void launch_local(const LocalProblem& P, cudaStream_t s) {
-  LocalTiles LT;
+template <typename T, int BM, int BN>
+static int plan_tiles(const LocalProblem& P, LocalTiles& LT) {
   LT.P = P;
   int total = 0;
   for (int p = 0; p < P.n_pat; ++p) {
     LT.tile_off[p] = total;
-    LT.tiles_m[p] = ceil_div(P.n_b[p], 64);
-    total += LT.tiles_m[p] * ceil_div(P.n_rhs[p], 64);
+    LT.tiles_m[p] = ceil_div(P.n_b[p], BM);
+    total += LT.tiles_m[p] * ceil_div(P.n_rhs[p], BN);
   }
   LT.tile_off[P.n_pat] = total;
+  return total;
+}
+
+// 64 x 64 tiles, or 32 x 32 tiles when the 64-wide tiling would not give every SM a CTA (small problems).
+template <typename T>
+static void launch_local(const LocalProblem& P, cudaStream_t s) {
+  LocalTiles LT;
+  int total = plan_tiles<T, 64, 64>(P, LT);
   if (total == 0) return;
-  k_local_gemm<T><<<total, 256, 0, s>>>(LT);
+  if (total < 152) {
+    total = plan_tiles<T, 32, 32>(P, LT);
+    k_local_gemm<T, 32, 32><<<total, 256, 0, s>>>(LT);
+  } else {
+    k_local_gemm<T, 64, 64><<<total, 256, 0, s>>>(LT);
+  }
   FETIRP_LAUNCH_CHECK();
 }
 
