@@ -5,4 +5,5 @@ Both the CUDA library's tests/bench and the CPU oracle read the same Problem obj
 """
 from .mesh import Pattern, heat_pattern, elastic_pattern, q1_laplace, q1_elastic3d, elastic_D, lame
 from .layout import Problem, Occurrence, build_grid_problem, cube_rotations, square_rotations, dense_B, set_nodal_load
-from .configs import heat_grid, elastic_grid, config
+from .configs import (heat_grid, elastic_grid, config, library_patterns, fill_structure, request_stream, LIBRARY,
+                      merge_structures, batched_uneven)

@@ -148,6 +148,8 @@ def build_grid_problem(name: str, patterns: list, cell_pattern: np.ndarray, grid
 
     occs = []
     for cidx in range(n_cells):
+        if cell_pattern[cidx] < 0:        # empty cell (partially filled box)
+            continue
         cell = []
         rem = cidx
         for d in range(dim):
@@ -165,11 +167,11 @@ def build_grid_problem(name: str, patterns: list, cell_pattern: np.ndarray, grid
             nmap += gi[:, d] * strides[d]
         occs.append(Occurrence(int(cell_pattern[cidx]), R, tuple(cell), nmap, None))
 
-    # multiplicity of every global node
+    # multiplicity of every global node (0 for nodes of empty cells only)
     mult = np.zeros(n_gn, dtype=np.int64)
     for o in occs:
         mult[o.node_map] += 1
-    assert np.all(mult >= 1)
+    assert np.all(mult[np.concatenate([o.node_map for o in occs])] >= 1)
 
     rng = np.random.default_rng([seed, 1])
     if load == "uniform":
@@ -180,15 +182,16 @@ def build_grid_problem(name: str, patterns: list, cell_pattern: np.ndarray, grid
         f_nodal = np.zeros(n_gn * dpn)
     else:
         raise ValueError(load)
+    f_nodal[np.repeat(mult == 0, dpn)] = 0.0
     for o in occs:
         dofs = (o.node_map[:, None] * dpn + np.arange(dpn)[None, :]).ravel()
         o.f_global = f_nodal[dofs] / np.repeat(mult[o.node_map], dpn)
 
-    # Dirichlet nodes
+    # Dirichlet nodes (only nodes some occurrence owns)
     if dirichlet == "x0":
-        dnodes = np.nonzero(gidx[:, 0] == 0)[0]
+        dnodes = np.nonzero((gidx[:, 0] == 0) & (mult > 0))[0]
     elif dirichlet == "all":
-        dnodes = np.nonzero(np.any((gidx == 0) | (gidx == np.array(nper) - 1), axis=1))[0]
+        dnodes = np.nonzero(np.any((gidx == 0) | (gidx == np.array(nper) - 1), axis=1) & (mult > 0))[0]
     elif dirichlet == "none":
         dnodes = np.zeros(0, dtype=np.int64)
     else:
@@ -210,51 +213,81 @@ def build_grid_problem(name: str, patterns: list, cell_pattern: np.ndarray, grid
     ug, start, cnt = np.unique(gs, return_index=True, return_counts=True)
     cells = np.array([o.cell for o in occs])
 
-    link_o, link_l, link_c, link_r, link_s = [], [], [], [], []
-    c_rows, kinds = [], []
-    row = 0
-    for g, st, ct in zip(ug, start, cnt):
-        g = int(g)
+    # Multiplier rows, in the order (global node, tree edge, Dirichlet row, component).  Nodes owned by two
+    # occurrences carry exactly one tree edge (vectorised); nodes with more owners take the union-find loop.
+    # Per node: its list of "row items" (a, b, la, lb) with b = -1 for a Dirichlet item, laid out in order.
+    is_dir = np.zeros(n_gn, dtype=bool)
+    is_dir[dnodes] = True
+    item_node, item_a, item_b, item_la, item_lb, item_rank = [], [], [], [], [], []
+    two = cnt == 2
+    if np.any(two):
+        st2 = start[two]
+        item_node.append(ug[two]); item_a.append(os_[st2]); item_b.append(os_[st2 + 1])
+        item_la.append(ls[st2]); item_lb.append(ls[st2 + 1]); item_rank.append(np.zeros(int(two.sum()), np.int64))
+    multi = np.nonzero(cnt > 2)[0]
+    ma, mb, mla, mlb, mn, mr = [], [], [], [], [], []
+    for t in multi:
+        g, st, ct = int(ug[t]), int(start[t]), int(cnt[t])
         S = os_[st:st + ct]
-        L = ls[st:st + ct]
-        if ct >= 2:
-            parent = list(range(ct))
+        Lc = ls[st:st + ct]
+        parent = list(range(ct))
 
-            def find(x):
-                while parent[x] != x:
-                    parent[x] = parent[parent[x]]
-                    x = parent[x]
-                return x
-            for a in range(ct):
-                for b in range(a + 1, ct):
-                    if np.abs(cells[S[a]] - cells[S[b]]).sum() != 1:
-                        continue
-                    ra, rb = find(a), find(b)
-                    if ra == rb:
-                        continue
-                    parent[rb] = ra
-                    for comp in range(dpn):
-                        link_o += [S[a], S[b]]
-                        link_l += [L[a], L[b]]
-                        link_c += [comp, comp]
-                        link_r += [row, row]
-                        link_s += [1, -1]
-                        c_rows.append(0.0)
-                        kinds.append(0)
-                        row += 1
-        if g in dmap:
-            for comp in range(dpn):
-                link_o.append(S[0]); link_l.append(L[0]); link_c.append(comp)
-                link_r.append(row); link_s.append(1)
-                c_rows.append(dvals[dmap[g], comp])
-                kinds.append(1)
-                row += 1
-    # Dirichlet nodes that are on no occurrence boundary cannot occur on a grid (x = 0 is a surface).
-    link_o = np.array(link_o, dtype=np.int64)
-    link_l = np.array(link_l, dtype=np.int32)
-    link_c = np.array(link_c, dtype=np.int8)
-    link_r = np.array(link_r, dtype=np.int32)
-    link_s = np.array(link_s, dtype=np.int8)
+        def find(x):
+            while parent[x] != x:
+                parent[x] = parent[parent[x]]
+                x = parent[x]
+            return x
+        rank = 0
+        for a in range(ct):
+            for b in range(a + 1, ct):
+                if np.abs(cells[S[a]] - cells[S[b]]).sum() != 1:
+                    continue
+                ra, rb = find(a), find(b)
+                if ra == rb:
+                    continue
+                parent[rb] = ra
+                mn.append(g); ma.append(S[a]); mb.append(S[b]); mla.append(Lc[a]); mlb.append(Lc[b]); mr.append(rank)
+                rank += 1
+    if mn:
+        item_node.append(np.array(mn)); item_a.append(np.array(ma)); item_b.append(np.array(mb))
+        item_la.append(np.array(mla)); item_lb.append(np.array(mlb)); item_rank.append(np.array(mr))
+    # Dirichlet items: lowest-index owner of a Dirichlet node, ranked after the node's tree edges
+    dmask = is_dir[ug]
+    if np.any(dmask):
+        std = start[dmask]
+        item_node.append(ug[dmask]); item_a.append(os_[std]); item_b.append(np.full(int(dmask.sum()), -1))
+        item_la.append(ls[std]); item_lb.append(np.full(int(dmask.sum()), -1))
+        item_rank.append(np.full(int(dmask.sum()), 1 << 30))
+    item_node = np.concatenate(item_node) if item_node else np.zeros(0, np.int64)
+    item_a = np.concatenate(item_a) if item_a else np.zeros(0, np.int64)
+    item_b = np.concatenate(item_b) if item_b else np.zeros(0, np.int64)
+    item_la = np.concatenate(item_la) if item_la else np.zeros(0, np.int64)
+    item_lb = np.concatenate(item_lb) if item_lb else np.zeros(0, np.int64)
+    item_rank = np.concatenate(item_rank) if item_rank else np.zeros(0, np.int64)
+    order = np.lexsort((item_rank, item_node))
+    item_node, item_a, item_b = item_node[order], item_a[order], item_b[order]
+    item_la, item_lb, item_rank = item_la[order], item_lb[order], item_rank[order]
+    n_items = len(item_node)
+    rows = (np.arange(n_items)[:, None] * dpn + np.arange(dpn)[None, :])          # row of (item, comp)
+    comp = np.broadcast_to(np.arange(dpn)[None, :], rows.shape)
+    glue = item_b >= 0
+    # gluing rows: +1 on a, -1 on b; Dirichlet rows: +1 on a
+    link_o = np.concatenate([np.repeat(item_a, dpn), np.repeat(item_b[glue], dpn)])
+    link_l = np.concatenate([np.repeat(item_la, dpn), np.repeat(item_lb[glue], dpn)]).astype(np.int32)
+    link_c = np.concatenate([comp.ravel(), comp[glue].ravel()]).astype(np.int8)
+    link_r = np.concatenate([rows.ravel(), rows[glue].ravel()]).astype(np.int32)
+    link_s = np.concatenate([np.ones(n_items * dpn), -np.ones(int(glue.sum()) * dpn)]).astype(np.int8)
+    row = n_items * dpn
+    c_rows = np.zeros(row)
+    kinds = np.repeat((~glue).astype(np.int8), dpn)
+    if np.any(~glue):
+        dvals_full = np.zeros((n_gn, dpn))
+        dvals_full[dnodes] = dvals
+        dr = rows[~glue]
+        c_rows[dr.ravel()] = dvals_full[item_node[~glue]].ravel()
+    # (Dirichlet nodes lie on x = 0, a boundary surface of every occurrence that owns them.)
+    by_row = np.argsort(link_r, kind="stable")     # every occurrence's links in increasing row order
+    link_o, link_l, link_c, link_r, link_s = link_o[by_row], link_l[by_row], link_c[by_row], link_r[by_row], link_s[by_row]
     for oi, o in enumerate(occs):
         sel = link_o == oi
         o.link_local_node = link_l[sel]
@@ -263,12 +296,13 @@ def build_grid_problem(name: str, patterns: list, cell_pattern: np.ndarray, grid
         o.link_sign = link_s[sel]
 
     centres = cells + 0.5
+    n_occ = len(occs)
     if k is None:
-        k = min(n_cells, 32)
-    k = min(k, n_cells)
+        k = min(n_occ, 32)
+    k = min(k, n_occ)
     groups = _rcb_groups(centres.astype(float), k)
     return Problem(name, dim, dpn, patterns, occs, tuple(grid), H, m, n_gn, gcoords, f_nodal,
-                   dnodes, dvals, row, np.array(c_rows), np.array(kinds, dtype=np.int8), groups, k, seed)
+                   dnodes, dvals, row, c_rows, kinds, groups, k, seed)
 
 
 def dense_B(prob: Problem) -> list:

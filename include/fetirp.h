@@ -75,6 +75,8 @@ typedef struct {
   int32_t use_graphs;  /* 1: the check_every iterations between read-backs are captured once as a CUDA graph
                           and replayed; 0: launched one by one; default 1 */
   int32_t timing_mask; /* with timing = 1: bit p set -> phase p is bracketed with events; 0 = every phase */
+  int64_t history_bytes; /* cap on the two direction-history arrays (a full history restarts the recurrence);
+                            0 = half of the free device memory */
 } fetirp_options;
 
 /* Phases of a solve, for the per-phase statistics. */
@@ -120,6 +122,15 @@ const char* fetirp_status_string(fetirp_status s);
 /* Create a context on opt->device (opt may be NULL for defaults).  *out receives the handle. */
 fetirp_status fetirp_create(const fetirp_options* opt, fetirp_ctx* out);
 
+/*
+ * A context that shares the patterns (factors) of `parent` read-only, with its own stream, occurrences and
+ * work buffers (opt NULL: the parent's options).  Patterns added to the parent later are not seen.  Several
+ * children may solve different structures concurrently from different host threads; the parent must outlive
+ * its children and must not be refactorised while they run.  fetirp_create_pattern and fetirp_factorize on a
+ * child return FETIRP_ESTATE.  (Serving pattern: a library of resident factors, one child per request slot.)
+ */
+fetirp_status fetirp_create_child(fetirp_ctx parent, const fetirp_options* opt, fetirp_ctx* out);
+
 /* Message of the last failed call on ctx (owned by ctx, valid until the next call); "" if none. */
 const char* fetirp_last_error(fetirp_ctx ctx);
 
@@ -161,6 +172,11 @@ fetirp_status fetirp_add_occurrence(fetirp_ctx ctx, int32_t pattern_id, const do
                                     const int32_t* lambda_row, const int8_t* sign, const double* f_global,
                                     int32_t* occ_id);
 
+/* Remove every occurrence (and the multivector groups) so that the context can take the next structure;
+ * patterns and device buffers are kept, so a reused context does not allocate again for a structure of
+ * the same size or smaller. */
+fetirp_status fetirp_clear_occurrences(fetirp_ctx ctx);
+
 /*
  * Multivector columns (the block of search directions of Table 1, right): occurrence s contributes its
  * share Delta(s) z of the preconditioned residual z to column group_of_occ[s] in [0, k), where
@@ -181,6 +197,17 @@ fetirp_status fetirp_set_groups(fetirp_ctx ctx, int32_t k, const int32_t* group_
  */
 fetirp_status fetirp_solve(fetirp_ctx ctx, int64_t n_lambda, const double* c, double* lambda_out,
                            double* u_out, fetirp_stats* stats);
+
+/*
+ * Autotuner of the multivector width: for every candidate k (1..64) the structure is solved once with k
+ * contiguous occurrence groups (by id) and timed with CUDA events; the fastest k is then set as the context's
+ * grouping (as fetirp_set_groups would) and returned in *best_k.  times_ms[n_cand] (may be NULL) receives the
+ * measured solve times (device time, FETIRP_ENOCONV solves count as +infinity).  Block iterations trade
+ * against the FP64 Gram work, which grows as k^2 per stored block, so the best k depends on the structure
+ * and on the precision.
+ */
+fetirp_status fetirp_autotune_k(fetirp_ctx ctx, int64_t n_lambda, const double* c, int32_t n_cand,
+                                const int32_t* candidates, int32_t* best_k, double* times_ms);
 
 /* As fetirp_solve with caller-allocated DEVICE buffers (c may be NULL); blocks until done. */
 fetirp_status fetirp_solve_device(fetirp_ctx ctx, int64_t n_lambda, const double* d_c, double* d_lambda,
@@ -241,6 +268,49 @@ fetirp_status fetirp_factorize(fetirp_ctx ctx);
  */
 fetirp_status fetirp_get_pattern(fetirp_ctx ctx, int32_t pattern_id, int32_t* n_b_out, int32_t* kernel_dim_out,
                                  double* splus, double* kernel);
+
+/* ------------------------------------------------------------------------------------------- serving
+ * Continuous batching of whole structures over a resident pattern library.  A server owns max_slots worker
+ * threads, each driving a child context (own stream) of the library context.  Submitted structures queue in
+ * arrival order; a slot takes the next structure as soon as it is free and the structure's device-memory
+ * estimate fits in what the other active structures leave of mem_budget_bytes (a structure is always
+ * admitted when nothing else runs).  Structures solved at the same time overlap on the GPU through their
+ * streams.  Each result is computed with the same kernels and buffers it would get alone, so it does not
+ * depend on what else is in flight.
+ */
+typedef struct fetirp_server_s* fetirp_server;
+
+/* A structure: occurrences of library patterns (arrays as in fetirp_add_occurrence, concatenated). */
+typedef struct {
+  int32_t n_occ;
+  const int32_t* pattern_id;     /* [n_occ] ids in the library context */
+  const double* rot;             /* [9 n_occ] row-major rotations, or NULL for identities */
+  const int32_t* link_offset;    /* [n_occ + 1] prefix offsets into the link arrays */
+  const int32_t* local_node;     /* links, concatenated over occurrences */
+  const int8_t* global_comp;
+  const int32_t* lambda_row;
+  const int8_t* sign;
+  const int64_t* f_offset;       /* [n_occ + 1] prefix offsets into f_global (each occurrence's n_dofs) */
+  const double* f_global;        /* loads, concatenated over occurrences */
+  int64_t n_lambda;
+  const double* c;               /* [n_lambda] or NULL */
+  int32_t k;                     /* multivector width; 0 = options default */
+  const int32_t* group_of_occ;   /* [n_occ] or NULL (contiguous groups) */
+} fetirp_structure;
+
+/* library: a context holding the patterns (not a child).  slot_opt: options of every slot's context (NULL:
+ * the library's options).  Every input is copied. */
+fetirp_status fetirp_server_create(fetirp_ctx library, const fetirp_options* slot_opt, int32_t max_slots,
+                                   int64_t mem_budget_bytes, fetirp_server* out);
+/* Queue a structure (copied) and return its ticket. */
+fetirp_status fetirp_server_submit(fetirp_server srv, const fetirp_structure* st, int64_t* ticket);
+/* Wait up to timeout_s seconds (0: just poll; < 0: forever) for a ticket.  *done = 1 when finished; then the
+ * outputs (host buffers of n_lambda and sum n_dofs doubles, may be NULL), stats and, through the return value,
+ * the solve's own status are delivered and the ticket is released.  latency_ms (may be NULL): submit -> done. */
+fetirp_status fetirp_server_wait(fetirp_server srv, int64_t ticket, double timeout_s, int32_t* done,
+                                 double* lambda_out, double* u_out, fetirp_stats* stats, double* latency_ms);
+/* Finish queued work, join the slots and release everything. */
+void fetirp_server_destroy(fetirp_server srv);
 
 #ifdef __cplusplus
 }

@@ -57,7 +57,8 @@ def solve_direct(prob):
     f = global_load(prob)
     n = K.shape[0]
     dd, dv = dirichlet_dofs(prob)
-    free = np.setdiff1d(np.arange(n), dd)
+    used = np.unique(np.concatenate([prob.occ_dofs(o) for o in range(prob.n_occ)]))   # nodes of occupied cells
+    free = np.setdiff1d(used, dd)
     u = np.zeros(n)
     u[dd] = dv
     rhs = f[free] - K[free][:, dd] @ dv

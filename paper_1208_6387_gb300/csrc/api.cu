@@ -17,7 +17,7 @@
 using namespace fetirp;
 
 namespace fetirp {
-unsigned long long g_launch_count = 0;
+thread_local unsigned long long g_launch_count = 0;
 }
 
 namespace {
@@ -109,11 +109,16 @@ struct PatternData {
   }
   DBuf<float> S32, S_hi, S_lo;   // FP32 S^+ and its tf32 pair (leading dimension lds)
   long long lds = 0;
+  long long ld_y = 0;          // Y/Z leading dimension (round_up(n_b, 4))
+};
+
+// How one context uses a pattern: its occurrences in the current structure and their loads and work vectors.
+// The factor (PatternData) itself is read-only after set-up and may be shared by several contexts.
+struct PatternUse {
   std::vector<int> occs;       // occurrences of this pattern (ids), q = position
   DBuf<int> d_occs;
   DBuf<double> F;              // npad x n_occ loads (pattern frame, new ordering)
   DBuf<double> U;              // npad x n_occ work (local solves)
-  long long ld_y = 0;          // Y/Z leading dimension
 };
 
 struct OccData {
@@ -131,7 +136,9 @@ struct fetirp_ctx_s {
   fetirp_options opt{};
   cudaStream_t stream = nullptr;
   std::string err;
-  std::vector<std::unique_ptr<PatternData>> pats;
+  std::vector<std::shared_ptr<PatternData>> pats;   // shared with child contexts
+  std::vector<PatternUse> use;                       // per pattern, this context's structure
+  bool is_child = false;
   std::vector<OccData> occs;
   int k_user = 0;
   std::vector<int> groups_user;
@@ -496,7 +503,7 @@ void invalidate(fetirp_ctx ctx) { ctx->prepared = false; }
 // Local-product buffers for a block of k columns in every precision (allocated before any graph capture).
 void ensure_apply_buffers(fetirp_ctx ctx, int k) {
   long long total = 0;
-  for (auto& P : ctx->pats) total += (long long)P->occs.size() * k * P->ld_y;
+  for (size_t p = 0; p < ctx->pats.size(); ++p) total += (long long)ctx->use[p].occs.size() * k * ctx->pats[p]->ld_y;
   ctx->Y64.ensure(total); ctx->Z64.ensure(total);
   ctx->Y32.ensure(total); ctx->Z32.ensure(total); ctx->Ylo32.ensure(total);
 }
@@ -511,16 +518,18 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   if (n_pat > MAXP) throw Error(FETIRP_EINVAL, "more than 16 patterns in one structure");
   // occurrence tables
   std::vector<int> obase(n_occ + 1, 0), occ_pat(n_occ), occ_q(n_occ), occ_gofs(n_occ), group(n_occ);
-  for (auto& P : ctx->pats) P->occs.clear();
+  ctx->use.resize(n_pat);
+  for (auto& u : ctx->use) u.occs.clear();
   for (int o = 0; o < n_occ; ++o) {
     PatternData& P = *ctx->pats[ctx->occs[o].pattern];
+    PatternUse& Us = ctx->use[ctx->occs[o].pattern];
     occ_pat[o] = ctx->occs[o].pattern;
-    occ_q[o] = (int)P.occs.size();
-    P.occs.push_back(o);
+    occ_q[o] = (int)Us.occs.size();
+    Us.occs.push_back(o);
     obase[o + 1] = obase[o] + P.n_b;
   }
   ctx->pofs.assign(n_pat + 1, 0);
-  for (int p = 0; p < n_pat; ++p) ctx->pofs[p + 1] = ctx->pofs[p] + ctx->pats[p]->kdim * (int)ctx->pats[p]->occs.size();
+  for (int p = 0; p < n_pat; ++p) ctx->pofs[p + 1] = ctx->pofs[p] + ctx->pats[p]->kdim * (int)ctx->use[p].occs.size();
   for (int o = 0; o < n_occ; ++o) occ_gofs[o] = ctx->pofs[occ_pat[o]] + occ_q[o] * ctx->pats[occ_pat[o]]->kdim;
   ctx->n_G = ctx->pofs[n_pat];
   // multivector groups
@@ -664,16 +673,16 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   // per-pattern loads (pattern frame, new ordering) and work
   for (int p = 0; p < n_pat; ++p) {
     PatternData& P = *ctx->pats[p];
-    const int no = (int)P.occs.size();
+    PatternUse& Us = ctx->use[p];
+    const int no = (int)Us.occs.size();
     std::vector<double> F((size_t)P.npad * std::max(no, 1), 0.0);
     for (int q = 0; q < no; ++q) {
-      const OccData& O = ctx->occs[P.occs[q]];
+      const OccData& O = ctx->occs[Us.occs[q]];
       for (int d = 0; d < P.n; ++d) F[(size_t)q * P.npad + P.newidx[d]] = O.f_local[d];
     }
-    P.F.upload(F, s);
-    P.U.ensure((size_t)P.npad * std::max(no, 1));
-    P.d_occs.upload(P.occs, s);
-    P.ld_y = round_up(P.n_b, 4);
+    Us.F.upload(F, s);
+    Us.U.ensure((size_t)P.npad * std::max(no, 1));
+    Us.d_occs.upload(Us.occs, s);
   }
   // coarse problem: G^T G (FP64), its inverse, e, lambda_0 (projector paragraph)
   PhaseScope ph(ctx, FETIRP_PHASE_COARSE, 0.0, 0.0);
@@ -697,9 +706,10 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
     // e_s = N^T f_s
     for (int p = 0; p < n_pat; ++p) {
       PatternData& P = *ctx->pats[p];
-      const int no = (int)P.occs.size();
+      PatternUse& Us = ctx->use[p];
+      const int no = (int)Us.occs.size();
       if (no == 0 || P.kdim == 0) continue;
-      gemm_f64(P.kdim, no, P.npad, 1.0, P.N.p, P.npad, 1, P.F.p, 1, P.npad, 0.0, ctx->e.p + ctx->pofs[p], 1, P.kdim,
+      gemm_f64(P.kdim, no, P.npad, 1.0, P.N.p, P.npad, 1, Us.F.p, 1, P.npad, 0.0, ctx->e.p + ctx->pofs[p], 1, P.kdim,
                s);
     }
     gemm_f64(ctx->n_G, 1, ctx->n_G, 1.0, ctx->Ginv.p, ctx->n_G, 1, ctx->e.p, 1, 1, 0.0, ctx->Ac.p, 1, 1, s);
@@ -711,13 +721,14 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   PatView<double> V{};
   for (int p = 0; p < n_pat; ++p) {
     PatternData& P = *ctx->pats[p];
-    const int no = (int)P.occs.size();
+    PatternUse& Us = ctx->use[p];
+    const int no = (int)Us.occs.size();
     if (no > 0) {
-      FETIRP_CUDA(cudaMemcpyAsync(P.U.p, P.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, s));
-      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, false, s, P.Dinv.p);
-      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, true, s, P.Dinv.p);
+      FETIRP_CUDA(cudaMemcpyAsync(Us.U.p, Us.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, s));
+      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, s, P.Dinv.p);
+      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, s, P.Dinv.p);
     }
-    V.base[p] = P.U.p; V.ld[p] = P.npad; V.off[p] = P.n_i;
+    V.base[p] = Us.U.p; V.ld[p] = P.npad; V.off[p] = P.n_i;
   }
   scatter<double>(L, V, 1, 0.0, ctx->d.p, s);
   axpy_f64(nl, -1.0, ctx->c.p, ctx->d.p, s);
@@ -796,7 +807,7 @@ void apply_F(fetirp_ctx ctx, const double* in, double* out, int k, int prec, boo
   std::vector<long long> base(n_pat);
   for (int p = 0; p < n_pat; ++p) {
     base[p] = total;
-    total += (long long)ctx->pats[p]->occs.size() * k * ctx->pats[p]->ld_y;
+    total += (long long)ctx->use[p].occs.size() * k * ctx->pats[p]->ld_y;
   }
   LocalProblem LP{};
   LP.n_pat = n_pat;
@@ -807,7 +818,7 @@ void apply_F(fetirp_ctx ctx, const double* in, double* out, int k, int prec, boo
       PatternData& P = *ctx->pats[p];
       Yv.base[p] = ctx->Y64.p + base[p]; Yv.ld[p] = P.ld_y; Yv.off[p] = 0;
       Zv.base[p] = ctx->Z64.p + base[p]; Zv.ld[p] = P.ld_y; Zv.off[p] = 0;
-      LP.S[p] = P.S64.p; LP.n_b[p] = P.n_b; LP.n_rhs[p] = (int)P.occs.size() * k; LP.ld[p] = P.ld_y;
+      LP.S[p] = P.S64.p; LP.n_b[p] = P.n_b; LP.n_rhs[p] = (int)ctx->use[p].occs.size() * k; LP.ld[p] = P.ld_y;
       LP.Y[p] = Yv.base[p]; LP.Z[p] = Zv.base[p];
     }
     run_local<double>(ctx, L, src, out, k, Yv, Zv, LP, 8.0);
@@ -818,7 +829,7 @@ void apply_F(fetirp_ctx ctx, const double* in, double* out, int k, int prec, boo
       PatternData& P = *ctx->pats[p];
       Yv.base[p] = ctx->Y32.p + base[p]; Yv.ld[p] = P.ld_y; Yv.off[p] = 0;
       Zv.base[p] = ctx->Z32.p + base[p]; Zv.ld[p] = P.ld_y; Zv.off[p] = 0;
-      LP.S[p] = P.S32.p; LP.n_b[p] = P.n_b; LP.n_rhs[p] = (int)P.occs.size() * k; LP.ld[p] = P.ld_y;
+      LP.S[p] = P.S32.p; LP.n_b[p] = P.n_b; LP.n_rhs[p] = (int)ctx->use[p].occs.size() * k; LP.ld[p] = P.ld_y;
       LP.Y[p] = Yv.base[p]; LP.Z[p] = Zv.base[p];
     }
     run_local<float>(ctx, L, src, out, k, Yv, Zv, LP, 4.0);
@@ -836,7 +847,7 @@ void apply_F(fetirp_ctx ctx, const double* in, double* out, int k, int prec, boo
       Zv.base[p] = ctx->Z32.p + base[p]; Zv.ld[p] = P.ld_y; Zv.off[p] = 0;
       T.S_hi[p] = P.S_hi.p; T.S_lo[p] = P.S_lo.p; T.lds[p] = P.lds;
       T.Y_hi[p] = Yh.base[p]; T.Y_lo[p] = Yl.base[p]; T.Z[p] = Zv.base[p]; T.ldy[p] = P.ld_y;
-      T.n_b[p] = P.n_b; T.n_rhs[p] = (int)P.occs.size() * k;
+      T.n_b[p] = P.n_b; T.n_rhs[p] = (int)ctx->use[p].occs.size() * k;
       flops += 2.0 * P.n_b * (double)P.n_b * T.n_rhs[p];
       bytes += 2.0 * P.n_b * (double)P.n_b * 4 + 3.0 * P.n_b * (double)T.n_rhs[p] * 4;
       rhs_elems += (double)P.n_b * T.n_rhs[p];
@@ -968,8 +979,9 @@ void account_iteration(fetirp_ctx ctx, int prec, long long a, double es) {
   B[FETIRP_PHASE_PROJECT] += 2.0 * (16.0 * nl * k + 8.0 * nG * nG);
   const double e_loc = prec == FETIRP_PREC_FP64 ? 8.0 : 4.0;
   double rhs = 0;
-  for (auto& P : ctx->pats) {
-    const double R = (double)P->occs.size() * k;
+  for (size_t pi = 0; pi < ctx->pats.size(); ++pi) {
+    const PatternData* P = ctx->pats[pi].get();
+    const double R = (double)ctx->use[pi].occs.size() * k;
     F[FETIRP_PHASE_LOCAL] += 2.0 * P->n_b * (double)P->n_b * R;
     B[FETIRP_PHASE_LOCAL] += (prec == FETIRP_PREC_TF32X3 ? 2.0 : 1.0) * e_loc * P->n_b * (double)P->n_b +
                              (prec == FETIRP_PREC_TF32X3 ? 3.0 : 2.0) * e_loc * P->n_b * R;
@@ -1109,24 +1121,26 @@ void recover(fetirp_ctx ctx, double* d_u_out) {
   PatView<double> V{};
   for (int p = 0; p < n_pat; ++p) {
     PatternData& P = *ctx->pats[p];
-    const int no = (int)P.occs.size();
+    PatternUse& Us = ctx->use[p];
+    const int no = (int)Us.occs.size();
     if (no > 0)
-      FETIRP_CUDA(cudaMemcpyAsync(P.U.p, P.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, s));
-    V.base[p] = P.U.p; V.ld[p] = P.npad; V.off[p] = P.n_i;
+      FETIRP_CUDA(cudaMemcpyAsync(Us.U.p, Us.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, s));
+    V.base[p] = Us.U.p; V.ld[p] = P.npad; V.off[p] = P.n_i;
   }
   gather<double>(L, ctx->lam.p, 1, V, s, -1.0, 1.0);
   for (int p = 0; p < n_pat; ++p) {
     PatternData& P = *ctx->pats[p];
-    const int no = (int)P.occs.size();
+    PatternUse& Us = ctx->use[p];
+    const int no = (int)Us.occs.size();
     if (no == 0) continue;
-    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, false, s, P.Dinv.p);
-    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, P.U.p, P.npad, no, true, s, P.Dinv.p);
+    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, s, P.Dinv.p);
+    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, s, P.Dinv.p);
     if (P.kdim > 0 && ctx->n_G > 0)
-      gemm_f64(P.npad, no, P.kdim, -1.0, P.N.p, 1, P.npad, ctx->Ac.p + ctx->pofs[p], 1, P.kdim, 1.0, P.U.p, 1,
+      gemm_f64(P.npad, no, P.kdim, -1.0, P.N.p, 1, P.npad, ctx->Ac.p + ctx->pofs[p], 1, P.kdim, 1.0, Us.U.p, 1,
                P.npad, s);
     const long long tot = (long long)P.n * no;
-    k_unpermute_rotate<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.n, P.dpn, P.npad, P.U.p, P.d_newidx.p,
-                                                                     P.d_occs.p, ctx->d_rot.p, ctx->d_uoff.p, no,
+    k_unpermute_rotate<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.n, P.dpn, P.npad, Us.U.p, P.d_newidx.p,
+                                                                     Us.d_occs.p, ctx->d_rot.p, ctx->d_uoff.p, no,
                                                                      d_u_out);
     FETIRP_LAUNCH_CHECK();
   }
@@ -1143,7 +1157,8 @@ void ensure_history(fetirp_ctx ctx) {
   const double es_h = ctx->opt.precision == FETIRP_PREC_FP64 ? 8.0 : 4.0;
   const double held = ctx->opt.precision == FETIRP_PREC_FP64 ? 8.0 * (ctx->Whist.n + ctx->Qhist.n)
                                                              : 4.0 * (ctx->Whist32.n + ctx->Qhist32.n);
-  long long limit = (long long)(0.5 * ((double)free_b + held) / (2.0 * es_h * std::max(nl, 1)));
+  const double avail = ctx->opt.history_bytes > 0 ? (double)ctx->opt.history_bytes : 0.5 * ((double)free_b + held);
+  long long limit = (long long)(avail / (2.0 * es_h * std::max(nl, 1)));
   long long cap = std::max<long long>(k, std::min(want, limit));
   cap = cap / k * k;
   if (ctx->opt.precision == FETIRP_PREC_FP64) {
@@ -1309,7 +1324,7 @@ void apply_noalloc(fetirp_ctx ctx, const double* V, double* Q, int k, int prec, 
   long long total = 0;
   for (int p = 0; p < n_pat; ++p) {
     pbase[p] = total;
-    total += (long long)ctx->pats[p]->occs.size() * k * ctx->pats[p]->ld_y;
+    total += (long long)ctx->use[p].occs.size() * k * ctx->pats[p]->ld_y;
   }
   auto up = [](size_t x) { return (x + 255) / 256 * 256; };
   const size_t nv = up(sizeof(double) * (size_t)L.n_lambda * k);
@@ -1341,7 +1356,7 @@ void apply_noalloc(fetirp_ctx ctx, const double* V, double* Q, int k, int prec, 
       Yf.base[p] = (float*)y; Zf.base[p] = (float*)z;
       Yd.ld[p] = Zd.ld[p] = Yf.ld[p] = Zf.ld[p] = P.ld_y;
       LP.S[p] = prec == FETIRP_PREC_FP64 ? (const void*)P.S64.p : (const void*)P.S32.p;
-      LP.n_b[p] = P.n_b; LP.n_rhs[p] = (int)P.occs.size() * k; LP.ld[p] = P.ld_y;
+      LP.n_b[p] = P.n_b; LP.n_rhs[p] = (int)ctx->use[p].occs.size() * k; LP.ld[p] = P.ld_y;
       LP.Y[p] = y; LP.Z[p] = z;
     }
     if (prec == FETIRP_PREC_FP64) {
@@ -1365,7 +1380,7 @@ void apply_noalloc(fetirp_ctx ctx, const double* V, double* Q, int k, int prec, 
       Yh.ld[p] = Yl.ld[p] = Zv.ld[p] = P.ld_y;
       T.S_hi[p] = P.S_hi.p; T.S_lo[p] = P.S_lo.p; T.lds[p] = P.lds;
       T.Y_hi[p] = Yh.base[p]; T.Y_lo[p] = Yl.base[p]; T.Z[p] = Zv.base[p]; T.ldy[p] = P.ld_y;
-      T.n_b[p] = P.n_b; T.n_rhs[p] = (int)P.occs.size() * k;
+      T.n_b[p] = P.n_b; T.n_rhs[p] = (int)ctx->use[p].occs.size() * k;
     }
     gather_split(L, V2, k, Yh, Yl, s);
     tc_gemm_tf32x3(T, ctx->tc_error.p, s);
@@ -1410,6 +1425,7 @@ void fetirp_default_options(fetirp_options* o) {
   o->eig_trunc_inner = 1e-6;
   o->use_graphs = 1;
   o->timing_mask = 0;
+  o->history_bytes = 0;
 }
 
 const char* fetirp_status_string(fetirp_status s) {
@@ -1452,6 +1468,17 @@ fetirp_status fetirp_create(const fetirp_options* opt, fetirp_ctx* out) {
   return FETIRP_OK;
 }
 
+fetirp_status fetirp_create_child(fetirp_ctx parent, const fetirp_options* opt, fetirp_ctx* out) {
+  if (!parent || !out) return FETIRP_EINVAL;
+  fetirp_options o = opt ? *opt : parent->opt;
+  o.device = parent->opt.device;
+  fetirp_status st = fetirp_create(&o, out);
+  if (st != FETIRP_OK) return st;
+  (*out)->pats = parent->pats;   // shared, read-only factors
+  (*out)->is_child = true;
+  return FETIRP_OK;
+}
+
 const char* fetirp_last_error(fetirp_ctx ctx) { return ctx ? ctx->err.c_str() : "invalid context"; }
 
 void fetirp_destroy(fetirp_ctx ctx) {
@@ -1471,7 +1498,8 @@ fetirp_status fetirp_create_pattern(fetirp_ctx ctx, int32_t n_nodes, int32_t dpn
     REQUIRE(n_bnd > 0 && n_bnd <= n_nodes, "n_bnd out of range");
     REQUIRE(expected_kernel_dim >= -1, "expected_kernel_dim must be >= -1");
     if ((int)ctx->pats.size() >= MAXP) throw Error(FETIRP_EINVAL, "at most 16 patterns per context");
-    auto P = std::make_unique<PatternData>();
+    if (ctx->is_child) throw Error(FETIRP_ESTATE, "patterns are added to the library context, not to a child");
+    auto P = std::make_shared<PatternData>();
     P->n_nodes = n_nodes; P->dpn = dpn; P->n = n_nodes * dpn; P->expected = expected_kernel_dim;
     const int n = P->n;
     REQUIRE(rowptr[0] == 0, "rowptr[0] must be 0");
@@ -1505,6 +1533,7 @@ fetirp_status fetirp_create_pattern(fetirp_ctx ctx, int32_t n_nodes, int32_t dpn
         P->newidx[old] = next; P->oldidx[next] = old; ++next;
       }
     P->npad = (int)round_up(n, TILE);
+    P->ld_y = round_up(P->n_b, 4);
     P->nbpad = (int)round_up(P->n_b, TILE);
     const int nt = P->npad / TILE;
     std::vector<uint8_t> nz((size_t)nt * nt, 0);
@@ -1523,7 +1552,7 @@ fetirp_status fetirp_create_pattern(fetirp_ctx ctx, int32_t n_nodes, int32_t dpn
     P->d_newidx.upload(P->newidx, ctx->stream);
     factorize_patterns(ctx, {P.get()});
     *pattern_id = (int)ctx->pats.size();
-    ctx->pats.push_back(std::move(P));
+    ctx->pats.push_back(P);
     invalidate(ctx);
     return FETIRP_OK;
   });
@@ -1598,6 +1627,16 @@ fetirp_status fetirp_add_occurrence(fetirp_ctx ctx, int32_t pattern_id, const do
   });
 }
 
+fetirp_status fetirp_clear_occurrences(fetirp_ctx ctx) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    ctx->occs.clear();
+    ctx->k_user = 0;
+    ctx->groups_user.clear();
+    invalidate(ctx);
+    return FETIRP_OK;
+  });
+}
+
 fetirp_status fetirp_set_groups(fetirp_ctx ctx, int32_t k, const int32_t* group_of_occ) {
   return guarded(ctx, [&]() -> fetirp_status {
     REQUIRE(k >= 1 && k <= 64, "k must be in 1..64");
@@ -1633,6 +1672,40 @@ fetirp_status fetirp_solve(fetirp_ctx ctx, int64_t n_lambda, const double* c, do
     FETIRP_CUDA(cudaMemcpyAsync(u_out, du.p, sizeof(double) * ctx->n_u, cudaMemcpyDeviceToHost, ctx->stream));
     FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
     return st;
+  });
+}
+
+fetirp_status fetirp_autotune_k(fetirp_ctx ctx, int64_t n_lambda, const double* c, int32_t n_cand,
+                                const int32_t* candidates, int32_t* best_k, double* times_ms) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    REQUIRE(n_cand >= 1 && candidates && best_k, "bad candidate list");
+    const int n_occ = (int)ctx->occs.size();
+    if (n_occ == 0) throw Error(FETIRP_ESTATE, "no occurrence has been added");
+    double best = 1e300;
+    int bk = -1;
+    std::vector<int> g(n_occ);
+    for (int i = 0; i < n_cand; ++i) {
+      const int k = std::max(1, std::min(candidates[i], std::min(64, n_occ)));
+      REQUIRE(candidates[i] >= 1 && candidates[i] <= 64, "candidate k out of 1..64");
+      for (int o = 0; o < n_occ; ++o) g[o] = (int)((long long)o * k / n_occ);
+      ctx->k_user = k;
+      ctx->groups_user = g;
+      invalidate(ctx);
+      prepare_timed(ctx, n_lambda, c, nullptr);
+      DBuf<double> dl(n_lambda), du(ctx->n_u);
+      fetirp_stats st{};
+      const fetirp_status rs = run_solve(ctx, dl.p, du.p, &st);
+      const double t = rs == FETIRP_OK ? st.solve_ms : 1e300;
+      if (times_ms) times_ms[i] = rs == FETIRP_OK ? t : INFINITY;
+      if (t < best) { best = t; bk = k; }
+    }
+    if (bk < 0) throw Error(FETIRP_ENOCONV, "no candidate k reached the tolerance");
+    for (int o = 0; o < n_occ; ++o) g[o] = (int)((long long)o * bk / n_occ);
+    ctx->k_user = bk;
+    ctx->groups_user = g;
+    invalidate(ctx);
+    *best_k = bk;
+    return FETIRP_OK;
   });
 }
 
@@ -1675,6 +1748,7 @@ fetirp_status fetirp_apply_block(fetirp_ctx ctx, int32_t k, const double* V, dou
 
 fetirp_status fetirp_factorize(fetirp_ctx ctx) {
   return guarded(ctx, [&]() -> fetirp_status {
+    if (ctx->is_child) throw Error(FETIRP_ESTATE, "a child context shares its parent's factors; factorise the parent");
     reset_phases(ctx);
     const unsigned long long l0 = g_launch_count;
     std::vector<PatternData*> all;

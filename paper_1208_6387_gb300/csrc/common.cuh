@@ -26,8 +26,9 @@ struct Error : public std::runtime_error {
                                 __FILE__ + ":" + std::to_string(__LINE__));                     \
   } while (0)
 
-// Every kernel launch of the library is followed by this check, which also counts the launch.
-extern unsigned long long g_launch_count;
+// Every kernel launch of the library is followed by this check, which also counts the launch (per host
+// thread: a context is driven by one thread at a time, so its counts stay exact when several run at once).
+extern thread_local unsigned long long g_launch_count;
 #define FETIRP_LAUNCH_CHECK()        \
   do {                               \
     ++::fetirp::g_launch_count;      \

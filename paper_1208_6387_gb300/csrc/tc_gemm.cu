@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "ops.cuh"
 #include "tc.cuh"
@@ -288,7 +289,9 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
+  static std::mutex mu;
   static EncodeTiledFn fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
   if (!fn) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -324,12 +327,15 @@ void split_tf32(const double* x, long long rows, long long cols, long long ld_in
 }
 
 void tc_init() {
-  static int attr_device = -1;
+  static std::mutex mu;
+  static bool attr_done[64] = {};
+  std::lock_guard<std::mutex> lock(mu);
   int dev = 0;
   FETIRP_CUDA(cudaGetDevice(&dev));
-  if (attr_device != dev) {
+  if (dev < 0 || dev >= 64) throw Error(1, "device ordinal out of range");
+  if (!attr_done[dev]) {
     FETIRP_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr_device = dev;
+    attr_done[dev] = true;
   }
   encode_fn();   // resolve the driver entry point outside any stream capture
 }

@@ -25,7 +25,7 @@ class fetirp_options(C.Structure):
                 ("max_outer", C.c_int32), ("inner_tol", C.c_double), ("pivot_tol", C.c_double),
                 ("eig_trunc", C.c_double), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
                 ("check_every", C.c_int32), ("timing", C.c_int32), ("eig_trunc_inner", C.c_double),
-                ("use_graphs", C.c_int32), ("timing_mask", C.c_int32)]
+                ("use_graphs", C.c_int32), ("timing_mask", C.c_int32), ("history_bytes", C.c_int64)]
 
 
 PHASES = ["factor", "coarse", "local", "gather", "scatter", "project", "gram", "reorth", "update", "recover",
@@ -45,6 +45,13 @@ class fetirp_stats(C.Structure):
             v = getattr(self, name)
             d[name] = list(v) if name.startswith("phase_") else v
         return d
+
+
+class fetirp_structure(C.Structure):
+    _fields_ = [("n_occ", C.c_int32), ("pattern_id", C.c_void_p), ("rot", C.c_void_p), ("link_offset", C.c_void_p),
+                ("local_node", C.c_void_p), ("global_comp", C.c_void_p), ("lambda_row", C.c_void_p),
+                ("sign", C.c_void_p), ("f_offset", C.c_void_p), ("f_global", C.c_void_p), ("n_lambda", C.c_int64),
+                ("c", C.c_void_p), ("k", C.c_int32), ("group_of_occ", C.c_void_p)]
 
 
 class FetirpError(RuntimeError):
@@ -68,6 +75,14 @@ _SIGS = {
                                         C.POINTER(C.c_int32)]),
     "fetirp_add_occurrence": (C.c_int, [P, C.c_int32, P, C.c_int32, P, P, P, P, P, C.POINTER(C.c_int32)]),
     "fetirp_set_groups": (C.c_int, [P, C.c_int32, P]),
+    "fetirp_clear_occurrences": (C.c_int, [P]),
+    "fetirp_autotune_k": (C.c_int, [P, C.c_int64, P, C.c_int32, P, C.POINTER(C.c_int32), P]),
+    "fetirp_create_child": (C.c_int, [P, C.POINTER(fetirp_options), C.POINTER(P)]),
+    "fetirp_server_create": (C.c_int, [P, C.POINTER(fetirp_options), C.c_int32, C.c_int64, C.POINTER(P)]),
+    "fetirp_server_submit": (C.c_int, [P, C.POINTER(fetirp_structure), C.POINTER(C.c_int64)]),
+    "fetirp_server_wait": (C.c_int, [P, C.c_int64, C.c_double, C.POINTER(C.c_int32), P, P, C.POINTER(fetirp_stats),
+                                     C.POINTER(C.c_double)]),
+    "fetirp_server_destroy": (None, [P]),
     "fetirp_solve": (C.c_int, [P, C.c_int64, P, P, P, C.POINTER(fetirp_stats)]),
     "fetirp_solve_device": (C.c_int, [P, C.c_int64, P, P, P, C.POINTER(fetirp_stats)]),
     "fetirp_apply_block": (C.c_int, [P, C.c_int32, P, P, C.c_int32]),
@@ -161,6 +176,86 @@ def fetirp_add_occurrence(ctx, pattern_id, rot, local_node, global_comp, lambda_
 def fetirp_set_groups(ctx, k, group_of_occ):
     g = np.ascontiguousarray(group_of_occ, dtype=np.int32)
     _check(ctx, lib().fetirp_set_groups(ctx, int(k), _ptr(g)))
+
+
+def fetirp_autotune_k(ctx, n_lambda, c, candidates=(4, 8, 16, 32)):
+    """Returns (best k, solve times in ms per candidate); the context keeps the best grouping."""
+    c = None if c is None else np.ascontiguousarray(c, dtype=np.float64)
+    cand = np.ascontiguousarray(candidates, dtype=np.int32)
+    times = np.zeros(len(cand))
+    bk = C.c_int32()
+    _check(ctx, lib().fetirp_autotune_k(ctx, int(n_lambda), _ptr(c), len(cand), _ptr(cand), C.byref(bk), _ptr(times)))
+    return bk.value, times
+
+
+def fetirp_clear_occurrences(ctx):
+    _check(ctx, lib().fetirp_clear_occurrences(ctx))
+
+
+def fetirp_create_child(parent, opts: fetirp_options | None = None):
+    h = C.c_void_p()
+    st = lib().fetirp_create_child(parent, C.byref(opts) if opts is not None else None, C.byref(h))
+    if st != FETIRP_OK:
+        raise FetirpError(st, "fetirp_create_child failed")
+    return h
+
+
+def structure_of(prob, pattern_ids=None):
+    """Marshal a fetirp_gen.Problem into a fetirp_structure (the arrays are kept alive on the returned
+    object).  pattern_ids maps the problem's pattern indices to library ids (default: identity)."""
+    pid = np.array([o.pattern if pattern_ids is None else pattern_ids[o.pattern] for o in prob.occs], dtype=np.int32)
+    rot = np.concatenate([o.rot.astype(np.float64).ravel() for o in prob.occs])
+    lo = np.concatenate([[0], np.cumsum([o.n_links for o in prob.occs])]).astype(np.int32)
+    cat = lambda f, dt: np.ascontiguousarray(np.concatenate([f(o) for o in prob.occs]).astype(dt))
+    ln, gc = cat(lambda o: o.link_local_node, np.int32), cat(lambda o: o.link_global_comp, np.int8)
+    lr, sg = cat(lambda o: o.link_lambda_row, np.int32), cat(lambda o: o.link_sign, np.int8)
+    fo = np.concatenate([[0], np.cumsum([len(o.f_global) for o in prob.occs])]).astype(np.int64)
+    fg = cat(lambda o: o.f_global, np.float64)
+    c = np.ascontiguousarray(prob.c, dtype=np.float64)
+    grp = np.ascontiguousarray(prob.groups, dtype=np.int32)
+    s = fetirp_structure(len(prob.occs), _ptr(pid), _ptr(rot), _ptr(lo), _ptr(ln), _ptr(gc), _ptr(lr), _ptr(sg),
+                         _ptr(fo), _ptr(fg), int(prob.n_lambda), _ptr(c), int(prob.k), _ptr(grp))
+    s._keep = (pid, rot, lo, ln, gc, lr, sg, fo, fg, c, grp)
+    return s
+
+
+def fetirp_server_create(library, slot_opts: fetirp_options | None, max_slots, mem_budget_bytes):
+    h = C.c_void_p()
+    st = lib().fetirp_server_create(library, C.byref(slot_opts) if slot_opts is not None else None, int(max_slots),
+                                    int(mem_budget_bytes), C.byref(h))
+    if st != FETIRP_OK:
+        raise FetirpError(st, "fetirp_server_create failed")
+    return h
+
+
+def fetirp_server_submit(srv, structure):
+    t = C.c_int64()
+    st = lib().fetirp_server_submit(srv, C.byref(structure), C.byref(t))
+    if st != FETIRP_OK:
+        raise FetirpError(st, "fetirp_server_submit failed")
+    return t.value
+
+
+def fetirp_server_wait(srv, ticket, n_lambda, n_u, timeout_s=-1.0, allow_noconv=False):
+    """Returns None if not done within timeout_s, else (lambda, u, stats dict, latency_ms)."""
+    done = C.c_int32()
+    lam = np.zeros(int(n_lambda))
+    u = np.zeros(int(n_u))
+    stt = fetirp_stats()
+    lat = C.c_double()
+    s = lib().fetirp_server_wait(srv, int(ticket), float(timeout_s), C.byref(done), _ptr(lam), _ptr(u), C.byref(stt),
+                                 C.byref(lat))
+    if not done.value:
+        if s != FETIRP_OK:
+            raise FetirpError(s, "fetirp_server_wait failed")
+        return None
+    if s != FETIRP_OK and not (allow_noconv and s == FETIRP_ENOCONV):
+        raise FetirpError(s, "structure failed in the server")
+    return lam, u, stt.as_dict(), lat.value
+
+
+def fetirp_server_destroy(srv):
+    lib().fetirp_server_destroy(srv)
 
 
 def fetirp_prepare(ctx, n_lambda, c=None):
