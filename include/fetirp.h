@@ -60,7 +60,7 @@ typedef struct {
   int32_t max_iter;    /* cap on block iterations over the whole solve; default 2000 */
   int32_t block_k;     /* multivector width k; 1 = classical FETI-CG; default 32 (clamped to the number
                           of occurrences; fetirp_set_groups overrides) */
-  int32_t max_outer;   /* cap on FP64 refinement steps of the mixed forms; default 12 */
+  int32_t max_outer;   /* cap on FP64 refinement steps of the mixed forms; default 30 */
   double inner_tol;    /* relative tolerance of each inner (low-precision) solve; default 1e-6 */
   double pivot_tol;    /* zero pivot when pivot <= pivot_tol * original diagonal; default 1e-9 */
   double eig_trunc;    /* a direction is dropped when its normalisation pivot <= eig_trunc * largest;

@@ -98,6 +98,8 @@ struct PatternData {
   DBuf<int64_t> d_rowptr;
   DBuf<int> d_col, d_newidx, zp;
   DBuf<double> d_val, L, diag0, S64, N, Nb, Dinv, LS, XS, DinvS, Sdag, Nwork;
+  DBuf<double> Kplus;          // dense K^+ (npad x npad, symmetric) for small patterns, else empty
+  bool has_kplus = false;
   DBuf<int> zpS, d_zpiv;
   std::vector<int> h_zp;
   int* h_zp_pinned = nullptr;
@@ -118,8 +120,11 @@ struct PatternUse {
   std::vector<int> occs;       // occurrences of this pattern (ids), q = position
   DBuf<int> d_occs;
   DBuf<double> F;              // npad x n_occ loads (pattern frame, new ordering)
-  DBuf<double> U;              // npad x n_occ work (local solves)
+  DBuf<double> U, U2;          // npad x n_occ work (local solves)
 };
+
+// Patterns up to this padded size keep a dense K^+ (the solves of d and of the recovery become one product).
+constexpr int KPLUS_MAX = 2048;
 
 struct OccData {
   int pattern = 0;
@@ -418,6 +423,16 @@ void factor_stage_b(PatternData& P, cudaStream_t s) {
     gemm_f64(nb, nb, kd, 1.0, A, kd, 1, E, 1, kd, 1.0, P.Sdag.p, nb, 1, s);     // + E D E^T
     Sdag = P.Sdag.p;
   }
+  if (npad <= KPLUS_MAX) {   // K^+ = X^T X with X = L^{-1} (zero-pivot rows of X are 0)
+    P.XS.ensure((size_t)npad * npad);
+    FETIRP_CUDA(cudaMemsetAsync(P.XS.p, 0, sizeof(double) * (size_t)npad * npad, s));
+    k_set_diag<<<ceil_div(npad, 128), 128, 0, s>>>(P.XS.p, npad, 0, npad, 1.0);
+    FETIRP_LAUNCH_CHECK();
+    tri_solve(P.L.p, npad, P.plan, P.zp.p, P.XS.p, npad, npad, false, s, P.Dinv.p);
+    P.Kplus.ensure((size_t)npad * npad);
+    gemm_f64(npad, npad, npad, 1.0, P.XS.p, npad, 1, P.XS.p, 1, npad, 0.0, P.Kplus.p, npad, 1, s);
+    P.has_kplus = true;
+  }
   P.S32.ensure((size_t)nb * nb);
   const size_t nn = (size_t)nb * nb;
   k_to_f32<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(nn, Sdag, P.S32.p);
@@ -682,6 +697,7 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
     }
     Us.F.upload(F, s);
     Us.U.ensure((size_t)P.npad * std::max(no, 1));
+    if (P.has_kplus) Us.U2.ensure((size_t)P.npad * std::max(no, 1));
     Us.d_occs.upload(Us.occs, s);
   }
   // coarse problem: G^T G (FP64), its inverse, e, lambda_0 (projector paragraph)
@@ -724,9 +740,14 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
     PatternUse& Us = ctx->use[p];
     const int no = (int)Us.occs.size();
     if (no > 0) {
-      FETIRP_CUDA(cudaMemcpyAsync(Us.U.p, Us.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, s));
-      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, s, P.Dinv.p);
-      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, s, P.Dinv.p);
+      if (P.has_kplus) {   // boundary rows of K^+ F
+        gemm_f64(P.n_b, no, P.npad, 1.0, P.Kplus.p + P.n_i, 1, P.npad, Us.F.p, 1, P.npad, 0.0, Us.U.p + P.n_i, 1,
+                 P.npad, s);
+      } else {
+        FETIRP_CUDA(cudaMemcpyAsync(Us.U.p, Us.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, s));
+        tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, s, P.Dinv.p);
+        tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, s, P.Dinv.p);
+      }
     }
     V.base[p] = Us.U.p; V.ld[p] = P.npad; V.off[p] = P.n_i;
   }
@@ -739,7 +760,7 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   ctx->W.ensure((size_t)nl * k); ctx->Q.ensure((size_t)nl * k); ctx->Zr.ensure((size_t)nl * k);
   ctx->V1.ensure((size_t)nl * 64); ctx->V2.ensure((size_t)nl * 64);
   ctx->eta.ensure((size_t)k * k); ctx->wr.ensure(k);
-  ctx->eta_part.ensure((size_t)(std::min(152, ceil_div(nl, 16)) + 1) * k * (k + 1)); ctx->T.ensure((size_t)k * k); ctx->alpha.ensure(k);
+  ctx->eta_part.ensure((size_t)(eta_chunks(nl) + 1) * k * (k + 1)); ctx->T.ensure((size_t)k * k); ctx->alpha.ensure(k);
   ctx->n_kept.ensure(1);
   ctx->d_state.ensure(4);
   if (!ctx->tc_error.p) { ctx->tc_error.alloc(1); ctx->tc_error.zero(s); }
@@ -947,18 +968,22 @@ void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
   apply_F(ctx, ctx->Zr.p, ctx->Q.p, k, prec, false, true);   // P~ = P^T F W (Table 1 line 5.1)
   {
     PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 0.0, 0.0);
-    eta_and_wr(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta.p, ctx->wr.p, ctx->eta_part, s);
+    eta_partials(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta_part, s);
   }
   {
     PhaseScope ph(ctx, FETIRP_PHASE_NORMALISE, 0.0, 0.0);
-    normalise(k, ctx->eta.p, ctx->wr.p, prec == FETIRP_PREC_FP64 ? ctx->opt.eig_trunc : ctx->opt.eig_trunc_inner,
-              ctx->T.p, ctx->alpha.p, ctx->n_kept.p, s);
+    normalise(k, ctx->eta_part.p, eta_chunks(nl),
+              prec == FETIRP_PREC_FP64 ? ctx->opt.eig_trunc : ctx->opt.eig_trunc_inner, ctx->T.p, ctx->alpha.p,
+              ctx->n_kept.p, s);
   }
   {
     PhaseScope ph(ctx, FETIRP_PHASE_UPDATE, 0.0, 0.0);
+    AdvanceArgs adv;
+    adv.cols = d_cols; adv.k = k; adv.cap = cap; adv.n_kept = ctx->n_kept.p;
+    adv.dropped = ctx->d_state.p + 1; adv.iters = ctx->d_state.p + 2;
+    adv.counter = reinterpret_cast<unsigned*>(ctx->d_state.p + 3);
     update<TH>(nl, k, ctx->Zr.p, ctx->Q.p, ctx->T.p, ctx->alpha.p, Wh, Qh, d_cols, cap, ctx->lam.p, ctx->r.p,
-               ctx->rr_part.p, ctx->rr_blocks, s);
-    advance(d_cols, k, cap, ctx->n_kept.p, ctx->d_state.p + 1, ctx->d_state.p + 2, s);
+               ctx->rr_part.p, ctx->rr_blocks, s, adv);
   }
 }
 
@@ -1068,7 +1093,8 @@ double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, His
   ctx->h_state[0] = (int)H.cols;
   ctx->h_state[1] = 0;
   ctx->h_state[2] = 0;
-  FETIRP_CUDA(cudaMemcpyAsync(ctx->d_state.p, ctx->h_state, 3 * sizeof(int), cudaMemcpyHostToDevice, s));
+  ctx->h_state[3] = 0;   // last-CTA counter of update()
+  FETIRP_CUDA(cudaMemcpyAsync(ctx->d_state.p, ctx->h_state, 4 * sizeof(int), cudaMemcpyHostToDevice, s));
   const int G = std::max(1, ctx->opt.check_every);
   int kept = k;
   while (rnorm > target && it_budget > 0 && kept > 0) {
@@ -1081,7 +1107,7 @@ double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, His
     }
     FETIRP_CUDA(cudaMemcpyAsync(ctx->h_rr, ctx->rr_part.p, sizeof(double) * ctx->rr_blocks,
                                 cudaMemcpyDeviceToHost, s));
-    FETIRP_CUDA(cudaMemcpyAsync(ctx->h_state + 3, ctx->n_kept.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FETIRP_CUDA(cudaMemcpyAsync(ctx->h_state + 4, ctx->n_kept.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     FETIRP_CUDA(cudaStreamSynchronize(s));
     if (ctx->opt.timing && g == G && ctx->opt.use_graphs)
       for (auto& r : ctx->gc.recs) {
@@ -1092,7 +1118,7 @@ double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, His
     double acc = 0.0;
     for (int i = 0; i < ctx->rr_blocks; ++i) acc += ctx->h_rr[i];
     rnorm = std::sqrt(acc);
-    kept = ctx->h_state[3];
+    kept = ctx->h_state[4];
     st.iterations += g;
     it_budget -= g;
   }
@@ -1133,13 +1159,19 @@ void recover(fetirp_ctx ctx, double* d_u_out) {
     PatternUse& Us = ctx->use[p];
     const int no = (int)Us.occs.size();
     if (no == 0) continue;
-    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, s, P.Dinv.p);
-    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, s, P.Dinv.p);
+    double* Usol = Us.U.p;
+    if (P.has_kplus) {
+      gemm_f64(P.npad, no, P.npad, 1.0, P.Kplus.p, 1, P.npad, Us.U.p, 1, P.npad, 0.0, Us.U2.p, 1, P.npad, s);
+      Usol = Us.U2.p;
+    } else {
+      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, s, P.Dinv.p);
+      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, s, P.Dinv.p);
+    }
     if (P.kdim > 0 && ctx->n_G > 0)
-      gemm_f64(P.npad, no, P.kdim, -1.0, P.N.p, 1, P.npad, ctx->Ac.p + ctx->pofs[p], 1, P.kdim, 1.0, Us.U.p, 1,
+      gemm_f64(P.npad, no, P.kdim, -1.0, P.N.p, 1, P.npad, ctx->Ac.p + ctx->pofs[p], 1, P.kdim, 1.0, Usol, 1,
                P.npad, s);
     const long long tot = (long long)P.n * no;
-    k_unpermute_rotate<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.n, P.dpn, P.npad, Us.U.p, P.d_newidx.p,
+    k_unpermute_rotate<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.n, P.dpn, P.npad, Usol, P.d_newidx.p,
                                                                      Us.d_occs.p, ctx->d_rot.p, ctx->d_uoff.p, no,
                                                                      d_u_out);
     FETIRP_LAUNCH_CHECK();
@@ -1414,7 +1446,7 @@ void fetirp_default_options(fetirp_options* o) {
   o->tol = 1e-8;
   o->max_iter = 2000;
   o->block_k = 32;
-  o->max_outer = 12;
+  o->max_outer = 30;
   o->inner_tol = 1e-6;
   o->pivot_tol = 1e-9;
   o->eig_trunc = 1e-12;

@@ -100,9 +100,10 @@ __global__ void k_reduce_chunks(int count, int chunks, const double* __restrict_
 
 // One CTA: pivoted Cholesky of eta with truncation, T = Pi M^{-T}, alpha = T^T (W^T r).
 // Pivot search by warp shuffles; the triangular inverse by a right-looking sweep, parallel over (row, column).
-__global__ void __launch_bounds__(512) k_normalise(int k, const double* __restrict__ eta,
-                                                   const double* __restrict__ wr, double trunc,
-                                                   double* __restrict__ T, double* __restrict__ alpha,
+// ext_partial: `chunks` row-chunk partials of the k x (k+1) block [eta | W^T r]; they are added here in chunk
+// order (one warp per output entry), so no separate reduction launch is needed.
+__global__ void __launch_bounds__(512) k_normalise(int k, const double* __restrict__ ext_partial, int chunks,
+                                                   double trunc, double* __restrict__ T, double* __restrict__ alpha,
                                                    int* __restrict__ n_kept) {
   __shared__ double A[64][65];    // eta, then (after the factorisation) X = M^{-1}
   __shared__ double Lc[64][65];   // Lc[i][step], original row index i
@@ -113,12 +114,22 @@ __global__ void __launch_bounds__(512) k_normalise(int k, const double* __restri
   __shared__ int s_r, s_p;
   __shared__ double s_dmax;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nout = k * (k + 1);
+  double* ext = &Lc[0][0];   // [eta | wr] (k (k+1) <= 64 * 65 entries) lives in Lc's storage until Lc is needed
+  for (int o = warp; o < nout; o += blockDim.x / 32) {
+    double v = 0.0;
+    for (int c = lane; c < chunks; c += 32) v += ext_partial[(size_t)c * nout + o];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) ext[o] = v;
+  }
+  __syncthreads();
   for (int idx = tid; idx < k * k; idx += blockDim.x) {
     const int i = idx / k, j = idx % k;
-    A[i][j] = 0.5 * (eta[(size_t)i * k + j] + eta[(size_t)j * k + i]);
-    Lc[i][j] = 0.0;
+    A[i][j] = 0.5 * (ext[i * (k + 1) + j] + ext[j * (k + 1) + i]);
   }
-  if (tid < k) { done[tid] = 0; rhs[tid] = wr[tid]; ipiv[tid] = -1; }
+  if (tid < k) { done[tid] = 0; rhs[tid] = ext[tid * (k + 1) + k]; ipiv[tid] = -1; }
+  __syncthreads();
+  for (int idx = tid; idx < 64 * 65; idx += blockDim.x) (&Lc[0][0])[idx] = 0.0;
   __syncthreads();
   if (warp == 0) {
     double m = 0.0;
@@ -220,7 +231,8 @@ __global__ void __launch_bounds__(256) k_update(int n, int k, const double* __re
                                                 const double* __restrict__ alpha, TH* __restrict__ Wn,
                                                 TH* __restrict__ Qn, const int* __restrict__ d_off, long long ldn,
                                                 double* __restrict__ lam,
-                                                double* __restrict__ r, double* __restrict__ rr_partial) {
+                                                double* __restrict__ r, double* __restrict__ rr_partial,
+                                                AdvanceArgs adv) {
   __shared__ double sT[64][65];
   __shared__ double beta[64];
   __shared__ double warp_rr[8];
@@ -272,6 +284,20 @@ __global__ void __launch_bounds__(256) k_update(int n, int k, const double* __re
     double s = 0.0;
     for (int w = 0; w < 8; ++w) s += warp_rr[w];
     rr_partial[blockIdx.x] = s;
+    // the last CTA to finish (every CTA has read the history offset by then) advances the history state
+    if (adv.cols) {
+      __threadfence();
+      const unsigned prev = atomicAdd(adv.counter, 1u);
+      if (prev == gridDim.x - 1) {
+        int c = *adv.cols + adv.k;
+        if ((long long)c + adv.k > adv.cap) c = 0;
+        *adv.cols = c;
+        *adv.dropped += adv.k - *adv.n_kept;
+        *adv.iters += 1;
+        *adv.counter = 0u;
+        __threadfence();
+      }
+    }
   }
 }
 
@@ -339,18 +365,15 @@ __global__ void k_reduce_chunks_warp(int count, int chunks, const double* __rest
   if (lane == 0) C[o] = v;
 }
 
-void eta_and_wr(int n, int k, const double* W, const double* Q, const double* r, double* eta, double* wr,
-                DBuf<double>& partial, cudaStream_t s) {
-  const int chunks = std::max(1, std::min(152, ceil_div(n, 16)));
+int eta_chunks(int n) { return std::max(1, std::min(152, ceil_div(n, 16))); }
+
+void eta_partials(int n, int k, const double* W, const double* Q, const double* r, DBuf<double>& partial,
+                  cudaStream_t s) {
+  const int chunks = eta_chunks(n);
   const int rows = ceil_div(n, chunks);
   const int nout = k * (k + 1);
   partial.ensure((size_t)chunks * nout + nout);
   k_eta_partial<<<chunks, 256, 0, s>>>(n, k, W, Q, r, rows, partial.p);
-  FETIRP_LAUNCH_CHECK();
-  double* ext = partial.p + (size_t)chunks * nout;
-  k_reduce_chunks_warp<<<ceil_div(nout, 8), 256, 0, s>>>(nout, chunks, partial.p, ext);
-  FETIRP_LAUNCH_CHECK();
-  k_split_eta<<<ceil_div(nout, 256), 256, 0, s>>>(k, ext, eta, wr);
   FETIRP_LAUNCH_CHECK();
 }
 
@@ -384,24 +407,25 @@ void small_gemm(int m, int k, const double* A, const double* B, double* C, cudaS
   FETIRP_LAUNCH_CHECK();
 }
 
-void normalise(int k, const double* eta, const double* wr, double trunc, double* T, double* alpha, int* n_kept,
+void normalise(int k, const double* ext_partial, int chunks, double trunc, double* T, double* alpha, int* n_kept,
                cudaStream_t s) {
   if (k > 64) throw Error(1, "block width k > 64 is not supported");
-  k_normalise<<<1, 512, 0, s>>>(k, eta, wr, trunc, T, alpha, n_kept);
+  k_normalise<<<1, 512, 0, s>>>(k, ext_partial, chunks, trunc, T, alpha, n_kept);
   FETIRP_LAUNCH_CHECK();
 }
 
 template <typename TH>
 void update(int n, int k, const double* W, const double* Q, const double* T, const double* alpha, TH* Wn, TH* Qn,
             const int* d_off, long long ldn, double* lam, double* r, double* rr_partial, int rr_blocks,
-            cudaStream_t s) {
-  k_update<TH><<<rr_blocks, 256, 0, s>>>(n, k, W, Q, T, alpha, Wn, Qn, d_off, ldn, lam, r, rr_partial);
+            cudaStream_t s, const AdvanceArgs& adv) {
+  k_update<TH><<<rr_blocks, 256, 0, s>>>(n, k, W, Q, T, alpha, Wn, Qn, d_off, ldn, lam, r, rr_partial, adv);
   FETIRP_LAUNCH_CHECK();
 }
 template void update<double>(int, int, const double*, const double*, const double*, const double*, double*,
-                             double*, const int*, long long, double*, double*, double*, int, cudaStream_t);
+                             double*, const int*, long long, double*, double*, double*, int, cudaStream_t,
+                             const AdvanceArgs&);
 template void update<float>(int, int, const double*, const double*, const double*, const double*, float*, float*,
-                            const int*, long long, double*, double*, double*, int, cudaStream_t);
+                            const int*, long long, double*, double*, double*, int, cudaStream_t, const AdvanceArgs&);
 
 // C[c][g] = sum over the rows of group g: w(row) * r[row] * Qh[row][c]  (= Qh^T S(r), the split multivector
 // S(r) having at most two nonzero groups per row).  Grid (128-column tiles, groups, row chunks): each CTA

@@ -107,24 +107,37 @@ void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, long lon
                  double* W, DBuf<double>& scratch, cudaStream_t s);
 // history count += k with restart, dropped and iteration counters (one thread)
 void advance(int* cols, int k, long long cap, const int* n_kept, int* dropped, int* iters, cudaStream_t s);
-// eta = W^T Q (k x k, row-major) and wr = W^T r (k) in one pass over the rows (FP64 sums, fixed order).
-void eta_and_wr(int n, int k, const double* W, const double* Q, const double* r, double* eta, double* wr,
-                DBuf<double>& partial, cudaStream_t s);
+// Row-chunk partials (eta_chunks(n) of them) of [eta | wr] = W^T [Q | r], a k x (k+1) block, FP64 sums;
+// normalise() adds them in chunk order.
+int eta_chunks(int n);
+void eta_partials(int n, int k, const double* W, const double* Q, const double* r, DBuf<double>& partial,
+                  cudaStream_t s);
 // C (m x k) = A (m x m) B (m x k), row-major, FP64, one warp per row (small coarse products).
 void small_gemm(int m, int k, const double* A, const double* B, double* C, cudaStream_t s);
-// Normalisation of eta = W^T P~ (k x k row-major) so that T^T eta T = I on the kept directions: pivoted
+// Normalisation of eta = W^T P~ (k x k) so that T^T eta T = I on the kept directions: pivoted
 // Cholesky eta = Pi M M^T Pi^T, stopping when the largest remaining pivot <= trunc * (largest diagonal);
 // T = Pi M^{-T} on the kept columns (zero columns for dropped ones); alpha = T^T wr with wr = W^T r.
-// One CTA, k <= 64.
-void normalise(int k, const double* eta, const double* wr, double trunc, double* T, double* alpha, int* n_kept,
+// Input: the row-chunk partials of [eta | wr] from eta_partials().  One CTA, k <= 64.
+void normalise(int k, const double* ext_partial, int chunks, double trunc, double* T, double* alpha, int* n_kept,
                cudaStream_t s);
 // Wn = W T, Qn = Q T (n x k each, written to history), lambda += Wn alpha, r -= Qn alpha, and
 // rr_partial[block] = partial sums of r^2 after the update.
+// History bookkeeping done by the last CTA of update(): stored directions += k (restart when the next block
+// would not fit), dropped and iteration counters.  cols = NULL: nothing.
+struct AdvanceArgs {
+  int* cols = nullptr;
+  int k = 0;
+  long long cap = 0;
+  const int* n_kept = nullptr;
+  int* dropped = nullptr;
+  int* iters = nullptr;
+  unsigned* counter = nullptr;   // zero between launches
+};
 // d_off (device, may be NULL): column offset added to Wn and Qn on the device.
 template <typename TH>
 void update(int n, int k, const double* W, const double* Q, const double* T, const double* alpha, TH* Wn, TH* Qn,
             const int* d_off, long long ldn, double* lam, double* r, double* rr_partial, int rr_blocks,
-            cudaStream_t s);
+            cudaStream_t s, const AdvanceArgs& adv = AdvanceArgs());
 void sum_sq(int n, const double* x, double* out_partial, int blocks, cudaStream_t s);
 void axpy_f64(int n, double a, const double* x, double* y, cudaStream_t s);
 
