@@ -165,7 +165,7 @@ def run_ours(args, rank, world, local):
 
     def make_ctx(precision, timing, mask):
         opts = F.fetirp_default_options(precision=precision, tol=1e-8, inner_tol=args.inner_tol, device=local,
-                                        timing=timing, timing_mask=mask)
+                                        timing=timing, timing_mask=mask, history_bytes=int(args.history_gb * 1e9))
         opts.cuda_stream = stream.cuda_stream
         c = F.fetirp_create(opts)
         F.load_problem(c, prob)
@@ -294,7 +294,7 @@ def run_ours(args, rank, world, local):
     for i in range(max(2, min(args.steps, 5)) + 1):
         t = time.perf_counter()
         c2 = F.fetirp_create(F.fetirp_default_options(precision=args.precision, tol=1e-8, inner_tol=args.inner_tol,
-                                                       device=local))
+                                                       device=local, history_bytes=int(args.history_gb * 1e9)))
         F.load_problem(c2, prob)
         F.fetirp_solve(c2, prob.n_lambda, prob.c, nu)
         F.fetirp_destroy(c2)
@@ -478,6 +478,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-reference", action="store_true")
+    ap.add_argument("--history-gb", type=float, default=0.0,
+                    help="cap on the direction history (GB); 0 = the library default (half of free memory)")
     ap.add_argument("--requests", type=int, default=1000, help="serving workload: number of structures")
     ap.add_argument("--rate", type=float, default=50.0, help="serving workload: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving workload: concurrent structures")
