@@ -98,8 +98,6 @@ struct PatternData {
   DBuf<int64_t> d_rowptr;
   DBuf<int> d_col, d_newidx, zp;
   DBuf<double> d_val, L, diag0, S64, N, Nb, Dinv, LS, XS, DinvS, Sdag, Nwork;
-  DBuf<double> Kplus;          // dense K^+ (npad x npad, symmetric) for small patterns, else empty
-  bool has_kplus = false;
   DBuf<int> zpS, d_zpiv;
   std::vector<int> h_zp;
   int* h_zp_pinned = nullptr;
@@ -120,11 +118,8 @@ struct PatternUse {
   std::vector<int> occs;       // occurrences of this pattern (ids), q = position
   DBuf<int> d_occs;
   DBuf<double> F;              // npad x n_occ loads (pattern frame, new ordering)
-  DBuf<double> U, U2;          // npad x n_occ work (local solves)
+  DBuf<double> U;              // npad x n_occ work (local solves)
 };
-
-// Patterns up to this padded size keep a dense K^+ (the solves of d and of the recovery become one product).
-constexpr int KPLUS_MAX = 2048;
 
 struct OccData {
   int pattern = 0;
@@ -172,6 +167,7 @@ struct fetirp_ctx_s {
   DBuf<double> lam, r, t1, W, Q, Zr, Whist, Qhist, C, eta, wr, T, alpha, rr_part, Xc, Ac, gram_part, V1, V2;
   DBuf<float> Whist32, Qhist32;   // direction history of the low-precision inner solves
   DBuf<double> tu_part;           // split partials of the history update
+  DBuf<unsigned> tu_tickets;      // per row tile: CTAs of the history update that have stored their partial
   DBuf<double> eta_part;          // row-chunk partials of eta and W^T r
   DBuf<int> n_kept;
   DBuf<double> Y64, Z64;
@@ -422,16 +418,6 @@ void factor_stage_b(PatternData& P, cudaStream_t s) {
     gemm_f64(nb, kd, kd, 1.0, E, kd, 1, D, kd, 1, 0.0, A, kd, 1, s);            // A <- E D
     gemm_f64(nb, nb, kd, 1.0, A, kd, 1, E, 1, kd, 1.0, P.Sdag.p, nb, 1, s);     // + E D E^T
     Sdag = P.Sdag.p;
-  }
-  if (npad <= KPLUS_MAX) {   // K^+ = X^T X with X = L^{-1} (zero-pivot rows of X are 0)
-    P.XS.ensure((size_t)npad * npad);
-    FETIRP_CUDA(cudaMemsetAsync(P.XS.p, 0, sizeof(double) * (size_t)npad * npad, s));
-    k_set_diag<<<ceil_div(npad, 128), 128, 0, s>>>(P.XS.p, npad, 0, npad, 1.0);
-    FETIRP_LAUNCH_CHECK();
-    tri_solve(P.L.p, npad, P.plan, P.zp.p, P.XS.p, npad, npad, false, s, P.Dinv.p);
-    P.Kplus.ensure((size_t)npad * npad);
-    gemm_f64(npad, npad, npad, 1.0, P.XS.p, npad, 1, P.XS.p, 1, npad, 0.0, P.Kplus.p, npad, 1, s);
-    P.has_kplus = true;
   }
   P.S32.ensure((size_t)nb * nb);
   const size_t nn = (size_t)nb * nb;
@@ -697,7 +683,6 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
     }
     Us.F.upload(F, s);
     Us.U.ensure((size_t)P.npad * std::max(no, 1));
-    if (P.has_kplus) Us.U2.ensure((size_t)P.npad * std::max(no, 1));
     Us.d_occs.upload(Us.occs, s);
   }
   // coarse problem: G^T G (FP64), its inverse, e, lambda_0 (projector paragraph)
@@ -740,21 +725,16 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
     PatternUse& Us = ctx->use[p];
     const int no = (int)Us.occs.size();
     if (no > 0) {
-      if (P.has_kplus) {   // boundary rows of K^+ F
-        gemm_f64(P.n_b, no, P.npad, 1.0, P.Kplus.p + P.n_i, 1, P.npad, Us.F.p, 1, P.npad, 0.0, Us.U.p + P.n_i, 1,
-                 P.npad, s);
-      } else {
-        FETIRP_CUDA(cudaMemcpyAsync(Us.U.p, Us.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, s));
-        tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, s, P.Dinv.p);
-        tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, s, P.Dinv.p);
-      }
+      FETIRP_CUDA(cudaMemcpyAsync(Us.U.p, Us.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, s));
+      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, s, P.Dinv.p);
+      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, s, P.Dinv.p);
     }
     V.base[p] = Us.U.p; V.ld[p] = P.npad; V.off[p] = P.n_i;
   }
   scatter<double>(L, V, 1, 0.0, ctx->d.p, s);
   axpy_f64(nl, -1.0, ctx->c.p, ctx->d.p, s);
   // work buffers
-  ctx->rr_blocks = std::max(1, std::min(152, ceil_div(nl, 8)));
+  ctx->rr_blocks = std::max(1, std::min(1024, ceil_div(nl, 32)));   // <= the pinned read-back size
   ctx->rr_part.ensure(ctx->rr_blocks);
   ctx->lam.ensure(nl); ctx->r.ensure(nl); ctx->t1.ensure(nl);
   ctx->W.ensure((size_t)nl * k); ctx->Q.ensure((size_t)nl * k); ctx->Zr.ensure((size_t)nl * k);
@@ -773,6 +753,8 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
 }
 
 // ----------------------------------------------------------------------------------------- operators
+// V <- P V = V - G (G^T G)^{-1} G^T V (Eq. 4), FP64 throughout: with the rigid modes of elasticity G^T G is
+// ill-conditioned enough that FP32 products leave G-components that make the inner operator nonsymmetric.
 void project(fetirp_ctx ctx, double* V, int k) {
   if (ctx->n_G == 0) return;
   cudaStream_t s = ctx->stream;
@@ -963,7 +945,7 @@ void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
   project(ctx, ctx->Zr.p, k);
   {
     PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 0.0, 0.0);
-    tall_update<TH>(nl, (int)cap, d_cols, k, Wh, cap, ctx->C.p, -1.0, ctx->Zr.p, ctx->tu_part, s);
+    tall_update<TH>(nl, (int)cap, d_cols, k, Wh, cap, ctx->C.p, -1.0, ctx->Zr.p, ctx->tu_part, ctx->tu_tickets, s);
   }
   apply_F(ctx, ctx->Zr.p, ctx->Q.p, k, prec, false, true);   // P~ = P^T F W (Table 1 line 5.1)
   {
@@ -1085,8 +1067,8 @@ double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, His
     }
     {
       PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 4.0 * nl * a, 2.0 * es * nl * a + 32.0 * nl);
-      tall_update<TH>(nl, a, nullptr, 1, Wh, cap, ctx->C.p, 1.0, ctx->lam.p, ctx->tu_part, s);
-      tall_update<TH>(nl, a, nullptr, 1, Qh, cap, ctx->C.p, -1.0, ctx->r.p, ctx->tu_part, s);
+      tall_update<TH>(nl, a, nullptr, 1, Wh, cap, ctx->C.p, 1.0, ctx->lam.p, ctx->tu_part, ctx->tu_tickets, s);
+      tall_update<TH>(nl, a, nullptr, 1, Qh, cap, ctx->C.p, -1.0, ctx->r.p, ctx->tu_part, ctx->tu_tickets, s);
     }
     rnorm = norm2(ctx, ctx->r.p, nl);
   }
@@ -1160,13 +1142,8 @@ void recover(fetirp_ctx ctx, double* d_u_out) {
     const int no = (int)Us.occs.size();
     if (no == 0) continue;
     double* Usol = Us.U.p;
-    if (P.has_kplus) {
-      gemm_f64(P.npad, no, P.npad, 1.0, P.Kplus.p, 1, P.npad, Us.U.p, 1, P.npad, 0.0, Us.U2.p, 1, P.npad, s);
-      Usol = Us.U2.p;
-    } else {
-      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, s, P.Dinv.p);
-      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, s, P.Dinv.p);
-    }
+    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, s, P.Dinv.p);
+    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, s, P.Dinv.p);
     if (P.kdim > 0 && ctx->n_G > 0)
       gemm_f64(P.npad, no, P.kdim, -1.0, P.N.p, 1, P.npad, ctx->Ac.p + ctx->pofs[p], 1, P.kdim, 1.0, Usol, 1,
                P.npad, s);
@@ -1204,7 +1181,7 @@ void ensure_history(fetirp_ctx ctx) {
   }
   if (cap != ctx->hist_cap && ctx->gc.exec) { cudaGraphExecDestroy(ctx->gc.exec); ctx->gc.exec = nullptr; }
   ctx->hist_cap = cap;
-  const void* before[4] = {ctx->C.p, ctx->gram_part.p, ctx->Whist32.p, ctx->tu_part.p};
+  const void* before[5] = {ctx->C.p, ctx->gram_part.p, ctx->Whist32.p, ctx->tu_part.p, ctx->tu_tickets.p};
   ctx->C.ensure((size_t)cap * k);
   // gram partials: the largest product is (cap x k) over nl rows
   const int ta = ceil_div(cap, 64), tb = ceil_div(k, 64);
@@ -1213,12 +1190,15 @@ void ensure_history(fetirp_ctx ctx) {
   const int gs_chunks = std::max(1, ceil_div(ctx->max_group_rows, 128));
   ctx->gram_part.ensure(std::max<size_t>(std::max<size_t>((size_t)(chunks + 1) * cap * k, (size_t)304 * 64 * 64),
                                          (size_t)gs_chunks * cap * k));
+  ctx->tu_part.ensure((size_t)tall_update_splits(nl, (int)cap) * nl * k);
   {
     const int tiles = ceil_div(nl, 64);
-    const int splits = std::max(1, std::min(std::max(1, 304 / tiles), ceil_div(cap, 32)));
-    ctx->tu_part.ensure((size_t)splits * nl * 64);
+    if (ctx->tu_tickets.n < (size_t)tiles) {
+      ctx->tu_tickets.alloc(tiles);
+      FETIRP_CUDA(cudaMemsetAsync(ctx->tu_tickets.p, 0, sizeof(unsigned) * tiles, ctx->stream));
+    }
   }
-  const void* after[4] = {ctx->C.p, ctx->gram_part.p, ctx->Whist32.p, ctx->tu_part.p};
+  const void* after[5] = {ctx->C.p, ctx->gram_part.p, ctx->Whist32.p, ctx->tu_part.p, ctx->tu_tickets.p};
   if (ctx->gc.exec && std::memcmp(before, after, sizeof(before)) != 0) {
     cudaGraphExecDestroy(ctx->gc.exec);
     ctx->gc.exec = nullptr;

@@ -66,20 +66,23 @@ __global__ void __launch_bounds__(256) k_potrf_tile(double* A, int npad, int k, 
     a[r][c] = T[(size_t)c * npad + r];
   }
   __syncthreads();
+  __shared__ double s_l, s_inv;
+  __shared__ int s_zero;
   for (int j = 0; j < TILE; ++j) {
     const int gj = k * TILE + j;
-    const double d = a[j][j];
-    const bool zero = !(d > tol * diag0[gj]);   // also catches NaN and negative roundoff
-    __syncthreads();
-    if (zero) {
-      for (int r = j + tid; r < TILE; r += 256) a[r][j] = 0.0;
-      if (tid == 0) zp[gj] = 1;
-    } else {
-      const double l = sqrt(d);
-      const double inv = 1.0 / l;
-      for (int r = j + tid; r < TILE; r += 256) a[r][j] = (r == j) ? l : a[r][j] * inv;
-      if (tid == 0) zp[gj] = 0;
+    if (tid == 0) {   // the pivot's square root and reciprocal once (FP64 divide and sqrt are costly)
+      const double d = a[j][j];
+      const bool zero = !(d > tol * diag0[gj]);   // also catches NaN and negative roundoff
+      s_zero = zero ? 1 : 0;
+      zp[gj] = zero ? 1 : 0;
+      const double l = zero ? 0.0 : sqrt(d);
+      s_l = l;
+      s_inv = zero ? 0.0 : 1.0 / l;
     }
+    __syncthreads();
+    const bool zero = s_zero != 0;
+    const double l = s_l, inv = s_inv;
+    for (int r = j + tid; r < TILE; r += 256) a[r][j] = zero ? 0.0 : ((r == j) ? l : a[r][j] * inv);
     __syncthreads();
     const int w = TILE - 1 - j;        // trailing columns j+1 .. TILE-1, rows >= column
     for (int idx = tid; idx < w * TILE; idx += 256) {
@@ -94,72 +97,82 @@ __global__ void __launch_bounds__(256) k_potrf_tile(double* A, int npad, int k, 
   }
 }
 
-// For step k: tiles (I, k), I in rows[0..cnt): L_Ik = A_Ik L_kk^{-T} (zero-pivot columns -> 0).
+// For step k: tiles (I, k), I in rows[0..cnt): L_Ik = A_Ik L_kk^{-T} (zero-pivot columns -> 0).  The rows of
+// a tile are independent, so grid.y splits each tile into four 16-row blocks (more SMs on the FP64 work).
+constexpr int TR_ROWS = 16;
 __global__ void __launch_bounds__(256) k_trsm_tiles(double* A, int npad, int k, const int* rows, const int* zp) {
   __shared__ double l[TILE][TILE + 1];
-  __shared__ double x[TILE][TILE + 1];
+  __shared__ double x[TR_ROWS][TILE + 1];
+  __shared__ double rinv[TILE];
   const int tid = threadIdx.x;
   const int I = rows[blockIdx.x];
+  const int rb = blockIdx.y * TR_ROWS;
   const double* D = A + (size_t)k * TILE * npad + (size_t)k * TILE;
-  double* X = A + (size_t)k * TILE * npad + (size_t)I * TILE;
+  double* X = A + (size_t)k * TILE * npad + (size_t)I * TILE + rb;
   for (int idx = tid; idx < TILE * TILE; idx += 256) {
     int r = idx % TILE, c = idx / TILE;
     l[r][c] = D[(size_t)c * npad + r];
+  }
+  for (int idx = tid; idx < TR_ROWS * TILE; idx += 256) {
+    int r = idx % TR_ROWS, c = idx / TR_ROWS;
     x[r][c] = X[(size_t)c * npad + r];
   }
   __syncthreads();
+  if (tid < TILE) rinv[tid] = zp[k * TILE + tid] != 0 ? 0.0 : 1.0 / l[tid][tid];
+  __syncthreads();
   for (int j = 0; j < TILE; ++j) {
-    const bool zero = zp[k * TILE + j] != 0;
-    if (tid < TILE) x[tid][j] = zero ? 0.0 : x[tid][j] / l[j][j];
+    if (tid < TR_ROWS) x[tid][j] *= rinv[j];
     __syncthreads();
     const int w = TILE - 1 - j;
-    for (int idx = tid; idx < w * TILE; idx += 256) {
-      int c = j + 1 + idx / TILE, r = idx % TILE;
+    for (int idx = tid; idx < w * TR_ROWS; idx += 256) {
+      int c = j + 1 + idx / TR_ROWS, r = idx % TR_ROWS;
       x[r][c] -= x[r][j] * l[c][j];
     }
     __syncthreads();
   }
-  for (int idx = tid; idx < TILE * TILE; idx += 256) {
-    int r = idx % TILE, c = idx / TILE;
+  for (int idx = tid; idx < TR_ROWS * TILE; idx += 256) {
+    int r = idx % TR_ROWS, c = idx / TR_ROWS;
     X[(size_t)c * npad + r] = x[r][c];
   }
 }
 
-// For step k: A_IJ -= L_Ik L_Jk^T for each pair (I, J).  64x64 output per CTA, 4x4 per thread.
+// For step k: A_IJ -= L_Ik L_Jk^T for each pair (I, J).  grid.y: the four 32 x 32 quadrants of the output
+// tile (2 x 2 per thread), the strictly upper quadrant of a diagonal tile skipped (never read).
 __global__ void __launch_bounds__(256) k_update_pairs(double* A, int npad, int k, const int2* pairs) {
-  __shared__ double sa[16][TILE + 1];   // [kk][row]
-  __shared__ double sb[16][TILE + 1];
+  __shared__ double sa[16][33];   // [kk][row]
+  __shared__ double sb[16][33];
   const int tid = threadIdx.x;
   const int2 pr = pairs[blockIdx.x];
   const int I = pr.x, J = pr.y;
-  const double* LI = A + (size_t)k * TILE * npad + (size_t)I * TILE;
-  const double* LJ = A + (size_t)k * TILE * npad + (size_t)J * TILE;
-  const int tx = tid % 16, ty = tid / 16;     // rows ty*4.., cols tx*4..
-  double acc[4][4] = {};
+  const int qr = (blockIdx.y & 1) * 32, qc = (blockIdx.y >> 1) * 32;
+  if (I == J && qr < qc) return;
+  const double* LI = A + (size_t)k * TILE * npad + (size_t)I * TILE + qr;
+  const double* LJ = A + (size_t)k * TILE * npad + (size_t)J * TILE + qc;
+  const int tx = tid % 16, ty = tid / 16;     // rows ty*2.., cols tx*2..
+  double acc[2][2] = {};
   for (int kk0 = 0; kk0 < TILE; kk0 += 16) {
-    for (int idx = tid; idx < 16 * TILE; idx += 256) {
-      int r = idx % TILE, kk = idx / TILE;
+    for (int idx = tid; idx < 16 * 32; idx += 256) {
+      int r = idx % 32, kk = idx / 32;
       sa[kk][r] = LI[(size_t)(kk0 + kk) * npad + r];
       sb[kk][r] = LJ[(size_t)(kk0 + kk) * npad + r];
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      double av[4], bv[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) { av[q] = sa[kk][ty * 4 + q]; bv[q] = sb[kk][tx * 4 + q]; }
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = fma(av[p], bv[q], acc[p][q]);
+      const double a0 = sa[kk][ty * 2], a1 = sa[kk][ty * 2 + 1];
+      const double b0 = sb[kk][tx * 2], b1 = sb[kk][tx * 2 + 1];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
     }
     __syncthreads();
   }
-  double* C = A + (size_t)J * TILE * npad + (size_t)I * TILE;
+  double* C = A + (size_t)(J * TILE + qc) * npad + (size_t)I * TILE + qr;
 #pragma unroll
-  for (int p = 0; p < 4; ++p)
+  for (int p = 0; p < 2; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) C[(size_t)(tx * 4 + q) * npad + ty * 4 + p] -= acc[p][q];
+    for (int q = 0; q < 2; ++q) C[(size_t)(tx * 2 + q) * npad + ty * 2 + p] -= acc[p][q];
 }
 
 // Inverse of every diagonal tile, all tiles in parallel (one CTA per tile): Dinv_J = L_JJ^{-1} by forward
@@ -177,9 +190,11 @@ __global__ void __launch_bounds__(256) k_tile_inverse(const double* L, int npad,
     x[r][c] = (r == c) ? 1.0 : 0.0;
   }
   __syncthreads();
+  __shared__ double rinv[TILE];
+  if (tid < TILE) rinv[tid] = zp[J * TILE + tid] != 0 ? 0.0 : 1.0 / l[tid][tid];
+  __syncthreads();
   for (int j = 0; j < TILE; ++j) {
-    const bool zero = zp[J * TILE + j] != 0;
-    if (tid < TILE) x[j][tid] = zero ? 0.0 : x[j][tid] / l[j][j];
+    if (tid < TILE) x[j][tid] *= rinv[j];
     __syncthreads();
     for (int idx = tid; idx < (TILE - 1 - j) * TILE; idx += 256) {
       int r = j + 1 + idx / TILE, c = idx % TILE;
@@ -194,37 +209,40 @@ __global__ void __launch_bounds__(256) k_tile_inverse(const double* L, int npad,
   }
 }
 
-// X_J <- Dinv_J X_J (forward) or Dinv_J^T X_J (backward) for a chunk of 16 right-hand sides (4 rows x 1 rhs
-// per thread), so that narrow solves spread over many SMs.
+// X_J <- Dinv_J X_J (forward) or Dinv_J^T X_J (backward) for a chunk of RC right-hand sides (64 RC / 256
+// outputs per thread).  Narrow solves use RC = 4 so that their FP64 work spreads over many SMs; every CTA owns
+// its right-hand sides, so the in-place update is race-free.
+template <int RC>
 __global__ void __launch_bounds__(256) k_tri_diag_inv(const double* __restrict__ Dinv, int J, double* X, int ldx,
                                                       int nrhs, int trans) {
+  constexpr int RPT = TILE * RC / 256, RS = 256 / RC;
   __shared__ double a[TILE][TILE + 1];   // a[r][c] = op(Dinv_J)(r, c)
-  __shared__ double x[TILE][17];         // x[row][rhs]
+  __shared__ double x[TILE][RC + 1];     // x[row][rhs]
   const int tid = threadIdx.x;
-  const int c0 = blockIdx.x * 16;
+  const int c0 = blockIdx.x * RC;
   const double* D = Dinv + (size_t)J * TILE * TILE;
   for (int idx = tid; idx < TILE * TILE; idx += 256) {
     int r = idx % TILE, c = idx / TILE;
     const double v = D[(size_t)c * TILE + r];   // Dinv(r, c)
     if (trans) a[c][r] = v; else a[r][c] = v;
   }
-  for (int idx = tid; idx < TILE * 16; idx += 256) {
+  for (int idx = tid; idx < TILE * RC; idx += 256) {
     int r = idx % TILE, c = idx / TILE;
     x[r][c] = (c0 + c < nrhs) ? X[(size_t)(c0 + c) * ldx + (size_t)J * TILE + r] : 0.0;
   }
   __syncthreads();
-  const int tx = tid % 16, ty = tid / 16;   // rhs tx, rows ty*4 .. +3
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int tx = tid % RC, ty = tid / RC;   // rhs tx, rows ty + RS u
+  double acc[RPT] = {};
 #pragma unroll 8
   for (int q = 0; q < TILE; ++q) {
     const double b = x[q][tx];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] = fma(a[ty * 4 + u][q], b, acc[u]);
+    for (int u = 0; u < RPT; ++u) acc[u] = fma(a[ty + RS * u][q], b, acc[u]);
   }
   const int c = c0 + tx;
   if (c < nrhs) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) X[(size_t)c * ldx + (size_t)J * TILE + ty * 4 + u] = acc[u];
+    for (int u = 0; u < RPT; ++u) X[(size_t)c * ldx + (size_t)J * TILE + ty + RS * u] = acc[u];
   }
 }
 
@@ -242,10 +260,12 @@ __global__ void __launch_bounds__(256) k_tri_diag(const double* L, int npad, int
     x[r][c] = (c0 + c < nrhs) ? X[(size_t)(c0 + c) * ldx + (size_t)J * TILE + r] : 0.0;
   }
   __syncthreads();
+  __shared__ double rinv[TILE];
+  if (tid < TILE) rinv[tid] = zp[J * TILE + tid] != 0 ? 0.0 : 1.0 / l[tid][tid];
+  __syncthreads();
   if (!trans) {
     for (int j = 0; j < TILE; ++j) {
-      const bool zero = zp[J * TILE + j] != 0;
-      if (tid < TILE) x[j][tid] = zero ? 0.0 : x[j][tid] / l[j][j];
+      if (tid < TILE) x[j][tid] *= rinv[j];
       __syncthreads();
       for (int idx = tid; idx < (TILE - 1 - j) * TILE; idx += 256) {
         int r = j + 1 + idx / TILE, c = idx % TILE;
@@ -255,8 +275,7 @@ __global__ void __launch_bounds__(256) k_tri_diag(const double* L, int npad, int
     }
   } else {
     for (int j = TILE - 1; j >= 0; --j) {
-      const bool zero = zp[J * TILE + j] != 0;
-      if (tid < TILE) x[j][tid] = zero ? 0.0 : x[j][tid] / l[j][j];
+      if (tid < TILE) x[j][tid] *= rinv[j];
       __syncthreads();
       for (int idx = tid; idx < j * TILE; idx += 256) {
         int r = idx / TILE, c = idx % TILE;   // rows r < j
@@ -272,42 +291,38 @@ __global__ void __launch_bounds__(256) k_tri_diag(const double* L, int npad, int
 }
 
 // After solving tile J: X_I -= L_IJ X_J (forward, I in list) or X_I -= L_JI^T X_J (backward, I in list).
-// grid (list count, chunks of 16 right-hand sides): 64 rows x 16 rhs per CTA, 4 rows x 1 rhs per thread, so
-// that narrow solves (one column per occurrence) still spread their FP64 work over many SMs.
+// grid (list count, chunks of 16 right-hand sides, four 16-row blocks): 16 rows x 16 rhs per CTA, one output
+// per thread, so that narrow solves (one column per occurrence) spread their FP64 work over many SMs.
 constexpr int TU_RHS = 16;
 __global__ void __launch_bounds__(256) k_tri_update(const double* L, int npad, int J, const int* list, double* X,
                                                     int ldx, int nrhs, int trans) {
-  __shared__ double sa[16][TILE + 1];   // [kk][row of output]
+  __shared__ double sa[16][17];        // [kk][row of output]
   __shared__ double sb[16][TU_RHS + 1]; // [kk][rhs]
   const int tid = threadIdx.x;
   const int I = list[blockIdx.x];
   const int c0 = blockIdx.y * TU_RHS;
-  const int tx = tid % 16, ty = tid / 16;   // rhs tx, rows ty*4 .. +3
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int rb = blockIdx.z * 16;
+  const int tx = tid % 16, ty = tid / 16;   // rhs tx, row ty
+  double acc = 0.0;
   for (int kk0 = 0; kk0 < TILE; kk0 += 16) {
-    for (int idx = tid; idx < 16 * TILE; idx += 256) {
-      const int r = idx % TILE, kk = idx / TILE;
-      if (!trans) sa[kk][r] = L[(size_t)(J * TILE + kk0 + kk) * npad + I * TILE + r];
-      else sa[kk][r] = L[(size_t)(I * TILE + r) * npad + J * TILE + kk0 + kk];
+    if (!trans) {
+      const int r = tid % 16, kk = tid / 16;
+      sa[kk][r] = L[(size_t)(J * TILE + kk0 + kk) * npad + I * TILE + rb + r];
+    } else {
+      const int kk = tid % 16, r = tid / 16;
+      sa[kk][r] = L[(size_t)(I * TILE + rb + r) * npad + J * TILE + kk0 + kk];
     }
     {
-      const int k2 = tid / 16, c = tid % 16;
+      const int k2 = tid % 16, c = tid / 16;
       sb[k2][c] = (c0 + c < nrhs) ? X[(size_t)(c0 + c) * ldx + (size_t)J * TILE + kk0 + k2] : 0.0;
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      const double b = sb[kk][tx];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u] = fma(sa[kk][ty * 4 + u], b, acc[u]);
-    }
+    for (int kk = 0; kk < 16; ++kk) acc = fma(sa[kk][ty], sb[kk][tx], acc);
     __syncthreads();
   }
   const int c = c0 + tx;
-  if (c < nrhs) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) X[(size_t)c * ldx + (size_t)I * TILE + ty * 4 + u] -= acc[u];
-  }
+  if (c < nrhs) X[(size_t)c * ldx + (size_t)I * TILE + rb + ty] -= acc;
 }
 
 // Generic strided GEMM, 32x32 output tile per CTA, 2x2 per thread (small FP64 products: more CTAs).
@@ -425,12 +440,12 @@ void chol_tiles(double* A, int npad, const TilePlan& plan, const double* diag0, 
     FETIRP_LAUNCH_CHECK();
     int nr = plan.col_off[k + 1] - plan.col_off[k];
     if (nr > 0) {
-      k_trsm_tiles<<<nr, 256, 0, s>>>(A, npad, k, plan.d_col_rows.p + plan.col_off[k], zp);
+      k_trsm_tiles<<<dim3(nr, TILE / TR_ROWS), 256, 0, s>>>(A, npad, k, plan.d_col_rows.p + plan.col_off[k], zp);
       FETIRP_LAUNCH_CHECK();
     }
     int np = plan.pair_off[k + 1] - plan.pair_off[k];
     if (np > 0) {
-      k_update_pairs<<<np, 256, 0, s>>>(A, npad, k, plan.d_pairs.p + plan.pair_off[k]);
+      k_update_pairs<<<dim3(np, 4), 256, 0, s>>>(A, npad, k, plan.d_pairs.p + plan.pair_off[k]);
       FETIRP_LAUNCH_CHECK();
     }
   }
@@ -447,7 +462,8 @@ void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, d
   if (nrhs <= 0) return;
   const int chunks = ceil_div(nrhs, TILE);
   auto diag = [&](int J, int tr) {
-    if (Dinv) k_tri_diag_inv<<<ceil_div(nrhs, 16), 256, 0, s>>>(Dinv, J, X, ldx, nrhs, tr);
+    if (Dinv && ceil_div(nrhs, 16) < 152) k_tri_diag_inv<4><<<ceil_div(nrhs, 4), 256, 0, s>>>(Dinv, J, X, ldx, nrhs, tr);
+    else if (Dinv) k_tri_diag_inv<16><<<ceil_div(nrhs, 16), 256, 0, s>>>(Dinv, J, X, ldx, nrhs, tr);
     else k_tri_diag<<<chunks, 256, 0, s>>>(L, npad, J, zp, X, ldx, nrhs, tr);
   };
   if (!trans) {
@@ -456,7 +472,7 @@ void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, d
       FETIRP_LAUNCH_CHECK();
       int nr = plan.col_off[J + 1] - plan.col_off[J];
       if (nr > 0) {
-        k_tri_update<<<dim3(nr, ceil_div(nrhs, TU_RHS)), 256, 0, s>>>(L, npad, J, plan.d_col_rows.p + plan.col_off[J],
+        k_tri_update<<<dim3(nr, ceil_div(nrhs, TU_RHS), TILE / 16), 256, 0, s>>>(L, npad, J, plan.d_col_rows.p + plan.col_off[J],
                                                                       X, ldx, nrhs, 0);
         FETIRP_LAUNCH_CHECK();
       }
@@ -467,7 +483,7 @@ void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, d
       FETIRP_LAUNCH_CHECK();
       int nr = plan.row_off[J + 1] - plan.row_off[J];
       if (nr > 0) {
-        k_tri_update<<<dim3(nr, ceil_div(nrhs, TU_RHS)), 256, 0, s>>>(L, npad, J, plan.d_row_cols.p + plan.row_off[J],
+        k_tri_update<<<dim3(nr, ceil_div(nrhs, TU_RHS), TILE / 16), 256, 0, s>>>(L, npad, J, plan.d_row_cols.p + plan.row_off[J],
                                                                       X, ldx, nrhs, 1);
         FETIRP_LAUNCH_CHECK();
       }

@@ -76,7 +76,7 @@ __global__ void k_g_apply(Layout L, const double* __restrict__ A, int k, double 
     const double* a = A + (size_t)L.occ_gofs[s] * k + g;
     double t = 0.0;
     for (int m = 0; m < kd; ++m) t = fma(Nb[m], a[(size_t)m * k], t);
-    acc = fma((double)sg, t, acc);
+    acc = sg > 0 ? acc + t : acc - t;
   }
   double* o = out + idx;
   *o = (beta == 0.0 ? 0.0 : beta * *o) + alpha * acc;
@@ -199,12 +199,14 @@ void gt_v(const Layout& L, const double* V, int k, double* X, cudaStream_t s) {
   FETIRP_LAUNCH_CHECK();
 }
 
+
 void g_apply(const Layout& L, const double* A, int k, double alpha, double beta, double* out, cudaStream_t s) {
   long long n = (long long)L.n_lambda * k;
   if (n == 0) return;
   k_g_apply<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, A, k, alpha, beta, out);
   FETIRP_LAUNCH_CHECK();
 }
+
 
 void gtg_dense(const Layout& L, const int*, const int*, int n_pairs, const int* pair_s, const int* pair_t,
                double* GtG, cudaStream_t s) {

@@ -112,15 +112,48 @@ __global__ void __launch_bounds__(512) k_normalise(int k, const double* __restri
   __shared__ int done[64];
   __shared__ double rhs[64];
   __shared__ int s_r, s_p;
-  __shared__ double s_dmax;
+  __shared__ double s_dmax, s_ipp, s_ilp;   // pivot reciprocal and its square root, computed once per step
+  __shared__ double dinv[64];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nout = k * (k + 1);
   double* ext = &Lc[0][0];   // [eta | wr] (k (k+1) <= 64 * 65 entries) lives in Lc's storage until Lc is needed
-  for (int o = warp; o < nout; o += blockDim.x / 32) {
-    double v = 0.0;
-    for (int c = lane; c < chunks; c += 32) v += ext_partial[(size_t)c * nout + o];
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) ext[o] = v;
+  // Sum of the chunk partials.  Every thread takes one output and a strided subset of the chunks (loads
+  // coalesced over the outputs and independent of one another), then the subsets are added in a fixed order.
+  const int groups = max(1, (int)blockDim.x / nout);
+  if (groups == 1) {
+    for (int o = tid; o < nout; o += blockDim.x) {
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      int c = 0;
+      for (; c + 3 < chunks; c += 4) {
+        v0 += ext_partial[(size_t)c * nout + o];
+        v1 += ext_partial[(size_t)(c + 1) * nout + o];
+        v2 += ext_partial[(size_t)(c + 2) * nout + o];
+        v3 += ext_partial[(size_t)(c + 3) * nout + o];
+      }
+      for (; c < chunks; ++c) v0 += ext_partial[(size_t)c * nout + o];
+      ext[o] = (v0 + v1) + (v2 + v3);
+    }
+  } else {
+    double* red = &A[0][0];   // groups * nout <= blockDim.x entries
+    if (tid < groups * nout) {
+      const int o = tid % nout, g = tid / nout;
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      int c = g;
+      for (; c + 3 * groups < chunks; c += 4 * groups) {
+        v0 += ext_partial[(size_t)c * nout + o];
+        v1 += ext_partial[(size_t)(c + groups) * nout + o];
+        v2 += ext_partial[(size_t)(c + 2 * groups) * nout + o];
+        v3 += ext_partial[(size_t)(c + 3 * groups) * nout + o];
+      }
+      for (; c < chunks; c += groups) v0 += ext_partial[(size_t)c * nout + o];
+      red[g * nout + o] = (v0 + v1) + (v2 + v3);
+    }
+    __syncthreads();
+    for (int o = tid; o < nout; o += blockDim.x) {
+      double v = 0.0;
+      for (int g = 0; g < groups; ++g) v += red[g * nout + o];
+      ext[o] = v;
+    }
   }
   __syncthreads();
   for (int idx = tid; idx < k * k; idx += blockDim.x) {
@@ -151,7 +184,11 @@ __global__ void __launch_bounds__(512) k_normalise(int k, const double* __restri
     }
     if (lane == 0) {
       s_p = (bi >= 0 && best > trunc * s_dmax && s_dmax > 0.0) ? bi : -1;
-      if (s_p >= 0) { done[bi] = 1; piv[0] = bi; s_r = 1; }
+      if (s_p >= 0) {
+        done[bi] = 1; piv[0] = bi; s_r = 1;
+        s_ipp = 1.0 / best;
+        s_ilp = sqrt(s_ipp);
+      }
     }
   }
   __syncthreads();
@@ -159,8 +196,7 @@ __global__ void __launch_bounds__(512) k_normalise(int k, const double* __restri
     const int p = s_p;
     if (p < 0) break;
     // column `step` of the factor and the trailing update (A[.][p] is not modified in this phase)
-    const double inv_pp = 1.0 / A[p][p];
-    const double inv_lp = sqrt(inv_pp);
+    const double inv_pp = s_ipp, inv_lp = s_ilp;
     for (int i = tid; i < k; i += blockDim.x) {
       if (i == p) Lc[i][step] = A[p][p] * inv_lp;
       else if (!done[i]) Lc[i][step] = A[i][p] * inv_lp;
@@ -186,7 +222,11 @@ __global__ void __launch_bounds__(512) k_normalise(int k, const double* __restri
       }
       if (lane == 0) {
         s_p = (step + 1 < k && bi >= 0 && best > trunc * s_dmax) ? bi : -1;
-        if (s_p >= 0) { done[bi] = 1; piv[step + 1] = bi; s_r = step + 2; }
+        if (s_p >= 0) {
+          done[bi] = 1; piv[step + 1] = bi; s_r = step + 2;
+          s_ipp = 1.0 / best;
+          s_ilp = sqrt(s_ipp);
+        }
       }
     }
     __syncthreads();
@@ -196,8 +236,10 @@ __global__ void __launch_bounds__(512) k_normalise(int k, const double* __restri
   // final after dividing by M[l][l], and rows below are updated
   for (int idx = tid; idx < 64 * 64; idx += blockDim.x) A[idx / 64][idx % 64] = (idx / 64 == idx % 64) ? 1.0 : 0.0;
   __syncthreads();
+  for (int l = tid; l < r; l += blockDim.x) dinv[l] = 1.0 / Lc[piv[l]][l];
+  __syncthreads();
   for (int l = 0; l < r; ++l) {
-    const double inv = 1.0 / Lc[piv[l]][l];
+    const double inv = dinv[l];
     for (int c = tid; c <= l; c += blockDim.x) A[l][c] *= inv;
     __syncthreads();
     for (int idx = tid; idx < (r - 1 - l) * (l + 1); idx += blockDim.x) {
@@ -224,7 +266,9 @@ __global__ void __launch_bounds__(512) k_normalise(int k, const double* __restri
 }
 
 // Wn = W T, Qn = Q T, lambda += W (T alpha), r -= Q (T alpha); per-CTA partial sums of the new r^2.
-// One warp per row (grid-stride), k <= 64.  The history (Wn, Qn) is stored in TH.
+// A warp takes 32 / kp rows at once (kp = k rounded up to a power of two), one lane per column: every element
+// of W and Q is loaded and converted once, and row j of the block is broadcast by shuffles.  For k > 32 a lane
+// holds two columns.  The history (Wn, Qn) is stored in TH; T is rounded to TH once per CTA.
 template <typename TH>
 __global__ void __launch_bounds__(256) k_update(int n, int k, const double* __restrict__ W,
                                                 const double* __restrict__ Q, const double* __restrict__ T,
@@ -233,51 +277,71 @@ __global__ void __launch_bounds__(256) k_update(int n, int k, const double* __re
                                                 double* __restrict__ lam,
                                                 double* __restrict__ r, double* __restrict__ rr_partial,
                                                 AdvanceArgs adv) {
-  __shared__ double sT[64][65];
+  __shared__ TH sT[64][65];
   __shared__ double beta[64];
   __shared__ double warp_rr[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int idx = tid; idx < k * k; idx += blockDim.x) sT[idx / k][idx % k] = T[idx];
-  __syncthreads();
+  for (int idx = tid; idx < k * k; idx += blockDim.x) sT[idx / k][idx % k] = (TH)T[idx];
   if (tid < k) {
     double v = 0.0;
-    for (int c = 0; c < k; ++c) v += sT[tid][c] * alpha[c];
+    for (int c = 0; c < k; ++c) v = fma(T[(size_t)tid * k + c], alpha[c], v);
     beta[tid] = v;
   }
   __syncthreads();
+  int kp = 1;
+  while (kp < k) kp <<= 1;
+  const int rows_w = kp >= 32 ? 1 : 32 / kp;          // rows per warp pass
+  const int seg = kp >= 32 ? 32 : kp;                  // lanes per row
+  const int sub = lane / seg, c0 = lane % seg;
+  const bool two = k > 32;                             // second column c0 + 32
+  const long long off = d_off ? (long long)*d_off : 0;
   double rr = 0.0;
-  const int warps_total = gridDim.x * 8;
-  if (d_off) {
-    Wn += *d_off;
-    Qn += *d_off;
-  }
-  for (int row = blockIdx.x * 8 + warp; row < n; row += warps_total) {
-    const double* w = W + (size_t)row * k;
-    const double* q = Q + (size_t)row * k;
-    double dl = 0.0, dr = 0.0;
-    for (int c = lane; c < k; c += 32) {
-      TH wn = TH(0), qn = TH(0);
-      for (int j = 0; j < k; ++j) {
-        wn = fma((TH)w[j], (TH)sT[j][c], wn);
-        qn = fma((TH)q[j], (TH)sT[j][c], qn);
+  const long long stride = (long long)gridDim.x * 8 * rows_w;
+  for (long long base = ((long long)blockIdx.x * 8 + warp) * rows_w; base < n; base += stride) {
+    const long long row = base + sub;
+    const bool ok = row < n;
+    const bool v0 = ok && c0 < k, v1 = two && ok && c0 + 32 < k;
+    const double w0 = v0 ? W[row * k + c0] : 0.0, q0 = v0 ? Q[row * k + c0] : 0.0;
+    const double w1 = v1 ? W[row * k + c0 + 32] : 0.0, q1 = v1 ? Q[row * k + c0 + 32] : 0.0;
+    const TH w0h = (TH)w0, q0h = (TH)q0, w1h = (TH)w1, q1h = (TH)q1;
+    TH wn0 = TH(0), qn0 = TH(0), wn1 = TH(0), qn1 = TH(0);
+    const int ca = c0 < k ? c0 : 0, cb = c0 + 32 < k ? c0 + 32 : 0;
+    for (int j = 0; j < k; ++j) {
+      const int src = j < 32 ? j : j - 32;
+      const TH wj = __shfl_sync(0xffffffffu, j < 32 ? w0h : w1h, src, seg);
+      const TH qj = __shfl_sync(0xffffffffu, j < 32 ? q0h : q1h, src, seg);
+      wn0 = fma(wj, sT[j][ca], wn0);
+      qn0 = fma(qj, sT[j][ca], qn0);
+      if (two) {
+        wn1 = fma(wj, sT[j][cb], wn1);
+        qn1 = fma(qj, sT[j][cb], qn1);
       }
-      Wn[(size_t)row * ldn + c] = wn;
-      Qn[(size_t)row * ldn + c] = qn;
-      dl = fma(w[c], beta[c], dl);
-      dr = fma(q[c], beta[c], dr);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    if (v0) {
+      Wn[row * ldn + off + c0] = wn0;
+      Qn[row * ldn + off + c0] = qn0;
+    }
+    if (v1) {
+      Wn[row * ldn + off + c0 + 32] = wn1;
+      Qn[row * ldn + off + c0 + 32] = qn1;
+    }
+    double dl = v0 ? w0 * beta[c0] : 0.0, dr = v0 ? q0 * beta[c0] : 0.0;
+    if (v1) {
+      dl = fma(w1, beta[c0 + 32], dl);
+      dr = fma(q1, beta[c0 + 32], dr);
+    }
+    for (int o = seg >> 1; o > 0; o >>= 1) {
       dl += __shfl_xor_sync(0xffffffffu, dl, o);
       dr += __shfl_xor_sync(0xffffffffu, dr, o);
     }
-    if (lane == 0) {
+    if (ok && c0 == 0) {
       lam[row] += dl;
       const double rn = r[row] - dr;
       r[row] = rn;
       rr = fma(rn, rn, rr);
     }
   }
+  for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
   if (lane == 0) warp_rr[warp] = rr;
   __syncthreads();
   if (tid == 0) {
@@ -407,6 +471,7 @@ void small_gemm(int m, int k, const double* A, const double* B, double* C, cudaS
   FETIRP_LAUNCH_CHECK();
 }
 
+
 void normalise(int k, const double* ext_partial, int chunks, double trunc, double* T, double* alpha, int* n_kept,
                cudaStream_t s) {
   if (k > 64) throw Error(1, "block width k > 64 is not supported");
@@ -428,42 +493,62 @@ template void update<float>(int, int, const double*, const double*, const double
                             const int*, long long, double*, double*, double*, int, cudaStream_t, const AdvanceArgs&);
 
 // C[c][g] = sum over the rows of group g: w(row) * r[row] * Qh[row][c]  (= Qh^T S(r), the split multivector
-// S(r) having at most two nonzero groups per row).  Grid (128-column tiles, groups, row chunks): each CTA
-// stages its chunk of (row, w r[row]) in shared memory, each thread owns one column and sums the chunk's rows
-// in order; chunk partials are then added in chunk order (deterministic).
+// S(r) having at most two nonzero groups per row).  Work items (64-column tile, group, 128-row chunk) are
+// taken from the live history count a on the device, so a fixed grid serves every iteration of a captured
+// graph.  Per item the chunk's (row, w r[row]) pairs are staged in shared memory, the 8 warps take every
+// 8th row (a warp reads 64 consecutive history columns of one row), and the warp sums are added in warp
+// order; chunk partials are then added in chunk order (deterministic).
 constexpr int GS_ROWS = 128;   // rows per chunk
+constexpr int GS_COLS = 64;    // history columns per item
+constexpr int GS_GRID = 608;   // 4 CTAs per SM
 template <typename TH>
-__global__ void __launch_bounds__(128) k_gram_split(int a_max, const int* __restrict__ d_a, int k,
+__global__ void __launch_bounds__(256) k_gram_split(int a_max, const int* __restrict__ d_a, int k,
                                                     const TH* __restrict__ Qh, long long ldq,
                                                     const double* __restrict__ r, const int* __restrict__ grp_ptr,
                                                     const int* __restrict__ grp_row, const double* __restrict__ grp_w,
                                                     int chunks, double* __restrict__ partial) {
   __shared__ int srow[GS_ROWS];
   __shared__ double sw[GS_ROWS];
+  __shared__ double red[8][GS_COLS];
   const int a = d_a ? min(*d_a, a_max) : a_max;
-  if ((int)blockIdx.x * 128 >= a) return;
-  const int c = blockIdx.x * 128 + threadIdx.x;
-  const int g = blockIdx.y, ch = blockIdx.z;
-  const int e0 = grp_ptr[g] + ch * GS_ROWS, e1 = min(grp_ptr[g + 1], e0 + GS_ROWS);
-  const int cnt = max(0, e1 - e0);
-  if (threadIdx.x < cnt) {
-    const int row = grp_row[e0 + threadIdx.x];
-    srow[threadIdx.x] = row;
-    sw[threadIdx.x] = grp_w[e0 + threadIdx.x] * r[row];
-  }
-  __syncthreads();
-  if (c >= a) return;
-  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  int i = 0;
-  for (; i + 8 <= cnt; i += 8) {
-    double q[8];
+  if (a <= 0) return;
+  const int ctiles = (a + GS_COLS - 1) / GS_COLS;
+  const int items = ctiles * k * chunks;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int ct = it % ctiles, rest = it / ctiles, g = rest % k, ch = rest / k;
+    const int e0 = grp_ptr[g] + ch * GS_ROWS, e1 = min(grp_ptr[g + 1], e0 + GS_ROWS);
+    const int cnt = max(0, e1 - e0);
+    __syncthreads();   // the previous item's shared-memory reads are done
+    if (tid < cnt) {
+      const int row = grp_row[e0 + tid];
+      srow[tid] = row;
+      sw[tid] = grp_w[e0 + tid] * r[row];
+    }
+    __syncthreads();
+    const int c0 = ct * GS_COLS + lane, c1 = c0 + 32;
+    const bool ok0 = c0 < a, ok1 = c1 < a;
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll 8
+    for (int i = warp; i < cnt; i += 8) {
+      const TH* q = Qh + (size_t)srow[i] * ldq;
+      const double wv = sw[i];
+      const double q0 = ok0 ? (double)q[c0] : 0.0;
+      const double q1 = ok1 ? (double)q[c1] : 0.0;
+      a0 = fma(wv, q0, a0);
+      a1 = fma(wv, q1, a1);
+    }
+    red[warp][lane] = a0;
+    red[warp][lane + 32] = a1;
+    __syncthreads();
+    if (tid < GS_COLS) {
+      const int c = ct * GS_COLS + tid;
+      double v = 0.0;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) q[u] = (double)Qh[(size_t)srow[i + u] * ldq + c];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] = fma(sw[i + u], q[u], acc[u]);
+      for (int w = 0; w < 8; ++w) v += red[w][tid];
+      if (c < a) partial[((size_t)ch * a + c) * k + g] = v;
+    }
   }
-  for (; i < cnt; ++i) acc[0] = fma(sw[i], (double)Qh[(size_t)srow[i] * ldq + c], acc[0]);
-  partial[((size_t)ch * a + c) * k + g] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 }
 
 __global__ void k_reduce_chunks_dyn(int a_max, const int* __restrict__ d_a, int k, int chunks,
@@ -484,8 +569,9 @@ void gram_split(int a_max, const int* d_a, int k, const TH* Qh, long long ldq, c
   if (a_max <= 0) return;
   const int chunks = std::max(1, ceil_div(max_group_rows, GS_ROWS));
   partial.ensure((size_t)chunks * a_max * k);
-  k_gram_split<TH><<<dim3(ceil_div(a_max, 128), k, chunks), 128, 0, s>>>(a_max, d_a, k, Qh, ldq, r, grp_ptr, grp_row,
-                                                                           grp_w, chunks, partial.p);
+  const int items = ceil_div(a_max, GS_COLS) * k * chunks;
+  k_gram_split<TH><<<std::min(items, GS_GRID), 256, 0, s>>>(a_max, d_a, k, Qh, ldq, r, grp_ptr, grp_row, grp_w,
+                                                             chunks, partial.p);
   FETIRP_LAUNCH_CHECK();
   k_reduce_chunks_dyn<<<ceil_div(a_max * k, 256), 256, 0, s>>>(a_max, d_a, k, chunks, partial.p, C);
   FETIRP_LAUNCH_CHECK();
@@ -497,93 +583,154 @@ template void gram_split<float>(int, const int*, int, const float*, long long, c
 
 // W[row][g] += alpha * sum_c Wh[row][c] C[c][g] over a history of `a` columns; products and sums in TH (FP32
 // history: FFMA; FP64 history: DFMA).  Grid (64-row tiles, history splits): each CTA sums its share of the
-// history columns for 64 rows x k columns (256 threads, 4 rows x k/16 columns each) into a partial; a second
-// pass adds the partials in split order and updates W (deterministic).
+// history columns for 64 rows x KP columns (KP = k rounded up to a power of two >= 8), with the next 32-column
+// tile of the history loaded into registers while the current one is used.  With one split the CTA updates W
+// itself; otherwise it stores a partial, and the last CTA of a row tile to finish (atomic ticket, reset by
+// that CTA) adds the partials in split order and updates W (deterministic).
 constexpr int TU_ROWS = 64, TU_CH = 32;
-template <typename TH>
-__global__ void __launch_bounds__(256) k_tall_update_partial(int n, int a_max, const int* __restrict__ d_a, int k,
-                                                             const TH* __restrict__ Wh, long long ldh,
-                                                             const double* __restrict__ C, int splits,
-                                                             TH* __restrict__ part) {
+template <typename TH, int KP>
+__global__ void __launch_bounds__(256) k_tall_update(int n, int a_max, const int* __restrict__ d_a, int k,
+                                                     const TH* __restrict__ Wh, long long ldh,
+                                                     const double* __restrict__ C, int splits, TH* __restrict__ part,
+                                                     unsigned* __restrict__ tickets, double alpha,
+                                                     double* __restrict__ W) {
+  constexpr int TXC = KP < 16 ? KP : 16;           // column threads
+  constexpr int TY = 256 / TXC;                     // row threads
+  constexpr int RPT = TU_ROWS / TY, CPT = KP / TXC;   // rows, columns per thread
+  constexpr int LA = TU_CH * TU_ROWS / 256;         // history elements a thread loads per tile
+  constexpr int LC = (TU_CH * KP + 255) / 256;      // C elements a thread loads per tile
   __shared__ TH sa[TU_CH][TU_ROWS + 1];   // [c][row]
-  __shared__ TH sc[TU_CH][64];            // [c][g]
+  __shared__ TH sc[TU_CH][KP];            // [c][g]
+  __shared__ bool last;
   const int a = d_a ? min(*d_a, a_max) : a_max;
+  if (a <= 0) return;
   const int r0 = blockIdx.x * TU_ROWS;
   const int per = (a + splits - 1) / splits;
-  const int c_begin = blockIdx.y * per, c_end = min(a, c_begin + per);
+  const int c_begin = min(a, (int)blockIdx.y * per), c_end = min(a, c_begin + per);
   const int tid = threadIdx.x;
-  const int ty = tid / 16, tx = tid % 16;       // rows ty*4 .. +3, columns tx, tx+16, tx+32, tx+48
-  TH acc[4][4] = {};
-  for (int c0 = c_begin; c0 < c_end; c0 += TU_CH) {
-    for (int idx = tid; idx < TU_CH * TU_ROWS; idx += 256) {
-      const int cc = idx % TU_CH, rr = idx / TU_CH;
-      sa[cc][rr] = (r0 + rr < n && c0 + cc < c_end) ? Wh[(size_t)(r0 + rr) * ldh + c0 + cc] : TH(0);
+  const int ty = tid / TXC, tx = tid % TXC;
+  TH acc[RPT][CPT] = {};
+  TH pa[LA], pc[LC];
+  auto load = [&](int c0) {
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+      const int idx = tid + 256 * i, cc = idx % TU_CH, rr = idx / TU_CH;
+      pa[i] = (r0 + rr < n && c0 + cc < c_end) ? Wh[(size_t)(r0 + rr) * ldh + c0 + cc] : TH(0);
     }
-    for (int idx = tid; idx < TU_CH * 64; idx += 256) {
-      const int cc = idx / 64, gg = idx % 64;
-      sc[cc][gg] = (c0 + cc < c_end && gg < k) ? (TH)C[(size_t)(c0 + cc) * k + gg] : TH(0);
+#pragma unroll
+    for (int i = 0; i < LC; ++i) {
+      const int idx = tid + 256 * i, cc = idx / KP, gg = idx % KP;
+      pc[i] = (idx < TU_CH * KP && c0 + cc < c_end && gg < k) ? (TH)C[(size_t)(c0 + cc) * k + gg] : TH(0);
+    }
+  };
+  if (c_begin < c_end) load(c_begin);
+  for (int c0 = c_begin; c0 < c_end; c0 += TU_CH) {
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+      const int idx = tid + 256 * i;
+      sa[idx % TU_CH][idx / TU_CH] = pa[i];
+    }
+#pragma unroll
+    for (int i = 0; i < LC; ++i) {
+      const int idx = tid + 256 * i;
+      if (idx < TU_CH * KP) sc[idx / KP][idx % KP] = pc[i];
     }
     __syncthreads();
+    if (c0 + TU_CH < c_end) load(c0 + TU_CH);   // in flight while this tile is used
 #pragma unroll 8
     for (int cc = 0; cc < TU_CH; ++cc) {
-      TH w[4], b[4];
+      TH w[RPT], b[CPT];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) { w[u] = sa[cc][ty * 4 + u]; b[u] = sc[cc][tx + 16 * u]; }
+      for (int u = 0; u < RPT; ++u) w[u] = sa[cc][ty + TY * u];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int v = 0; v < CPT; ++v) b[v] = sc[cc][tx + TXC * v];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(w[u], b[v], acc[u][v]);
+      for (int u = 0; u < RPT; ++u)
+#pragma unroll
+        for (int v = 0; v < CPT; ++v) acc[u][v] = fma(w[u], b[v], acc[u][v]);
     }
     __syncthreads();
   }
-  TH* P = part + (size_t)blockIdx.y * n * 64;
+  if (splits == 1) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int row = r0 + ty * 4 + u;
-    if (row >= n) continue;
+    for (int u = 0; u < RPT; ++u) {
+      const int row = r0 + ty + TY * u;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) P[(size_t)row * 64 + tx + 16 * v] = acc[u][v];
+      for (int v = 0; v < CPT; ++v) {
+        const int g = tx + TXC * v;
+        if (row < n && g < k) W[(size_t)row * k + g] += alpha * (double)acc[u][v];
+      }
+    }
+    return;
+  }
+  TH* P = part + (size_t)blockIdx.y * n * k;
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) {
+    const int row = r0 + ty + TY * u;
+#pragma unroll
+    for (int v = 0; v < CPT; ++v) {
+      const int g = tx + TXC * v;
+      if (row < n && g < k) P[(size_t)row * k + g] = acc[u][v];
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned prev = atomicAdd(&tickets[blockIdx.x], 1u);
+    last = prev == (unsigned)splits - 1;
+    if (last) tickets[blockIdx.x] = 0u;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int rows = min(TU_ROWS, n - r0);
+  for (int idx = tid; idx < rows * k; idx += 256) {
+    const size_t o = (size_t)r0 * k + idx;
+    TH v0 = TH(0), v1 = TH(0);
+    int sp = 0;
+    for (; sp + 1 < splits; sp += 2) {
+      v0 += __ldcg(part + (size_t)sp * n * k + o);
+      v1 += __ldcg(part + (size_t)(sp + 1) * n * k + o);
+    }
+    if (sp < splits) v0 += __ldcg(part + (size_t)sp * n * k + o);
+    W[o] += alpha * (double)(v0 + v1);
   }
 }
 
-template <typename TH>
-__global__ void k_tall_update_finish(int n, int k, int splits, const int* __restrict__ d_a, const TH* __restrict__ part,
-                                     double alpha, double* __restrict__ W) {
-  if (d_a && *d_a <= 0) return;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)n * k) return;
-  const int row = (int)(idx / k), g = (int)(idx % k);
-  TH acc = TH(0);
-  for (int sp = 0; sp < splits; ++sp) acc += part[((size_t)sp * n + row) * 64 + g];
-  W[idx] += alpha * (double)acc;
-}
-
-template <typename TH>
 int tall_update_splits(int n, int a_max) {
   const int tiles = ceil_div(n, TU_ROWS);
-  return std::max(1, std::min(std::max(1, 304 / tiles), ceil_div(a_max, TU_CH)));
+  return std::max(1, std::min(std::max(1, 1216 / tiles), ceil_div(a_max, TU_CH)));
 }
 
 template <typename TH>
 void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, long long ldh, const double* C, double alpha,
-                 double* W, DBuf<double>& scratch, cudaStream_t s) {
+                 double* W, DBuf<double>& scratch, DBuf<unsigned>& tickets, cudaStream_t s) {
   if (a_max <= 0 || n <= 0) return;
   if (k > 64) throw Error(1, "k > 64");
-  const int splits = tall_update_splits<TH>(n, a_max);
-  const size_t need = ((size_t)splits * n * 64 * sizeof(TH) + sizeof(double) - 1) / sizeof(double);
+  const int splits = tall_update_splits(n, a_max);
+  const int tiles = ceil_div(n, TU_ROWS);
+  const size_t need = ((size_t)splits * n * k * sizeof(TH) + sizeof(double) - 1) / sizeof(double);
   scratch.ensure(need);
+  if (tickets.n < (size_t)tiles) {   // tickets start at zero and every use leaves them at zero
+    tickets.alloc(tiles);
+    FETIRP_CUDA(cudaMemsetAsync(tickets.p, 0, sizeof(unsigned) * tiles, s));
+  }
   TH* part = reinterpret_cast<TH*>(scratch.p);
-  k_tall_update_partial<TH><<<dim3(ceil_div(n, TU_ROWS), splits), 256, 0, s>>>(n, a_max, d_a, k, Wh, ldh, C, splits,
-                                                                               part);
-  FETIRP_LAUNCH_CHECK();
-  const long long tot = (long long)n * k;
-  k_tall_update_finish<TH><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(n, k, splits, d_a, part, alpha, W);
+  const dim3 grid(tiles, splits);
+  if (k <= 8)
+    k_tall_update<TH, 8><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, ldh, C, splits, part, tickets.p, alpha, W);
+  else if (k <= 16)
+    k_tall_update<TH, 16><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, ldh, C, splits, part, tickets.p, alpha, W);
+  else if (k <= 32)
+    k_tall_update<TH, 32><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, ldh, C, splits, part, tickets.p, alpha, W);
+  else
+    k_tall_update<TH, 64><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, ldh, C, splits, part, tickets.p, alpha, W);
   FETIRP_LAUNCH_CHECK();
 }
 template void tall_update<double>(int, int, const int*, int, const double*, long long, const double*, double,
-                                  double*, DBuf<double>&, cudaStream_t);
+                                  double*, DBuf<double>&, DBuf<unsigned>&, cudaStream_t);
 template void tall_update<float>(int, int, const int*, int, const float*, long long, const double*, double, double*,
-                                 DBuf<double>&, cudaStream_t);
+                                 DBuf<double>&, DBuf<unsigned>&, cudaStream_t);
 
 // End of a block iteration: history count += k (restart when the next block would not fit), dropped
 // directions and iterations counted on the device.

@@ -101,10 +101,12 @@ void gram_split(int a_max, const int* d_a, int k, const TH* Qh, long long ldq, c
                 cudaStream_t s);
 // W (n x k, FP64) += alpha * Wh (n x a, history type TH, leading dimension ldh) * C (a x k, FP64), computed
 // in TH arithmetic.
-// scratch: split partials (grown here; callers that capture graphs size it first with the same arguments).
+// scratch: split partials, tall_update_splits(n, a_max) * n * k values of TH; tickets: one counter per 64-row
+// tile, zero between calls (both grown here; callers that capture graphs size them first).
+int tall_update_splits(int n, int a_max);
 template <typename TH>
 void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, long long ldh, const double* C, double alpha,
-                 double* W, DBuf<double>& scratch, cudaStream_t s);
+                 double* W, DBuf<double>& scratch, DBuf<unsigned>& tickets, cudaStream_t s);
 // history count += k with restart, dropped and iteration counters (one thread)
 void advance(int* cols, int k, long long cap, const int* n_kept, int* dropped, int* iters, cudaStream_t s);
 // Row-chunk partials (eta_chunks(n) of them) of [eta | wr] = W^T [Q | r], a k x (k+1) block, FP64 sums;
