@@ -43,12 +43,13 @@ PHASE_KERNELS = {  # the kernels each phase launches
     "factor": "k_potrf_tile, k_trsm_tiles, k_update_pairs, k_tile_inverse, k_tri_*", "coarse": "k_gtg, k_gemm_f64",
     "local": "k_local_gemm / k_tc_gemm", "gather": "k_gather", "scatter": "k_scatter",
     "project": "k_gt_v, k_small_gemm, k_g_apply", "gram": "k_gram_split + k_reduce_chunks_dyn, k_eta_partial",
-    "reorth": "k_tall_update_partial + k_tall_update_finish", "update": "k_split, k_update, k_advance",
+    "reorth": "k_tall_update", "update": "k_split, k_update",
     "recover": "k_tri_*, k_unpermute_rotate", "normalise": "k_normalise",
+    "iterate": "k_persist (whole block iterations in one cooperative launch)",
 }
 PHASE_BOUND = {  # roofline resource of each phase's kernels
     "factor": "alu", "coarse": "alu", "local": "alu", "gather": "hbm", "scatter": "hbm", "project": "hbm",
-    "gram": "alu", "reorth": "alu", "update": "alu", "recover": "alu", "normalise": "alu",
+    "gram": "alu", "reorth": "alu", "update": "alu", "recover": "alu", "normalise": "alu", "iterate": "hbm",
 }
 
 

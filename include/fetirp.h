@@ -77,6 +77,10 @@ typedef struct {
   int32_t timing_mask; /* with timing = 1: bit p set -> phase p is bracketed with events; 0 = every phase */
   int64_t history_bytes; /* cap on the two direction-history arrays (a full history restarts the recurrence);
                             0 = half of the free device memory */
+  int32_t persistent;  /* 1: structures small enough to be latency-bound (n_lambda <= 262144, k <= 32, FP64 or
+                          FP32 local products) run whole block iterations in one cooperative persistent
+                          launch with bounded grid barriers, stopping on the device at convergence; 0: CUDA
+                          graphs of per-phase kernels; default 1 */
 } fetirp_options;
 
 /* Phases of a solve, for the per-phase statistics. */
@@ -92,7 +96,8 @@ enum {
   FETIRP_PHASE_UPDATE = 8,   /* split of r, W T, P~ T, lambda and residual updates, norms */
   FETIRP_PHASE_RECOVER = 9,  /* alpha and u(s) */
   FETIRP_PHASE_NORMALISE = 10, /* F-normalisation of eta (pivoted Cholesky, one CTA) */
-  FETIRP_NPHASE = 11
+  FETIRP_PHASE_ITERATE = 11,   /* whole block iterations in one persistent launch (options.persistent) */
+  FETIRP_NPHASE = 12
 };
 
 typedef struct {
@@ -107,10 +112,10 @@ typedef struct {
   int64_t launches;           /* kernels launched by the call */
   /* with options.timing = 1: per phase (FETIRP_PHASE_*) device time, launches, and the algorithmic work
      counted from the sizes (flops and compulsory bytes, not hardware counters) */
-  double phase_ms[11];
-  int64_t phase_launches[11];
-  double phase_flops[11];
-  double phase_bytes[11];
+  double phase_ms[FETIRP_NPHASE];
+  int64_t phase_launches[FETIRP_NPHASE];
+  double phase_flops[FETIRP_NPHASE];
+  double phase_bytes[FETIRP_NPHASE];
 } fetirp_stats;
 
 /* Fill *opt with the defaults listed above. */

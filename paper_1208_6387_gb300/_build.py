@@ -12,6 +12,9 @@ OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libfetirp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]
+# per-source flags: the persistent iteration reads data written by other CTAs after grid barriers, so its
+# global loads are cached in L2 only (coherent across SMs), never in L1
+EXTRA = {"persist.cu": ["-Xptxas", "-dlcm=cg"]}
 
 
 def sources():
@@ -39,7 +42,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
 
     def one(pair):
         src, obj = pair
-        cmd = [cc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *EXTRA.get(os.path.basename(src), []), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")

@@ -152,6 +152,15 @@ struct fetirp_ctx_s {
       d_occ_group, d_pair_s, d_pair_t, d_rot, d_grp_ptr, d_grp_row, d_ell_row;
   DBuf<int8_t> d_ell_sign;
   DBuf<double> d_grp_w;
+  // tables of the persistent iteration: multivector columns of the row's slots, 1 / slot count, offsets of the
+  // row's slots in the local product buffers (for the current k)
+  DBuf<int> d_row_grp, d_row_zld, d_rowg_gofs;
+  DBuf<double> d_row_wt, d_rowg_coef;
+  DBuf<long long> d_row_z;
+  DBuf<unsigned> d_pbar;     // {barrier count, barrier generation, eta ticket, error flag}
+  DBuf<double> pers_eta, prr;
+  DBuf<unsigned long long> pers_clk;   // timing: per-phase nanoseconds of the persistent iteration
+  std::vector<double> h_prr;
   DBuf<int8_t> d_slot_sign, d_row_sign;
   DBuf<long long> d_uoff;
   int n_pairs = 0;
@@ -647,6 +656,55 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   ctx->d_grp_ptr.upload(grp_ptr, s);
   ctx->d_grp_row.upload(grp_row, s);
   ctx->d_grp_w.upload(grp_w, s);
+  {
+    std::vector<long long> pbase(n_pat + 1, 0);
+    for (int p = 0; p < n_pat; ++p)
+      pbase[p + 1] = pbase[p] + (long long)ctx->use[p].occs.size() * k * ctx->pats[p]->ld_y;
+    std::vector<int> row_grp(2 * (size_t)nl, -1), row_zld(2 * (size_t)nl, 0);
+    std::vector<double> row_wt(nl);
+    std::vector<long long> row_z(2 * (size_t)nl, 0);
+    for (int r = 0; r < nl; ++r) {
+      row_wt[r] = 1.0 / row_cnt[r];
+      for (int e = 0; e < row_cnt[r]; ++e) {
+        const int slot = row_slot[2 * (size_t)r + e];
+        const int o = slot_occ[slot];
+        const int p = occ_pat[o];
+        const long long ld = ctx->pats[p]->ld_y;
+        row_grp[2 * (size_t)r + e] = group[o];
+        row_z[2 * (size_t)r + e] = pbase[p] + (long long)occ_q[o] * k * ld + (slot - obase[o]);
+        row_zld[2 * (size_t)r + e] = (int)ld;
+      }
+    }
+    ctx->d_row_grp.upload(row_grp, s);
+    ctx->d_row_zld.upload(row_zld, s);
+    ctx->d_row_wt.upload(row_wt, s);
+    ctx->d_row_z.upload(row_z, s);
+    // G restricted to the row: coarse column of each slot's occurrence and sign * Nb[j][m] (m < 6)
+    std::vector<int> rowg_gofs(2 * (size_t)nl, -1);
+    std::vector<double> rowg_coef(12 * (size_t)nl, 0.0);
+    std::vector<std::vector<double>> hNb(n_pat);   // (pattern data is shared between contexts: copy locally)
+    for (int p = 0; p < n_pat; ++p) {
+      const PatternData& P = *ctx->pats[p];
+      if (P.kdim > 6) continue;   // such structures do not use the persistent iteration
+      hNb[p].resize((size_t)P.n_b * P.kdim);
+      if (P.kdim > 0)
+        FETIRP_CUDA(cudaMemcpyAsync(hNb[p].data(), P.Nb.p, sizeof(double) * hNb[p].size(), cudaMemcpyDeviceToHost, s));
+    }
+    FETIRP_CUDA(cudaStreamSynchronize(s));
+    for (int r = 0; r < nl; ++r)
+      for (int e = 0; e < row_cnt[r]; ++e) {
+        const int slot = row_slot[2 * (size_t)r + e];
+        const int o = slot_occ[slot];
+        const PatternData& P = *ctx->pats[occ_pat[o]];
+        if (P.kdim > 6 || P.kdim == 0) continue;
+        rowg_gofs[2 * (size_t)r + e] = occ_gofs[o];
+        for (int m = 0; m < P.kdim; ++m)
+          rowg_coef[(2 * (size_t)r + e) * 6 + m] =
+              row_sign[2 * (size_t)r + e] * hNb[occ_pat[o]][(size_t)(slot - obase[o]) * P.kdim + m];
+      }
+    ctx->d_rowg_gofs.upload(rowg_gofs, s);
+    ctx->d_rowg_coef.upload(rowg_coef, s);
+  }
   ctx->d_pair_s.upload(pair_s, s);
   ctx->d_pair_t.upload(pair_t, s);
   ctx->n_pairs = (int)pair_s.size();
@@ -970,10 +1028,12 @@ void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
 }
 
 // Algorithmic work of one iteration with `a` stored directions (the per-phase flops and compulsory bytes).
-void account_iteration(fetirp_ctx ctx, int prec, long long a, double es) {
+void account_iteration(fetirp_ctx ctx, int prec, long long a, double es, bool persistent = false) {
   const double nl = ctx->L.n_lambda, k = ctx->k, nG = ctx->n_G;
   double* F = ctx->phase_flops;
   double* B = ctx->phase_bytes;
+  double f0 = 0.0, b0 = 0.0;
+  for (int i = 0; i < FETIRP_NPHASE; ++i) { f0 += F[i]; b0 += B[i]; }
   F[FETIRP_PHASE_GRAM] += 4.0 * nl * a + 2.0 * nl * k * (k + 1.0);
   B[FETIRP_PHASE_GRAM] += es * nl * a + 24.0 * nl + 8.0 * nl * (2.0 * k + 1.0);
   F[FETIRP_PHASE_REORTH] += 2.0 * nl * a * k;
@@ -996,6 +1056,12 @@ void account_iteration(fetirp_ctx ctx, int prec, long long a, double es) {
   }
   B[FETIRP_PHASE_GATHER] += 8.0 * nl * k + (prec == FETIRP_PREC_TF32X3 ? 2.0 : 1.0) * e_loc * rhs;
   B[FETIRP_PHASE_SCATTER] += 8.0 * nl * k + e_loc * rhs;
+  if (persistent) {   // the whole iteration ran in one launch: its work is also that of the iterate phase
+    double f1 = 0.0, b1 = 0.0;
+    for (int i = 0; i < FETIRP_NPHASE; ++i) { f1 += F[i]; b1 += B[i]; }
+    F[FETIRP_PHASE_ITERATE] += f1 - f0;
+    B[FETIRP_PHASE_ITERATE] += b1 - b0;
+  }
 }
 
 // Replay (or run) G iterations; returns the residual norm after the last one and the kept count.
@@ -1043,6 +1109,83 @@ void run_iterations(fetirp_ctx ctx, int prec, int G, bool use_graph, TH* Wh, TH*
   }
 }
 
+// The persistent iteration serves latency-bound structures: FP64 or FP32 local products (SIMT), k <= 32, at
+// most six kernel modes per occurrence, n_lambda up to 262144.
+bool persist_eligible(fetirp_ctx ctx, int prec) {
+  if (!ctx->opt.persistent) return false;
+  if (prec != FETIRP_PREC_FP64 && prec != FETIRP_PREC_FP32) return false;
+  if (ctx->k > 32 || ctx->L.n_lambda > 262144) return false;
+  for (auto& P : ctx->pats)
+    if (P->kdim > 6) return false;
+  return persist_ctas(prec == FETIRP_PREC_FP64, ctx->k) > 0;
+}
+
+// Arguments of the persistent launch; sizes the buffers it needs (outside any capture).
+template <typename TH>
+PersistArgs persist_args(fetirp_ctx ctx, bool fp64, TH* Wh, TH* Qh) {
+  cudaStream_t s = ctx->stream;
+  const Layout& L = ctx->L;
+  const int nl = L.n_lambda, k = ctx->k, n_pat = (int)ctx->pats.size();
+  PersistArgs A{};
+  A.L = L;
+  A.n = nl;
+  A.k = k;
+  A.ncta = persist_ctas(fp64, k);
+  A.cap = ctx->hist_cap;
+  long long total = 0;
+  for (int p = 0; p < n_pat; ++p) {
+    PatternData& P = *ctx->pats[p];
+    A.ybase[p] = total;
+    A.ld[p] = P.ld_y;
+    A.n_rhs[p] = (int)ctx->use[p].occs.size() * k;
+    A.S[p] = fp64 ? (const void*)P.S64.p : (const void*)P.S32.p;
+    total += (long long)ctx->use[p].occs.size() * k * P.ld_y;
+  }
+  int tiles = 0;
+  for (int p = 0; p < n_pat; ++p) {
+    A.tile_off[p] = tiles;
+    A.tiles_m[p] = ceil_div(L.n_b[p], 16);
+    tiles += A.tiles_m[p] * ceil_div(A.n_rhs[p], 16);
+  }
+  A.tile_off[n_pat] = tiles;
+  if (fp64) {
+    ctx->Y64.ensure(total); ctx->Z64.ensure(total);
+    A.Ybuf = ctx->Y64.p; A.Zbuf = ctx->Z64.p;
+  } else {
+    ctx->Y32.ensure(total); ctx->Z32.ensure(total);
+    A.Ybuf = ctx->Y32.p; A.Zbuf = ctx->Z32.p;
+  }
+  A.row_grp = ctx->d_row_grp.p; A.row_wt = ctx->d_row_wt.p; A.row_z = ctx->d_row_z.p; A.row_zld = ctx->d_row_zld.p;
+  A.rowg_gofs = ctx->d_rowg_gofs.p; A.rowg_coef = ctx->d_rowg_coef.p;
+  A.r = ctx->r.p; A.lam = ctx->lam.p; A.Zr = ctx->Zr.p; A.Q = ctx->Q.p;
+  A.Wh = Wh; A.Qh = Qh;
+  A.grp_ptr = ctx->d_grp_ptr.p; A.grp_row = ctx->d_grp_row.p; A.grp_w = ctx->d_grp_w.p;
+  A.gs_chunks = std::max(1, ceil_div(ctx->max_group_rows, 128));
+  A.gram_part = ctx->gram_part.p; A.C = ctx->C.p;
+  A.Ginv = ctx->Ginv.p; A.Xc = ctx->Xc.p; A.Ac = ctx->Ac.p;
+  // history splits sized for the persistent grid (about one item per CTA; never more than tu_part holds)
+  A.tu_splits = std::max(1, std::min(tall_update_splits(nl, (int)ctx->hist_cap), A.ncta / ceil_div(nl, 64)));
+  A.tu_part = ctx->tu_part.p; A.tu_tickets = ctx->tu_tickets.p;
+  const int nout = k * (k + 1);
+  ctx->pers_eta.ensure((size_t)A.ncta * nout);
+  ctx->prr.ensure(A.ncta);
+  ctx->h_prr.assign(A.ncta, 0.0);
+  if (!ctx->d_pbar.p) ctx->d_pbar.alloc(4);
+  A.eta_part = ctx->pers_eta.p; A.eta_ticket = ctx->d_pbar.p + 2;
+  A.trunc = fp64 ? ctx->opt.eig_trunc : ctx->opt.eig_trunc_inner;
+  A.T = ctx->T.p; A.alpha = ctx->alpha.p; A.n_kept = ctx->n_kept.p;
+  A.rr_part = ctx->prr.p; A.state = ctx->d_state.p;
+  A.bar = ctx->d_pbar.p; A.err = reinterpret_cast<int*>(ctx->d_pbar.p + 3);
+  A.timeout_ns = 2000000000ull;
+  A.clk = nullptr;
+  if (ctx->opt.timing) {
+    if (!ctx->pers_clk.p) ctx->pers_clk.alloc(11);
+    FETIRP_CUDA(cudaMemsetAsync(ctx->pers_clk.p, 0, 11 * sizeof(unsigned long long), s));
+    A.clk = ctx->pers_clk.p;
+  }
+  return A;
+}
+
 // Block ORTHODIR iterations on P^T F_prec P (Table 1 right with full reorthogonalisation and
 // F-normalisation).  Updates lam and r in place until ||r|| <= target or the caps are hit.  Directions kept in
 // the history stay F_prec-orthonormal, so a later call with the same precision reuses them (Galerkin start).
@@ -1063,7 +1206,7 @@ double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, His
     const int a = (int)H.cols;
     {
       PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 2.0 * nl * a, nl * (es * a + 8.0));
-      gram<TH, double>(nl, a, 1, Wh, (int)cap, ctx->r.p, 1, ctx->C.p, ctx->gram_part, s);
+      hist_dot<TH>(nl, a, Wh, cap, ctx->r.p, ctx->C.p, ctx->gram_part, s);
     }
     {
       PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 4.0 * nl * a, 2.0 * es * nl * a + 32.0 * nl);
@@ -1079,6 +1222,52 @@ double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, His
   FETIRP_CUDA(cudaMemcpyAsync(ctx->d_state.p, ctx->h_state, 4 * sizeof(int), cudaMemcpyHostToDevice, s));
   const int G = std::max(1, ctx->opt.check_every);
   int kept = k;
+  if (persist_eligible(ctx, prec)) {
+    // whole block iterations in one cooperative launch; the device stops at ||r||^2 <= target^2
+    const bool fp64 = prec == FETIRP_PREC_FP64;
+    PersistArgs A = persist_args(ctx, fp64, Wh, Qh);
+    A.target2 = target * target;
+    while (rnorm > target && it_budget > 0 && kept > 0) {
+      FETIRP_CUDA(cudaMemsetAsync(ctx->d_pbar.p, 0, 4 * sizeof(unsigned), s));
+      FETIRP_CUDA(cudaMemsetAsync(ctx->tu_tickets.p, 0, sizeof(unsigned) * ctx->tu_tickets.n, s));
+      FETIRP_CUDA(cudaMemcpyAsync(ctx->h_state + 5, ctx->d_state.p + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+      A.max_iters = it_budget;
+      {
+        PhaseScope ph(ctx, FETIRP_PHASE_ITERATE, 0.0, 0.0);
+        persist_iterations(A, fp64, s);
+      }
+      FETIRP_CUDA(cudaMemcpyAsync(ctx->h_state, ctx->d_state.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      FETIRP_CUDA(cudaMemcpyAsync(ctx->h_state + 4, ctx->n_kept.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+      FETIRP_CUDA(cudaMemcpyAsync(ctx->h_state + 6, ctx->d_pbar.p + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
+      FETIRP_CUDA(cudaMemcpyAsync(ctx->h_prr.data(), ctx->prr.p, sizeof(double) * A.ncta, cudaMemcpyDeviceToHost, s));
+      FETIRP_CUDA(cudaStreamSynchronize(s));
+      if (ctx->h_state[6] != 0)
+        throw Error(FETIRP_ETIMEOUT, "a grid barrier of the persistent iteration did not complete in time");
+      if (A.clk) {   // phases inside the launch (CTA 0, barrier waits included); their sum is the iterate phase
+        unsigned long long ns[11];
+        FETIRP_CUDA(cudaMemcpy(ns, A.clk, sizeof(ns), cudaMemcpyDeviceToHost));
+        FETIRP_CUDA(cudaMemsetAsync(A.clk, 0, sizeof(ns), s));
+        // P8 (scatter, eta) contains the last CTA's eta reduction and normalisation, also booked as normalise
+        const int map[11] = {FETIRP_PHASE_GRAM, FETIRP_PHASE_GRAM, FETIRP_PHASE_REORTH, FETIRP_PHASE_GATHER,
+                             FETIRP_PHASE_LOCAL, FETIRP_PHASE_PROJECT, FETIRP_PHASE_PROJECT, FETIRP_PHASE_SCATTER,
+                             FETIRP_PHASE_UPDATE, FETIRP_PHASE_NORMALISE, FETIRP_PHASE_NORMALISE};
+        for (int i = 0; i < 11; ++i) ctx->graph_phase_ms[map[i]] += 1e-6 * (double)ns[i];
+      }
+      const int done = ctx->h_state[2] - ctx->h_state[5];
+      for (int i = 0; i < done; ++i) {   // host mirror of the device history count (same restart rule)
+        account_iteration(ctx, prec, H.cols, es, true);
+        H.cols += k;
+        if (H.cols + k > cap) H.cols = 0;
+      }
+      double acc = 0.0;
+      for (int i = 0; i < A.ncta; ++i) acc += ctx->h_prr[i];
+      rnorm = std::sqrt(acc);
+      kept = ctx->h_state[4];
+      st.iterations += done;
+      it_budget -= done;
+      if (done < A.max_iters) break;   // the device found ||r|| <= target (or no direction kept)
+    }
+  } else
   while (rnorm > target && it_budget > 0 && kept > 0) {
     const int g = std::min(G, it_budget);
     run_iterations<TH>(ctx, prec, g, g == G && ctx->opt.use_graphs, Wh, Qh);
@@ -1438,6 +1627,7 @@ void fetirp_default_options(fetirp_options* o) {
   o->use_graphs = 1;
   o->timing_mask = 0;
   o->history_bytes = 0;
+  o->persistent = 1;
 }
 
 const char* fetirp_status_string(fetirp_status s) {

@@ -55,45 +55,55 @@ __global__ void k_zero_zp_rows(double* A, int npad, const int* zp) {
   for (int c = threadIdx.x; c < npad; c += blockDim.x) A[(size_t)c * npad + j] = 0.0;
 }
 
-// Factor the diagonal tile k in place (one CTA, 256 threads).
+// Factor the diagonal tile k in place (one CTA, 256 threads).  Square-root-free inside the loop (a dependent
+// FP64 divide costs ~450 cycles and a square root ~700 on this GPU): step j takes only the reciprocal of the
+// pivot, the trailing update uses the unscaled column (a_rc -= a_rj a_cj / d_j, the same products as the
+// square-root form), and every column is scaled by 1 / sqrt(d_j) once at the end, in parallel, giving
+// L = L_unit D^{1/2}.  Zero pivots (d_j <= tol * diag0_j, or not finite) get a zero column as before.
 __global__ void __launch_bounds__(256) k_potrf_tile(double* A, int npad, int k, const double* diag0, int* zp,
                                                     double tol) {
   __shared__ double a[TILE][TILE + 1];   // a[row][col]
+  __shared__ double thr[TILE];           // tol * diag0 of the tile's dofs
+  __shared__ double rsq[TILE];           // 1 / sqrt(d_j), 0 for zero pivots
+  __shared__ double s_rinv;
+  __shared__ int s_zero;
   const int tid = threadIdx.x;
   double* T = A + (size_t)k * TILE * npad + (size_t)k * TILE;
   for (int idx = tid; idx < TILE * TILE; idx += 256) {
     int r = idx % TILE, c = idx / TILE;
     a[r][c] = T[(size_t)c * npad + r];
   }
+  if (tid < TILE) thr[tid] = tol * diag0[k * TILE + tid];
   __syncthreads();
-  __shared__ double s_l, s_inv;
-  __shared__ int s_zero;
   for (int j = 0; j < TILE; ++j) {
-    const int gj = k * TILE + j;
-    if (tid == 0) {   // the pivot's square root and reciprocal once (FP64 divide and sqrt are costly)
+    if (tid == 0) {
       const double d = a[j][j];
-      const bool zero = !(d > tol * diag0[gj]);   // also catches NaN and negative roundoff
+      const bool zero = !(d > thr[j]);   // also catches NaN and negative roundoff
       s_zero = zero ? 1 : 0;
-      zp[gj] = zero ? 1 : 0;
-      const double l = zero ? 0.0 : sqrt(d);
-      s_l = l;
-      s_inv = zero ? 0.0 : 1.0 / l;
+      s_rinv = zero ? 0.0 : 1.0 / d;
+      rsq[j] = zero ? 0.0 : d;          // d_j for now; 1 / sqrt(d_j) after the loop
     }
     __syncthreads();
-    const bool zero = s_zero != 0;
-    const double l = s_l, inv = s_inv;
-    for (int r = j + tid; r < TILE; r += 256) a[r][j] = zero ? 0.0 : ((r == j) ? l : a[r][j] * inv);
-    __syncthreads();
-    const int w = TILE - 1 - j;        // trailing columns j+1 .. TILE-1, rows >= column
-    for (int idx = tid; idx < w * TILE; idx += 256) {
-      int c = j + 1 + idx / TILE, r = idx % TILE;
-      if (r >= c) a[r][c] -= a[r][j] * a[c][j];
+    if (!s_zero) {
+      const double rinv = s_rinv;
+      const int w = TILE - 1 - j;        // trailing columns j+1 .. TILE-1, rows >= column
+      for (int idx = tid; idx < w * TILE; idx += 256) {
+        int c = j + 1 + idx / TILE, r = idx % TILE;
+        if (r >= c) a[r][c] -= (a[r][j] * a[c][j]) * rinv;
+      }
     }
     __syncthreads();
   }
+  if (tid < TILE) {
+    const int gj = k * TILE + tid;
+    const double d = rsq[tid];
+    zp[gj] = d > 0.0 ? 0 : 1;
+    rsq[tid] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+  }
+  __syncthreads();
   for (int idx = tid; idx < TILE * TILE; idx += 256) {
     int r = idx % TILE, c = idx / TILE;
-    T[(size_t)c * npad + r] = (r >= c) ? a[r][c] : 0.0;
+    T[(size_t)c * npad + r] = (r >= c) ? a[r][c] * rsq[c] : 0.0;
   }
 }
 

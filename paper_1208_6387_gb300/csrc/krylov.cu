@@ -1,6 +1,7 @@
 // Block Gram products, F-normalisation and the block update of multivector FETI (Table 1 right column,
 // lines 5.2-5.4, with the F-normalisation and full reorthogonalisation of the numerical-issues subsection).
 #include "ops.cuh"
+#include "normalise_warp.cuh"
 
 namespace fetirp {
 
@@ -98,56 +99,46 @@ __global__ void k_reduce_chunks(int count, int chunks, const double* __restrict_
   C[i] = acc;
 }
 
-// One CTA: pivoted Cholesky of eta with truncation, T = Pi M^{-T}, alpha = T^T (W^T r).
-// Pivot search by warp shuffles; the triangular inverse by a right-looking sweep, parallel over (row, column).
-// ext_partial: `chunks` row-chunk partials of the k x (k+1) block [eta | W^T r]; they are added here in chunk
-// order (one warp per output entry), so no separate reduction launch is needed.
+// KMAX = 32 (one-warp factorisation, small shared footprint) or 64 (block-wide factorisation).
+template <int KMAX>
 __global__ void __launch_bounds__(512) k_normalise(int k, const double* __restrict__ ext_partial, int chunks,
                                                    double trunc, double* __restrict__ T, double* __restrict__ alpha,
                                                    int* __restrict__ n_kept) {
-  __shared__ double A[64][65];    // eta, then (after the factorisation) X = M^{-1}
-  __shared__ double Lc[64][65];   // Lc[i][step], original row index i
-  __shared__ int piv[64];
-  __shared__ int ipiv[64];
-  __shared__ int done[64];
-  __shared__ double rhs[64];
+  __shared__ double A[KMAX][KMAX + 1];    // eta, then (after the factorisation) X = M^{-1}
+  __shared__ double Lc[KMAX][KMAX + 1];   // Lc[i][step], original row index i
+  __shared__ int piv[KMAX];
+  __shared__ int ipiv[KMAX];
+  __shared__ int done[KMAX];
+  __shared__ double rhs[KMAX];
   __shared__ int s_r, s_p;
   __shared__ double s_dmax, s_ipp, s_ilp;   // pivot reciprocal and its square root, computed once per step
-  __shared__ double dinv[64];
+  __shared__ double dinv[KMAX];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nout = k * (k + 1);
-  double* ext = &Lc[0][0];   // [eta | wr] (k (k+1) <= 64 * 65 entries) lives in Lc's storage until Lc is needed
+  double* ext = &Lc[0][0];   // [eta | wr] (k (k+1) <= KMAX (KMAX + 1) entries) lives in Lc's storage until needed
   // Sum of the chunk partials.  Every thread takes one output and a strided subset of the chunks (loads
   // coalesced over the outputs and independent of one another), then the subsets are added in a fixed order.
   const int groups = max(1, (int)blockDim.x / nout);
-  if (groups == 1) {
-    for (int o = tid; o < nout; o += blockDim.x) {
-      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-      int c = 0;
-      for (; c + 3 < chunks; c += 4) {
-        v0 += ext_partial[(size_t)c * nout + o];
-        v1 += ext_partial[(size_t)(c + 1) * nout + o];
-        v2 += ext_partial[(size_t)(c + 2) * nout + o];
-        v3 += ext_partial[(size_t)(c + 3) * nout + o];
+  // chunks g, g + groups, ...: eight independent loads at a time, summed as a tree (dependent FP64 adds are
+  // slow on this GPU, so the chains are kept short)
+  auto strided_sum = [&](int o, int g) {
+    double acc = 0.0;
+    for (int c = g; c < chunks; c += 8 * groups) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int cc = c + u * groups;
+        v[u] = cc < chunks ? ext_partial[(size_t)cc * nout + o] : 0.0;
       }
-      for (; c < chunks; ++c) v0 += ext_partial[(size_t)c * nout + o];
-      ext[o] = (v0 + v1) + (v2 + v3);
+      acc += ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
     }
+    return acc;
+  };
+  if (groups == 1) {
+    for (int o = tid; o < nout; o += blockDim.x) ext[o] = strided_sum(o, 0);
   } else {
     double* red = &A[0][0];   // groups * nout <= blockDim.x entries
-    if (tid < groups * nout) {
-      const int o = tid % nout, g = tid / nout;
-      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-      int c = g;
-      for (; c + 3 * groups < chunks; c += 4 * groups) {
-        v0 += ext_partial[(size_t)c * nout + o];
-        v1 += ext_partial[(size_t)(c + groups) * nout + o];
-        v2 += ext_partial[(size_t)(c + 2 * groups) * nout + o];
-        v3 += ext_partial[(size_t)(c + 3 * groups) * nout + o];
-      }
-      for (; c < chunks; c += groups) v0 += ext_partial[(size_t)c * nout + o];
-      red[g * nout + o] = (v0 + v1) + (v2 + v3);
-    }
+    if (tid < groups * nout) red[tid] = strided_sum(tid % nout, tid / nout);
     __syncthreads();
     for (int o = tid; o < nout; o += blockDim.x) {
       double v = 0.0;
@@ -162,8 +153,12 @@ __global__ void __launch_bounds__(512) k_normalise(int k, const double* __restri
   }
   if (tid < k) { done[tid] = 0; rhs[tid] = ext[tid * (k + 1) + k]; ipiv[tid] = -1; }
   __syncthreads();
-  for (int idx = tid; idx < 64 * 65; idx += blockDim.x) (&Lc[0][0])[idx] = 0.0;
+  for (int idx = tid; idx < KMAX * (KMAX + 1); idx += blockDim.x) (&Lc[0][0])[idx] = 0.0;
   __syncthreads();
+  if (KMAX <= 32) {
+    if (warp == 0) normalise_warp<KMAX + 1>(k, A, Lc, piv, dinv, rhs, trunc, T, alpha, n_kept);
+    return;
+  }
   if (warp == 0) {
     double m = 0.0;
     for (int i = lane; i < k; i += 32) m = fmax(m, A[i][i]);
@@ -234,7 +229,8 @@ __global__ void __launch_bounds__(512) k_normalise(int k, const double* __restri
   const int r = s_r;
   // X = M^{-1} with M[a][b] = Lc[piv[a]][b] (lower triangular r x r): X = I, then for each l the row X[l] is
   // final after dividing by M[l][l], and rows below are updated
-  for (int idx = tid; idx < 64 * 64; idx += blockDim.x) A[idx / 64][idx % 64] = (idx / 64 == idx % 64) ? 1.0 : 0.0;
+  for (int idx = tid; idx < KMAX * KMAX; idx += blockDim.x)
+    A[idx / KMAX][idx % KMAX] = (idx / KMAX == idx % KMAX) ? 1.0 : 0.0;
   __syncthreads();
   for (int l = tid; l < r; l += blockDim.x) dinv[l] = 1.0 / Lc[piv[l]][l];
   __syncthreads();
@@ -457,8 +453,18 @@ __global__ void __launch_bounds__(128) k_small_gemm(int m, int k, const double* 
     const int slices = 32 / kp;
     const int g = g0 + (lane % kp), sl = lane / kp;
     double acc = 0.0;
-    if (g < k)
-      for (int j = sl; j < m; j += slices) acc = fma(a[j], B[(size_t)j * k + g], acc);
+    if (g < k) {   // four independent partial sums: the loads of four terms are in flight together
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int j = sl;
+      for (; j + 3 * slices < m; j += 4 * slices) {
+        s0 = fma(a[j], B[(size_t)j * k + g], s0);
+        s1 = fma(a[j + slices], B[(size_t)(j + slices) * k + g], s1);
+        s2 = fma(a[j + 2 * slices], B[(size_t)(j + 2 * slices) * k + g], s2);
+        s3 = fma(a[j + 3 * slices], B[(size_t)(j + 3 * slices) * k + g], s3);
+      }
+      for (; j < m; j += slices) s0 = fma(a[j], B[(size_t)j * k + g], s0);
+      acc = (s0 + s1) + (s2 + s3);
+    }
     for (int off = kp; off < 32; off <<= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     if (sl == 0 && g < k) C[(size_t)row * k + g] = acc;
   }
@@ -475,7 +481,8 @@ void small_gemm(int m, int k, const double* A, const double* B, double* C, cudaS
 void normalise(int k, const double* ext_partial, int chunks, double trunc, double* T, double* alpha, int* n_kept,
                cudaStream_t s) {
   if (k > 64) throw Error(1, "block width k > 64 is not supported");
-  k_normalise<<<1, 512, 0, s>>>(k, ext_partial, chunks, trunc, T, alpha, n_kept);
+  if (k <= 32) k_normalise<32><<<1, 512, 0, s>>>(k, ext_partial, chunks, trunc, T, alpha, n_kept);
+  else k_normalise<64><<<1, 512, 0, s>>>(k, ext_partial, chunks, trunc, T, alpha, n_kept);
   FETIRP_LAUNCH_CHECK();
 }
 
@@ -509,6 +516,7 @@ __global__ void __launch_bounds__(256) k_gram_split(int a_max, const int* __rest
                                                     int chunks, double* __restrict__ partial) {
   __shared__ int srow[GS_ROWS];
   __shared__ double sw[GS_ROWS];
+  __shared__ float swh[GS_ROWS], swl[GS_ROWS];   // w r[row] split into FP32 hi + lo (FP32 history)
   __shared__ double red[8][GS_COLS];
   const int a = d_a ? min(*d_a, a_max) : a_max;
   if (a <= 0) return;
@@ -522,21 +530,54 @@ __global__ void __launch_bounds__(256) k_gram_split(int a_max, const int* __rest
     __syncthreads();   // the previous item's shared-memory reads are done
     if (tid < cnt) {
       const int row = grp_row[e0 + tid];
+      const double v = grp_w[e0 + tid] * r[row];
       srow[tid] = row;
-      sw[tid] = grp_w[e0 + tid] * r[row];
+      sw[tid] = v;
+      const float vh = (float)v;
+      swh[tid] = vh;
+      swl[tid] = (float)(v - (double)vh);
     }
     __syncthreads();
     const int c0 = ct * GS_COLS + lane, c1 = c0 + 32;
     const bool ok0 = c0 < a, ok1 = c1 < a;
     double a0 = 0.0, a1 = 0.0;
+    if (sizeof(TH) == 4) {
+      // FP32 history: double-single arithmetic on the FP32 pipe (Dekker 1971; Knuth TwoSum).  q * s_hi is
+      // split exactly into p + e by an FMA, q * s_lo is rounded (its error is ~2^-48 |q s|), and each column
+      // sum is an unevaluated pair (hi, lo) updated by TwoSum; FP64 converts only the pairs at the end.  The
+      // _rn intrinsics keep the compiler from contracting the error-free transformations into FMAs.
+      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
 #pragma unroll 8
-    for (int i = warp; i < cnt; i += 8) {
-      const TH* q = Qh + (size_t)srow[i] * ldq;
-      const double wv = sw[i];
-      const double q0 = ok0 ? (double)q[c0] : 0.0;
-      const double q1 = ok1 ? (double)q[c1] : 0.0;
-      a0 = fma(wv, q0, a0);
-      a1 = fma(wv, q1, a1);
+      for (int i = warp; i < cnt; i += 8) {
+        const TH* q = Qh + (size_t)srow[i] * ldq;
+        const float sh = swh[i], sl = swl[i];
+        const float q0 = ok0 ? (float)q[c0] : 0.f;
+        const float q1 = ok1 ? (float)q[c1] : 0.f;
+        {
+          const float p = __fmul_rn(q0, sh), e = fmaf(q0, sh, -p), t = fmaf(q0, sl, e);
+          const float u = __fadd_rn(h0, p), bb = __fsub_rn(u, h0);
+          l0 = __fadd_rn(l0, __fadd_rn(__fadd_rn(__fsub_rn(h0, __fsub_rn(u, bb)), __fsub_rn(p, bb)), t));
+          h0 = u;
+        }
+        {
+          const float p = __fmul_rn(q1, sh), e = fmaf(q1, sh, -p), t = fmaf(q1, sl, e);
+          const float u = __fadd_rn(h1, p), bb = __fsub_rn(u, h1);
+          l1 = __fadd_rn(l1, __fadd_rn(__fadd_rn(__fsub_rn(h1, __fsub_rn(u, bb)), __fsub_rn(p, bb)), t));
+          h1 = u;
+        }
+      }
+      a0 = (double)h0 + (double)l0;
+      a1 = (double)h1 + (double)l1;
+    } else {
+#pragma unroll 8
+      for (int i = warp; i < cnt; i += 8) {
+        const TH* q = Qh + (size_t)srow[i] * ldq;
+        const double wv = sw[i];
+        const double q0 = ok0 ? (double)q[c0] : 0.0;
+        const double q1 = ok1 ? (double)q[c1] : 0.0;
+        a0 = fma(wv, q0, a0);
+        a1 = fma(wv, q1, a1);
+      }
     }
     red[warp][lane] = a0;
     red[warp][lane + 32] = a1;
@@ -547,6 +588,85 @@ __global__ void __launch_bounds__(256) k_gram_split(int a_max, const int* __rest
 #pragma unroll
       for (int w = 0; w < 8; ++w) v += red[w][tid];
       if (c < a) partial[((size_t)ch * a + c) * k + g] = v;
+    }
+  }
+}
+
+// C[c] = sum over all rows of Qh[row][c] * r[row] (history times one vector: the Galerkin start).  Same item
+// loop and arithmetic as k_gram_split, with rows_per_chunk-row chunks staged 256 rows at a time; the chunk
+// partials (chunk-major, a per chunk) are added in chunk order by k_reduce_chunks.
+template <typename TH>
+__global__ void __launch_bounds__(256) k_hist_dot(int n, int a, const TH* __restrict__ Qh, long long ldq,
+                                                  const double* __restrict__ r, int rows_per_chunk, int chunks,
+                                                  double* __restrict__ partial) {
+  __shared__ double sr[256];
+  __shared__ float srh[256], srl[256];
+  __shared__ double red[8][GS_COLS];
+  const int ctiles = (a + GS_COLS - 1) / GS_COLS;
+  const int items = ctiles * chunks;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int ct = it % ctiles, ch = it / ctiles;
+    const int r0 = ch * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+    const int c0 = ct * GS_COLS + lane, c1 = c0 + 32;
+    const bool ok0 = c0 < a, ok1 = c1 < a;
+    double a0 = 0.0, a1 = 0.0;
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    for (int sb = r0; sb < r1; sb += 256) {
+      const int cnt = min(256, r1 - sb);
+      __syncthreads();
+      if (tid < cnt) {
+        const double v = r[sb + tid];
+        sr[tid] = v;
+        const float vh = (float)v;
+        srh[tid] = vh;
+        srl[tid] = (float)(v - (double)vh);
+      }
+      __syncthreads();
+      if (sizeof(TH) == 4) {
+#pragma unroll 8
+        for (int i = warp; i < cnt; i += 8) {
+          const TH* q = Qh + (size_t)(sb + i) * ldq;
+          const float sh = srh[i], sl = srl[i];
+          const float q0 = ok0 ? (float)q[c0] : 0.f;
+          const float q1 = ok1 ? (float)q[c1] : 0.f;
+          {
+            const float p = __fmul_rn(q0, sh), e = fmaf(q0, sh, -p), t = fmaf(q0, sl, e);
+            const float u = __fadd_rn(h0, p), bb = __fsub_rn(u, h0);
+            l0 = __fadd_rn(l0, __fadd_rn(__fadd_rn(__fsub_rn(h0, __fsub_rn(u, bb)), __fsub_rn(p, bb)), t));
+            h0 = u;
+          }
+          {
+            const float p = __fmul_rn(q1, sh), e = fmaf(q1, sh, -p), t = fmaf(q1, sl, e);
+            const float u = __fadd_rn(h1, p), bb = __fsub_rn(u, h1);
+            l1 = __fadd_rn(l1, __fadd_rn(__fadd_rn(__fsub_rn(h1, __fsub_rn(u, bb)), __fsub_rn(p, bb)), t));
+            h1 = u;
+          }
+        }
+      } else {
+#pragma unroll 8
+        for (int i = warp; i < cnt; i += 8) {
+          const TH* q = Qh + (size_t)(sb + i) * ldq;
+          const double wv = sr[i];
+          a0 = fma(wv, ok0 ? (double)q[c0] : 0.0, a0);
+          a1 = fma(wv, ok1 ? (double)q[c1] : 0.0, a1);
+        }
+      }
+    }
+    if (sizeof(TH) == 4) {
+      a0 = (double)h0 + (double)l0;
+      a1 = (double)h1 + (double)l1;
+    }
+    __syncthreads();
+    red[warp][lane] = a0;
+    red[warp][lane + 32] = a1;
+    __syncthreads();
+    if (tid < GS_COLS) {
+      const int c = ct * GS_COLS + tid;
+      double v = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) v += red[w][tid];
+      if (c < a) partial[(size_t)ch * a + c] = v;
     }
   }
 }
@@ -580,6 +700,26 @@ template void gram_split<double>(int, const int*, int, const double*, long long,
                                  const int*, const double*, int, double*, DBuf<double>&, cudaStream_t);
 template void gram_split<float>(int, const int*, int, const float*, long long, const double*, const int*, const int*,
                                 const double*, int, double*, DBuf<double>&, cudaStream_t);
+
+template <typename TH>
+void hist_dot(int n, int a, const TH* Qh, long long ldq, const double* r, double* C, DBuf<double>& partial,
+              cudaStream_t s) {
+  if (a <= 0 || n <= 0) return;
+  const int ctiles = ceil_div(a, GS_COLS);
+  int chunks = std::max(1, std::min(ceil_div(4 * GS_GRID, ctiles), ceil_div(n, 256)));
+  // the partials live in a buffer that captured graphs also use: never grow it here
+  if (partial.n < (size_t)a) throw Error(1, "hist_dot: partial buffer smaller than the history");
+  chunks = std::min<long long>(chunks, (long long)(partial.n / a));
+  const int rows = ceil_div(n, chunks);
+  k_hist_dot<TH><<<std::min(ctiles * chunks, GS_GRID), 256, 0, s>>>(n, a, Qh, ldq, r, rows, chunks, partial.p);
+  FETIRP_LAUNCH_CHECK();
+  k_reduce_chunks<<<ceil_div(a, 256), 256, 0, s>>>(a, chunks, partial.p, C);
+  FETIRP_LAUNCH_CHECK();
+}
+template void hist_dot<double>(int, int, const double*, long long, const double*, double*, DBuf<double>&,
+                               cudaStream_t);
+template void hist_dot<float>(int, int, const float*, long long, const double*, double*, DBuf<double>&,
+                              cudaStream_t);
 
 // W[row][g] += alpha * sum_c Wh[row][c] C[c][g] over a history of `a` columns; products and sums in TH (FP32
 // history: FFMA; FP64 history: DFMA).  Grid (64-row tiles, history splits): each CTA sums its share of the

@@ -11,11 +11,12 @@ struct LocalTiles {
   int tile_off[MAXP + 1];
 };
 
-template <typename T, int BM, int BN>
+template <typename T, int BM, int BN, int BK>
 __global__ void __launch_bounds__(256) k_local_gemm(LocalTiles LT) {
-  constexpr int BK = 16, TM = BM / 16, TN = BN / 16;   // per thread: TM rows x TN right-hand sides
-  __shared__ T sa[16][BM + 1];   // S(i, j): [j][i]
-  __shared__ T sb[16][BN + 1];   // Y(j, rhs): [j][rhs]
+  constexpr int TM = BM / 16, TN = BN / 16;   // per thread: TM rows x TN right-hand sides
+  constexpr int LA = (BK * BM + 255) / 256, LB = (BK * BN + 255) / 256;
+  __shared__ T sa[BK][BM + 1];   // S(i, j): [j][i]
+  __shared__ T sb[BK][BN + 1];   // Y(j, rhs): [j][rhs]
   int p = 0;
   while (p + 1 < LT.P.n_pat && (int)blockIdx.x >= LT.tile_off[p + 1]) ++p;
   const int t = blockIdx.x - LT.tile_off[p];
@@ -28,18 +29,22 @@ __global__ void __launch_bounds__(256) k_local_gemm(LocalTiles LT) {
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;   // rows tx*TM.., rhs ty*TN..
   T acc[TM][TN] = {};
   for (int k0 = 0; k0 < nb; k0 += BK) {
-    for (int idx = tid; idx < BK * BM; idx += 256) {
+#pragma unroll
+    for (int u = 0; u < LA; ++u) {
+      const int idx = tid + 256 * u;
       const int kk = idx % BK, r = idx / BK;
       const int i = m0 + r, j = k0 + kk;
-      sa[kk][r] = (i < nb && j < nb) ? S[(size_t)i * nb + j] : T(0);
+      if (idx < BK * BM) sa[kk][r] = (i < nb && j < nb) ? S[(size_t)i * nb + j] : T(0);
     }
-    for (int idx = tid; idx < BK * BN; idx += 256) {
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int idx = tid + 256 * u;
       const int kk = idx % BK, r = idx / BK;
       const int c = n0 + r, j = k0 + kk;
-      sb[kk][r] = (c < nr && j < nb) ? Y[(long long)c * ld + j] : T(0);
+      if (idx < BK * BN) sb[kk][r] = (c < nr && j < nb) ? Y[(long long)c * ld + j] : T(0);
     }
     __syncthreads();
-#pragma unroll
+#pragma unroll 16
     for (int kk = 0; kk < BK; ++kk) {
       T av[TM], bv[TN];
 #pragma unroll
@@ -78,17 +83,20 @@ static int plan_tiles(const LocalProblem& P, LocalTiles& LT) {
   return total;
 }
 
-// 64 x 64 tiles, or 32 x 32 tiles when the 64-wide tiling would not give every SM a CTA (small problems).
+// 64 x 64 tiles (K steps of 16), or, when that tiling would not give every SM a CTA (small problems),
+// 32 x 32 or 16 x 16 tiles with K steps of 64: fewer dependent load rounds per CTA, more CTAs.
 template <typename T>
 static void launch_local(const LocalProblem& P, cudaStream_t s) {
   LocalTiles LT;
   int total = plan_tiles<T, 64, 64>(P, LT);
   if (total == 0) return;
-  if (total < 152) {
-    total = plan_tiles<T, 32, 32>(P, LT);
-    k_local_gemm<T, 32, 32><<<total, 256, 0, s>>>(LT);
+  if (total >= 152) {
+    k_local_gemm<T, 64, 64, 16><<<total, 256, 0, s>>>(LT);
+  } else if ((total = plan_tiles<T, 32, 32>(P, LT)) >= 152) {
+    k_local_gemm<T, 32, 32, 64><<<total, 256, 0, s>>>(LT);
   } else {
-    k_local_gemm<T, 64, 64><<<total, 256, 0, s>>>(LT);
+    total = plan_tiles<T, 16, 16>(P, LT);
+    k_local_gemm<T, 16, 16, 64><<<total, 256, 0, s>>>(LT);
   }
   FETIRP_LAUNCH_CHECK();
 }

@@ -83,6 +83,74 @@ struct LocalProblem {
 void local_gemm_f64(const LocalProblem& P, cudaStream_t s);
 void local_gemm_f32(const LocalProblem& P, cudaStream_t s);
 
+// ---- persistent block iteration (latency-bound structures) -------------------------------------------
+// One cooperative launch runs whole block iterations (split, Gram, projections, reorthogonalisation, F,
+// eta, normalisation, update) as nine phases separated by grid barriers, and stops on the device when
+// ||r||^2 <= target2 or no direction was kept.  Every wait is bounded (timeout_ns); an expired wait sets *err.
+struct PersistArgs {
+  Layout L;
+  int n = 0, k = 0, ncta = 0;
+  long long cap = 0;
+  // local products: S_p (n_b x n_b row-major); Y and Z one buffer each, pattern p at ybase[p], column stride ld[p]
+  const void* S[MAXP];
+  long long ybase[MAXP];
+  long long ld[MAXP];
+  int n_rhs[MAXP];
+  int tiles_m[MAXP];
+  int tile_off[MAXP + 1];
+  void* Ybuf;
+  void* Zbuf;
+  // per-row tables: multivector columns of the row's slots (-1 none), 1 / slot count, Z offsets of the slots
+  const int* row_grp;
+  const double* row_wt;
+  const long long* row_z;
+  const int* row_zld;
+  // per row and slot: first coarse column of the slot's occurrence (-1 none) and sign * Nb[j][0..6)
+  const int* rowg_gofs;
+  const double* rowg_coef;
+  // iteration vectors and the direction history (element type of the history: TH)
+  double* r;
+  double* lam;
+  double* Zr;
+  double* Q;
+  void* Wh;
+  void* Qh;
+  // Gram of the split residual
+  const int* grp_ptr;
+  const int* grp_row;
+  const double* grp_w;
+  int gs_chunks;
+  double* gram_part;
+  double* C;
+  // coarse space
+  const double* Ginv;
+  double* Xc;
+  double* Ac;
+  // history update
+  int tu_splits;
+  void* tu_part;
+  unsigned* tu_tickets;
+  // eta and the normalisation
+  double* eta_part;
+  unsigned* eta_ticket;
+  double trunc;
+  double* T;
+  double* alpha;
+  int* n_kept;
+  // update and control: state = [history columns, dropped, iterations]
+  double* rr_part;
+  int* state;
+  int max_iters;
+  double target2;
+  unsigned* bar;
+  int* err;
+  unsigned long long timeout_ns;
+  // optional (timing): nanoseconds spent by CTA 0 in each of the nine phases, barrier wait included, summed
+  unsigned long long* clk;
+};
+void persist_iterations(const PersistArgs& A, bool fp64, cudaStream_t s);
+int persist_ctas(bool fp64, int k);   // co-resident CTAs of the launch (0 if the kernel cannot be co-resident)
+
 // ---- block Gram products and the F-normalised update (numerical-issues subsection) -----------------
 // C (a x b, row-major) = A^T B, A n x a (ld lda), B n x b (ld ldb), FP64 accumulation over n in a fixed
 // order (two passes: per-chunk partials, then an ordered sum).
@@ -101,6 +169,11 @@ void gram_split(int a_max, const int* d_a, int k, const TH* Qh, long long ldq, c
                 cudaStream_t s);
 // W (n x k, FP64) += alpha * Wh (n x a, history type TH, leading dimension ldh) * C (a x k, FP64), computed
 // in TH arithmetic.
+// C[c] = sum_rows Qh[row][c] r[row] for c < a (history times one vector, FP64-class sums); partial must hold
+// at least a values (it is not grown: captured graphs share it)
+template <typename TH>
+void hist_dot(int n, int a, const TH* Qh, long long ldq, const double* r, double* C, DBuf<double>& partial,
+              cudaStream_t s);
 // scratch: split partials, tall_update_splits(n, a_max) * n * k values of TH; tickets: one counter per 64-row
 // tile, zero between calls (both grown here; callers that capture graphs size them first).
 int tall_update_splits(int n, int a_max);

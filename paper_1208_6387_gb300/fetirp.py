@@ -25,19 +25,20 @@ class fetirp_options(C.Structure):
                 ("max_outer", C.c_int32), ("inner_tol", C.c_double), ("pivot_tol", C.c_double),
                 ("eig_trunc", C.c_double), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
                 ("check_every", C.c_int32), ("timing", C.c_int32), ("eig_trunc_inner", C.c_double),
-                ("use_graphs", C.c_int32), ("timing_mask", C.c_int32), ("history_bytes", C.c_int64)]
+                ("use_graphs", C.c_int32), ("timing_mask", C.c_int32), ("history_bytes", C.c_int64),
+                ("persistent", C.c_int32)]
 
 
 PHASES = ["factor", "coarse", "local", "gather", "scatter", "project", "gram", "reorth", "update", "recover",
-          "normalise"]
+          "normalise", "iterate"]
 
 
 class fetirp_stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("outer_steps", C.c_int32), ("f_applies", C.c_int32),
                 ("dropped_directions", C.c_int32), ("kernel_dim_total", C.c_int32), ("rel_residual", C.c_double),
                 ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("launches", C.c_int64),
-                ("phase_ms", C.c_double * 11), ("phase_launches", C.c_int64 * 11),
-                ("phase_flops", C.c_double * 11), ("phase_bytes", C.c_double * 11)]
+                ("phase_ms", C.c_double * 12), ("phase_launches", C.c_int64 * 12),
+                ("phase_flops", C.c_double * 12), ("phase_bytes", C.c_double * 12)]
 
     def as_dict(self):
         d = {}
