@@ -118,6 +118,12 @@ typedef struct {
   double phase_bytes[FETIRP_NPHASE];
 } fetirp_stats;
 
+/* Test hook of the bounded device waits (the method has no counterpart): the next solve that uses the
+ * persistent iteration launches it with a grid barrier that waits for one CTA more than the grid has and a
+ * 0.2 s limit, so every wait expires; the solve returns FETIRP_ETIMEOUT and the context stays usable (the
+ * following solve runs normally).  Nothing faults or hangs: each CTA stops waiting at the limit and returns. */
+fetirp_status fetirp_inject_barrier_stall(fetirp_ctx ctx);
+
 /* Fill *opt with the defaults listed above. */
 void fetirp_default_options(fetirp_options* opt);
 

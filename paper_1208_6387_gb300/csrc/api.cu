@@ -154,12 +154,13 @@ struct fetirp_ctx_s {
   DBuf<double> d_grp_w;
   // tables of the persistent iteration: multivector columns of the row's slots, 1 / slot count, offsets of the
   // row's slots in the local product buffers (for the current k)
-  DBuf<int> d_row_grp, d_row_zld, d_rowg_gofs;
+  DBuf<int> d_row_grp, d_row_zld, d_rowg_gofs, d_rowg_kd;
   DBuf<double> d_row_wt, d_rowg_coef;
   DBuf<long long> d_row_z;
-  DBuf<unsigned> d_pbar;     // {barrier count, barrier generation, eta ticket, error flag}
+  DBuf<unsigned> d_pbar;     // {barrier count, barrier generation, eta ticket, error flag, 64 group tickets}
   DBuf<double> pers_eta, prr;
   DBuf<unsigned long long> pers_clk;   // timing: per-phase nanoseconds of the persistent iteration
+  bool inject_stall = false;           // test hook: the next persistent launch waits for a CTA that never comes
   std::vector<double> h_prr;
   DBuf<int8_t> d_slot_sign, d_row_sign;
   DBuf<long long> d_uoff;
@@ -680,7 +681,7 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
     ctx->d_row_wt.upload(row_wt, s);
     ctx->d_row_z.upload(row_z, s);
     // G restricted to the row: coarse column of each slot's occurrence and sign * Nb[j][m] (m < 6)
-    std::vector<int> rowg_gofs(2 * (size_t)nl, -1);
+    std::vector<int> rowg_gofs(2 * (size_t)nl, -1), rowg_kd(2 * (size_t)nl, 0);
     std::vector<double> rowg_coef(12 * (size_t)nl, 0.0);
     std::vector<std::vector<double>> hNb(n_pat);   // (pattern data is shared between contexts: copy locally)
     for (int p = 0; p < n_pat; ++p) {
@@ -698,11 +699,13 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
         const PatternData& P = *ctx->pats[occ_pat[o]];
         if (P.kdim > 6 || P.kdim == 0) continue;
         rowg_gofs[2 * (size_t)r + e] = occ_gofs[o];
+        rowg_kd[2 * (size_t)r + e] = P.kdim;
         for (int m = 0; m < P.kdim; ++m)
           rowg_coef[(2 * (size_t)r + e) * 6 + m] =
               row_sign[2 * (size_t)r + e] * hNb[occ_pat[o]][(size_t)(slot - obase[o]) * P.kdim + m];
       }
     ctx->d_rowg_gofs.upload(rowg_gofs, s);
+    ctx->d_rowg_kd.upload(rowg_kd, s);
     ctx->d_rowg_coef.upload(rowg_coef, s);
   }
   ctx->d_pair_s.upload(pair_s, s);
@@ -1139,6 +1142,7 @@ PersistArgs persist_args(fetirp_ctx ctx, bool fp64, TH* Wh, TH* Qh) {
     A.ld[p] = P.ld_y;
     A.n_rhs[p] = (int)ctx->use[p].occs.size() * k;
     A.S[p] = fp64 ? (const void*)P.S64.p : (const void*)P.S32.p;
+    A.pocc[p] = ctx->use[p].d_occs.p;
     total += (long long)ctx->use[p].occs.size() * k * P.ld_y;
   }
   int tiles = 0;
@@ -1156,7 +1160,7 @@ PersistArgs persist_args(fetirp_ctx ctx, bool fp64, TH* Wh, TH* Qh) {
     A.Ybuf = ctx->Y32.p; A.Zbuf = ctx->Z32.p;
   }
   A.row_grp = ctx->d_row_grp.p; A.row_wt = ctx->d_row_wt.p; A.row_z = ctx->d_row_z.p; A.row_zld = ctx->d_row_zld.p;
-  A.rowg_gofs = ctx->d_rowg_gofs.p; A.rowg_coef = ctx->d_rowg_coef.p;
+  A.rowg_gofs = ctx->d_rowg_gofs.p; A.rowg_kd = ctx->d_rowg_kd.p; A.rowg_coef = ctx->d_rowg_coef.p;
   A.r = ctx->r.p; A.lam = ctx->lam.p; A.Zr = ctx->Zr.p; A.Q = ctx->Q.p;
   A.Wh = Wh; A.Qh = Qh;
   A.grp_ptr = ctx->d_grp_ptr.p; A.grp_row = ctx->d_grp_row.p; A.grp_w = ctx->d_grp_w.p;
@@ -1167,16 +1171,22 @@ PersistArgs persist_args(fetirp_ctx ctx, bool fp64, TH* Wh, TH* Qh) {
   A.tu_splits = std::max(1, std::min(tall_update_splits(nl, (int)ctx->hist_cap), A.ncta / ceil_div(nl, 64)));
   A.tu_part = ctx->tu_part.p; A.tu_tickets = ctx->tu_tickets.p;
   const int nout = k * (k + 1);
-  ctx->pers_eta.ensure((size_t)A.ncta * nout);
+  ctx->pers_eta.ensure((size_t)(A.ncta + 64) * nout);
   ctx->prr.ensure(A.ncta);
   ctx->h_prr.assign(A.ncta, 0.0);
-  if (!ctx->d_pbar.p) ctx->d_pbar.alloc(4);
-  A.eta_part = ctx->pers_eta.p; A.eta_ticket = ctx->d_pbar.p + 2;
+  if (!ctx->d_pbar.p) ctx->d_pbar.alloc(4 + 64);
+  A.eta_part = ctx->pers_eta.p; A.eta_ticket = ctx->d_pbar.p + 2; A.eta_gticket = ctx->d_pbar.p + 4;
   A.trunc = fp64 ? ctx->opt.eig_trunc : ctx->opt.eig_trunc_inner;
   A.T = ctx->T.p; A.alpha = ctx->alpha.p; A.n_kept = ctx->n_kept.p;
   A.rr_part = ctx->prr.p; A.state = ctx->d_state.p;
   A.bar = ctx->d_pbar.p; A.err = reinterpret_cast<int*>(ctx->d_pbar.p + 3);
   A.timeout_ns = 2000000000ull;
+  A.missing = 0;
+  if (ctx->inject_stall) {   // one launch only, with a short limit
+    A.missing = 1;
+    A.timeout_ns = 200000000ull;
+    ctx->inject_stall = false;
+  }
   A.clk = nullptr;
   if (ctx->opt.timing) {
     if (!ctx->pers_clk.p) ctx->pers_clk.alloc(11);
@@ -1228,7 +1238,7 @@ double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, His
     PersistArgs A = persist_args(ctx, fp64, Wh, Qh);
     A.target2 = target * target;
     while (rnorm > target && it_budget > 0 && kept > 0) {
-      FETIRP_CUDA(cudaMemsetAsync(ctx->d_pbar.p, 0, 4 * sizeof(unsigned), s));
+      FETIRP_CUDA(cudaMemsetAsync(ctx->d_pbar.p, 0, (4 + 64) * sizeof(unsigned), s));
       FETIRP_CUDA(cudaMemsetAsync(ctx->tu_tickets.p, 0, sizeof(unsigned) * ctx->tu_tickets.n, s));
       FETIRP_CUDA(cudaMemcpyAsync(ctx->h_state + 5, ctx->d_state.p + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
       A.max_iters = it_budget;
@@ -1944,6 +1954,13 @@ fetirp_status fetirp_apply_block(fetirp_ctx ctx, int32_t k, const double* V, dou
     check_tc_error(ctx);
     FETIRP_CUDA(cudaMemcpyAsync(Q, dq.p, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
     FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
+    return FETIRP_OK;
+  });
+}
+
+fetirp_status fetirp_inject_barrier_stall(fetirp_ctx ctx) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    ctx->inject_stall = true;
     return FETIRP_OK;
   });
 }

@@ -1,5 +1,6 @@
 // Shared host/device utilities of the fetirp library (no method arithmetic here).
 #pragma once
+#include <cstdlib>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -36,6 +37,14 @@ extern thread_local unsigned long long g_launch_count;
   } while (0)
 
 // Owning device buffer (cudaMalloc / cudaFree).
+inline bool poison_allocations() {
+  static const bool on = [] {
+    const char* v = std::getenv("FETIRP_POISON");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
 template <typename T>
 struct DBuf {
   T* p = nullptr;
@@ -54,6 +63,12 @@ struct DBuf {
     release();
     if (count == 0) return;
     FETIRP_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    // FETIRP_POISON=1 (debugging and tests): fill every new allocation with NaN bytes so that a read of memory
+    // the library never wrote shows up as NaN in the results; synchronous, so no stream work overtakes it
+    if (poison_allocations()) {
+      FETIRP_CUDA(cudaMemset(p, 0xFF, count * sizeof(T)));
+      FETIRP_CUDA(cudaDeviceSynchronize());
+    }
     n = count;
   }
   // grow-only reallocation (contents not kept)

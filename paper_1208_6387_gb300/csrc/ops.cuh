@@ -100,13 +100,16 @@ struct PersistArgs {
   int tile_off[MAXP + 1];
   void* Ybuf;
   void* Zbuf;
+  const int* pocc[MAXP];      // occurrences of every pattern, in local-product column order
   // per-row tables: multivector columns of the row's slots (-1 none), 1 / slot count, Z offsets of the slots
   const int* row_grp;
   const double* row_wt;
   const long long* row_z;
   const int* row_zld;
-  // per row and slot: first coarse column of the slot's occurrence (-1 none) and sign * Nb[j][0..6)
+  // per row and slot: first coarse column of the slot's occurrence (-1 none), its kernel modes, and
+  // sign * Nb[j][0..modes)
   const int* rowg_gofs;
+  const int* rowg_kd;
   const double* rowg_coef;
   // iteration vectors and the direction history (element type of the history: TH)
   double* r;
@@ -131,8 +134,9 @@ struct PersistArgs {
   void* tu_part;
   unsigned* tu_tickets;
   // eta and the normalisation
-  double* eta_part;
+  double* eta_part;            // CTA partials, then (after ncta * k (k+1) values) group sums
   unsigned* eta_ticket;
+  unsigned* eta_gticket;       // per group of 16 CTAs
   double trunc;
   double* T;
   double* alpha;
@@ -145,6 +149,7 @@ struct PersistArgs {
   unsigned* bar;
   int* err;
   unsigned long long timeout_ns;
+  int missing;                 // CTAs a barrier waits for beyond ncta: 0 (a test sets 1 to make the waits expire)
   // optional (timing): nanoseconds spent by CTA 0 in each of the nine phases, barrier wait included, summed
   unsigned long long* clk;
 };

@@ -1,14 +1,15 @@
 // Persistent block ORTHODIR iteration for latency-bound structures (small n_lambda, k <= 32, SIMT local
 // products).  One cooperative launch runs whole iterations of Table 1 (right) with full reorthogonalisation
 // and F-normalisation; the per-kernel launch and ramp cost of the multi-kernel form (about sixteen launches
-// per iteration) is replaced by nine grid barriers.  Phases of one iteration (a = stored history columns):
-//   P1  Z = S(r) (split multivector), Gram items of C = Q_h^T S(r), X = G^T S(r) per occurrence
+// per iteration) is replaced by eight grid barriers.  Phases of one iteration (a = stored history columns):
+//   P1  Gram items of C = Q_h^T S(r) and X = G^T S(r) per occurrence (one item list), Z = S(r)
 //   P2  C = sum of the Gram chunks, A = (G^T G)^{-1} X
 //   P3  Z <- Z - G A - W_h C   (projection and reorthogonalisation, split over the history columns)
-//   P4  Y = gather(Z) per pattern         P5  Z_loc = S^+ Y (local products, all occurrences)
-//   P6  X = G^T scatter(Z_loc)            P7  A = (G^T G)^{-1} X
-//   P8  Q = scatter(Z_loc) - G A, eta partials [Z^T Q | Z^T r]; the last CTA normalises (T, alpha)
-//   P9  W_h[:, a..a+k) = Z T, Q_h[...] = Q T, lambda += Z T alpha, r -= Q T alpha, ||r||^2 partials
+//   P4  Z_loc = S^+ gather(Z) (local products of all occurrences; the gather is done while staging)
+//   P5  X = G^T scatter(Z_loc)            P6  A = (G^T G)^{-1} X
+//   P7  Q = scatter(Z_loc) - G A, eta partials [Z^T Q | Z^T r]; a two-level reduction, then the last CTA
+//       normalises (T, alpha)
+//   P8  W_h[:, a..a+k) = Z T, Q_h[...] = Q T, lambda += Z T alpha, r -= Q T alpha, ||r||^2 partials
 // The residual test runs on the device at the start of every iteration.  Data written by other CTAs is read
 // after a barrier through L2 only: this file is compiled with -Xptxas -dlcm=cg, and no loads of mutable
 // data use the non-coherent path.  Every barrier wait is bounded by A.timeout_ns (globaltimer); an expired
@@ -22,7 +23,7 @@ namespace fetirp {
 namespace {
 
 constexpr int PT = 256;                      // threads per CTA
-constexpr int P_GS_ROWS = 128, P_GS_COLS = 64;
+constexpr int P_GS_ROWS = 128;
 constexpr int P_TU_ROWS = 64, P_TU_CH = 32;
 constexpr int P_GTV_COLS = 8, P_MAXKD = 6;
 constexpr int P_LT = 16, P_LK = 64;          // local products: 16 x 16 output tiles, K steps of 64
@@ -46,7 +47,7 @@ __device__ bool grid_sync(const PersistArgs& A) {
     const unsigned g = *gen;
     __threadfence();
     const unsigned prev = atomicAdd(A.bar, 1u);
-    if (prev == (unsigned)A.ncta - 1) {
+    if (prev == (unsigned)(A.ncta + A.missing) - 1) {
       atomicExch(A.bar, 0u);
       __threadfence();
       atomicAdd(A.bar + 1, 1u);
@@ -102,143 +103,177 @@ __device__ __forceinline__ double gapply(const PersistArgs& A, int row, int g) {
   for (int e = 0; e < 2; ++e) {
     const int g0 = A.rowg_gofs[2 * row + e];
     if (g0 < 0) continue;
+    const int kd = A.rowg_kd[2 * row + e];   // only the occurrence's own coarse rows of A are read
     const double* c = A.rowg_coef + (size_t)(2 * row + e) * P_MAXKD;
     const double* a = A.Ac + (size_t)g0 * k + g;
     double t = 0.0;
 #pragma unroll
-    for (int m = 0; m < P_MAXKD; ++m) t = fma(c[m], a[(size_t)m * k], t);
+    for (int m = 0; m < P_MAXKD; ++m)
+      if (m < kd) t = fma(c[m], a[(size_t)m * k], t);
     acc += t;
   }
   return acc;
 }
 
 // X[gofs(s)+m][g] = sum over the slots j of s: Nb[j][m] * y(j, g), y the trace of V on the slot's links, where
-// V is S(r) (from_split) or scatter(Z_loc).  Items: (occurrence, 8 columns); per item the threads split the
-// slots and the per-thread sums are added in a fixed order (deterministic).
+// V is S(r) (from_split) or scatter(Z_loc).  Item: (occurrence, 8 columns); the threads split the slots and the
+// per-thread sums are added in a fixed order (deterministic).
 template <typename TL, bool from_split>
-__device__ void phase_gtv(const PersistArgs& A, unsigned char* smem) {
+__device__ void gtv_item(const PersistArgs& A, int it, unsigned char* smem) {
   const Layout& L = A.L;
   const int k = A.k;
   double (*red)[P_MAXKD] = reinterpret_cast<double (*)[P_MAXKD]>(smem);
   const int cgroups = (k + P_GTV_COLS - 1) / P_GTV_COLS;
-  const int items = L.n_occ * cgroups;
   const int t = threadIdx.x;
-  for (int it = blockIdx.x; it < items; it += A.ncta) {
-    const int s = it / cgroups, gbase = (it % cgroups) * P_GTV_COLS;
-    const int p = L.occ_pat[s];
-    const int kd = L.kdim[p];
-    const double* Nb = L.Nb[p];
-    const int b0 = L.occ_obase[s], nb = L.occ_obase[s + 1] - b0;
-    const int g0 = L.occ_gofs[s];
-    const int kk = min(P_GTV_COLS, k - gbase);
-    const int lanes = PT / kk;
-    const int g = gbase + t % kk, sub = t / kk;
-    double acc[P_MAXKD] = {};
-    if (sub < lanes) {
-      for (int j = sub; j < nb; j += lanes) {
-        const int slot = b0 + j;
-        double y = 0.0;
-        for (int e = 0; e < L.ell_w; ++e) {
-          const int sg = L.ell_sign[(size_t)slot * L.ell_w + e];
-          if (sg == 0) continue;
-          const int row = L.ell_row[(size_t)slot * L.ell_w + e];
-          const double v = from_split ? split_val(A, row, g) : qraw<TL>(A, row, g);
-          y = fma((double)sg, v, y);
-        }
-#pragma unroll
-        for (int m = 0; m < P_MAXKD; ++m)
-          if (m < kd) acc[m] = fma(Nb[(size_t)j * kd + m], y, acc[m]);
+  const int s = it / cgroups, gbase = (it % cgroups) * P_GTV_COLS;
+  const int p = L.occ_pat[s];
+  const int kd = L.kdim[p];
+  const double* Nb = L.Nb[p];
+  const int b0 = L.occ_obase[s], nb = L.occ_obase[s + 1] - b0;
+  const int g0 = L.occ_gofs[s];
+  const int kk = min(P_GTV_COLS, k - gbase);
+  const int lanes = PT / kk;
+  const int g = gbase + t % kk, sub = t / kk;
+  double acc[P_MAXKD] = {};
+  if (sub < lanes) {
+    for (int j = sub; j < nb; j += lanes) {
+      const int slot = b0 + j;
+      double y = 0.0;
+      for (int e = 0; e < L.ell_w; ++e) {
+        const int sg = L.ell_sign[(size_t)slot * L.ell_w + e];
+        if (sg == 0) continue;
+        const int row = L.ell_row[(size_t)slot * L.ell_w + e];
+        const double v = from_split ? split_val(A, row, g) : qraw<TL>(A, row, g);
+        y = fma((double)sg, v, y);
       }
+#pragma unroll
+      for (int m = 0; m < P_MAXKD; ++m)
+        if (m < kd) acc[m] = fma(Nb[(size_t)j * kd + m], y, acc[m]);
     }
-    __syncthreads();   // the previous item's reads of red are done
+  }
+  __syncthreads();   // the previous item's reads of the shared buffer are done
 #pragma unroll
-    for (int m = 0; m < P_MAXKD; ++m) red[t][m] = acc[m];
-    __syncthreads();
-    if (t < kk) {
-      for (int m = 0; m < kd; ++m) {
-        double v = 0.0;
-        for (int q = 0; q < lanes; ++q) v += red[q * kk + t][m];
-        A.Xc[(size_t)(g0 + m) * k + gbase + t] = v;
+  for (int m = 0; m < P_MAXKD; ++m) red[t][m] = acc[m];
+  __syncthreads();
+  if (t < kk) {
+    for (int m = 0; m < kd; ++m) {
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      int q = 0;
+      for (; q + 3 < lanes; q += 4) {
+        v0 += red[q * kk + t][m];
+        v1 += red[(q + 1) * kk + t][m];
+        v2 += red[(q + 2) * kk + t][m];
+        v3 += red[(q + 3) * kk + t][m];
       }
+      for (; q < lanes; ++q) v0 += red[q * kk + t][m];
+      A.Xc[(size_t)(g0 + m) * k + gbase + t] = (v0 + v1) + (v2 + v3);
     }
   }
 }
 
-// C partials of Q_h^T S(r) (as the stand-alone split Gram: items (64 columns, group, 128-row chunk))
+template <typename TL, bool from_split>
+__device__ void phase_gtv(const PersistArgs& A, unsigned char* smem) {
+  const int items = A.L.n_occ * ((A.k + P_GTV_COLS - 1) / P_GTV_COLS);
+  for (int it = blockIdx.x; it < items; it += A.ncta) gtv_item<TL, from_split>(A, it, smem);
+}
+
+// C partials of Q_h^T S(r).  Item: (128 history columns, group, 128-row chunk); the chunk's (row, w r[row]) pairs
+// are staged in shared memory, the 8 warps take every 8th row, each lane four columns, the warp sums are added
+// in warp order (deterministic); FP32 history: double-single sums on the FP32 pipe (see the split Gram kernel).
+constexpr int P_GC = 128;
 template <typename TH>
-__device__ void phase_gram(const PersistArgs& A, int a, unsigned char* smem) {
-  if (a <= 0) return;
+__device__ void gram_item(const PersistArgs& A, int a, int it, unsigned char* smem) {
   int* srow = reinterpret_cast<int*>(smem);
   double* sw = reinterpret_cast<double*>(smem + 512);
   float* swh = reinterpret_cast<float*>(smem + 512 + 1024);
   float* swl = swh + P_GS_ROWS;
-  double (*red)[P_GS_COLS] = reinterpret_cast<double (*)[P_GS_COLS]>(smem + 512 + 1024 + 1024);
+  double (*red)[P_GC] = reinterpret_cast<double (*)[P_GC]>(smem + 512 + 1024 + 1024);
   const TH* Qh = (const TH*)A.Qh;
   const long long ldq = A.cap;
   const int k = A.k;
-  const int ctiles = (a + P_GS_COLS - 1) / P_GS_COLS;
-  const int items = ctiles * k * A.gs_chunks;
+  const int ctiles = (a + P_GC - 1) / P_GC;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int it = blockIdx.x; it < items; it += A.ncta) {
-    const int ct = it % ctiles, rest = it / ctiles, g = rest % k, ch = rest / k;
-    const int e0 = A.grp_ptr[g] + ch * P_GS_ROWS, e1 = min(A.grp_ptr[g + 1], e0 + P_GS_ROWS);
-    const int cnt = max(0, e1 - e0);
-    __syncthreads();
-    if (tid < cnt) {
-      const int row = A.grp_row[e0 + tid];
-      const double v = A.grp_w[e0 + tid] * A.r[row];
-      srow[tid] = row;
-      sw[tid] = v;
-      const float vh = (float)v;
-      swh[tid] = vh;
-      swl[tid] = (float)(v - (double)vh);
-    }
-    __syncthreads();
-    const int c0 = ct * P_GS_COLS + lane, c1 = c0 + 32;
-    const bool ok0 = c0 < a, ok1 = c1 < a;
-    double a0 = 0.0, a1 = 0.0;
-    if (sizeof(TH) == 4) {   // double-single sums on the FP32 pipe (see the stand-alone split Gram)
-      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-#pragma unroll 8
-      for (int i = warp; i < cnt; i += 8) {
-        const TH* q = Qh + (size_t)srow[i] * ldq;
-        const float sh = swh[i], sl = swl[i];
-        const float q0 = ok0 ? (float)q[c0] : 0.f;
-        const float q1 = ok1 ? (float)q[c1] : 0.f;
-        {
-          const float pp = __fmul_rn(q0, sh), e = fmaf(q0, sh, -pp), tt = fmaf(q0, sl, e);
-          const float u = __fadd_rn(h0, pp), bb = __fsub_rn(u, h0);
-          l0 = __fadd_rn(l0, __fadd_rn(__fadd_rn(__fsub_rn(h0, __fsub_rn(u, bb)), __fsub_rn(pp, bb)), tt));
-          h0 = u;
-        }
-        {
-          const float pp = __fmul_rn(q1, sh), e = fmaf(q1, sh, -pp), tt = fmaf(q1, sl, e);
-          const float u = __fadd_rn(h1, pp), bb = __fsub_rn(u, h1);
-          l1 = __fadd_rn(l1, __fadd_rn(__fadd_rn(__fsub_rn(h1, __fsub_rn(u, bb)), __fsub_rn(pp, bb)), tt));
-          h1 = u;
-        }
-      }
-      a0 = (double)h0 + (double)l0;
-      a1 = (double)h1 + (double)l1;
-    } else {
-#pragma unroll 8
-      for (int i = warp; i < cnt; i += 8) {
-        const TH* q = Qh + (size_t)srow[i] * ldq;
-        const double wv = sw[i];
-        a0 = fma(wv, ok0 ? (double)q[c0] : 0.0, a0);
-        a1 = fma(wv, ok1 ? (double)q[c1] : 0.0, a1);
-      }
-    }
-    red[warp][lane] = a0;
-    red[warp][lane + 32] = a1;
-    __syncthreads();
-    if (tid < P_GS_COLS) {
-      const int c = ct * P_GS_COLS + tid;
-      double v = 0.0;
+  const int ct = it % ctiles, rest = it / ctiles, g = rest % k, ch = rest / k;
+  const int e0 = A.grp_ptr[g] + ch * P_GS_ROWS, e1 = min(A.grp_ptr[g + 1], e0 + P_GS_ROWS);
+  const int cnt = max(0, e1 - e0);
+  __syncthreads();
+  if (tid < cnt) {
+    const int row = A.grp_row[e0 + tid];
+    const double v = A.grp_w[e0 + tid] * A.r[row];
+    srow[tid] = row;
+    sw[tid] = v;
+    const float vh = (float)v;
+    swh[tid] = vh;
+    swl[tid] = (float)(v - (double)vh);
+  }
+  __syncthreads();
+  int c[4];
+  bool ok[4];
 #pragma unroll
-      for (int w = 0; w < 8; ++w) v += red[w][tid];
-      if (c < a) A.gram_part[((size_t)ch * a + c) * k + g] = v;
+  for (int u = 0; u < 4; ++u) {
+    c[u] = ct * P_GC + lane + 32 * u;
+    ok[u] = c[u] < a;
+  }
+  double res[4];
+  if (sizeof(TH) == 4) {
+    float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int i = warp; i < cnt; i += 8) {
+      const TH* q = Qh + (size_t)srow[i] * ldq;
+      const float sh = swh[i], sl = swl[i];
+      float qv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) qv[u] = ok[u] ? (float)q[c[u]] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float pp = __fmul_rn(qv[u], sh), e = fmaf(qv[u], sh, -pp), tt = fmaf(qv[u], sl, e);
+        const float uu = __fadd_rn(h[u], pp), bb = __fsub_rn(uu, h[u]);
+        l[u] = __fadd_rn(l[u], __fadd_rn(__fadd_rn(__fsub_rn(h[u], __fsub_rn(uu, bb)), __fsub_rn(pp, bb)), tt));
+        h[u] = uu;
+      }
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) res[u] = (double)h[u] + (double)l[u];
+  } else {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (int i = warp; i < cnt; i += 8) {
+      const TH* q = Qh + (size_t)srow[i] * ldq;
+      const double wv = sw[i];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = fma(wv, ok[u] ? (double)q[c[u]] : 0.0, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) res[u] = acc[u];
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) red[warp][lane + 32 * u] = res[u];
+  __syncthreads();
+  if (tid < P_GC) {
+    const int cc = ct * P_GC + tid;
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) v += red[w][tid];
+    if (cc < a) A.gram_part[((size_t)ch * a + cc) * k + g] = v;
+  }
+}
+
+// P1: the Gram items and the G^T S(r) items as one list (balanced over the CTAs), then Z = S(r)
+template <typename TH, typename TL>
+__device__ void phase_one(const PersistArgs& A, int a, unsigned char* smem) {
+  const int n_gtv = A.L.n_G > 0 ? A.L.n_occ * ((A.k + P_GTV_COLS - 1) / P_GTV_COLS) : 0;
+  const int n_gram = a > 0 ? ((a + P_GC - 1) / P_GC) * A.k * A.gs_chunks : 0;
+  for (int it = blockIdx.x; it < n_gtv + n_gram; it += A.ncta) {
+    if (it < n_gtv) gtv_item<TL, true>(A, it, smem);
+    else gram_item<TH>(A, a, it - n_gtv, smem);
+  }
+  for (int row = blockIdx.x * PT + threadIdx.x; row < A.n; row += A.ncta * PT) {
+    double* z = A.Zr + (size_t)row * A.k;
+    for (int g = 0; g < A.k; ++g) z[g] = 0.0;
+    const int g0 = A.row_grp[2 * row], g1 = A.row_grp[2 * row + 1];
+    const double w = A.r[row] * A.row_wt[row];
+    if (g0 >= 0) z[g0] += w;
+    if (g1 >= 0) z[g1] += w;
   }
 }
 
@@ -399,53 +434,36 @@ __device__ void phase_tall(const PersistArgs& A, int a, unsigned char* smem) {
   }
 }
 
-// Y = gather(Z) (Eq. 7 blocked storage): items (occurrence, 8 columns)
-template <typename TL>
-__device__ void phase_gather(const PersistArgs& A) {
-  const Layout& L = A.L;
-  const int k = A.k;
-  TL* Y = (TL*)A.Ybuf;
-  const int cgroups = (k + P_GTV_COLS - 1) / P_GTV_COLS;
-  const int items = L.n_occ * cgroups;
-  for (int it = blockIdx.x; it < items; it += A.ncta) {
-    const int s = it / cgroups, gbase = (it % cgroups) * P_GTV_COLS;
-    const int p = L.occ_pat[s], q = L.occ_q[s];
-    const int b0 = L.occ_obase[s], nb = L.occ_obase[s + 1] - b0;
-    const int kk = min(P_GTV_COLS, k - gbase);
-    for (int idx = threadIdx.x; idx < nb * kk; idx += PT) {
-      const int g = gbase + idx / nb, j = idx % nb;
-      const int slot = b0 + j;
-      double y = 0.0;
-      for (int e = 0; e < L.ell_w; ++e) {
-        const int sg = L.ell_sign[(size_t)slot * L.ell_w + e];
-        if (sg == 0) continue;
-        y = fma((double)sg, A.Zr[(size_t)L.ell_row[(size_t)slot * L.ell_w + e] * k + g], y);
-      }
-      Y[A.ybase[p] + ((long long)q * k + g) * A.ld[p] + j] = (TL)y;
-    }
-  }
-}
-
-// Z_loc = S^+ Y for every pattern: 16 x 16 output tiles, K staged 64 at a time
+// Z_loc = S^+ Y for every pattern: 16 x 16 output tiles, K staged 64 at a time.  Y is not stored: the staged
+// right-hand-side entries are the gather of Z (Eq. 7) computed on the fly, y(slot, g) = sum over the slot's
+// links of sign * Z[row][g] (the same sum, in the same order, as a separate gather).
 template <typename TL>
 __device__ void phase_local(const PersistArgs& A, unsigned char* smem) {
   TL (*sa)[P_LT + 1] = reinterpret_cast<TL (*)[P_LT + 1]>(smem);
   TL (*sb)[P_LT + 1] = reinterpret_cast<TL (*)[P_LT + 1]>(smem + sizeof(TL) * P_LK * (P_LT + 1));
-  const int n_pat = A.L.n_pat;
+  int* cslot = reinterpret_cast<int*>(smem + 2 * sizeof(TL) * P_LK * (P_LT + 1));   // [16] first slot, -1 none
+  int* ccol = cslot + P_LT;                                                         // [16] multivector column
+  const Layout& L = A.L;
+  const int n_pat = L.n_pat;
+  const int k = A.k;
   const int items = A.tile_off[n_pat];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const TL* Ybuf = (const TL*)A.Ybuf;
   TL* Zbuf = (TL*)A.Zbuf;
   for (int it = blockIdx.x; it < items; it += A.ncta) {
     int p = 0;
     while (p + 1 < n_pat && it >= A.tile_off[p + 1]) ++p;
     const int t = it - A.tile_off[p];
     const int m0 = (t % A.tiles_m[p]) * P_LT, n0 = (t / A.tiles_m[p]) * P_LT;
-    const int nb = A.L.n_b[p], nr = A.n_rhs[p];
+    const int nb = L.n_b[p], nr = A.n_rhs[p];
     const long long ld = A.ld[p];
     const TL* S = (const TL*)A.S[p];
-    const TL* Y = Ybuf + A.ybase[p];
     TL* Z = Zbuf + A.ybase[p];
+    __syncthreads();   // the previous item's shared-memory reads are done
+    if (tid < P_LT) {
+      const int c = n0 + tid;
+      cslot[tid] = c < nr ? L.occ_obase[A.pocc[p][c / k]] : -1;
+      ccol[tid] = c % k;
+    }
     TL acc = TL(0);
     for (int k0 = 0; k0 < nb; k0 += P_LK) {
       __syncthreads();
@@ -455,8 +473,18 @@ __device__ void phase_local(const PersistArgs& A, unsigned char* smem) {
         const int kk = idx % P_LK, r = idx / P_LK;
         const int i = m0 + r, j = k0 + kk;
         sa[kk][r] = (i < nb && j < nb) ? S[(size_t)i * nb + j] : TL(0);
-        const int c = n0 + r;
-        sb[kk][r] = (c < nr && j < nb) ? Y[(long long)c * ld + j] : TL(0);
+        TL yv = TL(0);
+        if (cslot[r] >= 0 && j < nb) {
+          const int slot = cslot[r] + j, g = ccol[r];
+          double y = 0.0;
+          for (int e = 0; e < L.ell_w; ++e) {
+            const int sg = L.ell_sign[(size_t)slot * L.ell_w + e];
+            if (sg == 0) continue;
+            y = fma((double)sg, A.Zr[(size_t)L.ell_row[(size_t)slot * L.ell_w + e] * k + g], y);
+          }
+          yv = (TL)y;
+        }
+        sb[kk][r] = yv;
       }
       __syncthreads();
 #pragma unroll 16
@@ -515,11 +543,37 @@ __device__ void phase_q_eta(const PersistArgs& A, unsigned char* smem) {
     const int o = q * PT + tid;
     if (o < nout) A.eta_part[(size_t)blockIdx.x * nout + o] = acc[q];
   }
+  // two-level reduction of the CTA partials, in a fixed order whichever CTAs perform it: the last CTA of every
+  // group of 16 adds its group's partials, the last group reducer adds the group sums and normalises
+  __threadfence();
+  __syncthreads();
+  constexpr int GSZ = 16;
+  const int grp = blockIdx.x / GSZ, ng = (A.ncta + GSZ - 1) / GSZ;
+  const int gsize = min(GSZ, A.ncta - grp * GSZ);
+  if (tid == 0) {
+    const unsigned prev = atomicAdd(&A.eta_gticket[grp], 1u);
+    *s_last = prev == (unsigned)gsize - 1;
+    if (*s_last) A.eta_gticket[grp] = 0u;
+  }
+  __syncthreads();
+  if (!*s_last) return;
+  __threadfence();
+  double* gpart = A.eta_part + (size_t)A.ncta * nout;
+  for (int o = tid; o < nout; o += PT) {
+    double u[GSZ];
+#pragma unroll
+    for (int q = 0; q < GSZ; ++q) u[q] = q < gsize ? A.eta_part[(size_t)(grp * GSZ + q) * nout + o] : 0.0;
+#pragma unroll
+    for (int w = GSZ / 2; w > 0; w >>= 1)
+#pragma unroll
+      for (int q = 0; q < w; ++q) u[q] += u[q + w];
+    gpart[(size_t)grp * nout + o] = u[0];
+  }
   __threadfence();
   __syncthreads();
   if (tid == 0) {
     const unsigned prev = atomicAdd(A.eta_ticket, 1u);
-    *s_last = prev == (unsigned)A.ncta - 1;
+    *s_last = prev == (unsigned)ng - 1;
     if (*s_last) *A.eta_ticket = 0u;
   }
   __syncthreads();
@@ -527,40 +581,26 @@ __device__ void phase_q_eta(const PersistArgs& A, unsigned char* smem) {
   __threadfence();
   const bool stamp = A.clk && tid == 0;
   const unsigned long long t0 = stamp ? gtimer() : 0ull;
-  // the last CTA: eta and W^T r from the CTA partials (fixed order), then the one-warp normalisation
+  // the last group reducer: eta and W^T r from the group sums, then the one-warp normalisation
   double (*Am)[33] = reinterpret_cast<double (*)[33]>(smem);                       // [32][33]
   double (*Lc)[33] = reinterpret_cast<double (*)[33]>(smem + 32 * 33 * 8);         // [32][33]
   int* piv = reinterpret_cast<int*>(smem + 2 * 32 * 33 * 8);
   double* Dg = reinterpret_cast<double*>(smem + 2 * 32 * 33 * 8 + 32 * 4);
   double* rhs = Dg + 32;
   double* ext = &Lc[0][0];
-  {   // all threads: output o, every groups-th CTA partial, 16 independent loads per round; then the groups
-    const int groups = max(1, PT / nout);
-    double* red = &Am[0][0];   // groups * nout <= PT partial sums
-    for (int t = tid; t < groups * nout; t += PT) {
-      const int o = t % nout, g = t / nout;
-      double v = 0.0;
-      for (int c = g; c < A.ncta; c += 16 * groups) {
-        double u[16];
+  for (int o = tid; o < nout; o += PT) {
+    double v = 0.0;
+    for (int g = 0; g < ng; g += GSZ) {
+      double u[GSZ];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int cc = c + q * groups;
-          u[q] = cc < A.ncta ? A.eta_part[(size_t)cc * nout + o] : 0.0;
-        }
+      for (int q = 0; q < GSZ; ++q) u[q] = g + q < ng ? gpart[(size_t)(g + q) * nout + o] : 0.0;
 #pragma unroll
-        for (int w = 8; w > 0; w >>= 1)
+      for (int w = GSZ / 2; w > 0; w >>= 1)
 #pragma unroll
-          for (int q = 0; q < w; ++q) u[q] += u[q + w];
-        v += u[0];
-      }
-      red[t] = v;
+        for (int q = 0; q < w; ++q) u[q] += u[q + w];
+      v += u[0];
     }
-    __syncthreads();
-    for (int o = tid; o < nout; o += PT) {
-      double v = 0.0;
-      for (int g = 0; g < groups; ++g) v += red[g * nout + o];
-      ext[o] = v;
-    }
+    ext[o] = v;
   }
   __syncthreads();
   for (int idx = tid; idx < k * k; idx += PT) {
@@ -678,18 +718,7 @@ __global__ void __launch_bounds__(PT) k_persist(PersistArgs A) {
       if (!s_go) return;
     }
     const int a = A.state[0];
-    phase_gram<TH>(A, a, smem);
-    {   // P1 also: Z = S(r) and X = G^T S(r)
-      for (int row = blockIdx.x * PT + threadIdx.x; row < A.n; row += A.ncta * PT) {
-        double* z = A.Zr + (size_t)row * A.k;
-        for (int g = 0; g < A.k; ++g) z[g] = 0.0;
-        const int g0 = A.row_grp[2 * row], g1 = A.row_grp[2 * row + 1];
-        const double w = A.r[row] * A.row_wt[row];
-        if (g0 >= 0) z[g0] += w;
-        if (g1 >= 0) z[g1] += w;
-      }
-      if (A.L.n_G > 0) phase_gtv<TL, true>(A, smem);
-    }
+    phase_one<TH, TL>(A, a, smem);   // P1
     if (!phase_end(0)) return;
     // P2
     if (a > 0) {
@@ -711,9 +740,7 @@ __global__ void __launch_bounds__(PT) k_persist(PersistArgs A) {
     if (!phase_end(1)) return;
     phase_tall<TH, KP>(A, a, smem);   // P3
     if (!phase_end(2)) return;
-    phase_gather<TL>(A);              // P4
-    if (!phase_end(3)) return;
-    phase_local<TL>(A, smem);         // P5
+    phase_local<TL>(A, smem);         // P4 + P5: gather fused into the local products
     if (!phase_end(4)) return;
     if (A.L.n_G > 0) phase_gtv<TL, false>(A, smem);   // P6
     if (!phase_end(5)) return;

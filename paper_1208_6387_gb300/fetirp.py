@@ -91,6 +91,7 @@ _SIGS = {
     "fetirp_apply_block_device_noalloc": (C.c_int, [P, C.c_int32, P, P, C.c_int32]),
     "fetirp_prepare": (C.c_int, [P, C.c_int64, P]),
     "fetirp_factorize": (C.c_int, [P]),
+    "fetirp_inject_barrier_stall": (C.c_int, [P]),
     "fetirp_get_pattern": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), P, P]),
 }
 
@@ -311,6 +312,11 @@ def fetirp_apply_block_device_noalloc(ctx, k, V_ptr, Q_ptr, precision=FETIRP_PRE
 
 def fetirp_factorize(ctx):
     _check(ctx, lib().fetirp_factorize(ctx))
+
+
+def fetirp_inject_barrier_stall(ctx):
+    """Test hook: the next persistent launch waits for a CTA that never arrives (0.2 s limit) -> ETIMEOUT."""
+    _check(ctx, lib().fetirp_inject_barrier_stall(ctx))
 
 
 def fetirp_get_pattern(ctx, pattern_id, n_dofs=None):

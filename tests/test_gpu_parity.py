@@ -94,6 +94,45 @@ def test_solve_matches_direct(name, prec):
         assert st["outer_steps"] >= 1
 
 
+@pytest.mark.parametrize("name", ["c1", "heat_rot_ragged", "elastic_2x2x1", "c2"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_persistent_and_graph_paths_agree(name, prec):
+    """The persistent cooperative iteration (the default at these sizes) and the per-phase CUDA-graph path both
+    reproduce the direct solve; the graph path reads the residual every 4 iterations, so it may run a few more."""
+    prob = config("c2") if name == "c2" else CASES[name]()
+    us_ref, lam_ref, _, _ = direct(prob)
+    its = {}
+    for pers in (0, 1):
+        ctx = make_ctx(prob, precision=prec, tol=1e-12, inner_tol=1e-5, persistent=pers, timing=1)
+        try:
+            lam, u, st = F.fetirp_solve(ctx, prob.n_lambda, prob.c, F.n_u(prob))
+        finally:
+            F.fetirp_destroy(ctx)
+        assert rel(lam, lam_ref) < 1e-8, (pers, st)
+        for a, b in zip(F.split_u(prob, u), us_ref):
+            assert rel(a, b) < 1e-8
+        its[pers] = st["iterations"]
+        iterate_ms = st["phase_ms"][F.PHASES.index("iterate")]
+        assert (iterate_ms > 0) == (pers == 1)
+    assert abs(its[1] - its[0]) <= 4 * 8, its
+
+
+def test_bounded_barrier_wait_expires_and_context_recovers():
+    """A persistent launch whose grid barrier waits for a CTA that never arrives returns FETIRP_ETIMEOUT after
+    its time limit (no hang, no fault), and the same context then solves normally."""
+    prob = config("c1")
+    ctx = make_ctx(prob, tol=1e-10)
+    try:
+        F.fetirp_inject_barrier_stall(ctx)
+        with pytest.raises(F.FetirpError) as e:
+            F.fetirp_solve(ctx, prob.n_lambda, prob.c, F.n_u(prob))
+        assert e.value.status == F.FETIRP_ETIMEOUT
+        lam, u, st = F.fetirp_solve(ctx, prob.n_lambda, prob.c, F.n_u(prob))
+        assert st["rel_residual"] <= 1e-10
+    finally:
+        F.fetirp_destroy(ctx)
+
+
 def test_classical_k1_and_block_agree():
     """k = 1 is classical FETI-CG; block k = n_occ converges in no more iterations (convergence cannot be
     deteriorated) and both reach the same lambda."""
