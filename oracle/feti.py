@@ -93,7 +93,7 @@ class FetiOracle:
         self.nz = [N.shape[1] for N in self.Ns]
         self.GtG = self.G.T @ self.G
         self.GtG_inv = np.linalg.inv(self.GtG)
-        # multiplicity scaling Delta(s) (Eq. 5 scaling, sum_s Delta(s) = I) restricted to lambda rows
+        # multiplicity scaling Delta(s) (the diagonal scaling of Eqs. 4-5, sum_s Delta(s) = I) restricted to lambda rows
         inc = np.zeros((prob.n_lambda, prob.n_occ))
         for o, occ in enumerate(prob.occs):
             inc[occ.link_lambda_row, o] = 1.0

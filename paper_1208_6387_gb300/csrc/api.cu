@@ -814,7 +814,7 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
 }
 
 // ----------------------------------------------------------------------------------------- operators
-// V <- P V = V - G (G^T G)^{-1} G^T V (Eq. 4), FP64 throughout: with the rigid modes of elasticity G^T G is
+// V <- P V = V - G (G^T G)^{-1} G^T V (Eq. 6), FP64 throughout: with the rigid modes of elasticity G^T G is
 // ill-conditioned enough that FP32 products leave G-components that make the inner operator nonsymmetric.
 void project(fetirp_ctx ctx, double* V, int k) {
   if (ctx->n_G == 0) return;

@@ -1,5 +1,5 @@
 // Interface operators of one structure: the signed Boolean gather/scatter (Eq. 2, blocked storage of
-// Eq. 7), the coarse space G = [B(s) N(s)] of Eq. 3 and the multivector split.
+// Eq. 9), the coarse space G = [B(s) N(s)] of Eq. 3 and the multivector split.
 #include "ops.cuh"
 
 namespace fetirp {

@@ -52,7 +52,7 @@ void g_apply(const Layout& L, const double* A, int k, double alpha, double beta,
 void gtg_dense(const Layout& L, const int* nb_ptr, const int* nb_list, int n_pairs, const int* pair_s,
                const int* pair_t, double* GtG, cudaStream_t s);
 
-// ---- gather / scatter (Eq. 7 blocked storage, signed Boolean assembly) -------------------------------
+// ---- gather / scatter (Eq. 9 blocked storage, signed Boolean assembly) -------------------------------
 // Y[(q * k + g) * ld + off + j] = beta * Y[...] + alpha * sum over links of slot (s, j): sign * V[row][g]
 template <typename TO>
 void gather(const Layout& L, const double* V, int k, const PatView<TO>& Y, cudaStream_t s, double alpha = 1.0,

@@ -435,7 +435,7 @@ __device__ void phase_tall(const PersistArgs& A, int a, unsigned char* smem) {
 }
 
 // Z_loc = S^+ Y for every pattern: 16 x 16 output tiles, K staged 64 at a time.  Y is not stored: the staged
-// right-hand-side entries are the gather of Z (Eq. 7) computed on the fly, y(slot, g) = sum over the slot's
+// right-hand-side entries are the gather of Z (Eq. 9) computed on the fly, y(slot, g) = sum over the slot's
 // links of sign * Z[row][g] (the same sum, in the same order, as a separate gather).
 template <typename TL>
 __device__ void phase_local(const PersistArgs& A, unsigned char* smem) {

@@ -134,8 +134,8 @@ def test_bounded_barrier_wait_expires_and_context_recovers():
 
 
 def test_classical_k1_and_block_agree():
-    """k = 1 is classical FETI-CG; block k = n_occ converges in no more iterations (convergence cannot be
-    deteriorated) and both reach the same lambda."""
+    """k = 1 is classical FETI-CG; block k = n_occ needs no more iterations (the classical direction lies in
+    the block span, Section 3.1) and both reach the same lambda."""
     prob = config("c1")
     out = {}
     for k in (1, 4):

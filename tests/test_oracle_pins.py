@@ -185,8 +185,9 @@ def test_PtFP_symmetric_psd_and_choice_of_inverse():
 
 
 def test_multivector_invariants_and_iterations():
-    """Convergence cannot be deteriorated (the CG direction stays in the block span): block iterations
-    <= classical iterations; directions are F-orthonormal across blocks and lie in ker(G^T)."""
+    """The block form is never slower than classical CG (the CG direction stays in the block span, Section
+    3.1): block iterations <= classical iterations; directions are F-orthonormal across blocks and lie in
+    ker(G^T)."""
     for p in (config("c1"), heat_grid(4, (4, 2), kappas=(1.0, 50.0), checker=True, k=4), config("c3r")):
         o = FetiOracle(p)
         _, it_cg, _ = o.classical_cg(1e-10)
