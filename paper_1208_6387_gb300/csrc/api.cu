@@ -1000,13 +1000,13 @@ void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
   }
   {
     PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 0.0, 0.0);
-    gram_split<TH>((int)cap, d_cols, k, Qh, cap, ctx->r.p, ctx->d_grp_ptr.p, ctx->d_grp_row.p, ctx->d_grp_w.p,
+    gram_split<TH>((int)cap, d_cols, k, Qh, nl, k, ctx->r.p, ctx->d_grp_ptr.p, ctx->d_grp_row.p, ctx->d_grp_w.p,
                    ctx->max_group_rows, ctx->C.p, ctx->gram_part, s);
   }
   project(ctx, ctx->Zr.p, k);
   {
     PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 0.0, 0.0);
-    tall_update<TH>(nl, (int)cap, d_cols, k, Wh, cap, ctx->C.p, -1.0, ctx->Zr.p, ctx->tu_part, ctx->tu_tickets, s);
+    tall_update<TH>(nl, (int)cap, d_cols, k, Wh, k, ctx->C.p, -1.0, ctx->Zr.p, ctx->tu_part, ctx->tu_tickets, s);
   }
   apply_F(ctx, ctx->Zr.p, ctx->Q.p, k, prec, false, true);   // P~ = P^T F W (Table 1 line 5.1)
   {
@@ -1025,7 +1025,7 @@ void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
     adv.cols = d_cols; adv.k = k; adv.cap = cap; adv.n_kept = ctx->n_kept.p;
     adv.dropped = ctx->d_state.p + 1; adv.iters = ctx->d_state.p + 2;
     adv.counter = reinterpret_cast<unsigned*>(ctx->d_state.p + 3);
-    update<TH>(nl, k, ctx->Zr.p, ctx->Q.p, ctx->T.p, ctx->alpha.p, Wh, Qh, d_cols, cap, ctx->lam.p, ctx->r.p,
+    update<TH>(nl, k, ctx->Zr.p, ctx->Q.p, ctx->T.p, ctx->alpha.p, Wh, Qh, d_cols, ctx->lam.p, ctx->r.p,
                ctx->rr_part.p, ctx->rr_blocks, s, adv);
   }
 }
@@ -1216,12 +1216,12 @@ double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, His
     const int a = (int)H.cols;
     {
       PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 2.0 * nl * a, nl * (es * a + 8.0));
-      hist_dot<TH>(nl, a, Wh, cap, ctx->r.p, ctx->C.p, ctx->gram_part, s);
+      hist_dot<TH>(nl, a, Wh, k, ctx->r.p, ctx->C.p, ctx->gram_part, s);
     }
     {
       PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 4.0 * nl * a, 2.0 * es * nl * a + 32.0 * nl);
-      tall_update<TH>(nl, a, nullptr, 1, Wh, cap, ctx->C.p, 1.0, ctx->lam.p, ctx->tu_part, ctx->tu_tickets, s);
-      tall_update<TH>(nl, a, nullptr, 1, Qh, cap, ctx->C.p, -1.0, ctx->r.p, ctx->tu_part, ctx->tu_tickets, s);
+      tall_update<TH>(nl, a, nullptr, 1, Wh, k, ctx->C.p, 1.0, ctx->lam.p, ctx->tu_part, ctx->tu_tickets, s);
+      tall_update<TH>(nl, a, nullptr, 1, Qh, k, ctx->C.p, -1.0, ctx->r.p, ctx->tu_part, ctx->tu_tickets, s);
     }
     rnorm = norm2(ctx, ctx->r.p, nl);
   }

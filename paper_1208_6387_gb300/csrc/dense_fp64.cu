@@ -56,17 +56,19 @@ __global__ void k_zero_zp_rows(double* A, int npad, const int* zp) {
 }
 
 // Factor the diagonal tile k in place (one CTA, 256 threads).  Square-root-free inside the loop (a dependent
-// FP64 divide costs ~450 cycles and a square root ~700 on this GPU): step j takes only the reciprocal of the
-// pivot, the trailing update uses the unscaled column (a_rc -= a_rj a_cj / d_j, the same products as the
-// square-root form), and every column is scaled by 1 / sqrt(d_j) once at the end, in parallel, giving
-// L = L_unit D^{1/2}.  Zero pivots (d_j <= tol * diag0_j, or not finite) get a zero column as before.
+// FP64 divide costs ~450 cycles and a square root ~700 on this GPU): step j scales the remaining column by the
+// pivot's reciprocal (multipliers l_r = a_rj / d_j), the trailing update is one FMA per entry with the unscaled
+// column, a_rc -= l_r a_cj, and every column is scaled by 1 / sqrt(d_j) once at the end, in parallel, giving
+// L = L_unit D^{1/2}.  One step of lookahead: thread 0 updates the next diagonal entry first and forms its
+// reciprocal while the other threads finish the update.  Zero pivots (d_j <= tol * diag0_j, or not finite) get
+// a zero multiplier column (no update) and a zero column of L.
 __global__ void __launch_bounds__(256) k_potrf_tile(double* A, int npad, int k, const double* diag0, int* zp,
                                                     double tol) {
   __shared__ double a[TILE][TILE + 1];   // a[row][col]
   __shared__ double thr[TILE];           // tol * diag0 of the tile's dofs
-  __shared__ double rsq[TILE];           // 1 / sqrt(d_j), 0 for zero pivots
+  __shared__ double dd[TILE];            // pivots d_j (0 for zero pivots), then 1 / sqrt(d_j)
+  __shared__ double lcol[TILE];          // multipliers of the current step
   __shared__ double s_rinv;
-  __shared__ int s_zero;
   const int tid = threadIdx.x;
   double* T = A + (size_t)k * TILE * npad + (size_t)k * TILE;
   for (int idx = tid; idx < TILE * TILE; idx += 256) {
@@ -75,35 +77,42 @@ __global__ void __launch_bounds__(256) k_potrf_tile(double* A, int npad, int k, 
   }
   if (tid < TILE) thr[tid] = tol * diag0[k * TILE + tid];
   __syncthreads();
-  for (int j = 0; j < TILE; ++j) {
-    if (tid == 0) {
-      const double d = a[j][j];
-      const bool zero = !(d > thr[j]);   // also catches NaN and negative roundoff
-      s_zero = zero ? 1 : 0;
-      s_rinv = zero ? 0.0 : 1.0 / d;
-      rsq[j] = zero ? 0.0 : d;          // d_j for now; 1 / sqrt(d_j) after the loop
-    }
+  if (tid == 0) {
+    const double d = a[0][0];
+    const bool zero = !(d > thr[0]);   // also catches NaN and negative roundoff
+    dd[0] = zero ? 0.0 : d;
+    s_rinv = zero ? 0.0 : 1.0 / d;
+  }
+  __syncthreads();
+  const int rr = tid % TILE, cg = tid / TILE;   // update: row rr, columns j+1+cg, j+5+cg, ...
+  for (int j = 0; j + 1 < TILE; ++j) {
+    const double rinv = s_rinv;
+    for (int r = j + 1 + tid; r < TILE; r += 256) lcol[r] = a[r][j] * rinv;
     __syncthreads();
-    if (!s_zero) {
-      const double rinv = s_rinv;
-      const int w = TILE - 1 - j;        // trailing columns j+1 .. TILE-1, rows >= column
-      for (int idx = tid; idx < w * TILE; idx += 256) {
-        int c = j + 1 + idx / TILE, r = idx % TILE;
-        if (r >= c) a[r][c] -= (a[r][j] * a[c][j]) * rinv;
-      }
+    if (tid == 0) {   // lookahead: the next pivot and its reciprocal
+      const double d = fma(-lcol[j + 1], a[j + 1][j], a[j + 1][j + 1]);
+      a[j + 1][j + 1] = d;
+      const bool zero = !(d > thr[j + 1]);
+      dd[j + 1] = zero ? 0.0 : d;
+      s_rinv = zero ? 0.0 : 1.0 / d;
+    }
+    if (rr > j) {
+      const double lr = lcol[rr];
+      for (int c = j + 1 + cg; c <= rr; c += 4)
+        if (c != j + 1 || rr != j + 1) a[rr][c] = fma(-lr, a[c][j], a[rr][c]);
     }
     __syncthreads();
   }
   if (tid < TILE) {
     const int gj = k * TILE + tid;
-    const double d = rsq[tid];
+    const double d = dd[tid];
     zp[gj] = d > 0.0 ? 0 : 1;
-    rsq[tid] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+    dd[tid] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
   }
   __syncthreads();
   for (int idx = tid; idx < TILE * TILE; idx += 256) {
     int r = idx % TILE, c = idx / TILE;
-    T[(size_t)c * npad + r] = (r >= c) ? a[r][c] * rsq[c] : 0.0;
+    T[(size_t)c * npad + r] = (r >= c) ? a[r][c] * dd[c] : 0.0;
   }
 }
 

@@ -262,14 +262,15 @@ __global__ void __launch_bounds__(512) k_normalise(int k, const double* __restri
 }
 
 // Wn = W T, Qn = Q T, lambda += W (T alpha), r -= Q (T alpha); per-CTA partial sums of the new r^2.
-// A warp takes 32 / kp rows at once (kp = k rounded up to a power of two), one lane per column: every element
-// of W and Q is loaded and converted once, and row j of the block is broadcast by shuffles.  For k > 32 a lane
-// holds two columns.  The history (Wn, Qn) is stored in TH; T is rounded to TH once per CTA.
+// History: a warp takes 32 / kp rows at once (kp = k rounded up to a power of two), one lane per column:
+// every element of W and Q is converted once and row j of the block is broadcast by shuffles (TH arithmetic;
+// for k > 32 a lane holds two columns).  lambda and r: one thread per row, FP64 dot products with T alpha
+// (a reduction across lanes would cost several times the FP64 operations, and FP64 is the scarce pipe).
 template <typename TH>
 __global__ void __launch_bounds__(256) k_update(int n, int k, const double* __restrict__ W,
                                                 const double* __restrict__ Q, const double* __restrict__ T,
                                                 const double* __restrict__ alpha, TH* __restrict__ Wn,
-                                                TH* __restrict__ Qn, const int* __restrict__ d_off, long long ldn,
+                                                TH* __restrict__ Qn, const int* __restrict__ d_off,
                                                 double* __restrict__ lam,
                                                 double* __restrict__ r, double* __restrict__ rr_partial,
                                                 AdvanceArgs adv) {
@@ -290,16 +291,15 @@ __global__ void __launch_bounds__(256) k_update(int n, int k, const double* __re
   const int seg = kp >= 32 ? 32 : kp;                  // lanes per row
   const int sub = lane / seg, c0 = lane % seg;
   const bool two = k > 32;                             // second column c0 + 32
-  const long long off = d_off ? (long long)*d_off : 0;
-  double rr = 0.0;
+  const long long off = d_off ? (long long)*d_off : 0;   // a multiple of k: the new block of the history
+  const size_t blk = hist_col(off, n, k);
   const long long stride = (long long)gridDim.x * 8 * rows_w;
   for (long long base = ((long long)blockIdx.x * 8 + warp) * rows_w; base < n; base += stride) {
     const long long row = base + sub;
     const bool ok = row < n;
     const bool v0 = ok && c0 < k, v1 = two && ok && c0 + 32 < k;
-    const double w0 = v0 ? W[row * k + c0] : 0.0, q0 = v0 ? Q[row * k + c0] : 0.0;
-    const double w1 = v1 ? W[row * k + c0 + 32] : 0.0, q1 = v1 ? Q[row * k + c0 + 32] : 0.0;
-    const TH w0h = (TH)w0, q0h = (TH)q0, w1h = (TH)w1, q1h = (TH)q1;
+    const TH w0h = v0 ? (TH)W[row * k + c0] : TH(0), q0h = v0 ? (TH)Q[row * k + c0] : TH(0);
+    const TH w1h = v1 ? (TH)W[row * k + c0 + 32] : TH(0), q1h = v1 ? (TH)Q[row * k + c0 + 32] : TH(0);
     TH wn0 = TH(0), qn0 = TH(0), wn1 = TH(0), qn1 = TH(0);
     const int ca = c0 < k ? c0 : 0, cb = c0 + 32 < k ? c0 + 32 : 0;
     for (int j = 0; j < k; ++j) {
@@ -314,28 +314,34 @@ __global__ void __launch_bounds__(256) k_update(int n, int k, const double* __re
       }
     }
     if (v0) {
-      Wn[row * ldn + off + c0] = wn0;
-      Qn[row * ldn + off + c0] = qn0;
+      Wn[blk + row * k + c0] = wn0;
+      Qn[blk + row * k + c0] = qn0;
     }
     if (v1) {
-      Wn[row * ldn + off + c0 + 32] = wn1;
-      Qn[row * ldn + off + c0 + 32] = qn1;
+      Wn[blk + row * k + c0 + 32] = wn1;
+      Qn[blk + row * k + c0 + 32] = qn1;
     }
-    double dl = v0 ? w0 * beta[c0] : 0.0, dr = v0 ? q0 * beta[c0] : 0.0;
-    if (v1) {
-      dl = fma(w1, beta[c0 + 32], dl);
-      dr = fma(q1, beta[c0 + 32], dr);
+  }
+  double rr = 0.0;
+  for (long long row = (long long)blockIdx.x * blockDim.x + tid; row < n; row += (long long)gridDim.x * blockDim.x) {
+    const double* w = W + row * k;
+    const double* q = Q + row * k;
+    double l0 = 0.0, l1 = 0.0, d0 = 0.0, d1 = 0.0;
+    int c = 0;
+    for (; c + 1 < k; c += 2) {
+      l0 = fma(w[c], beta[c], l0);
+      l1 = fma(w[c + 1], beta[c + 1], l1);
+      d0 = fma(q[c], beta[c], d0);
+      d1 = fma(q[c + 1], beta[c + 1], d1);
     }
-    for (int o = seg >> 1; o > 0; o >>= 1) {
-      dl += __shfl_xor_sync(0xffffffffu, dl, o);
-      dr += __shfl_xor_sync(0xffffffffu, dr, o);
+    if (c < k) {
+      l0 = fma(w[c], beta[c], l0);
+      d0 = fma(q[c], beta[c], d0);
     }
-    if (ok && c0 == 0) {
-      lam[row] += dl;
-      const double rn = r[row] - dr;
-      r[row] = rn;
-      rr = fma(rn, rn, rr);
-    }
+    lam[row] += l0 + l1;
+    const double rn = r[row] - (d0 + d1);
+    r[row] = rn;
+    rr = fma(rn, rn, rr);
   }
   for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
   if (lane == 0) warp_rr[warp] = rr;
@@ -425,7 +431,8 @@ __global__ void k_reduce_chunks_warp(int count, int chunks, const double* __rest
   if (lane == 0) C[o] = v;
 }
 
-int eta_chunks(int n) { return std::max(1, std::min(152, ceil_div(n, 16))); }
+// up to four chunks per SM (the sums are FP64-pipe bound: more resident warps keep the pipe busy)
+int eta_chunks(int n) { return std::max(1, std::min(608, ceil_div(n, 256))); }
 
 void eta_partials(int n, int k, const double* W, const double* Q, const double* r, DBuf<double>& partial,
                   cudaStream_t s) {
@@ -488,16 +495,15 @@ void normalise(int k, const double* ext_partial, int chunks, double trunc, doubl
 
 template <typename TH>
 void update(int n, int k, const double* W, const double* Q, const double* T, const double* alpha, TH* Wn, TH* Qn,
-            const int* d_off, long long ldn, double* lam, double* r, double* rr_partial, int rr_blocks,
+            const int* d_off, double* lam, double* r, double* rr_partial, int rr_blocks,
             cudaStream_t s, const AdvanceArgs& adv) {
-  k_update<TH><<<rr_blocks, 256, 0, s>>>(n, k, W, Q, T, alpha, Wn, Qn, d_off, ldn, lam, r, rr_partial, adv);
+  k_update<TH><<<rr_blocks, 256, 0, s>>>(n, k, W, Q, T, alpha, Wn, Qn, d_off, lam, r, rr_partial, adv);
   FETIRP_LAUNCH_CHECK();
 }
 template void update<double>(int, int, const double*, const double*, const double*, const double*, double*,
-                             double*, const int*, long long, double*, double*, double*, int, cudaStream_t,
-                             const AdvanceArgs&);
+                             double*, const int*, double*, double*, double*, int, cudaStream_t, const AdvanceArgs&);
 template void update<float>(int, int, const double*, const double*, const double*, const double*, float*, float*,
-                            const int*, long long, double*, double*, double*, int, cudaStream_t, const AdvanceArgs&);
+                            const int*, double*, double*, double*, int, cudaStream_t, const AdvanceArgs&);
 
 // C[c][g] = sum over the rows of group g: w(row) * r[row] * Qh[row][c]  (= Qh^T S(r), the split multivector
 // S(r) having at most two nonzero groups per row).  Work items (64-column tile, group, 128-row chunk) are
@@ -510,10 +516,10 @@ constexpr int GS_COLS = 64;    // history columns per item
 constexpr int GS_GRID = 608;   // 4 CTAs per SM
 template <typename TH>
 __global__ void __launch_bounds__(256) k_gram_split(int a_max, const int* __restrict__ d_a, int k,
-                                                    const TH* __restrict__ Qh, long long ldq,
+                                                    const TH* __restrict__ Qh, int n, int hk,
                                                     const double* __restrict__ r, const int* __restrict__ grp_ptr,
                                                     const int* __restrict__ grp_row, const double* __restrict__ grp_w,
-                                                    int chunks, double* __restrict__ partial) {
+                                                    int chunks, int rows_per_chunk, double* __restrict__ partial) {
   __shared__ int srow[GS_ROWS];
   __shared__ double sw[GS_ROWS];
   __shared__ float swh[GS_ROWS], swl[GS_ROWS];   // w r[row] split into FP32 hi + lo (FP32 history)
@@ -525,60 +531,67 @@ __global__ void __launch_bounds__(256) k_gram_split(int a_max, const int* __rest
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int ct = it % ctiles, rest = it / ctiles, g = rest % k, ch = rest / k;
-    const int e0 = grp_ptr[g] + ch * GS_ROWS, e1 = min(grp_ptr[g + 1], e0 + GS_ROWS);
-    const int cnt = max(0, e1 - e0);
-    __syncthreads();   // the previous item's shared-memory reads are done
-    if (tid < cnt) {
-      const int row = grp_row[e0 + tid];
-      const double v = grp_w[e0 + tid] * r[row];
-      srow[tid] = row;
-      sw[tid] = v;
-      const float vh = (float)v;
-      swh[tid] = vh;
-      swl[tid] = (float)(v - (double)vh);
-    }
-    __syncthreads();
+    const int e0 = grp_ptr[g] + ch * rows_per_chunk, e_end = min(grp_ptr[g + 1], e0 + rows_per_chunk);
     const int c0 = ct * GS_COLS + lane, c1 = c0 + 32;
     const bool ok0 = c0 < a, ok1 = c1 < a;
+    const TH* q0p = Qh + hist_col(ok0 ? c0 : 0, n, hk);
+    const TH* q1p = Qh + hist_col(ok1 ? c1 : 0, n, hk);
     double a0 = 0.0, a1 = 0.0;
-    if (sizeof(TH) == 4) {
-      // FP32 history: double-single arithmetic on the FP32 pipe (Dekker 1971; Knuth TwoSum).  q * s_hi is
-      // split exactly into p + e by an FMA, q * s_lo is rounded (its error is ~2^-48 |q s|), and each column
-      // sum is an unevaluated pair (hi, lo) updated by TwoSum; FP64 converts only the pairs at the end.  The
-      // _rn intrinsics keep the compiler from contracting the error-free transformations into FMAs.
-      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-#pragma unroll 8
-      for (int i = warp; i < cnt; i += 8) {
-        const TH* q = Qh + (size_t)srow[i] * ldq;
-        const float sh = swh[i], sl = swl[i];
-        const float q0 = ok0 ? (float)q[c0] : 0.f;
-        const float q1 = ok1 ? (float)q[c1] : 0.f;
-        {
-          const float p = __fmul_rn(q0, sh), e = fmaf(q0, sh, -p), t = fmaf(q0, sl, e);
-          const float u = __fadd_rn(h0, p), bb = __fsub_rn(u, h0);
-          l0 = __fadd_rn(l0, __fadd_rn(__fadd_rn(__fsub_rn(h0, __fsub_rn(u, bb)), __fsub_rn(p, bb)), t));
-          h0 = u;
-        }
-        {
-          const float p = __fmul_rn(q1, sh), e = fmaf(q1, sh, -p), t = fmaf(q1, sl, e);
-          const float u = __fadd_rn(h1, p), bb = __fsub_rn(u, h1);
-          l1 = __fadd_rn(l1, __fadd_rn(__fadd_rn(__fsub_rn(h1, __fsub_rn(u, bb)), __fsub_rn(p, bb)), t));
-          h1 = u;
-        }
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    for (int sb = e0; sb < e_end; sb += GS_ROWS) {   // the chunk in stages of GS_ROWS rows
+      const int cnt = min(GS_ROWS, e_end - sb);
+      __syncthreads();   // the previous stage's (or item's) shared-memory reads are done
+      if (tid < cnt) {
+        const int row = grp_row[sb + tid];
+        const double v = grp_w[sb + tid] * r[row];
+        srow[tid] = row;
+        sw[tid] = v;
+        const float vh = (float)v;
+        swh[tid] = vh;
+        swl[tid] = (float)(v - (double)vh);
       }
-      a0 = (double)h0 + (double)l0;
-      a1 = (double)h1 + (double)l1;
-    } else {
-#pragma unroll 8
-      for (int i = warp; i < cnt; i += 8) {
-        const TH* q = Qh + (size_t)srow[i] * ldq;
-        const double wv = sw[i];
-        const double q0 = ok0 ? (double)q[c0] : 0.0;
-        const double q1 = ok1 ? (double)q[c1] : 0.0;
-        a0 = fma(wv, q0, a0);
-        a1 = fma(wv, q1, a1);
+      __syncthreads();
+      if (sizeof(TH) == 4) {
+        // FP32 history: double-single arithmetic on the FP32 pipe (Dekker 1971; Knuth TwoSum).  q * s_hi is
+        // split exactly into p + e by an FMA, q * s_lo is rounded (its error is ~2^-48 |q s|), and each column
+        // sum is an unevaluated pair (hi, lo) updated by TwoSum; FP64 converts only the pairs at the end.  The
+        // _rn intrinsics keep the compiler from contracting the error-free transformations into FMAs.
+  #pragma unroll 8
+        for (int i = warp; i < cnt; i += 8) {
+          const size_t ro = (size_t)srow[i] * hk;
+          const float sh = swh[i], sl = swl[i];
+          const float q0 = ok0 ? (float)q0p[ro] : 0.f;
+          const float q1 = ok1 ? (float)q1p[ro] : 0.f;
+          {
+            const float p = __fmul_rn(q0, sh), e = fmaf(q0, sh, -p), t = fmaf(q0, sl, e);
+            const float u = __fadd_rn(h0, p), bb = __fsub_rn(u, h0);
+            l0 = __fadd_rn(l0, __fadd_rn(__fadd_rn(__fsub_rn(h0, __fsub_rn(u, bb)), __fsub_rn(p, bb)), t));
+            h0 = u;
+          }
+          {
+            const float p = __fmul_rn(q1, sh), e = fmaf(q1, sh, -p), t = fmaf(q1, sl, e);
+            const float u = __fadd_rn(h1, p), bb = __fsub_rn(u, h1);
+            l1 = __fadd_rn(l1, __fadd_rn(__fadd_rn(__fsub_rn(h1, __fsub_rn(u, bb)), __fsub_rn(p, bb)), t));
+            h1 = u;
+          }
+        }
+      } else {
+  #pragma unroll 8
+        for (int i = warp; i < cnt; i += 8) {
+          const size_t ro = (size_t)srow[i] * hk;
+          const double wv = sw[i];
+          const double q0 = ok0 ? (double)q0p[ro] : 0.0;
+          const double q1 = ok1 ? (double)q1p[ro] : 0.0;
+          a0 = fma(wv, q0, a0);
+          a1 = fma(wv, q1, a1);
+        }
       }
     }
+    if (sizeof(TH) == 4) {
+      a0 = (double)h0 + (double)l0;
+      a1 = (double)h1 + (double)l1;
+    }
+    __syncthreads();   // an item with an empty chunk has no stage barrier before this
     red[warp][lane] = a0;
     red[warp][lane + 32] = a1;
     __syncthreads();
@@ -596,7 +609,7 @@ __global__ void __launch_bounds__(256) k_gram_split(int a_max, const int* __rest
 // loop and arithmetic as k_gram_split, with rows_per_chunk-row chunks staged 256 rows at a time; the chunk
 // partials (chunk-major, a per chunk) are added in chunk order by k_reduce_chunks.
 template <typename TH>
-__global__ void __launch_bounds__(256) k_hist_dot(int n, int a, const TH* __restrict__ Qh, long long ldq,
+__global__ void __launch_bounds__(256) k_hist_dot(int n, int a, const TH* __restrict__ Qh, int hk,
                                                   const double* __restrict__ r, int rows_per_chunk, int chunks,
                                                   double* __restrict__ partial) {
   __shared__ double sr[256];
@@ -610,6 +623,8 @@ __global__ void __launch_bounds__(256) k_hist_dot(int n, int a, const TH* __rest
     const int r0 = ch * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
     const int c0 = ct * GS_COLS + lane, c1 = c0 + 32;
     const bool ok0 = c0 < a, ok1 = c1 < a;
+    const TH* q0p = Qh + hist_col(ok0 ? c0 : 0, n, hk);
+    const TH* q1p = Qh + hist_col(ok1 ? c1 : 0, n, hk);
     double a0 = 0.0, a1 = 0.0;
     float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
     for (int sb = r0; sb < r1; sb += 256) {
@@ -626,10 +641,10 @@ __global__ void __launch_bounds__(256) k_hist_dot(int n, int a, const TH* __rest
       if (sizeof(TH) == 4) {
 #pragma unroll 8
         for (int i = warp; i < cnt; i += 8) {
-          const TH* q = Qh + (size_t)(sb + i) * ldq;
+          const size_t ro = (size_t)(sb + i) * hk;
           const float sh = srh[i], sl = srl[i];
-          const float q0 = ok0 ? (float)q[c0] : 0.f;
-          const float q1 = ok1 ? (float)q[c1] : 0.f;
+          const float q0 = ok0 ? (float)q0p[ro] : 0.f;
+          const float q1 = ok1 ? (float)q1p[ro] : 0.f;
           {
             const float p = __fmul_rn(q0, sh), e = fmaf(q0, sh, -p), t = fmaf(q0, sl, e);
             const float u = __fadd_rn(h0, p), bb = __fsub_rn(u, h0);
@@ -646,10 +661,10 @@ __global__ void __launch_bounds__(256) k_hist_dot(int n, int a, const TH* __rest
       } else {
 #pragma unroll 8
         for (int i = warp; i < cnt; i += 8) {
-          const TH* q = Qh + (size_t)(sb + i) * ldq;
+          const size_t ro = (size_t)(sb + i) * hk;
           const double wv = sr[i];
-          a0 = fma(wv, ok0 ? (double)q[c0] : 0.0, a0);
-          a1 = fma(wv, ok1 ? (double)q[c1] : 0.0, a1);
+          a0 = fma(wv, ok0 ? (double)q0p[ro] : 0.0, a0);
+          a1 = fma(wv, ok1 ? (double)q1p[ro] : 0.0, a1);
         }
       }
     }
@@ -683,26 +698,28 @@ __global__ void k_reduce_chunks_dyn(int a_max, const int* __restrict__ d_a, int 
 }
 
 template <typename TH>
-void gram_split(int a_max, const int* d_a, int k, const TH* Qh, long long ldq, const double* r, const int* grp_ptr,
+void gram_split(int a_max, const int* d_a, int k, const TH* Qh, int n, int hk, const double* r, const int* grp_ptr,
                 const int* grp_row, const double* grp_w, int max_group_rows, double* C, DBuf<double>& partial,
                 cudaStream_t s) {
   if (a_max <= 0) return;
-  const int chunks = std::max(1, ceil_div(max_group_rows, GS_ROWS));
+  // large groups: 512-row chunks (fewer items and partials), walked in 128-row stages
+  const int rows_per_chunk = max_group_rows > 8192 ? 4 * GS_ROWS : GS_ROWS;
+  const int chunks = std::max(1, ceil_div(max_group_rows, rows_per_chunk));
   partial.ensure((size_t)chunks * a_max * k);
   const int items = ceil_div(a_max, GS_COLS) * k * chunks;
-  k_gram_split<TH><<<std::min(items, GS_GRID), 256, 0, s>>>(a_max, d_a, k, Qh, ldq, r, grp_ptr, grp_row, grp_w,
-                                                             chunks, partial.p);
+  k_gram_split<TH><<<std::min(items, GS_GRID), 256, 0, s>>>(a_max, d_a, k, Qh, n, hk, r, grp_ptr, grp_row, grp_w,
+                                                             chunks, rows_per_chunk, partial.p);
   FETIRP_LAUNCH_CHECK();
   k_reduce_chunks_dyn<<<ceil_div(a_max * k, 256), 256, 0, s>>>(a_max, d_a, k, chunks, partial.p, C);
   FETIRP_LAUNCH_CHECK();
 }
-template void gram_split<double>(int, const int*, int, const double*, long long, const double*, const int*,
+template void gram_split<double>(int, const int*, int, const double*, int, int, const double*, const int*,
                                  const int*, const double*, int, double*, DBuf<double>&, cudaStream_t);
-template void gram_split<float>(int, const int*, int, const float*, long long, const double*, const int*, const int*,
+template void gram_split<float>(int, const int*, int, const float*, int, int, const double*, const int*, const int*,
                                 const double*, int, double*, DBuf<double>&, cudaStream_t);
 
 template <typename TH>
-void hist_dot(int n, int a, const TH* Qh, long long ldq, const double* r, double* C, DBuf<double>& partial,
+void hist_dot(int n, int a, const TH* Qh, int hk, const double* r, double* C, DBuf<double>& partial,
               cudaStream_t s) {
   if (a <= 0 || n <= 0) return;
   const int ctiles = ceil_div(a, GS_COLS);
@@ -711,15 +728,13 @@ void hist_dot(int n, int a, const TH* Qh, long long ldq, const double* r, double
   if (partial.n < (size_t)a) throw Error(1, "hist_dot: partial buffer smaller than the history");
   chunks = std::min<long long>(chunks, (long long)(partial.n / a));
   const int rows = ceil_div(n, chunks);
-  k_hist_dot<TH><<<std::min(ctiles * chunks, GS_GRID), 256, 0, s>>>(n, a, Qh, ldq, r, rows, chunks, partial.p);
+  k_hist_dot<TH><<<std::min(ctiles * chunks, GS_GRID), 256, 0, s>>>(n, a, Qh, hk, r, rows, chunks, partial.p);
   FETIRP_LAUNCH_CHECK();
   k_reduce_chunks<<<ceil_div(a, 256), 256, 0, s>>>(a, chunks, partial.p, C);
   FETIRP_LAUNCH_CHECK();
 }
-template void hist_dot<double>(int, int, const double*, long long, const double*, double*, DBuf<double>&,
-                               cudaStream_t);
-template void hist_dot<float>(int, int, const float*, long long, const double*, double*, DBuf<double>&,
-                              cudaStream_t);
+template void hist_dot<double>(int, int, const double*, int, const double*, double*, DBuf<double>&, cudaStream_t);
+template void hist_dot<float>(int, int, const float*, int, const double*, double*, DBuf<double>&, cudaStream_t);
 
 // W[row][g] += alpha * sum_c Wh[row][c] C[c][g] over a history of `a` columns; products and sums in TH (FP32
 // history: FFMA; FP64 history: DFMA).  Grid (64-row tiles, history splits): each CTA sums its share of the
@@ -730,7 +745,7 @@ template void hist_dot<float>(int, int, const float*, long long, const double*, 
 constexpr int TU_ROWS = 64, TU_CH = 32;
 template <typename TH, int KP>
 __global__ void __launch_bounds__(256) k_tall_update(int n, int a_max, const int* __restrict__ d_a, int k,
-                                                     const TH* __restrict__ Wh, long long ldh,
+                                                     const TH* __restrict__ Wh, int hk,
                                                      const double* __restrict__ C, int splits, TH* __restrict__ part,
                                                      unsigned* __restrict__ tickets, double alpha,
                                                      double* __restrict__ W) {
@@ -752,10 +767,13 @@ __global__ void __launch_bounds__(256) k_tall_update(int n, int a_max, const int
   TH acc[RPT][CPT] = {};
   TH pa[LA], pc[LC];
   auto load = [&](int c0) {
+    const int cc = tid % TU_CH;   // the same history column for all of the thread's loads
+    const bool okc = c0 + cc < c_end;
+    const TH* col = Wh + hist_col(okc ? c0 + cc : 0, n, hk);
 #pragma unroll
     for (int i = 0; i < LA; ++i) {
-      const int idx = tid + 256 * i, cc = idx % TU_CH, rr = idx / TU_CH;
-      pa[i] = (r0 + rr < n && c0 + cc < c_end) ? Wh[(size_t)(r0 + rr) * ldh + c0 + cc] : TH(0);
+      const int rr = (tid + 256 * i) / TU_CH;
+      pa[i] = (r0 + rr < n && okc) ? col[(size_t)(r0 + rr) * hk] : TH(0);
     }
 #pragma unroll
     for (int i = 0; i < LC; ++i) {
@@ -843,7 +861,7 @@ int tall_update_splits(int n, int a_max) {
 }
 
 template <typename TH>
-void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, long long ldh, const double* C, double alpha,
+void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, int hk, const double* C, double alpha,
                  double* W, DBuf<double>& scratch, DBuf<unsigned>& tickets, cudaStream_t s) {
   if (a_max <= 0 || n <= 0) return;
   if (k > 64) throw Error(1, "k > 64");
@@ -858,18 +876,18 @@ void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, long lon
   TH* part = reinterpret_cast<TH*>(scratch.p);
   const dim3 grid(tiles, splits);
   if (k <= 8)
-    k_tall_update<TH, 8><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, ldh, C, splits, part, tickets.p, alpha, W);
+    k_tall_update<TH, 8><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, hk, C, splits, part, tickets.p, alpha, W);
   else if (k <= 16)
-    k_tall_update<TH, 16><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, ldh, C, splits, part, tickets.p, alpha, W);
+    k_tall_update<TH, 16><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, hk, C, splits, part, tickets.p, alpha, W);
   else if (k <= 32)
-    k_tall_update<TH, 32><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, ldh, C, splits, part, tickets.p, alpha, W);
+    k_tall_update<TH, 32><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, hk, C, splits, part, tickets.p, alpha, W);
   else
-    k_tall_update<TH, 64><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, ldh, C, splits, part, tickets.p, alpha, W);
+    k_tall_update<TH, 64><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, hk, C, splits, part, tickets.p, alpha, W);
   FETIRP_LAUNCH_CHECK();
 }
-template void tall_update<double>(int, int, const int*, int, const double*, long long, const double*, double,
-                                  double*, DBuf<double>&, DBuf<unsigned>&, cudaStream_t);
-template void tall_update<float>(int, int, const int*, int, const float*, long long, const double*, double, double*,
+template void tall_update<double>(int, int, const int*, int, const double*, int, const double*, double, double*,
+                                  DBuf<double>&, DBuf<unsigned>&, cudaStream_t);
+template void tall_update<float>(int, int, const int*, int, const float*, int, const double*, double, double*,
                                  DBuf<double>&, DBuf<unsigned>&, cudaStream_t);
 
 // End of a block iteration: history count += k (restart when the next block would not fit), dropped

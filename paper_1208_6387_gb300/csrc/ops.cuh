@@ -83,6 +83,15 @@ struct LocalProblem {
 void local_gemm_f64(const LocalProblem& P, cudaStream_t s);
 void local_gemm_f32(const LocalProblem& P, cudaStream_t s);
 
+// ---- direction history layout ----------------------------------------------------------------------
+// The stored directions W_h, Q_h (n rows, `cap` columns) are kept in blocks of hk columns, one block per block
+// iteration: each block is n x hk, row-major and contiguous.  Writing a block is one contiguous stream and a
+// row tile of a block is one contiguous piece (a row-major n x cap array would put every row of a large
+// structure on its own page).  Column c of row `row` is at hist_col(c, n, hk) + row * hk.
+__host__ __device__ __forceinline__ size_t hist_col(long long c, long long n, int hk) {
+  return (size_t)(c / hk) * (size_t)n * (size_t)hk + (size_t)(c % hk);
+}
+
 // ---- persistent block iteration (latency-bound structures) -------------------------------------------
 // One cooperative launch runs whole block iterations (split, Gram, projections, reorthogonalisation, F,
 // eta, normalisation, update) as nine phases separated by grid barriers, and stops on the device when
@@ -165,25 +174,26 @@ template <typename TA, typename TB>
 void gram(int n, int a, int b, const TA* A, int lda, const TB* B, int ldb, double* C, DBuf<double>& partial,
           cudaStream_t s);
 // Reorthogonalisation coefficients C = Qh^T S(r) (a x k, row-major) of the split multivector S(r) without
-// forming it: group g's rows (grp_ptr/grp_row) with weights grp_w = 1/(occurrences of the row).  FP64 sums.
-// The number of stored directions a is read from d_a on the device when d_a != NULL (at most a_max), so one
-// captured launch serves every iteration.
+// forming it: group g's rows (grp_ptr/grp_row) with weights grp_w = 1/(occurrences of the row).  FP64 sums
+// (double-single for an FP32 history).  Qh: n rows in the block layout of width hk (hist_col).  The number of
+// stored directions a is read from d_a on the device when d_a != NULL (at most a_max), so one captured launch
+// serves every iteration.
 template <typename TH>
-void gram_split(int a_max, const int* d_a, int k, const TH* Qh, long long ldq, const double* r, const int* grp_ptr,
+void gram_split(int a_max, const int* d_a, int k, const TH* Qh, int n, int hk, const double* r, const int* grp_ptr,
                 const int* grp_row, const double* grp_w, int max_group_rows, double* C, DBuf<double>& partial,
                 cudaStream_t s);
-// W (n x k, FP64) += alpha * Wh (n x a, history type TH, leading dimension ldh) * C (a x k, FP64), computed
-// in TH arithmetic.
-// C[c] = sum_rows Qh[row][c] r[row] for c < a (history times one vector, FP64-class sums); partial must hold
-// at least a values (it is not grown: captured graphs share it)
+// C[c] = sum_rows Qh[row][c] r[row] for c < a (history times one vector, FP64-class sums; Qh in the block
+// layout of width hk); partial must hold at least a values (it is not grown: captured graphs share it)
 template <typename TH>
-void hist_dot(int n, int a, const TH* Qh, long long ldq, const double* r, double* C, DBuf<double>& partial,
+void hist_dot(int n, int a, const TH* Qh, int hk, const double* r, double* C, DBuf<double>& partial,
               cudaStream_t s);
+// W (n x k, FP64) += alpha * Wh (n x a, history type TH, block layout of width hk) * C (a x k, FP64),
+// computed in TH arithmetic.
 // scratch: split partials, tall_update_splits(n, a_max) * n * k values of TH; tickets: one counter per 64-row
 // tile, zero between calls (both grown here; callers that capture graphs size them first).
 int tall_update_splits(int n, int a_max);
 template <typename TH>
-void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, long long ldh, const double* C, double alpha,
+void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, int hk, const double* C, double alpha,
                  double* W, DBuf<double>& scratch, DBuf<unsigned>& tickets, cudaStream_t s);
 // history count += k with restart, dropped and iteration counters (one thread)
 void advance(int* cols, int k, long long cap, const int* n_kept, int* dropped, int* iters, cudaStream_t s);
@@ -213,10 +223,11 @@ struct AdvanceArgs {
   int* iters = nullptr;
   unsigned* counter = nullptr;   // zero between launches
 };
-// d_off (device, may be NULL): column offset added to Wn and Qn on the device.
+// Wn, Qn: the history (block layout of width k); d_off (device, may be NULL): the column where the new block
+// starts (a multiple of k).
 template <typename TH>
 void update(int n, int k, const double* W, const double* Q, const double* T, const double* alpha, TH* Wn, TH* Qn,
-            const int* d_off, long long ldn, double* lam, double* r, double* rr_partial, int rr_blocks,
+            const int* d_off, double* lam, double* r, double* rr_partial, int rr_blocks,
             cudaStream_t s, const AdvanceArgs& adv = AdvanceArgs());
 void sum_sq(int n, const double* x, double* out_partial, int blocks, cudaStream_t s);
 void axpy_f64(int n, double a, const double* x, double* y, cudaStream_t s);

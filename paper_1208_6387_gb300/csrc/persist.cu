@@ -189,8 +189,7 @@ __device__ void gram_item(const PersistArgs& A, int a, int it, unsigned char* sm
   float* swl = swh + P_GS_ROWS;
   double (*red)[P_GC] = reinterpret_cast<double (*)[P_GC]>(smem + 512 + 1024 + 1024);
   const TH* Qh = (const TH*)A.Qh;
-  const long long ldq = A.cap;
-  const int k = A.k;
+  const int k = A.k;   // also the history block width
   const int ctiles = (a + P_GC - 1) / P_GC;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ct = it % ctiles, rest = it / ctiles, g = rest % k, ch = rest / k;
@@ -207,23 +206,24 @@ __device__ void gram_item(const PersistArgs& A, int a, int it, unsigned char* sm
     swl[tid] = (float)(v - (double)vh);
   }
   __syncthreads();
-  int c[4];
   bool ok[4];
+  const TH* qp[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    c[u] = ct * P_GC + lane + 32 * u;
-    ok[u] = c[u] < a;
+    const int c = ct * P_GC + lane + 32 * u;
+    ok[u] = c < a;
+    qp[u] = Qh + hist_col(ok[u] ? c : 0, A.n, k);
   }
   double res[4];
   if (sizeof(TH) == 4) {
     float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
     for (int i = warp; i < cnt; i += 8) {
-      const TH* q = Qh + (size_t)srow[i] * ldq;
+      const size_t ro = (size_t)srow[i] * k;
       const float sh = swh[i], sl = swl[i];
       float qv[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) qv[u] = ok[u] ? (float)q[c[u]] : 0.f;
+      for (int u = 0; u < 4; ++u) qv[u] = ok[u] ? (float)qp[u][ro] : 0.f;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const float pp = __fmul_rn(qv[u], sh), e = fmaf(qv[u], sh, -pp), tt = fmaf(qv[u], sl, e);
@@ -238,10 +238,10 @@ __device__ void gram_item(const PersistArgs& A, int a, int it, unsigned char* sm
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll 4
     for (int i = warp; i < cnt; i += 8) {
-      const TH* q = Qh + (size_t)srow[i] * ldq;
+      const size_t ro = (size_t)srow[i] * k;
       const double wv = sw[i];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u] = fma(wv, ok[u] ? (double)q[c[u]] : 0.0, acc[u]);
+      for (int u = 0; u < 4; ++u) acc[u] = fma(wv, ok[u] ? (double)qp[u][ro] : 0.0, acc[u]);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) res[u] = acc[u];
@@ -329,7 +329,6 @@ __device__ void phase_tall(const PersistArgs& A, int a, unsigned char* smem) {
     return;
   }
   const TH* Wh = (const TH*)A.Wh;
-  const long long ldh = A.cap;
   TH* part = (TH*)A.tu_part;
   const int splits = A.tu_splits;
   const int per = (a + splits - 1) / splits;
@@ -342,10 +341,13 @@ __device__ void phase_tall(const PersistArgs& A, int a, unsigned char* smem) {
     TH acc[RPT][CPT] = {};
     TH pa[LA], pc[LC];
     auto load = [&](int c0) {
+      const int cc = tid % P_TU_CH;   // the same history column for all of the thread's loads
+      const bool okc = c0 + cc < c_end;
+      const TH* col = Wh + hist_col(okc ? c0 + cc : 0, n, k);
 #pragma unroll
       for (int i = 0; i < LA; ++i) {
-        const int idx = tid + PT * i, cc = idx % P_TU_CH, rr = idx / P_TU_CH;
-        pa[i] = (r0 + rr < n && c0 + cc < c_end) ? Wh[(size_t)(r0 + rr) * ldh + c0 + cc] : TH(0);
+        const int rr = (tid + PT * i) / P_TU_CH;
+        pa[i] = (r0 + rr < n && okc) ? col[(size_t)(r0 + rr) * k] : TH(0);
       }
 #pragma unroll
       for (int i = 0; i < LC; ++i) {
@@ -628,9 +630,8 @@ __device__ void phase_update(const PersistArgs& A, int a, unsigned char* smem) {
   double* warp_rr = beta + 32;
   const int n = A.n, k = A.k;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  TH* Wn = (TH*)A.Wh;
-  TH* Qn = (TH*)A.Qh;
-  const long long ldn = A.cap;
+  TH* Wn = (TH*)A.Wh + hist_col(a, A.n, A.k);   // the new block (a is a multiple of k)
+  TH* Qn = (TH*)A.Qh + hist_col(a, A.n, A.k);
   for (int idx = tid; idx < k * k; idx += PT) sT[idx / k][idx % k] = (TH)A.T[idx];
   if (tid < k) {
     double v = 0.0;
@@ -659,8 +660,8 @@ __device__ void phase_update(const PersistArgs& A, int a, unsigned char* smem) {
       qn = fma(qj, sT[j][ca], qn);
     }
     if (ok) {
-      Wn[row * ldn + a + c0] = wn;
-      Qn[row * ldn + a + c0] = qn;
+      Wn[row * k + c0] = wn;
+      Qn[row * k + c0] = qn;
     }
     double dl = ok ? w0 * beta[c0] : 0.0, dr = ok ? q0 * beta[c0] : 0.0;
     for (int o = seg >> 1; o > 0; o >>= 1) {
