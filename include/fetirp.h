@@ -236,6 +236,21 @@ fetirp_status fetirp_apply_block(fetirp_ctx ctx, int32_t k, const double* V, dou
 fetirp_status fetirp_apply_block_device(fetirp_ctx ctx, int32_t k, const double* d_V, double* d_Q,
                                         int32_t precision);
 
+/* Q = P^T F P S(r) for the k split columns of one interface vector r (the multivector of Section 3.1:
+ * column g holds r on the rows of the occurrences of group g, scaled by 1 / the row's occurrence count),
+ * computed in the sparse-column form.  F acts on S(r) only where a split column touches an occurrence (its own
+ * group and its neighbours' groups: at most seven right-hand sides per occurrence in 3D instead of k), and
+ * F G X with X = (G^T G)^{-1} G^T S(r) comes from precomputed local coarse responses
+ * M_s = S^+(s) B(s)^T G restricted to the kernel modes of s and its neighbours (by linearity of Table 1
+ * row 5.1).  The result equals fetirp_apply_block on the dense S(r) in the same precision.
+ *   r: n_lambda doubles; Q: n_lambda x k row-major doubles (k = the structure's multivector width), caller
+ *      owned.  _device: device pointers, asynchronous on the context's stream; otherwise host buffers.
+ *   The first call for a structure builds the pair lists and M (FP64 products, kept in FP64 and FP32).
+ * Errors: FETIRP_ESTATE before a structure is prepared; FETIRP_EINVAL for NULL buffers, an unknown precision,
+ * or more than 48 coarse columns touching one occurrence. */
+fetirp_status fetirp_apply_split(fetirp_ctx ctx, const double* r, double* Q, int32_t precision);
+fetirp_status fetirp_apply_split_device(fetirp_ctx ctx, const double* d_r, double* d_Q, int32_t precision);
+
 /*
  * Allocation-free variant of fetirp_apply_block_device (this entry point has no counterpart in the paper; it
  * exists for callers of the library).  Some callers cannot let a library allocate device memory while they

@@ -1,6 +1,7 @@
 // C ABI of the library (include/fetirp.h): patterns, occurrences, the coarse problem, the block interface
 // operator and the multivector FETI solver driver.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -132,6 +133,24 @@ struct OccData {
 
 }  // namespace
 
+// Sparse-column form of P^T F P S(r): right-hand sides (occurrence, group) only where the split column touches
+// the occurrence, and the local coarse responses M_s = S^+ B(s)^T G_nbr(s).  Built once per structure and k.
+struct SplitPlan {
+  int k = -1;
+  int n_pairs = 0;
+  int pair_off[fetirp::MAXP + 1] = {};
+  long long ybase[fetirp::MAXP] = {};
+  long long ytotal = 0;
+  DBuf<int> d_pair_occ, d_pair_g, d_pair_of;   // per pair; pair_of[s * k + g] = pattern-local index or -1
+  DBuf<int> d_mcol_ptr, d_mcol_row;            // per occurrence: coarse rows of its columns of M
+  DBuf<long long> d_moff, d_mld;               // offset of M_s; column stride per pattern
+  DBuf<double> M64;                            // S^+ E (FP64 form)
+  DBuf<float> M32;                             // S^dag E rounded to FP32 (low-precision forms)
+  DBuf<double> Vs, Yc;                         // S(r) (n x k) and the coarse responses per slot (n_slots x k)
+  DBuf<double> Y64, Z64;
+  DBuf<float> Y32, Z32, Ylo32;
+};
+
 struct fetirp_ctx_s {
   fetirp_options opt{};
   cudaStream_t stream = nullptr;
@@ -162,6 +181,8 @@ struct fetirp_ctx_s {
   DBuf<unsigned long long> pers_clk;   // timing: per-phase nanoseconds of the persistent iteration
   bool inject_stall = false;           // test hook: the next persistent launch waits for a CTA that never comes
   std::vector<double> h_prr;
+  std::vector<int> h_group;            // multivector column of every occurrence (current structure)
+  SplitPlan sp;
   DBuf<int8_t> d_slot_sign, d_row_sign;
   DBuf<long long> d_uoff;
   int n_pairs = 0;
@@ -555,6 +576,8 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   REQUIRE((int)group.size() == n_occ, "groups do not match the number of occurrences");
   if (k > 64) throw Error(FETIRP_EINVAL, "block width k > 64 is not supported");
   ctx->k = k;
+  ctx->h_group = group;
+  ctx->sp.k = -1;   // the sparse-column plan belongs to the previous structure
   // links -> gather CSR by slot, scatter lists by row
   const int n_slots = obase[n_occ];
   std::vector<int> cnt_slot(n_slots, 0);
@@ -1951,6 +1974,264 @@ fetirp_status fetirp_apply_block(fetirp_ctx ctx, int32_t k, const double* V, dou
     DBuf<double> dv(n), dq(n);
     dv.upload(V, n, ctx->stream);
     apply_F(ctx, dv.p, dq.p, k, precision, true, true);
+    check_tc_error(ctx);
+    FETIRP_CUDA(cudaMemcpyAsync(Q, dq.p, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
+    return FETIRP_OK;
+  });
+}
+
+}  // extern "C" (reopened below)
+
+namespace {
+
+// Pairs, local coarse responses and buffers of the sparse-column form (host tables from the links).
+void split_plan_build(fetirp_ctx ctx) {
+  cudaStream_t s = ctx->stream;
+  SplitPlan& SP = ctx->sp;
+  const Layout& L = ctx->L;
+  const int n_occ = L.n_occ, k = ctx->k, n_pat = (int)ctx->pats.size(), nl = L.n_lambda;
+  std::vector<int> obase(n_occ + 1, 0), occ_pat(n_occ), occ_gofs(n_occ);
+  for (int p = 0; p < n_pat; ++p)
+    for (size_t q = 0; q < ctx->use[p].occs.size(); ++q) occ_pat[ctx->use[p].occs[q]] = p;
+  for (int o = 0; o < n_occ; ++o) {
+    obase[o + 1] = obase[o] + ctx->pats[occ_pat[o]]->n_b;
+    occ_gofs[o] = ctx->pofs[occ_pat[o]] + 0;
+  }
+  for (int p = 0; p < n_pat; ++p)
+    for (size_t q = 0; q < ctx->use[p].occs.size(); ++q)
+      occ_gofs[ctx->use[p].occs[q]] = ctx->pofs[p] + (int)q * ctx->pats[p]->kdim;
+  // owners of every row: (occurrence, boundary dof, sign)
+  struct Own { int o, j, sg; };
+  std::vector<std::array<Own, 2>> own(nl);
+  std::vector<int> nown(nl, 0);
+  for (int o = 0; o < n_occ; ++o) {
+    const OccData& O = ctx->occs[o];
+    for (size_t i = 0; i < O.link_row.size(); ++i) {
+      const int r = O.link_row[i];
+      own[r][nown[r]++] = Own{o, O.link_j[i], O.link_sign[i]};
+    }
+  }
+  std::vector<std::vector<int>> nbr(n_occ);
+  for (int r = 0; r < nl; ++r)
+    if (nown[r] == 2) {
+      nbr[own[r][0].o].push_back(own[r][1].o);
+      nbr[own[r][1].o].push_back(own[r][0].o);
+    }
+  for (auto& v : nbr) { std::sort(v.begin(), v.end()); v.erase(std::unique(v.begin(), v.end()), v.end()); }
+  // pairs, pattern by pattern in local-product column order
+  std::vector<int> pair_occ, pair_g, pair_of((size_t)n_occ * k, -1);
+  for (int p = 0; p < n_pat; ++p) {
+    SP.pair_off[p] = (int)pair_occ.size();
+    for (int o : ctx->use[p].occs) {
+      std::vector<int> gs{ctx->h_group[o]};
+      for (int t : nbr[o]) gs.push_back(ctx->h_group[t]);
+      std::sort(gs.begin(), gs.end());
+      gs.erase(std::unique(gs.begin(), gs.end()), gs.end());
+      for (int g : gs) {
+        pair_of[(size_t)o * k + g] = (int)pair_occ.size() - SP.pair_off[p];
+        pair_occ.push_back(o);
+        pair_g.push_back(g);
+      }
+    }
+  }
+  SP.pair_off[n_pat] = (int)pair_occ.size();
+  SP.n_pairs = (int)pair_occ.size();
+  SP.ytotal = 0;
+  for (int p = 0; p < n_pat; ++p) {
+    SP.ybase[p] = SP.ytotal;
+    SP.ytotal += (long long)(SP.pair_off[p + 1] - SP.pair_off[p]) * ctx->pats[p]->ld_y;
+  }
+  // E_s = B(s)^T G over the kernel modes of s and its neighbours; M = S E per pattern (FP64 products)
+  std::vector<std::vector<double>> hNb(n_pat);
+  for (int p = 0; p < n_pat; ++p) {
+    const PatternData& P = *ctx->pats[p];
+    hNb[p].resize((size_t)P.n_b * P.kdim);
+    if (P.kdim > 0)
+      FETIRP_CUDA(cudaMemcpyAsync(hNb[p].data(), P.Nb.p, sizeof(double) * hNb[p].size(), cudaMemcpyDeviceToHost, s));
+  }
+  FETIRP_CUDA(cudaStreamSynchronize(s));
+  std::vector<int> mcol_ptr(n_occ + 1, 0), mcol_row;
+  std::vector<long long> moff(n_occ, 0), mld(fetirp::MAXP, 1), mbase(n_pat + 1, 0);
+  std::vector<std::vector<double>> E(n_pat);
+  std::vector<int> mcols(n_pat, 0);
+  for (int p = 0; p < n_pat; ++p) {
+    const long long ld = ctx->pats[p]->ld_y;
+    mld[p] = ld;
+    for (int o : ctx->use[p].occs) {
+      std::vector<int> us{o};
+      for (int t : nbr[o]) us.push_back(t);
+      std::sort(us.begin(), us.end());
+      std::vector<int> col0(us.size());
+      int nc = 0;
+      for (size_t i = 0; i < us.size(); ++i) { col0[i] = nc; nc += ctx->pats[occ_pat[us[i]]]->kdim; }
+      if (nc > 48) throw Error(FETIRP_EINVAL, "sparse-column form: more than 48 coarse columns touch one occurrence");
+      moff[o] = (long long)mcols[p];   // columns before o within pattern p (made absolute below)
+      mcols[p] += nc;
+      const size_t base = E[p].size();
+      E[p].resize(base + (size_t)nc * ld, 0.0);
+      const OccData& O = ctx->occs[o];
+      for (size_t i = 0; i < O.link_row.size(); ++i) {
+        const int r = O.link_row[i], j = O.link_j[i], sgo = O.link_sign[i];
+        for (int e = 0; e < nown[r]; ++e) {
+          const Own& w = own[r][e];
+          const size_t ui = std::lower_bound(us.begin(), us.end(), w.o) - us.begin();
+          const int kd = ctx->pats[occ_pat[w.o]]->kdim;
+          for (int m = 0; m < kd; ++m)
+            E[p][base + (size_t)(col0[ui] + m) * ld + j] += (double)(sgo * w.sg) * hNb[occ_pat[w.o]][(size_t)w.j * kd + m];
+        }
+      }
+      for (size_t i = 0; i < us.size(); ++i)
+        for (int m = 0; m < ctx->pats[occ_pat[us[i]]]->kdim; ++m) mcol_row.push_back(occ_gofs[us[i]] + m);
+      mcol_ptr[o + 1] = nc;
+    }
+  }
+  for (int o = 0; o < n_occ; ++o) mcol_ptr[o + 1] += mcol_ptr[o];
+  // mcol_row was filled pattern by pattern: reorder to occurrence order
+  {
+    std::vector<int> rows(mcol_row.size());
+    size_t pos = 0;
+    std::vector<size_t> start(n_occ);
+    for (int p = 0; p < n_pat; ++p)
+      for (int o : ctx->use[p].occs) { start[o] = pos; pos += mcol_ptr[o + 1] - mcol_ptr[o]; }
+    for (int o = 0; o < n_occ; ++o)
+      for (int c = 0; c < mcol_ptr[o + 1] - mcol_ptr[o]; ++c) rows[mcol_ptr[o] + c] = mcol_row[start[o] + c];
+    mcol_row.swap(rows);
+  }
+  long long mtotal = 0;
+  for (int p = 0; p < n_pat; ++p) { mbase[p] = mtotal; mtotal += (long long)mcols[p] * mld[p]; }
+  for (int p = 0; p < n_pat; ++p)
+    for (int o : ctx->use[p].occs) moff[o] = mbase[p] + moff[o] * mld[p];
+  DBuf<double> dE(std::max<long long>(mtotal, 1)), dMd(std::max<long long>(mtotal, 1));
+  for (int p = 0; p < n_pat; ++p)
+    if (!E[p].empty())
+      FETIRP_CUDA(cudaMemcpyAsync(dE.p + mbase[p], E[p].data(), sizeof(double) * E[p].size(), cudaMemcpyHostToDevice, s));
+  SP.M64.ensure(std::max<long long>(mtotal, 1));
+  SP.M32.ensure(std::max<long long>(mtotal, 1));
+  for (int pass = 0; pass < 2; ++pass) {   // S^+ E, then S^dag E
+    LocalProblem LP{};
+    LP.n_pat = n_pat;
+    for (int p = 0; p < n_pat; ++p) {
+      const PatternData& P = *ctx->pats[p];
+      LP.S[p] = pass == 0 ? (const void*)P.S64.p : (const void*)(P.kdim > 0 ? P.Sdag.p : P.S64.p);
+      LP.n_b[p] = P.n_b;
+      LP.n_rhs[p] = mcols[p];
+      LP.ld[p] = mld[p];
+      LP.Y[p] = dE.p + mbase[p];
+      LP.Z[p] = (pass == 0 ? SP.M64.p : dMd.p) + mbase[p];
+    }
+    local_gemm_f64(LP, s);
+  }
+  k_to_f32<<<(unsigned)((mtotal + 255) / 256), 256, 0, s>>>((size_t)mtotal, dMd.p, SP.M32.p);
+  FETIRP_LAUNCH_CHECK();
+  SP.d_pair_occ.upload(pair_occ, s);
+  SP.d_pair_g.upload(pair_g, s);
+  SP.d_pair_of.upload(pair_of, s);
+  SP.d_mcol_ptr.upload(mcol_ptr, s);
+  SP.d_mcol_row.upload(mcol_row, s);
+  SP.d_moff.upload(moff, s);
+  SP.d_mld.upload(mld, s);
+  SP.Vs.ensure((size_t)nl * k);
+  SP.Yc.ensure((size_t)std::max(L.n_slots, 1) * k);
+  FETIRP_CUDA(cudaStreamSynchronize(s));   // the temporaries dE, dMd are released on return
+  SP.k = k;
+}
+
+// Q = P^T F P S(r) by the sparse-column form (equal to apply_F on the dense S(r))
+void apply_split(fetirp_ctx ctx, const double* d_r, double* d_Q, int prec) {
+  SplitPlan& SP = ctx->sp;
+  if (SP.k != ctx->k) split_plan_build(ctx);
+  cudaStream_t s = ctx->stream;
+  const Layout& L = ctx->L;
+  const int k = ctx->k, n_pat = (int)ctx->pats.size();
+  split(L, d_r, k, SP.Vs.p, s);
+  if (ctx->n_G > 0) {   // X = (G^T G)^{-1} G^T S(r) and its local responses M_s X
+    gt_v(L, SP.Vs.p, k, ctx->Xc.p, s);
+    small_gemm(ctx->n_G, k, ctx->Ginv.p, ctx->Xc.p, ctx->Ac.p, s);
+    if (prec == FETIRP_PREC_FP64)
+      coarse_response<double>(L, k, SP.M64.p, SP.d_moff.p, SP.d_mcol_ptr.p, SP.d_mcol_row.p, SP.d_mld.p, ctx->Ac.p,
+                              SP.Yc.p, s);
+    else
+      coarse_response<float>(L, k, SP.M32.p, SP.d_moff.p, SP.d_mcol_ptr.p, SP.d_mcol_row.p, SP.d_mld.p, ctx->Ac.p,
+                             SP.Yc.p, s);
+  } else {
+    SP.Yc.zero(s);
+  }
+  auto view = [&](auto* base, auto& V) {
+    for (int p = 0; p < n_pat; ++p) { V.base[p] = base + SP.ybase[p]; V.ld[p] = ctx->pats[p]->ld_y; }
+    for (int p = 0; p <= n_pat; ++p) V.pair_off[p] = SP.pair_off[p];
+  };
+  const long long tot = std::max<long long>(SP.ytotal, 1);
+  if (prec == FETIRP_PREC_FP64) {
+    SP.Y64.ensure(tot); SP.Z64.ensure(tot);
+    PairView<double> Y{}, Z{};
+    view(SP.Y64.p, Y); view(SP.Z64.p, Z);
+    gather_pairs_f64(L, SP.Vs.p, k, SP.d_pair_occ.p, SP.d_pair_g.p, SP.n_pairs, Y, s);
+    LocalProblem LP{};
+    LP.n_pat = n_pat;
+    for (int p = 0; p < n_pat; ++p) {
+      LP.S[p] = ctx->pats[p]->S64.p; LP.n_b[p] = ctx->pats[p]->n_b; LP.ld[p] = Y.ld[p];
+      LP.n_rhs[p] = SP.pair_off[p + 1] - SP.pair_off[p]; LP.Y[p] = Y.base[p]; LP.Z[p] = Z.base[p];
+    }
+    local_gemm_f64(LP, s);
+    scatter_pairs<double>(L, Z, k, SP.d_pair_of.p, SP.Yc.p, d_Q, s);
+  } else {
+    SP.Y32.ensure(tot); SP.Z32.ensure(tot);
+    PairView<float> Y{}, Z{};
+    view(SP.Y32.p, Y); view(SP.Z32.p, Z);
+    if (prec == FETIRP_PREC_FP32) {
+      gather_pairs_f32(L, SP.Vs.p, k, SP.d_pair_occ.p, SP.d_pair_g.p, SP.n_pairs, Y, s);
+      LocalProblem LP{};
+      LP.n_pat = n_pat;
+      for (int p = 0; p < n_pat; ++p) {
+        LP.S[p] = ctx->pats[p]->S32.p; LP.n_b[p] = ctx->pats[p]->n_b; LP.ld[p] = Y.ld[p];
+        LP.n_rhs[p] = SP.pair_off[p + 1] - SP.pair_off[p]; LP.Y[p] = Y.base[p]; LP.Z[p] = Z.base[p];
+      }
+      local_gemm_f32(LP, s);
+    } else {
+      SP.Ylo32.ensure(tot);
+      PairView<float> Yl{};
+      view(SP.Ylo32.p, Yl);
+      gather_pairs_split(L, SP.Vs.p, k, SP.d_pair_occ.p, SP.d_pair_g.p, SP.n_pairs, Y, Yl, s);
+      if (!ctx->tc_error.p) { ctx->tc_error.alloc(1); ctx->tc_error.zero(s); }
+      TcProblem T;
+      T.n_pat = n_pat;
+      for (int p = 0; p < n_pat; ++p) {
+        const PatternData& P = *ctx->pats[p];
+        T.S_hi[p] = P.S_hi.p; T.S_lo[p] = P.S_lo.p; T.lds[p] = P.lds;
+        T.Y_hi[p] = Y.base[p]; T.Y_lo[p] = Yl.base[p]; T.Z[p] = Z.base[p]; T.ldy[p] = Y.ld[p];
+        T.n_b[p] = P.n_b; T.n_rhs[p] = SP.pair_off[p + 1] - SP.pair_off[p];
+      }
+      tc_gemm_tf32x3(T, ctx->tc_error.p, s);
+    }
+    scatter_pairs<float>(L, Z, k, SP.d_pair_of.p, SP.Yc.p, d_Q, s);
+  }
+  project(ctx, d_Q, k);   // P^T
+}
+
+}  // namespace
+
+extern "C" {
+
+fetirp_status fetirp_apply_split_device(fetirp_ctx ctx, const double* d_r, double* d_Q, int32_t precision) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    if (!ctx->prepared) throw Error(FETIRP_ESTATE, "call fetirp_prepare or fetirp_solve first");
+    REQUIRE(d_r && d_Q, "NULL buffer");
+    REQUIRE(precision >= FETIRP_PREC_FP64 && precision <= FETIRP_PREC_TF32X3, "unsupported precision");
+    apply_split(ctx, d_r, d_Q, precision);
+    return FETIRP_OK;
+  });
+}
+
+fetirp_status fetirp_apply_split(fetirp_ctx ctx, const double* r, double* Q, int32_t precision) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    if (!ctx->prepared) throw Error(FETIRP_ESTATE, "call fetirp_prepare or fetirp_solve first");
+    REQUIRE(r && Q, "NULL buffer");
+    REQUIRE(precision >= FETIRP_PREC_FP64 && precision <= FETIRP_PREC_TF32X3, "unsupported precision");
+    const size_t nl = (size_t)ctx->L.n_lambda, n = nl * ctx->k;
+    DBuf<double> dr(nl), dq(n);
+    dr.upload(r, nl, ctx->stream);
+    apply_split(ctx, dr.p, dq.p, precision);
     check_tc_error(ctx);
     FETIRP_CUDA(cudaMemcpyAsync(Q, dq.p, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
     FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));

@@ -191,6 +191,108 @@ __global__ void k_split(Layout L, const double* __restrict__ r, int k, double* _
   }
 }
 
+// ---- sparse-column form of P^T F P S(r) -------------------------------------------------------------
+// Y for the (occurrence, group) pairs only: pair i (pattern p, pattern-local index i - pair_off[p]) gathers
+// column pair_g[i] of V on the slots of occurrence pair_occ[i] (the same sum as the dense gather).
+template <typename TO>
+__global__ void __launch_bounds__(256) k_gather_pairs(Layout L, const double* __restrict__ V, int k,
+                                                      const int* __restrict__ pair_occ,
+                                                      const int* __restrict__ pair_g, PairView<TO> Y) {
+  const int i = blockIdx.x;
+  const int s = pair_occ[i], g = pair_g[i];
+  const int p = L.occ_pat[s];
+  const int b0 = L.occ_obase[s], nb = L.occ_obase[s + 1] - b0;
+  TO* y = Y.base[p] + (long long)(i - Y.pair_off[p]) * Y.ld[p];
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) y[j] = (TO)trace_of(L, V, k, b0 + j, g);
+}
+
+// as k_gather_pairs, the FP32 value split into a tf32 pair (hi = tf32(y), lo = y - hi)
+__global__ void __launch_bounds__(256) k_gather_pairs_split(Layout L, const double* __restrict__ V, int k,
+                                                            const int* __restrict__ pair_occ,
+                                                            const int* __restrict__ pair_g, PairView<float> Yh,
+                                                            PairView<float> Yl) {
+  const int i = blockIdx.x;
+  const int s = pair_occ[i], g = pair_g[i];
+  const int p = L.occ_pat[s];
+  const int b0 = L.occ_obase[s], nb = L.occ_obase[s + 1] - b0;
+  const long long o = (long long)(i - Yh.pair_off[p]) * Yh.ld[p];
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    const float v = (float)trace_of(L, V, k, b0 + j, g);
+    uint32_t t;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
+    const float h = __uint_as_float(t);
+    Yh.base[p][o + j] = h;
+    Yl.base[p][o + j] = v - h;
+  }
+}
+
+// Yc[slot][g] = sum_c M_s[j][c] A[mrow[c]][g]: the local response of occurrence s to the coarse correction
+// G X restricted to its own and its neighbours' kernel modes (M_s = S^+ B(s)^T G_nbr(s), precomputed).
+// Grid (occurrence, 64-slot chunk); thread = (slot j, quarter of the k columns): each M entry is loaded once
+// (coalesced over j) and used for the thread's columns; A's rows of the occurrence are staged in shared memory.
+template <typename TM>
+__global__ void __launch_bounds__(256) k_coarse_response(Layout L, int k, const TM* __restrict__ M,
+                                                         const long long* __restrict__ moff,
+                                                         const int* __restrict__ mcol_ptr,
+                                                         const int* __restrict__ mcol_row, const long long* mld,
+                                                         const double* __restrict__ A, double* __restrict__ Yc) {
+  __shared__ TM sa[48][64];   // A rows of the occurrence's columns (<= 7 x 6 modes, k <= 64), in TM
+  const int s = blockIdx.x;
+  const int p = L.occ_pat[s];
+  const int b0 = L.occ_obase[s], nb = L.occ_obase[s + 1] - b0;
+  const int c0 = mcol_ptr[s], nc = mcol_ptr[s + 1] - c0;
+  for (int idx = threadIdx.x; idx < nc * k; idx += blockDim.x) {
+    const int c = idx / k, g = idx % k;
+    sa[c][g] = (TM)A[(size_t)mcol_row[c0 + c] * k + g];
+  }
+  __syncthreads();
+  const int j = blockIdx.y * 64 + threadIdx.x % 64;
+  if (j >= nb) return;
+  const int gq = threadIdx.x / 64;                 // columns g = gq, gq + 4, ...
+  const TM* m = M + moff[s] + j;
+  const long long ld = mld[p];
+  TM acc[16];   // k <= 64: at most 16 columns per thread; TM arithmetic (FP64 form: FP64, else FP32)
+#pragma unroll
+  for (int u = 0; u < 16; ++u) acc[u] = TM(0);
+  for (int c = 0; c < nc; ++c) {
+    const TM mv = m[(long long)c * ld];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int g = gq + 4 * u;
+      if (g < k) acc[u] = fma(mv, sa[c][g], acc[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int g = gq + 4 * u;
+    if (g < k) Yc[(size_t)(b0 + j) * k + g] = (double)acc[u];
+  }
+}
+
+// out[row][g] = sum over the row's slots: sign * (Z_loc(pair(s, g), j) - Yc[slot][g]); pairs that do not exist
+// (the split column does not touch the occurrence) contribute no local solution.
+template <typename TI>
+__global__ void k_scatter_pairs(Layout L, PairView<TI> Z, int k, const int* __restrict__ pair_of,
+                                const double* __restrict__ Yc, double* __restrict__ out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)L.n_lambda * k) return;
+  const int row = (int)(idx / k), g = (int)(idx % k);
+  double acc = 0.0;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int sg = L.row_sign[2 * row + e];
+    if (sg == 0) continue;
+    const int slot = L.row_slot[2 * row + e];
+    const int s = L.slot_occ[slot];
+    const int p = L.occ_pat[s];
+    const int j = slot - L.occ_obase[s];
+    const int lp = pair_of[(size_t)s * k + g];
+    const double z = lp >= 0 ? (double)Z.base[p][(long long)lp * Z.ld[p] + j] : 0.0;
+    acc += (double)sg * (z - Yc[(size_t)slot * k + g]);
+  }
+  out[idx] = acc;
+}
+
 // ------------------------------------------------------------------------------------------------ host
 void gt_v(const Layout& L, const double* V, int k, double* X, cudaStream_t s) {
   if (L.n_occ == 0) return;
@@ -250,5 +352,51 @@ template void gather<double>(const Layout&, const double*, int, const PatView<do
 template void gather<float>(const Layout&, const double*, int, const PatView<float>&, cudaStream_t, double, double);
 template void scatter<double>(const Layout&, const PatView<double>&, int, double, double*, cudaStream_t);
 template void scatter<float>(const Layout&, const PatView<float>&, int, double, double*, cudaStream_t);
+
+void gather_pairs_f64(const Layout& L, const double* V, int k, const int* pair_occ, const int* pair_g, int n_pairs,
+                      const PairView<double>& Y, cudaStream_t s) {
+  if (n_pairs == 0) return;
+  k_gather_pairs<double><<<n_pairs, 256, 0, s>>>(L, V, k, pair_occ, pair_g, Y);
+  FETIRP_LAUNCH_CHECK();
+}
+void gather_pairs_f32(const Layout& L, const double* V, int k, const int* pair_occ, const int* pair_g, int n_pairs,
+                      const PairView<float>& Y, cudaStream_t s) {
+  if (n_pairs == 0) return;
+  k_gather_pairs<float><<<n_pairs, 256, 0, s>>>(L, V, k, pair_occ, pair_g, Y);
+  FETIRP_LAUNCH_CHECK();
+}
+void gather_pairs_split(const Layout& L, const double* V, int k, const int* pair_occ, const int* pair_g, int n_pairs,
+                        const PairView<float>& Yh, const PairView<float>& Yl, cudaStream_t s) {
+  if (n_pairs == 0) return;
+  k_gather_pairs_split<<<n_pairs, 256, 0, s>>>(L, V, k, pair_occ, pair_g, Yh, Yl);
+  FETIRP_LAUNCH_CHECK();
+}
+template <typename TM>
+void coarse_response(const Layout& L, int k, const TM* M, const long long* moff, const int* mcol_ptr,
+                     const int* mcol_row, const long long* mld, const double* A, double* Yc, cudaStream_t s) {
+  if (L.n_occ == 0) return;
+  if (k > 64) throw Error(1, "k > 64");
+  int max_nb = 1;
+  for (int p = 0; p < L.n_pat; ++p) max_nb = std::max(max_nb, L.n_b[p]);
+  k_coarse_response<TM><<<dim3(L.n_occ, ceil_div(max_nb, 64)), 256, 0, s>>>(L, k, M, moff, mcol_ptr, mcol_row, mld,
+                                                                            A, Yc);
+  FETIRP_LAUNCH_CHECK();
+}
+template void coarse_response<double>(const Layout&, int, const double*, const long long*, const int*, const int*,
+                                       const long long*, const double*, double*, cudaStream_t);
+template void coarse_response<float>(const Layout&, int, const float*, const long long*, const int*, const int*,
+                                      const long long*, const double*, double*, cudaStream_t);
+template <typename TI>
+void scatter_pairs(const Layout& L, const PairView<TI>& Z, int k, const int* pair_of, const double* Yc, double* out,
+                   cudaStream_t s) {
+  long long n = (long long)L.n_lambda * k;
+  if (n == 0) return;
+  k_scatter_pairs<TI><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, Z, k, pair_of, Yc, out);
+  FETIRP_LAUNCH_CHECK();
+}
+template void scatter_pairs<double>(const Layout&, const PairView<double>&, int, const int*, const double*, double*,
+                                    cudaStream_t);
+template void scatter_pairs<float>(const Layout&, const PairView<float>&, int, const int*, const double*, double*,
+                                   cudaStream_t);
 
 }  // namespace fetirp

@@ -83,6 +83,30 @@ struct LocalProblem {
 void local_gemm_f64(const LocalProblem& P, cudaStream_t s);
 void local_gemm_f32(const LocalProblem& P, cudaStream_t s);
 
+// ---- sparse-column form of P^T F P S(r) (right-hand sides only where the split column touches) ----------
+// Pattern p's pair right-hand sides: base[p] + (i - pair_off[p]) * ld[p] for global pair index i.
+template <typename T>
+struct PairView {
+  T* base[MAXP];
+  long long ld[MAXP];
+  int pair_off[MAXP + 1];
+};
+void gather_pairs_f64(const Layout& L, const double* V, int k, const int* pair_occ, const int* pair_g, int n_pairs,
+                      const PairView<double>& Y, cudaStream_t s);
+void gather_pairs_f32(const Layout& L, const double* V, int k, const int* pair_occ, const int* pair_g, int n_pairs,
+                      const PairView<float>& Y, cudaStream_t s);
+void gather_pairs_split(const Layout& L, const double* V, int k, const int* pair_occ, const int* pair_g, int n_pairs,
+                        const PairView<float>& Yh, const PairView<float>& Yl, cudaStream_t s);
+// Yc[slot][g] = (M_s A)[j][g]: M_s is n_b x c_s column-major at M + moff[s] with column stride mld[pattern];
+// its columns are the coarse rows mcol_row[mcol_ptr[s] .. mcol_ptr[s+1]) of A (n_G x k)
+template <typename TM>
+void coarse_response(const Layout& L, int k, const TM* M, const long long* moff, const int* mcol_ptr,
+                     const int* mcol_row, const long long* mld, const double* A, double* Yc, cudaStream_t s);
+// out[row][g] = sum over the row's slots: sign * (Z(pair_of[s][g], j) - Yc[slot][g])
+template <typename TI>
+void scatter_pairs(const Layout& L, const PairView<TI>& Z, int k, const int* pair_of, const double* Yc, double* out,
+                   cudaStream_t s);
+
 // ---- direction history layout ----------------------------------------------------------------------
 // The stored directions W_h, Q_h (n rows, `cap` columns) are kept in blocks of hk columns, one block per block
 // iteration: each block is n x hk, row-major and contiguous.  Writing a block is one contiguous stream and a

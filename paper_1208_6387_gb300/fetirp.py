@@ -92,6 +92,8 @@ _SIGS = {
     "fetirp_prepare": (C.c_int, [P, C.c_int64, P]),
     "fetirp_factorize": (C.c_int, [P]),
     "fetirp_inject_barrier_stall": (C.c_int, [P]),
+    "fetirp_apply_split": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_int]),
+    "fetirp_apply_split_device": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_int]),
     "fetirp_get_pattern": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), P, P]),
 }
 
@@ -294,6 +296,18 @@ def fetirp_apply_block(ctx, V, precision=FETIRP_PREC_FP64):
     Q = np.zeros_like(V)
     _check(ctx, lib().fetirp_apply_block(ctx, V.shape[1], _ptr(V), _ptr(Q), int(precision)))
     return Q
+
+
+def fetirp_apply_split(ctx, r, k, precision=FETIRP_PREC_FP64):
+    """Q = P^T F P S(r) (n_lambda x k) by the sparse-column form; r: host vector."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    Q = np.zeros((r.shape[0], int(k)))
+    _check(ctx, lib().fetirp_apply_split(ctx, _ptr(r), _ptr(Q), int(precision)))
+    return Q
+
+
+def fetirp_apply_split_device(ctx, r_ptr, Q_ptr, precision=FETIRP_PREC_FP64):
+    _check(ctx, lib().fetirp_apply_split_device(ctx, C.c_void_p(r_ptr), C.c_void_p(Q_ptr), int(precision)))
 
 
 def fetirp_apply_block_device(ctx, k, V_ptr, Q_ptr, precision=FETIRP_PREC_FP64):

@@ -133,6 +133,28 @@ def test_bounded_barrier_wait_expires_and_context_recovers():
         F.fetirp_destroy(ctx)
 
 
+@pytest.mark.parametrize("name", list(CASES) + ["c2"])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-4), ("tf32x3", 5e-4)])
+def test_sparse_column_apply_matches_dense_and_oracle(name, prec, tol):
+    """The sparse-column form of P^T F P S(r) equals the dense block operator on S(r) in the same
+    precision, and the oracle's P^T F P S(r)."""
+    prob = config("c2") if name == "c2" else CASES[name]()
+    orc = FetiOracle(prob)
+    rng = np.random.default_rng(11)
+    r = rng.standard_normal(prob.n_lambda)
+    Vs = orc.split(r)
+    ref = orc.PtFP(Vs)
+    ctx = make_ctx(prob, precision=prec)
+    try:
+        F.fetirp_prepare(ctx, prob.n_lambda, prob.c)
+        Qs = F.fetirp_apply_split(ctx, r, prob.k, F.PRECISIONS[prec])
+        Qd = F.fetirp_apply_block(ctx, Vs, F.PRECISIONS[prec])
+    finally:
+        F.fetirp_destroy(ctx)
+    assert rel(Qs, ref) < tol, (rel(Qs, ref), rel(Qd, ref))
+    assert rel(Qs, Qd) < (1e-11 if prec == "fp64" else tol)
+
+
 def test_classical_k1_and_block_agree():
     """k = 1 is classical FETI-CG; block k = n_occ needs no more iterations (the classical direction lies in
     the block span, Section 3.1) and both reach the same lambda."""
