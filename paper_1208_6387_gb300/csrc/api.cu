@@ -175,6 +175,9 @@ struct fetirp_ctx_s {
   // row's slots in the local product buffers (for the current k)
   DBuf<int> d_row_grp, d_row_zld, d_rowg_gofs, d_rowg_kd;
   DBuf<double> d_row_wt, d_rowg_coef;
+  DBuf<int> d_slot_code;        // per link: 2 row + e (its entry in the per-row tables)
+  DBuf<double> d_gtv_part;      // G^T V per-chunk partial sums
+  DBuf<unsigned> d_gtv_ticket;  // G^T V last-CTA tickets (self-resetting)
   DBuf<long long> d_row_z;
   DBuf<unsigned> d_pbar;     // {barrier count, barrier generation, eta ticket, error flag, 64 group tickets}
   DBuf<double> pers_eta, prr;
@@ -607,13 +610,17 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   for (int i = 0; i < n_slots; ++i) slot_ptr[i + 1] = slot_ptr[i] + cnt_slot[i];
   std::vector<int> slot_row(slot_ptr[n_slots]), fill(slot_ptr.begin(), slot_ptr.end() - 1);
   std::vector<int8_t> slot_sign(slot_ptr[n_slots]);
+  std::vector<int> slot_code(slot_ptr[n_slots]);   // 2 row + e: the link's entry in the per-row tables
   for (int r = 0; r < nl; ++r)   // rows in increasing order inside every slot
     for (int e = 0; e < row_cnt[r]; ++e) {
       const int slot = row_slot[2 * (size_t)r + e];
       slot_row[fill[slot]] = r;
       slot_sign[fill[slot]] = row_sign[2 * (size_t)r + e];
+      slot_code[fill[slot]] = 2 * r + e;
       fill[slot]++;
     }
+  int max_links = 1;   // links of the largest occurrence
+  for (int o = 0; o < n_occ; ++o) max_links = std::max(max_links, slot_ptr[obase[o + 1]] - slot_ptr[obase[o]]);
   std::vector<int> slot_occ(n_slots);
   for (int o = 0; o < n_occ; ++o)
     for (int j = obase[o]; j < obase[o + 1]; ++j) slot_occ[j] = o;
@@ -665,6 +672,7 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   ctx->d_slot_ptr.upload(slot_ptr, s);
   ctx->d_slot_row.upload(slot_row, s);
   ctx->d_slot_sign.upload(slot_sign, s);
+  ctx->d_slot_code.upload(slot_code, s);
   ctx->d_row_slot.upload(row_slot, s);
   ctx->d_row_sign.upload(row_sign, s);
   ctx->d_slot_occ.upload(slot_occ, s);
@@ -750,10 +758,24 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   L.ell_w = ell_w; L.ell_row = ctx->d_ell_row.p; L.ell_sign = ctx->d_ell_sign.p;
   L.occ_obase = ctx->d_occ_obase.p; L.occ_pat = ctx->d_occ_pat.p; L.occ_q = ctx->d_occ_q.p;
   L.occ_gofs = ctx->d_occ_gofs.p; L.occ_group = ctx->d_occ_group.p;
+  int max_nb = 1;
   for (int p = 0; p < n_pat; ++p) {
     L.Nb[p] = ctx->pats[p]->Nb.p;
     L.n_b[p] = ctx->pats[p]->n_b;
     L.kdim[p] = ctx->pats[p]->kdim;
+    max_nb = std::max(max_nb, ctx->pats[p]->n_b);
+  }
+  L.rowg_gofs = ctx->d_rowg_gofs.p; L.rowg_kd = ctx->d_rowg_kd.p; L.rowg_coef = ctx->d_rowg_coef.p;
+  L.slot_code = ctx->d_slot_code.p;
+  {  // G^T V chunks: at most 512 links per CTA, and at least two CTAs per SM while chunks keep >= 64 links
+    int chunks =
+        std::max(ceil_div(max_links, 512), std::min(ceil_div(max_links, 64), ceil_div(2 * 152, std::max(n_occ, 1))));
+    L.gtv_chunk = (int)round_up(ceil_div(max_links, chunks), 32);
+    L.gtv_chunks = ceil_div(max_links, L.gtv_chunk);
+    ctx->d_gtv_part.ensure((size_t)std::max(n_occ, 1) * L.gtv_chunks * 6 * 64);
+    ctx->d_gtv_ticket.ensure((size_t)std::max(n_occ, 1));
+    ctx->d_gtv_ticket.zero(s);
+    L.gtv_part = ctx->d_gtv_part.p; L.gtv_ticket = ctx->d_gtv_ticket.p;
   }
   // per-pattern loads (pattern frame, new ordering) and work
   for (int p = 0; p < n_pat; ++p) {

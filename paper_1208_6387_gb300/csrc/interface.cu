@@ -14,49 +14,88 @@ __device__ __forceinline__ double trace_of(const Layout& L, const double* __rest
   return y;
 }
 
-// X[gofs(s)+m][g] = sum_{links of s} sign * Nb[j][m] * V[row][g]        (one CTA per occurrence)
-// Thread t takes column g = t % k and every (256/k)-th boundary dof; partial sums per kernel mode m live in
-// registers and are reduced over the threads of one column in a fixed order (deterministic).
+// X[gofs(s)+m][g] = sum_{links (row, e) of s} (sign Nb[j])[m] * V[row][g], the signed coefficients taken from the
+// per-row tables.  Grid (occurrence, chunk of its links); warp w takes every 8th link of the chunk, four links
+// at a time (independent loads: link code, then its row of V and its coefficients), lane = column g (and g + 32
+// for k <= 64), so every link reads one contiguous row of V.  The warps' sums are added in warp order; with
+// several chunks per occurrence the last CTA of the occurrence (ticket) adds the chunks' partial sums in chunk
+// order and re-arms the ticket (deterministic, no atomics on values).
 constexpr int GTV_THREADS = 256;
-constexpr int GTV_COLS = 8;     // columns per CTA (grid.y splits the block of k columns)
 constexpr int MAX_KDIM = 6;
-__global__ void __launch_bounds__(GTV_THREADS) k_gt_v(Layout L, const double* __restrict__ V, int k,
-                                                       double* __restrict__ X) {
-  __shared__ double red[GTV_THREADS][MAX_KDIM];
-  const int s = blockIdx.x;
-  const int p = L.occ_pat[s];
-  const int kd = L.kdim[p];
-  const double* Nb = L.Nb[p];
-  const int b0 = L.occ_obase[s], nb = L.occ_obase[s + 1] - b0;
-  const int g0 = L.occ_gofs[s];
-  const int t = threadIdx.x;
-  const int gbase = blockIdx.y * GTV_COLS;
-  const int kk = min(GTV_COLS, k - gbase);
-  const int lanes = GTV_THREADS / kk;       // threads per column
-  const int g = gbase + t % kk, sub = t / kk;
-  double acc[MAX_KDIM] = {};
-  if (sub < lanes) {
-#pragma unroll 2
-    for (int j = sub; j < nb; j += lanes) {
-      const double y = trace_of(L, V, k, b0 + j, g);
+template <bool WIDE>   // WIDE: 32 < k <= 64 (two columns per lane)
+__global__ void __launch_bounds__(GTV_THREADS, WIDE ? 2 : 3) k_gt_v(Layout L, const double* __restrict__ V, int k,
+                                                          double* __restrict__ X, int chunk) {
+  __shared__ double red[GTV_THREADS / 32][MAX_KDIM][64];
+  __shared__ int s_last;
+  const int s = blockIdx.x, c = blockIdx.y, nch = gridDim.y;
+  const int kd = L.kdim[L.occ_pat[s]];
+  const int l0 = L.slot_ptr[L.occ_obase[s]], nl = L.slot_ptr[L.occ_obase[s + 1]] - l0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool c0 = lane < k, c1 = WIDE && lane + 32 < k;
+  const int i_end = min(nl, (c + 1) * chunk);
+  double a0[MAX_KDIM] = {}, a1[MAX_KDIM] = {};
+  if (kd > 0) {
+    for (int i = c * chunk + w; i < i_end; i += 32) {
+      int code[4];
 #pragma unroll
-      for (int m = 0; m < MAX_KDIM; ++m)
-        if (m < kd) acc[m] = fma(Nb[(size_t)j * kd + m], y, acc[m]);
+      for (int u = 0; u < 4; ++u) code[u] = i + 8 * u < i_end ? L.slot_code[l0 + i + 8 * u] : -1;
+      double v0[4], v1[4], cf[4][MAX_KDIM];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int cu = max(code[u], 0);
+        const double* vr = V + (size_t)(cu >> 1) * k + lane;
+        v0[u] = c0 ? vr[0] : 0.0;
+        v1[u] = WIDE && c1 ? vr[32] : 0.0;
+        const double* cp = L.rowg_coef + (size_t)cu * MAX_KDIM;
+#pragma unroll
+        for (int m = 0; m < MAX_KDIM; ++m) cf[u][m] = (m < kd && code[u] >= 0) ? cp[m] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int m = 0; m < MAX_KDIM; ++m) {
+          a0[m] = fma(cf[u][m], v0[u], a0[m]);
+          if (WIDE) a1[m] = fma(cf[u][m], v1[u], a1[m]);
+        }
     }
   }
 #pragma unroll
-  for (int m = 0; m < MAX_KDIM; ++m) red[t][m] = acc[m];
+  for (int m = 0; m < MAX_KDIM; ++m) {
+    red[w][m][lane] = a0[m];
+    red[w][m][lane + 32] = a1[m];
+  }
   __syncthreads();
-  if (t < kk) {
-    for (int m = 0; m < kd; ++m) {
-      double v = 0.0;
-      for (int q = 0; q < lanes; ++q) v += red[q * kk + t][m];
-      X[(size_t)(g0 + m) * k + gbase + t] = v;
-    }
+  const int t = threadIdx.x;
+  double* part = L.gtv_part + (size_t)s * nch * MAX_KDIM * 64;
+  for (int i = t; i < kd * k; i += blockDim.x) {
+    const int m = i / k, g = i % k;
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < GTV_THREADS / 32; ++q) v += red[q][m][g];
+    if (nch == 1)
+      X[(size_t)(L.occ_gofs[s] + m) * k + g] = v;
+    else
+      part[((size_t)c * MAX_KDIM + m) * 64 + g] = v;
   }
+  if (nch == 1) return;
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(&L.gtv_ticket[s], 1u) == (unsigned)(nch - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int i = t; i < kd * k; i += blockDim.x) {
+    const int m = i / k, g = i % k;
+    double v = 0.0;
+    for (int q = 0; q < nch; ++q) v += __ldcg(part + ((size_t)q * MAX_KDIM + m) * 64 + g);
+    X[(size_t)(L.occ_gofs[s] + m) * k + g] = v;
+  }
+  if (t == 0) L.gtv_ticket[s] = 0u;
 }
 
-// out[row][g] = beta*out + alpha * sum_{slots of row} sign * sum_m Nb[j][m] A[gofs+m][g]
+// out[row][g] = beta*out + alpha * sum over the row's slots: (sign Nb[j]) . A[gofs(s)..][g], from the per-row
+// tables (coarse column, kernel dimension and signed coefficients of each slot), so that the only dependent
+// load is A's (small, cache-resident)
 __global__ void k_g_apply(Layout L, const double* __restrict__ A, int k, double alpha, double beta,
                           double* __restrict__ out) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -65,18 +104,16 @@ __global__ void k_g_apply(Layout L, const double* __restrict__ A, int k, double 
   double acc = 0.0;
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
-    const int sg = L.row_sign[2 * row + e];
-    if (sg == 0) continue;
-    const int slot = L.row_slot[2 * row + e];
-    const int s = L.slot_occ[slot];
-    const int p = L.occ_pat[s];
-    const int kd = L.kdim[p];
-    const int j = slot - L.occ_obase[s];
-    const double* Nb = L.Nb[p] + (size_t)j * kd;
-    const double* a = A + (size_t)L.occ_gofs[s] * k + g;
+    const int g0 = L.rowg_gofs[2 * row + e];
+    if (g0 < 0) continue;
+    const int kd = L.rowg_kd[2 * row + e];
+    const double* c = L.rowg_coef + (size_t)(2 * row + e) * MAX_KDIM;
+    const double* a = A + (size_t)g0 * k + g;
     double t = 0.0;
-    for (int m = 0; m < kd; ++m) t = fma(Nb[m], a[(size_t)m * k], t);
-    acc = sg > 0 ? acc + t : acc - t;
+#pragma unroll
+    for (int m = 0; m < MAX_KDIM; ++m)
+      if (m < kd) t = fma(c[m], a[(size_t)m * k], t);
+    acc += t;
   }
   double* o = out + idx;
   *o = (beta == 0.0 ? 0.0 : beta * *o) + alpha * acc;
@@ -119,42 +156,88 @@ __global__ void __launch_bounds__(128) k_gtg(Layout L, const int* __restrict__ p
   }
 }
 
-template <typename TO>
-__global__ void k_gather(Layout L, const double* __restrict__ V, int k, PatView<TO> Y, double alpha, double beta) {
+// Gather of one tile of GT_SLOTS slots of an occurrence (grid: occurrence x tile).  The tile's slot pointers and
+// links (a contiguous range of the slot CSR) are staged in shared memory; warp w takes slots w, w + 8, ...: the
+// first link of all its eight slots is loaded at once (most slots have one link), further links after; lane =
+// column g (and g + 32), so a link reads one contiguous row of V.  The traces go through a shared tile and are
+// written column by column (pattern frame, Eq. 9 blocked storage), coalesced over the slots.  Per slot the
+// links are added in CSR order, as the plain definition does.
+constexpr int GT_SLOTS = 64, GT_LINKS = 512;
+template <typename TO, bool SPLIT>   // SPLIT: FP32 value split into a tf32 pair, hi -> Y, lo -> Y2
+__global__ void __launch_bounds__(256) k_gather_tile(Layout L, const double* __restrict__ V, int k, PatView<TO> Y,
+                                                     PatView<TO> Y2, double alpha, double beta) {
+  __shared__ int sptr[GT_SLOTS + 1];
+  __shared__ int srow[GT_LINKS];
+  __shared__ int8_t ssg[GT_LINKS];
+  __shared__ double tile[GT_SLOTS][65];
   const int s = blockIdx.x;
-  const int p = L.occ_pat[s];
-  const int q = L.occ_q[s];
   const int b0 = L.occ_obase[s], nb = L.occ_obase[s + 1] - b0;
-  TO* base = Y.base[p];
-  const long long ld = Y.ld[p], off = Y.off[p];
-  const int gbase = blockIdx.y * GTV_COLS, kk = min(GTV_COLS, k - gbase);
-  for (int idx = threadIdx.x; idx < nb * kk; idx += blockDim.x) {
-    const int g = gbase + idx / nb, j = idx % nb;
-    const double acc = trace_of(L, V, k, b0 + j, g);
-    TO* y = base + ((long long)q * k + g) * ld + off + j;
-    *y = (TO)((beta == 0.0 ? 0.0 : beta * (double)*y) + alpha * acc);
+  const int j0 = blockIdx.y * GT_SLOTS;
+  if (j0 >= nb) return;   // grid.y covers the largest occurrence
+  const int p = L.occ_pat[s], q = L.occ_q[s];
+  const int ns = min(GT_SLOTS, nb - j0);
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t <= ns) sptr[t] = L.slot_ptr[b0 + j0 + t];
+  __syncthreads();
+  const int e0 = sptr[0], ne = sptr[ns] - e0;
+  const bool fits = ne <= GT_LINKS;
+  if (fits)
+    for (int i = t; i < ne; i += blockDim.x) {
+      srow[i] = L.slot_row[e0 + i];
+      ssg[i] = L.slot_sign[e0 + i];
+    }
+  __syncthreads();
+  const int* lr = fits ? srow : L.slot_row + e0;
+  const int8_t* ls = fits ? ssg : L.slot_sign + e0;
+  const bool c0 = lane < k, c1 = lane + 32 < k;
+  double y0[8], y1[8];
+  int ea[8], eb[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int jl = w + 8 * u;
+    ea[u] = jl < ns ? sptr[jl] - e0 : 0;
+    eb[u] = jl < ns ? sptr[jl + 1] - e0 : 0;
+    y0[u] = 0.0;
+    y1[u] = 0.0;
+    if (ea[u] < eb[u]) {
+      const double sg = (double)ls[ea[u]];
+      const double* vr = V + (size_t)lr[ea[u]] * k + lane;
+      if (c0) y0[u] = fma(sg, vr[0], 0.0);
+      if (c1) y1[u] = fma(sg, vr[32], 0.0);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    for (int e = ea[u] + 1; e < eb[u]; ++e) {
+      const double sg = (double)ls[e];
+      const double* vr = V + (size_t)lr[e] * k + lane;
+      if (c0) y0[u] = fma(sg, vr[0], y0[u]);
+      if (c1) y1[u] = fma(sg, vr[32], y1[u]);
+    }
+    const int jl = w + 8 * u;
+    if (jl < ns) {
+      tile[jl][lane] = y0[u];
+      tile[jl][lane + 32] = y1[u];
+    }
+  }
+  __syncthreads();
+  const long long ld = Y.ld[p], off = Y.off[p] + j0;
+  for (int idx = t; idx < k * GT_SLOTS; idx += blockDim.x) {
+    const int g = idx / GT_SLOTS, jl = idx % GT_SLOTS;
+    if (jl >= ns) continue;
+    const long long o = ((long long)q * k + g) * ld + off + jl;
+    if (SPLIT) {
+      const float v = (float)tile[jl][g];
+      uint32_t h;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+      Y.base[p][o] = (TO)__uint_as_float(h);
+      Y2.base[p][o] = (TO)(v - __uint_as_float(h));
+    } else {
+      TO* y = Y.base[p] + o;
+      *y = (TO)((beta == 0.0 ? 0.0 : beta * (double)*y) + alpha * tile[jl][g]);
+    }
   }
 }
-
-// Gather with the result split into a tf32 pair: hi = tf32(y) (round to nearest), lo = y - hi (FP32).
-__global__ void k_gather_split(Layout L, const double* __restrict__ V, int k, PatView<float> Yh, PatView<float> Yl) {
-  const int s = blockIdx.x;
-  const int p = L.occ_pat[s];
-  const int q = L.occ_q[s];
-  const int b0 = L.occ_obase[s], nb = L.occ_obase[s + 1] - b0;
-  const int gbase = blockIdx.y * GTV_COLS, kk = min(GTV_COLS, k - gbase);
-  for (int idx = threadIdx.x; idx < nb * kk; idx += blockDim.x) {
-    const int g = gbase + idx / nb, j = idx % nb;
-    const float v = (float)trace_of(L, V, k, b0 + j, g);
-    uint32_t t;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
-    const float h = __uint_as_float(t);
-    const long long o = ((long long)q * k + g) * Yh.ld[p] + Yh.off[p] + j;
-    Yh.base[p][o] = h;
-    Yl.base[p][o] = v - h;
-  }
-}
-
 template <typename TI>
 __global__ void k_scatter(Layout L, PatView<TI> Z, int k, double beta, double* __restrict__ out) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -297,7 +380,10 @@ __global__ void k_scatter_pairs(Layout L, PairView<TI> Z, int k, const int* __re
 void gt_v(const Layout& L, const double* V, int k, double* X, cudaStream_t s) {
   if (L.n_occ == 0) return;
   if (k > 64) throw Error(1, "k > 64");
-  k_gt_v<<<dim3(L.n_occ, ceil_div(k, GTV_COLS)), GTV_THREADS, 0, s>>>(L, V, k, X);
+  if (k > 32)
+    k_gt_v<true><<<dim3(L.n_occ, L.gtv_chunks), GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
+  else
+    k_gt_v<false><<<dim3(L.n_occ, L.gtv_chunks), GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
   FETIRP_LAUNCH_CHECK();
 }
 
@@ -318,11 +404,18 @@ void gtg_dense(const Layout& L, const int*, const int*, int n_pairs, const int* 
   FETIRP_LAUNCH_CHECK();
 }
 
+static int max_slots(const Layout& L) {
+  int m = 1;
+  for (int p = 0; p < L.n_pat; ++p) m = std::max(m, L.n_b[p]);
+  return m;
+}
 template <typename TO>
 void gather(const Layout& L, const double* V, int k, const PatView<TO>& Y, cudaStream_t s, double alpha,
             double beta) {
   if (L.n_occ == 0) return;
-  k_gather<TO><<<dim3(L.n_occ, ceil_div(k, GTV_COLS)), 256, 0, s>>>(L, V, k, Y, alpha, beta);
+  if (k > 64) throw Error(1, "k > 64");
+  k_gather_tile<TO, false><<<dim3(L.n_occ, ceil_div(max_slots(L), GT_SLOTS)), 256, 0, s>>>(L, V, k, Y, Y, alpha,
+                                                                                            beta);
   FETIRP_LAUNCH_CHECK();
 }
 
@@ -337,7 +430,9 @@ void scatter(const Layout& L, const PatView<TI>& Z, int k, double beta, double* 
 void gather_split(const Layout& L, const double* V, int k, const PatView<float>& Yh, const PatView<float>& Yl,
                   cudaStream_t s) {
   if (L.n_occ == 0) return;
-  k_gather_split<<<dim3(L.n_occ, ceil_div(k, GTV_COLS)), 256, 0, s>>>(L, V, k, Yh, Yl);
+  if (k > 64) throw Error(1, "k > 64");
+  k_gather_tile<float, true><<<dim3(L.n_occ, ceil_div(max_slots(L), GT_SLOTS)), 256, 0, s>>>(L, V, k, Yh, Yl, 1.0,
+                                                                                             0.0);
   FETIRP_LAUNCH_CHECK();
 }
 

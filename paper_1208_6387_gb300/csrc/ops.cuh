@@ -23,6 +23,7 @@ struct Layout {
   const int* slot_ptr;
   const int* slot_row;
   const int8_t* slot_sign;
+  const int* slot_code;   // 2 row + e: the link's entry (row, e-th slot of the row) in the per-row tables
   // the same links in ELL form: ell_w entries per slot (sign 0 = padding, row 0)
   int ell_w = 1;
   const int* ell_row;
@@ -41,6 +42,16 @@ struct Layout {
   const double* Nb[MAXP];   // n_b x kdim row-major: kernel restricted to the boundary (pattern frame)
   int n_b[MAXP];
   int kdim[MAXP];
+  // G by row: for each of the row's two slots, the occurrence's first coarse column (-1: none), its kernel
+  // dimension and sign * Nb[j][m] (m < 6)
+  const int* rowg_gofs;
+  const int* rowg_kd;
+  const double* rowg_coef;
+  // G^T V: links per CTA, CTAs per occurrence, per-chunk partial sums (n_occ x gtv_chunks x 6 x 64) and the
+  // per-occurrence tickets of the last-CTA reduction (zero between launches)
+  int gtv_chunk = 1, gtv_chunks = 1;
+  double* gtv_part;
+  unsigned* gtv_ticket;
 };
 
 // ---- coarse space G = [ ... B(s) N(s) ... ] (Eq. 3) ------------------------------------------------
