@@ -176,6 +176,8 @@ struct fetirp_ctx_s {
   DBuf<int> d_row_grp, d_row_zld, d_rowg_gofs, d_rowg_kd;
   DBuf<double> d_row_wt, d_rowg_coef;
   DBuf<int> d_slot_code;        // per link: 2 row + e (its entry in the per-row tables)
+  int n_grp_entries = 0;        // entries of the per-group row lists
+  DBuf<double> grp_wr;          // per entry: w r[row] in FP64 and as an FP32 pair (history Gram scratch)
   DBuf<double> d_gtv_part;      // G^T V per-chunk partial sums
   DBuf<unsigned> d_gtv_ticket;  // G^T V last-CTA tickets (self-resetting)
   DBuf<long long> d_row_z;
@@ -683,6 +685,8 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   ctx->d_occ_group.upload(group, s);
   ctx->max_group_rows = 0;
   for (int g = 0; g < k; ++g) ctx->max_group_rows = std::max(ctx->max_group_rows, grp_ptr[g + 1] - grp_ptr[g]);
+  ctx->n_grp_entries = grp_ptr[k];
+  ctx->grp_wr.ensure(2 * (size_t)std::max(ctx->n_grp_entries, 1));
   ctx->d_ell_row.upload(ell_row, s);
   ctx->d_ell_sign.upload(ell_sign, s);
   ctx->d_grp_ptr.upload(grp_ptr, s);
@@ -1046,7 +1050,7 @@ void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
   {
     PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 0.0, 0.0);
     gram_split<TH>((int)cap, d_cols, k, Qh, nl, k, ctx->r.p, ctx->d_grp_ptr.p, ctx->d_grp_row.p, ctx->d_grp_w.p,
-                   ctx->max_group_rows, ctx->C.p, ctx->gram_part, s);
+                   ctx->n_grp_entries, ctx->max_group_rows, ctx->C.p, ctx->gram_part, ctx->grp_wr, s);
   }
   project(ctx, ctx->Zr.p, k);
   {
@@ -1434,7 +1438,7 @@ void ensure_history(fetirp_ctx ctx) {
   const int gs_chunks = std::max(1, ceil_div(ctx->max_group_rows, 128));
   ctx->gram_part.ensure(std::max<size_t>(std::max<size_t>((size_t)(chunks + 1) * cap * k, (size_t)304 * 64 * 64),
                                          (size_t)gs_chunks * cap * k));
-  ctx->tu_part.ensure((size_t)tall_update_splits(nl, (int)cap) * nl * k);
+  ctx->tu_part.ensure(std::max(tall_update_scratch(nl, (int)cap, k, true), tall_update_scratch(nl, (int)cap, k, false)));
   {
     const int tiles = ceil_div(nl, 64);
     if (ctx->tu_tickets.n < (size_t)tiles) {

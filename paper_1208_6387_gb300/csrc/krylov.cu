@@ -149,6 +149,9 @@ __global__ void __launch_bounds__(512) k_normalise(int k, const double* __restri
   __syncthreads();
   for (int idx = tid; idx < k * k; idx += blockDim.x) {
     const int i = idx / k, j = idx % k;
+    // both triangles are summed and averaged: the computed W^T Q is not symmetric to working accuracy (W is
+    // rebuilt from an FP32 history, in range(P) only to FP32 accuracy), and one triangle alone slows the
+    // mixed-precision inner solve by an order of magnitude on the 3D elastic structure
     A[i][j] = 0.5 * (ext[i * (k + 1) + j] + ext[j * (k + 1) + i]);
   }
   if (tid < k) { done[tid] = 0; rhs[tid] = ext[tid * (k + 1) + k]; ipiv[tid] = -1; }
@@ -506,20 +509,34 @@ template void update<float>(int, int, const double*, const double*, const double
                             const int*, double*, double*, double*, int, cudaStream_t, const AdvanceArgs&);
 
 // C[c][g] = sum over the rows of group g: w(row) * r[row] * Qh[row][c]  (= Qh^T S(r), the split multivector
-// S(r) having at most two nonzero groups per row).  Work items (64-column tile, group, 128-row chunk) are
-// taken from the live history count a on the device, so a fixed grid serves every iteration of a captured
-// graph.  Per item the chunk's (row, w r[row]) pairs are staged in shared memory, the 8 warps take every
-// 8th row (a warp reads 64 consecutive history columns of one row), and the warp sums are added in warp
-// order; chunk partials are then added in chunk order (deterministic).
-constexpr int GS_ROWS = 128;   // rows per chunk
+// S(r) having at most two nonzero groups per row).  The products w(row) r[row] of the group lists are formed
+// once per call (k_group_wr: FP64, and split into an FP32 hi + lo pair for an FP32 history).  Work items
+// (64-column tile, group, 256-row chunk) are taken from the live history count a on the device, so a fixed
+// grid serves every iteration of a captured graph.  Per item the chunk's rows and weights are staged in shared
+// memory with one round of independent loads, the 8 warps take every 8th row (a warp reads 64 consecutive
+// history columns of one row), and the warp sums are added in warp order; chunk partials are then added in
+// chunk order (deterministic).
+constexpr int GS_ROWS = 256;   // rows per chunk
 constexpr int GS_COLS = 64;    // history columns per item
-constexpr int GS_GRID = 608;   // 4 CTAs per SM
+constexpr int GS_GRID = 1216;  // 8 CTAs per SM
+__global__ void k_group_wr(int total, const int* __restrict__ grp_row, const double* __restrict__ grp_w,
+                           const double* __restrict__ r, double* __restrict__ wd, float* __restrict__ wh,
+                           float* __restrict__ wl) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const double v = grp_w[e] * r[grp_row[e]];
+  wd[e] = v;
+  const float vh = (float)v;
+  wh[e] = vh;
+  wl[e] = (float)(v - (double)vh);
+}
 template <typename TH>
 __global__ void __launch_bounds__(256) k_gram_split(int a_max, const int* __restrict__ d_a, int k,
                                                     const TH* __restrict__ Qh, int n, int hk,
-                                                    const double* __restrict__ r, const int* __restrict__ grp_ptr,
-                                                    const int* __restrict__ grp_row, const double* __restrict__ grp_w,
-                                                    int chunks, int rows_per_chunk, double* __restrict__ partial) {
+                                                    const int* __restrict__ grp_ptr, const int* __restrict__ grp_row,
+                                                    const double* __restrict__ wd, const float* __restrict__ wh,
+                                                    const float* __restrict__ wl, int chunks,
+                                                    double* __restrict__ partial) {
   __shared__ int srow[GS_ROWS];
   __shared__ double sw[GS_ROWS];
   __shared__ float swh[GS_ROWS], swl[GS_ROWS];   // w r[row] split into FP32 hi + lo (FP32 history)
@@ -531,26 +548,25 @@ __global__ void __launch_bounds__(256) k_gram_split(int a_max, const int* __rest
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int ct = it % ctiles, rest = it / ctiles, g = rest % k, ch = rest / k;
-    const int e0 = grp_ptr[g] + ch * rows_per_chunk, e_end = min(grp_ptr[g + 1], e0 + rows_per_chunk);
+    const int e0 = grp_ptr[g] + ch * GS_ROWS, cnt = min(GS_ROWS, grp_ptr[g + 1] - e0);
     const int c0 = ct * GS_COLS + lane, c1 = c0 + 32;
     const bool ok0 = c0 < a, ok1 = c1 < a;
     const TH* q0p = Qh + hist_col(ok0 ? c0 : 0, n, hk);
     const TH* q1p = Qh + hist_col(ok1 ? c1 : 0, n, hk);
     double a0 = 0.0, a1 = 0.0;
     float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-    for (int sb = e0; sb < e_end; sb += GS_ROWS) {   // the chunk in stages of GS_ROWS rows
-      const int cnt = min(GS_ROWS, e_end - sb);
-      __syncthreads();   // the previous stage's (or item's) shared-memory reads are done
-      if (tid < cnt) {
-        const int row = grp_row[sb + tid];
-        const double v = grp_w[sb + tid] * r[row];
-        srow[tid] = row;
-        sw[tid] = v;
-        const float vh = (float)v;
-        swh[tid] = vh;
-        swl[tid] = (float)(v - (double)vh);
+    __syncthreads();   // the previous item's shared-memory reads are done
+    if (tid < cnt) {
+      srow[tid] = grp_row[e0 + tid];
+      if (sizeof(TH) == 4) {
+        swh[tid] = wh[e0 + tid];
+        swl[tid] = wl[e0 + tid];
+      } else {
+        sw[tid] = wd[e0 + tid];
       }
-      __syncthreads();
+    }
+    __syncthreads();
+    {
       if (sizeof(TH) == 4) {
         // FP32 history: double-single arithmetic on the FP32 pipe (Dekker 1971; Knuth TwoSum).  q * s_hi is
         // split exactly into p + e by an FMA, q * s_lo is rounded (its error is ~2^-48 |q s|), and each column
@@ -591,8 +607,7 @@ __global__ void __launch_bounds__(256) k_gram_split(int a_max, const int* __rest
       a0 = (double)h0 + (double)l0;
       a1 = (double)h1 + (double)l1;
     }
-    __syncthreads();   // an item with an empty chunk has no stage barrier before this
-    red[warp][lane] = a0;
+    red[warp][lane] = a0;   // (the previous item's reads of red ended before this item's staging barrier)
     red[warp][lane + 32] = a1;
     __syncthreads();
     if (tid < GS_COLS) {
@@ -699,24 +714,31 @@ __global__ void k_reduce_chunks_dyn(int a_max, const int* __restrict__ d_a, int 
 
 template <typename TH>
 void gram_split(int a_max, const int* d_a, int k, const TH* Qh, int n, int hk, const double* r, const int* grp_ptr,
-                const int* grp_row, const double* grp_w, int max_group_rows, double* C, DBuf<double>& partial,
-                cudaStream_t s) {
+                const int* grp_row, const double* grp_w, int n_entries, int max_group_rows, double* C,
+                DBuf<double>& partial, DBuf<double>& wr, cudaStream_t s) {
   if (a_max <= 0) return;
-  // large groups: 512-row chunks (fewer items and partials), walked in 128-row stages
-  const int rows_per_chunk = max_group_rows > 8192 ? 4 * GS_ROWS : GS_ROWS;
-  const int chunks = std::max(1, ceil_div(max_group_rows, rows_per_chunk));
+  const int chunks = std::max(1, ceil_div(max_group_rows, GS_ROWS));
   partial.ensure((size_t)chunks * a_max * k);
+  wr.ensure(2 * (size_t)std::max(n_entries, 1));
+  double* wd = wr.p;
+  float* wh = reinterpret_cast<float*>(wr.p + std::max(n_entries, 1));
+  float* wl = wh + std::max(n_entries, 1);
+  if (n_entries > 0) {
+    k_group_wr<<<ceil_div(n_entries, 256), 256, 0, s>>>(n_entries, grp_row, grp_w, r, wd, wh, wl);
+    FETIRP_LAUNCH_CHECK();
+  }
   const int items = ceil_div(a_max, GS_COLS) * k * chunks;
-  k_gram_split<TH><<<std::min(items, GS_GRID), 256, 0, s>>>(a_max, d_a, k, Qh, n, hk, r, grp_ptr, grp_row, grp_w,
-                                                             chunks, rows_per_chunk, partial.p);
+  k_gram_split<TH><<<std::min(items, GS_GRID), 256, 0, s>>>(a_max, d_a, k, Qh, n, hk, grp_ptr, grp_row, wd, wh, wl,
+                                                             chunks, partial.p);
   FETIRP_LAUNCH_CHECK();
   k_reduce_chunks_dyn<<<ceil_div(a_max * k, 256), 256, 0, s>>>(a_max, d_a, k, chunks, partial.p, C);
   FETIRP_LAUNCH_CHECK();
 }
 template void gram_split<double>(int, const int*, int, const double*, int, int, const double*, const int*,
-                                 const int*, const double*, int, double*, DBuf<double>&, cudaStream_t);
+                                 const int*, const double*, int, int, double*, DBuf<double>&, DBuf<double>&,
+                                 cudaStream_t);
 template void gram_split<float>(int, const int*, int, const float*, int, int, const double*, const int*, const int*,
-                                const double*, int, double*, DBuf<double>&, cudaStream_t);
+                                const double*, int, int, double*, DBuf<double>&, DBuf<double>&, cudaStream_t);
 
 template <typename TH>
 void hist_dot(int n, int a, const TH* Qh, int hk, const double* r, double* C, DBuf<double>& partial,
@@ -746,7 +768,7 @@ constexpr int TU_ROWS = 64, TU_CH = 32;
 template <typename TH, int KP>
 __global__ void __launch_bounds__(256) k_tall_update(int n, int a_max, const int* __restrict__ d_a, int k,
                                                      const TH* __restrict__ Wh, int hk,
-                                                     const double* __restrict__ C, int splits, TH* __restrict__ part,
+                                                     const TH* __restrict__ C, int splits, TH* __restrict__ part,
                                                      unsigned* __restrict__ tickets, double alpha,
                                                      double* __restrict__ W) {
   constexpr int TXC = KP < 16 ? KP : 16;           // column threads
@@ -778,7 +800,7 @@ __global__ void __launch_bounds__(256) k_tall_update(int n, int a_max, const int
 #pragma unroll
     for (int i = 0; i < LC; ++i) {
       const int idx = tid + 256 * i, cc = idx / KP, gg = idx % KP;
-      pc[i] = (idx < TU_CH * KP && c0 + cc < c_end && gg < k) ? (TH)C[(size_t)(c0 + cc) * k + gg] : TH(0);
+      pc[i] = (idx < TU_CH * KP && c0 + cc < c_end && gg < k) ? C[(size_t)(c0 + cc) * k + gg] : TH(0);
     }
   };
   if (c_begin < c_end) load(c_begin);
@@ -855,9 +877,24 @@ __global__ void __launch_bounds__(256) k_tall_update(int n, int a_max, const int
   }
 }
 
+// Cf[i] = (float)C[i] for the first a * k coefficients (a read on the device): the FP32 history update then
+// loads FP32 coefficients (one conversion per coefficient instead of one per coefficient and row tile)
+__global__ void k_coef_to_f32(int a_max, const int* __restrict__ d_a, int k, const double* __restrict__ C,
+                              float* __restrict__ Cf) {
+  const int a = d_a ? min(*d_a, a_max) : a_max;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a * k; i += gridDim.x * blockDim.x) Cf[i] = (float)C[i];
+}
+
 int tall_update_splits(int n, int a_max) {
   const int tiles = ceil_div(n, TU_ROWS);
   return std::max(1, std::min(std::max(1, 1216 / tiles), ceil_div(a_max, TU_CH)));
+}
+
+// scratch of tall_update in TH elements: split partials, then (FP32 history) the FP32 coefficients
+static size_t tu_cf_off(int n, int a_max, int k) { return ((size_t)tall_update_splits(n, a_max) * n * k + 63) / 64 * 64; }
+size_t tall_update_scratch(int n, int a_max, int k, bool fp32) {
+  const size_t elems = fp32 ? tu_cf_off(n, a_max, k) + (size_t)a_max * k : (size_t)tall_update_splits(n, a_max) * n * k;
+  return (elems * (fp32 ? 4 : 8) + 7) / 8;
 }
 
 template <typename TH>
@@ -867,22 +904,29 @@ void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, int hk, 
   if (k > 64) throw Error(1, "k > 64");
   const int splits = tall_update_splits(n, a_max);
   const int tiles = ceil_div(n, TU_ROWS);
-  const size_t need = ((size_t)splits * n * k * sizeof(TH) + sizeof(double) - 1) / sizeof(double);
-  scratch.ensure(need);
+  const size_t cf_off = tu_cf_off(n, a_max, k);
+  scratch.ensure(tall_update_scratch(n, a_max, k, sizeof(TH) == 4));
   if (tickets.n < (size_t)tiles) {   // tickets start at zero and every use leaves them at zero
     tickets.alloc(tiles);
     FETIRP_CUDA(cudaMemsetAsync(tickets.p, 0, sizeof(unsigned) * tiles, s));
   }
   TH* part = reinterpret_cast<TH*>(scratch.p);
+  const TH* Ct = reinterpret_cast<const TH*>(C);
+  if (sizeof(TH) == 4) {
+    float* Cf = reinterpret_cast<float*>(part + cf_off);
+    k_coef_to_f32<<<std::min(ceil_div(a_max * k, 256), 1216), 256, 0, s>>>(a_max, d_a, k, C, Cf);
+    FETIRP_LAUNCH_CHECK();
+    Ct = reinterpret_cast<const TH*>(Cf);
+  }
   const dim3 grid(tiles, splits);
   if (k <= 8)
-    k_tall_update<TH, 8><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, hk, C, splits, part, tickets.p, alpha, W);
+    k_tall_update<TH, 8><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, hk, Ct, splits, part, tickets.p, alpha, W);
   else if (k <= 16)
-    k_tall_update<TH, 16><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, hk, C, splits, part, tickets.p, alpha, W);
+    k_tall_update<TH, 16><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, hk, Ct, splits, part, tickets.p, alpha, W);
   else if (k <= 32)
-    k_tall_update<TH, 32><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, hk, C, splits, part, tickets.p, alpha, W);
+    k_tall_update<TH, 32><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, hk, Ct, splits, part, tickets.p, alpha, W);
   else
-    k_tall_update<TH, 64><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, hk, C, splits, part, tickets.p, alpha, W);
+    k_tall_update<TH, 64><<<grid, 256, 0, s>>>(n, a_max, d_a, k, Wh, hk, Ct, splits, part, tickets.p, alpha, W);
   FETIRP_LAUNCH_CHECK();
 }
 template void tall_update<double>(int, int, const int*, int, const double*, int, const double*, double, double*,

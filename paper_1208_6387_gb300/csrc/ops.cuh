@@ -213,10 +213,11 @@ void gram(int n, int a, int b, const TA* A, int lda, const TB* B, int ldb, doubl
 // (double-single for an FP32 history).  Qh: n rows in the block layout of width hk (hist_col).  The number of
 // stored directions a is read from d_a on the device when d_a != NULL (at most a_max), so one captured launch
 // serves every iteration.
+// n_entries = grp_ptr[k]; wr: scratch of 2 n_entries doubles (the weighted split values, FP64 and FP32 hi + lo).
 template <typename TH>
 void gram_split(int a_max, const int* d_a, int k, const TH* Qh, int n, int hk, const double* r, const int* grp_ptr,
-                const int* grp_row, const double* grp_w, int max_group_rows, double* C, DBuf<double>& partial,
-                cudaStream_t s);
+                const int* grp_row, const double* grp_w, int n_entries, int max_group_rows, double* C,
+                DBuf<double>& partial, DBuf<double>& wr, cudaStream_t s);
 // C[c] = sum_rows Qh[row][c] r[row] for c < a (history times one vector, FP64-class sums; Qh in the block
 // layout of width hk); partial must hold at least a values (it is not grown: captured graphs share it)
 template <typename TH>
@@ -227,6 +228,8 @@ void hist_dot(int n, int a, const TH* Qh, int hk, const double* r, double* C, DB
 // scratch: split partials, tall_update_splits(n, a_max) * n * k values of TH; tickets: one counter per 64-row
 // tile, zero between calls (both grown here; callers that capture graphs size them first).
 int tall_update_splits(int n, int a_max);
+// device scratch (in doubles) that tall_update needs for n rows, a_max columns, k outputs
+size_t tall_update_scratch(int n, int a_max, int k, bool fp32);
 template <typename TH>
 void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, int hk, const double* C, double alpha,
                  double* W, DBuf<double>& scratch, DBuf<unsigned>& tickets, cudaStream_t s);
