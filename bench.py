@@ -9,7 +9,7 @@ device when the timed region starts; the L2 cache is flushed between steps (a 25
 whole working set fits in L2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision fp64|fp32]
-                    [--k K] [--workload c2|c1]
+                    [--k K] [--workload c2|c1|c3]
 
 Under torchrun (N > 1) every rank solves its own independently seeded structure (weak scaling, no collective
 on the data path); rank 0 prints the JSON line with the slowest rank's time.
@@ -41,14 +41,18 @@ WORKLOADS = {
 }
 PHASE_KERNELS = {  # the kernels each phase launches
     "factor": "k_potrf_tile, k_trsm_tiles, k_update_pairs, k_tile_inverse, k_tri_*", "coarse": "k_gtg, k_gemm_f64",
-    "local": "k_local_gemm / k_tc_gemm", "gather": "k_gather", "scatter": "k_scatter",
-    "project": "k_gt_v, k_small_gemm, k_g_apply", "gram": "k_gram_split + k_reduce_chunks_dyn, k_eta_partial",
-    "reorth": "k_tall_update", "update": "k_split, k_update",
+    "local": "k_local_gemm / k_tc_gemm", "gather": "k_gather_tile", "scatter": "k_scatter",
+    "project": "k_gt_v, k_small_gemm, k_g_apply",
+    "gram": "k_group_wr, k_gram_split + k_reduce_chunks_dyn, k_eta_partial + k_eta_group_sums",
+    "reorth": "k_tall_update / k_tall_update_w32", "update": "k_split, k_update",
     "recover": "k_tri_*, k_unpermute_rotate", "normalise": "k_normalise",
     "iterate": "k_persist (whole block iterations in one cooperative launch)",
 }
+# DRAM bytes (read + write) of one k_persist launch from an ncu capture of the bench command (profiles/
+# k_persist_c2.md: C2, FP32 inner products, k = 8); reported as the roofline's traffic for that configuration only
+PERSIST_C2_TRAFFIC_BYTES = 1.157120e6 + 0.392960e6
 PHASE_BOUND = {  # roofline resource of each phase's kernels
-    "factor": "alu", "coarse": "alu", "local": "alu", "gather": "hbm", "scatter": "hbm", "project": "hbm",
+    "factor": "alu", "coarse": "alu", "local": "alu", "gather": "hbm", "scatter": "hbm", "project": "alu",
     "gram": "alu", "reorth": "alu", "update": "alu", "recover": "alu", "normalise": "alu", "iterate": "hbm",
 }
 
@@ -241,13 +245,21 @@ def run_ours(args, rank, world, local):
         peak_note = f"hbm_gbs of {src}"
     else:
         achieved = ph_fl[dom] / (ph_ms[dom] / 1e3) / 1e12
-        fp32 = (name in ("local", "reorth") and args.precision != "fp64")
-        peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
         unit = "TFLOP/s"
-        peak_note = ("FP32 SIMT peak derived from 152 SMs x 128 lanes x 2070 MHz" if fp32 else
-                     "FP64 nominal 1.25 TFLOP/s (152 SMs x 2070 MHz; DFMA probe measured 1.19)")
+        if name == "local" and args.precision == "tf32x3":   # tcgen05 kind::tf32 (useful flops, 3 MMAs each)
+            bound = "tensor"
+            peak = peaks["bf16_tflops"] * 1.1 / 2.25
+            peak_note = f"tf32 tensor: bf16_tflops of {src} x 1.1/2.25 (nominal tf32/bf16 ratio)"
+        elif name in ("local", "reorth") and args.precision != "fp64":
+            peak = FP32_PEAK_TFLOPS
+            peak_note = "FP32 SIMT peak derived from 152 SMs x 128 lanes x 2070 MHz"
+        else:
+            peak = FP64_PEAK_TFLOPS
+            peak_note = "FP64 nominal 1.25 TFLOP/s (152 SMs x 2070 MHz; DFMA probe measured 1.19)"
     roof = {"kernel": PHASE_KERNELS[name], "phase": name, "bound": bound, "achieved": round(achieved, 4),
-            "peak": round(peak, 3), "unit": unit, "frac": round(achieved / peak, 5), "traffic": None,
+            "peak": round(peak, 3), "unit": unit, "frac": round(achieved / peak, 5),
+            "traffic": (PERSIST_C2_TRAFFIC_BYTES if (name == "iterate" and args.workload == "c2"
+                                                     and args.precision == "fp32" and prob.k == 8) else None),
             "peak_source": peak_note, "launches_per_step": float(ph_ln[dom]) / args.steps,
             "ms_per_launch": round(per_launch_ms, 5),
             "share_of_step": round(float(ph_ms[dom]) / total_ms, 4) if world == 1 else None,

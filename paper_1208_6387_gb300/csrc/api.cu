@@ -177,8 +177,10 @@ struct fetirp_ctx_s {
   DBuf<double> d_row_wt, d_rowg_coef;
   DBuf<int> d_slot_code;        // per link: 2 row + e (its entry in the per-row tables)
   int n_grp_entries = 0;        // entries of the per-group row lists
+  double n_gcoef = 0;           // coefficients of G by row (sum over rows and their slots of the mode count)
   DBuf<double> grp_wr;          // per entry: w r[row] in FP64 and as an FP32 pair (history Gram scratch)
   DBuf<double> d_gtv_part;      // G^T V per-chunk partial sums
+  DBuf<double> sg_part;         // inner-dimension slices of (G^T G)^{-1} X
   DBuf<unsigned> d_gtv_ticket;  // G^T V last-CTA tickets (self-resetting)
   DBuf<long long> d_row_z;
   DBuf<unsigned> d_pbar;     // {barrier count, barrier generation, eta ticket, error flag, 64 group tickets}
@@ -739,6 +741,8 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
           rowg_coef[(2 * (size_t)r + e) * 6 + m] =
               row_sign[2 * (size_t)r + e] * hNb[occ_pat[o]][(size_t)(slot - obase[o]) * P.kdim + m];
       }
+    ctx->n_gcoef = 0;
+    for (int kd : rowg_kd) ctx->n_gcoef += kd;
     ctx->d_rowg_gofs.upload(rowg_gofs, s);
     ctx->d_rowg_kd.upload(rowg_kd, s);
     ctx->d_rowg_coef.upload(rowg_coef, s);
@@ -769,6 +773,7 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
     L.kdim[p] = ctx->pats[p]->kdim;
     max_nb = std::max(max_nb, ctx->pats[p]->n_b);
   }
+  L.row_grp = ctx->d_row_grp.p; L.row_wt = ctx->d_row_wt.p;
   L.rowg_gofs = ctx->d_rowg_gofs.p; L.rowg_kd = ctx->d_rowg_kd.p; L.rowg_coef = ctx->d_rowg_coef.p;
   L.slot_code = ctx->d_slot_code.p;
   {  // G^T V chunks: at most 512 links per CTA, and at least two CTAs per SM while chunks keep >= 64 links
@@ -809,6 +814,7 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   else ctx->c.zero(s);
   ctx->Xc.ensure((size_t)std::max(ctx->n_G, 1) * 64);
   ctx->Ac.ensure((size_t)std::max(ctx->n_G, 1) * 64);
+  ctx->sg_part.ensure((size_t)small_gemm_parts(std::max(ctx->n_G, 1)) * std::max(ctx->n_G, 1) * 64);
   if (ctx->n_G > 0) {
     gtg_dense(L, nullptr, nullptr, ctx->n_pairs, ctx->d_pair_s.p, ctx->d_pair_t.p, ctx->GtG.p, s);
     ctx->planG = dense_plan(ctx->n_Gpad / TILE);
@@ -850,7 +856,7 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   ctx->W.ensure((size_t)nl * k); ctx->Q.ensure((size_t)nl * k); ctx->Zr.ensure((size_t)nl * k);
   ctx->V1.ensure((size_t)nl * 64); ctx->V2.ensure((size_t)nl * 64);
   ctx->eta.ensure((size_t)k * k); ctx->wr.ensure(k);
-  ctx->eta_part.ensure((size_t)(eta_chunks(nl) + 1) * k * (k + 1)); ctx->T.ensure((size_t)k * k); ctx->alpha.ensure(k);
+  ctx->eta_part.ensure((size_t)(eta_chunks(nl) + ETA_GROUPS) * k * (k + 1)); ctx->T.ensure((size_t)k * k); ctx->alpha.ensure(k);
   ctx->n_kept.ensure(1);
   ctx->d_state.ensure(4);
   if (!ctx->tc_error.p) { ctx->tc_error.alloc(1); ctx->tc_error.zero(s); }
@@ -869,11 +875,12 @@ void project(fetirp_ctx ctx, double* V, int k) {
   if (ctx->n_G == 0) return;
   cudaStream_t s = ctx->stream;
   const double nl = ctx->L.n_lambda, nG = ctx->n_G;
-  PhaseScope ph(ctx, FETIRP_PHASE_PROJECT, 2.0 * nG * nG * k + 4.0 * nl * k * 6.0, 16.0 * nl * k + 8.0 * nG * nG);
+  // G^T V and G A: 2 flops per coefficient of G (sign N_b[j][m] per link) and column, each; (G^T G)^{-1} X
+  PhaseScope ph(ctx, FETIRP_PHASE_PROJECT, 2.0 * nG * nG * k + 4.0 * ctx->n_gcoef * k, 16.0 * nl * k + 8.0 * nG * nG);
   ctx->Xc.ensure((size_t)ctx->n_G * k);
   ctx->Ac.ensure((size_t)ctx->n_G * k);
   gt_v(ctx->L, V, k, ctx->Xc.p, s);
-  small_gemm(ctx->n_G, k, ctx->Ginv.p, ctx->Xc.p, ctx->Ac.p, s);
+  small_gemm(ctx->n_G, k, ctx->Ginv.p, ctx->Xc.p, ctx->Ac.p, s, ctx->sg_part.p);
   g_apply(ctx->L, ctx->Ac.p, k, -1.0, 1.0, V, s);
 }
 
@@ -1039,6 +1046,7 @@ template <> float* hist_q<float>(fetirp_ctx ctx) { return ctx->Qhist32.p; }
 // C = Q_h^T S(r) is taken from the split structure of S(r) (at most two nonzero columns per row).
 template <typename TH>
 void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
+  int eta_off = 0;
   cudaStream_t s = ctx->stream;
   const int nl = ctx->L.n_lambda, k = ctx->k;
   const long long cap = ctx->hist_cap;
@@ -1060,11 +1068,11 @@ void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
   apply_F(ctx, ctx->Zr.p, ctx->Q.p, k, prec, false, true);   // P~ = P^T F W (Table 1 line 5.1)
   {
     PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 0.0, 0.0);
-    eta_partials(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta_part, s);
+    eta_off = eta_partials(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta_part, s);
   }
   {
     PhaseScope ph(ctx, FETIRP_PHASE_NORMALISE, 0.0, 0.0);
-    normalise(k, ctx->eta_part.p, eta_chunks(nl),
+    normalise(k, ctx->eta_part.p + (size_t)eta_off * k * (k + 1), eta_off ? ETA_GROUPS : eta_chunks(nl),
               prec == FETIRP_PREC_FP64 ? ctx->opt.eig_trunc : ctx->opt.eig_trunc_inner, ctx->T.p, ctx->alpha.p,
               ctx->n_kept.p, s);
   }
@@ -1094,7 +1102,7 @@ void account_iteration(fetirp_ctx ctx, int prec, long long a, double es, bool pe
   F[FETIRP_PHASE_NORMALISE] += (2.0 / 3.0) * k * k * k;   // pivoted Cholesky + triangular inverse, O(k^3)
   B[FETIRP_PHASE_NORMALISE] += 8.0 * (2.0 * k * k + 2.0 * k);
   B[FETIRP_PHASE_UPDATE] += 8.0 * nl * (3.0 * k + 4.0) + 2.0 * es * nl * k;
-  F[FETIRP_PHASE_PROJECT] += 2.0 * (2.0 * nG * nG * k + 24.0 * nl * k);
+  F[FETIRP_PHASE_PROJECT] += 2.0 * (2.0 * nG * nG * k + 4.0 * ctx->n_gcoef * k);
   B[FETIRP_PHASE_PROJECT] += 2.0 * (16.0 * nl * k + 8.0 * nG * nG);
   const double e_loc = prec == FETIRP_PREC_FP64 ? 8.0 : 4.0;
   double rhs = 0;
@@ -1439,6 +1447,7 @@ void ensure_history(fetirp_ctx ctx) {
   ctx->gram_part.ensure(std::max<size_t>(std::max<size_t>((size_t)(chunks + 1) * cap * k, (size_t)304 * 64 * 64),
                                          (size_t)gs_chunks * cap * k));
   ctx->tu_part.ensure(std::max(tall_update_scratch(nl, (int)cap, k, true), tall_update_scratch(nl, (int)cap, k, false)));
+  tall_update_init();
   {
     const int tiles = ceil_div(nl, 64);
     if (ctx->tu_tickets.n < (size_t)tiles) {
@@ -1565,11 +1574,12 @@ unsigned char* noalloc_scratch(int device) {
   return g_noalloc_addr[device];
 }
 
-// P V with caller-provided coarse vectors (no context buffer is touched).
+// P V with caller-provided coarse vectors (the context's structure scratch of G^T V and of the coarse product,
+// allocated when the structure was built, is used; nothing is allocated here).
 void project_with(fetirp_ctx ctx, double* V, int k, double* Xc, double* Ac) {
   if (ctx->n_G == 0) return;
   gt_v(ctx->L, V, k, Xc, ctx->stream);
-  small_gemm(ctx->n_G, k, ctx->Ginv.p, Xc, Ac, ctx->stream);
+  small_gemm(ctx->n_G, k, ctx->Ginv.p, Xc, Ac, ctx->stream, ctx->sg_part.p);
   g_apply(ctx->L, Ac, k, -1.0, 1.0, V, ctx->stream);
 }
 
@@ -2173,7 +2183,7 @@ void apply_split(fetirp_ctx ctx, const double* d_r, double* d_Q, int prec) {
   split(L, d_r, k, SP.Vs.p, s);
   if (ctx->n_G > 0) {   // X = (G^T G)^{-1} G^T S(r) and its local responses M_s X
     gt_v(L, SP.Vs.p, k, ctx->Xc.p, s);
-    small_gemm(ctx->n_G, k, ctx->Ginv.p, ctx->Xc.p, ctx->Ac.p, s);
+    small_gemm(ctx->n_G, k, ctx->Ginv.p, ctx->Xc.p, ctx->Ac.p, s, ctx->sg_part.p);
     if (prec == FETIRP_PREC_FP64)
       coarse_response<double>(L, k, SP.M64.p, SP.d_moff.p, SP.d_mcol_ptr.p, SP.d_mcol_row.p, SP.d_mld.p, ctx->Ac.p,
                               SP.Yc.p, s);

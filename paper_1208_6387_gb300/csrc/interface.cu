@@ -259,19 +259,18 @@ __global__ void k_scatter(Layout L, PatView<TI> Z, int k, double beta, double* _
   *o = (beta == 0.0 ? 0.0 : beta * *o) + acc;
 }
 
+// S(r)[row][g] = sum over the row's slots in column g of r[row] / (slots of the row); one thread per element
+// (coalesced stores), from the per-row column and weight tables
 __global__ void k_split(Layout L, const double* __restrict__ r, int k, double* __restrict__ Z) {
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= L.n_lambda) return;
-  double* z = Z + (size_t)row * k;
-  for (int g = 0; g < k; ++g) z[g] = 0.0;
-  int cnt = (L.row_sign[2 * row] != 0) + (L.row_sign[2 * row + 1] != 0);
-  if (cnt == 0) return;
-  const double w = r[row] / cnt;
-  for (int e = 0; e < 2; ++e) {
-    if (L.row_sign[2 * row + e] == 0) continue;
-    const int s = L.slot_occ[L.row_slot[2 * row + e]];
-    z[L.occ_group[s]] += w;
-  }
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)L.n_lambda * k) return;
+  const int row = (int)(idx / k), g = (int)(idx % k);
+  const int g0 = L.row_grp[2 * row], g1 = L.row_grp[2 * row + 1];
+  const double w = r[row] * L.row_wt[row];
+  double z = 0.0;
+  if (g0 == g) z += w;
+  if (g1 == g) z += w;
+  Z[idx] = z;
 }
 
 // ---- sparse-column form of P^T F P S(r) -------------------------------------------------------------
@@ -438,7 +437,7 @@ void gather_split(const Layout& L, const double* V, int k, const PatView<float>&
 
 void split(const Layout& L, const double* r, int k, double* Z, cudaStream_t s) {
   if (L.n_lambda == 0) return;
-  k_split<<<ceil_div(L.n_lambda, 256), 256, 0, s>>>(L, r, k, Z);
+  k_split<<<(unsigned)ceil_div((long long)L.n_lambda * k, 256), 256, 0, s>>>(L, r, k, Z);
   FETIRP_LAUNCH_CHECK();
 }
 

@@ -1,5 +1,7 @@
 // Block Gram products, F-normalisation and the block update of multivector FETI (Table 1 right column,
 // lines 5.2-5.4, with the F-normalisation and full reorthogonalisation of the numerical-issues subsection).
+#include <mutex>
+
 #include "ops.cuh"
 #include "normalise_warp.cuh"
 
@@ -437,14 +439,38 @@ __global__ void k_reduce_chunks_warp(int count, int chunks, const double* __rest
 // up to four chunks per SM (the sums are FP64-pipe bound: more resident warps keep the pipe busy)
 int eta_chunks(int n) { return std::max(1, std::min(608, ceil_div(n, 256))); }
 
-void eta_partials(int n, int k, const double* W, const double* Q, const double* r, DBuf<double>& partial,
-                  cudaStream_t s) {
+// out[g][o] = sum of the chunk partials c = g, g + G, g + 2G, ... of output o (G = gridDim.y groups), four
+// independent running sums added in a fixed order: the first level of the eta reduction, spread over many SMs
+// (the FP64 adds of all chunks on the one normalising SM would take longer than the product itself)
+__global__ void k_eta_group_sums(int nout, int chunks, const double* __restrict__ partial, double* __restrict__ out) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.y, G = gridDim.y;
+  if (o >= nout) return;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int c = g;
+  for (; c + 3 * G < chunks; c += 4 * G) {
+    a0 += partial[(size_t)c * nout + o];
+    a1 += partial[(size_t)(c + G) * nout + o];
+    a2 += partial[(size_t)(c + 2 * G) * nout + o];
+    a3 += partial[(size_t)(c + 3 * G) * nout + o];
+  }
+  for (; c < chunks; c += G) a0 += partial[(size_t)c * nout + o];
+  out[(size_t)g * nout + o] = (a0 + a1) + (a2 + a3);
+}
+
+int eta_partials(int n, int k, const double* W, const double* Q, const double* r, DBuf<double>& partial,
+                 cudaStream_t s) {
   const int chunks = eta_chunks(n);
   const int rows = ceil_div(n, chunks);
   const int nout = k * (k + 1);
-  partial.ensure((size_t)chunks * nout + nout);
+  partial.ensure((size_t)(chunks + ETA_GROUPS) * nout);
   k_eta_partial<<<chunks, 256, 0, s>>>(n, k, W, Q, r, rows, partial.p);
   FETIRP_LAUNCH_CHECK();
+  if (chunks <= ETA_GROUPS) return 0;
+  k_eta_group_sums<<<dim3(ceil_div(nout, 256), ETA_GROUPS), 256, 0, s>>>(nout, chunks, partial.p,
+                                                                         partial.p + (size_t)chunks * nout);
+  FETIRP_LAUNCH_CHECK();
+  return chunks;   // the normalisation reads ETA_GROUPS group sums from this chunk offset
 }
 
 // C (m x k, row-major) = A (m x m, row-major) B (m x k, row-major) in FP64.  One CTA per 4 rows of C, one warp
@@ -452,9 +478,13 @@ void eta_partials(int n, int k, const double* W, const double* Q, const double* 
 // two <= 32, so that every lane does useful FMAs; the slices of a column are added by a fixed shuffle tree.
 __global__ void __launch_bounds__(128) k_small_gemm(int m, int k, const double* __restrict__ A,
                                                     const double* __restrict__ B, double* __restrict__ C) {
+  // grid.y > 1: split of the inner dimension; part y sums j in [y m / Y, (y + 1) m / Y) and writes its own
+  // m x k slice of C (the slices are added in order by k_sum_slices)
   const int row = blockIdx.x * 4 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= m) return;
+  const int j0 = (int)((long long)blockIdx.y * m / gridDim.y), j1 = (int)((long long)(blockIdx.y + 1) * m / gridDim.y);
+  C += (size_t)blockIdx.y * m * k;
   const double* a = A + (size_t)row * m;
   for (int g0 = 0; g0 < k; g0 += 32) {
     const int kk = min(32, k - g0);
@@ -465,14 +495,14 @@ __global__ void __launch_bounds__(128) k_small_gemm(int m, int k, const double* 
     double acc = 0.0;
     if (g < k) {   // four independent partial sums: the loads of four terms are in flight together
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int j = sl;
-      for (; j + 3 * slices < m; j += 4 * slices) {
+      int j = j0 + sl;
+      for (; j + 3 * slices < j1; j += 4 * slices) {
         s0 = fma(a[j], B[(size_t)j * k + g], s0);
         s1 = fma(a[j + slices], B[(size_t)(j + slices) * k + g], s1);
         s2 = fma(a[j + 2 * slices], B[(size_t)(j + 2 * slices) * k + g], s2);
         s3 = fma(a[j + 3 * slices], B[(size_t)(j + 3 * slices) * k + g], s3);
       }
-      for (; j < m; j += slices) s0 = fma(a[j], B[(size_t)j * k + g], s0);
+      for (; j < j1; j += slices) s0 = fma(a[j], B[(size_t)j * k + g], s0);
       acc = (s0 + s1) + (s2 + s3);
     }
     for (int off = kp; off < 32; off <<= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
@@ -480,11 +510,30 @@ __global__ void __launch_bounds__(128) k_small_gemm(int m, int k, const double* 
   }
 }
 
-void small_gemm(int m, int k, const double* A, const double* B, double* C, cudaStream_t s) {
+// C[i] = sum of the `parts` slices P[p][i] in slice order
+__global__ void k_sum_slices(int count, int parts, const double* __restrict__ P, double* __restrict__ C) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double acc = P[i];
+  for (int q = 1; q < parts; ++q) acc += P[(size_t)q * count + i];
+  C[i] = acc;
+}
+
+int small_gemm_parts(int m) {
+  // FP64 FMAs bound this product on this GPU: enough CTAs to reach every SM, inner slices of >= 128 terms
+  return std::max(1, std::min(SMALL_GEMM_MAX_PARTS, std::min(ceil_div(608, ceil_div(m, 4)), m / 128)));
+}
+
+void small_gemm(int m, int k, const double* A, const double* B, double* C, cudaStream_t s, double* part) {
   if (m <= 0 || k <= 0) return;
   if (k > 64) throw Error(1, "k > 64");
-  k_small_gemm<<<ceil_div(m, 4), 128, 0, s>>>(m, k, A, B, C);
+  const int parts = part ? small_gemm_parts(m) : 1;
+  k_small_gemm<<<dim3(ceil_div(m, 4), parts), 128, 0, s>>>(m, k, A, B, parts > 1 ? part : C);
   FETIRP_LAUNCH_CHECK();
+  if (parts > 1) {
+    k_sum_slices<<<ceil_div(m * k, 256), 256, 0, s>>>(m * k, parts, part, C);
+    FETIRP_LAUNCH_CHECK();
+  }
 }
 
 
@@ -877,12 +926,120 @@ __global__ void __launch_bounds__(256) k_tall_update(int n, int a_max, const int
   }
 }
 
+// The FP32-history update for k = 32 on a tall block (one split): 256-row tiles, each thread 8 rows (ty + 32 u)
+// x 4 columns (4 tx ..), with 16-byte shared loads along the history index (3 loads per 32 FMAs, so the FP32
+// pipe rather than the shared-memory port bounds it).  The 32-column history block of a tile is one contiguous
+// 32 KB range in the block layout (width 32); it is copied to shared memory with 16-byte asynchronous copies
+// (cp.async) into two stages, the next tile in flight while the current one is used.  Rows >= n and history
+// columns >= a (a is a multiple of 32 here) are zero-filled by the copy.  Per output the history columns are
+// added in increasing order, one FMA each, as in k_tall_update.
+constexpr int TW_ROWS = 256, TW_LD = 36;
+constexpr int TW_STAGE_FLOATS = TW_ROWS * TW_LD + 32 * 32;
+constexpr int TW_SMEM = 2 * TW_STAGE_FLOATS * 4;
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 16 : 0;   // source bytes; the rest of the 16 is zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__global__ void __launch_bounds__(256, 2) k_tall_update_w32(int n, int a_max, const int* __restrict__ d_a,
+                                                           const float* __restrict__ Wh,
+                                                           const float* __restrict__ Cf, double alpha,
+                                                           double* __restrict__ W) {
+  extern __shared__ __align__(16) float tw_smem[];
+  const int a = d_a ? min(*d_a, a_max) : a_max;
+  if (a <= 0) return;
+  const int r0 = blockIdx.x * TW_ROWS;
+  const int tid = threadIdx.x, tx = tid >> 5, ty = tid & 31;
+  float acc[8][4];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[u][j] = 0.f;
+  auto issue = [&](int c0, int st) {   // tile of history columns c0 .. c0 + 31 into stage st
+    float* sa = tw_smem + st * TW_STAGE_FLOATS;
+    float* sc = sa + TW_ROWS * TW_LD;
+    const float* blk = Wh + (size_t)(c0 >> 5) * n * 32;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int q = tid + 256 * i, row = q >> 3, part = q & 7;
+      const int rr = r0 + row;
+      const bool ok = c0 + part * 4 + 4 <= a && rr < n;
+      cp_async16(sa + row * TW_LD + part * 4, blk + (size_t)(ok ? rr : 0) * 32 + part * 4, ok);
+    }
+    const int cc = tid >> 3, gp = tid & 7;
+    const bool okc = c0 + cc < a;
+    cp_async16(sc + cc * 32 + gp * 4, Cf + (size_t)(okc ? c0 + cc : 0) * 32 + gp * 4, okc);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  const int ntile = (a + 31) / 32;
+  issue(0, 0);
+  for (int t = 0; t < ntile; ++t) {
+    if (t + 1 < ntile) {
+      issue((t + 1) * 32, (t + 1) & 1);   // the stage it overwrites was released by the barrier below
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();   // tile t is in shared memory for every thread
+    const float* sa = tw_smem + (t & 1) * TW_STAGE_FLOATS;
+    const float* sc = sa + TW_ROWS * TW_LD;
+#pragma unroll 1
+    for (int cq = 0; cq < 8; ++cq) {
+      float4 bv[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = *reinterpret_cast<const float4*>(sc + (cq * 4 + j) * 32 + tx * 4);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 av = *reinterpret_cast<const float4*>(sa + (ty + 32 * u) * TW_LD + cq * 4);
+        acc[u][0] = fmaf(av.x, bv[0].x, acc[u][0]);
+        acc[u][1] = fmaf(av.x, bv[0].y, acc[u][1]);
+        acc[u][2] = fmaf(av.x, bv[0].z, acc[u][2]);
+        acc[u][3] = fmaf(av.x, bv[0].w, acc[u][3]);
+        acc[u][0] = fmaf(av.y, bv[1].x, acc[u][0]);
+        acc[u][1] = fmaf(av.y, bv[1].y, acc[u][1]);
+        acc[u][2] = fmaf(av.y, bv[1].z, acc[u][2]);
+        acc[u][3] = fmaf(av.y, bv[1].w, acc[u][3]);
+        acc[u][0] = fmaf(av.z, bv[2].x, acc[u][0]);
+        acc[u][1] = fmaf(av.z, bv[2].y, acc[u][1]);
+        acc[u][2] = fmaf(av.z, bv[2].z, acc[u][2]);
+        acc[u][3] = fmaf(av.z, bv[2].w, acc[u][3]);
+        acc[u][0] = fmaf(av.w, bv[3].x, acc[u][0]);
+        acc[u][1] = fmaf(av.w, bv[3].y, acc[u][1]);
+        acc[u][2] = fmaf(av.w, bv[3].z, acc[u][2]);
+        acc[u][3] = fmaf(av.w, bv[3].w, acc[u][3]);
+      }
+    }
+    __syncthreads();   // every thread is done with stage t & 1 before tile t + 2 is copied into it
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int row = r0 + ty + 32 * u;
+    if (row >= n) continue;
+    double* w = W + (size_t)row * 32 + tx * 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] += alpha * (double)acc[u][j];
+  }
+}
+
 // Cf[i] = (float)C[i] for the first a * k coefficients (a read on the device): the FP32 history update then
 // loads FP32 coefficients (one conversion per coefficient instead of one per coefficient and row tile)
 __global__ void k_coef_to_f32(int a_max, const int* __restrict__ d_a, int k, const double* __restrict__ C,
                               float* __restrict__ Cf) {
   const int a = d_a ? min(*d_a, a_max) : a_max;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a * k; i += gridDim.x * blockDim.x) Cf[i] = (float)C[i];
+}
+
+void tall_update_init() {
+  static std::mutex mu;
+  static bool attr_set[64] = {};
+  std::lock_guard<std::mutex> lock(mu);
+  int dev = 0;
+  FETIRP_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw Error(1, "device ordinal out of range");
+  if (!attr_set[dev]) {
+    FETIRP_CUDA(cudaFuncSetAttribute(k_tall_update_w32, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM));
+    attr_set[dev] = true;
+  }
 }
 
 int tall_update_splits(int n, int a_max) {
@@ -917,6 +1074,13 @@ void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, int hk, 
     k_coef_to_f32<<<std::min(ceil_div(a_max * k, 256), 1216), 256, 0, s>>>(a_max, d_a, k, C, Cf);
     FETIRP_LAUNCH_CHECK();
     Ct = reinterpret_cast<const TH*>(Cf);
+  }
+  if (sizeof(TH) == 4 && splits == 1 && k == 32 && hk == 32 && a_max % 32 == 0) {
+    tall_update_init();
+    k_tall_update_w32<<<ceil_div(n, TW_ROWS), 256, TW_SMEM, s>>>(n, a_max, d_a, reinterpret_cast<const float*>(Wh),
+                                                                 reinterpret_cast<const float*>(Ct), alpha, W);
+    FETIRP_LAUNCH_CHECK();
+    return;
   }
   const dim3 grid(tiles, splits);
   if (k <= 8)

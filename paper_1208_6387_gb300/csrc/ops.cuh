@@ -42,6 +42,9 @@ struct Layout {
   const double* Nb[MAXP];   // n_b x kdim row-major: kernel restricted to the boundary (pattern frame)
   int n_b[MAXP];
   int kdim[MAXP];
+  // split by row: the multivector column of each of the row's two slots (-1: none) and 1 / (slots of the row)
+  const int* row_grp;
+  const double* row_wt;
   // G by row: for each of the row's two slots, the occurrence's first coarse column (-1: none), its kernel
   // dimension and sign * Nb[j][m] (m < 6)
   const int* rowg_gofs;
@@ -230,18 +233,27 @@ void hist_dot(int n, int a, const TH* Qh, int hk, const double* r, double* C, DB
 int tall_update_splits(int n, int a_max);
 // device scratch (in doubles) that tall_update needs for n rows, a_max columns, k outputs
 size_t tall_update_scratch(int n, int a_max, int k, bool fp32);
+// one-time kernel attribute set-up of the history update (large dynamic shared memory); call outside capture
+void tall_update_init();
 template <typename TH>
 void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, int hk, const double* C, double alpha,
                  double* W, DBuf<double>& scratch, DBuf<unsigned>& tickets, cudaStream_t s);
 // history count += k with restart, dropped and iteration counters (one thread)
 void advance(int* cols, int k, long long cap, const int* n_kept, int* dropped, int* iters, cudaStream_t s);
-// Row-chunk partials (eta_chunks(n) of them) of [eta | wr] = W^T [Q | r], a k x (k+1) block, FP64 sums;
-// normalise() adds them in chunk order.
+// Row-chunk partials (eta_chunks(n) of them) of [eta | wr] = W^T [Q | r], a k x (k+1) block, FP64 sums.  With
+// more than ETA_GROUPS chunks they are first added into ETA_GROUPS group sums (fixed order) stored after the
+// chunks; the return value is the offset, in blocks of k (k+1), of what normalise() must add (0: the chunks
+// themselves, eta_chunks(n) of them; else the ETA_GROUPS group sums).
+constexpr int ETA_GROUPS = 16;
 int eta_chunks(int n);
-void eta_partials(int n, int k, const double* W, const double* Q, const double* r, DBuf<double>& partial,
-                  cudaStream_t s);
+int eta_partials(int n, int k, const double* W, const double* Q, const double* r, DBuf<double>& partial,
+                 cudaStream_t s);
 // C (m x k) = A (m x m) B (m x k), row-major, FP64, one warp per row (small coarse products).
-void small_gemm(int m, int k, const double* A, const double* B, double* C, cudaStream_t s);
+// part (optional, small_gemm_parts(m) * m * k doubles): the inner dimension is split over that many CTA rows
+// and the slices added in order (deterministic)
+constexpr int SMALL_GEMM_MAX_PARTS = 8;
+int small_gemm_parts(int m);
+void small_gemm(int m, int k, const double* A, const double* B, double* C, cudaStream_t s, double* part = nullptr);
 // Normalisation of eta = W^T P~ (k x k) so that T^T eta T = I on the kept directions: pivoted
 // Cholesky eta = Pi M M^T Pi^T, stopping when the largest remaining pivot <= trunc * (largest diagonal);
 // T = Pi M^{-T} on the kept columns (zero columns for dropped ones); alpha = T^T wr with wr = W^T r.
