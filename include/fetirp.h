@@ -268,7 +268,9 @@ fetirp_status fetirp_apply_split_device(fetirp_ctx ctx, const double* d_r, doubl
  *  - Sharing: every call on a device uses the same array and it keeps the previous call's contents; the
  *    call overwrites every scratch entry it reads, so nothing has to start at zero.  Calls that overlap on the
  *    GPU (other streams, other host threads, other contexts on the same device) race on the array and must
- *    be serialised by the caller.
+ *    be serialised by the caller.  The partial sums of G^T V and of the coarse product (G^T G)^{-1} X use
+ *    small buffers of the context itself, allocated by fetirp_prepare, so two overlapping calls on one
+ *    context race on those as well.
  *  - Requires fetirp_prepare (or a solve) on ctx first; enqueued on the context's stream.
  */
 #define FETIRP_NOALLOC_SCRATCH_BYTES (32u << 20)
