@@ -81,6 +81,16 @@ typedef struct {
                           FP32 local products) run whole block iterations in one cooperative persistent
                           launch with bounded grid barriers, stopping on the device at convergence; 0: CUDA
                           graphs of per-phase kernels; default 1 */
+  /* Caller-supplied device allocator (for example a framework's caching allocator); both NULL (the default)
+     = cudaMalloc / cudaFree.  Set both or neither.  alloc(bytes, stream, alloc_user) returns device memory
+     on options.device, 256-byte aligned, usable on `stream` (the context's stream), or NULL (the call then
+     returns FETIRP_ENOMEM); free(ptr, alloc_user) releases one pointer that alloc returned, after the library
+     has synchronised the device.  The library calls them from the host thread of the call (server calls:
+     from its worker threads), only while one of its entry points runs or the context (or a context sharing
+     its patterns) is destroyed; they must stay valid until then. */
+  void* (*alloc)(size_t bytes, void* stream, void* alloc_user);
+  void (*free)(void* ptr, void* alloc_user);
+  void* alloc_user;
 } fetirp_options;
 
 /* Phases of a solve, for the per-phase statistics. */

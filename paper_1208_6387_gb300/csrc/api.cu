@@ -267,6 +267,12 @@ fetirp_status guarded(fetirp_ctx ctx, F&& f) {
   try {
     ctx->err.clear();
     FETIRP_CUDA(cudaSetDevice(ctx->opt.device));
+    DevAllocator a;   // the context's device allocator hooks, if any, for this thread while the call runs
+    a.alloc = ctx->opt.alloc;
+    a.free = ctx->opt.free;
+    a.user = ctx->opt.alloc_user;
+    a.stream = ctx->stream;
+    AllocatorScope scope(a);
     return f();
   } catch (const Error& e) {
     set_err(ctx, e.what());
@@ -1723,7 +1729,8 @@ fetirp_status fetirp_create(const fetirp_options* opt, fetirp_ctx* out) {
   const fetirp_options& o = ctx->opt;
   if (!(o.tol > 0) || o.max_iter < 1 || o.block_k < 1 || o.max_outer < 1 || !(o.inner_tol > 0) ||
       !(o.pivot_tol > 0) || !(o.eig_trunc > 0) || !(o.eig_trunc_inner > 0) || o.check_every < 0 ||
-      (o.precision != FETIRP_PREC_FP64 && o.precision != FETIRP_PREC_FP32 && o.precision != FETIRP_PREC_TF32X3))
+      (o.precision != FETIRP_PREC_FP64 && o.precision != FETIRP_PREC_FP32 && o.precision != FETIRP_PREC_TF32X3) ||
+      ((o.alloc == nullptr) != (o.free == nullptr)))
     return FETIRP_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) return FETIRP_ECUDA;

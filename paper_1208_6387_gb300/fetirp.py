@@ -20,13 +20,36 @@ FETIRP_PREC_FP64, FETIRP_PREC_FP32, FETIRP_PREC_TF32X3 = 0, 1, 2
 PRECISIONS = {"fp64": FETIRP_PREC_FP64, "fp32": FETIRP_PREC_FP32, "tf32x3": FETIRP_PREC_TF32X3}
 
 
+# device allocator hooks of fetirp_options: alloc(bytes, stream, user) -> device pointer; free(ptr, user)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
 class fetirp_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32), ("block_k", C.c_int32),
                 ("max_outer", C.c_int32), ("inner_tol", C.c_double), ("pivot_tol", C.c_double),
                 ("eig_trunc", C.c_double), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
                 ("check_every", C.c_int32), ("timing", C.c_int32), ("eig_trunc_inner", C.c_double),
                 ("use_graphs", C.c_int32), ("timing_mask", C.c_int32), ("history_bytes", C.c_int64),
-                ("persistent", C.c_int32)]
+                ("persistent", C.c_int32), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+def caching_allocator_hooks(device: int = 0):
+    """(alloc, free) hooks for fetirp_options that take device memory from PyTorch's caching allocator on the
+    given device and the context's stream.  Keep the returned objects alive while any context that uses them
+    exists."""
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device=device, stream=int(stream or 0))
+        except Exception:
+            return None   # the library reports FETIRP_ENOMEM
+
+    def _free(ptr, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return ALLOC_FN(_alloc), FREE_FN(_free)
 
 
 PHASES = ["factor", "coarse", "local", "gather", "scatter", "project", "gram", "reorth", "update", "recover",

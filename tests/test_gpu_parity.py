@@ -212,3 +212,44 @@ def test_single_occurrence_and_invalid_inputs():
         F.fetirp_create_pattern(ctx, pat.n_nodes, 1, K.indptr, K.indices, K.data, pat.bnd_nodes, 2)
     assert e.value.status == F.FETIRP_ESINGULAR
     F.fetirp_destroy(ctx)
+
+
+def test_caller_allocator_hooks():
+    """With the allocator hooks of fetirp_options set (here PyTorch's caching allocator), the library's device
+    buffers come from the hooks and all go back through them when the context is destroyed, and the solve is
+    bitwise the one computed on cudaMalloc'd buffers (both precisions, persistent and graph iterations)."""
+    import ctypes as C
+    import torch
+
+    prob = CASES["heat_rot_ragged"]()
+    count = {"alloc": 0, "free": 0}
+
+    def _alloc(nbytes, stream, user):
+        count["alloc"] += 1
+        return torch.cuda.caching_allocator_alloc(int(nbytes), device=0, stream=int(stream or 0))
+
+    def _free(ptr, user):
+        count["free"] += 1
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a_cb, f_cb = F.ALLOC_FN(_alloc), F.FREE_FN(_free)
+    for prec in ("fp64", "fp32"):
+        for pers in (1, 0):
+            res = []
+            for hooks in (False, True):
+                kw = dict(precision=prec, tol=1e-10, inner_tol=1e-5, persistent=pers)
+                if hooks:
+                    kw.update(alloc=a_cb, free=f_cb)
+                ctx = make_ctx(prob, **kw)
+                try:
+                    lam, u, st = F.fetirp_solve(ctx, prob.n_lambda, prob.c, F.n_u(prob))
+                finally:
+                    F.fetirp_destroy(ctx)
+                res.append((lam, u))
+            assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1]), (prec, pers)
+    assert count["alloc"] > 0 and count["free"] == count["alloc"], count
+    # only one of the two hooks: refused
+    o = F.fetirp_default_options()
+    o.alloc = a_cb
+    h = C.c_void_p()
+    assert F.lib().fetirp_create(C.byref(o), C.byref(h)) == F.FETIRP_EINVAL
