@@ -347,6 +347,10 @@ fetirp_status fetirp_server_submit(fetirp_server srv, const fetirp_structure* st
  * the solve's own status are delivered and the ticket is released.  latency_ms (may be NULL): submit -> done. */
 fetirp_status fetirp_server_wait(fetirp_server srv, int64_t ticket, double timeout_s, int32_t* done,
                                  double* lambda_out, double* u_out, fetirp_stats* stats, double* latency_ms);
+/* Non-blocking check of a ticket: fetirp_server_wait with timeout_s = 0 (same outputs, same release of the
+ * ticket once *done = 1). */
+fetirp_status fetirp_server_poll(fetirp_server srv, int64_t ticket, int32_t* done, double* lambda_out,
+                                 double* u_out, fetirp_stats* stats, double* latency_ms);
 /* Finish queued work, join the slots and release everything. */
 void fetirp_server_destroy(fetirp_server srv);
 

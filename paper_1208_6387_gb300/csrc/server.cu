@@ -198,6 +198,11 @@ fetirp_status fetirp_server_wait(fetirp_server srv, int64_t ticket, double timeo
   return st;
 }
 
+fetirp_status fetirp_server_poll(fetirp_server srv, int64_t ticket, int32_t* done, double* lambda_out,
+                                 double* u_out, fetirp_stats* stats, double* latency_ms) {
+  return fetirp_server_wait(srv, ticket, 0.0, done, lambda_out, u_out, stats, latency_ms);
+}
+
 void fetirp_server_destroy(fetirp_server srv) {
   if (!srv) return;
   {

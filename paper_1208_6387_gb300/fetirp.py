@@ -106,6 +106,8 @@ _SIGS = {
     "fetirp_server_submit": (C.c_int, [P, C.POINTER(fetirp_structure), C.POINTER(C.c_int64)]),
     "fetirp_server_wait": (C.c_int, [P, C.c_int64, C.c_double, C.POINTER(C.c_int32), P, P, C.POINTER(fetirp_stats),
                                      C.POINTER(C.c_double)]),
+    "fetirp_server_poll": (C.c_int, [P, C.c_int64, C.POINTER(C.c_int32), P, P, C.POINTER(fetirp_stats),
+                                     C.POINTER(C.c_double)]),
     "fetirp_server_destroy": (None, [P]),
     "fetirp_solve": (C.c_int, [P, C.c_int64, P, P, P, C.POINTER(fetirp_stats)]),
     "fetirp_solve_device": (C.c_int, [P, C.c_int64, P, P, P, C.POINTER(fetirp_stats)]),
@@ -275,6 +277,23 @@ def fetirp_server_wait(srv, ticket, n_lambda, n_u, timeout_s=-1.0, allow_noconv=
     if not done.value:
         if s != FETIRP_OK:
             raise FetirpError(s, "fetirp_server_wait failed")
+        return None
+    if s != FETIRP_OK and not (allow_noconv and s == FETIRP_ENOCONV):
+        raise FetirpError(s, "structure failed in the server")
+    return lam, u, stt.as_dict(), lat.value
+
+
+def fetirp_server_poll(srv, ticket, n_lambda, n_u, allow_noconv=False):
+    """Non-blocking: None while the structure is not done, else (lambda, u, stats dict, latency_ms)."""
+    done = C.c_int32()
+    lam = np.zeros(int(n_lambda))
+    u = np.zeros(int(n_u))
+    stt = fetirp_stats()
+    lat = C.c_double()
+    s = lib().fetirp_server_poll(srv, int(ticket), C.byref(done), _ptr(lam), _ptr(u), C.byref(stt), C.byref(lat))
+    if not done.value:
+        if s != FETIRP_OK:
+            raise FetirpError(s, "fetirp_server_poll failed")
         return None
     if s != FETIRP_OK and not (allow_noconv and s == FETIRP_ENOCONV):
         raise FetirpError(s, "structure failed in the server")

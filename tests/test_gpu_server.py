@@ -73,3 +73,28 @@ def test_admission_by_memory_budget(library):
     assert all(r is not None for r in res)
     lat = [r[3] for r in res]
     assert max(lat) > min(lat)          # queued behind one another
+
+
+def test_poll_delivers_the_same_results(library):
+    """fetirp_server_poll never blocks: polling every ticket until it is done (bounded on the host) delivers
+    the results that fetirp_server_wait delivers, bitwise."""
+    import time
+    ctx, pats, pids = library
+    reqs = _requests(pats, n=3)
+    waited = _serve(ctx, pids, reqs, slots=2, budget=8 << 30)
+    opts = F.fetirp_default_options(precision="fp32", tol=1e-10, history_bytes=256 << 20)
+    srv = F.fetirp_server_create(ctx, opts, 2, 8 << 30)
+    try:
+        tickets = [F.fetirp_server_submit(srv, F.structure_of(prob, {0: pids[li]})) for li, prob in reqs]
+        polled = [None] * len(reqs)
+        deadline = time.monotonic() + 120.0
+        while any(p is None for p in polled) and time.monotonic() < deadline:
+            for i, (t, (_, prob)) in enumerate(zip(tickets, reqs)):
+                if polled[i] is None:
+                    polled[i] = F.fetirp_server_poll(srv, t, prob.n_lambda, F.n_u(prob))
+            time.sleep(0.001)
+    finally:
+        F.fetirp_server_destroy(srv)
+    assert all(p is not None for p in polled)
+    for a, b in zip(waited, polled):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
