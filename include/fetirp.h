@@ -56,7 +56,7 @@ enum {
 
 typedef struct {
   int32_t precision;   /* FETIRP_PREC_*, default FP64 */
-  double tol;          /* target ||r_j|| / ||r_0||, r = P^T (d - F lambda) (Table 1 line 3); default 1e-8 */
+  double tol;          /* target ||r_j|| / ||r_0||, r = P^T (d - F lambda) (the residual of Table 1); default 1e-8 */
   int32_t max_iter;    /* cap on block iterations over the whole solve; default 2000 */
   int32_t block_k;     /* multivector width k; 1 = classical FETI-CG; default 32 (clamped to the number
                           of occurrences; fetirp_set_groups overrides) */
@@ -235,7 +235,7 @@ fetirp_status fetirp_solve_device(fetirp_ctx ctx, int64_t n_lambda, const double
                                   double* d_u, fetirp_stats* stats);
 
 /*
- * The block interface operator Q = P^T F P V on a block of k directions (Table 1 line 5.1), with
+ * The block interface operator Q = P^T F P V on a block of k directions (the F-apply of Table 1), with
  * P = I - G (G^T G)^{-1} G^T.  V and Q are n_lambda x k, row-major (k contiguous), FP64, host memory.
  * precision: FETIRP_PREC_* for the local products.  Blocks until done.  Requires n_lambda to have been
  * fixed by a previous fetirp_solve or fetirp_prepare.
@@ -251,8 +251,8 @@ fetirp_status fetirp_apply_block_device(fetirp_ctx ctx, int32_t k, const double*
  * computed in the sparse-column form.  F acts on S(r) only where a split column touches an occurrence (its own
  * group and its neighbours' groups: at most seven right-hand sides per occurrence in 3D instead of k), and
  * F G X with X = (G^T G)^{-1} G^T S(r) comes from precomputed local coarse responses
- * M_s = S^+(s) B(s)^T G restricted to the kernel modes of s and its neighbours (by linearity of Table 1
- * row 5.1).  The result equals fetirp_apply_block on the dense S(r) in the same precision.
+ * M_s = S^+(s) B(s)^T G restricted to the kernel modes of s and its neighbours (by linearity of the
+ * F-apply of Table 1).  The result equals fetirp_apply_block on the dense S(r) in the same precision.
  *   r: n_lambda doubles; Q: n_lambda x k row-major doubles (k = the structure's multivector width), caller
  *      owned.  _device: device pointers, asynchronous on the context's stream; otherwise host buffers.
  *   The first call for a structure builds the pair lists and M (FP64 products, kept in FP64 and FP32).

@@ -144,7 +144,7 @@ class FetiOracle:
         return V - self.G @ (self.GtG_inv @ (self.G.T @ V))
 
     def lambda0(self):
-        """lambda_0 = G (G^T G)^{-1} e (Table 1 line 2 with lambda_00 = 0)."""
+        """lambda_0 = G (G^T G)^{-1} e (the initialisation of Table 1 with lambda_00 = 0)."""
         return self.G @ (self.GtG_inv @ self.e())
 
     def PtFP(self, V):
@@ -187,8 +187,8 @@ class FetiOracle:
     def multivector(self, tol=1e-8, max_it=1000, eps_eta=1e-12, groups=None, k=None, reorth_depth=None):
         """Multivector FETI (Table 1, right column) with full reorthogonalisation and F-normalisation
         (numerical-issues subsection): eta = W^T P~ is replaced by I through W <- W eta^{-1/2},
-        reorth_depth = number of previous blocks orthogonalised against (None = all; 1 = the recurrence of
-        Table 1 lines 5.6-5.7, where beta = -(W^T P~)^{-1} P~^T Z = -P~^T Z after normalisation);
+        reorth_depth = number of previous blocks orthogonalised against (None = all; 1 = the short recurrence
+        of Table 1, where beta = -(W^T P~)^{-1} P~^T Z = -P~^T Z after normalisation);
         P~ <- P~ eta^{-1/2}, eta^{-1/2} taken from a symmetric eigendecomposition in which eigenvalues below
         eps_eta * max are dropped (the pseudo-inverse that handles redundant directions)."""
         d = self.d()
@@ -203,7 +203,7 @@ class FetiOracle:
             hist_blocks = list(zip(Ws, Ps)) if reorth_depth is None else list(zip(Ws, Ps))[-reorth_depth:]
             for Wi, Pi in hist_blocks:       # (full) reorthogonalisation against previous blocks
                 Wt = Wt - Wi @ (Pi.T @ Wt)
-            Pt = self.project(self.F(Wt))    # Table 1 line 5.1
+            Pt = self.project(self.F(Wt))    # F-image of the directions (Table 1)
             eta = Wt.T @ Pt
             eta = 0.5 * (eta + eta.T)
             ev, V = np.linalg.eigh(eta)
@@ -212,13 +212,13 @@ class FetiOracle:
                 break
             T = V[:, keep] / np.sqrt(ev[keep])[None, :]
             Wt, Pt = Wt @ T, Pt @ T
-            alpha = Wt.T @ r                  # line 5.2 with W^T P~ = I
-            lam = lam + Wt @ alpha            # line 5.3
-            r = r - Pt @ alpha                # line 5.4
+            alpha = Wt.T @ r                  # step length, with W^T P~ = I
+            lam = lam + Wt @ alpha            # iterate update
+            r = r - Pt @ alpha                # residual update
             Ws.append(Wt); Ps.append(Pt)
             it += 1
             hist.append(np.linalg.norm(r) / r0)
-            Wt = self.project(self.split(self.project(r), groups, k))   # line 5.5 + split
+            Wt = self.project(self.split(self.project(r), groups, k))   # new directions from the residual, split
         return lam, it, np.array(hist)
 
     # ---- recovery -------------------------------------------------------------------------------

@@ -1011,7 +1011,7 @@ double norm2(fetirp_ctx ctx, const double* x, int n) {
   return std::sqrt(acc);
 }
 
-// Residual r = P^T (d - F lambda) in FP64 (Table 1 line 3).
+// Residual r = P^T (d - F lambda) in FP64 (the projected residual of Table 1).
 void residual(fetirp_ctx ctx) {
   const int nl = ctx->L.n_lambda;
   apply_F(ctx, ctx->lam.p, ctx->r.p, 1, FETIRP_PREC_FP64, false, false);
@@ -1071,7 +1071,7 @@ void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
     PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 0.0, 0.0);
     tall_update<TH>(nl, (int)cap, d_cols, k, Wh, k, ctx->C.p, -1.0, ctx->Zr.p, ctx->tu_part, ctx->tu_tickets, s);
   }
-  apply_F(ctx, ctx->Zr.p, ctx->Q.p, k, prec, false, true);   // P~ = P^T F W (Table 1 line 5.1)
+  apply_F(ctx, ctx->Zr.p, ctx->Q.p, k, prec, false, true);   // P~ = P^T F W (the F-image of the directions, Table 1)
   {
     PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 0.0, 0.0);
     eta_off = eta_partials(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta_part, s);

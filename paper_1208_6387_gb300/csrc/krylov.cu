@@ -1,5 +1,6 @@
-// Block Gram products, F-normalisation and the block update of multivector FETI (Table 1 right column,
-// lines 5.2-5.4, with the F-normalisation and full reorthogonalisation of the numerical-issues subsection).
+// Block Gram products, F-normalisation and the block update of multivector FETI (Table 1 right column: step
+// length, iterate and residual updates, with the F-normalisation and full reorthogonalisation of the
+// numerical-issues subsection).
 #include <mutex>
 
 #include "ops.cuh"

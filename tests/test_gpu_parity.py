@@ -136,7 +136,7 @@ def test_bounded_barrier_wait_expires_and_context_recovers():
 @pytest.mark.parametrize("name", list(CASES) + ["c2"])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-4), ("tf32x3", 5e-4)])
 def test_sparse_column_apply_matches_dense_and_oracle(name, prec, tol):
-    """The sparse-column form of P^T F P S(r) (SURVEY a5b) equals the dense block operator on S(r) in the same
+    """The sparse-column form of P^T F P S(r) equals the dense block operator on S(r) in the same
     precision, and the oracle's P^T F P S(r)."""
     prob = config("c2") if name == "c2" else CASES[name]()
     orc = FetiOracle(prob)
