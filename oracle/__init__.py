@@ -12,6 +12,8 @@ Contents
              projector paragraph), classical FETI-CG (Table 1, left) and multivector FETI (Table 1, right) with
              full reorthogonalisation and F-normalisation (Sec. 3.3), and the block operator P^T F P V.
   brute   -- brute force for tiny meshes: Moore-Penrose pseudo-inverses and a dense solve of Eq. 3.
+  precond -- the Dirichlet, lumped and superlumped preconditioners (Eqs. 4-5) with multiplicity or stiffness
+             scaling, the preconditioner-weighted projector and lambda_0, and Table 1 with a preconditioner.
 
 Parity pins live in tests/test_oracle_*.py.  Parity against the paper's printed numbers (Tables 2-4) is
 unpinned: the donut meshes they were measured on are not available, so only trends can be compared.
