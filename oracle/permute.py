@@ -1,0 +1,30 @@
+"""The permutation multivector of Section 3.1 (Eq. 8) for a truly periodic structure: the block of search
+directions is made of the interface vector and its images under the rotation of the structure by one, two, ...
+occurrences, z -> [z, Pi z, Pi^2 z, ..., Pi^(n-1) z], Pi being the permutation of the interface partitions (with
+the orientation signs of the multiplier rows).  The rest is the multivector FETI of Table 1 (right) as in
+FetiOracle.multivector.  Plain FP64 numpy/scipy; test infrastructure only (see oracle/__init__.py).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from .feti import FetiOracle
+
+
+class PermutationFeti(FetiOracle):
+    """target[r], sign[r]: row r of an interface vector moves to row target[r] with factor sign[r] under the
+    rotation by one occurrence (the map a periodic structure's user supplies)."""
+
+    def __init__(self, prob, target, sign, n_images=None):
+        super().__init__(prob)
+        n = prob.n_lambda
+        self.Pi = sp.csr_matrix((np.asarray(sign, float), (np.asarray(target), np.arange(n))), shape=(n, n))
+        self.n_images = prob.n_occ if n_images is None else n_images
+
+    def split(self, z, groups=None, k=None):
+        """[z, Pi z, ..., Pi^(m-1) z] with m = n_images (Eq. 8: the permuted interface partitions)."""
+        cols = [np.asarray(z, dtype=float)]
+        for _ in range(self.n_images - 1):
+            cols.append(self.Pi @ cols[-1])
+        return np.stack(cols, axis=1)

@@ -1,0 +1,86 @@
+"""Pins of the periodic ring stand-in and of the permutation multivector (Section 3.1, Eq. 8): the
+isoparametric element by the patch test, the periodicity of the dual operator under the supplied
+permutation, agreement with the direct solve, and the paper's claims that the block iteration cannot be slower
+than the classical one and gains more with more repetitions."""
+import numpy as np
+import pytest
+
+from fetirp_gen.ring import q1_laplace_quad, ring_heat, ring_permutation, sector_pattern
+from oracle.direct import direct
+from oracle.permute import PermutationFeti
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_quad_element_on_a_square_is_the_q1_closed_form():
+    """On the unit square the isoparametric element is the Q1 matrix: diagonal 2/3, edge neighbours -1/6,
+    opposite corner -1/3 (corner order (0,0), (1,0), (0,1), (1,1)), in either orientation of the corners."""
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])
+    ref = np.array([[4, -1, -1, -2], [-1, 4, -2, -1], [-1, -2, 4, -1], [-2, -1, -1, 4]]) / 6.0
+    assert np.allclose(q1_laplace_quad(xy), ref, atol=1e-15)
+    flipped = xy[:, ::-1]           # a left-handed corner order: same matrix
+    assert np.allclose(q1_laplace_quad(flipped), ref, atol=1e-15)
+
+
+def test_sector_stiffness_is_psd_with_constant_kernel():
+    pat = sector_pattern(5, 4, 3)
+    K = pat.K.toarray()
+    assert np.allclose(K, K.T, atol=1e-14)
+    assert np.abs(K @ np.ones(K.shape[0])).max() < 1e-13
+    ev = np.linalg.eigvalsh(K)
+    assert ev[0] > -1e-13 and ev[1] > 1e-6 * ev[-1]
+
+
+def test_patch_test_linear_field_on_the_ring():
+    """Zero source, Dirichlet data of a linear field on both arcs: the direct solve reproduces the field at
+    every node (isoparametric bilinear elements are linearly complete)."""
+    f = lambda x: 0.3 + 1.7 * x[:, 0] - 0.9 * x[:, 1]
+    prob = ring_heat(5, m_t=3, m_r=3, dirichlet="both", dirichlet_fn=f, load="zero")
+    us, _, _, _ = direct(prob)
+    for o, u in enumerate(us):
+        assert np.abs(u - f(prob.global_coords[prob.occs[o].node_map])).max() < 1e-12
+
+
+@pytest.mark.parametrize("n", [3, 5, 9])
+def test_ring_sizes_and_periodicity(n):
+    m_t, m_r = 4, 3
+    prob = ring_heat(n, m_t=m_t, m_r=m_r, seed=2)
+    assert prob.n_lambda == n * (m_r + 1) + n * m_t       # radial lines + inner-arc Dirichlet nodes
+    target, sign = ring_permutation(prob)
+    pf = PermutationFeti(prob, target, sign)
+    Pi = pf.Pi.toarray()
+    assert np.array_equal(np.linalg.matrix_power(Pi, n), np.eye(prob.n_lambda))
+    Fd = pf.dense_F()
+    assert np.abs(Fd @ Pi - Pi @ Fd).max() <= 1e-12 * np.abs(Fd).max()
+    V = np.random.default_rng(0).standard_normal(prob.n_lambda)
+    assert rel(pf.project(pf.Pi @ V), pf.Pi @ pf.project(V)) < 1e-12
+
+
+@pytest.mark.parametrize("n", [5, 9])
+def test_permutation_multivector_reproduces_the_direct_solve(n):
+    prob = ring_heat(n, m_t=4, m_r=4, seed=1)
+    target, sign = ring_permutation(prob)
+    pf = PermutationFeti(prob, target, sign)
+    us_ref, lam_ref, _, _ = direct(prob)
+    lam, it, hist = pf.multivector(tol=1e-12)
+    assert hist[-1] <= 1e-12 and rel(lam, lam_ref) < 1e-9
+    _, us = pf.recover(lam)
+    for a, b in zip(us, us_ref):
+        assert rel(a, b) < 1e-9
+    lam_c, it_c, _ = pf.classical_cg(tol=1e-12)
+    assert it <= it_c
+
+
+def test_more_repetitions_gain_more():
+    """The relative saving of the permutation multivector over classical FETI grows with the number of
+    repetitions of the pattern (the trend of the paper's assessments)."""
+    saving = {}
+    for n in (5, 9):
+        prob = ring_heat(n, m_t=4, m_r=4, seed=1)
+        pf = PermutationFeti(prob, *ring_permutation(prob))
+        it_b = pf.multivector(tol=1e-10)[1]
+        it_c = pf.classical_cg(tol=1e-10)[1]
+        saving[n] = 1.0 - it_b / it_c
+    assert saving[9] > saving[5] > 0.3
