@@ -7,4 +7,5 @@ from .mesh import Pattern, heat_pattern, elastic_pattern, q1_laplace, q1_elastic
 from .layout import Problem, Occurrence, build_grid_problem, cube_rotations, square_rotations, dense_B, set_nodal_load
 from .configs import (heat_grid, elastic_grid, config, library_patterns, fill_structure, request_stream, LIBRARY,
                       merge_structures, batched_uneven)
-from .ring import ring_heat, ring_permutation, sector_pattern, q1_laplace_quad
+from .ring import (ring_heat, ring_elastic, ring_structure, ring_permutation, sector_pattern, q1_laplace_quad,
+                   q1_plane_strain_quad)

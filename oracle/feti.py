@@ -19,11 +19,18 @@ from .direct import B_matrix, rotation_blocks
 
 def analytic_kernel(pat):
     """N(s) of a floating pattern in its own frame (Sec. 2, floating subdomains): constants for heat; the
-    3 translations and 3 infinitesimal rotations about the centroid for 3D elasticity."""
+    2 translations and the rotation for plane elasticity; the 3 translations and 3 infinitesimal rotations
+    about the centroid for 3D elasticity."""
     n = pat.n_nodes
     if pat.dpn == 1:
         return np.ones((n, 1))
     x = pat.coords - pat.coords.mean(0)
+    if pat.dpn == 2:   # plane elasticity: 2 translations and the in-plane rotation (-y, x) about the centroid
+        N = np.zeros((n, 2, 3))
+        N[:, 0, 0] = 1.0
+        N[:, 1, 1] = 1.0
+        N[:, 0, 2], N[:, 1, 2] = -x[:, 1], x[:, 0]
+        return N.reshape(n * 2, 3)
     N = np.zeros((n, 3, 6))
     for c in range(3):
         N[:, c, c] = 1.0
@@ -35,10 +42,13 @@ def analytic_kernel(pat):
 
 
 def fixed_dofs(pat):
-    """Dofs whose removal leaves a nonsingular stiffness: one node for heat; the 3-2-1 set on three corner
-    nodes (0,0,0), (H,0,0), (0,H,0) for elasticity."""
+    """Dofs whose removal leaves a nonsingular stiffness: one node for heat; for plane elasticity both
+    components of node 0 and the y component of node m (the far end of the first grid line); the 3-2-1 set on
+    three corner nodes (0,0,0), (H,0,0), (0,H,0) for 3D elasticity."""
     if pat.dpn == 1:
         return np.array([0])
+    if pat.dpn == 2:   # both components of node 0, the y component of node m (first grid line, x differs)
+        return np.array([0, 1, 2 * pat.m + 1])
     m1 = pat.m + 1
     a, b, c = 0, pat.m, pat.m * m1
     return np.array([3 * a, 3 * a + 1, 3 * a + 2, 3 * b + 1, 3 * b + 2, 3 * c + 2])

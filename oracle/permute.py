@@ -13,13 +13,13 @@ from .feti import FetiOracle
 
 
 class PermutationFeti(FetiOracle):
-    """target[r], sign[r]: row r of an interface vector moves to row target[r] with factor sign[r] under the
-    rotation by one occurrence (the map a periodic structure's user supplies)."""
+    """Pi: the n_lambda x n_lambda map of interface vectors under the rotation of the structure by one
+    occurrence (a signed permutation of the rows, with the rotation of vector components; the map a periodic
+    structure's user supplies)."""
 
-    def __init__(self, prob, target, sign, n_images=None):
+    def __init__(self, prob, Pi, n_images=None):
         super().__init__(prob)
-        n = prob.n_lambda
-        self.Pi = sp.csr_matrix((np.asarray(sign, float), (np.asarray(target), np.arange(n))), shape=(n, n))
+        self.Pi = sp.csr_matrix(Pi)
         self.n_images = prob.n_occ if n_images is None else n_images
 
     def split(self, z, groups=None, k=None):
