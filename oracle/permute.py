@@ -28,3 +28,25 @@ class PermutationFeti(FetiOracle):
         for _ in range(self.n_images - 1):
             cols.append(self.Pi @ cols[-1])
         return np.stack(cols, axis=1)
+
+
+class PreconditionedPermutationFeti:
+    """The permutation multivector with a preconditioner of Eqs. 4-5 (the setting of the paper's donut
+    assessments, which use the Dirichlet one): PreconditionedFeti's operators and loop, the split replaced by
+    [z, Pi z, ..., Pi^(m-1) z] with z = Q tilde-F^{-1} r."""
+
+    def __new__(cls, prob, Pi, kind="dirichlet", scaling="stiffness", n_images=None):
+        from .precond import PreconditionedFeti
+        pf = PreconditionedFeti(prob, kind, scaling)
+        Pi = sp.csr_matrix(Pi)
+        m = prob.n_occ if n_images is None else n_images
+
+        def split(z, groups=None, k=None):
+            cols = [np.asarray(z, dtype=float)]
+            for _ in range(m - 1):
+                cols.append(Pi @ cols[-1])
+            return np.stack(cols, axis=1)
+
+        pf.split = split
+        pf.Pi = Pi
+        return pf

@@ -117,3 +117,22 @@ def test_more_repetitions_gain_more():
         it_c = pf.classical_cg(tol=1e-10)[1]
         saving[n] = 1.0 - it_b / it_c
     assert saving[9] > saving[5] > 0.3
+
+
+@pytest.mark.parametrize("make", [ring_heat, ring_elastic])
+def test_dirichlet_preconditioned_permutation_block_is_flat_in_the_repetitions(make):
+    """With the Dirichlet preconditioner (the setting of the paper's donut assessments) the permutation
+    multivector reproduces the direct solve, and its iteration count does not grow from 5 to 9 repetitions while
+    the classical count does (the trend of Tables 2-3)."""
+    from oracle.permute import PreconditionedPermutationFeti
+    its = {}
+    for n in (5, 9):
+        prob = make(n, m_t=6, m_r=6, seed=3)
+        pf = PreconditionedPermutationFeti(prob, ring_permutation(prob), "dirichlet")
+        us_ref, lam_ref, _, _ = direct(prob)
+        lam, it_b, hist = pf.multivector(tol=1e-10)
+        assert hist[-1] <= 1e-10 and rel(lam, lam_ref) < 1e-8
+        it_c = pf.classical_cg(tol=1e-10)[1]
+        its[n] = (it_c, it_b)
+        assert it_b < it_c
+    assert its[9][1] <= its[5][1] + 1 and its[9][0] > its[5][0]
