@@ -178,9 +178,10 @@ fetirp_status fetirp_create_pattern(fetirp_ctx ctx, int32_t n_nodes, int32_t dof
 
 /*
  * Add an occurrence of a pattern (Eq. 2 with the rotation of the elasticity subsection).
- *  rot[9]: row-major R with global = R * local, or NULL for the identity.  Only signed permutation
- *     matrices with determinant +1 (the 24 rotations of the cube) are accepted; the rotation is folded into
- *     the links, so the hot path stays a signed gather/scatter.
+ *  rot[9]: row-major R with global = R * local, or NULL for the identity.  For patterns with more than one
+ *     dof per node only signed permutation matrices with determinant +1 (the 24 rotations of the cube) are
+ *     accepted; the rotation is folded into the links, so the hot path stays a signed gather/scatter.  With
+ *     one dof per node the field has no components to turn, so any rotation is accepted and not used.
  *  n_links and the four link arrays: the rows of B(s) in the GLOBAL frame: entry sign[i] (+1 or -1) in
  *     multiplier row lambda_row[i] on component global_comp[i] of pattern node local_node[i], which must
  *     be one of the pattern's boundary nodes.  Every multiplier row must end up with one or two entries in

@@ -1847,7 +1847,7 @@ fetirp_status fetirp_add_occurrence(fetirp_ctx ctx, int32_t pattern_id, const do
     const PatternData& P = *ctx->pats[pattern_id];
     OccData O;
     O.pattern = pattern_id;
-    if (rot) {
+    if (rot && P.dpn > 1) {   // one dof per node: the rotation only places the pattern, no component turns
       int det = 0;
       for (int r = 0; r < 3; ++r) {
         int nzc = 0;
