@@ -1,15 +1,16 @@
 """Benchmark: repeated-pattern multivector FETI solves on one GB300.
 
-Workload (default): 2D heat, two square patterns of 32x32 Q1 elements with conductivity 1 and 1000 in a
-seeded checkerboard over an 8x8 occurrence grid, u = 0 on x = 0, f ~ U(0,1) (n_lambda = 3904).
-A step is one pass of the whole method on that structure: FP64 pattern factorisation (both patterns),
-coarse problem and d, block ORTHODIR to ||r|| / ||r0|| <= 1e-8 (mixed forms: FP32 local products inside FP64
-refinement), and the recovery of lambda and u.  Inputs (pattern stiffness, links, loads) are resident on the
-device when the timed region starts; the L2 cache is flushed between steps (a 256 MB write) because the
-whole working set fits in L2.
+Workload (default): 3D elasticity, three 16^3-element Q1 cube patterns (E = 1, nu = 0.3), 4 x 6 x 8 = 192
+occurrences with seeded rotations of the cube, clamped face x = 0, body force N(0,1) per dof (n_lambda =
+427,392, 1152 rigid modes).  A step is one pass of the whole method on that structure: FP64 factorisation of the
+three patterns (zero-pivot detection, kernel, S^+), coarse problem and d, block ORTHODIR with k = 32 to
+||r|| / ||r0|| <= 1e-8 (local products on the tensor cores in tf32x3 inside FP64 outer refinement), and the
+recovery of lambda and u.  Inputs (pattern stiffness, links, loads) are resident on the device when the timed
+region starts; the operands of every step are larger than L2 (the S^dag operators alone are 0.5 GB), and L2 is
+flushed between steps as well.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision fp64|fp32]
-                    [--k K] [--workload c2|c1|c3]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision fp64|fp32|tf32x3]
+                    [--k K] [--workload c3|c2|c1|c5]
 
 Under torchrun (N > 1) every rank solves its own independently seeded structure (weak scaling, no collective
 on the data path); rank 0 prints the JSON line with the slowest rank's time.
@@ -39,6 +40,12 @@ WORKLOADS = {
     "c5": "serving: structures arriving by a seeded Poisson process (mean 50/s), each 4-128 occurrences of one of "
           "6 resident patterns (2D heat 16^2/32^2/64^2, 3D elastic 8^3/12^3/16^3), admitted by device memory",
 }
+DEFAULTS = {  # per workload: local-product precision, multivector width, direction-history cap (GB; 0 = library)
+    "c3": ("tf32x3", 32, 32.0), "c2": ("fp32", 8, 0.0), "c1": ("fp64", 4, 0.0), "c5": ("fp32", 8, 0.0),
+}
+# Block iterations of the default workload (C3, k = 32, tol 1e-8): the count the library's FP64 solve needs
+# on this structure, used to scale the oracle's sampled per-iteration cost to a whole solve.
+C3_ITERATIONS = 120
 PHASE_KERNELS = {  # the kernels each phase launches
     "factor": "k_potrf_tile, k_trsm_tiles, k_update_pairs, k_tile_inverse, k_tri_*", "coarse": "k_gtg, k_gemm_f64",
     "local": "k_local_gemm / k_tc_gemm", "gather": "k_gather_tile", "scatter": "k_scatter",
@@ -47,13 +54,12 @@ PHASE_KERNELS = {  # the kernels each phase launches
     "reorth": "k_tall_update / k_tall_update_w32", "update": "k_split, k_update",
     "recover": "k_tri_*, k_unpermute_rotate", "normalise": "k_normalise",
     "iterate": "k_persist (whole block iterations in one cooperative launch)",
+    "outer": "FP64 residual: k_gather_tile, k_local_gemm<double>, k_scatter, projection",
 }
-# DRAM bytes (read + write) of one k_persist launch from an ncu capture of the bench command (profiles/
-# k_persist_c2.md: C2, FP32 inner products, k = 8); reported as the roofline's traffic for that configuration only
-PERSIST_C2_TRAFFIC_BYTES = 1.157120e6 + 0.392960e6
 PHASE_BOUND = {  # roofline resource of each phase's kernels
     "factor": "alu", "coarse": "alu", "local": "alu", "gather": "hbm", "scatter": "hbm", "project": "alu",
     "gram": "alu", "reorth": "alu", "update": "alu", "recover": "alu", "normalise": "alu", "iterate": "hbm",
+    "outer": "alu",
 }
 
 
@@ -150,6 +156,15 @@ def h2d_bytes(prob):
     return b
 
 
+def fapply_bytes(prob, k, es):
+    """Algorithmic bytes of one block F-apply (one Q = P^T F P Z over k columns): the local operators streamed
+    once (sum_p n_b^2 / 2 entries of size es, the symmetric factor's half) + the block read and written in FP64
+    (2 n_lambda k 8) + the coarse vectors (2 n_G k 8)."""
+    nb = sum(p.n_b ** 2 / 2 for p in prob.patterns)
+    n_G = sum(prob.patterns[o.pattern].kernel_dim for o in prob.occs)
+    return nb * es + 2 * prob.n_lambda * k * 8 + 2 * n_G * k * 8
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_1208_6387_gb300.fetirp as F
@@ -167,10 +182,11 @@ def run_ours(args, rank, world, local):
     lam_d = torch.empty(prob.n_lambda, dtype=torch.float64, device=dev)
     u_d = torch.empty(nu, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    hist_bytes = int(args.history_gb * 1e9)
 
-    def make_ctx(precision, timing, mask):
+    def make_ctx(precision, timing, mask=0):
         opts = F.fetirp_default_options(precision=precision, tol=1e-8, inner_tol=args.inner_tol, device=local,
-                                        timing=timing, timing_mask=mask, history_bytes=int(args.history_gb * 1e9))
+                                        timing=timing, timing_mask=mask, history_bytes=hist_bytes)
         opts.cuda_stream = stream.cuda_stream
         c = F.fetirp_create(opts)
         F.load_problem(c, prob)
@@ -184,16 +200,16 @@ def run_ours(args, rank, world, local):
         with torch.cuda.stream(stream):
             flush.zero_()
 
-    # untimed: every phase bracketed by events, to find the dominant kernel phase
+    # untimed probe: every phase bracketed by events (phase shares of one step)
     ctx = make_ctx(args.precision, 1, 0)
     probe = []
-    for _ in range(args.warmup):
+    for _ in range(max(1, args.warmup // 3)):
         flush_l2()
         probe.append(step(ctx))
     F.fetirp_destroy(ctx)
-    dom = int(np.argmax(np.sum([s["phase_ms"] for s in probe], axis=0)))
-    # timed: only the dominant phase is bracketed (two event nodes per occurrence of that phase)
-    ctx = make_ctx(args.precision, 1, 1 << dom)
+    probe_ms = np.sum([s["phase_ms"] for s in probe], axis=0) / max(len(probe), 1)
+    # timed: every phase bracketed by events (two event nodes per phase occurrence inside the captured graphs)
+    ctx = make_ctx(args.precision, 1, 0)
     for _ in range(args.warmup):
         flush_l2()
         step(ctx)
@@ -202,8 +218,9 @@ def run_ours(args, rank, world, local):
         torch.distributed.barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stats = []
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
+    import tempfile
+    clk_dir = tempfile.mkdtemp(prefix="fetirp_clocks_")
+    clk = Clocks(os.path.join(clk_dir, f"clocks_rank{rank}.csv"))
     torch.cuda.synchronize()
     with clk:
         t0 = time.perf_counter()
@@ -225,123 +242,192 @@ def run_ours(args, rank, world, local):
 
     value, ms_per_step = job_throughput(sum(step_ms), args.steps, world, reduce_max)
     total_ms = ms_per_step * args.steps
-
-    # check the last result against the definition (residual reported by the library, FP64)
     rel_res = max(s["rel_residual"] for s in stats)
 
-    # roofline of the dominant phase's kernels, CUDA events on the library's stream over the timed steps
     ph_ms = np.sum([s["phase_ms"] for s in stats], axis=0)
     ph_fl = np.sum([s["phase_flops"] for s in stats], axis=0)
     ph_by = np.sum([s["phase_bytes"] for s in stats], axis=0)
     ph_ln = np.sum([s["phase_launches"] for s in stats], axis=0)
-    probe_ms = np.sum([s["phase_ms"] for s in probe], axis=0) / max(len(probe), 1)
-    name = F.PHASES[dom]
-    bound = PHASE_BOUND[name]
     peaks, src = load_peaks()
-    per_launch_ms = ph_ms[dom] / max(ph_ln[dom], 1)
-    if bound == "hbm":
-        achieved = ph_by[dom] / (ph_ms[dom] / 1e3) / 1e9
-        peak, unit = peaks["hbm_gbs"], "GB/s"
-        peak_note = f"hbm_gbs of {src}"
-    else:
-        achieved = ph_fl[dom] / (ph_ms[dom] / 1e3) / 1e12
-        unit = "TFLOP/s"
-        if name == "local" and args.precision == "tf32x3":   # tcgen05 kind::tf32 (useful flops, 3 MMAs each)
-            bound = "tensor"
-            peak = peaks["bf16_tflops"] * 1.1 / 2.25
-            peak_note = f"tf32 tensor: bf16_tflops of {src} x 1.1/2.25 (nominal tf32/bf16 ratio)"
-        elif name in ("local", "reorth") and args.precision != "fp64":
-            peak = FP32_PEAK_TFLOPS
-            peak_note = "FP32 SIMT peak derived from 152 SMs x 128 lanes x 2070 MHz"
-        else:
-            peak = FP64_PEAK_TFLOPS
-            peak_note = "FP64 nominal 1.25 TFLOP/s (152 SMs x 2070 MHz; DFMA probe measured 1.19)"
-    roof = {"kernel": PHASE_KERNELS[name], "phase": name, "bound": bound, "achieved": round(achieved, 4),
-            "peak": round(peak, 3), "unit": unit, "frac": round(achieved / peak, 5),
-            "traffic": (PERSIST_C2_TRAFFIC_BYTES if (name == "iterate" and args.workload == "c2"
-                                                     and args.precision == "fp32" and prob.k == 8) else None),
-            "peak_source": peak_note, "launches_per_step": float(ph_ln[dom]) / args.steps,
-            "ms_per_launch": round(per_launch_ms, 5),
-            "share_of_step": round(float(ph_ms[dom]) / total_ms, 4) if world == 1 else None,
-            "phases_ms_per_step_untimed_probe": {F.PHASES[i]: round(float(probe_ms[i]), 4)
-                                                 for i in range(len(F.PHASES))}}
+    iters = float(np.mean([s["iterations"] for s in stats]))
+    roof = roofline(args, prob, F, peaks, src, ph_ms, ph_fl, ph_ln, stats)
+    roof["share_of_step"] = round(float(ph_ms[F.PHASES.index(roof["phase"])]) / total_ms, 4) if world == 1 else None
+    roof["phases_ms_per_step"] = {F.PHASES[i]: round(float(ph_ms[i]) / args.steps, 3) for i in range(len(F.PHASES))}
+    roof["phases_ms_per_step_untimed_probe"] = {F.PHASES[i]: round(float(probe_ms[i]), 3)
+                                                for i in range(len(F.PHASES))}
+    # the direction-history work (Gram products incl. eta, and the reorthogonalisation), its own key
+    hg = [F.PHASES.index("gram"), F.PHASES.index("reorth")]
+    hist_ms = float(sum(ph_ms[i] for i in hg))
+    hist_by = float(sum(ph_by[i] for i in hg))
+    history = {"kernels": PHASE_KERNELS["gram"] + "; " + PHASE_KERNELS["reorth"],
+               "ms_per_step": round(hist_ms / args.steps, 3), "ms_per_iteration": round(hist_ms / args.steps / iters, 4),
+               "bytes_per_step": hist_by / args.steps,
+               "achieved_gbs": round(hist_by / (hist_ms / 1e3) / 1e9, 2) if hist_ms > 0 else None,
+               "peak_gbs": peaks["hbm_gbs"], "frac": round(hist_by / (hist_ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4)
+               if hist_ms > 0 else None,
+               "note": "algorithmic bytes of the history reads and block passes (library accounting), HBM of " + src}
     F.fetirp_destroy(ctx)
-    ctx = make_ctx(args.precision, 0, 0)
-    F.fetirp_prepare(ctx, prob.n_lambda, prob.c)
 
-    # block F-applies/s: the block operator alone, device resident, k columns
-    k = prob.k
-    V = torch.randn(prob.n_lambda, k, dtype=torch.float64, device=dev)
-    Qo = torch.empty_like(V)
-    prec = F.PRECISIONS[args.precision]
-    for _ in range(5):
-        F.fetirp_apply_block_device(ctx, k, V.data_ptr(), Qo.data_ptr(), prec)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n_app = 50
-    a.record(stream)
-    for _ in range(n_app):
-        F.fetirp_apply_block_device(ctx, k, V.data_ptr(), Qo.data_ptr(), prec)
-    b.record(stream)
-    torch.cuda.synchronize()
-    fapply_per_s = n_app / (a.elapsed_time(b) / 1e3)
-
-    # the plain FP64 form of the same step, for comparison (same k, 3 steps, events on the stream)
-    plain_ms = None
-    if args.precision != "fp64" and not args.no_fp64_reference:
-        F.fetirp_destroy(ctx)
-        ctx = make_ctx("fp64", 0, 0)
-        step(ctx)
-        times = []
+    def fapply_rate(precision, n_app):
+        c = make_ctx(precision, 0)
+        F.fetirp_prepare(c, prob.n_lambda, prob.c)
+        k = prob.k
+        V = torch.randn(prob.n_lambda, k, dtype=torch.float64, device=dev)
+        Qo = torch.empty_like(V)
+        prec = F.PRECISIONS[precision]
         for _ in range(3):
+            F.fetirp_apply_block_device(c, k, V.data_ptr(), Qo.data_ptr(), prec)
+        F.fetirp_device_status(c)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n_app):
+            F.fetirp_apply_block_device(c, k, V.data_ptr(), Qo.data_ptr(), prec)
+        b.record(stream)
+        torch.cuda.synchronize()
+        F.fetirp_device_status(c)
+        F.fetirp_destroy(c)
+        return n_app / (a.elapsed_time(b) / 1e3)
+
+    fapply = {args.precision: round(fapply_rate(args.precision, 50), 2)}
+
+    # the plain FP64 form of the same step (same k, same history cap), for comparison: one timed solve
+    plain = None
+    if args.precision != "fp64" and not args.no_fp64_reference:
+        c = make_ctx("fp64", 0)
+        if args.workload != "c3":
+            step(c)   # small structures: one untimed solve first (graph capture, buffers)
+        times, its = [], []
+        for _ in range(1 if args.workload == "c3" else 3):
             flush_l2()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            step(ctx)
+            st = step(c)
             b.record(stream)
             torch.cuda.synchronize()
             times.append(a.elapsed_time(b))
-        plain_ms = statistics.median(times)
+            its.append(st["iterations"])
+        F.fetirp_destroy(c)
+        fapply["fp64"] = round(fapply_rate("fp64", 10 if args.workload == "c3" else 50), 3)
+        plain = {"time_to_solution_ms": round(statistics.median(times), 2), "iterations": its[-1],
+                 "block_f_applies_per_s": fapply["fp64"],
+                 "speedup_of_mixed_time_to_solution": round(statistics.median(times) / ms_per_step, 3),
+                 "speedup_of_mixed_f_applies": round(fapply[args.precision] / fapply["fp64"], 3)}
 
     # e2e: the public API from host buffers (create, patterns, occurrences, solve, outputs to host, destroy)
     e2e_times = []
-    for i in range(max(2, min(args.steps, 5)) + 1):
+    for i in range(3 if args.workload == "c3" else max(2, min(args.steps, 5)) + 1):
         t = time.perf_counter()
         c2 = F.fetirp_create(F.fetirp_default_options(precision=args.precision, tol=1e-8, inner_tol=args.inner_tol,
-                                                       device=local, history_bytes=int(args.history_gb * 1e9)))
+                                                       device=local, history_bytes=hist_bytes))
         F.load_problem(c2, prob)
         F.fetirp_solve(c2, prob.n_lambda, prob.c, nu)
         F.fetirp_destroy(c2)
         if i > 0:
             e2e_times.append(time.perf_counter() - t)
     e2e_s = statistics.median(e2e_times)
-    F.fetirp_destroy(ctx)
     launches = int(np.mean([s["launches"] for s in stats]))
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
-        "data": "synthetic (seeded Q1 meshes, loads; no datasets)",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+" + args.precision,
+        "data": "synthetic (seeded Q1 meshes, rotations, loads; no datasets)",
         "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "precision": args.precision,
                    "block_k": prob.k, "n_lambda": prob.n_lambda, "n_occ": prob.n_occ,
-                   "l2": "flushed between steps (256 MB write)", "tol": 1e-8,
+                   "l2": "operands larger than L2 and L2 flushed between steps (256 MB write)", "tol": 1e-8,
+                   "history_gb": args.history_gb,
                    "step": "factorise patterns + coarse + d + block ORTHODIR + recovery"},
-        "time_to_solution_ms": round(ms_per_step, 4),
+        "time_to_solution_ms": round(ms_per_step, 3),
         "iterations": stats[-1]["iterations"], "outer_steps": stats[-1]["outer_steps"],
         "rel_residual": rel_res,
-        "block_f_applies_per_s": round(fapply_per_s, 2),
-        "plain_fp64_ms_per_step": None if plain_ms is None else round(plain_ms, 3),
+        "block_f_applies_per_s": fapply,
+        "plain_fp64": plain,
         "gpu_launches": launches * args.steps,
         "e2e": {"value": round(world / e2e_s, 4), "unit": "solves/s", "h2d_bytes_per_step": h2d_bytes(prob),
                 "d2h_bytes_per_step": (prob.n_lambda + nu) * 8},
         "roofline": roof,
+        "history_gram": history,
         "clocks": clk.summary(local),
         "wall_s": round(wall, 4),
     }
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args, prob)
+        out["cpu_baseline"] = cpu_baseline(args, prob, stats[-1]["iterations"])
     if world > 1:
         torch.distributed.destroy_process_group()
     return out
+
+
+def roofline(args, prob, F, peaks, src, ph_ms, ph_fl, ph_ln, stats):
+    """Roofline of the dominant kernel of the F-apply, from the library's per-launch CUDA events over the timed
+    steps (events on the library's stream) and the algorithmic work of one launch.
+    tf32x3: k_tc_gemm, flops 2 sum_p n_b^2 R_p per launch (useful; three tf32 products are issued for each)
+    against the tf32 tensor peak = the measured sustained bf16 rate x 1.1 / 2.25 (nominal tf32 / bf16 ratio).
+    Persistent iteration (FP32 / FP64 SIMT, latency-bound structures): k_persist, the F-apply bytes of every
+    block iteration in the launch against the measured HBM copy rate."""
+    loc, itp = F.PHASES.index("local"), F.PHASES.index("iterate")
+    if ph_ln[itp] > 0:
+        es = 8 if args.precision == "fp64" else 4
+        n_it = float(sum(s["iterations"] for s in stats))
+        per_launch_ms = ph_ms[itp] / ph_ln[itp]
+        bytes_per_launch = fapply_bytes(prob, prob.k, es) * n_it / ph_ln[itp]
+        achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+        return {"kernel": "k_persist", "phase": "iterate", "bound": "hbm", "achieved": round(achieved, 3),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 6),
+                "traffic": None, "bytes_per_launch": bytes_per_launch, "launches": int(ph_ln[itp]),
+                "ms_per_launch": round(per_launch_ms, 4),
+                "peak_source": "hbm_gbs of " + src,
+                "work": "F-apply bytes (operators once + 2 n_lambda k 8 + 2 n_G k 8) x block iterations per launch"}
+    per_launch_ms = ph_ms[loc] / max(ph_ln[loc], 1)
+    flops_per_launch = ph_fl[loc] / max(ph_ln[loc], 1)
+    achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12
+    if args.precision == "tf32x3":
+        kern, bound = "k_tc_gemm (tcgen05 kind::tf32, 3 products)", "tensor"
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * 1.1 / 2.25
+        note = f"tf32 tensor: bf16_tflops_sustained of {src} x 1.1/2.25 (nominal tf32/bf16 ratio)"
+    elif args.precision == "fp32":
+        kern, bound, peak = "k_local_gemm<float>", "alu", FP32_PEAK_TFLOPS
+        note = "FP32 SIMT peak derived from 152 SMs x 128 lanes x 2070 MHz"
+    else:
+        kern, bound, peak = "k_local_gemm<double>", "alu", FP64_PEAK_TFLOPS
+        note = "FP64 nominal 1.25 TFLOP/s (152 SMs x 2070 MHz)"
+    out = {"kernel": kern, "phase": "local", "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 2),
+           "unit": "TFLOP/s", "frac": round(achieved / peak, 5), "traffic": None,
+           "flops_per_launch": flops_per_launch, "launches": int(ph_ln[loc]), "ms_per_launch": round(per_launch_ms, 4),
+           "peak_source": note, "work": "2 sum_p n_b^2 R_p per launch (R_p = occurrences of p x k)"}
+    if args.precision == "tf32x3":
+        out["issued_frac"] = round(3 * achieved / peak, 4)
+    return out
+
+
+class OracleSampler:
+    """Bounded sample of the oracle on a structure too large to solve on the host within the benchmark.  The
+    oracle's set-up (FetiOracle: pattern factorisations, G, G^T G and its inverse) is timed in full once; each
+    sample then times one F-apply of a k-column block through the oracle's generalized inverse restricted to
+    n_sample_occ occurrences (scaled to all of them) and one projection.  Estimated solve time = set-up +
+    n_it x (F-apply + 2 projections).  The oracle's history reorthogonalisation is left out, so the estimate
+    favours the oracle."""
+
+    def __init__(self, prob):
+        from oracle.feti import FetiOracle
+        self.prob = prob
+        t = time.perf_counter()
+        self.o = FetiOracle(prob, use_schur=False)
+        self.t_setup = time.perf_counter() - t
+        self.V = np.random.default_rng(5).standard_normal((prob.n_lambda, prob.k))
+
+    def sample(self, n_it, n_sample_occ=8):
+        o, prob, V = self.o, self.prob, self.V
+        t = time.perf_counter()
+        for s in range(n_sample_occ):
+            o.Bs[s] @ o.kplus(s, o.Bs[s].T @ V)
+        t_f = (time.perf_counter() - t) * prob.n_occ / n_sample_occ
+        t = time.perf_counter()
+        o.project(V)
+        t_p = time.perf_counter() - t
+        est = self.t_setup + n_it * (t_f + 2 * t_p)
+        return est, (f"oracle set-up timed in full ({self.t_setup:.1f} s); one k={prob.k} F-apply on {n_sample_occ} "
+                     f"of {prob.n_occ} occurrences ({t_f * n_sample_occ / prob.n_occ:.2f} s, scaled "
+                     f"x{prob.n_occ / n_sample_occ:g}) and one projection ({t_p:.2f} s); solve = set-up + {n_it} "
+                     f"iterations x (F-apply + 2 projections), reorthogonalisation not counted")
 
 
 def oracle_step(prob):
@@ -352,43 +438,63 @@ def oracle_step(prob):
     return it
 
 
-def cpu_baseline(args, prob):
-    """The oracle as it stands (numpy/scipy FP64 multivector FETI), one full solve of the same workload."""
+def cpu_baseline(args, prob, n_it):
+    """The oracle as it stands (numpy/scipy FP64): one full solve of the workload when it finishes in seconds
+    (C1, C2), else a bounded sample scaled to a solve."""
+    cores = len(os.sched_getaffinity(0))
+    if args.workload == "c3":
+        est, what = OracleSampler(prob).sample(n_it)
+        return {"value": round(1.0 / est, 6), "unit": "solves/s", "cores": cores, "kind": "oracle",
+                "sample": what + f"; estimated {est:.1f} s per solve; numpy/scipy default BLAS threads"}
     t = time.perf_counter()
     it = oracle_step(prob)
     dt = time.perf_counter() - t
-    return {"value": round(1.0 / dt, 5), "unit": "solves/s", "cores": len(os.sched_getaffinity(0)),
+    return {"value": round(1.0 / dt, 5), "unit": "solves/s", "cores": cores,
             "kind": "oracle", "sample": f"one full solve of the same workload ({it} block iterations, "
                                         f"{dt:.1f} s; numpy/scipy default BLAS threads)"}
 
 
 def run_reference(args, rank, world):
-    """The oracle timed on the host cores (rank 0 only), same workload/metric; each step one full solve."""
+    """The oracle timed on the host cores (rank 0 only), same workload/metric; each step one full solve (C1, C2)
+    or, for C3, one bounded sample scaled to a solve (the oracle's set-up, one sampled block F-apply and one
+    projection; see _oracle_sample)."""
     from fetirp_gen import config
     if rank != 0:
         return None
     prob = config(args.workload, seed=args.seed, k=args.k)
+    cores = len(os.sched_getaffinity(0))
+    if args.workload == "c3":
+        sampler = []
+
+        def one():   # the set-up is timed once (first warm-up step), every step samples the iteration
+            if not sampler:
+                sampler.append(OracleSampler(prob))
+            return sampler[0].sample(C3_ITERATIONS, n_sample_occ=4)
+    else:
+        def one():
+            t = time.perf_counter()
+            it = oracle_step(prob)
+            return time.perf_counter() - t, f"one full oracle solve ({it} block iterations)"
     for _ in range(args.warmup):
-        oracle_step(prob)
-    times = []
+        one()
+    times, what = [], ""
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        t = time.perf_counter()
-        oracle_step(prob)
-        times.append(time.perf_counter() - t)
+        est, what = one()
+        times.append(est)
     wall = time.perf_counter() - t0
     value = args.steps / sum(times)
-    cores = len(os.sched_getaffinity(0))
+    sample = ("each step " + what) if args.workload != "c3" else ("each step a bounded sample: " + what)
     return {
-        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "solves/s", "n_gpus": world,
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded Q1 meshes, loads; no datasets)",
+        "data": "synthetic (seeded Q1 meshes, rotations, loads; no datasets)",
         "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "block_k": prob.k,
                    "n_lambda": prob.n_lambda, "n_occ": prob.n_occ, "tol": 1e-8},
-        "cpu_baseline": {"value": round(value, 5), "unit": "solves/s", "cores": cores, "kind": "oracle",
-                         "sample": "each step one full oracle solve of the workload"},
-        "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": round(wall, 3),
     }
 
@@ -481,18 +587,20 @@ def run_serving(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "tf32x3"])
-    ap.add_argument("--k", type=int, default=8, help="multivector width (autotuned choice for C2 on GB300)")
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "tf32x3"],
+                    help="local-product arithmetic (default per workload: c3 tf32x3, c2 fp32)")
+    ap.add_argument("--k", type=int, default=None, help="multivector width (default per workload: c3 32, c2 8)")
     ap.add_argument("--inner-tol", type=float, default=1e-6)
-    ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="c3", choices=list(WORKLOADS))
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-reference", action="store_true")
-    ap.add_argument("--history-gb", type=float, default=0.0,
-                    help="cap on the direction history (GB); 0 = the library default (half of free memory)")
+    ap.add_argument("--history-gb", type=float, default=None,
+                    help="cap on the direction history (GB); 0 = the library default (half of free memory); "
+                         "default per workload: c3 32, others 0")
     ap.add_argument("--requests", type=int, default=1000, help="serving workload: number of structures")
     ap.add_argument("--rate", type=float, default=50.0, help="serving workload: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving workload: concurrent structures")
@@ -500,14 +608,16 @@ def main():
     ap.add_argument("--seq-sample", type=int, default=40, help="serving workload: requests timed sequentially")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    d_prec, d_k, d_hist = DEFAULTS[args.workload]
+    args.precision = args.precision or d_prec
+    args.k = args.k or d_k
+    args.history_gb = d_hist if args.history_gb is None else args.history_gb
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     elif args.workload == "c5":
         out = run_serving(args) if rank == 0 else None
     else:
-        if args.workload != "c2":
-            args.no_cpu_baseline = True   # the oracle's sample is defined for the default workload
         out = run_ours(args, rank, world, local)
     if rank == 0 and out is not None:
         print(json.dumps(out), flush=True)

@@ -107,7 +107,9 @@ enum {
   FETIRP_PHASE_RECOVER = 9,  /* alpha and u(s) */
   FETIRP_PHASE_NORMALISE = 10, /* F-normalisation of eta (pivoted Cholesky, one CTA) */
   FETIRP_PHASE_ITERATE = 11,   /* whole block iterations in one persistent launch (options.persistent) */
-  FETIRP_NPHASE = 12
+  FETIRP_PHASE_OUTER = 12,     /* FP64 residual evaluations r = P^T (d - F lambda) (initial residual and every
+                                  outer refinement step; their F-apply is not booked under local/gather/scatter) */
+  FETIRP_NPHASE = 13
 };
 
 typedef struct {
@@ -178,10 +180,11 @@ fetirp_status fetirp_create_pattern(fetirp_ctx ctx, int32_t n_nodes, int32_t dof
 
 /*
  * Add an occurrence of a pattern (Eq. 2 with the rotation of the elasticity subsection).
- *  rot[9]: row-major R with global = R * local, or NULL for the identity.  For patterns with more than one
- *     dof per node only signed permutation matrices with determinant +1 (the 24 rotations of the cube) are
- *     accepted; the rotation is folded into the links, so the hot path stays a signed gather/scatter.  With
- *     one dof per node the field has no components to turn, so any rotation is accepted and not used.
+ *  rot[9]: row-major R with global = R * local, or NULL for the identity.  R must be a proper rotation:
+ *     finite, R R^T = I and det R = +1, both to 1e-12 (FETIRP_EINVAL otherwise).  For patterns with more than
+ *     one dof per node only signed permutation matrices (the 24 rotations of the cube) are accepted; the
+ *     rotation is folded into the links, so the hot path stays a signed gather/scatter.  With one dof per node
+ *     the field has no components to turn, so any proper rotation is accepted and not used.
  *  n_links and the four link arrays: the rows of B(s) in the GLOBAL frame: entry sign[i] (+1 or -1) in
  *     multiplier row lambda_row[i] on component global_comp[i] of pattern node local_node[i], which must
  *     be one of the pattern's boundary nodes.  Every multiplier row must end up with one or two entries in
@@ -243,9 +246,21 @@ fetirp_status fetirp_solve_device(fetirp_ctx ctx, int64_t n_lambda, const double
  */
 fetirp_status fetirp_apply_block(fetirp_ctx ctx, int32_t k, const double* V, double* Q, int32_t precision);
 
-/* As fetirp_apply_block on DEVICE buffers; enqueued on the context's stream, returns without waiting. */
+/* As fetirp_apply_block on DEVICE buffers; enqueued on the context's stream, returns without waiting.  A
+ * bounded wait of the tensor-core pipeline (FETIRP_PREC_TF32X3) that expired is reported only through
+ * fetirp_device_status, since the call returns before the kernel has run. */
 fetirp_status fetirp_apply_block_device(fetirp_ctx ctx, int32_t k, const double* d_V, double* d_Q,
                                         int32_t precision);
+
+/*
+ * Completion status of the device work enqueued by the asynchronous "_device" entry points
+ * (fetirp_apply_block_device, fetirp_apply_split_device, fetirp_apply_block_device_noalloc): waits for the
+ * context's stream, then returns FETIRP_ETIMEOUT (and clears the flag) when a bounded wait inside the
+ * tensor-core pipeline expired since the last check, in which case the outputs of those calls are not valid;
+ * FETIRP_OK otherwise.  The blocking entry points (fetirp_solve, fetirp_apply_block, fetirp_apply_split) make
+ * this check themselves.
+ */
+fetirp_status fetirp_device_status(fetirp_ctx ctx);
 
 /* Q = P^T F P S(r) for the k split columns of one interface vector r (the multivector of Section 3.1:
  * column g holds r on the rows of the occurrences of group g, scaled by 1 / the row's occurrence count),

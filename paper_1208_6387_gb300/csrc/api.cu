@@ -225,12 +225,14 @@ struct fetirp_ctx_s {
   long long phase_launches[FETIRP_NPHASE] = {};
   double graph_phase_ms[FETIRP_NPHASE] = {};
   bool phases_pending = false;          // a fetirp_factorize call's phases belong to the next solve
+  int phase_override = -1;              // >= 0: every phase scope books into this phase (outer residual, recovery)
   // device-resident iteration state and the captured iteration graph
   DBuf<int> d_state;                    // [0] stored directions, [1] dropped directions, [2] iterations
   int* h_state = nullptr;               // pinned mirror for read-back
   double* h_rr = nullptr;               // pinned read-back of the residual partials
   bool owns_stream = false;
   bool capturing = false;
+  bool in_iteration = false;            // enqueuing block iterations outside a capture (accounted per iteration)
   std::vector<cudaStream_t> fstreams;   // one per concurrently factorised pattern
   cudaEvent_t fork_ev = nullptr;
   std::vector<cudaEvent_t> join_ev;
@@ -256,6 +258,18 @@ struct fetirp_ctx_s {
 };
 
 namespace {
+
+// Books every phase scope opened while it lives into one phase (work that belongs to a step of its own, such as
+// the FP64 residual of the outer refinement, whose F-apply would otherwise count as local product, gather and
+// scatter).  The outermost override wins.
+struct PhaseOverride {
+  fetirp_ctx ctx;
+  int saved;
+  PhaseOverride(fetirp_ctx c, int ph) : ctx(c), saved(c->phase_override) {
+    if (saved < 0) ctx->phase_override = ph;
+  }
+  ~PhaseOverride() { ctx->phase_override = saved; }
+};
 
 void set_err(fetirp_ctx ctx, const std::string& m) {
   if (ctx) ctx->err = m;
@@ -293,8 +307,10 @@ struct PhaseScope {
   int phase;
   unsigned long long l0;
   int e0 = -1;
-  PhaseScope(fetirp_ctx c, int ph, double flops, double bytes) : ctx(c), phase(ph), l0(g_launch_count) {
-    if (!ctx->capturing) {   // inside a captured graph the work is accounted per replay instead
+  PhaseScope(fetirp_ctx c, int ph_, double flops, double bytes)
+      : ctx(c), phase(c->phase_override >= 0 ? c->phase_override : ph_), l0(g_launch_count) {
+    const int ph = phase;
+    if (!ctx->capturing && !ctx->in_iteration) {   // block iterations are accounted per iteration instead
       ctx->phase_flops[ph] += flops;
       ctx->phase_bytes[ph] += bytes;
     }
@@ -1013,6 +1029,7 @@ double norm2(fetirp_ctx ctx, const double* x, int n) {
 
 // Residual r = P^T (d - F lambda) in FP64 (the projected residual of Table 1).
 void residual(fetirp_ctx ctx) {
+  PhaseOverride ov(ctx, FETIRP_PHASE_OUTER);
   const int nl = ctx->L.n_lambda;
   apply_F(ctx, ctx->lam.p, ctx->r.p, 1, FETIRP_PREC_FP64, false, false);
   // r = d - F lambda
@@ -1028,6 +1045,7 @@ void residual(fetirp_ctx ctx) {
 // from directions that were stored in FP32 (their rounding leaves range(P) at the 1e-7 level).
 void reproject_lambda(fetirp_ctx ctx) {
   if (ctx->n_G == 0) return;
+  PhaseOverride ov(ctx, FETIRP_PHASE_OUTER);
   const int nl = ctx->L.n_lambda;
   cudaStream_t s = ctx->stream;
   axpy_f64(nl, -1.0, ctx->lambda0.p, ctx->lam.p, s);
@@ -1171,7 +1189,14 @@ void run_iterations(fetirp_ctx ctx, int prec, int G, bool use_graph, TH* Wh, TH*
     g_launch_count += gc.total_launches;
     for (int p = 0; p < FETIRP_NPHASE; ++p) ctx->phase_launches[p] += gc.launches[p];
   } else {
-    for (int i = 0; i < G; ++i) enqueue_iteration<TH>(ctx, prec, Wh, Qh);
+    ctx->in_iteration = true;
+    try {
+      for (int i = 0; i < G; ++i) enqueue_iteration<TH>(ctx, prec, Wh, Qh);
+    } catch (...) {
+      ctx->in_iteration = false;
+      throw;
+    }
+    ctx->in_iteration = false;
   }
 }
 
@@ -1374,6 +1399,7 @@ double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, His
 
 void recover(fetirp_ctx ctx, double* d_u_out) {
   cudaStream_t s = ctx->stream;
+  PhaseOverride ov(ctx, FETIRP_PHASE_RECOVER);
   PhaseScope ph(ctx, FETIRP_PHASE_RECOVER, 0.0, 0.0);
   const Layout& L = ctx->L;
   const int nl = L.n_lambda;
@@ -1847,6 +1873,20 @@ fetirp_status fetirp_add_occurrence(fetirp_ctx ctx, int32_t pattern_id, const do
     const PatternData& P = *ctx->pats[pattern_id];
     OccData O;
     O.pattern = pattern_id;
+    if (rot) {   // a proper rotation: finite, R R^T = I and det R = +1 (to 1e-12)
+      for (int i = 0; i < 9; ++i) REQUIRE(std::isfinite(rot[i]), "non-finite rotation entry");
+      double dev = 0.0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double d = a == b ? -1.0 : 0.0;
+          for (int c = 0; c < 3; ++c) d += rot[3 * a + c] * rot[3 * b + c];
+          dev = std::max(dev, std::fabs(d));
+        }
+      const double detr = rot[0] * (rot[4] * rot[8] - rot[5] * rot[7]) - rot[1] * (rot[3] * rot[8] - rot[5] * rot[6]) +
+                          rot[2] * (rot[3] * rot[7] - rot[4] * rot[6]);
+      REQUIRE(dev <= 1e-12 && std::fabs(detr - 1.0) <= 1e-12,
+              "rot must be a proper rotation (R R^T = I and det R = +1 to 1e-12)");
+    }
     if (rot && P.dpn > 1) {   // one dof per node: the rotation only places the pattern, no component turns
       int det = 0;
       for (int r = 0; r < 3; ++r) {
@@ -2278,6 +2318,13 @@ fetirp_status fetirp_apply_split(fetirp_ctx ctx, const double* r, double* Q, int
     check_tc_error(ctx);
     FETIRP_CUDA(cudaMemcpyAsync(Q, dq.p, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
     FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
+    return FETIRP_OK;
+  });
+}
+
+fetirp_status fetirp_device_status(fetirp_ctx ctx) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    check_tc_error(ctx);   // synchronises the context stream, reads the flag and clears it
     return FETIRP_OK;
   });
 }

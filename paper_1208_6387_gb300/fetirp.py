@@ -53,15 +53,15 @@ def caching_allocator_hooks(device: int = 0):
 
 
 PHASES = ["factor", "coarse", "local", "gather", "scatter", "project", "gram", "reorth", "update", "recover",
-          "normalise", "iterate"]
+          "normalise", "iterate", "outer"]
 
 
 class fetirp_stats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("outer_steps", C.c_int32), ("f_applies", C.c_int32),
                 ("dropped_directions", C.c_int32), ("kernel_dim_total", C.c_int32), ("rel_residual", C.c_double),
                 ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("launches", C.c_int64),
-                ("phase_ms", C.c_double * 12), ("phase_launches", C.c_int64 * 12),
-                ("phase_flops", C.c_double * 12), ("phase_bytes", C.c_double * 12)]
+                ("phase_ms", C.c_double * 13), ("phase_launches", C.c_int64 * 13),
+                ("phase_flops", C.c_double * 13), ("phase_bytes", C.c_double * 13)]
 
     def as_dict(self):
         d = {}
@@ -117,6 +117,7 @@ _SIGS = {
     "fetirp_prepare": (C.c_int, [P, C.c_int64, P]),
     "fetirp_factorize": (C.c_int, [P]),
     "fetirp_inject_barrier_stall": (C.c_int, [P]),
+    "fetirp_device_status": (C.c_int, [P]),
     "fetirp_apply_split": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_int]),
     "fetirp_apply_split_device": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_int]),
     "fetirp_get_pattern": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), P, P]),
@@ -364,6 +365,12 @@ def fetirp_apply_block_device_noalloc(ctx, k, V_ptr, Q_ptr, precision=FETIRP_PRE
     device allocation in the call; see include/fetirp.h for the size limit and the sharing rules)."""
     _check(ctx, lib().fetirp_apply_block_device_noalloc(ctx, int(k), C.c_void_p(V_ptr), C.c_void_p(Q_ptr),
                                                          int(precision)))
+
+
+def fetirp_device_status(ctx):
+    """Waits for the context's stream; raises FetirpError(FETIRP_ETIMEOUT) if a bounded tensor-core wait of an
+    asynchronous _device call expired since the last check."""
+    _check(ctx, lib().fetirp_device_status(ctx))
 
 
 def fetirp_factorize(ctx):

@@ -205,9 +205,16 @@ def test_single_occurrence_and_invalid_inputs():
     with pytest.raises(F.FetirpError) as e:   # link on an interior node
         F.fetirp_add_occurrence(ctx, 0, None, [5], [0], [0], [1], np.zeros(pat.n_dofs))
     assert e.value.status == F.FETIRP_EINVAL
-    with pytest.raises(F.FetirpError) as e:   # not a rotation of the cube
-        F.fetirp_add_occurrence(ctx, 0, np.eye(3) * 0.5, [0], [0], [0], [1], np.zeros(pat.n_dofs))
-    assert e.value.status == F.FETIRP_EINVAL
+    c, s_ = np.cos(0.7), np.sin(0.7)
+    bad_rot = {"scaled": np.eye(3) * 0.5, "reflection": np.diag([1.0, 1.0, -1.0]),
+               "nan": np.full((3, 3), np.nan), "sheared": np.array([[1.0, 1e-9, 0], [0, 1, 0], [0, 0, 1]])}
+    for what, R in bad_rot.items():   # not a proper rotation: refused even where no component turns
+        with pytest.raises(F.FetirpError) as e:
+            F.fetirp_add_occurrence(ctx, 0, R, [0], [0], [0], [1], np.zeros(pat.n_dofs))
+        assert e.value.status == F.FETIRP_EINVAL, what
+    # a proper rotation by 0.7 rad is accepted for a scalar field (nothing to turn)
+    F.fetirp_add_occurrence(ctx, 0, np.array([[c, -s_, 0], [s_, c, 0], [0, 0, 1.0]]), [0], [0], [0], [1],
+                            np.zeros(pat.n_dofs))
     with pytest.raises(F.FetirpError) as e:   # wrong expected kernel dimension
         F.fetirp_create_pattern(ctx, pat.n_nodes, 1, K.indptr, K.indices, K.data, pat.bnd_nodes, 2)
     assert e.value.status == F.FETIRP_ESINGULAR
