@@ -181,10 +181,13 @@ fetirp_status fetirp_create_pattern(fetirp_ctx ctx, int32_t n_nodes, int32_t dof
 /*
  * Add an occurrence of a pattern (Eq. 2 with the rotation of the elasticity subsection).
  *  rot[9]: row-major R with global = R * local, or NULL for the identity.  R must be a proper rotation:
- *     finite, R R^T = I and det R = +1, both to 1e-12 (FETIRP_EINVAL otherwise).  For patterns with more than
- *     one dof per node only signed permutation matrices (the 24 rotations of the cube) are accepted; the
- *     rotation is folded into the links, so the hot path stays a signed gather/scatter.  With one dof per node
- *     the field has no components to turn, so any proper rotation is accepted and not used.
+ *     finite, R R^T = I and det R = +1, both to 1e-12 (FETIRP_EINVAL otherwise).  With one dof per node the
+ *     field has no components to turn, so the rotation is not used.  With two dofs per node R may not couple
+ *     z with x or y (entries above 1e-12 there: FETIRP_EINVAL).  Vector fields: a signed permutation (the
+ *     rotations of the cube, of the square) is folded into the links, so the hot path stays a signed
+ *     gather/scatter; any other rotation keeps the links in the global frame and the gathered traces are turned
+ *     into the pattern frame node by node (R^T) on the device, and the local solutions back (R), before the
+ *     scatter.  Such occurrences use the per-phase iteration and are not accepted by fetirp_apply_split.
  *  n_links and the four link arrays: the rows of B(s) in the GLOBAL frame: entry sign[i] (+1 or -1) in
  *     multiplier row lambda_row[i] on component global_comp[i] of pattern node local_node[i], which must
  *     be one of the pattern's boundary nodes.  Every multiplier row must end up with one or two entries in
@@ -209,6 +212,28 @@ fetirp_status fetirp_clear_occurrences(fetirp_ctx ctx);
  * Without this call the occurrences are split into min(block_k, n_occ) contiguous groups by id.
  */
 fetirp_status fetirp_set_groups(fetirp_ctx ctx, int32_t k, const int32_t* group_of_occ);
+
+/*
+ * The permutation multivector of Section 3.1 (Eq. 8) for a periodic structure: the block of search directions
+ * built from the residual z is [z, Pi z, Pi^2 z, ..., Pi^(n_images-1) z] instead of the occurrence split, Pi
+ * being the map of interface vectors under the rotation of the structure by one occurrence (a signed
+ * permutation of the multiplier rows, with the rotation of vector components by the structure's rotation).
+ *  n_lambda, rowptr[n_lambda + 1], col[nnz], val[nnz]: Pi as a CSR matrix (row i of Pi z = sum val z[col]).
+ *     Every power Pi^g (g < n_images) may have at most 8 entries per row (FETIRP_EINVAL otherwise).
+ *     rowptr = NULL switches back to the occurrence split.
+ *  n_images: the block width k, 1..64 (n_images = number of occurrences for a ring of them).
+ *  shortcut: 1 = the periodic shortcut of Table 1 (right): since F commutes with Pi on such a structure, the
+ *     F-image of the block is [p, Pi p, ...] with one single-column F-apply p = P^T F P z, and the image of the
+ *     reorthogonalised block follows by the same linear combination of the stored images (no F-apply of k
+ *     columns).  The next fetirp_prepare / fetirp_solve checks P^T F P Pi v = Pi P^T F P v on a seeded vector in
+ *     FP64 (relative 1e-9) and returns FETIRP_EINVAL when the structure is not periodic under Pi.
+ *     0 = the F-apply of the whole block, as for any multivector.
+ * The setting stays until fetirp_set_groups, fetirp_clear_occurrences or a call with rowptr = NULL.  Solves
+ * with a permutation use the per-phase iteration (CUDA graphs), not the persistent kernel.  fetirp_apply_split
+ * needs the occurrence split and returns FETIRP_EINVAL meanwhile.  Every input is copied.
+ */
+fetirp_status fetirp_set_permutation(fetirp_ctx ctx, int64_t n_lambda, const int64_t* rowptr, const int32_t* col,
+                                     const double* val, int32_t n_images, int32_t shortcut);
 
 /*
  * Solve for lambda and the displacements (Table 1 and the recovery u(s) = K^+ (f - B^T lambda) + N alpha).

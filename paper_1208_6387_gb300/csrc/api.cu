@@ -72,18 +72,18 @@ __global__ void k_to_f32(size_t n, const double* __restrict__ x, float* __restri
 // original dof order and the global frame: u_g[node][c] = sum_c' R[c][c'] u_l[node][c'].
 __global__ void k_unpermute_rotate(int n_dofs, int dpn, int npad, const double* __restrict__ U,
                                    const int* __restrict__ newidx, const int* __restrict__ occ_list,
-                                   const int* __restrict__ rot, const long long* __restrict__ uoff, int n_occ_p,
+                                   const double* __restrict__ rot, const long long* __restrict__ uoff, int n_occ_p,
                                    double* __restrict__ out) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)n_dofs * n_occ_p) return;
   const int q = (int)(idx / n_dofs), d = (int)(idx % n_dofs);
   const int s = occ_list[q];
   const int node = d / dpn, c = d % dpn;
-  const int* R = rot + 9 * s;
+  const double* R = rot + 9 * s;
   double v = 0.0;
   for (int c2 = 0; c2 < dpn; ++c2) {
-    const int r = R[3 * c + c2];
-    if (r != 0) v += r * U[(size_t)q * npad + newidx[node * dpn + c2]];
+    const double r = dpn > 1 ? R[3 * c + c2] : 1.0;
+    if (r != 0.0) v = fma(r, U[(size_t)q * npad + newidx[node * dpn + c2]], v);
   }
   out[uoff[s] + d] = v;
 }
@@ -124,7 +124,9 @@ struct PatternUse {
 
 struct OccData {
   int pattern = 0;
-  int R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  int R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};     // signed permutation folded into the links
+  bool general = false;                       // a rotation of a vector field that is not a signed permutation
+  double Rd[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}; // the rotation (row-major, global = R local) in both cases
   std::vector<double> f_local;  // pattern frame, original dof order
   std::vector<int> link_j, link_row;
   std::vector<int8_t> link_sign;
@@ -161,6 +163,17 @@ struct fetirp_ctx_s {
   std::vector<OccData> occs;
   int k_user = 0;
   std::vector<int> groups_user;
+  // permutation multivector (Eq. 8): column g of the block is Pi^g z; Pi^g in ELL form (pw entries per row and
+  // column, weight 0 = padding), built on the host when the permutation is set
+  struct Perm {
+    bool on = false, shortcut = false;
+    int k = 0, pw = 1;
+    int64_t n = 0;
+    std::vector<int> src;       // [(row k + g) pw + e]
+    std::vector<double> w;
+    DBuf<int> d_src, d_grp_src;
+    DBuf<double> d_w;
+  } perm;
 
   // structure state (prepare)
   bool prepared = false;
@@ -168,7 +181,8 @@ struct fetirp_ctx_s {
   int k = 1, n_G = 0, n_Gpad = 0;
   Layout L{};
   DBuf<int> d_slot_ptr, d_slot_row, d_row_slot, d_slot_occ, d_occ_obase, d_occ_pat, d_occ_q, d_occ_gofs,
-      d_occ_group, d_pair_s, d_pair_t, d_rot, d_grp_ptr, d_grp_row, d_ell_row;
+      d_occ_group, d_pair_s, d_pair_t, d_grp_ptr, d_grp_row, d_ell_row, d_gen_occ;
+  DBuf<double> d_rot, d_gen_R, d_slot_nb;   // rotation of every occurrence; general rotations and their slot kernels
   DBuf<int8_t> d_ell_sign;
   DBuf<double> d_grp_w;
   // tables of the persistent iteration: multivector columns of the row's slots, 1 / slot count, offsets of the
@@ -193,6 +207,7 @@ struct fetirp_ctx_s {
   DBuf<int8_t> d_slot_sign, d_row_sign;
   DBuf<long long> d_uoff;
   int n_pairs = 0;
+  int n_gen = 0;                       // occurrences with a general rotation (turned on the device)
   int max_group_rows = 0;
   std::vector<int> pofs;               // first coarse column of every pattern
   std::vector<long long> uoff;         // offset of every occurrence in u_out
@@ -217,9 +232,10 @@ struct fetirp_ctx_s {
 
   // per-phase accounting (CUDA events when opt.timing = 1)
   struct PhaseRec { int phase; int e0, e1; };
-  std::vector<cudaEvent_t> ev_pool;
+  std::vector<cudaEvent_t> ev_pool;     // events recorded directly on the stream (reused by every call)
   size_t ev_used = 0;
-  size_t ev_reserved = 0;
+  std::vector<cudaEvent_t> gev_pool;    // event nodes of the captured iteration graph (live with the graph)
+  size_t gev_used = 0;
   std::vector<PhaseRec> recs;
   double phase_flops[FETIRP_NPHASE] = {}, phase_bytes[FETIRP_NPHASE] = {};
   long long phase_launches[FETIRP_NPHASE] = {};
@@ -248,6 +264,7 @@ struct fetirp_ctx_s {
   ~fetirp_ctx_s() {
     if (gc.exec) cudaGraphExecDestroy(gc.exec);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : gev_pool) cudaEventDestroy(e);
     if (h_state) cudaFreeHost(h_state);
     if (h_rr) cudaFreeHost(h_rr);
     for (cudaStream_t st : fstreams) cudaStreamDestroy(st);
@@ -317,16 +334,18 @@ struct PhaseScope {
     if (ctx->opt.timing && (ctx->opt.timing_mask == 0 || ((ctx->opt.timing_mask >> ph) & 1))) e0 = record();
   }
   int record() {
-    if (ctx->ev_used == ctx->ev_pool.size()) {
+    std::vector<cudaEvent_t>& pool = ctx->capturing ? ctx->gev_pool : ctx->ev_pool;
+    size_t& used = ctx->capturing ? ctx->gev_used : ctx->ev_used;
+    if (used == pool.size()) {
       cudaEvent_t e;
       FETIRP_CUDA(cudaEventCreate(&e));
-      ctx->ev_pool.push_back(e);
+      pool.push_back(e);
     }
-    const int id = (int)ctx->ev_used++;
+    const int id = (int)used++;
     if (ctx->capturing)   // an event node inside the captured graph, re-recorded at every replay
-      FETIRP_CUDA(cudaEventRecordWithFlags(ctx->ev_pool[id], ctx->stream, cudaEventRecordExternal));
+      FETIRP_CUDA(cudaEventRecordWithFlags(pool[id], ctx->stream, cudaEventRecordExternal));
     else
-      FETIRP_CUDA(cudaEventRecord(ctx->ev_pool[id], ctx->stream));
+      FETIRP_CUDA(cudaEventRecord(pool[id], ctx->stream));
     return id;
   }
   ~PhaseScope() {
@@ -344,7 +363,7 @@ struct PhaseScope {
 };
 
 void reset_phases(fetirp_ctx ctx) {
-  ctx->ev_used = ctx->ev_reserved;   // events owned by the captured graph stay reserved
+  ctx->ev_used = 0;   // the captured graph's events are a pool of their own
   ctx->recs.clear();
   for (int i = 0; i < FETIRP_NPHASE; ++i) {
     ctx->phase_flops[i] = ctx->phase_bytes[i] = ctx->graph_phase_ms[i] = 0.0;
@@ -560,6 +579,7 @@ TilePlan dense_plan(int nt) {
 
 // ----------------------------------------------------------------------------------------- structure
 void invalidate(fetirp_ctx ctx) { ctx->prepared = false; }
+void check_periodic(fetirp_ctx ctx);
 
 // Local-product buffers for a block of k columns in every precision (allocated before any graph capture).
 void ensure_apply_buffers(fetirp_ctx ctx, int k) {
@@ -595,7 +615,11 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   ctx->n_G = ctx->pofs[n_pat];
   // multivector groups
   int k;
-  if (ctx->k_user > 0) {
+  if (ctx->perm.on) {   // the block is [z, Pi z, ...]; occurrence groups only serve the tables below
+    if (ctx->perm.n != n_lambda) throw Error(FETIRP_EINVAL, "the permutation's size differs from n_lambda");
+    k = ctx->perm.k;
+    for (int o = 0; o < n_occ; ++o) group[o] = (int)((long long)o * std::min(k, n_occ) / n_occ);
+  } else if (ctx->k_user > 0) {
     k = ctx->k_user;
     group = ctx->groups_user;
   } else {
@@ -672,12 +696,27 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
     }
     grp[g1].push_back({r, w});
   }
-  std::vector<int> grp_ptr(k + 1, 0), grp_row;
+  std::vector<int> grp_ptr(k + 1, 0), grp_row, grp_src;
   std::vector<double> grp_w;
-  for (int g = 0; g < k; ++g) {
-    std::sort(grp[g].begin(), grp[g].end());
-    for (auto& e : grp[g]) { grp_row.push_back(e.first); grp_w.push_back(e.second); }
-    grp_ptr[g + 1] = (int)grp_row.size();
+  if (ctx->perm.on) {   // column g of S(r) = Pi^g r: entries (row, source row, weight) of Pi^g, row by row
+    const int pw = ctx->perm.pw;
+    for (int g = 0; g < k; ++g) {
+      for (int r = 0; r < nl; ++r)
+        for (int e = 0; e < pw; ++e) {
+          const size_t i = ((size_t)r * k + g) * pw + e;
+          if (ctx->perm.w[i] == 0.0) continue;
+          grp_row.push_back(r);
+          grp_src.push_back(ctx->perm.src[i]);
+          grp_w.push_back(ctx->perm.w[i]);
+        }
+      grp_ptr[g + 1] = (int)grp_row.size();
+    }
+  } else {
+    for (int g = 0; g < k; ++g) {
+      std::sort(grp[g].begin(), grp[g].end());
+      for (auto& e : grp[g]) { grp_row.push_back(e.first); grp_w.push_back(e.second); }
+      grp_ptr[g + 1] = (int)grp_row.size();
+    }
   }
   // neighbour pairs (s, t) sharing a row, plus (s, s)
   std::vector<std::vector<int>> nbr(n_occ);
@@ -716,6 +755,11 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   ctx->d_grp_ptr.upload(grp_ptr, s);
   ctx->d_grp_row.upload(grp_row, s);
   ctx->d_grp_w.upload(grp_w, s);
+  if (ctx->perm.on) {
+    ctx->perm.d_grp_src.upload(grp_src, s);
+    ctx->perm.d_src.upload(ctx->perm.src, s);
+    ctx->perm.d_w.upload(ctx->perm.w, s);
+  }
   {
     std::vector<long long> pbase(n_pat + 1, 0);
     for (int p = 0; p < n_pat; ++p)
@@ -751,6 +795,19 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
         FETIRP_CUDA(cudaMemcpyAsync(hNb[p].data(), P.Nb.p, sizeof(double) * hNb[p].size(), cudaMemcpyDeviceToHost, s));
     }
     FETIRP_CUDA(cudaStreamSynchronize(s));
+    // the kernel restricted to a slot, in the global frame: N_b[j] for folded rotations; for a general
+    // rotation the slot (node b, global component c) takes sum_c2 R[c][c2] N_b[b dpn + c2]
+    auto nb_of = [&](int slot, int m) -> double {
+      const int o = slot_occ[slot];
+      const PatternData& P = *ctx->pats[occ_pat[o]];
+      const int j = slot - obase[o];
+      const std::vector<double>& nb = hNb[occ_pat[o]];
+      if (!ctx->occs[o].general) return nb[(size_t)j * P.kdim + m];
+      const int b = j / P.dpn, c = j % P.dpn;
+      double v = 0.0;
+      for (int c2 = 0; c2 < P.dpn; ++c2) v += ctx->occs[o].Rd[3 * c + c2] * nb[(size_t)(b * P.dpn + c2) * P.kdim + m];
+      return v;
+    };
     for (int r = 0; r < nl; ++r)
       for (int e = 0; e < row_cnt[r]; ++e) {
         const int slot = row_slot[2 * (size_t)r + e];
@@ -759,10 +816,26 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
         if (P.kdim > 6 || P.kdim == 0) continue;
         rowg_gofs[2 * (size_t)r + e] = occ_gofs[o];
         rowg_kd[2 * (size_t)r + e] = P.kdim;
-        for (int m = 0; m < P.kdim; ++m)
-          rowg_coef[(2 * (size_t)r + e) * 6 + m] =
-              row_sign[2 * (size_t)r + e] * hNb[occ_pat[o]][(size_t)(slot - obase[o]) * P.kdim + m];
+        for (int m = 0; m < P.kdim; ++m) rowg_coef[(2 * (size_t)r + e) * 6 + m] = row_sign[2 * (size_t)r + e] * nb_of(slot, m);
       }
+    std::vector<int> gen_occ;
+    std::vector<double> gen_R;
+    for (int o = 0; o < n_occ; ++o)
+      if (ctx->occs[o].general) {
+        gen_occ.push_back(o);
+        gen_R.insert(gen_R.end(), ctx->occs[o].Rd, ctx->occs[o].Rd + 9);
+      }
+    ctx->n_gen = (int)gen_occ.size();
+    if (ctx->n_gen > 0) {
+      for (int p = 0; p < n_pat; ++p)
+        if (ctx->pats[p]->kdim > 6) throw Error(FETIRP_EINVAL, "general rotations need kernel dimensions <= 6");
+      std::vector<double> snb((size_t)n_slots * 6, 0.0);
+      for (int slot = 0; slot < n_slots; ++slot)
+        for (int m = 0; m < ctx->pats[occ_pat[slot_occ[slot]]]->kdim; ++m) snb[(size_t)slot * 6 + m] = nb_of(slot, m);
+      ctx->d_gen_occ.upload(gen_occ, s);
+      ctx->d_gen_R.upload(gen_R, s);
+      ctx->d_slot_nb.upload(snb, s);
+    }
     ctx->n_gcoef = 0;
     for (int kd : rowg_kd) ctx->n_gcoef += kd;
     ctx->d_rowg_gofs.upload(rowg_gofs, s);
@@ -772,8 +845,8 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   ctx->d_pair_s.upload(pair_s, s);
   ctx->d_pair_t.upload(pair_t, s);
   ctx->n_pairs = (int)pair_s.size();
-  std::vector<int> rot(9 * (size_t)n_occ);
-  for (int o = 0; o < n_occ; ++o) std::memcpy(&rot[9 * (size_t)o], ctx->occs[o].R, sizeof(int) * 9);
+  std::vector<double> rot(9 * (size_t)n_occ);
+  for (int o = 0; o < n_occ; ++o) std::memcpy(&rot[9 * (size_t)o], ctx->occs[o].Rd, sizeof(double) * 9);
   ctx->d_rot.upload(rot, s);
   ctx->uoff.assign(n_occ + 1, 0);
   for (int o = 0; o < n_occ; ++o) ctx->uoff[o + 1] = ctx->uoff[o] + ctx->pats[occ_pat[o]]->n;
@@ -798,6 +871,11 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   L.row_grp = ctx->d_row_grp.p; L.row_wt = ctx->d_row_wt.p;
   L.rowg_gofs = ctx->d_rowg_gofs.p; L.rowg_kd = ctx->d_rowg_kd.p; L.rowg_coef = ctx->d_rowg_coef.p;
   L.slot_code = ctx->d_slot_code.p;
+  for (int p = 0; p < n_pat; ++p) L.dpn[p] = ctx->pats[p]->dpn;
+  L.n_gen = ctx->n_gen;
+  L.gen_occ = ctx->n_gen ? ctx->d_gen_occ.p : nullptr;
+  L.gen_R = ctx->n_gen ? ctx->d_gen_R.p : nullptr;
+  L.slot_nb = ctx->n_gen ? ctx->d_slot_nb.p : nullptr;
   {  // G^T V chunks: at most 512 links per CTA, and at least two CTAs per SM while chunks keep >= 64 links
     int chunks =
         std::max(ceil_div(max_links, 512), std::min(ceil_div(max_links, 64), ceil_div(2 * 152, std::max(n_occ, 1))));
@@ -869,6 +947,7 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
     }
     V.base[p] = Us.U.p; V.ld[p] = P.npad; V.off[p] = P.n_i;
   }
+  rotate_traces<double>(L, V, 1, false, s);
   scatter<double>(L, V, 1, 0.0, ctx->d.p, s);
   axpy_f64(nl, -1.0, ctx->c.p, ctx->d.p, s);
   // work buffers
@@ -888,6 +967,7 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   ctx->n_lambda = n_lambda;
   ctx->prepared = true;
   FETIRP_CUDA(cudaStreamSynchronize(s));
+  if (ctx->perm.on && ctx->perm.shortcut && k > 1) check_periodic(ctx);
 }
 
 // ----------------------------------------------------------------------------------------- operators
@@ -921,6 +1001,7 @@ void run_local(fetirp_ctx ctx, const Layout& L, const double* src, double* out, 
   {
     PhaseScope ph(ctx, FETIRP_PHASE_GATHER, 0.0, vbytes + rhs_elems * es);
     gather<T>(L, src, k, Yv, s);
+    rotate_traces<T>(L, Yv, k, true, s);
   }
   {
     PhaseScope ph(ctx, FETIRP_PHASE_LOCAL, flops, sbytes + 2.0 * rhs_elems * es);
@@ -929,6 +1010,7 @@ void run_local(fetirp_ctx ctx, const Layout& L, const double* src, double* out, 
   }
   {
     PhaseScope ph(ctx, FETIRP_PHASE_SCATTER, 0.0, vbytes + rhs_elems * es);
+    rotate_traces<T>(L, Zv, k, false, s);
     scatter<T>(L, Zv, k, 0.0, out, s);
   }
 }
@@ -998,6 +1080,7 @@ void apply_F(fetirp_ctx ctx, const double* in, double* out, int k, int prec, boo
     {
       PhaseScope ph(ctx, FETIRP_PHASE_GATHER, 0.0, vbytes + 2.0 * rhs_elems * 4);
       gather_split(L, src, k, Yh, Yl, s);
+      rotate_split(L, Yh, Yl, k, s);   // general rotations: turned to the pattern frame and split again
     }
     {
       PhaseScope ph(ctx, FETIRP_PHASE_LOCAL, flops, bytes);
@@ -1005,12 +1088,45 @@ void apply_F(fetirp_ctx ctx, const double* in, double* out, int k, int prec, boo
     }
     {
       PhaseScope ph(ctx, FETIRP_PHASE_SCATTER, 0.0, vbytes + rhs_elems * 4);
+      rotate_traces<float>(L, Zv, k, false, s);
       scatter<float>(L, Zv, k, 0.0, out, s);
     }
   } else {
     throw Error(FETIRP_EINVAL, "unsupported precision");
   }
   if (project_out) project(ctx, out, k);
+}
+
+// The periodic shortcut computes the F-image of [z, Pi z, ...] from the one of z, which is exact only when Pi
+// commutes with P^T F P (a structure made of rotated copies, Pi the map of multiplier rows under the rotation).
+// Checked once per structure in FP64 on a seeded vector: P^T F P (Pi v) against Pi (P^T F P v).
+void check_periodic(fetirp_ctx ctx) {
+  cudaStream_t s = ctx->stream;
+  const int nl = ctx->L.n_lambda, k = ctx->perm.k, pw = ctx->perm.pw;
+  std::vector<double> v(nl);
+  uint64_t x = 0x9E3779B97F4A7C15ull;
+  for (int i = 0; i < nl; ++i) {   // splitmix64 values in [-1, 1)
+    x += 0x9E3779B97F4A7C15ull;
+    uint64_t z = x;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[i] = (double)(z >> 11) * 0x1.0p-52 - 1.0;
+  }
+  ctx->V1.upload(v.data(), nl, s);
+  perm_split(nl, k, pw, ctx->perm.d_src.p, ctx->perm.d_w.p, ctx->V1.p, ctx->t1.p, s, 1);   // Pi v
+  apply_F(ctx, ctx->t1.p, ctx->W.p, 1, FETIRP_PREC_FP64, true, true);                       // P^T F P Pi v
+  apply_F(ctx, ctx->V1.p, ctx->Q.p, 1, FETIRP_PREC_FP64, true, true);                       // P^T F P v
+  perm_split(nl, k, pw, ctx->perm.d_src.p, ctx->perm.d_w.p, ctx->Q.p, ctx->t1.p, s, 1);     // Pi P^T F P v
+  std::vector<double> a(nl), b(nl);
+  FETIRP_CUDA(cudaMemcpyAsync(a.data(), ctx->W.p, sizeof(double) * nl, cudaMemcpyDeviceToHost, s));
+  FETIRP_CUDA(cudaMemcpyAsync(b.data(), ctx->t1.p, sizeof(double) * nl, cudaMemcpyDeviceToHost, s));
+  FETIRP_CUDA(cudaStreamSynchronize(s));
+  double dn = 0.0, bn = 0.0;
+  for (int i = 0; i < nl; ++i) { dn += (a[i] - b[i]) * (a[i] - b[i]); bn += b[i] * b[i]; }
+  if (!(std::sqrt(dn) <= 1e-9 * std::sqrt(bn)))
+    throw Error(FETIRP_EINVAL, "the periodic shortcut needs P^T F P Pi = Pi P^T F P; relative mismatch " +
+                                   std::to_string(std::sqrt(dn / std::max(bn, 1e-300))));
 }
 
 double norm2(fetirp_ctx ctx, const double* x, int n) {
@@ -1075,21 +1191,41 @@ void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
   const int nl = ctx->L.n_lambda, k = ctx->k;
   const long long cap = ctx->hist_cap;
   int* d_cols = ctx->d_state.p;
+  const bool permuted = ctx->perm.on;
   {
     PhaseScope ph(ctx, FETIRP_PHASE_UPDATE, 0.0, 0.0);
-    split(ctx->L, ctx->r.p, k, ctx->Zr.p, s);
+    if (permuted)   // Eq. 8: [r, Pi r, ..., Pi^(k-1) r]
+      perm_split(nl, k, ctx->perm.pw, ctx->perm.d_src.p, ctx->perm.d_w.p, ctx->r.p, ctx->Zr.p, s);
+    else
+      split(ctx->L, ctx->r.p, k, ctx->Zr.p, s);
   }
   {
     PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 0.0, 0.0);
     gram_split<TH>((int)cap, d_cols, k, Qh, nl, k, ctx->r.p, ctx->d_grp_ptr.p, ctx->d_grp_row.p, ctx->d_grp_w.p,
-                   ctx->n_grp_entries, ctx->max_group_rows, ctx->C.p, ctx->gram_part, ctx->grp_wr, s);
+                   ctx->n_grp_entries, ctx->max_group_rows, ctx->C.p, ctx->gram_part, ctx->grp_wr, s,
+                   permuted ? ctx->perm.d_grp_src.p : nullptr);
   }
   project(ctx, ctx->Zr.p, k);
   {
     PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 0.0, 0.0);
     tall_update<TH>(nl, (int)cap, d_cols, k, Wh, k, ctx->C.p, -1.0, ctx->Zr.p, ctx->tu_part, ctx->tu_tickets, s);
   }
-  apply_F(ctx, ctx->Zr.p, ctx->Q.p, k, prec, false, true);   // P~ = P^T F W (the F-image of the directions, Table 1)
+  if (permuted && ctx->perm.shortcut) {
+    // periodic shortcut (Table 1, right, for a periodic structure): F commutes with Pi, so the F-image of
+    // [r, Pi r, ...] is [p, Pi p, ...] with the one column p = P^T F P r; the reorthogonalised block's image
+    // follows by the same linear combination, P~ = [p, Pi p, ...] - Q_h C, with no further F-apply
+    apply_F(ctx, ctx->r.p, ctx->t1.p, 1, prec, true, true);
+    {
+      PhaseScope ph(ctx, FETIRP_PHASE_UPDATE, 0.0, 0.0);
+      perm_split(nl, k, ctx->perm.pw, ctx->perm.d_src.p, ctx->perm.d_w.p, ctx->t1.p, ctx->Q.p, s);
+    }
+    {
+      PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 0.0, 0.0);
+      tall_update<TH>(nl, (int)cap, d_cols, k, Qh, k, ctx->C.p, -1.0, ctx->Q.p, ctx->tu_part, ctx->tu_tickets, s);
+    }
+  } else {
+    apply_F(ctx, ctx->Zr.p, ctx->Q.p, k, prec, false, true);   // P~ = P^T F W (the F-image of the directions, Table 1)
+  }
   {
     PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 0.0, 0.0);
     eta_off = eta_partials(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta_part, s);
@@ -1129,17 +1265,22 @@ void account_iteration(fetirp_ctx ctx, int prec, long long a, double es, bool pe
   F[FETIRP_PHASE_PROJECT] += 2.0 * (2.0 * nG * nG * k + 4.0 * ctx->n_gcoef * k);
   B[FETIRP_PHASE_PROJECT] += 2.0 * (16.0 * nl * k + 8.0 * nG * nG);
   const double e_loc = prec == FETIRP_PREC_FP64 ? 8.0 : 4.0;
+  const double kf = ctx->perm.on && ctx->perm.shortcut ? 1.0 : k;   // columns of the iteration's F-apply
+  if (kf != k) {   // periodic shortcut: one more history pass (Q -= Q_h C) and one more permuted copy
+    F[FETIRP_PHASE_REORTH] += 2.0 * nl * a * k;
+    B[FETIRP_PHASE_REORTH] += es * nl * a + 16.0 * nl * k;
+  }
   double rhs = 0;
   for (size_t pi = 0; pi < ctx->pats.size(); ++pi) {
     const PatternData* P = ctx->pats[pi].get();
-    const double R = (double)ctx->use[pi].occs.size() * k;
+    const double R = (double)ctx->use[pi].occs.size() * kf;
     F[FETIRP_PHASE_LOCAL] += 2.0 * P->n_b * (double)P->n_b * R;
     B[FETIRP_PHASE_LOCAL] += (prec == FETIRP_PREC_TF32X3 ? 2.0 : 1.0) * e_loc * P->n_b * (double)P->n_b +
                              (prec == FETIRP_PREC_TF32X3 ? 3.0 : 2.0) * e_loc * P->n_b * R;
     rhs += P->n_b * R;
   }
-  B[FETIRP_PHASE_GATHER] += 8.0 * nl * k + (prec == FETIRP_PREC_TF32X3 ? 2.0 : 1.0) * e_loc * rhs;
-  B[FETIRP_PHASE_SCATTER] += 8.0 * nl * k + e_loc * rhs;
+  B[FETIRP_PHASE_GATHER] += 8.0 * nl * kf + (prec == FETIRP_PREC_TF32X3 ? 2.0 : 1.0) * e_loc * rhs;
+  B[FETIRP_PHASE_SCATTER] += 8.0 * nl * kf + e_loc * rhs;
   if (persistent) {   // the whole iteration ran in one launch: its work is also that of the iterate phase
     double f1 = 0.0, b1 = 0.0;
     for (int i = 0; i < FETIRP_NPHASE; ++i) { f1 += F[i]; b1 += B[i]; }
@@ -1162,7 +1303,7 @@ void run_iterations(fetirp_ctx ctx, int prec, int G, bool use_graph, TH* Wh, TH*
       if (gc.exec) { cudaGraphExecDestroy(gc.exec); gc.exec = nullptr; }
       gc.recs.clear();
       for (auto& v : gc.launches) v = 0;
-      ctx->ev_used = ctx->ev_reserved = 0;
+      ctx->gev_used = 0;
       const unsigned long long l0 = g_launch_count;
       cudaGraph_t graph = nullptr;
       FETIRP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -1183,7 +1324,7 @@ void run_iterations(fetirp_ctx ctx, int prec, int G, bool use_graph, TH* Wh, TH*
       gc.total_launches = (long long)(g_launch_count - l0);
       g_launch_count = l0;   // captured, not launched
       gc.prec = prec; gc.k = ctx->k; gc.G = G; gc.th = th; gc.cap = ctx->hist_cap; gc.timing = tkey;
-      ctx->ev_reserved = ctx->ev_used;
+
     }
     FETIRP_CUDA(cudaGraphLaunch(gc.exec, s));
     g_launch_count += gc.total_launches;
@@ -1206,6 +1347,8 @@ bool persist_eligible(fetirp_ctx ctx, int prec) {
   if (!ctx->opt.persistent) return false;
   if (prec != FETIRP_PREC_FP64 && prec != FETIRP_PREC_FP32) return false;
   if (ctx->k > 32 || ctx->L.n_lambda > 262144) return false;
+  if (ctx->L.n_gen > 0) return false;   // general rotations turn the traces in separate passes
+  if (ctx->perm.on) return false;       // the persistent phases build the occurrence split
   for (auto& P : ctx->pats)
     if (P->kdim > 6) return false;
   return persist_ctas(prec == FETIRP_PREC_FP64, ctx->k) > 0;
@@ -1381,7 +1524,7 @@ double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, His
     if (ctx->opt.timing && g == G && ctx->opt.use_graphs)
       for (auto& r : ctx->gc.recs) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ctx->ev_pool[r.e0], ctx->ev_pool[r.e1]) == cudaSuccess)
+        if (cudaEventElapsedTime(&ms, ctx->gev_pool[r.e0], ctx->gev_pool[r.e1]) == cudaSuccess)
           ctx->graph_phase_ms[r.phase] += ms;
       }
     double acc = 0.0;
@@ -1423,7 +1566,9 @@ void recover(fetirp_ctx ctx, double* d_u_out) {
       FETIRP_CUDA(cudaMemcpyAsync(Us.U.p, Us.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, s));
     V.base[p] = Us.U.p; V.ld[p] = P.npad; V.off[p] = P.n_i;
   }
+  rotate_traces<double>(L, V, 1, false, s);   // general rotations: f(s) to the global frame, add -B^T lambda,
   gather<double>(L, ctx->lam.p, 1, V, s, -1.0, 1.0);
+  rotate_traces<double>(L, V, 1, true, s);    // and back to the pattern frame
   for (int p = 0; p < n_pat; ++p) {
     PatternData& P = *ctx->pats[p];
     PatternUse& Us = ctx->use[p];
@@ -1543,6 +1688,7 @@ fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_st
     }
   }
   st.rel_residual = r0 > 0.0 ? rn / r0 : 0.0;
+  st.f_applies = st.iterations;   // one block F-apply per block iteration
   check_tc_error(ctx);
   if (d_lambda)
     FETIRP_CUDA(cudaMemcpyAsync(d_lambda, ctx->lam.p, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
@@ -1663,11 +1809,15 @@ void apply_noalloc(fetirp_ctx ctx, const double* V, double* Q, int k, int prec, 
     }
     if (prec == FETIRP_PREC_FP64) {
       gather<double>(L, V2, k, Yd, s);
+      rotate_traces<double>(L, Yd, k, true, s);
       local_gemm_f64(LP, s);
+      rotate_traces<double>(L, Zd, k, false, s);
       scatter<double>(L, Zd, k, 0.0, Q, s);
     } else {
       gather<float>(L, V2, k, Yf, s);
+      rotate_traces<float>(L, Yf, k, true, s);
       local_gemm_f32(LP, s);
+      rotate_traces<float>(L, Zf, k, false, s);
       scatter<float>(L, Zf, k, 0.0, Q, s);
     }
   } else {
@@ -1685,7 +1835,9 @@ void apply_noalloc(fetirp_ctx ctx, const double* V, double* Q, int k, int prec, 
       T.n_b[p] = P.n_b; T.n_rhs[p] = (int)ctx->use[p].occs.size() * k;
     }
     gather_split(L, V2, k, Yh, Yl, s);
+    rotate_split(L, Yh, Yl, k, s);
     tc_gemm_tf32x3(T, ctx->tc_error.p, s);
+    rotate_traces<float>(L, Zv, k, false, s);
     scatter<float>(L, Zv, k, 0.0, Q, s);
   }
   project_with(ctx, Q, k, Xc, Ac);
@@ -1888,26 +2040,28 @@ fetirp_status fetirp_add_occurrence(fetirp_ctx ctx, int32_t pattern_id, const do
               "rot must be a proper rotation (R R^T = I and det R = +1 to 1e-12)");
     }
     if (rot && P.dpn > 1) {   // one dof per node: the rotation only places the pattern, no component turns
-      int det = 0;
-      for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < P.dpn; ++c)
+        for (int c2 = P.dpn; c2 < 3; ++c2)
+          REQUIRE(std::fabs(rot[3 * c + c2]) <= 1e-12 && std::fabs(rot[3 * c2 + c]) <= 1e-12,
+                  "rotation mixes a modelled component with an absent one");
+      bool perm = true;   // a signed permutation (the rotations of the cube): folded into the links
+      for (int r = 0; r < P.dpn; ++r) {
         int nzc = 0;
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < P.dpn; ++c) {
           const double v = rot[3 * r + c];
-          REQUIRE(v == 0.0 || v == 1.0 || v == -1.0, "rotation must be a signed permutation (90-degree steps)");
+          if (v != 0.0 && v != 1.0 && v != -1.0) perm = false;
           if (v != 0.0) ++nzc;
-          O.R[3 * r + c] = (int)v;
         }
-        REQUIRE(nzc == 1, "rotation must be a signed permutation (90-degree steps)");
+        if (nzc != 1) perm = false;
       }
-      const int* R = O.R;
-      det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) + R[2] * (R[3] * R[7] - R[4] * R[6]);
-      REQUIRE(det == 1, "rotation must have determinant +1");
-      if (P.dpn > 1)
-        for (int c = 0; c < P.dpn; ++c)
-          for (int c2 = P.dpn; c2 < 3; ++c2)
-            REQUIRE(O.R[3 * c + c2] == 0, "rotation mixes a modelled component with an absent one");
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+          const bool modelled = r < P.dpn && c < P.dpn;
+          O.Rd[3 * r + c] = modelled ? rot[3 * r + c] : (r == c ? 1.0 : 0.0);
+          O.R[3 * r + c] = perm ? (int)O.Rd[3 * r + c] : (r == c ? 1 : 0);
+        }
+      O.general = !perm;
     }
-    if (P.dpn == 1) { const int I[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}; std::memcpy(O.R, I, sizeof(I)); }
     O.link_j.resize(n_links);
     O.link_row.resize(n_links);
     O.link_sign.resize(n_links);
@@ -1918,8 +2072,8 @@ fetirp_status fetirp_add_occurrence(fetirp_ctx ctx, int32_t pattern_id, const do
       REQUIRE(sign[i] == 1 || sign[i] == -1, "link sign must be +1 or -1");
       REQUIRE(lambda_row[i] >= 0, "negative lambda_row");
       const int c = global_comp[i];
-      int c2 = 0, rs = 1;
-      if (P.dpn > 1)
+      int c2 = c, rs = 1;   // general rotation: the slot holds the global component, turned on the device
+      if (P.dpn > 1 && !O.general)
         for (int cc = 0; cc < P.dpn; ++cc)
           if (O.R[3 * c + cc] != 0) { c2 = cc; rs = O.R[3 * c + cc]; }
       O.link_j[i] = P.bpos[local_node[i]] * P.dpn + c2;
@@ -1934,7 +2088,7 @@ fetirp_status fetirp_add_occurrence(fetirp_ctx ctx, int32_t pattern_id, const do
         for (int c = 0; c < P.dpn; ++c) {
           const double fg = f_global[node * P.dpn + c];
           REQUIRE(std::isfinite(fg), "non-finite load");
-          v += (P.dpn > 1 ? O.R[3 * c + c2] : (c == c2 ? 1 : 0)) * fg;
+          v += (P.dpn > 1 ? O.Rd[3 * c + c2] : (c == c2 ? 1.0 : 0.0)) * fg;
         }
         O.f_local[node * P.dpn + c2] = v;
       }
@@ -1950,6 +2104,7 @@ fetirp_status fetirp_clear_occurrences(fetirp_ctx ctx) {
     ctx->occs.clear();
     ctx->k_user = 0;
     ctx->groups_user.clear();
+    ctx->perm.on = false;
     invalidate(ctx);
     return FETIRP_OK;
   });
@@ -1963,6 +2118,7 @@ fetirp_status fetirp_set_groups(fetirp_ctx ctx, int32_t k, const int32_t* group_
     for (int o = 0; o < n; ++o) REQUIRE(group_of_occ[o] >= 0 && group_of_occ[o] < k, "group id out of range");
     ctx->k_user = k;
     ctx->groups_user.assign(group_of_occ, group_of_occ + n);
+    ctx->perm.on = false;
     invalidate(ctx);
     return FETIRP_OK;
   });
@@ -2073,6 +2229,9 @@ void split_plan_build(fetirp_ctx ctx) {
   cudaStream_t s = ctx->stream;
   SplitPlan& SP = ctx->sp;
   const Layout& L = ctx->L;
+  if (L.n_gen > 0)
+    throw Error(FETIRP_EINVAL, "the sparse-column form takes rotations of vector fields in 90-degree steps only");
+  if (ctx->perm.on) throw Error(FETIRP_EINVAL, "the sparse-column form needs the occurrence split, not a permutation");
   const int n_occ = L.n_occ, k = ctx->k, n_pat = (int)ctx->pats.size(), nl = L.n_lambda;
   std::vector<int> obase(n_occ + 1, 0), occ_pat(n_occ), occ_gofs(n_occ);
   for (int p = 0; p < n_pat; ++p)
@@ -2318,6 +2477,75 @@ fetirp_status fetirp_apply_split(fetirp_ctx ctx, const double* r, double* Q, int
     check_tc_error(ctx);
     FETIRP_CUDA(cudaMemcpyAsync(Q, dq.p, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
     FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
+    return FETIRP_OK;
+  });
+}
+
+fetirp_status fetirp_set_permutation(fetirp_ctx ctx, int64_t n_lambda, const int64_t* rowptr, const int32_t* col,
+                                     const double* val, int32_t n_images, int32_t shortcut) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    if (!rowptr) {   // back to the occurrence split
+      ctx->perm.on = false;
+      invalidate(ctx);
+      return FETIRP_OK;
+    }
+    REQUIRE(n_lambda > 0 && n_lambda < (1LL << 31), "n_lambda out of range");
+    REQUIRE(col && val, "NULL permutation array");
+    REQUIRE(n_images >= 1 && n_images <= 64, "n_images must be in 1..64");
+    REQUIRE(shortcut == 0 || shortcut == 1, "shortcut must be 0 or 1");
+    const int n = (int)n_lambda;
+    REQUIRE(rowptr[0] == 0, "rowptr[0] must be 0");
+    for (int i = 0; i < n; ++i) REQUIRE(rowptr[i + 1] >= rowptr[i], "rowptr must be non-decreasing");
+    for (int64_t e = 0; e < rowptr[n]; ++e) {
+      REQUIRE(col[e] >= 0 && col[e] < n, "permutation column out of range");
+      REQUIRE(std::isfinite(val[e]), "non-finite permutation entry");
+    }
+    // powers Pi^g, g < n_images, row by row: (Pi^g)[row] = sum_e Pi[row][c_e] (Pi^(g-1))[c_e]
+    constexpr int PW_MAX = 8;
+    using Row = std::vector<std::pair<int, double>>;
+    std::vector<Row> cur(n), next(n);
+    for (int i = 0; i < n; ++i) cur[i] = {{i, 1.0}};
+    std::vector<std::vector<Row>> pows;
+    pows.push_back(cur);
+    int pw = 1;
+    for (int g = 1; g < n_images; ++g) {
+      for (int i = 0; i < n; ++i) {
+        Row acc;
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+          for (const auto& t : cur[col[e]]) acc.push_back({t.first, val[e] * t.second});
+        std::sort(acc.begin(), acc.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        Row merged;
+        for (const auto& t : acc) {
+          if (!merged.empty() && merged.back().first == t.first) merged.back().second += t.second;
+          else merged.push_back(t);
+        }
+        Row kept;
+        for (const auto& t : merged)
+          if (t.second != 0.0) kept.push_back(t);
+        if ((int)kept.size() > PW_MAX)
+          throw Error(FETIRP_EINVAL, "a row of a power of the permutation has more than 8 entries");
+        pw = std::max(pw, (int)kept.size());
+        next[i] = std::move(kept);
+      }
+      cur.swap(next);
+      pows.push_back(cur);
+    }
+    auto& P = ctx->perm;
+    P.k = n_images;
+    P.pw = pw;
+    P.n = n_lambda;
+    P.src.assign((size_t)n * n_images * pw, 0);
+    P.w.assign((size_t)n * n_images * pw, 0.0);
+    for (int g = 0; g < n_images; ++g)
+      for (int i = 0; i < n; ++i)
+        for (size_t e = 0; e < pows[g][i].size(); ++e) {
+          const size_t at = ((size_t)i * n_images + g) * pw + e;
+          P.src[at] = pows[g][i][e].first;
+          P.w[at] = pows[g][i][e].second;
+        }
+    P.shortcut = shortcut == 1;
+    P.on = true;
+    invalidate(ctx);
     return FETIRP_OK;
   });
 }

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(128) k_gtg(Layout L, const int* __restrict__ p
   const int b0 = L.occ_obase[s], b1 = L.occ_obase[s + 1];
   double acc[MAX_KDIM * MAX_KDIM] = {};
   for (int slot = b0 + threadIdx.x; slot < b1; slot += blockDim.x) {
-    const double* ns = L.Nb[ps] + (size_t)(slot - b0) * ks;
+    const double* ns = L.slot_nb ? L.slot_nb + (size_t)slot * MAX_KDIM : L.Nb[ps] + (size_t)(slot - b0) * ks;
     for (int e = L.slot_ptr[slot]; e < L.slot_ptr[slot + 1]; ++e) {
       const int row = L.slot_row[e];
       const int sg = L.slot_sign[e];
@@ -139,7 +139,8 @@ __global__ void __launch_bounds__(128) k_gtg(Layout L, const int* __restrict__ p
         if (sg2 == 0) continue;
         const int slot2 = L.row_slot[2 * row + f];
         if (L.slot_occ[slot2] != t) continue;
-        const double* nt = L.Nb[pt] + (size_t)(slot2 - L.occ_obase[t]) * kt;
+        const double* nt =
+            L.slot_nb ? L.slot_nb + (size_t)slot2 * MAX_KDIM : L.Nb[pt] + (size_t)(slot2 - L.occ_obase[t]) * kt;
         const double w = (double)(sg * sg2);
         for (int m = 0; m < ks; ++m)
           for (int m2 = 0; m2 < kt; ++m2) acc[m * MAX_KDIM + m2] = fma(w * ns[m], nt[m2], acc[m * MAX_KDIM + m2]);
@@ -238,6 +239,43 @@ __global__ void __launch_bounds__(256) k_gather_tile(Layout L, const double* __r
     }
   }
 }
+// Node-by-node rotation of the traces of the occurrences with a general rotation (grid: node-column tiles x
+// listed occurrence).  MODE 0: y <- R y (pattern frame -> global frame); 1: y <- R^T y; 2: the trace is the
+// tf32 pair y = Y + Y2 (from the splitting gather): y <- R^T y, split again into a tf32 pair (hi -> Y,
+// lo -> Y2).  Products in FP64.
+template <typename T, int MODE>
+__global__ void k_rotate_traces(Layout L, PatView<T> Y, PatView<T> Y2, int k) {
+  const int i = blockIdx.y;
+  const int s = L.gen_occ[i];
+  const int p = L.occ_pat[s], q = L.occ_q[s];
+  const int dpn = L.dpn[p];
+  const int nbn = L.n_b[p] / dpn;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nbn * k) return;
+  const int g = (int)(idx / nbn), b = (int)(idx % nbn);
+  const double* R = L.gen_R + 9 * (size_t)i;
+  const long long o = ((long long)q * k + g) * Y.ld[p] + Y.off[p] + (long long)b * dpn;
+  T* y = Y.base[p] + o;
+  double v[3] = {0.0, 0.0, 0.0}, w[3];
+  for (int c = 0; c < dpn; ++c) v[c] = MODE == 2 ? (double)y[c] + (double)Y2.base[p][o + c] : (double)y[c];
+  for (int c = 0; c < dpn; ++c) {
+    double t = 0.0;
+    for (int c2 = 0; c2 < dpn; ++c2) t = fma(MODE == 0 ? R[3 * c + c2] : R[3 * c2 + c], v[c2], t);
+    w[c] = t;
+  }
+  for (int c = 0; c < dpn; ++c) {
+    if (MODE == 2) {
+      const float f = (float)w[c];
+      uint32_t h;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(f));
+      y[c] = (T)__uint_as_float(h);
+      Y2.base[p][o + c] = (T)(f - __uint_as_float(h));
+    } else {
+      y[c] = (T)w[c];
+    }
+  }
+}
+
 template <typename TI>
 __global__ void k_scatter(Layout L, PatView<TI> Z, int k, double beta, double* __restrict__ out) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -432,6 +470,50 @@ void gather_split(const Layout& L, const double* V, int k, const PatView<float>&
   if (k > 64) throw Error(1, "k > 64");
   k_gather_tile<float, true><<<dim3(L.n_occ, ceil_div(max_slots(L), GT_SLOTS)), 256, 0, s>>>(L, V, k, Yh, Yl, 1.0,
                                                                                              0.0);
+  FETIRP_LAUNCH_CHECK();
+}
+
+__global__ void k_perm_split(int n, int k, int pw, const int* __restrict__ src, const double* __restrict__ w,
+                             const double* __restrict__ r, double* __restrict__ Z, int g_only) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int kk = g_only >= 0 ? 1 : k;
+  if (idx >= (long long)n * kk) return;
+  const int row = (int)(idx / kk), g = g_only >= 0 ? g_only : (int)(idx % kk);
+  const size_t e0 = ((size_t)row * k + g) * pw;
+  double z = 0.0;
+  for (int e = 0; e < pw; ++e) {
+    const double we = w[e0 + e];
+    if (we != 0.0) z = fma(we, r[src[e0 + e]], z);
+  }
+  Z[idx] = z;
+}
+void perm_split(int n, int k, int pw, const int* src, const double* w, const double* r, double* Z, cudaStream_t s,
+                int g_only) {
+  const long long tot = (long long)n * (g_only >= 0 ? 1 : k);
+  if (tot == 0) return;
+  k_perm_split<<<(unsigned)ceil_div(tot, 256), 256, 0, s>>>(n, k, pw, src, w, r, Z, g_only);
+  FETIRP_LAUNCH_CHECK();
+}
+
+static int max_nodes(const Layout& L) {
+  int m = 1;
+  for (int p = 0; p < L.n_pat; ++p) m = std::max(m, L.n_b[p] / std::max(L.dpn[p], 1));
+  return m;
+}
+template <typename T>
+void rotate_traces(const Layout& L, const PatView<T>& Y, int k, bool to_local, cudaStream_t s) {
+  if (L.n_gen == 0) return;
+  const dim3 grid((unsigned)ceil_div((long long)max_nodes(L) * k, 256), L.n_gen);
+  if (to_local) k_rotate_traces<T, 1><<<grid, 256, 0, s>>>(L, Y, Y, k);
+  else k_rotate_traces<T, 0><<<grid, 256, 0, s>>>(L, Y, Y, k);
+  FETIRP_LAUNCH_CHECK();
+}
+template void rotate_traces<double>(const Layout&, const PatView<double>&, int, bool, cudaStream_t);
+template void rotate_traces<float>(const Layout&, const PatView<float>&, int, bool, cudaStream_t);
+void rotate_split(const Layout& L, const PatView<float>& Yh, const PatView<float>& Yl, int k, cudaStream_t s) {
+  if (L.n_gen == 0) return;
+  const dim3 grid((unsigned)ceil_div((long long)max_nodes(L) * k, 256), L.n_gen);
+  k_rotate_traces<float, 2><<<grid, 256, 0, s>>>(L, Yh, Yl, k);
   FETIRP_LAUNCH_CHECK();
 }
 

@@ -569,12 +569,12 @@ template void update<float>(int, int, const double*, const double*, const double
 constexpr int GS_ROWS = 256;   // rows per chunk
 constexpr int GS_COLS = 64;    // history columns per item
 constexpr int GS_GRID = 1216;  // 8 CTAs per SM
-__global__ void k_group_wr(int total, const int* __restrict__ grp_row, const double* __restrict__ grp_w,
-                           const double* __restrict__ r, double* __restrict__ wd, float* __restrict__ wh,
-                           float* __restrict__ wl) {
+__global__ void k_group_wr(int total, const int* __restrict__ grp_row, const int* __restrict__ grp_src,
+                           const double* __restrict__ grp_w, const double* __restrict__ r, double* __restrict__ wd,
+                           float* __restrict__ wh, float* __restrict__ wl) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= total) return;
-  const double v = grp_w[e] * r[grp_row[e]];
+  const double v = grp_w[e] * r[grp_src ? grp_src[e] : grp_row[e]];
   wd[e] = v;
   const float vh = (float)v;
   wh[e] = vh;
@@ -765,7 +765,7 @@ __global__ void k_reduce_chunks_dyn(int a_max, const int* __restrict__ d_a, int 
 template <typename TH>
 void gram_split(int a_max, const int* d_a, int k, const TH* Qh, int n, int hk, const double* r, const int* grp_ptr,
                 const int* grp_row, const double* grp_w, int n_entries, int max_group_rows, double* C,
-                DBuf<double>& partial, DBuf<double>& wr, cudaStream_t s) {
+                DBuf<double>& partial, DBuf<double>& wr, cudaStream_t s, const int* grp_src) {
   if (a_max <= 0) return;
   const int chunks = std::max(1, ceil_div(max_group_rows, GS_ROWS));
   partial.ensure((size_t)chunks * a_max * k);
@@ -774,7 +774,7 @@ void gram_split(int a_max, const int* d_a, int k, const TH* Qh, int n, int hk, c
   float* wh = reinterpret_cast<float*>(wr.p + std::max(n_entries, 1));
   float* wl = wh + std::max(n_entries, 1);
   if (n_entries > 0) {
-    k_group_wr<<<ceil_div(n_entries, 256), 256, 0, s>>>(n_entries, grp_row, grp_w, r, wd, wh, wl);
+    k_group_wr<<<ceil_div(n_entries, 256), 256, 0, s>>>(n_entries, grp_row, grp_src, grp_w, r, wd, wh, wl);
     FETIRP_LAUNCH_CHECK();
   }
   const int items = ceil_div(a_max, GS_COLS) * k * chunks;
@@ -786,9 +786,10 @@ void gram_split(int a_max, const int* d_a, int k, const TH* Qh, int n, int hk, c
 }
 template void gram_split<double>(int, const int*, int, const double*, int, int, const double*, const int*,
                                  const int*, const double*, int, int, double*, DBuf<double>&, DBuf<double>&,
-                                 cudaStream_t);
+                                 cudaStream_t, const int*);
 template void gram_split<float>(int, const int*, int, const float*, int, int, const double*, const int*, const int*,
-                                const double*, int, int, double*, DBuf<double>&, DBuf<double>&, cudaStream_t);
+                                const double*, int, int, double*, DBuf<double>&, DBuf<double>&, cudaStream_t,
+                                const int*);
 
 template <typename TH>
 void hist_dot(int n, int a, const TH* Qh, int hk, const double* r, double* C, DBuf<double>& partial,

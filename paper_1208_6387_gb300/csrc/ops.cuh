@@ -55,6 +55,16 @@ struct Layout {
   int gtv_chunk = 1, gtv_chunks = 1;
   double* gtv_part;
   unsigned* gtv_ticket;
+  // occurrences whose rotation is not a signed permutation (vector fields only): their links stay in the global
+  // frame (slot = boundary node x dofs per node + GLOBAL component), and the traces are turned into the pattern
+  // frame (R^T per node) after the gather and back (R) before the scatter.  gen_R: 9 doubles (row-major R) per
+  // listed occurrence.  slot_nb (NULL when n_gen = 0): the global-frame kernel restricted to every slot,
+  // MAX_KDIM values per slot (R-hat N_b of the slot's occurrence).
+  int n_gen = 0;
+  const int* gen_occ = nullptr;
+  const double* gen_R = nullptr;
+  const double* slot_nb = nullptr;
+  int dpn[MAXP];
 };
 
 // ---- coarse space G = [ ... B(s) N(s) ... ] (Eq. 3) ------------------------------------------------
@@ -71,6 +81,14 @@ void gtg_dense(const Layout& L, const int* nb_ptr, const int* nb_list, int n_pai
 template <typename TO>
 void gather(const Layout& L, const double* V, int k, const PatView<TO>& Y, cudaStream_t s, double alpha = 1.0,
             double beta = 0.0);
+// Turn the traces of the occurrences with a general rotation (Layout.gen_occ) between the global frame and the
+// pattern frame, node by node, in place: to_local: y <- R^T y (after the gather); else y <- R y (before the
+// scatter).  Y as in gather; k columns.
+template <typename T>
+void rotate_traces(const Layout& L, const PatView<T>& Y, int k, bool to_local, cudaStream_t s);
+// to the pattern frame as rotate_traces(to_local) on the tf32 pairs (Yh + Yl) that gather_split wrote for
+// every occurrence, then split again into a tf32 pair in place (hi -> Yh, lo -> Yl)
+void rotate_split(const Layout& L, const PatView<float>& Yh, const PatView<float>& Yl, int k, cudaStream_t s);
 // As gather, FP32 result split into a tf32 pair (hi = tf32(y), lo = y - hi) for the tensor-core product.
 // Yh and Yl share leading dimensions and offsets.
 void gather_split(const Layout& L, const double* V, int k, const PatView<float>& Yh, const PatView<float>& Yl,
@@ -82,6 +100,11 @@ void scatter(const Layout& L, const PatView<TI>& Z, int k, double beta, double* 
 // ---- multivector split (occurrence share of the residual) ------------------------------------------
 // Z[row][g] = sum over the row's occurrences s with group(s) = g: r[row] / (number of occurrences in row)
 void split(const Layout& L, const double* r, int k, double* Z, cudaStream_t s);
+// The permutation multivector of Eq. 8: Z[row][g] = sum_e w[(row k + g) pw + e] r[src[...]] over the pw entries of
+// row `row` of Pi^g (column g = Pi^g r; padding entries have w = 0).  g_only >= 0: only that column, written
+// to Z as a single vector (Z[row]).
+void perm_split(int n, int k, int pw, const int* src, const double* w, const double* r, double* Z, cudaStream_t s,
+                int g_only = -1);
 
 // ---- local products Z_p = S_p^+ Y_p ----------------------------------------------------------------
 // FP64 (DFMA) and FP32 (FFMA) SIMT forms; one launch for every pattern.
@@ -217,10 +240,13 @@ void gram(int n, int a, int b, const TA* A, int lda, const TB* B, int ldb, doubl
 // stored directions a is read from d_a on the device when d_a != NULL (at most a_max), so one captured launch
 // serves every iteration.
 // n_entries = grp_ptr[k]; wr: scratch of 2 n_entries doubles (the weighted split values, FP64 and FP32 hi + lo).
+// grp_src (optional): the entry's value is w r[grp_src[e]] instead of w r[grp_row[e]] (a column of S(r) that
+// takes r from other rows, as the permutation multivector [r, Pi r, ...] does).
 template <typename TH>
 void gram_split(int a_max, const int* d_a, int k, const TH* Qh, int n, int hk, const double* r, const int* grp_ptr,
                 const int* grp_row, const double* grp_w, int n_entries, int max_group_rows, double* C,
-                DBuf<double>& partial, DBuf<double>& wr, cudaStream_t s);
+                DBuf<double>& partial, DBuf<double>& wr, cudaStream_t s,
+                const int* grp_src = nullptr);
 // C[c] = sum_rows Qh[row][c] r[row] for c < a (history times one vector, FP64-class sums; Qh in the block
 // layout of width hk); partial must hold at least a values (it is not grown: captured graphs share it)
 template <typename TH>

@@ -118,6 +118,7 @@ _SIGS = {
     "fetirp_factorize": (C.c_int, [P]),
     "fetirp_inject_barrier_stall": (C.c_int, [P]),
     "fetirp_device_status": (C.c_int, [P]),
+    "fetirp_set_permutation": (C.c_int, [P, C.c_int64, P, P, P, C.c_int32, C.c_int32]),
     "fetirp_apply_split": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_int]),
     "fetirp_apply_split_device": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_int]),
     "fetirp_get_pattern": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), P, P]),
@@ -365,6 +366,22 @@ def fetirp_apply_block_device_noalloc(ctx, k, V_ptr, Q_ptr, precision=FETIRP_PRE
     device allocation in the call; see include/fetirp.h for the size limit and the sharing rules)."""
     _check(ctx, lib().fetirp_apply_block_device_noalloc(ctx, int(k), C.c_void_p(V_ptr), C.c_void_p(Q_ptr),
                                                          int(precision)))
+
+
+def fetirp_set_permutation(ctx, Pi, n_images, shortcut=False):
+    """The permutation multivector [z, Pi z, ...] (Pi: scipy sparse n_lambda x n_lambda, or None for the
+    occurrence split); argument marshalling only."""
+    if Pi is None:
+        _check(ctx, lib().fetirp_set_permutation(ctx, 0, None, None, None, 1, 0))
+        return
+    import scipy.sparse as sp
+    M = sp.csr_matrix(Pi)
+    M.sort_indices()
+    rowptr = np.ascontiguousarray(M.indptr, dtype=np.int64)
+    col = np.ascontiguousarray(M.indices, dtype=np.int32)
+    val = np.ascontiguousarray(M.data, dtype=np.float64)
+    _check(ctx, lib().fetirp_set_permutation(ctx, int(M.shape[0]), _ptr(rowptr), _ptr(col), _ptr(val),
+                                             int(n_images), 1 if shortcut else 0))
 
 
 def fetirp_device_status(ctx):

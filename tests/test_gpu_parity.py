@@ -1,10 +1,10 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element, on seeded inputs
 that span several tiles and ragged tails.  Tolerances: FP64 paths 1e-10 relative (operator) and 1e-8
-(solve, the target of the method).  FP32 local products: 2e-4 relative on the projected operator.  The FP32
-rounding of S^+ and of the traces is ~6e-8 per entry, but S^+ of a floating pattern carries large
-near-rigid components that the projector P removes again, so the relative error of P^T F P V is the FP32
-unit roundoff times that cancellation ratio (measured ~3e-5 for the elastic cases).  Solves reach 1e-8
-after the FP64 refinement in every precision."""
+(solve, the target of the method).  Low-precision local products on the projected operator: FP32 2e-6 and
+tf32x3 1e-5 relative.  The FP32 rounding of S^dag and of the traces is ~6e-8 per entry; the projected
+operator's measured error is 0.8-2.2e-7 (FP32) and 0.25-1.9e-6 (tf32x3: tf32 operand pairs, FP32 sums) over
+these cases, the larger values on the elastic ones, so the bounds keep a margin of about 10x and 5x.  Solves
+reach 1e-8 after the FP64 refinement in every precision."""
 import numpy as np
 import pytest
 
@@ -58,7 +58,7 @@ def test_pattern_operators(name):
 
 
 @pytest.mark.parametrize("name", list(CASES) + ["c2"])
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-4)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-6), ("tf32x3", 1e-5)])
 def test_apply_block_matches_oracle(name, prec, tol):
     prob = config("c2") if name == "c2" else CASES[name]()
     orc = FetiOracle(prob)
