@@ -469,9 +469,9 @@ void factor_stage_b(PatternData& P, cudaStream_t s) {
   k_set_diag<<<ceil_div(nbp, 128), 128, 0, s>>>(P.XS.p, nbp, 0, nbp, 1.0);
   FETIRP_LAUNCH_CHECK();
   tile_inverses(P.LS.p, nbp, P.zpS.p, P.DinvS.p, s);
-  tri_solve(P.LS.p, nbp, P.planS, P.zpS.p, P.XS.p, nbp, nbp, false, s, P.DinvS.p);   // X = L_S^{-1}
+  tri_solve(P.LS.p, nbp, P.planS, P.zpS.p, P.XS.p, nbp, nbp, false, s, P.DinvS.p, true);   // X = L_S^{-1}
   P.S64.ensure((size_t)P.n_b * P.n_b);
-  gemm_f64(P.n_b, P.n_b, nbp, 1.0, P.XS.p, nbp, 1, P.XS.p, 1, nbp, 0.0, P.S64.p, P.n_b, 1, s);
+  lauum(P.XS.p, nbp, nbp, P.n_b, P.S64.p, P.n_b, s);   // S^+ = X^T X
   // Moore-Penrose inverse S^dag = Pi S^+ Pi, Pi = I - N_b (N_b^T N_b)^{-1} N_b^T, for the low-precision local
   // products: S^+ from zero pivots carries large components along the kernel (a body held at a few dofs)
   // that the projector P removes again, so rounding them would survive that cancellation; S^dag has none.
@@ -563,8 +563,8 @@ void spd_inverse(fetirp_ctx ctx, const double* A_rowmajor, int n, int npad, Tile
     if (h[i]) throw Error(FETIRP_ESINGULAR, "coarse matrix G^T G is singular (an occurrence is not constrained)");
   k_set_diag<<<ceil_div(npad, 128), 128, 0, s>>>(X.p, npad, 0, npad, 1.0);
   FETIRP_LAUNCH_CHECK();
-  tri_solve(A.p, npad, plan, zp.p, X.p, npad, npad, false, s);
-  gemm_f64(n, n, npad, 1.0, X.p, npad, 1, X.p, 1, npad, 0.0, out_rowmajor, n, 1, s);
+  tri_solve(A.p, npad, plan, zp.p, X.p, npad, npad, false, s, nullptr, true);   // X = L^{-1}
+  lauum(X.p, npad, npad, n, out_rowmajor, n, s);                               // A^{-1} = X^T X
   FETIRP_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -34,8 +34,12 @@ void chol_tiles(double* A, int npad, const TilePlan& plan, const double* diag0, 
 // X <- L^{-1} X (trans = false) or X <- L^{-T} X (trans = true), X column-major npad x nrhs (ld = ldx),
 // zero-pivot rows of the result set to 0.  Right-looking over tile columns, skipping zero tiles.
 // Dinv (optional): inverted diagonal tiles from tile_inverses(); each diagonal step is then a parallel product.
+// identity_rhs (forward solves only): X holds the identity on entry, so in step J only the first 64 (J + 1)
+// columns can be nonzero (L^{-1} is lower triangular) and the others are skipped: a third of the work.
 void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, double* X, int ldx, int nrhs,
-               bool trans, cudaStream_t s, const double* Dinv = nullptr);
+               bool trans, cudaStream_t s, const double* Dinv = nullptr, bool identity_rhs = false);
+// C (n_out x n_out, ld ldc) = X^T X for a lower-triangular X (column-major, ld, krows rows summed).
+void lauum(const double* X, int ld, int krows, int n_out, double* C, int ldc, cudaStream_t s);
 // Dinv (npad/64 tiles of 64 x 64, column-major) = inverses of the diagonal tiles of L (zero pivots -> 0).
 void tile_inverses(const double* L, int npad, const int* zp, double* Dinv, cudaStream_t s);
 

@@ -441,7 +441,66 @@ __global__ void __launch_bounds__(256) k_gemm_f64(int M, int N, int K, double al
   }
 }
 
+// C = X^T X for a lower-triangular X (column-major, ld), the product S^+ = L_S^{-T} L_S^{-1} of the pattern
+// set-up.  One CTA per lower output tile (I >= J) of 64 x 64, 4 x 4 outputs per thread: C_IJ sums
+// X(k, i) X(k, j) over rows k >= 64 I only (X(k, i) = 0 for k < i), and the tile is written to C and, mirrored,
+// to C_JI.  A third of the flops of the dense product (triangular operand, symmetric result).
+__global__ void __launch_bounds__(256) k_lauum(const double* __restrict__ X, int ld, int krows, int n_out,
+                                               double* __restrict__ C, int ldc) {
+  __shared__ double sa[16][TILE + 1];   // [kk][i]
+  __shared__ double sb[16][TILE + 1];   // [kk][j]
+  // lower tile index -> (I, J), I >= J: blockIdx.x = I (I + 1) / 2 + J
+  const int t = blockIdx.x;
+  int I = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((I + 1) * (I + 2) / 2 <= t) ++I;
+  while (I * (I + 1) / 2 > t) --I;
+  const int J = t - I * (I + 1) / 2;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const double* XI = X + (size_t)I * TILE * ld;
+  const double* XJ = X + (size_t)J * TILE * ld;
+  double acc[4][4] = {};
+  for (int k0 = I * TILE; k0 < krows; k0 += 16) {
+    for (int idx = tid; idx < 16 * TILE; idx += 256) {
+      const int kk = idx % 16, c = idx / 16;
+      const int k = k0 + kk;
+      sa[kk][c] = k < krows ? XI[(size_t)c * ld + k] : 0.0;
+      sb[kk][c] = k < krows ? XJ[(size_t)c * ld + k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { av[q] = sa[kk][ty * 4 + q]; bv[q] = sb[kk][tx * 4 + q]; }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(av[p], bv[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int i = I * TILE + ty * 4 + p;
+    if (i >= n_out) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = J * TILE + tx * 4 + q;
+      if (j >= n_out) continue;
+      C[(size_t)i * ldc + j] = acc[p][q];
+      if (I != J) C[(size_t)j * ldc + i] = acc[p][q];
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------------------ host
+void lauum(const double* X, int ld, int krows, int n_out, double* C, int ldc, cudaStream_t s) {
+  const int nt = ceil_div(n_out, TILE);
+  if (nt <= 0) return;
+  k_lauum<<<nt * (nt + 1) / 2, 256, 0, s>>>(X, ld, krows, n_out, C, ldc);
+  FETIRP_LAUNCH_CHECK();
+}
+
 void copy_diag(const double* A, int npad, double* diag, cudaStream_t s) {
   k_copy_diag<<<ceil_div(npad, 256), 256, 0, s>>>(A, npad, diag);
   FETIRP_LAUNCH_CHECK();
@@ -476,10 +535,11 @@ void tile_inverses(const double* L, int npad, const int* zp, double* Dinv, cudaS
   FETIRP_LAUNCH_CHECK();
 }
 
-void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, double* X, int ldx, int nrhs,
-               bool trans, cudaStream_t s, const double* Dinv) {
-  if (nrhs <= 0) return;
-  const int chunks = ceil_div(nrhs, TILE);
+void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, double* X, int ldx, int nrhs_all,
+               bool trans, cudaStream_t s, const double* Dinv, bool identity_rhs) {
+  if (nrhs_all <= 0) return;
+  int nrhs = nrhs_all;
+  int chunks = ceil_div(nrhs, TILE);
   auto diag = [&](int J, int tr) {
     if (Dinv && ceil_div(nrhs, 16) < 152) k_tri_diag_inv<4><<<ceil_div(nrhs, 4), 256, 0, s>>>(Dinv, J, X, ldx, nrhs, tr);
     else if (Dinv) k_tri_diag_inv<16><<<ceil_div(nrhs, 16), 256, 0, s>>>(Dinv, J, X, ldx, nrhs, tr);
@@ -487,6 +547,10 @@ void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, d
   };
   if (!trans) {
     for (int J = 0; J < plan.nt; ++J) {
+      if (identity_rhs) {   // columns c >= 64 (J + 1) of L^{-1} are still zero in block rows <= J
+        nrhs = std::min(nrhs_all, (J + 1) * TILE);
+        chunks = ceil_div(nrhs, TILE);
+      }
       diag(J, 0);
       FETIRP_LAUNCH_CHECK();
       int nr = plan.col_off[J + 1] - plan.col_off[J];
