@@ -189,6 +189,10 @@ struct fetirp_ctx_s {
   // row's slots in the local product buffers (for the current k)
   DBuf<int> d_row_grp, d_row_zld, d_rowg_gofs, d_rowg_kd;
   DBuf<double> d_row_wt, d_rowg_coef;
+  // double-single projection of the inner solves: coefficients of G and (G^T G)^{-1} as FP32 pairs, and the
+  // split coarse vectors
+  DBuf<float> ds_coef, ds_ginv, ds_xa;
+  bool ds_project = false;              // set while the inner iterations of a mixed form are enqueued
   DBuf<int> d_slot_code;        // per link: 2 row + e (its entry in the per-row tables)
   int n_grp_entries = 0;        // entries of the per-group row lists
   double n_gcoef = 0;           // coefficients of G by row (sum over rows and their slots of the mode count)
@@ -841,6 +845,18 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
     ctx->d_rowg_gofs.upload(rowg_gofs, s);
     ctx->d_rowg_kd.upload(rowg_kd, s);
     ctx->d_rowg_coef.upload(rowg_coef, s);
+    {
+      std::vector<float> ch(rowg_coef.size()), cl(rowg_coef.size());
+      for (size_t i = 0; i < rowg_coef.size(); ++i) {
+        ch[i] = (float)rowg_coef[i];
+        cl[i] = (float)(rowg_coef[i] - (double)ch[i]);
+      }
+      ctx->ds_coef.ensure(2 * rowg_coef.size());
+      FETIRP_CUDA(cudaMemcpyAsync(ctx->ds_coef.p, ch.data(), sizeof(float) * ch.size(), cudaMemcpyHostToDevice, s));
+      FETIRP_CUDA(cudaMemcpyAsync(ctx->ds_coef.p + ch.size(), cl.data(), sizeof(float) * cl.size(),
+                                  cudaMemcpyHostToDevice, s));
+      FETIRP_CUDA(cudaStreamSynchronize(s));   // the host vectors go out of scope
+    }
   }
   ctx->d_pair_s.upload(pair_s, s);
   ctx->d_pair_t.upload(pair_t, s);
@@ -870,6 +886,8 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   }
   L.row_grp = ctx->d_row_grp.p; L.row_wt = ctx->d_row_wt.p;
   L.rowg_gofs = ctx->d_rowg_gofs.p; L.rowg_kd = ctx->d_rowg_kd.p; L.rowg_coef = ctx->d_rowg_coef.p;
+  L.rowg_coef_hi = ctx->ds_coef.p;
+  L.rowg_coef_lo = ctx->ds_coef.p + 12 * (size_t)nl;
   L.slot_code = ctx->d_slot_code.p;
   for (int p = 0; p < n_pat; ++p) L.dpn[p] = ctx->pats[p]->dpn;
   L.n_gen = ctx->n_gen;
@@ -920,6 +938,10 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
     ctx->planG = dense_plan(ctx->n_Gpad / TILE);
     ctx->planG.upload(s);
     spd_inverse(ctx, ctx->GtG.p, ctx->n_G, ctx->n_Gpad, ctx->planG, ctx->zpG, ctx->Ginv.p);
+    const long long ng2 = (long long)ctx->n_G * ctx->n_G;
+    ctx->ds_ginv.ensure(2 * (size_t)ng2);
+    split_pairs(ng2, ctx->Ginv.p, ctx->ds_ginv.p, ctx->ds_ginv.p + ng2, s);
+    ctx->ds_xa.ensure(4 * (size_t)ctx->n_G * 64);
     // e_s = N^T f_s
     for (int p = 0; p < n_pat; ++p) {
       PatternData& P = *ctx->pats[p];
@@ -981,6 +1003,20 @@ void project(fetirp_ctx ctx, double* V, int k) {
   PhaseScope ph(ctx, FETIRP_PHASE_PROJECT, 2.0 * nG * nG * k + 4.0 * ctx->n_gcoef * k, 16.0 * nl * k + 8.0 * nG * nG);
   ctx->Xc.ensure((size_t)ctx->n_G * k);
   ctx->Ac.ensure((size_t)ctx->n_G * k);
+  if (ctx->ds_project) {   // inner solves of the mixed forms: double-single sums on the FP32 pipe (~2^-46)
+    const long long ngk = (long long)ctx->n_G * k;
+    float* xh = ctx->ds_xa.p;
+    float* xl = xh + (size_t)ctx->n_G * 64;
+    float* ah = xl + (size_t)ctx->n_G * 64;
+    float* al = ah + (size_t)ctx->n_G * 64;
+    const long long ng2 = (long long)ctx->n_G * ctx->n_G;
+    gt_v_ds(ctx->L, V, k, ctx->Xc.p, s);
+    split_pairs(ngk, ctx->Xc.p, xh, xl, s);
+    small_gemm_ds(ctx->n_G, k, ctx->ds_ginv.p, ctx->ds_ginv.p + ng2, xh, xl, ctx->Ac.p, s);
+    split_pairs(ngk, ctx->Ac.p, ah, al, s);
+    g_apply_ds(ctx->L, ah, al, k, -1.0, 1.0, V, s);
+    return;
+  }
   gt_v(ctx->L, V, k, ctx->Xc.p, s);
   small_gemm(ctx->n_G, k, ctx->Ginv.p, ctx->Xc.p, ctx->Ac.p, s, ctx->sg_part.p);
   g_apply(ctx->L, ctx->Ac.p, k, -1.0, 1.0, V, s);
@@ -1189,6 +1225,12 @@ void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
   int eta_off = 0;
   cudaStream_t s = ctx->stream;
   const int nl = ctx->L.n_lambda, k = ctx->k;
+  struct DsScope {   // double-single projections while the inner iteration of a mixed form is enqueued
+    fetirp_ctx c;
+    bool saved;
+    DsScope(fetirp_ctx c_, bool on) : c(c_), saved(c_->ds_project) { c->ds_project = on; }
+    ~DsScope() { c->ds_project = saved; }
+  } ds_scope(ctx, prec != FETIRP_PREC_FP64);
   const long long cap = ctx->hist_cap;
   int* d_cols = ctx->d_state.p;
   const bool permuted = ctx->perm.on;
@@ -1228,7 +1270,7 @@ void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
   }
   {
     PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 0.0, 0.0);
-    eta_off = eta_partials(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta_part, s);
+    eta_off = eta_partials(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta_part, s, prec != FETIRP_PREC_FP64);
   }
   {
     PhaseScope ph(ctx, FETIRP_PHASE_NORMALISE, 0.0, 0.0);

@@ -119,6 +119,120 @@ __global__ void k_g_apply(Layout L, const double* __restrict__ A, int k, double 
   *o = (beta == 0.0 ? 0.0 : beta * *o) + alpha * acc;
 }
 
+// ---- double-single forms of G^T V and G A (the projections inside the inner solves of the mixed forms) -------
+// The same sums on the FP32 pipe: every FP64 operand is an unevaluated pair hi + lo of FP32 values (48 bits; the
+// coefficients of G and the coarse vectors are split once per call or per structure, V when it is loaded), each
+// product is Dekker's exact product of the high parts plus the cross terms, and each running sum a (hi, lo)
+// pair updated by Knuth's TwoSum; ~2^-46 relative, converted to FP64 at the end (Dekker 1971; Knuth, TAOCP
+// vol. 2).  On this GPU the FP32 pipe issues ~75 times the FP64 one.
+__device__ __forceinline__ void dsm(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  const float ph = __fmul_rn(ah, bh);
+  float pl = fmaf(ah, bh, -ph);
+  pl = fmaf(ah, bl, pl);
+  pl = fmaf(al, bh, pl);
+  const float t = __fadd_rn(sh, ph), bb = __fsub_rn(t, sh);
+  const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(ph, bb));
+  sl = __fadd_rn(sl, __fadd_rn(e, pl));
+  sh = t;
+}
+__device__ __forceinline__ void dsplit(double v, float& h, float& l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+
+__global__ void k_split_pairs(long long n, const double* __restrict__ x, float* __restrict__ h,
+                              float* __restrict__ l) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dsplit(x[i], h[i], l[i]);
+}
+
+template <bool WIDE>
+__global__ void __launch_bounds__(GTV_THREADS, WIDE ? 2 : 3) k_gt_v_ds(Layout L, const double* __restrict__ V, int k,
+                                                            double* __restrict__ X, int chunk) {
+  __shared__ double red[GTV_THREADS / 32][MAX_KDIM][64];
+  __shared__ int s_last;
+  const int s = blockIdx.x, c = blockIdx.y, nch = gridDim.y;
+  const int kd = L.kdim[L.occ_pat[s]];
+  const int l0 = L.slot_ptr[L.occ_obase[s]], nl = L.slot_ptr[L.occ_obase[s + 1]] - l0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool c0 = lane < k, c1 = WIDE && lane + 32 < k;
+  const int i_end = min(nl, (c + 1) * chunk);
+  float h0[MAX_KDIM] = {}, e0[MAX_KDIM] = {}, h1[MAX_KDIM] = {}, e1[MAX_KDIM] = {};
+  if (kd > 0) {
+    for (int i = c * chunk + w; i < i_end; i += 8) {
+      const int code = L.slot_code[l0 + i];
+      const double* vr = V + (size_t)(code >> 1) * k + lane;
+      float vh0, vl0, vh1 = 0.f, vl1 = 0.f;
+      dsplit(c0 ? vr[0] : 0.0, vh0, vl0);
+      if (WIDE) dsplit(c1 ? vr[32] : 0.0, vh1, vl1);
+      const float* ch = L.rowg_coef_hi + (size_t)code * MAX_KDIM;
+      const float* cl = L.rowg_coef_lo + (size_t)code * MAX_KDIM;
+#pragma unroll
+      for (int m = 0; m < MAX_KDIM; ++m)
+        if (m < kd) {
+          const float a = ch[m], b = cl[m];
+          dsm(a, b, vh0, vl0, h0[m], e0[m]);
+          if (WIDE) dsm(a, b, vh1, vl1, h1[m], e1[m]);
+        }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < MAX_KDIM; ++m) {
+    red[w][m][lane] = (double)h0[m] + (double)e0[m];
+    red[w][m][lane + 32] = (double)h1[m] + (double)e1[m];
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  double* part = L.gtv_part + (size_t)s * nch * MAX_KDIM * 64;
+  for (int i = t; i < kd * k; i += blockDim.x) {
+    const int m = i / k, g = i % k;
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < GTV_THREADS / 32; ++q) v += red[q][m][g];
+    if (nch == 1)
+      X[(size_t)(L.occ_gofs[s] + m) * k + g] = v;
+    else
+      part[((size_t)c * MAX_KDIM + m) * 64 + g] = v;
+  }
+  if (nch == 1) return;
+  __threadfence();
+  __syncthreads();
+  if (t == 0) s_last = atomicAdd(&L.gtv_ticket[s], 1u) == (unsigned)(nch - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int i = t; i < kd * k; i += blockDim.x) {
+    const int m = i / k, g = i % k;
+    double v = 0.0;
+    for (int q = 0; q < nch; ++q) v += __ldcg(part + ((size_t)q * MAX_KDIM + m) * 64 + g);
+    X[(size_t)(L.occ_gofs[s] + m) * k + g] = v;
+  }
+  if (t == 0) L.gtv_ticket[s] = 0u;
+}
+
+// out = beta out + alpha G A with A given as FP32 pairs (Ah + Al)
+__global__ void k_g_apply_ds(Layout L, const float* __restrict__ Ah, const float* __restrict__ Al, int k,
+                             double alpha, double beta, double* __restrict__ out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)L.n_lambda * k) return;
+  const int row = (int)(idx / k), g = (int)(idx % k);
+  float h = 0.f, l = 0.f;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int g0 = L.rowg_gofs[2 * row + e];
+    if (g0 < 0) continue;
+    const int kd = L.rowg_kd[2 * row + e];
+    const float* ch = L.rowg_coef_hi + (size_t)(2 * row + e) * MAX_KDIM;
+    const float* cl = L.rowg_coef_lo + (size_t)(2 * row + e) * MAX_KDIM;
+    const size_t a0 = (size_t)g0 * k + g;
+#pragma unroll
+    for (int m = 0; m < MAX_KDIM; ++m)
+      if (m < kd) dsm(ch[m], cl[m], Ah[a0 + (size_t)m * k], Al[a0 + (size_t)m * k], h, l);
+  }
+  double* o = out + idx;
+  *o = (beta == 0.0 ? 0.0 : beta * *o) + alpha * ((double)h + (double)l);
+}
+
 // Block (s, t) of G^T G for one neighbour pair: sum over rows linking s and t.  Threads split the boundary
 // dofs of s; per-thread partials are reduced in a fixed order.
 __global__ void __launch_bounds__(128) k_gtg(Layout L, const int* __restrict__ pair_s, const int* __restrict__ pair_t,
@@ -424,6 +538,31 @@ void gt_v(const Layout& L, const double* V, int k, double* X, cudaStream_t s) {
   FETIRP_LAUNCH_CHECK();
 }
 
+
+void gt_v_ds(const Layout& L, const double* V, int k, double* X, cudaStream_t s) {
+  if (L.n_occ == 0) return;
+  if (k > 64) throw Error(1, "k > 64");
+  if (!L.rowg_coef_hi) throw Error(1, "double-single coefficients of G not built");
+  if (k > 32)
+    k_gt_v_ds<true><<<dim3(L.n_occ, L.gtv_chunks), GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
+  else
+    k_gt_v_ds<false><<<dim3(L.n_occ, L.gtv_chunks), GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
+  FETIRP_LAUNCH_CHECK();
+}
+
+void split_pairs(long long n, const double* x, float* h, float* l, cudaStream_t s) {
+  if (n <= 0) return;
+  k_split_pairs<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, x, h, l);
+  FETIRP_LAUNCH_CHECK();
+}
+
+void g_apply_ds(const Layout& L, const float* Ah, const float* Al, int k, double alpha, double beta, double* out,
+                cudaStream_t s) {
+  long long n = (long long)L.n_lambda * k;
+  if (n == 0) return;
+  k_g_apply_ds<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, Ah, Al, k, alpha, beta, out);
+  FETIRP_LAUNCH_CHECK();
+}
 
 void g_apply(const Layout& L, const double* A, int k, double alpha, double beta, double* out, cudaStream_t s) {
   long long n = (long long)L.n_lambda * k;

@@ -94,6 +94,69 @@ __global__ void __launch_bounds__(256) k_eta_partial(int n, int k, const double*
   }
 }
 
+// The same [eta | wr] partials in double-single arithmetic on the FP32 pipe (the inner solves of the mixed forms;
+// this GPU's FP32 pipe issues ~75 times the FP64 one).  Every FP64 element is split once, when it is staged, into
+// an unevaluated pair hi + lo of FP32 values (|lo| <= 2^-24 |hi|, 48 bits in all); each product is formed from
+// the pairs with Dekker's exact product of the high parts by an FMA plus the two cross terms, and added to a
+// (hi, lo) running sum by Knuth's TwoSum (Dekker 1971; Knuth, TAOCP vol. 2).  Relative accuracy of a column sum
+// ~2^-46, converted to FP64 at the end.  The _rn intrinsics keep the compiler from contracting the error-free
+// transformations into FMAs.
+__device__ __forceinline__ void ds_madd(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  const float ph = __fmul_rn(ah, bh);
+  float pl = fmaf(ah, bh, -ph);
+  pl = fmaf(ah, bl, pl);
+  pl = fmaf(al, bh, pl);
+  const float t = __fadd_rn(sh, ph), bb = __fsub_rn(t, sh);
+  const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(ph, bb));
+  sl = __fadd_rn(sl, __fadd_rn(e, pl));
+  sh = t;
+}
+__device__ __forceinline__ void ds_split(double v, float& h, float& l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+__global__ void __launch_bounds__(256) k_eta_partial_ds(int n, int k, const double* __restrict__ W,
+                                                        const double* __restrict__ Q, const double* __restrict__ r,
+                                                        int rows_per_chunk, double* __restrict__ partial) {
+  __shared__ float swh[16][64], swl[16][64];
+  __shared__ float sqh[16][65], sql[16][65];
+  const int r0 = blockIdx.x * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+  const int nout = k * (k + 1);
+  for (int base = 0; base < nout; base += 5 * 256) {
+    float ah[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, al[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int rr = r0; rr < r1; rr += 16) {
+      const int nrow = min(16, r1 - rr);
+      for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
+        const int q = idx / 64, c = idx % 64;
+        const bool ok = q < nrow && c < k;
+        ds_split(ok ? W[(size_t)(rr + q) * k + c] : 0.0, swh[q][c], swl[q][c]);
+        ds_split(ok ? Q[(size_t)(rr + q) * k + c] : 0.0, sqh[q][c], sql[q][c]);
+      }
+      if (threadIdx.x < 16) ds_split(threadIdx.x < nrow ? r[rr + threadIdx.x] : 0.0, sqh[threadIdx.x][64],
+                                     sql[threadIdx.x][64]);
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const int o = base + q * 256 + threadIdx.x;
+        if (o < nout) {
+          const int i = o / (k + 1), j = o % (k + 1);
+          const int jj = (j == k) ? 64 : j;
+          float h = ah[q], l = al[q];
+          for (int t = 0; t < nrow; ++t) ds_madd(swh[t][i], swl[t][i], sqh[t][jj], sql[t][jj], h, l);
+          ah[q] = h;
+          al[q] = l;
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const int o = base + q * 256 + threadIdx.x;
+      if (o < nout) partial[(size_t)blockIdx.x * nout + o] = (double)ah[q] + (double)al[q];
+    }
+  }
+}
+
 __global__ void k_reduce_chunks(int count, int chunks, const double* __restrict__ partial, double* __restrict__ C) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
@@ -460,12 +523,13 @@ __global__ void k_eta_group_sums(int nout, int chunks, const double* __restrict_
 }
 
 int eta_partials(int n, int k, const double* W, const double* Q, const double* r, DBuf<double>& partial,
-                 cudaStream_t s) {
+                 cudaStream_t s, bool ds) {
   const int chunks = eta_chunks(n);
   const int rows = ceil_div(n, chunks);
   const int nout = k * (k + 1);
   partial.ensure((size_t)(chunks + ETA_GROUPS) * nout);
-  k_eta_partial<<<chunks, 256, 0, s>>>(n, k, W, Q, r, rows, partial.p);
+  if (ds) k_eta_partial_ds<<<chunks, 256, 0, s>>>(n, k, W, Q, r, rows, partial.p);
+  else k_eta_partial<<<chunks, 256, 0, s>>>(n, k, W, Q, r, rows, partial.p);
   FETIRP_LAUNCH_CHECK();
   if (chunks <= ETA_GROUPS) return 0;
   k_eta_group_sums<<<dim3(ceil_div(nout, 256), ETA_GROUPS), 256, 0, s>>>(nout, chunks, partial.p,
@@ -509,6 +573,48 @@ __global__ void __launch_bounds__(128) k_small_gemm(int m, int k, const double* 
     for (int off = kp; off < 32; off <<= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     if (sl == 0 && g < k) C[(size_t)row * k + g] = acc;
   }
+}
+
+// C = A B in double-single arithmetic (A: m x m, B: m x k, both as FP32 pairs), one warp per row of C with the
+// same lane layout as k_small_gemm (no inner split: each lane's column sum is a (hi, lo) pair, and the slices
+// of a column are added in FP64 by the shuffle tree)
+__global__ void __launch_bounds__(128) k_small_gemm_ds(int m, int k, const float* __restrict__ Ah,
+                                                       const float* __restrict__ Al, const float* __restrict__ Bh,
+                                                       const float* __restrict__ Bl, double* __restrict__ C) {
+  const int row = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  const float* ah = Ah + (size_t)row * m;
+  const float* al = Al + (size_t)row * m;
+  for (int g0 = 0; g0 < k; g0 += 32) {
+    const int kk = min(32, k - g0);
+    int kp = 1;
+    while (kp < kk) kp <<= 1;
+    const int slices = 32 / kp;
+    const int g = g0 + (lane % kp), sl = lane / kp;
+    double acc = 0.0;
+    if (g < k) {
+      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+      int j = sl;
+      for (; j + slices < m; j += 2 * slices) {
+        ds_madd(ah[j], al[j], Bh[(size_t)j * k + g], Bl[(size_t)j * k + g], h0, l0);
+        ds_madd(ah[j + slices], al[j + slices], Bh[(size_t)(j + slices) * k + g], Bl[(size_t)(j + slices) * k + g],
+                h1, l1);
+      }
+      for (; j < m; j += slices) ds_madd(ah[j], al[j], Bh[(size_t)j * k + g], Bl[(size_t)j * k + g], h0, l0);
+      acc = ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
+    }
+    for (int off = kp; off < 32; off <<= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (sl == 0 && g < k) C[(size_t)row * k + g] = acc;
+  }
+}
+
+void small_gemm_ds(int m, int k, const float* Ah, const float* Al, const float* Bh, const float* Bl, double* C,
+                   cudaStream_t s) {
+  if (m <= 0 || k <= 0) return;
+  if (k > 64) throw Error(1, "k > 64");
+  k_small_gemm_ds<<<ceil_div(m, 4), 128, 0, s>>>(m, k, Ah, Al, Bh, Bl, C);
+  FETIRP_LAUNCH_CHECK();
 }
 
 // C[i] = sum of the `parts` slices P[p][i] in slice order

@@ -60,6 +60,9 @@ struct Layout {
   // frame (R^T per node) after the gather and back (R) before the scatter.  gen_R: 9 doubles (row-major R) per
   // listed occurrence.  slot_nb (NULL when n_gen = 0): the global-frame kernel restricted to every slot,
   // MAX_KDIM values per slot (R-hat N_b of the slot's occurrence).
+  // the coefficients rowg_coef as FP32 pairs (hi + lo) for the double-single projections (NULL: not built)
+  const float* rowg_coef_hi = nullptr;
+  const float* rowg_coef_lo = nullptr;
   int n_gen = 0;
   const int* gen_occ = nullptr;
   const double* gen_R = nullptr;
@@ -72,6 +75,16 @@ struct Layout {
 void gt_v(const Layout& L, const double* V, int k, double* X, cudaStream_t s);
 // out[row][g] = beta * out[row][g] + alpha * (G A)[row][g]
 void g_apply(const Layout& L, const double* A, int k, double alpha, double beta, double* out, cudaStream_t s);
+// Double-single forms (FP32 pairs, ~2^-46 relative; the inner solves of the mixed forms): X = G^T V, and
+// out = beta out + alpha G A with A given as pairs Ah + Al (split_pairs); need Layout.rowg_coef_hi/lo.
+void gt_v_ds(const Layout& L, const double* V, int k, double* X, cudaStream_t s);
+void g_apply_ds(const Layout& L, const float* Ah, const float* Al, int k, double alpha, double beta, double* out,
+                cudaStream_t s);
+// h[i] + l[i] = x[i] to ~2^-48 (h = fl32(x), l = fl32(x - h))
+void split_pairs(long long n, const double* x, float* h, float* l, cudaStream_t s);
+// C (m x k) = A B with A given as FP32 pairs (m x m) and B as FP32 pairs (m x k), double-single sums, FP64 out
+void small_gemm_ds(int m, int k, const float* Ah, const float* Al, const float* Bh, const float* Bl, double* C,
+                   cudaStream_t s);
 // dense G^T G (n_G x n_G, row-major), nb_ptr/nb_list: neighbour occurrences of every occurrence
 void gtg_dense(const Layout& L, const int* nb_ptr, const int* nb_list, int n_pairs, const int* pair_s,
                const int* pair_t, double* GtG, cudaStream_t s);
@@ -272,8 +285,10 @@ void advance(int* cols, int k, long long cap, const int* n_kept, int* dropped, i
 // themselves, eta_chunks(n) of them; else the ETA_GROUPS group sums).
 constexpr int ETA_GROUPS = 16;
 int eta_chunks(int n);
+// ds: the products and sums in double-single FP32 arithmetic (~2^-46 relative; the inner solves of the mixed
+// forms), else FP64.
 int eta_partials(int n, int k, const double* W, const double* Q, const double* r, DBuf<double>& partial,
-                 cudaStream_t s);
+                 cudaStream_t s, bool ds = false);
 // C (m x k) = A (m x m) B (m x k), row-major, FP64, one warp per row (small coarse products).
 // part (optional, small_gemm_parts(m) * m * k doubles): the inner dimension is split over that many CTA rows
 // and the slices added in order (deterministic)

@@ -142,8 +142,11 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcPa
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int p = 0;
   while (p + 1 < P.n_pat && (int)blockIdx.x >= P.tile_off[p + 1]) ++p;
+  // right-hand-side tiles inner: the CTAs of a wave share few 128-row tiles of S (read from DRAM once, then
+  // served from L2 to the other CTAs of the row), and Y (a few tens of MB per pattern) stays in L2
   const int t = blockIdx.x - P.tile_off[p];
-  const int m0 = (t % P.tiles_m[p]) * BM, n0 = (t / P.tiles_m[p]) * BN;
+  const int tiles_n = (P.n_rhs[p] + BN - 1) / BN;
+  const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
   const int nk = (P.n_b[p] + BK - 1) / BK;
 
   if (threadIdx.x == 0) {
