@@ -235,6 +235,39 @@ fetirp_status fetirp_set_groups(fetirp_ctx ctx, int32_t k, const int32_t* group_
 fetirp_status fetirp_set_permutation(fetirp_ctx ctx, int64_t n_lambda, const int64_t* rowptr, const int32_t* col,
                                      const double* val, int32_t n_images, int32_t shortcut);
 
+/* Preconditioners of Eqs. 4-5 and their scaling (fetirp_set_preconditioner). */
+enum {
+  FETIRP_PRECOND_NONE = 0,        /* identity (the default): P = I - G (G^T G)^{-1} G^T */
+  FETIRP_PRECOND_DIRICHLET = 1,   /* X(s) = S(s) = K_bb - K_bi K_ii^{-1} K_ib, the primal Schur complement */
+  FETIRP_PRECOND_LUMPED = 2,      /* X(s) = K_bb, the boundary block of the stiffness */
+  FETIRP_PRECOND_SUPERLUMPED = 3  /* X(s) = diag(K_bb) */
+};
+enum {
+  FETIRP_SCALING_MULTIPLICITY = 0, /* Delta(s) = 1 / (occurrences sharing the row) */
+  FETIRP_SCALING_STIFFNESS = 1     /* on a gluing row between s and t at dof i: Delta(s) = K(t)_ii / (K(s)_ii +
+                                      K(t)_ii), the diagonals in the global frame; 1 on a Dirichlet row */
+};
+
+/*
+ * The preconditioner of the solves of this context (Eqs. 4-5): tilde-F^{-1} = sum_s Delta(s) B(s) X(s) B(s)^T
+ * Delta(s), with sum_s Delta(s) = I on the multiplier rows, and the projector of Eqs. 6-7 in its metric,
+ * Q = I - tilde-F^{-1} G (G^T tilde-F^{-1} G)^{-1} G^T, lambda_0 = tilde-F^{-1} G (G^T tilde-F^{-1} G)^{-1} e.
+ * The iteration is Table 1 (right column) with the preconditioner: the block is the split (by Delta, or the
+ * permutation images of fetirp_set_permutation) of z = Q tilde-F^{-1} r, r = Q^T (d - F lambda), and the stopping
+ * rule is ||r_j|| / ||r_0|| <= tol on that r.  X(s) is the pattern's operator in the pattern frame, formed at the
+ * next fetirp_prepare / fetirp_solve in FP64 (Dirichlet: n_b right-hand sides through the interior block of the
+ * pattern factor); tilde-F^{-1} and Q are applied in FP64 in every precision, and the direction history is kept
+ * in FP64.  With the mixed forms the inner operator carries the ~1e-7 rounding of the low-precision local
+ * products; on strongly heterogeneous structures (the 1 / 1000 checkerboard) that rounding of the soft
+ * occurrences exceeds what the preconditioner resolves on the stiff ones and the solve does not converge
+ * (FETIRP_ENOCONV): use FETIRP_PREC_FP64 there.  A preconditioned solve uses the per-phase iteration (CUDA graphs)
+ * and the full F-apply of the block (no periodic shortcut).  The setting stays until changed.
+ * fetirp_apply_block and fetirp_apply_split keep the unpreconditioned projector P.
+ * Errors: FETIRP_EINVAL for an unknown kind or scaling; the next prepare returns FETIRP_EINVAL when stiffness
+ * scaling meets a non-positive diagonal.
+ */
+fetirp_status fetirp_set_preconditioner(fetirp_ctx ctx, int32_t kind, int32_t scaling);
+
 /*
  * Solve for lambda and the displacements (Table 1 and the recovery u(s) = K^+ (f - B^T lambda) + N alpha).
  *  n_lambda: number of multiplier rows (max lambda_row + 1 over all occurrences).

@@ -219,6 +219,16 @@ struct fetirp_ctx_s {
   DBuf<double> GtG, Ginv, e, d, lambda0, c;
   TilePlan planG;
   DBuf<int> zpG;
+  // preconditioner of Eqs. 4-5 (FETIRP_PRECOND_*): the scaling of every link / row entry, the local operators
+  // X_p of the patterns (pattern frame), the coarse matrix G^T tilde-F^{-1} G of the weighted projector and its
+  // inverse, scratch blocks
+  struct Precond {
+    int kind = 0, scaling = 1;
+    DBuf<double> link_w, row_w, row_d, grp_wd, GtMG, GtMGinv, T1, T2;
+    DBuf<double> X[MAXP];
+    TilePlan plan;
+    DBuf<int> zp;
+  } pc;
 
   // work
   DBuf<double> lam, r, t1, W, Q, Zr, Whist, Qhist, C, eta, wr, T, alpha, rr_part, Xc, Ac, gram_part, V1, V2;
@@ -584,6 +594,7 @@ TilePlan dense_plan(int nt) {
 // ----------------------------------------------------------------------------------------- structure
 void invalidate(fetirp_ctx ctx) { ctx->prepared = false; }
 void check_periodic(fetirp_ctx ctx);
+void precond_setup(fetirp_ctx ctx);
 
 // Local-product buffers for a block of k columns in every precision (allocated before any graph capture).
 void ensure_apply_buffers(fetirp_ctx ctx, int k) {
@@ -759,6 +770,57 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   ctx->d_grp_ptr.upload(grp_ptr, s);
   ctx->d_grp_row.upload(grp_row, s);
   ctx->d_grp_w.upload(grp_w, s);
+  if (ctx->pc.kind != 0) {
+    // scaling Delta(s) of every row entry (Eqs. 4-5, sum over the row's entries = 1): multiplicity 1 / count, or
+    // stiffness: the other side's share of the diagonal stiffness at the link's dof (global frame); 1 on
+    // Dirichlet rows
+    auto kdiag = [&](int slot) -> double {   // diagonal of R-hat K R-hat^T at the slot's global dof
+      const int o = slot_occ[slot];
+      const PatternData& P = *ctx->pats[occ_pat[o]];
+      const int j = slot - obase[o];
+      const int b = j / P.dpn, c = j % P.dpn, node = P.bnd_nodes[b];
+      auto entry = [&](int i, int jj) {
+        for (int64_t e = P.rowptr[i]; e < P.rowptr[i + 1]; ++e)
+          if (P.col[e] == jj) return P.val[e];
+        return 0.0;
+      };
+      if (!ctx->occs[o].general) return entry(node * P.dpn + c, node * P.dpn + c);
+      const double* R = ctx->occs[o].Rd;
+      double v = 0.0;
+      for (int c2 = 0; c2 < P.dpn; ++c2)
+        for (int c3 = 0; c3 < P.dpn; ++c3)
+          v += R[3 * c + c2] * R[3 * c + c3] * entry(node * P.dpn + c2, node * P.dpn + c3);
+      return v;
+    };
+    std::vector<double> delta(2 * (size_t)nl, 0.0), row_w(2 * (size_t)nl, 0.0);
+    for (int r = 0; r < nl; ++r) {
+      if (row_cnt[r] == 1) { delta[2 * (size_t)r] = 1.0; continue; }
+      if (ctx->pc.scaling == 0) { delta[2 * (size_t)r] = delta[2 * (size_t)r + 1] = 0.5; continue; }
+      const double k0 = kdiag(row_slot[2 * (size_t)r]), k1 = kdiag(row_slot[2 * (size_t)r + 1]);
+      if (!(k0 > 0.0 && k1 > 0.0)) throw Error(FETIRP_EINVAL, "stiffness scaling needs a positive diagonal");
+      delta[2 * (size_t)r] = k1 / (k0 + k1);
+      delta[2 * (size_t)r + 1] = k0 / (k0 + k1);
+    }
+    for (size_t i = 0; i < delta.size(); ++i) row_w[i] = row_sign[i] * delta[i];
+    std::vector<double> link_w(slot_row.size());
+    for (size_t e = 0; e < slot_row.size(); ++e) link_w[e] = slot_sign[e] * delta[(size_t)slot_code[e]];
+    // group lists with the Delta weights (same rows as grp_row): the split of the preconditioned residual
+    std::vector<double> grp_wd(grp_row.size(), 0.0);
+    if (!ctx->perm.on)
+      for (int g = 0; g < k; ++g)
+        for (int i = grp_ptr[g]; i < grp_ptr[g + 1]; ++i) {
+          const int r = grp_row[i];
+          for (int e = 0; e < row_cnt[r]; ++e)
+            if (group[slot_occ[row_slot[2 * (size_t)r + e]]] == g) grp_wd[i] += delta[2 * (size_t)r + e];
+        }
+    else
+      grp_wd = grp_w;
+    ctx->pc.row_d.upload(delta, s);
+    ctx->pc.row_w.upload(row_w, s);
+    ctx->pc.link_w.upload(link_w, s);
+    ctx->pc.grp_wd.upload(grp_wd, s);
+    FETIRP_CUDA(cudaStreamSynchronize(s));
+  }
   if (ctx->perm.on) {
     ctx->perm.d_grp_src.upload(grp_src, s);
     ctx->perm.d_src.upload(ctx->perm.src, s);
@@ -989,7 +1051,8 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   ctx->n_lambda = n_lambda;
   ctx->prepared = true;
   FETIRP_CUDA(cudaStreamSynchronize(s));
-  if (ctx->perm.on && ctx->perm.shortcut && k > 1) check_periodic(ctx);
+  if (ctx->pc.kind != 0) precond_setup(ctx);
+  if (ctx->perm.on && ctx->perm.shortcut && k > 1 && ctx->pc.kind == 0) check_periodic(ctx);
 }
 
 // ----------------------------------------------------------------------------------------- operators
@@ -1012,7 +1075,7 @@ void project(fetirp_ctx ctx, double* V, int k) {
     const long long ng2 = (long long)ctx->n_G * ctx->n_G;
     gt_v_ds(ctx->L, V, k, ctx->Xc.p, s);
     split_pairs(ngk, ctx->Xc.p, xh, xl, s);
-    small_gemm_ds(ctx->n_G, k, ctx->ds_ginv.p, ctx->ds_ginv.p + ng2, xh, xl, ctx->Ac.p, s);
+    small_gemm_ds(ctx->n_G, k, ctx->ds_ginv.p, ctx->ds_ginv.p + ng2, xh, xl, ctx->Ac.p, s, ctx->sg_part.p);
     split_pairs(ngk, ctx->Ac.p, ah, al, s);
     g_apply_ds(ctx->L, ah, al, k, -1.0, 1.0, V, s);
     return;
@@ -1133,6 +1196,141 @@ void apply_F(fetirp_ctx ctx, const double* in, double* out, int k, int prec, boo
   if (project_out) project(ctx, out, k);
 }
 
+// ---------------------------------------------------------------------------------------- preconditioners
+// tilde-F^{-1} V = sum_s Delta(s) B(s) X(s) B(s)^T Delta(s) V (Eqs. 4-5) on a block of k columns, FP64: the
+// scaled gather, the local operator of the occurrence's pattern (pattern frame), the scaled scatter.
+void apply_M(fetirp_ctx ctx, const double* in, double* out, int k) {
+  cudaStream_t s = ctx->stream;
+  const Layout& L = ctx->L;
+  const int n_pat = (int)ctx->pats.size();
+  long long total = 0;
+  std::vector<long long> base(n_pat);
+  for (int p = 0; p < n_pat; ++p) {
+    base[p] = total;
+    total += (long long)ctx->use[p].occs.size() * k * ctx->pats[p]->ld_y;
+  }
+  ctx->Y64.ensure(total);
+  ctx->Z64.ensure(total);
+  PatView<double> Yv{}, Zv{};
+  LocalProblem LP{};
+  LP.n_pat = n_pat;
+  for (int p = 0; p < n_pat; ++p) {
+    PatternData& P = *ctx->pats[p];
+    Yv.base[p] = ctx->Y64.p + base[p]; Yv.ld[p] = P.ld_y; Yv.off[p] = 0;
+    Zv.base[p] = ctx->Z64.p + base[p]; Zv.ld[p] = P.ld_y; Zv.off[p] = 0;
+    LP.S[p] = ctx->pc.X[p].p; LP.n_b[p] = P.n_b; LP.n_rhs[p] = (int)ctx->use[p].occs.size() * k; LP.ld[p] = P.ld_y;
+    LP.Y[p] = Yv.base[p]; LP.Z[p] = Zv.base[p];
+  }
+  gather_w(L, in, k, Yv, ctx->pc.link_w.p, s);
+  rotate_traces<double>(L, Yv, k, true, s);
+  local_gemm_f64(LP, s);
+  rotate_traces<double>(L, Zv, k, false, s);
+  scatter_w(L, Zv, k, ctx->pc.row_w.p, out, s);
+}
+
+// The projector of Eqs. 6-7 in the preconditioner's metric, on a block of k columns in place:
+//   Q V  = V - tilde-F^{-1} G (G^T tilde-F^{-1} G)^{-1} G^T V        (transpose = false)
+//   Q^T V = V - G (G^T tilde-F^{-1} G)^{-1} G^T tilde-F^{-1} V        (transpose = true)
+// Without a preconditioner both are P = I - G (G^T G)^{-1} G^T.
+void project_q(fetirp_ctx ctx, double* V, int k, bool transpose) {
+  if (ctx->pc.kind == 0) { project(ctx, V, k); return; }
+  if (ctx->n_G == 0) return;
+  cudaStream_t s = ctx->stream;
+  const Layout& L = ctx->L;
+  const int nl = L.n_lambda;
+  PhaseScope ph(ctx, FETIRP_PHASE_PROJECT, 0.0, 0.0);
+  double* T1 = ctx->pc.T1.p;
+  double* T2 = ctx->pc.T2.p;
+  if (transpose) {
+    apply_M(ctx, V, T1, k);
+    gt_v(L, T1, k, ctx->Xc.p, s);
+    small_gemm(ctx->n_G, k, ctx->pc.GtMGinv.p, ctx->Xc.p, ctx->Ac.p, s, ctx->sg_part.p);
+    g_apply(L, ctx->Ac.p, k, -1.0, 1.0, V, s);
+  } else {
+    gt_v(L, V, k, ctx->Xc.p, s);
+    small_gemm(ctx->n_G, k, ctx->pc.GtMGinv.p, ctx->Xc.p, ctx->Ac.p, s, ctx->sg_part.p);
+    g_apply(L, ctx->Ac.p, k, 1.0, 0.0, T1, s);
+    apply_M(ctx, T1, T2, k);
+    axpy_f64(nl * k, -1.0, T2, V, s);
+  }
+}
+
+// Local operators X_p of the chosen preconditioner, G^T tilde-F^{-1} G and its inverse, and lambda_0 in the
+// preconditioner's metric (Table 1's initialisation with the projector of Eqs. 6-7).
+void precond_setup(fetirp_ctx ctx) {
+  cudaStream_t s = ctx->stream;
+  const Layout& L = ctx->L;
+  const int nl = L.n_lambda, n_pat = (int)ctx->pats.size();
+  auto& pc = ctx->pc;
+  for (int p = 0; p < n_pat; ++p) {
+    const PatternData& P = *ctx->pats[p];
+    const int nb = P.n_b;
+    // K_bb in the pattern frame, boundary dofs in slot order (bpos * dpn + c)
+    std::vector<double> Kbb((size_t)nb * nb, 0.0);
+    std::vector<int> slot_of(P.n, -1);
+    for (int b = 0; b < (int)P.bnd_nodes.size(); ++b)
+      for (int c = 0; c < P.dpn; ++c) slot_of[P.bnd_nodes[b] * P.dpn + c] = b * P.dpn + c;
+    for (int i = 0; i < P.n; ++i) {
+      if (slot_of[i] < 0) continue;
+      for (int64_t e = P.rowptr[i]; e < P.rowptr[i + 1]; ++e) {
+        const int j = slot_of[P.col[e]];
+        if (j < 0) continue;
+        if (pc.kind == FETIRP_PRECOND_SUPERLUMPED && j != slot_of[i]) continue;
+        Kbb[(size_t)slot_of[i] * nb + j] += P.val[e];
+      }
+    }
+    pc.X[p].upload(Kbb, s);
+    if (pc.kind == FETIRP_PRECOND_DIRICHLET) {
+      // S = K_bb - K_bi K_ii^{-1} K_ib with W = L_ii^{-1} K_ib from the interior block of the factor (the forward
+      // solve of the interior rows involves only L_ii), S -= W^T W
+      const int npad = P.npad, ni = P.n_i;
+      std::vector<double> rhs((size_t)npad * nb, 0.0);   // column-major, new (interior-first) ordering
+      for (int i = 0; i < P.n; ++i) {
+        const int nr = P.newidx[i];
+        if (nr >= ni) continue;
+        for (int64_t e = P.rowptr[i]; e < P.rowptr[i + 1]; ++e) {
+          const int j = slot_of[P.col[e]];
+          if (j >= 0) rhs[(size_t)j * npad + nr] += P.val[e];
+        }
+      }
+      DBuf<double> Wd;
+      Wd.upload(rhs, s);
+      tri_solve(P.L.p, npad, P.plan, P.zp.p, Wd.p, npad, nb, false, s, P.Dinv.p);
+      gemm_f64(nb, nb, ni, -1.0, Wd.p, npad, 1, Wd.p, 1, npad, 1.0, pc.X[p].p, nb, 1, s);
+      FETIRP_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+  pc.T1.ensure((size_t)nl * 64);
+  pc.T2.ensure((size_t)nl * 64);
+  if (ctx->n_G == 0) return;
+  const int nG = ctx->n_G;
+  // G^T tilde-F^{-1} G, 64 columns of G at a time
+  pc.GtMG.ensure((size_t)nG * nG);
+  pc.GtMGinv.ensure((size_t)nG * nG);
+  std::vector<double> unit;
+  DBuf<double> dunit;
+  for (int c0 = 0; c0 < nG; c0 += 64) {
+    const int kb = std::min(64, nG - c0);
+    unit.assign((size_t)nG * kb, 0.0);
+    for (int i = 0; i < kb; ++i) unit[(size_t)(c0 + i) * kb + i] = 1.0;
+    dunit.upload(unit, s);
+    g_apply(L, dunit.p, kb, 1.0, 0.0, pc.T1.p, s);
+    apply_M(ctx, pc.T1.p, pc.T2.p, kb);
+    gt_v(L, pc.T2.p, kb, ctx->Xc.p, s);
+    FETIRP_CUDA(cudaMemcpy2DAsync(pc.GtMG.p + c0, sizeof(double) * nG, ctx->Xc.p, sizeof(double) * kb,
+                                  sizeof(double) * kb, nG, cudaMemcpyDeviceToDevice, s));
+    FETIRP_CUDA(cudaStreamSynchronize(s));   // unit and dunit are reused by the next block
+  }
+  pc.plan = dense_plan(ctx->n_Gpad / TILE);
+  pc.plan.upload(s);
+  spd_inverse(ctx, pc.GtMG.p, nG, ctx->n_Gpad, pc.plan, pc.zp, pc.GtMGinv.p);
+  // lambda_0 = tilde-F^{-1} G (G^T tilde-F^{-1} G)^{-1} e
+  gemm_f64(nG, 1, nG, 1.0, pc.GtMGinv.p, nG, 1, ctx->e.p, 1, 1, 0.0, ctx->Ac.p, 1, 1, s);
+  g_apply(L, ctx->Ac.p, 1, 1.0, 0.0, pc.T1.p, s);
+  apply_M(ctx, pc.T1.p, ctx->lambda0.p, 1);
+  FETIRP_CUDA(cudaStreamSynchronize(s));
+}
+
 // The periodic shortcut computes the F-image of [z, Pi z, ...] from the one of z, which is exact only when Pi
 // commutes with P^T F P (a structure made of rotated copies, Pi the map of multiplier rows under the rotation).
 // Checked once per structure in FP64 on a seeded vector: P^T F P (Pi v) against Pi (P^T F P v).
@@ -1190,7 +1388,7 @@ void residual(fetirp_ctx ctx) {
   FETIRP_CUDA(cudaMemcpyAsync(ctx->t1.p, ctx->d.p, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
   axpy_f64(nl, -1.0, ctx->r.p, ctx->t1.p, s);
   FETIRP_CUDA(cudaMemcpyAsync(ctx->r.p, ctx->t1.p, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
-  project(ctx, ctx->r.p, 1);
+  project_q(ctx, ctx->r.p, 1, true);
 }
 
 // lambda <- lambda_0 + P (lambda - lambda_0) in FP64: keeps G^T lambda = e exactly after corrections built
@@ -1201,7 +1399,7 @@ void reproject_lambda(fetirp_ctx ctx) {
   const int nl = ctx->L.n_lambda;
   cudaStream_t s = ctx->stream;
   axpy_f64(nl, -1.0, ctx->lambda0.p, ctx->lam.p, s);
-  project(ctx, ctx->lam.p, 1);
+  project_q(ctx, ctx->lam.p, 1, false);
   axpy_f64(nl, 1.0, ctx->lambda0.p, ctx->lam.p, s);
 }
 
@@ -1220,8 +1418,68 @@ template <> float* hist_q<float>(fetirp_ctx ctx) { return ctx->Qhist32.p; }
 // number of stored directions lives on the device (d_state[0]); every kernel that depends on it reads it there.
 // Reorthogonalisation coefficients C = Q_h^T W are FP64 sums; since Q_h lies in range(P) and W = P S(r),
 // C = Q_h^T S(r) is taken from the split structure of S(r) (at most two nonzero columns per row).
+// One block iteration with a preconditioner of Eqs. 4-5 (Table 1, right column, preconditioned): the directions
+// are the split of z = Q tilde-F^{-1} r (scaled by Delta, or the permutation images of z), made admissible by Q,
+// reorthogonalised against the history and made admissible again (the extra Q keeps the rounding of the
+// subtraction out of range(G)); their F-image is Q^T F W.  The reorthogonalisation coefficients Q_h^T Q S(z) =
+// Q_h^T S(z) come from the split structure as in the unpreconditioned iteration.
+template <typename TH>
+void enqueue_iteration_pc(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
+  cudaStream_t s = ctx->stream;
+  const int nl = ctx->L.n_lambda, k = ctx->k;
+  const long long cap = ctx->hist_cap;
+  int* d_cols = ctx->d_state.p;
+  double* z = ctx->t1.p;
+  const bool permuted = ctx->perm.on;
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_PROJECT, 0.0, 0.0);
+    apply_M(ctx, ctx->r.p, z, 1);
+  }
+  project_q(ctx, z, 1, false);
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_UPDATE, 0.0, 0.0);
+    if (permuted) perm_split(nl, k, ctx->perm.pw, ctx->perm.d_src.p, ctx->perm.d_w.p, z, ctx->Zr.p, s);
+    else split_w(ctx->L, z, k, ctx->pc.row_d.p, ctx->Zr.p, s);
+  }
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 0.0, 0.0);
+    gram_split<TH>((int)cap, d_cols, k, Qh, nl, k, z, ctx->d_grp_ptr.p, ctx->d_grp_row.p, ctx->pc.grp_wd.p,
+                   ctx->n_grp_entries, ctx->max_group_rows, ctx->C.p, ctx->gram_part, ctx->grp_wr, s,
+                   permuted ? ctx->perm.d_grp_src.p : nullptr);
+  }
+  project_q(ctx, ctx->Zr.p, k, false);
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_REORTH, 0.0, 0.0);
+    tall_update<TH>(nl, (int)cap, d_cols, k, Wh, k, ctx->C.p, -1.0, ctx->Zr.p, ctx->tu_part, ctx->tu_tickets, s);
+  }
+  project_q(ctx, ctx->Zr.p, k, false);
+  apply_F(ctx, ctx->Zr.p, ctx->Q.p, k, prec, false, false);
+  project_q(ctx, ctx->Q.p, k, true);   // P~ = Q^T F W
+  int eta_off = 0;
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 0.0, 0.0);
+    eta_off = eta_partials(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta_part, s, prec != FETIRP_PREC_FP64);
+  }
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_NORMALISE, 0.0, 0.0);
+    normalise(k, ctx->eta_part.p + (size_t)eta_off * k * (k + 1), eta_off ? ETA_GROUPS : eta_chunks(nl),
+              prec == FETIRP_PREC_FP64 ? ctx->opt.eig_trunc : ctx->opt.eig_trunc_inner, ctx->T.p, ctx->alpha.p,
+              ctx->n_kept.p, s);
+  }
+  {
+    PhaseScope ph(ctx, FETIRP_PHASE_UPDATE, 0.0, 0.0);
+    AdvanceArgs adv;
+    adv.cols = d_cols; adv.k = k; adv.cap = cap; adv.n_kept = ctx->n_kept.p;
+    adv.dropped = ctx->d_state.p + 1; adv.iters = ctx->d_state.p + 2;
+    adv.counter = reinterpret_cast<unsigned*>(ctx->d_state.p + 3);
+    update<TH>(nl, k, ctx->Zr.p, ctx->Q.p, ctx->T.p, ctx->alpha.p, Wh, Qh, d_cols, ctx->lam.p, ctx->r.p,
+               ctx->rr_part.p, ctx->rr_blocks, s, adv);
+  }
+}
+
 template <typename TH>
 void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
+  if (ctx->pc.kind != 0) { enqueue_iteration_pc<TH>(ctx, prec, Wh, Qh); return; }
   int eta_off = 0;
   cudaStream_t s = ctx->stream;
   const int nl = ctx->L.n_lambda, k = ctx->k;
@@ -1391,6 +1649,7 @@ bool persist_eligible(fetirp_ctx ctx, int prec) {
   if (ctx->k > 32 || ctx->L.n_lambda > 262144) return false;
   if (ctx->L.n_gen > 0) return false;   // general rotations turn the traces in separate passes
   if (ctx->perm.on) return false;       // the persistent phases build the occurrence split
+  if (ctx->pc.kind != 0) return false;  // the persistent phases use the unweighted projector
   for (auto& P : ctx->pats)
     if (P->kdim > 6) return false;
   return persist_ctas(prec == FETIRP_PREC_FP64, ctx->k) > 0;
@@ -1630,6 +1889,8 @@ void recover(fetirp_ctx ctx, double* d_u_out) {
   }
 }
 
+bool hist_fp64(fetirp_ctx ctx) { return ctx->opt.precision == FETIRP_PREC_FP64 || ctx->pc.kind != 0; }
+
 void ensure_history(fetirp_ctx ctx) {
   const int nl = ctx->L.n_lambda, k = ctx->k;
   // History: at most n_lambda directions can be F-orthogonal, and at most max_iter blocks are made; the two
@@ -1638,14 +1899,18 @@ void ensure_history(fetirp_ctx ctx) {
   // the two history arrays may take half of the device memory that is free (HBM is the limit, not a constant)
   size_t free_b = 0, total_b = 0;
   FETIRP_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  const double es_h = ctx->opt.precision == FETIRP_PREC_FP64 ? 8.0 : 4.0;
-  const double held = ctx->opt.precision == FETIRP_PREC_FP64 ? 8.0 * (ctx->Whist.n + ctx->Qhist.n)
+  // FP64 history for the plain form, and for every preconditioned solve: the split of the weighted projection
+  // (Q_h^T Q S(z) = Q_h^T S(z)) holds only for images exactly in range(Q^T), and rounding them to FP32 leaves
+  // components that the preconditioner's contrast amplifies (measured: no convergence on the 1 / 1000 checkerboard)
+  const bool h64 = hist_fp64(ctx);
+  const double es_h = h64 ? 8.0 : 4.0;
+  const double held = h64 ? 8.0 * (ctx->Whist.n + ctx->Qhist.n)
                                                              : 4.0 * (ctx->Whist32.n + ctx->Qhist32.n);
   const double avail = ctx->opt.history_bytes > 0 ? (double)ctx->opt.history_bytes : 0.5 * ((double)free_b + held);
   long long limit = (long long)(avail / (2.0 * es_h * std::max(nl, 1)));
   long long cap = std::max<long long>(k, std::min(want, limit));
   cap = cap / k * k;
-  if (ctx->opt.precision == FETIRP_PREC_FP64) {
+  if (h64) {
     if (cap != ctx->hist_cap || (long long)ctx->Whist.n < (long long)nl * cap) {
       ctx->Whist.alloc((size_t)nl * cap);
       ctx->Qhist.alloc((size_t)nl * cap);
@@ -1721,7 +1986,8 @@ fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_st
       // outer FP64 defect correction: inner solves on the low-precision operator reuse their directions
       for (int outer = 0; outer < ctx->opt.max_outer && rn > target && budget > 0; ++outer) {
         const double inner_target = std::max(ctx->opt.inner_tol * rn, 0.5 * target);
-        block_orthodir<float>(ctx, prec, inner_target, rn, H, st, budget);
+        if (hist_fp64(ctx)) block_orthodir<double>(ctx, prec, inner_target, rn, H, st, budget);
+        else block_orthodir<float>(ctx, prec, inner_target, rn, H, st, budget);
         reproject_lambda(ctx);
         residual(ctx);
         rn = norm2(ctx, ctx->r.p, nl);
@@ -2587,6 +2853,17 @@ fetirp_status fetirp_set_permutation(fetirp_ctx ctx, int64_t n_lambda, const int
         }
     P.shortcut = shortcut == 1;
     P.on = true;
+    invalidate(ctx);
+    return FETIRP_OK;
+  });
+}
+
+fetirp_status fetirp_set_preconditioner(fetirp_ctx ctx, int32_t kind, int32_t scaling) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    REQUIRE(kind >= FETIRP_PRECOND_NONE && kind <= FETIRP_PRECOND_SUPERLUMPED, "unknown preconditioner");
+    REQUIRE(scaling == FETIRP_SCALING_MULTIPLICITY || scaling == FETIRP_SCALING_STIFFNESS, "unknown scaling");
+    ctx->pc.kind = kind;
+    ctx->pc.scaling = scaling;
     invalidate(ctx);
     return FETIRP_OK;
   });

@@ -159,21 +159,33 @@ __global__ void __launch_bounds__(GTV_THREADS, WIDE ? 2 : 3) k_gt_v_ds(Layout L,
   const int i_end = min(nl, (c + 1) * chunk);
   float h0[MAX_KDIM] = {}, e0[MAX_KDIM] = {}, h1[MAX_KDIM] = {}, e1[MAX_KDIM] = {};
   if (kd > 0) {
-    for (int i = c * chunk + w; i < i_end; i += 8) {
-      const int code = L.slot_code[l0 + i];
-      const double* vr = V + (size_t)(code >> 1) * k + lane;
-      float vh0, vl0, vh1 = 0.f, vl1 = 0.f;
-      dsplit(c0 ? vr[0] : 0.0, vh0, vl0);
-      if (WIDE) dsplit(c1 ? vr[32] : 0.0, vh1, vl1);
-      const float* ch = L.rowg_coef_hi + (size_t)code * MAX_KDIM;
-      const float* cl = L.rowg_coef_lo + (size_t)code * MAX_KDIM;
+    for (int i = c * chunk + w; i < i_end; i += 32) {   // four links per step: their loads are in flight together
+      int code[4];
 #pragma unroll
-      for (int m = 0; m < MAX_KDIM; ++m)
-        if (m < kd) {
-          const float a = ch[m], b = cl[m];
-          dsm(a, b, vh0, vl0, h0[m], e0[m]);
-          if (WIDE) dsm(a, b, vh1, vl1, h1[m], e1[m]);
-        }
+      for (int u = 0; u < 4; ++u) code[u] = i + 8 * u < i_end ? L.slot_code[l0 + i + 8 * u] : -1;
+      double v0[4], v1[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double* vr = V + (size_t)(max(code[u], 0) >> 1) * k + lane;
+        v0[u] = (c0 && code[u] >= 0) ? vr[0] : 0.0;
+        v1[u] = (WIDE && c1 && code[u] >= 0) ? vr[32] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (code[u] < 0) continue;
+        float vh0, vl0, vh1 = 0.f, vl1 = 0.f;
+        dsplit(v0[u], vh0, vl0);
+        if (WIDE) dsplit(v1[u], vh1, vl1);
+        const float* ch = L.rowg_coef_hi + (size_t)code[u] * MAX_KDIM;
+        const float* cl = L.rowg_coef_lo + (size_t)code[u] * MAX_KDIM;
+#pragma unroll
+        for (int m = 0; m < MAX_KDIM; ++m)
+          if (m < kd) {
+            const float a = ch[m], b = cl[m];
+            dsm(a, b, vh0, vl0, h0[m], e0[m]);
+            if (WIDE) dsm(a, b, vh1, vl1, h1[m], e1[m]);
+          }
+      }
     }
   }
 #pragma unroll

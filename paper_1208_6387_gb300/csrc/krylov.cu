@@ -115,44 +115,80 @@ __device__ __forceinline__ void ds_split(double v, float& h, float& l) {
   h = (float)v;
   l = (float)(v - (double)h);
 }
+// Register tiling: every thread sums 4 x 4 outputs (rows i of W, columns j of [Q | r]) over a slice of the chunk's
+// rows, so each staged pair is read once per 4 products; the slices are added in slice order at the end.
+constexpr int ETA_DS_ROWS = 32;   // rows staged per step
 __global__ void __launch_bounds__(256) k_eta_partial_ds(int n, int k, const double* __restrict__ W,
                                                         const double* __restrict__ Q, const double* __restrict__ r,
                                                         int rows_per_chunk, double* __restrict__ partial) {
-  __shared__ float swh[16][64], swl[16][64];
-  __shared__ float sqh[16][65], sql[16][65];
+  __shared__ float swh[ETA_DS_ROWS][68], swl[ETA_DS_ROWS][68];   // W rows, columns 0..k-1 (padded to 68)
+  __shared__ float sqh[ETA_DS_ROWS][68], sql[ETA_DS_ROWS][68];   // [Q | r] rows, columns 0..k (padded)
+  __shared__ double red[256][4];
   const int r0 = blockIdx.x * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
   const int nout = k * (k + 1);
-  for (int base = 0; base < nout; base += 5 * 256) {
-    float ah[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, al[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int rr = r0; rr < r1; rr += 16) {
-      const int nrow = min(16, r1 - rr);
-      for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
-        const int q = idx / 64, c = idx % 64;
-        const bool ok = q < nrow && c < k;
-        ds_split(ok ? W[(size_t)(rr + q) * k + c] : 0.0, swh[q][c], swl[q][c]);
-        ds_split(ok ? Q[(size_t)(rr + q) * k + c] : 0.0, sqh[q][c], sql[q][c]);
-      }
-      if (threadIdx.x < 16) ds_split(threadIdx.x < nrow ? r[rr + threadIdx.x] : 0.0, sqh[threadIdx.x][64],
-                                     sql[threadIdx.x][64]);
+  const int bi = (k + 3) / 4, bj = (k + 4) / 4, nblk = bi * bj;
+  const int slices = max(1, 256 / nblk);
+  const int tid = threadIdx.x;
+  const int sl = tid / nblk;
+  const bool active = sl < slices;
+  for (int b0 = 0; b0 < nblk; b0 += 256) {   // more than 256 blocks (k > 60): several passes
+    const int blk = b0 + (slices > 1 ? tid % nblk : tid);
+    const bool act = active && blk < nblk;
+    const int i0 = (blk / bj) * 4, j0 = (blk % bj) * 4;
+    float h[4][4] = {}, l[4][4] = {};
+    for (int rr = r0; rr < r1; rr += ETA_DS_ROWS) {
+      const int nrow = min(ETA_DS_ROWS, r1 - rr);
       __syncthreads();
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        const int o = base + q * 256 + threadIdx.x;
-        if (o < nout) {
-          const int i = o / (k + 1), j = o % (k + 1);
-          const int jj = (j == k) ? 64 : j;
-          float h = ah[q], l = al[q];
-          for (int t = 0; t < nrow; ++t) ds_madd(swh[t][i], swl[t][i], sqh[t][jj], sql[t][jj], h, l);
-          ah[q] = h;
-          al[q] = l;
+      // only the k (W) and k + 1 ([Q | r]) used columns are converted (an FP64 -> FP32 conversion issues on this
+      // GPU's narrow FP64 path); the padding columns the 4 x 4 blocks may touch are zero-filled without one
+      const int kq = k + 1;
+      for (int idx = tid; idx < ETA_DS_ROWS * kq; idx += 256) {
+        const int q = idx / kq, c = idx % kq;
+        if (q < nrow) {
+          if (c < k) ds_split(W[(size_t)(rr + q) * k + c], swh[q][c], swl[q][c]);
+          ds_split(c < k ? Q[(size_t)(rr + q) * k + c] : r[rr + q], sqh[q][c], sql[q][c]);
+        } else {
+          if (c < k) { swh[q][c] = 0.f; swl[q][c] = 0.f; }
+          sqh[q][c] = 0.f; sql[q][c] = 0.f;
         }
       }
+      for (int idx = tid; idx < ETA_DS_ROWS * (68 - k); idx += 256) {   // columns >= k of W, >= k + 1 of Q
+        const int q = idx / (68 - k), c = k + idx % (68 - k);
+        swh[q][c] = 0.f; swl[q][c] = 0.f;
+        if (c > k) { sqh[q][c] = 0.f; sql[q][c] = 0.f; }
+      }
       __syncthreads();
-    }
+      if (act)
+        for (int t = sl; t < nrow; t += slices) {
+          float ah[4], al[4], bh[4], bl[4];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      const int o = base + q * 256 + threadIdx.x;
-      if (o < nout) partial[(size_t)blockIdx.x * nout + o] = (double)ah[q] + (double)al[q];
+          for (int u = 0; u < 4; ++u) {
+            ah[u] = swh[t][i0 + u]; al[u] = swl[t][i0 + u];
+            bh[u] = sqh[t][j0 + u]; bl[u] = sql[t][j0 + u];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) ds_madd(ah[u], al[u], bh[v], bl[v], h[u][v], l[u][v]);
+        }
+    }
+    // add the slices in slice order, 4 outputs of the block at a time
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      __syncthreads();
+#pragma unroll
+      for (int v = 0; v < 4; ++v) red[tid][v] = act ? (double)h[u][v] + (double)l[u][v] : 0.0;
+      __syncthreads();
+      if (act && sl == 0) {
+        const int i = i0 + u;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          double acc = red[tid][v];
+          for (int q = 1; q < slices; ++q) acc += red[tid + q * nblk][v];
+          const int j = j0 + v;
+          if (i < k && j <= k) partial[(size_t)blockIdx.x * nout + (size_t)i * (k + 1) + j] = acc;
+        }
+      }
     }
   }
 }
@@ -575,48 +611,6 @@ __global__ void __launch_bounds__(128) k_small_gemm(int m, int k, const double* 
   }
 }
 
-// C = A B in double-single arithmetic (A: m x m, B: m x k, both as FP32 pairs), one warp per row of C with the
-// same lane layout as k_small_gemm (no inner split: each lane's column sum is a (hi, lo) pair, and the slices
-// of a column are added in FP64 by the shuffle tree)
-__global__ void __launch_bounds__(128) k_small_gemm_ds(int m, int k, const float* __restrict__ Ah,
-                                                       const float* __restrict__ Al, const float* __restrict__ Bh,
-                                                       const float* __restrict__ Bl, double* __restrict__ C) {
-  const int row = blockIdx.x * 4 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= m) return;
-  const float* ah = Ah + (size_t)row * m;
-  const float* al = Al + (size_t)row * m;
-  for (int g0 = 0; g0 < k; g0 += 32) {
-    const int kk = min(32, k - g0);
-    int kp = 1;
-    while (kp < kk) kp <<= 1;
-    const int slices = 32 / kp;
-    const int g = g0 + (lane % kp), sl = lane / kp;
-    double acc = 0.0;
-    if (g < k) {
-      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-      int j = sl;
-      for (; j + slices < m; j += 2 * slices) {
-        ds_madd(ah[j], al[j], Bh[(size_t)j * k + g], Bl[(size_t)j * k + g], h0, l0);
-        ds_madd(ah[j + slices], al[j + slices], Bh[(size_t)(j + slices) * k + g], Bl[(size_t)(j + slices) * k + g],
-                h1, l1);
-      }
-      for (; j < m; j += slices) ds_madd(ah[j], al[j], Bh[(size_t)j * k + g], Bl[(size_t)j * k + g], h0, l0);
-      acc = ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
-    }
-    for (int off = kp; off < 32; off <<= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    if (sl == 0 && g < k) C[(size_t)row * k + g] = acc;
-  }
-}
-
-void small_gemm_ds(int m, int k, const float* Ah, const float* Al, const float* Bh, const float* Bl, double* C,
-                   cudaStream_t s) {
-  if (m <= 0 || k <= 0) return;
-  if (k > 64) throw Error(1, "k > 64");
-  k_small_gemm_ds<<<ceil_div(m, 4), 128, 0, s>>>(m, k, Ah, Al, Bh, Bl, C);
-  FETIRP_LAUNCH_CHECK();
-}
-
 // C[i] = sum of the `parts` slices P[p][i] in slice order
 __global__ void k_sum_slices(int count, int parts, const double* __restrict__ P, double* __restrict__ C) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -643,6 +637,56 @@ void small_gemm(int m, int k, const double* A, const double* B, double* C, cudaS
   }
 }
 
+
+// C = A B in double-single arithmetic (A: m x m, B: m x k, both as FP32 pairs), one warp per row of C with the
+// same lane layout as k_small_gemm (no inner split: each lane's column sum is a (hi, lo) pair, and the slices
+// of a column are added in FP64 by the shuffle tree)
+__global__ void __launch_bounds__(128) k_small_gemm_ds(int m, int k, const float* __restrict__ Ah,
+                                                       const float* __restrict__ Al, const float* __restrict__ Bh,
+                                                       const float* __restrict__ Bl, double* __restrict__ C) {
+  // grid.y > 1: split of the inner dimension as in k_small_gemm (slices added in order by k_sum_slices)
+  const int row = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  const int j0 = (int)((long long)blockIdx.y * m / gridDim.y), j1 = (int)((long long)(blockIdx.y + 1) * m / gridDim.y);
+  C += (size_t)blockIdx.y * m * k;
+  const float* ah = Ah + (size_t)row * m;
+  const float* al = Al + (size_t)row * m;
+  for (int g0 = 0; g0 < k; g0 += 32) {
+    const int kk = min(32, k - g0);
+    int kp = 1;
+    while (kp < kk) kp <<= 1;
+    const int slices = 32 / kp;
+    const int g = g0 + (lane % kp), sl = lane / kp;
+    double acc = 0.0;
+    if (g < k) {
+      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+      int j = j0 + sl;
+      for (; j + slices < j1; j += 2 * slices) {
+        ds_madd(ah[j], al[j], Bh[(size_t)j * k + g], Bl[(size_t)j * k + g], h0, l0);
+        ds_madd(ah[j + slices], al[j + slices], Bh[(size_t)(j + slices) * k + g], Bl[(size_t)(j + slices) * k + g],
+                h1, l1);
+      }
+      for (; j < j1; j += slices) ds_madd(ah[j], al[j], Bh[(size_t)j * k + g], Bl[(size_t)j * k + g], h0, l0);
+      acc = ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
+    }
+    for (int off = kp; off < 32; off <<= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (sl == 0 && g < k) C[(size_t)row * k + g] = acc;
+  }
+}
+
+void small_gemm_ds(int m, int k, const float* Ah, const float* Al, const float* Bh, const float* Bl, double* C,
+                   cudaStream_t s, double* part) {
+  if (m <= 0 || k <= 0) return;
+  if (k > 64) throw Error(1, "k > 64");
+  const int parts = part ? small_gemm_parts(m) : 1;
+  k_small_gemm_ds<<<dim3(ceil_div(m, 4), parts), 128, 0, s>>>(m, k, Ah, Al, Bh, Bl, parts > 1 ? part : C);
+  FETIRP_LAUNCH_CHECK();
+  if (parts > 1) {
+    k_sum_slices<<<ceil_div(m * k, 256), 256, 0, s>>>(m * k, parts, part, C);
+    FETIRP_LAUNCH_CHECK();
+  }
+}
 
 void normalise(int k, const double* ext_partial, int chunks, double trunc, double* T, double* alpha, int* n_kept,
                cudaStream_t s) {

@@ -84,7 +84,7 @@ void g_apply_ds(const Layout& L, const float* Ah, const float* Al, int k, double
 void split_pairs(long long n, const double* x, float* h, float* l, cudaStream_t s);
 // C (m x k) = A B with A given as FP32 pairs (m x m) and B as FP32 pairs (m x k), double-single sums, FP64 out
 void small_gemm_ds(int m, int k, const float* Ah, const float* Al, const float* Bh, const float* Bl, double* C,
-                   cudaStream_t s);
+                   cudaStream_t s, double* part = nullptr);
 // dense G^T G (n_G x n_G, row-major), nb_ptr/nb_list: neighbour occurrences of every occurrence
 void gtg_dense(const Layout& L, const int* nb_ptr, const int* nb_list, int n_pairs, const int* pair_s,
                const int* pair_t, double* GtG, cudaStream_t s);
@@ -118,6 +118,15 @@ void split(const Layout& L, const double* r, int k, double* Z, cudaStream_t s);
 // to Z as a single vector (Z[row]).
 void perm_split(int n, int k, int pw, const int* src, const double* w, const double* r, double* Z, cudaStream_t s,
                 int g_only = -1);
+
+// ---- preconditioners of Eqs. 4-5 (weighted assembly) ----------------------------------------------
+// Y(slot, g) = sum over the slot's links e: link_w[e] V[row_e][g] (link_w: sign x scaling, slot CSR order)
+void gather_w(const Layout& L, const double* V, int k, const PatView<double>& Y, const double* link_w,
+              cudaStream_t s);
+// out[row][g] = sum over the row's slots: row_w[2 row + e] Z(slot_e, g)
+void scatter_w(const Layout& L, const PatView<double>& Z, int k, const double* row_w, double* out, cudaStream_t s);
+// the scaled occurrence split: Z[row][g] = sum over the row's slots in column g of row_d[2 row + e] z[row]
+void split_w(const Layout& L, const double* z, int k, const double* row_d, double* Z, cudaStream_t s);
 
 // ---- local products Z_p = S_p^+ Y_p ----------------------------------------------------------------
 // FP64 (DFMA) and FP32 (FFMA) SIMT forms; one launch for every pattern.

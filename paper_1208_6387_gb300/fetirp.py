@@ -119,6 +119,7 @@ _SIGS = {
     "fetirp_inject_barrier_stall": (C.c_int, [P]),
     "fetirp_device_status": (C.c_int, [P]),
     "fetirp_set_permutation": (C.c_int, [P, C.c_int64, P, P, P, C.c_int32, C.c_int32]),
+    "fetirp_set_preconditioner": (C.c_int, [P, C.c_int32, C.c_int32]),
     "fetirp_apply_split": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_int]),
     "fetirp_apply_split_device": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_int]),
     "fetirp_get_pattern": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), P, P]),
@@ -382,6 +383,16 @@ def fetirp_set_permutation(ctx, Pi, n_images, shortcut=False):
     val = np.ascontiguousarray(M.data, dtype=np.float64)
     _check(ctx, lib().fetirp_set_permutation(ctx, int(M.shape[0]), _ptr(rowptr), _ptr(col), _ptr(val),
                                              int(n_images), 1 if shortcut else 0))
+
+
+PRECONDITIONERS = {"identity": 0, "dirichlet": 1, "lumped": 2, "superlumped": 3}
+SCALINGS = {"multiplicity": 0, "stiffness": 1}
+
+
+def fetirp_set_preconditioner(ctx, kind="identity", scaling="stiffness"):
+    """The preconditioner of Eqs. 4-5 by name (identity, dirichlet, lumped, superlumped) and its scaling
+    (multiplicity, stiffness); argument marshalling only."""
+    _check(ctx, lib().fetirp_set_preconditioner(ctx, PRECONDITIONERS[kind], SCALINGS[scaling]))
 
 
 def fetirp_device_status(ctx):
