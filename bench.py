@@ -37,11 +37,15 @@ WORKLOADS = {
     "c1": "2D heat, one 8x8 Q1 pattern on 2x2 occurrences, u=0 on x=0, f~U(0,1), n_lambda=52",
     "c3": "3D elasticity, three 16^3 Q1 cube patterns, 4x6x8 occurrences with seeded cube rotations, clamped x=0, "
           "N(0,1) per dof, n_lambda=427392",
+    "c4": "batched uneven 3D elasticity: hex patterns 8^3/12^3/16^3/24^3, 256 occurrences drawn with weights "
+          "0.4/0.3/0.2/0.1, each pattern's occurrences one clamped block, all blocks solved in one structure, "
+          "multivector width autotuned over {4,8,16,32}",
     "c5": "serving: structures arriving by a seeded Poisson process (mean 50/s), each 4-128 occurrences of one of "
           "6 resident patterns (2D heat 16^2/32^2/64^2, 3D elastic 8^3/12^3/16^3), admitted by device memory",
 }
 DEFAULTS = {  # per workload: local-product precision, multivector width, direction-history cap (GB; 0 = library)
-    "c3": ("tf32x3", 32, 32.0), "c2": ("fp32", 8, 0.0), "c1": ("fp64", 4, 0.0), "c5": ("fp32", 8, 0.0),
+    "c3": ("tf32x3", 32, 32.0), "c2": ("fp32", 8, 0.0), "c1": ("fp64", 4, 0.0), "c5": ("auto", 32, 0.0),
+    "c4": ("auto", 0, 32.0),   # k = 0: autotuned
 }
 # Block iterations of the default workload (C3, k = 32, tol 1e-8): the count the library's FP64 solve needs
 # on this structure, used to scale the oracle's sampled per-iteration cost to a whole solve.
@@ -175,8 +179,27 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    prob = config(args.workload, seed=rank_seed(args.seed, rank), k=args.k)
+    prob = config(args.workload, seed=rank_seed(args.seed, rank), k=args.k or None)
     stream = torch.cuda.Stream(device=dev)
+    if args.precision == "auto":   # the library's rule: FP32 SIMT for latency-bound structures, else tf32x3
+        max_nb = max(p.n_b for p in prob.patterns)
+        args.fprec = "fp32" if (max_nb <= 512 and prob.n_lambda <= 262144) else "tf32x3"
+    else:
+        args.fprec = args.precision
+    autotune = None
+    if not args.k:   # the library's autotuner picks the multivector width (untimed, before the steps)
+        o = F.fetirp_default_options(precision=args.precision, tol=1e-8, inner_tol=args.inner_tol, device=local,
+                                     history_bytes=int(args.history_gb * 1e9))
+        o.cuda_stream = stream.cuda_stream
+        c = F.fetirp_create(o)
+        F.load_problem(c, prob)
+        cand = (4, 8, 16, 32)
+        best, times = F.fetirp_autotune_k(c, prob.n_lambda, prob.c, cand)
+        F.fetirp_destroy(c)
+        prob.k = best
+        prob.groups = (np.arange(prob.n_occ) * best // prob.n_occ).astype(np.int32)
+        autotune = {"candidates": list(cand), "solve_ms": [round(float(t), 2) for t in times], "best_k": best,
+                    "grouping": "contiguous occurrence ids"}
     nu = F.n_u(prob)
     c_d = torch.tensor(prob.c, dtype=torch.float64, device=dev)
     lam_d = torch.empty(prob.n_lambda, dtype=torch.float64, device=dev)
@@ -288,16 +311,16 @@ def run_ours(args, rank, world, local):
         F.fetirp_destroy(c)
         return n_app / (a.elapsed_time(b) / 1e3)
 
-    fapply = {args.precision: round(fapply_rate(args.precision, 50), 2)}
+    fapply = {args.fprec: round(fapply_rate(args.fprec, 50), 2)}
 
     # the plain FP64 form of the same step (same k, same history cap), for comparison: one timed solve
     plain = None
     if args.precision != "fp64" and not args.no_fp64_reference:
         c = make_ctx("fp64", 0)
-        if args.workload != "c3":
+        if args.workload not in ("c3", "c4"):
             step(c)   # small structures: one untimed solve first (graph capture, buffers)
         times, its = [], []
-        for _ in range(1 if args.workload == "c3" else 3):
+        for _ in range(1 if args.workload in ("c3", "c4") else 3):
             flush_l2()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -307,15 +330,15 @@ def run_ours(args, rank, world, local):
             times.append(a.elapsed_time(b))
             its.append(st["iterations"])
         F.fetirp_destroy(c)
-        fapply["fp64"] = round(fapply_rate("fp64", 10 if args.workload == "c3" else 50), 3)
+        fapply["fp64"] = round(fapply_rate("fp64", 10 if args.workload in ("c3", "c4") else 50), 3)
         plain = {"time_to_solution_ms": round(statistics.median(times), 2), "iterations": its[-1],
                  "block_f_applies_per_s": fapply["fp64"],
                  "speedup_of_mixed_time_to_solution": round(statistics.median(times) / ms_per_step, 3),
-                 "speedup_of_mixed_f_applies": round(fapply[args.precision] / fapply["fp64"], 3)}
+                 "speedup_of_mixed_f_applies": round(fapply[args.fprec] / fapply["fp64"], 3)}
 
     # e2e: the public API from host buffers (create, patterns, occurrences, solve, outputs to host, destroy)
     e2e_times = []
-    for i in range(3 if args.workload == "c3" else max(2, min(args.steps, 5)) + 1):
+    for i in range(3 if args.workload in ("c3", "c4") else max(2, min(args.steps, 5)) + 1):
         t = time.perf_counter()
         c2 = F.fetirp_create(F.fetirp_default_options(precision=args.precision, tol=1e-8, inner_tol=args.inner_tol,
                                                        device=local, history_bytes=hist_bytes))
@@ -329,7 +352,7 @@ def run_ours(args, rank, world, local):
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+" + args.precision,
+        "vs_baseline": None, "dtype": "f64" if args.fprec == "fp64" else "f64+" + args.fprec,
         "data": "synthetic (seeded Q1 meshes, rotations, loads; no datasets)",
         "config": {"workload": WORKLOADS[args.workload], "name": args.workload, "precision": args.precision,
                    "block_k": prob.k, "n_lambda": prob.n_lambda, "n_occ": prob.n_occ,
@@ -337,6 +360,8 @@ def run_ours(args, rank, world, local):
                    "history_gb": args.history_gb,
                    "step": "factorise patterns + coarse + d + block ORTHODIR + recovery"},
         "time_to_solution_ms": round(ms_per_step, 3),
+        "setup_ms_per_step": round(float(ph_ms[F.PHASES.index("factor")] + ph_ms[F.PHASES.index("coarse")]) / args.steps, 2),
+        "autotune": autotune,
         "iterations": stats[-1]["iterations"], "outer_steps": stats[-1]["outer_steps"],
         "rel_residual": rel_res,
         "block_f_applies_per_s": fapply,
@@ -365,7 +390,7 @@ def roofline(args, prob, F, peaks, src, ph_ms, ph_fl, ph_ln, stats):
     block iteration in the launch against the measured HBM copy rate."""
     loc, itp = F.PHASES.index("local"), F.PHASES.index("iterate")
     if ph_ln[itp] > 0:
-        es = 8 if args.precision == "fp64" else 4
+        es = 8 if args.fprec == "fp64" else 4
         n_it = float(sum(s["iterations"] for s in stats))
         per_launch_ms = ph_ms[itp] / ph_ln[itp]
         bytes_per_launch = fapply_bytes(prob, prob.k, es) * n_it / ph_ln[itp]
@@ -379,11 +404,11 @@ def roofline(args, prob, F, peaks, src, ph_ms, ph_fl, ph_ln, stats):
     per_launch_ms = ph_ms[loc] / max(ph_ln[loc], 1)
     flops_per_launch = ph_fl[loc] / max(ph_ln[loc], 1)
     achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12
-    if args.precision == "tf32x3":
+    if args.fprec == "tf32x3":
         kern, bound = "k_tc_gemm (tcgen05 kind::tf32, 3 products)", "tensor"
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * 1.1 / 2.25
         note = f"tf32 tensor: bf16_tflops_sustained of {src} x 1.1/2.25 (nominal tf32/bf16 ratio)"
-    elif args.precision == "fp32":
+    elif args.fprec == "fp32":
         kern, bound, peak = "k_local_gemm<float>", "alu", FP32_PEAK_TFLOPS
         note = "FP32 SIMT peak derived from 152 SMs x 128 lanes x 2070 MHz"
     else:
@@ -393,7 +418,7 @@ def roofline(args, prob, F, peaks, src, ph_ms, ph_fl, ph_ln, stats):
            "unit": "TFLOP/s", "frac": round(achieved / peak, 5), "traffic": None,
            "flops_per_launch": flops_per_launch, "launches": int(ph_ln[loc]), "ms_per_launch": round(per_launch_ms, 4),
            "peak_source": note, "work": "2 sum_p n_b^2 R_p per launch (R_p = occurrences of p x k)"}
-    if args.precision == "tf32x3":
+    if args.fprec == "tf32x3":
         out["issued_frac"] = round(3 * achieved / peak, 4)
     return out
 
@@ -442,7 +467,7 @@ def cpu_baseline(args, prob, n_it):
     """The oracle as it stands (numpy/scipy FP64): one full solve of the workload when it finishes in seconds
     (C1, C2), else a bounded sample scaled to a solve."""
     cores = len(os.sched_getaffinity(0))
-    if args.workload == "c3":
+    if args.workload in ("c3", "c4"):
         est, what = OracleSampler(prob).sample(n_it)
         return {"value": round(1.0 / est, 6), "unit": "solves/s", "cores": cores, "kind": "oracle",
                 "sample": what + f"; estimated {est:.1f} s per solve; numpy/scipy default BLAS threads"}
@@ -461,7 +486,7 @@ def run_reference(args, rank, world):
     from fetirp_gen import config
     if rank != 0:
         return None
-    prob = config(args.workload, seed=args.seed, k=args.k)
+    prob = config(args.workload, seed=args.seed, k=args.k or None)
     cores = len(os.sched_getaffinity(0))
     if args.workload == "c3":
         sampler = []
@@ -552,6 +577,7 @@ def run_serving(args):
     # the plain sequential FP64 form on a sample of the same requests (one context, one after the other)
     seq = F.fetirp_create_child(lib, F.fetirp_default_options(precision="fp64", tol=1e-8,
                                                              history_bytes=args.mem_budget // 2))
+    seq_k = 8   # the plain FP64 form at its own best width (FP64 local products make wide blocks costly)
     ns = min(args.seq_sample, len(probs))
     ts = []
     for i in range(ns):
@@ -560,7 +586,8 @@ def run_serving(args):
         for occ in prob.occs:
             F.fetirp_add_occurrence(seq, pids[pi], occ.rot.astype(float), occ.link_local_node, occ.link_global_comp,
                                     occ.link_lambda_row, occ.link_sign, occ.f_global)
-        F.fetirp_set_groups(seq, prob.k, prob.groups)
+        kk = min(seq_k, prob.n_occ)
+        F.fetirp_set_groups(seq, kk, (np.arange(prob.n_occ) * kk // prob.n_occ).astype(np.int32))
         t = time.perf_counter()
         F.fetirp_solve(seq, prob.n_lambda, prob.c, F.n_u(prob), allow_noconv=True)
         ts.append(time.perf_counter() - t)
@@ -571,7 +598,8 @@ def run_serving(args):
         "metric": "served solves/s (p50/p99 latency) to 1e-8 rel. residual", "value": round(value, 3),
         "unit": "solves/s", "n_gpus": 1, "steps": len(reqs), "warmup": 0,
         "ms_per_step": round(1e3 * (t_end - t0) / len(reqs), 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64+" + ("fp32|tf32x3" if args.precision == "auto" else args.precision),
         "data": "synthetic (seeded Q1 meshes, loads, Poisson arrivals; no datasets)",
         "config": {"workload": WORKLOADS["c5"], "name": "c5", "requests": len(reqs), "rate_per_s": args.rate,
                    "slots": args.slots, "mem_budget_bytes": args.mem_budget, "precision": args.precision,
@@ -579,7 +607,7 @@ def run_serving(args):
         "latency_ms": {"p50": round(float(np.percentile(lat_a, 50)), 3),
                        "p99": round(float(np.percentile(lat_a, 99)), 3), "max": round(float(lat_a.max()), 3)},
         "converged": conv, "library_setup_s": round(lib_s, 3),
-        "sequential_fp64": {"sample": ns, "solves_per_s": round(ns / sum(ts), 3) if ts else None,
+        "sequential_fp64": {"sample": ns, "block_k": seq_k, "solves_per_s": round(ns / sum(ts), 3) if ts else None,
                             "mean_ms": round(1e3 * float(np.mean(ts)), 3) if ts else None},
     }
 
@@ -590,10 +618,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "tf32x3"],
-                    help="local-product arithmetic (default per workload: c3 tf32x3, c2 fp32)")
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "tf32x3", "auto"],
+                    help="local-product arithmetic (default per workload: c3 tf32x3, c2 fp32, c5 auto)")
     ap.add_argument("--k", type=int, default=None, help="multivector width (default per workload: c3 32, c2 8)")
-    ap.add_argument("--inner-tol", type=float, default=1e-6)
+    ap.add_argument("--inner-tol", type=float, default=0.0,
+                    help="relative tolerance of the inner solves; 0 = the library's per-precision default")
     ap.add_argument("--workload", default="c3", choices=list(WORKLOADS))
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

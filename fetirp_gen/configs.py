@@ -45,7 +45,8 @@ def elastic_grid(m: int, grid=(2, 2, 2), n_patterns: int = 1, seed: int = 0, k=N
 def config(name: str, seed: int = 0, k=None):
     """Named workloads: c1 (2D heat 8x8 pattern, 2x2 occurrences, k = 4), c2 (2D heat, 32x32 patterns with
     conductivity 1 / 1000 checkerboard over 8x8), c3 (3D elasticity, three 16^3 patterns, 4x6x8
-    occurrences with rotations), c3r (reduced c3: 4^3 patterns on 2x2x2)."""
+    occurrences with rotations), c4 (batched uneven 3D elasticity: 8^3/12^3/16^3/24^3 patterns, 256 occurrences
+    in four clamped blocks solved together), c3r (reduced c3: 4^3 patterns on 2x2x2)."""
     if name == "c1":
         return heat_grid(8, (2, 2), seed=seed, k=4 if k is None else k, name="c1_heat8_2x2")
     if name == "c2":
@@ -54,6 +55,8 @@ def config(name: str, seed: int = 0, k=None):
     if name == "c3":
         return elastic_grid(16, (4, 6, 8), n_patterns=3, seed=seed, k=32 if k is None else k,
                             name="c3_elastic16_4x6x8")
+    if name == "c4":
+        return batched_uneven(seed=seed, k_each=16 if k is None else max(1, k // 4))   # <= 64 columns in all
     if name == "c3r":
         return elastic_grid(4, (2, 2, 2), n_patterns=3, seed=seed, k=8 if k is None else k,
                             name="c3r_elastic4_2x2x2")

@@ -50,18 +50,23 @@ typedef enum {
 enum {
   FETIRP_PREC_FP64 = 0, /* plain FP64 form */
   FETIRP_PREC_FP32 = 1, /* FP32 products wrapped in FP64 outer refinement (defect correction) */
-  FETIRP_PREC_TF32X3 = 2 /* tensor cores (tcgen05 kind::tf32), operands split hi+lo, 3 products, FP32
-                            accumulation in TMEM; wrapped in FP64 outer refinement */
+  FETIRP_PREC_TF32X3 = 2, /* tensor cores (tcgen05 kind::tf32), operands split hi+lo, 3 products, FP32
+                             accumulation in TMEM; wrapped in FP64 outer refinement */
+  FETIRP_PREC_AUTO = 3    /* solves only (fetirp_options.precision): per structure, FP32 for latency-bound ones
+                             (every used pattern with n_b <= 512 and n_lambda <= 262144, which then run the
+                             persistent iteration), TF32X3 otherwise; both inside the FP64 refinement */
 };
 
 typedef struct {
-  int32_t precision;   /* FETIRP_PREC_*, default FP64 */
+  int32_t precision;   /* FETIRP_PREC_* of the solves, default FP64 */
   double tol;          /* target ||r_j|| / ||r_0||, r = P^T (d - F lambda) (the residual of Table 1); default 1e-8 */
   int32_t max_iter;    /* cap on block iterations over the whole solve; default 2000 */
   int32_t block_k;     /* multivector width k; 1 = classical FETI-CG; default 32 (clamped to the number
                           of occurrences; fetirp_set_groups overrides) */
   int32_t max_outer;   /* cap on FP64 refinement steps of the mixed forms; default 30 */
-  double inner_tol;    /* relative tolerance of each inner (low-precision) solve; default 1e-6 */
+  double inner_tol;    /* relative tolerance of each inner (low-precision) solve; 0 (the default) = 1e-6 with FP32
+                          local products and 1e-5 with TF32X3, whose operator is accurate to ~1e-6 relative (a
+                          tighter inner target than the operator's accuracy only adds stagnating iterations) */
   double pivot_tol;    /* zero pivot when pivot <= pivot_tol * original diagonal; default 1e-9 */
   double eig_trunc;    /* a direction is dropped when its normalisation pivot <= eig_trunc * largest;
                           default 1e-12 */

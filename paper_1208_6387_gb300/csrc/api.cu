@@ -1976,7 +1976,15 @@ fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_st
   const double target = ctx->opt.tol * r0;
   int budget = ctx->opt.max_iter;
   Hist H;
-  const int prec = ctx->opt.precision;
+  int prec = ctx->opt.precision;
+  if (prec == FETIRP_PREC_AUTO) {   // latency-bound structures: FP32 SIMT products (persistent); else tf32x3
+    int max_nb = 0;
+    for (size_t p = 0; p < ctx->pats.size(); ++p)
+      if (!ctx->use[p].occs.empty()) max_nb = std::max(max_nb, ctx->pats[p]->n_b);
+    prec = (max_nb <= 512 && nl <= 262144) ? FETIRP_PREC_FP32 : FETIRP_PREC_TF32X3;
+  }
+  // relative tolerance of every inner solve: the user's, or (0) one above the operator's rounding level
+  const double inner_tol = ctx->opt.inner_tol > 0.0 ? ctx->opt.inner_tol : (prec == FETIRP_PREC_TF32X3 ? 1e-5 : 1e-6);
   if (r0 > 0.0) {
     if (prec == FETIRP_PREC_FP64) {
       rn = block_orthodir<double>(ctx, FETIRP_PREC_FP64, target, rn, H, st, budget);
@@ -1985,7 +1993,7 @@ fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_st
     } else {
       // outer FP64 defect correction: inner solves on the low-precision operator reuse their directions
       for (int outer = 0; outer < ctx->opt.max_outer && rn > target && budget > 0; ++outer) {
-        const double inner_target = std::max(ctx->opt.inner_tol * rn, 0.5 * target);
+        const double inner_target = std::max(inner_tol * rn, 0.5 * target);
         if (hist_fp64(ctx)) block_orthodir<double>(ctx, prec, inner_target, rn, H, st, budget);
         else block_orthodir<float>(ctx, prec, inner_target, rn, H, st, budget);
         reproject_lambda(ctx);
@@ -2177,7 +2185,7 @@ void fetirp_default_options(fetirp_options* o) {
   o->max_iter = 2000;
   o->block_k = 32;
   o->max_outer = 30;
-  o->inner_tol = 1e-6;
+  o->inner_tol = 0.0;
   o->pivot_tol = 1e-9;
   o->eig_trunc = 1e-12;
   o->cuda_stream = nullptr;
@@ -2213,9 +2221,10 @@ fetirp_status fetirp_create(const fetirp_options* opt, fetirp_ctx* out) {
   if (opt) ctx->opt = *opt;
   else fetirp_default_options(&ctx->opt);
   const fetirp_options& o = ctx->opt;
-  if (!(o.tol > 0) || o.max_iter < 1 || o.block_k < 1 || o.max_outer < 1 || !(o.inner_tol > 0) ||
+  if (!(o.tol > 0) || o.max_iter < 1 || o.block_k < 1 || o.max_outer < 1 || !(o.inner_tol >= 0) ||
       !(o.pivot_tol > 0) || !(o.eig_trunc > 0) || !(o.eig_trunc_inner > 0) || o.check_every < 0 ||
-      (o.precision != FETIRP_PREC_FP64 && o.precision != FETIRP_PREC_FP32 && o.precision != FETIRP_PREC_TF32X3) ||
+      (o.precision != FETIRP_PREC_FP64 && o.precision != FETIRP_PREC_FP32 && o.precision != FETIRP_PREC_TF32X3 &&
+       o.precision != FETIRP_PREC_AUTO) ||
       ((o.alloc == nullptr) != (o.free == nullptr)))
     return FETIRP_EINVAL;
   int ndev = 0;

@@ -345,14 +345,19 @@ void tc_init() {
 
 void tc_gemm_tf32x3(const TcProblem& T, int* d_error, cudaStream_t s) {
   tc_init();
-  for (int base = 0; base < T.n_pat; base += TC_MAXP) {
+  // patterns with work only: a structure need not use every pattern of the context (a tensor map of an empty
+  // right-hand-side block would be invalid)
+  std::vector<int> busy;
+  for (int p = 0; p < T.n_pat; ++p)
+    if (T.n_rhs[p] > 0 && T.n_b[p] > 0) busy.push_back(p);
+  for (int base = 0; base < (int)busy.size(); base += TC_MAXP) {
     TcParams P;
     std::memset(&P, 0, sizeof(P));
-    P.n_pat = std::min(TC_MAXP, T.n_pat - base);
+    P.n_pat = std::min(TC_MAXP, (int)busy.size() - base);
     P.error = d_error;
     int total = 0;
     for (int i = 0; i < P.n_pat; ++i) {
-      const int p = base + i;
+      const int p = busy[base + i];
       make_map(&P.a_hi[i], T.S_hi[p], T.n_b[p], T.n_b[p], T.lds[p]);
       make_map(&P.a_lo[i], T.S_lo[p], T.n_b[p], T.n_b[p], T.lds[p]);
       make_map(&P.b_hi[i], T.Y_hi[p], T.n_rhs[p], T.n_b[p], T.ldy[p]);

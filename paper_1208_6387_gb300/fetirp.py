@@ -16,8 +16,9 @@ LIB_PATH = os.path.join(HERE, "lib", "libfetirp.so")
 
 FETIRP_OK, FETIRP_EINVAL, FETIRP_ENOMEM, FETIRP_ESINGULAR, FETIRP_ENOCONV, FETIRP_ECUDA, FETIRP_ESTATE, \
     FETIRP_ETIMEOUT = range(8)
-FETIRP_PREC_FP64, FETIRP_PREC_FP32, FETIRP_PREC_TF32X3 = 0, 1, 2
-PRECISIONS = {"fp64": FETIRP_PREC_FP64, "fp32": FETIRP_PREC_FP32, "tf32x3": FETIRP_PREC_TF32X3}
+FETIRP_PREC_FP64, FETIRP_PREC_FP32, FETIRP_PREC_TF32X3, FETIRP_PREC_AUTO = 0, 1, 2, 3
+PRECISIONS = {"fp64": FETIRP_PREC_FP64, "fp32": FETIRP_PREC_FP32, "tf32x3": FETIRP_PREC_TF32X3,
+              "auto": FETIRP_PREC_AUTO}
 
 
 # device allocator hooks of fetirp_options: alloc(bytes, stream, user) -> device pointer; free(ptr, user)

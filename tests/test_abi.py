@@ -48,6 +48,7 @@ def test_defaults_and_status_strings(libpath):
     import paper_1208_6387_gb300.fetirp as F
     o = F.fetirp_default_options()
     assert o.tol == 1e-8 and o.block_k == 32 and o.precision == F.FETIRP_PREC_FP64
+    assert o.inner_tol == 0.0   # per-precision inner tolerance
     assert F.lib().fetirp_status_string(4) == b"FETIRP_ENOCONV"
 
 

@@ -260,3 +260,33 @@ def test_caller_allocator_hooks():
     o.alloc = a_cb
     h = C.c_void_p()
     assert F.lib().fetirp_create(C.byref(o), C.byref(h)) == F.FETIRP_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_structure_using_part_of_the_patterns(prec):
+    """A context holding more patterns than the structure uses (a serving library): the patterns without
+    occurrences get no local product, in every precision (a tensor-core operand of zero right-hand sides is
+    skipped), and the solve matches the direct one."""
+    from fetirp_gen.mesh import heat_pattern
+    prob = CASES["heat_rot_ragged"]()
+    us_ref, lam_ref, _, _ = direct(prob)
+    ctx = F.fetirp_create(F.fetirp_default_options(precision=prec, tol=1e-12, inner_tol=1e-5, persistent=0))
+    try:
+        extra = heat_pattern(7, name="unused")
+        K = extra.K.tocsr()
+        F.fetirp_create_pattern(ctx, extra.n_nodes, 1, K.indptr, K.indices, K.data, extra.bnd_nodes, 1)   # id 0
+        pids = []
+        for pat in prob.patterns:
+            K = pat.K.tocsr()
+            pids.append(F.fetirp_create_pattern(ctx, pat.n_nodes, pat.dpn, K.indptr, K.indices, K.data,
+                                                pat.bnd_nodes, pat.kernel_dim))
+        for occ in prob.occs:
+            F.fetirp_add_occurrence(ctx, pids[occ.pattern], occ.rot.astype(float), occ.link_local_node,
+                                    occ.link_global_comp, occ.link_lambda_row, occ.link_sign, occ.f_global)
+        F.fetirp_set_groups(ctx, prob.k, prob.groups)
+        lam, u, st = F.fetirp_solve(ctx, prob.n_lambda, prob.c, F.n_u(prob))
+    finally:
+        F.fetirp_destroy(ctx)
+    assert rel(lam, lam_ref) < 1e-8
+    for a, b in zip(F.split_u(prob, u), us_ref):
+        assert rel(a, b) < 1e-8
