@@ -23,10 +23,13 @@ namespace fetirp {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 32;        // BK fp32 = 128 bytes = one swizzle row
-constexpr int STAGES = 3;
-constexpr int TILE_BYTES = BM * BK * 4;           // 16 KB (A or B tile, BM == BN)
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;       // A_hi, A_lo, B_hi, B_lo
+// 128 x 256 output tile per CTA (one MMA of M = 128, N = 256): a wider tile loads 25 % fewer operand bytes per
+// flop from L2 than a square 128 x 128 one, which the three-product split makes the limiter
+constexpr int BM = 128, BN = 256, BK = 32;        // BK fp32 = 128 bytes = one swizzle row
+constexpr int STAGES = 2;
+constexpr int TILE_A_BYTES = BM * BK * 4;         // 16 KB
+constexpr int TILE_B_BYTES = BN * BK * 4;         // 32 KB
+constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + 2 * TILE_B_BYTES;   // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // a bounded wait gives up after 2 s
 
@@ -185,9 +188,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcPa
       mbar_expect_tx(&full[s], STAGE_BYTES);
       const int kx = kb * BK;
       tma_load_2d(&P.a_hi[p], &full[s], st, kx, m0);
-      tma_load_2d(&P.a_lo[p], &full[s], st + TILE_BYTES, kx, m0);
-      tma_load_2d(&P.b_hi[p], &full[s], st + 2 * TILE_BYTES, kx, n0);
-      tma_load_2d(&P.b_lo[p], &full[s], st + 3 * TILE_BYTES, kx, n0);
+      tma_load_2d(&P.a_lo[p], &full[s], st + TILE_A_BYTES, kx, m0);
+      tma_load_2d(&P.b_hi[p], &full[s], st + 2 * TILE_A_BYTES, kx, n0);
+      tma_load_2d(&P.b_lo[p], &full[s], st + 2 * TILE_A_BYTES + TILE_B_BYTES, kx, n0);
       *n_loaded = kb + 1;
     }
   } else if (warp == 1 && lane == 0) {
@@ -206,8 +209,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcPa
       if (*abort_flag) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       uint8_t* st = smem + s * STAGE_BYTES;
-      const uint64_t ahi = smem_desc(st), alo = smem_desc(st + TILE_BYTES);
-      const uint64_t bhi = smem_desc(st + 2 * TILE_BYTES), blo = smem_desc(st + 3 * TILE_BYTES);
+      const uint64_t ahi = smem_desc(st), alo = smem_desc(st + TILE_A_BYTES);
+      const uint64_t bhi = smem_desc(st + 2 * TILE_A_BYTES), blo = smem_desc(st + 2 * TILE_A_BYTES + TILE_B_BYTES);
 #pragma unroll
       for (int kk = 0; kk < BK / 8; ++kk) {
         const uint64_t koff = (uint64_t)((kk * 8 * 4) >> 4);   // 32 bytes per K step of 8 tf32
@@ -305,13 +308,13 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2D fp32 map over a row-major (rows x cols, leading dimension ld) array; box 32 (cols) x 128 (rows).
-void make_map(CUtensorMap* m, const float* base, long long rows, long long cols, long long ld) {
+// 2D fp32 map over a row-major (rows x cols, leading dimension ld) array; box 32 (cols) x box_rows (rows).
+void make_map(CUtensorMap* m, const float* base, long long rows, long long cols, long long ld, int box_rows) {
   if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 4) % 16)
     throw Error(1, "tensor-core operand not 16-byte aligned");
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
-  cuuint32_t box[2] = {BK, 128};
+  cuuint32_t box[2] = {BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -358,10 +361,10 @@ void tc_gemm_tf32x3(const TcProblem& T, int* d_error, cudaStream_t s) {
     int total = 0;
     for (int i = 0; i < P.n_pat; ++i) {
       const int p = busy[base + i];
-      make_map(&P.a_hi[i], T.S_hi[p], T.n_b[p], T.n_b[p], T.lds[p]);
-      make_map(&P.a_lo[i], T.S_lo[p], T.n_b[p], T.n_b[p], T.lds[p]);
-      make_map(&P.b_hi[i], T.Y_hi[p], T.n_rhs[p], T.n_b[p], T.ldy[p]);
-      make_map(&P.b_lo[i], T.Y_lo[p], T.n_rhs[p], T.n_b[p], T.ldy[p]);
+      make_map(&P.a_hi[i], T.S_hi[p], T.n_b[p], T.n_b[p], T.lds[p], BM);
+      make_map(&P.a_lo[i], T.S_lo[p], T.n_b[p], T.n_b[p], T.lds[p], BM);
+      make_map(&P.b_hi[i], T.Y_hi[p], T.n_rhs[p], T.n_b[p], T.ldy[p], BN);
+      make_map(&P.b_lo[i], T.Y_lo[p], T.n_rhs[p], T.n_b[p], T.ldy[p], BN);
       P.Z[i] = T.Z[p];
       P.ldz[i] = T.ldy[p];
       P.n_b[i] = T.n_b[p];
