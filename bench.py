@@ -4,13 +4,13 @@ Workload (default): 3D elasticity, three 16^3-element Q1 cube patterns (E = 1, n
 occurrences with seeded rotations of the cube, clamped face x = 0, body force N(0,1) per dof (n_lambda =
 427,392, 1152 rigid modes).  A step is one pass of the whole method on that structure: FP64 factorisation of the
 three patterns (zero-pivot detection, kernel, S^+), coarse problem and d, block ORTHODIR with k = 32 to
-||r|| / ||r0|| <= 1e-8 (local products on the tensor cores in tf32x3 inside FP64 outer refinement), and the
+||r|| / ||r0|| <= 1e-8 (local products on the tensor cores in bf16 pairs inside FP64 outer refinement), and the
 recovery of lambda and u.  Inputs (pattern stiffness, links, loads) are resident on the device when the timed
-region starts; the operands of every step are larger than L2 (the S^dag operators alone are 0.5 GB), and L2 is
-flushed between steps as well.
+region starts; the operands of every step are larger than L2 (the S^dag operators alone are 0.25 GB in bf16
+pairs), and L2 is flushed between steps as well.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision fp64|fp32|tf32x3]
-                    [--k K] [--workload c3|c2|c1|c5]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision fp64|fp32|tf32x3|bf16x3|auto] [--k K] [--workload c3|c2|c1|c4|c5]
 
 Under torchrun (N > 1) every rank solves its own independently seeded structure (weak scaling, no collective
 on the data path); rank 0 prints the JSON line with the slowest rank's time.
@@ -44,7 +44,7 @@ WORKLOADS = {
           "6 resident patterns (2D heat 16^2/32^2/64^2, 3D elastic 8^3/12^3/16^3), admitted by device memory",
 }
 DEFAULTS = {  # per workload: local-product precision, multivector width, direction-history cap (GB; 0 = library)
-    "c3": ("tf32x3", 32, 32.0), "c2": ("fp32", 8, 0.0), "c1": ("fp64", 4, 0.0), "c5": ("auto", 32, 0.0),
+    "c3": ("bf16x3", 32, 32.0), "c2": ("fp32", 8, 0.0), "c1": ("fp64", 4, 0.0), "c5": ("auto", 32, 0.0),
     "c4": ("auto", 0, 32.0),   # k = 0: autotuned
 }
 # Block iterations of the default workload (C3, k = 32, tol 1e-8): the count the library's FP64 solve needs
@@ -384,8 +384,9 @@ def run_ours(args, rank, world, local):
 def roofline(args, prob, F, peaks, src, ph_ms, ph_fl, ph_ln, stats):
     """Roofline of the dominant kernel of the F-apply, from the library's per-launch CUDA events over the timed
     steps (events on the library's stream) and the algorithmic work of one launch.
-    tf32x3: k_tc_gemm, flops 2 sum_p n_b^2 R_p per launch (useful; three tf32 products are issued for each)
-    against the tf32 tensor peak = the measured sustained bf16 rate x 1.1 / 2.25 (nominal tf32 / bf16 ratio).
+    tf32x3 / bf16x3: k_tc_gemm, flops 2 sum_p n_b^2 R_p per launch (useful; three products are issued for each)
+    against the tensor peak of the operand type: the measured sustained bf16 rate (bf16x3), times 1.1 / 2.25
+    (the nominal tf32 / bf16 ratio) for tf32x3.
     Persistent iteration (FP32 / FP64 SIMT, latency-bound structures): k_persist, the F-apply bytes of every
     block iteration in the launch against the measured HBM copy rate."""
     loc, itp = F.PHASES.index("local"), F.PHASES.index("iterate")
@@ -408,6 +409,10 @@ def roofline(args, prob, F, peaks, src, ph_ms, ph_fl, ph_ln, stats):
         kern, bound = "k_tc_gemm (tcgen05 kind::tf32, 3 products)", "tensor"
         peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * 1.1 / 2.25
         note = f"tf32 tensor: bf16_tflops_sustained of {src} x 1.1/2.25 (nominal tf32/bf16 ratio)"
+    elif args.fprec == "bf16x3":
+        kern, bound = "k_tc_gemm (tcgen05 kind::f16, bf16 operands, 3 products)", "tensor"
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        note = f"bf16 tensor: bf16_tflops_sustained of {src}"
     elif args.fprec == "fp32":
         kern, bound, peak = "k_local_gemm<float>", "alu", FP32_PEAK_TFLOPS
         note = "FP32 SIMT peak derived from 152 SMs x 128 lanes x 2070 MHz"
@@ -418,7 +423,7 @@ def roofline(args, prob, F, peaks, src, ph_ms, ph_fl, ph_ln, stats):
            "unit": "TFLOP/s", "frac": round(achieved / peak, 5), "traffic": None,
            "flops_per_launch": flops_per_launch, "launches": int(ph_ln[loc]), "ms_per_launch": round(per_launch_ms, 4),
            "peak_source": note, "work": "2 sum_p n_b^2 R_p per launch (R_p = occurrences of p x k)"}
-    if args.fprec == "tf32x3":
+    if args.fprec in ("tf32x3", "bf16x3"):
         out["issued_frac"] = round(3 * achieved / peak, 4)
     return out
 
@@ -618,8 +623,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "tf32x3", "auto"],
-                    help="local-product arithmetic (default per workload: c3 tf32x3, c2 fp32, c5 auto)")
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "tf32x3", "bf16x3", "auto"],
+                    help="local-product arithmetic (default per workload: c3 bf16x3, c2 fp32, c4/c5 auto)")
     ap.add_argument("--k", type=int, default=None, help="multivector width (default per workload: c3 32, c2 8)")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="relative tolerance of the inner solves; 0 = the library's per-precision default")

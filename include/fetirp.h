@@ -52,9 +52,14 @@ enum {
   FETIRP_PREC_FP32 = 1, /* FP32 products wrapped in FP64 outer refinement (defect correction) */
   FETIRP_PREC_TF32X3 = 2, /* tensor cores (tcgen05 kind::tf32), operands split hi+lo, 3 products, FP32
                              accumulation in TMEM; wrapped in FP64 outer refinement */
-  FETIRP_PREC_AUTO = 3    /* solves only (fetirp_options.precision): per structure, FP32 for latency-bound ones
+  FETIRP_PREC_AUTO = 3,   /* solves only (fetirp_options.precision): per structure, FP32 for latency-bound ones
                              (every used pattern with n_b <= 512 and n_lambda <= 262144, which then run the
                              persistent iteration), TF32X3 otherwise; both inside the FP64 refinement */
+  FETIRP_PREC_BF16X3 = 4  /* tensor cores (tcgen05 kind::f16 with bf16 operands, twice the tf32 rate), operands
+                             split into bf16 pairs (16 significant bits), 3 products, FP32 accumulation in TMEM;
+                             operator accurate to ~1e-5 relative; wrapped in FP64 outer refinement.  Rotations of
+                             vector fields in 90-degree steps only; not taken by fetirp_apply_split or
+                             fetirp_apply_block_device_noalloc */
 };
 
 typedef struct {
@@ -65,8 +70,8 @@ typedef struct {
                           of occurrences; fetirp_set_groups overrides) */
   int32_t max_outer;   /* cap on FP64 refinement steps of the mixed forms; default 30 */
   double inner_tol;    /* relative tolerance of each inner (low-precision) solve; 0 (the default) = 1e-6 with FP32
-                          local products and 1e-5 with TF32X3, whose operator is accurate to ~1e-6 relative (a
-                          tighter inner target than the operator's accuracy only adds stagnating iterations) */
+                          local products, 1e-5 with TF32X3 and 1e-4 with BF16X3, each above the operator's
+                          accuracy (a tighter inner target only adds stagnating iterations) */
   double pivot_tol;    /* zero pivot when pivot <= pivot_tol * original diagonal; default 1e-9 */
   double eig_trunc;    /* a direction is dropped when its normalisation pivot <= eig_trunc * largest;
                           default 1e-12 */

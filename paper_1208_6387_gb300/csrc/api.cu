@@ -110,6 +110,9 @@ struct PatternData {
   }
   DBuf<float> S32, S_hi, S_lo;   // FP32 S^+ and its tf32 pair (leading dimension lds)
   long long lds = 0;
+  DBuf<__nv_bfloat16> Sb_hi, Sb_lo;   // bf16 pair of S^dag (leading dimension ldsb, a multiple of 8)
+  long long ldsb = 0;
+  long long ld_y8 = 0;                // Y/Z leading dimension of the bf16 products (round_up(n_b, 8))
   long long ld_y = 0;          // Y/Z leading dimension (round_up(n_b, 4))
 };
 
@@ -399,6 +402,11 @@ void collect_phases(fetirp_ctx ctx, fetirp_stats& st) {
   }
 }
 
+// Arithmetic forms of the block operator (the solve's AUTO choice is not one)
+bool operator_precision(int p) {
+  return p == FETIRP_PREC_FP64 || p == FETIRP_PREC_FP32 || p == FETIRP_PREC_TF32X3 || p == FETIRP_PREC_BF16X3;
+}
+
 #define REQUIRE(cond, msg) \
   do {                     \
     if (!(cond)) throw Error(FETIRP_EINVAL, msg); \
@@ -520,6 +528,11 @@ void factor_stage_b(PatternData& P, cudaStream_t s) {
   P.S_hi.ensure((size_t)nb * P.lds);
   P.S_lo.ensure((size_t)nb * P.lds);
   split_tf32(Sdag, nb, nb, nb, P.S_hi.p, P.S_lo.p, P.lds, s);
+  P.ldsb = round_up(nb, 8);
+  P.ld_y8 = P.ldsb;
+  P.Sb_hi.ensure((size_t)nb * P.ldsb);
+  P.Sb_lo.ensure((size_t)nb * P.ldsb);
+  split_bf16(Sdag, nb, nb, nb, P.Sb_hi.p, P.Sb_lo.p, P.ldsb, s);
 }
 
 void factorize_patterns(fetirp_ctx ctx, const std::vector<PatternData*>& pats) {
@@ -598,8 +611,12 @@ void precond_setup(fetirp_ctx ctx);
 
 // Local-product buffers for a block of k columns in every precision (allocated before any graph capture).
 void ensure_apply_buffers(fetirp_ctx ctx, int k) {
-  long long total = 0;
-  for (size_t p = 0; p < ctx->pats.size(); ++p) total += (long long)ctx->use[p].occs.size() * k * ctx->pats[p]->ld_y;
+  long long total = 0, total8 = 0;
+  for (size_t p = 0; p < ctx->pats.size(); ++p) {
+    total += (long long)ctx->use[p].occs.size() * k * ctx->pats[p]->ld_y;
+    total8 += (long long)ctx->use[p].occs.size() * k * ctx->pats[p]->ld_y8;
+  }
+  total = std::max(total, total8);   // the bf16 products use the FP32 buffers with leading dimension ld_y8
   ctx->Y64.ensure(total); ctx->Z64.ensure(total);
   ctx->Y32.ensure(total); ctx->Z32.ensure(total); ctx->Ylo32.ensure(total);
 }
@@ -1190,6 +1207,47 @@ void apply_F(fetirp_ctx ctx, const double* in, double* out, int k, int prec, boo
       rotate_traces<float>(L, Zv, k, false, s);
       scatter<float>(L, Zv, k, 0.0, out, s);
     }
+  } else if (prec == FETIRP_PREC_BF16X3) {
+    if (L.n_gen > 0)
+      throw Error(FETIRP_EINVAL, "bf16x3 takes rotations of vector fields in 90-degree steps only");
+    long long total8 = 0;
+    std::vector<long long> base8(n_pat);
+    for (int p = 0; p < n_pat; ++p) {
+      base8[p] = total8;
+      total8 += (long long)ctx->use[p].occs.size() * k * ctx->pats[p]->ld_y8;
+    }
+    ctx->Y32.ensure(total8); ctx->Ylo32.ensure(total8); ctx->Z32.ensure(total8);
+    if (!ctx->tc_error.p) { ctx->tc_error.alloc(1); ctx->tc_error.zero(s); }
+    PatView<__nv_bfloat16> Yh{}, Yl{};
+    PatView<float> Zv{};
+    TcProblem T;
+    T.n_pat = n_pat;
+    double flops = 0, bytes = 0, rhs_elems = 0;
+    for (int p = 0; p < n_pat; ++p) {
+      PatternData& P = *ctx->pats[p];
+      Yh.base[p] = reinterpret_cast<__nv_bfloat16*>(ctx->Y32.p) + base8[p]; Yh.ld[p] = P.ld_y8; Yh.off[p] = 0;
+      Yl.base[p] = reinterpret_cast<__nv_bfloat16*>(ctx->Ylo32.p) + base8[p]; Yl.ld[p] = P.ld_y8; Yl.off[p] = 0;
+      Zv.base[p] = ctx->Z32.p + base8[p]; Zv.ld[p] = P.ld_y8; Zv.off[p] = 0;
+      T.S_hi[p] = P.Sb_hi.p; T.S_lo[p] = P.Sb_lo.p; T.lds[p] = P.ldsb;
+      T.Y_hi[p] = Yh.base[p]; T.Y_lo[p] = Yl.base[p]; T.Z[p] = Zv.base[p]; T.ldy[p] = P.ld_y8;
+      T.n_b[p] = P.n_b; T.n_rhs[p] = (int)ctx->use[p].occs.size() * k;
+      flops += 2.0 * P.n_b * (double)P.n_b * T.n_rhs[p];
+      bytes += 2.0 * P.n_b * (double)P.n_b * 2 + 2.0 * P.n_b * (double)T.n_rhs[p] * 2 + 4.0 * P.n_b * T.n_rhs[p];
+      rhs_elems += (double)P.n_b * T.n_rhs[p];
+    }
+    const double vbytes = 8.0 * L.n_lambda * k;
+    {
+      PhaseScope ph(ctx, FETIRP_PHASE_GATHER, 0.0, vbytes + 2.0 * rhs_elems * 2);
+      gather_split_bf16(L, src, k, Yh, Yl, s);
+    }
+    {
+      PhaseScope ph(ctx, FETIRP_PHASE_LOCAL, flops, bytes);
+      tc_gemm_bf16x3(T, ctx->tc_error.p, s);
+    }
+    {
+      PhaseScope ph(ctx, FETIRP_PHASE_SCATTER, 0.0, vbytes + rhs_elems * 4);
+      scatter<float>(L, Zv, k, 0.0, out, s);
+    }
   } else {
     throw Error(FETIRP_EINVAL, "unsupported precision");
   }
@@ -1564,7 +1622,8 @@ void account_iteration(fetirp_ctx ctx, int prec, long long a, double es, bool pe
   B[FETIRP_PHASE_UPDATE] += 8.0 * nl * (3.0 * k + 4.0) + 2.0 * es * nl * k;
   F[FETIRP_PHASE_PROJECT] += 2.0 * (2.0 * nG * nG * k + 4.0 * ctx->n_gcoef * k);
   B[FETIRP_PHASE_PROJECT] += 2.0 * (16.0 * nl * k + 8.0 * nG * nG);
-  const double e_loc = prec == FETIRP_PREC_FP64 ? 8.0 : 4.0;
+  const double e_loc = prec == FETIRP_PREC_FP64 ? 8.0 : prec == FETIRP_PREC_BF16X3 ? 2.0 : 4.0;
+  const bool pair = prec == FETIRP_PREC_TF32X3 || prec == FETIRP_PREC_BF16X3;   // operands as hi/lo pairs
   const double kf = ctx->perm.on && ctx->perm.shortcut ? 1.0 : k;   // columns of the iteration's F-apply
   if (kf != k) {   // periodic shortcut: one more history pass (Q -= Q_h C) and one more permuted copy
     F[FETIRP_PHASE_REORTH] += 2.0 * nl * a * k;
@@ -1575,11 +1634,11 @@ void account_iteration(fetirp_ctx ctx, int prec, long long a, double es, bool pe
     const PatternData* P = ctx->pats[pi].get();
     const double R = (double)ctx->use[pi].occs.size() * kf;
     F[FETIRP_PHASE_LOCAL] += 2.0 * P->n_b * (double)P->n_b * R;
-    B[FETIRP_PHASE_LOCAL] += (prec == FETIRP_PREC_TF32X3 ? 2.0 : 1.0) * e_loc * P->n_b * (double)P->n_b +
+    B[FETIRP_PHASE_LOCAL] += (pair ? 2.0 : 1.0) * e_loc * P->n_b * (double)P->n_b +
                              (prec == FETIRP_PREC_TF32X3 ? 3.0 : 2.0) * e_loc * P->n_b * R;
     rhs += P->n_b * R;
   }
-  B[FETIRP_PHASE_GATHER] += 8.0 * nl * kf + (prec == FETIRP_PREC_TF32X3 ? 2.0 : 1.0) * e_loc * rhs;
+  B[FETIRP_PHASE_GATHER] += 8.0 * nl * kf + (pair ? 2.0 : 1.0) * e_loc * rhs;
   B[FETIRP_PHASE_SCATTER] += 8.0 * nl * kf + e_loc * rhs;
   if (persistent) {   // the whole iteration ran in one launch: its work is also that of the iterate phase
     double f1 = 0.0, b1 = 0.0;
@@ -1984,7 +2043,10 @@ fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_st
     prec = (max_nb <= 512 && nl <= 262144) ? FETIRP_PREC_FP32 : FETIRP_PREC_TF32X3;
   }
   // relative tolerance of every inner solve: the user's, or (0) one above the operator's rounding level
-  const double inner_tol = ctx->opt.inner_tol > 0.0 ? ctx->opt.inner_tol : (prec == FETIRP_PREC_TF32X3 ? 1e-5 : 1e-6);
+  const double inner_tol = ctx->opt.inner_tol > 0.0   ? ctx->opt.inner_tol
+                           : prec == FETIRP_PREC_BF16X3 ? 1e-4
+                           : prec == FETIRP_PREC_TF32X3 ? 1e-5
+                                                        : 1e-6;
   if (r0 > 0.0) {
     if (prec == FETIRP_PREC_FP64) {
       rn = block_orthodir<double>(ctx, FETIRP_PREC_FP64, target, rn, H, st, budget);
@@ -2223,8 +2285,7 @@ fetirp_status fetirp_create(const fetirp_options* opt, fetirp_ctx* out) {
   const fetirp_options& o = ctx->opt;
   if (!(o.tol > 0) || o.max_iter < 1 || o.block_k < 1 || o.max_outer < 1 || !(o.inner_tol >= 0) ||
       !(o.pivot_tol > 0) || !(o.eig_trunc > 0) || !(o.eig_trunc_inner > 0) || o.check_every < 0 ||
-      (o.precision != FETIRP_PREC_FP64 && o.precision != FETIRP_PREC_FP32 && o.precision != FETIRP_PREC_TF32X3 &&
-       o.precision != FETIRP_PREC_AUTO) ||
+      !(operator_precision(o.precision) || o.precision == FETIRP_PREC_AUTO) ||
       ((o.alloc == nullptr) != (o.free == nullptr)))
     return FETIRP_EINVAL;
   int ndev = 0;
@@ -2514,7 +2575,7 @@ fetirp_status fetirp_apply_block_device(fetirp_ctx ctx, int32_t k, const double*
     if (!ctx->prepared) throw Error(FETIRP_ESTATE, "call fetirp_prepare or fetirp_solve first");
     REQUIRE(k >= 1 && k <= 64, "k must be in 1..64");
     REQUIRE(d_V && d_Q, "NULL buffer");
-    REQUIRE(precision >= FETIRP_PREC_FP64 && precision <= FETIRP_PREC_TF32X3, "unsupported precision");
+    REQUIRE(operator_precision(precision), "unsupported precision");
     apply_F(ctx, d_V, d_Q, k, precision, true, true);
     return FETIRP_OK;
   });
@@ -2525,7 +2586,7 @@ fetirp_status fetirp_apply_block(fetirp_ctx ctx, int32_t k, const double* V, dou
     if (!ctx->prepared) throw Error(FETIRP_ESTATE, "call fetirp_prepare or fetirp_solve first");
     REQUIRE(k >= 1 && k <= 64, "k must be in 1..64");
     REQUIRE(V && Q, "NULL buffer");
-    REQUIRE(precision >= FETIRP_PREC_FP64 && precision <= FETIRP_PREC_TF32X3, "unsupported precision");
+    REQUIRE(operator_precision(precision), "unsupported precision");
     const size_t n = (size_t)ctx->L.n_lambda * k;
     DBuf<double> dv(n), dq(n);
     dv.upload(V, n, ctx->stream);

@@ -290,7 +290,9 @@ __global__ void __launch_bounds__(128) k_gtg(Layout L, const int* __restrict__ p
 // written column by column (pattern frame, Eq. 9 blocked storage), coalesced over the slots.  Per slot the
 // links are added in CSR order, as the plain definition does.
 constexpr int GT_SLOTS = 64, GT_LINKS = 512;
-template <typename TO, bool SPLIT>   // SPLIT: FP32 value split into a tf32 pair, hi -> Y, lo -> Y2
+// SPLIT 0: plain; 1: FP32 value split into a tf32 pair (TO = float); 2: split into a bf16 pair (TO = bf16),
+// hi -> Y, lo -> Y2
+template <typename TO, int SPLIT>
 __global__ void __launch_bounds__(256) k_gather_tile(Layout L, const double* __restrict__ V, int k, PatView<TO> Y,
                                                      PatView<TO> Y2, double alpha, double beta) {
   __shared__ int sptr[GT_SLOTS + 1];
@@ -353,12 +355,17 @@ __global__ void __launch_bounds__(256) k_gather_tile(Layout L, const double* __r
     const int g = idx / GT_SLOTS, jl = idx % GT_SLOTS;
     if (jl >= ns) continue;
     const long long o = ((long long)q * k + g) * ld + off + jl;
-    if (SPLIT) {
+    if constexpr (SPLIT == 1) {
       const float v = (float)tile[jl][g];
       uint32_t h;
       asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
       Y.base[p][o] = (TO)__uint_as_float(h);
       Y2.base[p][o] = (TO)(v - __uint_as_float(h));
+    } else if constexpr (SPLIT == 2) {
+      const float v = (float)tile[jl][g];
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      Y.base[p][o] = (TO)h;
+      Y2.base[p][o] = (TO)__float2bfloat16_rn(v - __bfloat162float(h));
     } else {
       TO* y = Y.base[p] + o;
       *y = (TO)((beta == 0.0 ? 0.0 : beta * (double)*y) + alpha * tile[jl][g]);
@@ -602,7 +609,7 @@ void gather(const Layout& L, const double* V, int k, const PatView<TO>& Y, cudaS
             double beta) {
   if (L.n_occ == 0) return;
   if (k > 64) throw Error(1, "k > 64");
-  k_gather_tile<TO, false><<<dim3(L.n_occ, ceil_div(max_slots(L), GT_SLOTS)), 256, 0, s>>>(L, V, k, Y, Y, alpha,
+  k_gather_tile<TO, 0><<<dim3(L.n_occ, ceil_div(max_slots(L), GT_SLOTS)), 256, 0, s>>>(L, V, k, Y, Y, alpha,
                                                                                             beta);
   FETIRP_LAUNCH_CHECK();
 }
@@ -619,7 +626,7 @@ void gather_split(const Layout& L, const double* V, int k, const PatView<float>&
                   cudaStream_t s) {
   if (L.n_occ == 0) return;
   if (k > 64) throw Error(1, "k > 64");
-  k_gather_tile<float, true><<<dim3(L.n_occ, ceil_div(max_slots(L), GT_SLOTS)), 256, 0, s>>>(L, V, k, Yh, Yl, 1.0,
+  k_gather_tile<float, 1><<<dim3(L.n_occ, ceil_div(max_slots(L), GT_SLOTS)), 256, 0, s>>>(L, V, k, Yh, Yl, 1.0,
                                                                                              0.0);
   FETIRP_LAUNCH_CHECK();
 }
@@ -665,6 +672,15 @@ void rotate_split(const Layout& L, const PatView<float>& Yh, const PatView<float
   if (L.n_gen == 0) return;
   const dim3 grid((unsigned)ceil_div((long long)max_nodes(L) * k, 256), L.n_gen);
   k_rotate_traces<float, 2><<<grid, 256, 0, s>>>(L, Yh, Yl, k);
+  FETIRP_LAUNCH_CHECK();
+}
+
+void gather_split_bf16(const Layout& L, const double* V, int k, const PatView<__nv_bfloat16>& Yh,
+                       const PatView<__nv_bfloat16>& Yl, cudaStream_t s) {
+  if (L.n_occ == 0) return;
+  if (k > 64) throw Error(1, "k > 64");
+  k_gather_tile<__nv_bfloat16, 2><<<dim3(L.n_occ, ceil_div(max_slots(L), GT_SLOTS)), 256, 0, s>>>(L, V, k, Yh, Yl,
+                                                                                                   1.0, 0.0);
   FETIRP_LAUNCH_CHECK();
 }
 

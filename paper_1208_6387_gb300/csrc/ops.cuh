@@ -1,5 +1,7 @@
 // Device layout of one structure and the interface operators of the hot path.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace fetirp {
@@ -106,6 +108,9 @@ void rotate_split(const Layout& L, const PatView<float>& Yh, const PatView<float
 // Yh and Yl share leading dimensions and offsets.
 void gather_split(const Layout& L, const double* V, int k, const PatView<float>& Yh, const PatView<float>& Yl,
                   cudaStream_t s);
+// As gather_split with a bf16 pair (hi = bf16(y), lo = bf16(y - hi)) for the bf16 tensor-core product.
+void gather_split_bf16(const Layout& L, const double* V, int k, const PatView<__nv_bfloat16>& Yh,
+                       const PatView<__nv_bfloat16>& Yl, cudaStream_t s);
 // out[row][g] = beta * out[row][g] + sum over the row's slots: sign * Z(slot, g)
 template <typename TI>
 void scatter(const Layout& L, const PatView<TI>& Z, int k, double beta, double* out, cudaStream_t s);

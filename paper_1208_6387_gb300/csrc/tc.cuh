@@ -1,18 +1,21 @@
 // Tensor-core (tcgen05) local products; see tc_gemm.cu.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace fetirp {
 
 constexpr int TC_MAXP = 4;   // patterns per launch (tensor maps travel as kernel parameters)
 
+// Operands are tf32 pairs (FP32 arrays) or bf16 pairs (bf16 arrays); leading dimensions in elements, 16-byte rows.
 struct TcProblem {
   int n_pat = 0;
-  const float* S_hi[16];   // n_b x n_b, leading dimension lds (multiple of 4), tf32-rounded high part
-  const float* S_lo[16];   // S - S_hi
+  const void* S_hi[16];    // n_b x n_b, leading dimension lds, rounded high part
+  const void* S_lo[16];    // S - S_hi, rounded
   long long lds[16];
-  const float* Y_hi[16];   // n_rhs x n_b (K contiguous), leading dimension ldy (multiple of 4)
-  const float* Y_lo[16];
+  const void* Y_hi[16];    // n_rhs x n_b (K contiguous), leading dimension ldy
+  const void* Y_lo[16];
   float* Z[16];            // n_rhs x n_b, leading dimension ldy
   long long ldy[16];
   int n_b[16];
@@ -22,10 +25,15 @@ struct TcProblem {
 // Z = (S_hi + S_lo)(Y_hi + Y_lo) without the lo*lo term, FP32 accumulation in TMEM.  d_error: device int
 // that receives a nonzero code if a bounded wait inside the kernel expired (0 otherwise).
 void tc_gemm_tf32x3(const TcProblem& T, int* d_error, cudaStream_t s);
+// The same with bf16 pairs (kind::f16: twice the tf32 tensor rate, 16 significant bits per pair).
+void tc_gemm_bf16x3(const TcProblem& T, int* d_error, cudaStream_t s);
 
 // One-time kernel attribute set-up (large dynamic shared memory); call before any graph capture.
 void tc_init();
 
+// hi = bf16(x), lo = bf16(x - hi) (round to nearest); x is FP64, outputs bf16 with leading dimension ld_out.
+void split_bf16(const double* x, long long rows, long long cols, long long ld_in, __nv_bfloat16* hi,
+                __nv_bfloat16* lo, long long ld_out, cudaStream_t s);
 // hi = tf32(x) (round to nearest), lo = x - hi; x is FP64, outputs FP32 with leading dimension ld_out.
 void split_tf32(const double* x, long long rows, long long cols, long long ld_in, float* hi, float* lo,
                 long long ld_out, cudaStream_t s);

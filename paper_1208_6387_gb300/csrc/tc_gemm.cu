@@ -1,12 +1,14 @@
-// Tensor-core local products Z_p = S_p^+ Y_p on sm_103a: tcgen05.mma kind::tf32 with the accumulator in
-// TMEM, operands staged by TMA (128-byte swizzle) through a 3-stage mbarrier pipeline.
+// Tensor-core local products Z_p = S_p^+ Y_p on sm_103a: tcgen05.mma (kind::tf32, or kind::f16 with bf16
+// operands) with the accumulator in TMEM, operands staged by TMA (128-byte swizzle) through a 2-stage mbarrier
+// pipeline.
 //
-// Precision: both operands are split into tf32 pairs, x = hi + lo with hi = tf32(x) and lo = x - hi, and
-// the product is taken as hi*hi + hi*lo + lo*hi (three MMAs into one FP32 accumulator).  The dropped lo*lo
-// term and the truncation of lo to tf32 leave a relative error near 2^-21 per product, close to FP32 local
-// products, which the FP64 outer refinement of the solver then removes.
+// Precision: both operands are split into pairs, x = hi + lo with hi = round(x) to the operand type and
+// lo = x - hi rounded again, and the product is taken as hi*hi + hi*lo + lo*hi (three MMAs into one FP32
+// accumulator).  tf32 pairs carry ~22 significant bits (relative error near 2^-21 per product, close to FP32
+// local products); bf16 pairs carry 16 (near 2^-16, at twice the tensor rate of tf32).  The FP64 outer
+// refinement of the solver removes either error.
 //
-// One CTA computes a 128 (rows of S^+) x 128 (right-hand sides) tile of one pattern.  Warp roles: warp 0
+// One CTA computes a 128 (rows of S^+) x 256 (right-hand sides) tile of one pattern.  Warp roles: warp 0
 // lane 0 issues TMA loads, warp 1 lane 0 issues the MMAs, all four warps drain TMEM in the epilogue.  Every
 // wait on an mbarrier is bounded: on expiry the CTA records an error code, stops issuing work, waits (again
 // bounded) for its own MMAs to retire, frees TMEM and returns.
@@ -25,10 +27,11 @@ namespace {
 
 // 128 x 256 output tile per CTA (one MMA of M = 128, N = 256): a wider tile loads 25 % fewer operand bytes per
 // flop from L2 than a square 128 x 128 one, which the three-product split makes the limiter
-constexpr int BM = 128, BN = 256, BK = 32;        // BK fp32 = 128 bytes = one swizzle row
+constexpr int BM = 128, BN = 256;
+constexpr int ROW_BYTES = 128;                    // one K step of a tile row = one 128-byte swizzle row
 constexpr int STAGES = 2;
-constexpr int TILE_A_BYTES = BM * BK * 4;         // 16 KB
-constexpr int TILE_B_BYTES = BN * BK * 4;         // 32 KB
+constexpr int TILE_A_BYTES = BM * ROW_BYTES;      // 16 KB
+constexpr int TILE_B_BYTES = BN * ROW_BYTES;      // 32 KB
 constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + 2 * TILE_B_BYTES;   // A_hi, A_lo, B_hi, B_lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // a bounded wait gives up after 2 s
@@ -92,12 +95,13 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p) {
   return d;
 }
 
-// Instruction descriptor: D f32, A/B tf32, both K-major, N = BN, M = BM.
+// Instruction descriptor: D f32, A/B tf32 (kind::tf32) or bf16 (kind::f16), both K-major, N = BN, M = BM.
+template <bool BF16>
 __device__ __forceinline__ uint32_t instr_desc() {
   uint32_t d = 0;
-  d |= 1u << 4;                    // D format f32
-  d |= 2u << 7;                    // A format tf32
-  d |= 2u << 10;                   // B format tf32
+  d |= 1u << 4;                          // D format f32
+  d |= (BF16 ? 1u : 2u) << 7;            // A format: bf16 (kind::f16) or tf32
+  d |= (BF16 ? 1u : 2u) << 10;           // B format
   d |= (uint32_t)(BN >> 3) << 17;  // N / 8
   d |= (uint32_t)(BM >> 4) << 24;  // M / 16
   return d;
@@ -109,6 +113,14 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
       ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
@@ -131,7 +143,11 @@ struct TcParams {
 
 }  // namespace
 
+// BF16: operands are bf16 pairs (kind::f16, K = 16 per MMA, 64 per 128-byte row), else tf32 pairs
+// (kind::tf32, K = 8 per MMA, 32 per row); either way four MMAs of 32 bytes of K cover one row.
+template <bool BF16>
 __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcParams P) {
+  constexpr int BK = ROW_BYTES / (BF16 ? 2 : 4);   // K elements per stage
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -195,7 +211,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcPa
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    const uint32_t idesc = instr_desc();
+    const uint32_t idesc = instr_desc<BF16>();
     int issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
@@ -212,11 +228,17 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcPa
       const uint64_t ahi = smem_desc(st), alo = smem_desc(st + TILE_A_BYTES);
       const uint64_t bhi = smem_desc(st + 2 * TILE_A_BYTES), blo = smem_desc(st + 2 * TILE_A_BYTES + TILE_B_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < BK / 8; ++kk) {
-        const uint64_t koff = (uint64_t)((kk * 8 * 4) >> 4);   // 32 bytes per K step of 8 tf32
-        mma_tf32(tmem, ahi + koff, bhi + koff, idesc, (kb | kk) ? 1u : 0u);
-        mma_tf32(tmem, ahi + koff, blo + koff, idesc, 1u);
-        mma_tf32(tmem, alo + koff, bhi + koff, idesc, 1u);
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t koff = (uint64_t)((kk * 32) >> 4);   // 32 bytes per MMA: 8 tf32 or 16 bf16 of K
+        if (BF16) {
+          mma_f16(tmem, ahi + koff, bhi + koff, idesc, (kb | kk) ? 1u : 0u);
+          mma_f16(tmem, ahi + koff, blo + koff, idesc, 1u);
+          mma_f16(tmem, alo + koff, bhi + koff, idesc, 1u);
+        } else {
+          mma_tf32(tmem, ahi + koff, bhi + koff, idesc, (kb | kk) ? 1u : 0u);
+          mma_tf32(tmem, ahi + koff, blo + koff, idesc, 1u);
+          mma_tf32(tmem, alo + koff, bhi + koff, idesc, 1u);
+        }
       }
       mma_commit(&empty[s]);   // frees the stage once these MMAs have read it
       ++issued;
@@ -308,15 +330,18 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2D fp32 map over a row-major (rows x cols, leading dimension ld) array; box 32 (cols) x box_rows (rows).
-void make_map(CUtensorMap* m, const float* base, long long rows, long long cols, long long ld, int box_rows) {
-  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 4) % 16)
+// 2D map over a row-major (rows x cols, leading dimension ld) array of fp32 (esize 4) or bf16 (esize 2); box of
+// one 128-byte row of K (32 or 64 elements) x box_rows rows.
+void make_map(CUtensorMap* m, const void* base, long long rows, long long cols, long long ld, int box_rows,
+              int esize) {
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * esize) % 16)
     throw Error(1, "tensor-core operand not 16-byte aligned");
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
-  cuuint32_t box[2] = {BK, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * esize)};
+  cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / esize), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+  CUresult r = encode_fn()(m, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                           const_cast<void*>(base), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Error(5, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
@@ -340,14 +365,17 @@ void tc_init() {
   FETIRP_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) throw Error(1, "device ordinal out of range");
   if (!attr_done[dev]) {
-    FETIRP_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    FETIRP_CUDA(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    FETIRP_CUDA(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     attr_done[dev] = true;
   }
   encode_fn();   // resolve the driver entry point outside any stream capture
 }
 
-void tc_gemm_tf32x3(const TcProblem& T, int* d_error, cudaStream_t s) {
+namespace {
+void tc_gemm_split(const TcProblem& T, bool bf16, int* d_error, cudaStream_t s) {
   tc_init();
+  const int es = bf16 ? 2 : 4;
   // patterns with work only: a structure need not use every pattern of the context (a tensor map of an empty
   // right-hand-side block would be invalid)
   std::vector<int> busy;
@@ -361,10 +389,10 @@ void tc_gemm_tf32x3(const TcProblem& T, int* d_error, cudaStream_t s) {
     int total = 0;
     for (int i = 0; i < P.n_pat; ++i) {
       const int p = busy[base + i];
-      make_map(&P.a_hi[i], T.S_hi[p], T.n_b[p], T.n_b[p], T.lds[p], BM);
-      make_map(&P.a_lo[i], T.S_lo[p], T.n_b[p], T.n_b[p], T.lds[p], BM);
-      make_map(&P.b_hi[i], T.Y_hi[p], T.n_rhs[p], T.n_b[p], T.ldy[p], BN);
-      make_map(&P.b_lo[i], T.Y_lo[p], T.n_rhs[p], T.n_b[p], T.ldy[p], BN);
+      make_map(&P.a_hi[i], T.S_hi[p], T.n_b[p], T.n_b[p], T.lds[p], BM, es);
+      make_map(&P.a_lo[i], T.S_lo[p], T.n_b[p], T.n_b[p], T.lds[p], BM, es);
+      make_map(&P.b_hi[i], T.Y_hi[p], T.n_rhs[p], T.n_b[p], T.ldy[p], BN, es);
+      make_map(&P.b_lo[i], T.Y_lo[p], T.n_rhs[p], T.n_b[p], T.ldy[p], BN, es);
       P.Z[i] = T.Z[p];
       P.ldz[i] = T.ldy[p];
       P.n_b[i] = T.n_b[p];
@@ -375,9 +403,38 @@ void tc_gemm_tf32x3(const TcProblem& T, int* d_error, cudaStream_t s) {
     }
     P.tile_off[P.n_pat] = total;
     if (total == 0) continue;
-    k_tc_gemm<<<total, 128, SMEM_BYTES, s>>>(P);
+    if (bf16) k_tc_gemm<true><<<total, 128, SMEM_BYTES, s>>>(P);
+    else k_tc_gemm<false><<<total, 128, SMEM_BYTES, s>>>(P);
     FETIRP_LAUNCH_CHECK();
   }
+}
+}  // namespace
+
+void tc_gemm_tf32x3(const TcProblem& T, int* d_error, cudaStream_t s) { tc_gemm_split(T, false, d_error, s); }
+void tc_gemm_bf16x3(const TcProblem& T, int* d_error, cudaStream_t s) { tc_gemm_split(T, true, d_error, s); }
+
+// hi = bf16(x) (round to nearest), lo = bf16(x - hi); x is FP64, outputs bf16 with leading dimension ld_out
+__global__ void k_split_bf16(const double* __restrict__ x, long long rows, long long cols, long long ld_in,
+                             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long ld_out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * ld_out) return;
+  const long long r = idx / ld_out, c = idx % ld_out;
+  float h = 0.f, l = 0.f;
+  if (c < cols) {
+    const float v = (float)x[r * ld_in + c];
+    h = __bfloat162float(__float2bfloat16_rn(v));
+    l = v - h;
+  }
+  hi[idx] = __float2bfloat16_rn(h);
+  lo[idx] = __float2bfloat16_rn(l);
+}
+
+void split_bf16(const double* x, long long rows, long long cols, long long ld_in, __nv_bfloat16* hi,
+                __nv_bfloat16* lo, long long ld_out, cudaStream_t s) {
+  const long long n = rows * ld_out;
+  if (n == 0) return;
+  k_split_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, rows, cols, ld_in, hi, lo, ld_out);
+  FETIRP_LAUNCH_CHECK();
 }
 
 }  // namespace fetirp

@@ -16,9 +16,9 @@ LIB_PATH = os.path.join(HERE, "lib", "libfetirp.so")
 
 FETIRP_OK, FETIRP_EINVAL, FETIRP_ENOMEM, FETIRP_ESINGULAR, FETIRP_ENOCONV, FETIRP_ECUDA, FETIRP_ESTATE, \
     FETIRP_ETIMEOUT = range(8)
-FETIRP_PREC_FP64, FETIRP_PREC_FP32, FETIRP_PREC_TF32X3, FETIRP_PREC_AUTO = 0, 1, 2, 3
+FETIRP_PREC_FP64, FETIRP_PREC_FP32, FETIRP_PREC_TF32X3, FETIRP_PREC_AUTO, FETIRP_PREC_BF16X3 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": FETIRP_PREC_FP64, "fp32": FETIRP_PREC_FP32, "tf32x3": FETIRP_PREC_TF32X3,
-              "auto": FETIRP_PREC_AUTO}
+              "auto": FETIRP_PREC_AUTO, "bf16x3": FETIRP_PREC_BF16X3}
 
 
 # device allocator hooks of fetirp_options: alloc(bytes, stream, user) -> device pointer; free(ptr, user)

@@ -33,7 +33,7 @@ def test_c3_operator_matches_oracle_on_sampled_columns(c3):
         F.fetirp_prepare(ctx, c3.n_lambda, c3.c)
         V = np.random.default_rng(21).standard_normal((c3.n_lambda, 32))
         Qo = orc.PtFP(V[:, cols])
-        for prec, tol in (("fp64", 1e-9), ("fp32", 5e-4), ("tf32x3", 5e-4)):
+        for prec, tol in (("fp64", 1e-9), ("fp32", 5e-4), ("tf32x3", 5e-4), ("bf16x3", 1e-3)):
             Q = F.fetirp_apply_block(ctx, V, F.PRECISIONS[prec])[:, cols]
             rel = np.linalg.norm(Q - Qo) / np.linalg.norm(Qo)
             assert rel < tol, (prec, rel)
@@ -42,8 +42,9 @@ def test_c3_operator_matches_oracle_on_sampled_columns(c3):
         F.fetirp_destroy(ctx)
 
 
-def test_c3_solve_satisfies_the_equations(c3):
-    ctx = F.fetirp_create(F.fetirp_default_options(precision="tf32x3", tol=1e-8, max_iter=3000))
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_c3_solve_satisfies_the_equations(c3, prec):
+    ctx = F.fetirp_create(F.fetirp_default_options(precision=prec, tol=1e-8, max_iter=3000))
     try:
         F.load_problem(ctx, c3)
         lam, u, st = F.fetirp_solve(ctx, c3.n_lambda, c3.c, F.n_u(c3))
@@ -61,9 +62,10 @@ def test_c3_solve_satisfies_the_equations(c3):
         num += res @ res
         den += c3.occs[s].f_global @ c3.occs[s].f_global
     assert np.sqrt(num / den) < 1e-6
-    # continuity: B u = c (u of magnitude ~ |u|, so relative to |u|)
+    # continuity: B u = c (u of magnitude ~ |u|, so relative to |u|).  The defect is the dual residual of the
+    # solve, stopped at 1e-8 relative: here |B u - c| / |u| ~ 0.21 x the final relative residual, so <= 2.1e-9
     ucat = np.concatenate(us)
-    assert np.linalg.norm(B @ ucat - c3.c) / np.linalg.norm(ucat) < 1e-9
+    assert np.linalg.norm(B @ ucat - c3.c) / np.linalg.norm(ucat) < 3e-9
     # (G^T lambda = e follows from the equilibrium: N(s)^T (f(s) - B(s)^T lambda) = N(s)^T K(s) u(s) = 0.)
     # Together, equilibrium and continuity are the global FE equations (Eq. 1) with B of full row rank, so they
     # determine u and lambda.

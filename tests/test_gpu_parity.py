@@ -58,7 +58,7 @@ def test_pattern_operators(name):
 
 
 @pytest.mark.parametrize("name", list(CASES) + ["c2"])
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-6), ("tf32x3", 1e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-6), ("tf32x3", 1e-5), ("bf16x3", 5e-5)])
 def test_apply_block_matches_oracle(name, prec, tol):
     prob = config("c2") if name == "c2" else CASES[name]()
     orc = FetiOracle(prob)
@@ -77,11 +77,11 @@ def test_apply_block_matches_oracle(name, prec, tol):
 
 
 @pytest.mark.parametrize("name", list(CASES) + ["c2"])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x3"])
 def test_solve_matches_direct(name, prec):
     prob = config("c2") if name == "c2" else CASES[name]()
     us_ref, lam_ref, _, _ = direct(prob)
-    ctx = make_ctx(prob, precision=prec, tol=1e-12, inner_tol=1e-5)
+    ctx = make_ctx(prob, precision=prec, tol=1e-12)   # inner tolerance: the library's per-precision default
     try:
         lam, u, st = F.fetirp_solve(ctx, prob.n_lambda, prob.c, F.n_u(prob))
     finally:
@@ -90,7 +90,7 @@ def test_solve_matches_direct(name, prec):
     assert rel(lam, lam_ref) < 1e-8, st
     for a, b in zip(F.split_u(prob, u), us_ref):
         assert rel(a, b) < 1e-8
-    if prec == "fp32":
+    if prec != "fp64":
         assert st["outer_steps"] >= 1
 
 
