@@ -44,7 +44,7 @@ WORKLOADS = {
           "6 resident patterns (2D heat 16^2/32^2/64^2, 3D elastic 8^3/12^3/16^3), admitted by device memory",
 }
 DEFAULTS = {  # per workload: local-product precision, multivector width, direction-history cap (GB; 0 = library)
-    "c3": ("bf16x3", 32, 32.0), "c2": ("fp32", 8, 0.0), "c1": ("fp64", 4, 0.0), "c5": ("auto", 32, 0.0),
+    "c3": ("bf16x3", 32, 32.0), "c2": ("fp32", 8, 0.0), "c1": ("fp64", 4, 0.0), "c5": ("auto", 8, 0.0),
     "c4": ("auto", 0, 32.0),   # k = 0: autotuned
 }
 # Block iterations of the default workload (C3, k = 32, tol 1e-8): the count the library's FP64 solve needs
@@ -552,6 +552,7 @@ def run_serving(args):
     opts = F.fetirp_default_options(precision=args.precision, tol=1e-8, inner_tol=args.inner_tol,
                                     history_bytes=args.mem_budget // max(1, args.slots) // 2)
     srv = F.fetirp_server_create(lib, opts, args.slots, args.mem_budget)
+    F.fetirp_server_set_batching(srv, args.batch)
     lat, stats_l, done_t = [None] * len(reqs), [None] * len(reqs), [None] * len(reqs)
     tickets = [None] * len(reqs)
     ready = threading.Event()
@@ -607,7 +608,8 @@ def run_serving(args):
         "dtype": "f64" if args.precision == "fp64" else "f64+" + ("fp32|tf32x3" if args.precision == "auto" else args.precision),
         "data": "synthetic (seeded Q1 meshes, loads, Poisson arrivals; no datasets)",
         "config": {"workload": WORKLOADS["c5"], "name": "c5", "requests": len(reqs), "rate_per_s": args.rate,
-                   "slots": args.slots, "mem_budget_bytes": args.mem_budget, "precision": args.precision,
+                   "slots": args.slots, "batch": args.batch, "mem_budget_bytes": args.mem_budget,
+                   "precision": args.precision,
                    "block_k": args.k},
         "latency_ms": {"p50": round(float(np.percentile(lat_a, 50)), 3),
                        "p99": round(float(np.percentile(lat_a, 99)), 3), "max": round(float(lat_a.max()), 3)},
@@ -640,6 +642,8 @@ def main():
     ap.add_argument("--slots", type=int, default=4, help="serving workload: concurrent structures")
     ap.add_argument("--mem-budget", type=int, default=64 << 30, help="serving workload: device-memory budget")
     ap.add_argument("--seq-sample", type=int, default=40, help="serving workload: requests timed sequentially")
+    ap.add_argument("--batch", type=int, default=1,
+                    help="serving workload: structures of one pattern a slot may solve together (1 = none)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     d_prec, d_k, d_hist = DEFAULTS[args.workload]

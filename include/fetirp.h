@@ -279,6 +279,18 @@ enum {
 fetirp_status fetirp_set_preconditioner(fetirp_ctx ctx, int32_t kind, int32_t scaling);
 
 /*
+ * Declare the structure a union of independent sub-structures (the batching of the serving loop): block b owns
+ * the multiplier rows [row_offset[b], row_offset[b + 1]) and nothing couples the blocks.  The next solves then
+ * stop when ||r|| <= tol * min_b ||r0_b|| (r restricted to block b), so that every block meets the relative
+ * tolerance on its own, and fetirp_stats.rel_residual reports the worst block's ||r_b|| / ||r0_b||.  With
+ * multivector groups that do not mix blocks, the block iteration of the union is the blocks' own iterations
+ * carried out together (F, P and the block Gram matrices are block diagonal), so one local-product launch per
+ * iteration serves every block.  n_blocks = 0 (or row_offset = NULL) removes the setting; so does
+ * fetirp_clear_occurrences.  row_offset[n_blocks] must equal the n_lambda of the solve (FETIRP_EINVAL otherwise).
+ */
+fetirp_status fetirp_set_row_blocks(fetirp_ctx ctx, int32_t n_blocks, const int64_t* row_offset);
+
+/*
  * Solve for lambda and the displacements (Table 1 and the recovery u(s) = K^+ (f - B^T lambda) + N alpha).
  *  n_lambda: number of multiplier rows (max lambda_row + 1 over all occurrences).
  *  c[n_lambda]: right-hand side of B u = c (Dirichlet values on Dirichlet rows, 0 on gluing rows), or NULL
@@ -424,6 +436,13 @@ typedef struct {
  * the library's options).  Every input is copied. */
 fetirp_status fetirp_server_create(fetirp_ctx library, const fetirp_options* slot_opt, int32_t max_slots,
                                    int64_t mem_budget_bytes, fetirp_server* out);
+/* Continuous batching of F-applies across requests: a slot that takes the next structure also takes, up to
+ * max_structures in all, queued structures made of the same single library pattern while the union stays within
+ * 64 multivector columns and the memory budget, and solves them together as independent blocks of one structure
+ * (fetirp_set_row_blocks): every local-product launch then serves all of them, and each result meets the
+ * relative tolerance on its own (the same solution as alone, to that tolerance; not bitwise).  1 (the default)
+ * = one structure per solve.  FETIRP_EINVAL outside 1..64. */
+fetirp_status fetirp_server_set_batching(fetirp_server srv, int32_t max_structures);
 /* Queue a structure (copied) and return its ticket. */
 fetirp_status fetirp_server_submit(fetirp_server srv, const fetirp_structure* st, int64_t* ticket);
 /* Wait up to timeout_s seconds (0: just poll; < 0: forever) for a ticket.  *done = 1 when finished; then the

@@ -12,8 +12,8 @@ OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libfetirp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]
-# per-source flags: the persistent iteration reads data written by other CTAs after grid barriers, so its
-# global loads are cached in L2 only (coherent across SMs), never in L1
+# per-source flags: the persistent iteration reads data written by other CTAs after grid barriers (ordered by the
+# barrier's acquire fence); caching its global loads in L2 only is a second guard
 EXTRA = {"persist.cu": ["-Xptxas", "-dlcm=cg"]}
 
 

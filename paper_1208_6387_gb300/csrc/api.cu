@@ -166,6 +166,7 @@ struct fetirp_ctx_s {
   std::vector<OccData> occs;
   int k_user = 0;
   std::vector<int> groups_user;
+  std::vector<int64_t> row_blocks;   // multiplier-row offsets of independent sub-structures (empty: one)
   // permutation multivector (Eq. 8): column g of the block is Pi^g z; Pi^g in ELL form (pw entries per row and
   // column, weight 0 = padding), built on the host when the permutation is set
   struct Perm {
@@ -627,6 +628,7 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   if (n_occ == 0) throw Error(FETIRP_ESTATE, "no occurrence has been added");
   REQUIRE(n_lambda > 0 && n_lambda < (1LL << 31), "n_lambda out of range");
   const int nl = (int)n_lambda;
+  REQUIRE(ctx->row_blocks.empty() || ctx->row_blocks.back() == n_lambda, "row blocks do not cover n_lambda rows");
   const int n_pat = (int)ctx->pats.size();
   if (n_pat > MAXP) throw Error(FETIRP_EINVAL, "more than 16 patterns in one structure");
   // occurrence tables
@@ -2032,7 +2034,22 @@ fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_st
   residual(ctx);
   const double r0 = norm2(ctx, ctx->r.p, nl);
   double rn = r0;
-  const double target = ctx->opt.tol * r0;
+  // independent sub-structures (fetirp_set_row_blocks): stop when ||r|| <= tol * min_b ||r0_b||, so that every
+  // block meets the relative tolerance on its own (||r_b|| <= ||r||); the reported residual is the worst block's
+  double r0_ref = r0;
+  std::vector<double> r0_blk;
+  if (ctx->row_blocks.size() > 2) {
+    std::vector<double> h(nl);
+    FETIRP_CUDA(cudaMemcpyAsync(h.data(), ctx->r.p, sizeof(double) * nl, cudaMemcpyDeviceToHost, s));
+    FETIRP_CUDA(cudaStreamSynchronize(s));
+    for (size_t b = 0; b + 1 < ctx->row_blocks.size(); ++b) {
+      double acc = 0.0;
+      for (int64_t i = ctx->row_blocks[b]; i < ctx->row_blocks[b + 1]; ++i) acc += h[i] * h[i];
+      r0_blk.push_back(std::sqrt(acc));
+      if (r0_blk.back() > 0.0) r0_ref = std::min(r0_ref, r0_blk.back());
+    }
+  }
+  const double target = ctx->opt.tol * r0_ref;
   int budget = ctx->opt.max_iter;
   Hist H;
   int prec = ctx->opt.precision;
@@ -2066,6 +2083,18 @@ fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_st
     }
   }
   st.rel_residual = r0 > 0.0 ? rn / r0 : 0.0;
+  if (!r0_blk.empty() && r0 > 0.0) {   // the worst block's own relative residual
+    std::vector<double> h(nl);
+    FETIRP_CUDA(cudaMemcpyAsync(h.data(), ctx->r.p, sizeof(double) * nl, cudaMemcpyDeviceToHost, s));
+    FETIRP_CUDA(cudaStreamSynchronize(s));
+    double worst = 0.0;
+    for (size_t b = 0; b < r0_blk.size(); ++b) {
+      double acc = 0.0;
+      for (int64_t i = ctx->row_blocks[b]; i < ctx->row_blocks[b + 1]; ++i) acc += h[i] * h[i];
+      if (r0_blk[b] > 0.0) worst = std::max(worst, std::sqrt(acc) / r0_blk[b]);
+    }
+    st.rel_residual = worst;
+  }
   st.f_applies = st.iterations;   // one block F-apply per block iteration
   check_tc_error(ctx);
   if (d_lambda)
@@ -2480,6 +2509,7 @@ fetirp_status fetirp_add_occurrence(fetirp_ctx ctx, int32_t pattern_id, const do
 fetirp_status fetirp_clear_occurrences(fetirp_ctx ctx) {
   return guarded(ctx, [&]() -> fetirp_status {
     ctx->occs.clear();
+    ctx->row_blocks.clear();
     ctx->k_user = 0;
     ctx->groups_user.clear();
     ctx->perm.on = false;
@@ -2935,6 +2965,20 @@ fetirp_status fetirp_set_preconditioner(fetirp_ctx ctx, int32_t kind, int32_t sc
     ctx->pc.kind = kind;
     ctx->pc.scaling = scaling;
     invalidate(ctx);
+    return FETIRP_OK;
+  });
+}
+
+fetirp_status fetirp_set_row_blocks(fetirp_ctx ctx, int32_t n_blocks, const int64_t* row_offset) {
+  return guarded(ctx, [&]() -> fetirp_status {
+    if (n_blocks == 0 || !row_offset) {
+      ctx->row_blocks.clear();
+      return FETIRP_OK;
+    }
+    REQUIRE(n_blocks >= 1, "n_blocks < 0");
+    REQUIRE(row_offset[0] == 0, "row_offset[0] must be 0");
+    for (int b = 0; b < n_blocks; ++b) REQUIRE(row_offset[b + 1] > row_offset[b], "row blocks must be non-empty");
+    ctx->row_blocks.assign(row_offset, row_offset + n_blocks + 1);
     return FETIRP_OK;
   });
 }

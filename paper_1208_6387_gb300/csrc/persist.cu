@@ -11,9 +11,13 @@
 //       normalises (T, alpha)
 //   P8  W_h[:, a..a+k) = Z T, Q_h[...] = Q T, lambda += Z T alpha, r -= Q T alpha, ||r||^2 partials
 // The residual test runs on the device at the start of every iteration.  Data written by other CTAs is read
-// after a barrier through L2 only: this file is compiled with -Xptxas -dlcm=cg, and no loads of mutable
-// data use the non-coherent path.  Every barrier wait is bounded by A.timeout_ns (globaltimer); an expired
-// wait sets *A.err and the CTA returns, so a failure ends the launch instead of hanging it.
+// after a grid barrier: every CTA's writes happen before its __threadfence() and arrival, and the polling thread
+// observes the new generation, then executes a fence.acq_rel.gpu before the CTA-wide __syncthreads() that
+// releases the other threads, so their later loads of the other CTAs' data are ordered after those writes in
+// the PTX memory model (acquire at GPU scope, made CTA-wide by the barrier).  No loads of mutable data use the
+// non-coherent (ld.global.nc / __ldg) path.  The file is also compiled with -Xptxas -dlcm=cg (global loads
+// cached in L2 only) as a second guard.  Every barrier wait is bounded by A.timeout_ns (globaltimer); an
+// expired wait sets *A.err and the CTA returns, so a failure ends the launch instead of hanging it.
 #include <mutex>
 
 #include "ops.cuh"
@@ -63,6 +67,7 @@ __device__ bool grid_sync(const PersistArgs& A) {
       }
     }
     __threadfence();
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");   // acquire: the other CTAs' writes before their arrival
     if (*(volatile int*)A.err) ok = 0;
     s_ok = ok;
   }

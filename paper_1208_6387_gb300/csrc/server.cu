@@ -64,11 +64,22 @@ struct fetirp_server_s {
   int64_t in_use = 0;
   int active = 0;
   bool stop = false;
+  int max_batch = 1;   // structures one slot may take together (fetirp_server_set_batching)
+
+  static int32_t width_of(const Request* r, const fetirp_options& o) {
+    const int32_t k = r->k > 0 ? r->k : o.block_k;
+    return std::max(1, std::min(k, r->n_occ));
+  }
+  static int32_t single_pattern(const Request* r) {   // the one library pattern of r, or -1
+    for (int32_t o = 1; o < r->n_occ; ++o)
+      if (r->pattern_id[o] != r->pattern_id[0]) return -1;
+    return r->pattern_id[0];
+  }
 
   void worker_loop() {
     fetirp_ctx child = nullptr;
     for (;;) {
-      Request* r = nullptr;
+      std::vector<Request*> batch;
       {
         std::unique_lock<std::mutex> lock(mu);
         cv_work.wait(lock, [&] {
@@ -78,42 +89,88 @@ struct fetirp_server_s {
           return active == 0 || in_use + f->mem <= budget;
         });
         if (pending.empty()) break;   // stop requested and queue drained
-        r = pending.front();
+        Request* r = pending.front();
         pending.pop_front();
         in_use += r->mem;
+        batch.push_back(r);
+        // continuous batching: queued structures of the same library pattern join this slot's solve while the
+        // union stays within 64 multivector columns and the memory budget (they are solved as independent
+        // blocks of one structure, so every local-product launch serves all of them)
+        const int32_t pat = single_pattern(r);
+        int32_t width = width_of(r, opt);
+        for (auto it = pending.begin(); max_batch > 1 && pat >= 0 && it != pending.end() &&
+                                        (int)batch.size() < max_batch;) {
+          Request* q = *it;
+          const int32_t wq = width_of(q, opt);
+          if (single_pattern(q) == pat && width + wq <= 64 && in_use + q->mem <= budget) {
+            batch.push_back(q);
+            width += wq;
+            in_use += q->mem;
+            it = pending.erase(it);
+          } else {
+            ++it;
+          }
+        }
         ++active;
       }
       fetirp_status st = FETIRP_OK;
       if (!child) st = fetirp_create_child(lib, &opt, &child);
       if (st == FETIRP_OK) st = fetirp_clear_occurrences(child);
-      for (int32_t o = 0; st == FETIRP_OK && o < r->n_occ; ++o) {
-        const int32_t l0 = r->link_offset[o], l1 = r->link_offset[o + 1];
-        int32_t id = 0;
-        st = fetirp_add_occurrence(child, r->pattern_id[o], r->rot.empty() ? nullptr : &r->rot[9 * (size_t)o],
-                                   l1 - l0, r->local_node.data() + l0, r->global_comp.data() + l0,
-                                   r->lambda_row.data() + l0, r->sign.data() + l0, r->f_global.data() + r->f_offset[o],
-                                   &id);
+      int64_t row0 = 0;
+      std::vector<int64_t> row_off{0}, u_off{0};
+      std::vector<int32_t> groups;
+      int32_t g0 = 0;
+      for (Request* r : batch) {
+        for (int32_t o = 0; st == FETIRP_OK && o < r->n_occ; ++o) {
+          const int32_t l0 = r->link_offset[o], l1 = r->link_offset[o + 1];
+          std::vector<int32_t> rows(r->lambda_row.begin() + l0, r->lambda_row.begin() + l1);
+          for (auto& x : rows) x += (int32_t)row0;   // the request's multiplier rows, after the earlier ones
+          int32_t id = 0;
+          st = fetirp_add_occurrence(child, r->pattern_id[o], r->rot.empty() ? nullptr : &r->rot[9 * (size_t)o],
+                                     l1 - l0, r->local_node.data() + l0, r->global_comp.data() + l0, rows.data(),
+                                     r->sign.data() + l0, r->f_global.data() + r->f_offset[o], &id);
+        }
+        const int32_t k = width_of(r, opt);
+        for (int32_t o = 0; o < r->n_occ; ++o)
+          groups.push_back(g0 + (r->group_of_occ.empty() ? (int32_t)((int64_t)o * k / r->n_occ)
+                                                         : std::min(r->group_of_occ[o], k - 1)));
+        g0 += k;
+        row0 += r->n_lambda;
+        row_off.push_back(row0);
+        u_off.push_back(u_off.back() + r->f_offset.back());
       }
-      if (st == FETIRP_OK && (r->k > 0 || !r->group_of_occ.empty())) {
-        std::vector<int32_t> g = r->group_of_occ;
-        int32_t k = r->k > 0 ? r->k : opt.block_k;
-        k = std::max(1, std::min(k, r->n_occ));
-        if (g.empty())
-          for (int32_t o = 0; o < r->n_occ; ++o) g.push_back((int32_t)((int64_t)o * k / r->n_occ));
-        st = fetirp_set_groups(child, k, g.data());
-      }
+      const bool explicit_groups = batch.size() > 1 || batch[0]->k > 0 || !batch[0]->group_of_occ.empty();
+      if (st == FETIRP_OK && explicit_groups) st = fetirp_set_groups(child, g0, groups.data());
+      if (st == FETIRP_OK && batch.size() > 1)
+        st = fetirp_set_row_blocks(child, (int32_t)batch.size(), row_off.data());
+      std::vector<double> lam, u, c;
+      fetirp_stats stats{};
       if (st == FETIRP_OK) {
-        r->lambda.resize((size_t)r->n_lambda);
-        r->u.resize((size_t)r->f_offset.back());
-        st = fetirp_solve(child, r->n_lambda, r->c.empty() ? nullptr : r->c.data(), r->lambda.data(), r->u.data(),
-                          &r->stats);
+        lam.resize((size_t)row0);
+        u.resize((size_t)u_off.back());
+        bool any_c = false;
+        for (Request* r : batch) any_c = any_c || !r->c.empty();
+        if (any_c) {
+          c.assign((size_t)row0, 0.0);
+          for (size_t b = 0; b < batch.size(); ++b)
+            if (!batch[b]->c.empty()) std::copy(batch[b]->c.begin(), batch[b]->c.end(), c.begin() + row_off[b]);
+        }
+        st = fetirp_solve(child, row0, c.empty() ? nullptr : c.data(), lam.data(), u.data(), &stats);
       }
       {
         std::lock_guard<std::mutex> lock(mu);
-        r->status = st;
-        r->done = true;
-        r->t_done = Clock::now();
-        in_use -= r->mem;
+        for (size_t b = 0; b < batch.size(); ++b) {
+          Request* r = batch[b];
+          r->status = st;
+          if (!lam.empty()) {
+            r->lambda.assign(lam.begin() + row_off[b], lam.begin() + row_off[b + 1]);
+            r->u.assign(u.begin() + u_off[b], u.begin() + u_off[b + 1]);
+          }
+          r->stats = stats;
+          r->done = true;
+          r->t_done = Clock::now();
+          in_use -= r->mem;
+        }
         --active;
       }
       cv_done.notify_all();
@@ -137,6 +194,13 @@ fetirp_status fetirp_server_create(fetirp_ctx library, const fetirp_options* slo
   fetirp_server_s* p = srv.get();
   for (int32_t i = 0; i < max_slots; ++i) p->workers.emplace_back([p] { p->worker_loop(); });
   *out = srv.release();
+  return FETIRP_OK;
+}
+
+fetirp_status fetirp_server_set_batching(fetirp_server srv, int32_t max_structures) {
+  if (!srv || max_structures < 1 || max_structures > 64) return FETIRP_EINVAL;
+  std::lock_guard<std::mutex> lock(srv->mu);
+  srv->max_batch = max_structures;
   return FETIRP_OK;
 }
 

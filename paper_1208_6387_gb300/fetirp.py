@@ -110,6 +110,7 @@ _SIGS = {
     "fetirp_server_poll": (C.c_int, [P, C.c_int64, C.POINTER(C.c_int32), P, P, C.POINTER(fetirp_stats),
                                      C.POINTER(C.c_double)]),
     "fetirp_server_destroy": (None, [P]),
+    "fetirp_server_set_batching": (C.c_int, [P, C.c_int32]),
     "fetirp_solve": (C.c_int, [P, C.c_int64, P, P, P, C.POINTER(fetirp_stats)]),
     "fetirp_solve_device": (C.c_int, [P, C.c_int64, P, P, P, C.POINTER(fetirp_stats)]),
     "fetirp_apply_block": (C.c_int, [P, C.c_int32, P, P, C.c_int32]),
@@ -121,6 +122,7 @@ _SIGS = {
     "fetirp_device_status": (C.c_int, [P]),
     "fetirp_set_permutation": (C.c_int, [P, C.c_int64, P, P, P, C.c_int32, C.c_int32]),
     "fetirp_set_preconditioner": (C.c_int, [P, C.c_int32, C.c_int32]),
+    "fetirp_set_row_blocks": (C.c_int, [P, C.c_int32, P]),
     "fetirp_apply_split": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_int]),
     "fetirp_apply_split_device": (C.c_int, [P, C.c_void_p, C.c_void_p, C.c_int]),
     "fetirp_get_pattern": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), P, P]),
@@ -261,6 +263,12 @@ def fetirp_server_create(library, slot_opts: fetirp_options | None, max_slots, m
     return h
 
 
+def fetirp_server_set_batching(srv, max_structures):
+    st = lib().fetirp_server_set_batching(srv, int(max_structures))
+    if st != FETIRP_OK:
+        raise FetirpError(st, "fetirp_server_set_batching")
+
+
 def fetirp_server_submit(srv, structure):
     t = C.c_int64()
     st = lib().fetirp_server_submit(srv, C.byref(structure), C.byref(t))
@@ -394,6 +402,15 @@ def fetirp_set_preconditioner(ctx, kind="identity", scaling="stiffness"):
     """The preconditioner of Eqs. 4-5 by name (identity, dirichlet, lumped, superlumped) and its scaling
     (multiplicity, stiffness); argument marshalling only."""
     _check(ctx, lib().fetirp_set_preconditioner(ctx, PRECONDITIONERS[kind], SCALINGS[scaling]))
+
+
+def fetirp_set_row_blocks(ctx, row_offsets):
+    """Independent sub-structures owning the multiplier rows [row_offsets[b], row_offsets[b + 1]) (None: one)."""
+    if row_offsets is None:
+        _check(ctx, lib().fetirp_set_row_blocks(ctx, 0, None))
+        return
+    ro = np.ascontiguousarray(row_offsets, dtype=np.int64)
+    _check(ctx, lib().fetirp_set_row_blocks(ctx, len(ro) - 1, _ptr(ro)))
 
 
 def fetirp_device_status(ctx):
