@@ -51,11 +51,13 @@ DEFAULTS = {  # per workload: local-product precision, multivector width, direct
 # on this structure, used to scale the oracle's sampled per-iteration cost to a whole solve.
 C3_ITERATIONS = 120
 PHASE_KERNELS = {  # the kernels each phase launches
-    "factor": "k_potrf_tile, k_trsm_tiles, k_update_pairs, k_tile_inverse, k_tri_*", "coarse": "k_gtg, k_gemm_f64",
-    "local": "k_local_gemm / k_tc_gemm", "gather": "k_gather_tile", "scatter": "k_scatter",
-    "project": "k_gt_v, k_small_gemm, k_g_apply",
-    "gram": "k_group_wr, k_gram_split + k_reduce_chunks_dyn, k_eta_partial + k_eta_group_sums",
-    "reorth": "k_tall_update / k_tall_update_w32", "update": "k_split, k_update",
+    "factor": "k_potrf_tile, k_trsm_tiles, k_update_pairs, k_tile_inverse, k_tri_*, k_lauum, k_split_tf32/bf16",
+    "coarse": "k_gtg, k_gemm_f64",
+    "local": "k_local_gemm / k_tc_gemm", "gather": "k_gather_tile, k_rotate_traces", "scatter": "k_scatter",
+    "project": "k_gt_v, k_small_gemm, k_g_apply (FP64); k_split_pairs, k_gt_v_ds, k_small_gemm_ds, k_g_apply_ds "
+               "(mixed forms)",
+    "gram": "k_group_wr, k_gram_split + k_reduce_chunks_dyn, k_eta_partial(_ds) + k_eta_group_sums",
+    "reorth": "k_tall_update / k_tall_update_w32", "update": "k_split / k_perm_split, k_update",
     "recover": "k_tri_*, k_unpermute_rotate", "normalise": "k_normalise",
     "iterate": "k_persist (whole block iterations in one cooperative launch)",
     "outer": "FP64 residual: k_gather_tile, k_local_gemm<double>, k_scatter, projection",

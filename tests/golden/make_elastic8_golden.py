@@ -1,8 +1,8 @@
-"""Writes elastic8_2x3x4.npz: the oracle's direct solution (oracle.direct: global assembly, sparse LU of Eq. 1,
+"""Writes elastic8_3x4x4.npz: the oracle's direct solution (oracle.direct: global assembly, sparse LU of Eq. 1,
 lambda from the subdomain equilibria of Eq. 2) of the medium elastic structure used by tests/test_gpu_medium.py
-(three 8^3 Q1 cube patterns on a 2 x 3 x 4 grid of rotated occurrences, clamped x = 0, N(0,1) loads, seed 3).
-The direct solve takes about a minute on the host, so its result is stored; the file also holds the sizes and
-a checksum of the inputs, which the test compares with the generator's current output.
+(three 8^3 Q1 cube patterns on a 3 x 4 x 4 grid of rotated occurrences, 16 per pattern, k = 30, clamped x = 0,
+N(0,1) loads, seed 3).  The direct solve takes minutes on the host, so its result is stored; the file also holds
+the sizes and a checksum of the inputs, which the test compares with the generator's current output.
 
     python tests/golden/make_elastic8_golden.py
 """
@@ -19,7 +19,7 @@ from oracle.direct import direct  # noqa: E402
 
 
 def medium_problem():
-    return elastic_grid(8, (2, 3, 4), n_patterns=3, k=24, seed=3)
+    return elastic_grid(8, (3, 4, 4), n_patterns=3, k=30, seed=3)
 
 
 def input_checksum(prob):
@@ -32,7 +32,7 @@ def main():
     prob = medium_problem()
     us, lam, res, _ = direct(prob)
     assert res < 1e-10, res
-    np.savez_compressed(os.path.join(HERE, "elastic8_2x3x4.npz"), lam=lam, u=np.concatenate(us),
+    np.savez_compressed(os.path.join(HERE, "elastic8_3x4x4.npz"), lam=lam, u=np.concatenate(us),
                         checksum=input_checksum(prob))
     print("n_lambda", prob.n_lambda, "consistency residual", res)
 

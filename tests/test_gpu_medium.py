@@ -1,9 +1,9 @@
 """GPU parity at a size that reaches every tile path of the tensor-core local product: three 8^3 Q1 cube
-patterns (n_b = 1158: nine full 128-row tiles and a ragged one) on a 2 x 3 x 4 grid of rotated occurrences with
-k = 24 (R_p = 8 x 24 = 192 right-hand sides per pattern: a full and a ragged 128-column tile), three patterns in
-one launch.  lambda and u are compared element by element with the oracle's direct solve (stored by
-tests/golden/make_elastic8_golden.py, which calls only the oracle) in every precision, at 1e-8 relative; the
-block operator is compared with the oracle's P^T F P V."""
+patterns (n_b = 1158: nine full 128-row tiles and a ragged one of 6 rows) on a 3 x 4 x 4 grid of rotated
+occurrences, 16 per pattern, with k = 30 (R_p = 16 x 30 = 480 right-hand sides per pattern: a full 256-column
+tile and a ragged one of 224), three patterns in one launch.  lambda and u are compared element by element with
+the oracle's direct solve (stored by tests/golden/make_elastic8_golden.py, which calls only the oracle) in every
+precision, at 1e-8 relative; the block operator is compared with the oracle's P^T F P V."""
 import os
 
 import numpy as np
@@ -23,7 +23,7 @@ def _golden():
     mk = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mk)
     prob = mk.medium_problem()
-    g = np.load(os.path.join(HERE, "golden", "elastic8_2x3x4.npz"))
+    g = np.load(os.path.join(HERE, "golden", "elastic8_3x4x4.npz"))
     assert np.allclose(g["checksum"], mk.input_checksum(prob), rtol=1e-12, atol=0), "inputs changed since the golden"
     return prob, g["lam"], g["u"]
 
