@@ -536,9 +536,9 @@ void factor_stage_b(PatternData& P, cudaStream_t s) {
   split_bf16(Sdag, nb, nb, nb, P.Sb_hi.p, P.Sb_lo.p, P.ldsb, s);
 }
 
-void factorize_patterns(fetirp_ctx ctx, const std::vector<PatternData*>& pats) {
-  PhaseScope ph(ctx, FETIRP_PHASE_FACTOR, 0.0, 0.0);
-  const size_t np = pats.size();
+// Per-pattern work on concurrent streams: fork_patterns(ctx, n) makes n streams wait for the work enqueued so far
+// on the context stream; join_patterns(ctx, n) makes the context stream wait for all of them.
+void fork_patterns(fetirp_ctx ctx, size_t np) {
   while (ctx->fstreams.size() < np) {
     cudaStream_t st;
     FETIRP_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -546,16 +546,9 @@ void factorize_patterns(fetirp_ctx ctx, const std::vector<PatternData*>& pats) {
   }
   if (!ctx->fork_ev) FETIRP_CUDA(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
   FETIRP_CUDA(cudaEventRecord(ctx->fork_ev, ctx->stream));
-  for (size_t i = 0; i < np; ++i) {
-    FETIRP_CUDA(cudaStreamWaitEvent(ctx->fstreams[i], ctx->fork_ev, 0));
-    factor_stage_a(*pats[i], ctx->opt.pivot_tol, ctx->fstreams[i]);
-  }
-  for (size_t i = 0; i < np; ++i) FETIRP_CUDA(cudaStreamSynchronize(ctx->fstreams[i]));
-  for (size_t i = 0; i < np; ++i) {
-    factor_check(*pats[i]);
-    pats[i]->upload_zpiv(ctx->fstreams[i]);
-  }
-  for (size_t i = 0; i < np; ++i) factor_stage_b(*pats[i], ctx->fstreams[i]);
+  for (size_t i = 0; i < np; ++i) FETIRP_CUDA(cudaStreamWaitEvent(ctx->fstreams[i], ctx->fork_ev, 0));
+}
+void join_patterns(fetirp_ctx ctx, size_t np) {
   for (size_t i = 0; i < np; ++i) {
     if (ctx->join_ev.size() <= i) {
       cudaEvent_t e;
@@ -565,6 +558,20 @@ void factorize_patterns(fetirp_ctx ctx, const std::vector<PatternData*>& pats) {
     FETIRP_CUDA(cudaEventRecord(ctx->join_ev[i], ctx->fstreams[i]));
     FETIRP_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->join_ev[i], 0));
   }
+}
+
+void factorize_patterns(fetirp_ctx ctx, const std::vector<PatternData*>& pats) {
+  PhaseScope ph(ctx, FETIRP_PHASE_FACTOR, 0.0, 0.0);
+  const size_t np = pats.size();
+  fork_patterns(ctx, np);
+  for (size_t i = 0; i < np; ++i) factor_stage_a(*pats[i], ctx->opt.pivot_tol, ctx->fstreams[i]);
+  for (size_t i = 0; i < np; ++i) FETIRP_CUDA(cudaStreamSynchronize(ctx->fstreams[i]));
+  for (size_t i = 0; i < np; ++i) {
+    factor_check(*pats[i]);
+    pats[i]->upload_zpiv(ctx->fstreams[i]);
+  }
+  for (size_t i = 0; i < np; ++i) factor_stage_b(*pats[i], ctx->fstreams[i]);
+  join_patterns(ctx, np);
   FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 
@@ -1037,19 +1044,23 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   } else {
     ctx->lambda0.zero(s);
   }
-  // d = sum_s B(s) K(s)^+ f(s) - c (Eq. 3)
+  // d = sum_s B(s) K(s)^+ f(s) - c (Eq. 3).  Only the boundary rows of K^+ f enter d: the backward sweep stops at
+  // the first boundary block row (the boundary is ordered last).  Patterns on concurrent streams.
   PatView<double> V{};
+  fork_patterns(ctx, n_pat);
   for (int p = 0; p < n_pat; ++p) {
     PatternData& P = *ctx->pats[p];
     PatternUse& Us = ctx->use[p];
     const int no = (int)Us.occs.size();
+    cudaStream_t ps = ctx->fstreams[p];
     if (no > 0) {
-      FETIRP_CUDA(cudaMemcpyAsync(Us.U.p, Us.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, s));
-      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, s, P.Dinv.p);
-      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, s, P.Dinv.p);
+      FETIRP_CUDA(cudaMemcpyAsync(Us.U.p, Us.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, ps));
+      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, ps, P.Dinv.p);
+      tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, ps, P.Dinv.p, false, P.n_i / TILE);
     }
     V.base[p] = Us.U.p; V.ld[p] = P.npad; V.off[p] = P.n_i;
   }
+  join_patterns(ctx, n_pat);
   rotate_traces<double>(L, V, 1, false, s);
   scatter<double>(L, V, 1, 0.0, ctx->d.p, s);
   axpy_f64(nl, -1.0, ctx->c.p, ctx->d.p, s);
@@ -1931,23 +1942,26 @@ void recover(fetirp_ctx ctx, double* d_u_out) {
   rotate_traces<double>(L, V, 1, false, s);   // general rotations: f(s) to the global frame, add -B^T lambda,
   gather<double>(L, ctx->lam.p, 1, V, s, -1.0, 1.0);
   rotate_traces<double>(L, V, 1, true, s);    // and back to the pattern frame
+  fork_patterns(ctx, n_pat);   // patterns on concurrent streams
   for (int p = 0; p < n_pat; ++p) {
     PatternData& P = *ctx->pats[p];
     PatternUse& Us = ctx->use[p];
     const int no = (int)Us.occs.size();
     if (no == 0) continue;
+    cudaStream_t ps = ctx->fstreams[p];
     double* Usol = Us.U.p;
-    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, s, P.Dinv.p);
-    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, s, P.Dinv.p);
+    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, ps, P.Dinv.p);
+    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, ps, P.Dinv.p);
     if (P.kdim > 0 && ctx->n_G > 0)
       gemm_f64(P.npad, no, P.kdim, -1.0, P.N.p, 1, P.npad, ctx->Ac.p + ctx->pofs[p], 1, P.kdim, 1.0, Usol, 1,
-               P.npad, s);
+               P.npad, ps);
     const long long tot = (long long)P.n * no;
-    k_unpermute_rotate<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.n, P.dpn, P.npad, Usol, P.d_newidx.p,
-                                                                     Us.d_occs.p, ctx->d_rot.p, ctx->d_uoff.p, no,
-                                                                     d_u_out);
+    k_unpermute_rotate<<<(unsigned)((tot + 255) / 256), 256, 0, ps>>>(P.n, P.dpn, P.npad, Usol, P.d_newidx.p,
+                                                                      Us.d_occs.p, ctx->d_rot.p, ctx->d_uoff.p, no,
+                                                                      d_u_out);
     FETIRP_LAUNCH_CHECK();
   }
+  join_patterns(ctx, n_pat);
 }
 
 bool hist_fp64(fetirp_ctx ctx) { return ctx->opt.precision == FETIRP_PREC_FP64 || ctx->pc.kind != 0; }

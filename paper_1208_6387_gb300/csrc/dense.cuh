@@ -36,8 +36,12 @@ void chol_tiles(double* A, int npad, const TilePlan& plan, const double* diag0, 
 // Dinv (optional): inverted diagonal tiles from tile_inverses(); each diagonal step is then a parallel product.
 // identity_rhs (forward solves only): X holds the identity on entry, so in step J only the first 64 (J + 1)
 // columns can be nonzero (L^{-1} is lower triangular) and the others are skipped: a third of the work.
+// stop_tile (backward solves only): only the block rows J >= stop_tile of the solution are wanted; each of them
+// depends on later block rows only, so the sweep stops there and updates no earlier block row (X above
+// stop_tile is left partly updated).
 void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, double* X, int ldx, int nrhs,
-               bool trans, cudaStream_t s, const double* Dinv = nullptr, bool identity_rhs = false);
+               bool trans, cudaStream_t s, const double* Dinv = nullptr, bool identity_rhs = false,
+               int stop_tile = 0);
 // C (n_out x n_out, ld ldc) = X^T X for a lower-triangular X (column-major, ld, krows rows summed).
 void lauum(const double* X, int ld, int krows, int n_out, double* C, int ldc, cudaStream_t s);
 // Dinv (npad/64 tiles of 64 x 64, column-major) = inverses of the diagonal tiles of L (zero pivots -> 0).

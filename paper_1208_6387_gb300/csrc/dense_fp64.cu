@@ -1,5 +1,7 @@
 // Dense FP64 tile kernels of the pattern set-up: Cholesky with zero-pivot detection (Sec. 2, floating
 // subdomains), right-looking multi-right-hand-side triangular solves and a strided generic GEMM.
+#include <algorithm>
+
 #include "dense.cuh"
 
 namespace fetirp {
@@ -536,7 +538,7 @@ void tile_inverses(const double* L, int npad, const int* zp, double* Dinv, cudaS
 }
 
 void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, double* X, int ldx, int nrhs_all,
-               bool trans, cudaStream_t s, const double* Dinv, bool identity_rhs) {
+               bool trans, cudaStream_t s, const double* Dinv, bool identity_rhs, int stop_tile) {
   if (nrhs_all <= 0) return;
   int nrhs = nrhs_all;
   int chunks = ceil_div(nrhs, TILE);
@@ -561,12 +563,18 @@ void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, d
       }
     }
   } else {
-    for (int J = plan.nt - 1; J >= 0; --J) {
+    const int J0 = std::max(0, stop_tile);
+    for (int J = plan.nt - 1; J >= J0; --J) {
       diag(J, 1);
       FETIRP_LAUNCH_CHECK();
-      int nr = plan.row_off[J + 1] - plan.row_off[J];
+      // targets: the block rows I < J of row J (ascending), those >= J0 only
+      int b = plan.row_off[J];
+      const int e = plan.row_off[J + 1];
+      if (J0 > 0)
+        b = (int)(std::lower_bound(plan.row_cols.begin() + b, plan.row_cols.begin() + e, J0) - plan.row_cols.begin());
+      const int nr = e - b;
       if (nr > 0) {
-        k_tri_update<<<dim3(nr, ceil_div(nrhs, TU_RHS), TILE / 16), 256, 0, s>>>(L, npad, J, plan.d_row_cols.p + plan.row_off[J],
+        k_tri_update<<<dim3(nr, ceil_div(nrhs, TU_RHS), TILE / 16), 256, 0, s>>>(L, npad, J, plan.d_row_cols.p + b,
                                                                       X, ldx, nrhs, 1);
         FETIRP_LAUNCH_CHECK();
       }

@@ -1,5 +1,8 @@
 // Interface operators of one structure: the signed Boolean gather/scatter (Eq. 2, blocked storage of
 // Eq. 9), the coarse space G = [B(s) N(s)] of Eq. 3 and the multivector split.
+#include <type_traits>
+
+#include "ds.cuh"
 #include "ops.cuh"
 
 namespace fetirp {
@@ -135,10 +138,7 @@ __device__ __forceinline__ void dsm(float ah, float al, float bh, float bl, floa
   sl = __fadd_rn(sl, __fadd_rn(e, pl));
   sh = t;
 }
-__device__ __forceinline__ void dsplit(double v, float& h, float& l) {
-  h = (float)v;
-  l = (float)(v - (double)h);
-}
+__device__ __forceinline__ void dsplit(double v, float& h, float& l) { d2ds(v, h, l); }
 
 __global__ void k_split_pairs(long long n, const double* __restrict__ x, float* __restrict__ h,
                               float* __restrict__ l) {
@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(GTV_THREADS, WIDE ? 2 : 3) k_gt_v_ds(Layout L,
   }
 #pragma unroll
   for (int m = 0; m < MAX_KDIM; ++m) {
-    red[w][m][lane] = (double)h0[m] + (double)e0[m];
-    red[w][m][lane + 32] = (double)h1[m] + (double)e1[m];
+    red[w][m][lane] = ds2d(h0[m], e0[m]);
+    red[w][m][lane + 32] = ds2d(h1[m], e1[m]);
   }
   __syncthreads();
   const int t = threadIdx.x;
@@ -242,7 +242,11 @@ __global__ void k_g_apply_ds(Layout L, const float* __restrict__ Ah, const float
       if (m < kd) dsm(ch[m], cl[m], Ah[a0 + (size_t)m * k], Al[a0 + (size_t)m * k], h, l);
   }
   double* o = out + idx;
-  *o = (beta == 0.0 ? 0.0 : beta * *o) + alpha * ((double)h + (double)l);
+  const double x = ds2d(h, l);
+  // the projection's call (alpha = -1, beta = 1) costs one FP64 add per element
+  const bool minus = bits64(alpha) == bits64(-1.0), keep = bits64(beta) == bits64(1.0);
+  if (keep && minus) *o = *o - x;
+  else *o = is_zero(beta) ? alpha * x : fma(alpha, x, beta * *o);
 }
 
 // Block (s, t) of G^T G for one neighbour pair: sum over rows linking s and t.  Threads split the boundary
@@ -291,14 +295,17 @@ __global__ void __launch_bounds__(128) k_gtg(Layout L, const int* __restrict__ p
 // links are added in CSR order, as the plain definition does.
 constexpr int GT_SLOTS = 64, GT_LINKS = 512;
 // SPLIT 0: plain; 1: FP32 value split into a tf32 pair (TO = float); 2: split into a bf16 pair (TO = bf16),
-// hi -> Y, lo -> Y2
+// hi -> Y, lo -> Y2.  The links are summed in FP64: the first link's signed value by a sign-bit flip, each further
+// one (a minority of the slots have more than one) by an FP64 add; FP32 and narrower outputs are then rounded to
+// FP32 by integer operations (d2f_rn), so that the narrow FP64 pipe does no per-element conversion.
 template <typename TO, int SPLIT>
 __global__ void __launch_bounds__(256) k_gather_tile(Layout L, const double* __restrict__ V, int k, PatView<TO> Y,
                                                      PatView<TO> Y2, double alpha, double beta) {
+  using ACC = std::conditional_t<std::is_same<TO, double>::value, double, float>;
   __shared__ int sptr[GT_SLOTS + 1];
   __shared__ int srow[GT_LINKS];
   __shared__ int8_t ssg[GT_LINKS];
-  __shared__ double tile[GT_SLOTS][65];
+  __shared__ ACC tile[GT_SLOTS][65];
   const int s = blockIdx.x;
   const int b0 = L.occ_obase[s], nb = L.occ_obase[s + 1] - b0;
   const int j0 = blockIdx.y * GT_SLOTS;
@@ -329,24 +336,24 @@ __global__ void __launch_bounds__(256) k_gather_tile(Layout L, const double* __r
     y0[u] = 0.0;
     y1[u] = 0.0;
     if (ea[u] < eb[u]) {
-      const double sg = (double)ls[ea[u]];
+      const bool neg = ls[ea[u]] < 0;
       const double* vr = V + (size_t)lr[ea[u]] * k + lane;
-      if (c0) y0[u] = fma(sg, vr[0], 0.0);
-      if (c1) y1[u] = fma(sg, vr[32], 0.0);
+      if (c0) y0[u] = neg_if(vr[0], neg);
+      if (c1) y1[u] = neg_if(vr[32], neg);
     }
   }
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     for (int e = ea[u] + 1; e < eb[u]; ++e) {
-      const double sg = (double)ls[e];
+      const bool neg = ls[e] < 0;
       const double* vr = V + (size_t)lr[e] * k + lane;
-      if (c0) y0[u] = fma(sg, vr[0], y0[u]);
-      if (c1) y1[u] = fma(sg, vr[32], y1[u]);
+      if (c0) y0[u] += neg_if(vr[0], neg);
+      if (c1) y1[u] += neg_if(vr[32], neg);
     }
     const int jl = w + 8 * u;
     if (jl < ns) {
-      tile[jl][lane] = y0[u];
-      tile[jl][lane + 32] = y1[u];
+      tile[jl][lane] = from_f64<ACC>(y0[u]);
+      tile[jl][lane + 32] = from_f64<ACC>(y1[u]);
     }
   }
   __syncthreads();
@@ -356,19 +363,20 @@ __global__ void __launch_bounds__(256) k_gather_tile(Layout L, const double* __r
     if (jl >= ns) continue;
     const long long o = ((long long)q * k + g) * ld + off + jl;
     if constexpr (SPLIT == 1) {
-      const float v = (float)tile[jl][g];
+      const float v = tile[jl][g];
       uint32_t h;
       asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
       Y.base[p][o] = (TO)__uint_as_float(h);
       Y2.base[p][o] = (TO)(v - __uint_as_float(h));
     } else if constexpr (SPLIT == 2) {
-      const float v = (float)tile[jl][g];
+      const float v = tile[jl][g];
       const __nv_bfloat16 h = __float2bfloat16_rn(v);
       Y.base[p][o] = (TO)h;
       Y2.base[p][o] = (TO)__float2bfloat16_rn(v - __bfloat162float(h));
     } else {
       TO* y = Y.base[p] + o;
-      *y = (TO)((beta == 0.0 ? 0.0 : beta * (double)*y) + alpha * tile[jl][g]);
+      const ACC a = (ACC)alpha, b = (ACC)beta;
+      *y = (TO)(b == ACC(0) ? a * tile[jl][g] : b * (ACC)*y + a * tile[jl][g]);
     }
   }
 }
@@ -424,10 +432,15 @@ __global__ void k_scatter(Layout L, PatView<TI> Z, int k, double beta, double* _
     const int p = L.occ_pat[s];
     const int q = L.occ_q[s];
     const int j = slot - L.occ_obase[s];
-    acc += (double)sg * (double)Z.base[p][((long long)q * k + g) * Z.ld[p] + Z.off[p] + j];
+    const TI z = Z.base[p][((long long)q * k + g) * Z.ld[p] + Z.off[p] + j];
+    double v;
+    if constexpr (std::is_same<TI, float>::value) v = f2d(z);   // exact, integer operations
+    else v = (double)z;
+    v = neg_if(v, sg < 0);
+    acc = e == 0 ? v : acc + v;   // the first slot costs no FP64 add
   }
   double* o = out + idx;
-  *o = (beta == 0.0 ? 0.0 : beta * *o) + acc;
+  *o = is_zero(beta) ? acc : beta * *o + acc;
 }
 
 // S(r)[row][g] = sum over the row's slots in column g of r[row] / (slots of the row); one thread per element
@@ -437,10 +450,12 @@ __global__ void k_split(Layout L, const double* __restrict__ r, int k, double* _
   if (idx >= (long long)L.n_lambda * k) return;
   const int row = (int)(idx / k), g = (int)(idx % k);
   const int g0 = L.row_grp[2 * row], g1 = L.row_grp[2 * row + 1];
-  const double w = r[row] * L.row_wt[row];
+  const bool m0 = g0 == g, m1 = g1 == g;
   double z = 0.0;
-  if (g0 == g) z += w;
-  if (g1 == g) z += w;
+  if (m0 || m1) {   // at most two of a row's k elements: the FP64 product only there
+    const double w = r[row] * L.row_wt[row];
+    z = m0 && m1 ? w + w : w;
+  }
   Z[idx] = z;
 }
 

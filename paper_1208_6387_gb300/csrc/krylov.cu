@@ -3,6 +3,7 @@
 // numerical-issues subsection).
 #include <mutex>
 
+#include "ds.cuh"
 #include "ops.cuh"
 #include "normalise_warp.cuh"
 
@@ -111,10 +112,7 @@ __device__ __forceinline__ void ds_madd(float ah, float al, float bh, float bl, 
   sl = __fadd_rn(sl, __fadd_rn(e, pl));
   sh = t;
 }
-__device__ __forceinline__ void ds_split(double v, float& h, float& l) {
-  h = (float)v;
-  l = (float)(v - (double)h);
-}
+__device__ __forceinline__ void ds_split(double v, float& h, float& l) { d2ds(v, h, l); }
 // Register tiling: every thread sums 4 x 4 outputs (rows i of W, columns j of [Q | r]) over a slice of the chunk's
 // rows, so each staged pair is read once per 4 products; the slices are added in slice order at the end.
 constexpr int ETA_DS_ROWS = 32;   // rows staged per step
@@ -177,7 +175,7 @@ __global__ void __launch_bounds__(256) k_eta_partial_ds(int n, int k, const doub
     for (int u = 0; u < 4; ++u) {
       __syncthreads();
 #pragma unroll
-      for (int v = 0; v < 4; ++v) red[tid][v] = act ? (double)h[u][v] + (double)l[u][v] : 0.0;
+      for (int v = 0; v < 4; ++v) red[tid][v] = act ? ds2d(h[u][v], l[u][v]) : 0.0;
       __syncthreads();
       if (act && sl == 0) {
         const int i = i0 + u;
@@ -403,8 +401,9 @@ __global__ void __launch_bounds__(256) k_update(int n, int k, const double* __re
     const long long row = base + sub;
     const bool ok = row < n;
     const bool v0 = ok && c0 < k, v1 = two && ok && c0 + 32 < k;
-    const TH w0h = v0 ? (TH)W[row * k + c0] : TH(0), q0h = v0 ? (TH)Q[row * k + c0] : TH(0);
-    const TH w1h = v1 ? (TH)W[row * k + c0 + 32] : TH(0), q1h = v1 ? (TH)Q[row * k + c0 + 32] : TH(0);
+    const TH w0h = v0 ? from_f64<TH>(W[row * k + c0]) : TH(0), q0h = v0 ? from_f64<TH>(Q[row * k + c0]) : TH(0);
+    const TH w1h = v1 ? from_f64<TH>(W[row * k + c0 + 32]) : TH(0);
+    const TH q1h = v1 ? from_f64<TH>(Q[row * k + c0 + 32]) : TH(0);
     TH wn0 = TH(0), qn0 = TH(0), wn1 = TH(0), qn1 = TH(0);
     const int ca = c0 < k ? c0 : 0, cb = c0 + 32 < k ? c0 + 32 : 0;
     for (int j = 0; j < k; ++j) {
@@ -668,7 +667,7 @@ __global__ void __launch_bounds__(128) k_small_gemm_ds(int m, int k, const float
                 h1, l1);
       }
       for (; j < j1; j += slices) ds_madd(ah[j], al[j], Bh[(size_t)j * k + g], Bl[(size_t)j * k + g], h0, l0);
-      acc = ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
+      acc = ds2d(h0, l0) + ds2d(h1, l1);
     }
     for (int off = kp; off < 32; off <<= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     if (sl == 0 && g < k) C[(size_t)row * k + g] = acc;
@@ -714,11 +713,11 @@ template void update<float>(int, int, const double*, const double*, const double
 // (64-column tile, group, 256-row chunk) are taken from the live history count a on the device, so a fixed
 // grid serves every iteration of a captured graph.  Per item the chunk's rows and weights are staged in shared
 // memory with one round of independent loads, the 8 warps take every 8th row (a warp reads 64 consecutive
-// history columns of one row), and the warp sums are added in warp order; chunk partials are then added in
-// chunk order (deterministic).
+// history columns of one row; eight rows' loads are issued together before their products), and the warp sums
+// are added in warp order; chunk partials are then added in chunk order (deterministic).
 constexpr int GS_ROWS = 256;   // rows per chunk
 constexpr int GS_COLS = 64;    // history columns per item
-constexpr int GS_GRID = 1216;  // 8 CTAs per SM
+constexpr int GS_GRID = 608;   // 4 CTAs per SM (64 registers a thread: the batched loads)
 __global__ void k_group_wr(int total, const int* __restrict__ grp_row, const int* __restrict__ grp_src,
                            const double* __restrict__ grp_w, const double* __restrict__ r, double* __restrict__ wd,
                            float* __restrict__ wh, float* __restrict__ wl) {
@@ -726,12 +725,10 @@ __global__ void k_group_wr(int total, const int* __restrict__ grp_row, const int
   if (e >= total) return;
   const double v = grp_w[e] * r[grp_src ? grp_src[e] : grp_row[e]];
   wd[e] = v;
-  const float vh = (float)v;
-  wh[e] = vh;
-  wl[e] = (float)(v - (double)vh);
+  d2ds(v, wh[e], wl[e]);
 }
 template <typename TH>
-__global__ void __launch_bounds__(256) k_gram_split(int a_max, const int* __restrict__ d_a, int k,
+__global__ void __launch_bounds__(256, 4) k_gram_split(int a_max, const int* __restrict__ d_a, int k,
                                                     const TH* __restrict__ Qh, int n, int hk,
                                                     const int* __restrict__ grp_ptr, const int* __restrict__ grp_row,
                                                     const double* __restrict__ wd, const float* __restrict__ wh,
@@ -772,23 +769,36 @@ __global__ void __launch_bounds__(256) k_gram_split(int a_max, const int* __rest
         // split exactly into p + e by an FMA, q * s_lo is rounded (its error is ~2^-48 |q s|), and each column
         // sum is an unevaluated pair (hi, lo) updated by TwoSum; FP64 converts only the pairs at the end.  The
         // _rn intrinsics keep the compiler from contracting the error-free transformations into FMAs.
-  #pragma unroll 8
-        for (int i = warp; i < cnt; i += 8) {
-          const size_t ro = (size_t)srow[i] * hk;
-          const float sh = swh[i], sl = swl[i];
-          const float q0 = ok0 ? (float)q0p[ro] : 0.f;
-          const float q1 = ok1 ? (float)q1p[ro] : 0.f;
-          {
-            const float p = __fmul_rn(q0, sh), e = fmaf(q0, sh, -p), t = fmaf(q0, sl, e);
-            const float u = __fadd_rn(h0, p), bb = __fsub_rn(u, h0);
-            l0 = __fadd_rn(l0, __fadd_rn(__fadd_rn(__fsub_rn(h0, __fsub_rn(u, bb)), __fsub_rn(p, bb)), t));
-            h0 = u;
+        for (int i0 = warp; i0 < cnt; i0 += 64) {   // rows i0, i0 + 8, ..., i0 + 56: loads first, then products
+          float qa[8], qb[8], sh[8], sl[8];
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            const int i = i0 + 8 * v;
+            const bool okr = i < cnt;
+            const int ic = okr ? i : 0;   // every shared index stays below GS_ROWS
+            const size_t ro = (size_t)srow[ic] * hk;
+            qa[v] = okr && ok0 ? (float)q0p[ro] : 0.f;
+            qb[v] = okr && ok1 ? (float)q1p[ro] : 0.f;
+            sh[v] = okr ? swh[ic] : 0.f;
+            sl[v] = okr ? swl[ic] : 0.f;
           }
-          {
-            const float p = __fmul_rn(q1, sh), e = fmaf(q1, sh, -p), t = fmaf(q1, sl, e);
-            const float u = __fadd_rn(h1, p), bb = __fsub_rn(u, h1);
-            l1 = __fadd_rn(l1, __fadd_rn(__fadd_rn(__fsub_rn(h1, __fsub_rn(u, bb)), __fsub_rn(p, bb)), t));
-            h1 = u;
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            if (i0 + 8 * v >= cnt) break;
+            {
+              const float q0 = qa[v];
+              const float p = __fmul_rn(q0, sh[v]), e = fmaf(q0, sh[v], -p), t = fmaf(q0, sl[v], e);
+              const float u = __fadd_rn(h0, p), bb = __fsub_rn(u, h0);
+              l0 = __fadd_rn(l0, __fadd_rn(__fadd_rn(__fsub_rn(h0, __fsub_rn(u, bb)), __fsub_rn(p, bb)), t));
+              h0 = u;
+            }
+            {
+              const float q1 = qb[v];
+              const float p = __fmul_rn(q1, sh[v]), e = fmaf(q1, sh[v], -p), t = fmaf(q1, sl[v], e);
+              const float u = __fadd_rn(h1, p), bb = __fsub_rn(u, h1);
+              l1 = __fadd_rn(l1, __fadd_rn(__fadd_rn(__fsub_rn(h1, __fsub_rn(u, bb)), __fsub_rn(p, bb)), t));
+              h1 = u;
+            }
           }
         }
       } else {
@@ -804,8 +814,8 @@ __global__ void __launch_bounds__(256) k_gram_split(int a_max, const int* __rest
       }
     }
     if (sizeof(TH) == 4) {
-      a0 = (double)h0 + (double)l0;
-      a1 = (double)h1 + (double)l1;
+      a0 = ds2d(h0, l0);
+      a1 = ds2d(h1, l1);
     }
     red[warp][lane] = a0;   // (the previous item's reads of red ended before this item's staging barrier)
     red[warp][lane + 32] = a1;
@@ -848,9 +858,7 @@ __global__ void __launch_bounds__(256) k_hist_dot(int n, int a, const TH* __rest
       if (tid < cnt) {
         const double v = r[sb + tid];
         sr[tid] = v;
-        const float vh = (float)v;
-        srh[tid] = vh;
-        srl[tid] = (float)(v - (double)vh);
+        d2ds(v, srh[tid], srl[tid]);
       }
       __syncthreads();
       if (sizeof(TH) == 4) {
@@ -884,8 +892,8 @@ __global__ void __launch_bounds__(256) k_hist_dot(int n, int a, const TH* __rest
       }
     }
     if (sizeof(TH) == 4) {
-      a0 = (double)h0 + (double)l0;
-      a1 = (double)h1 + (double)l1;
+      a0 = ds2d(h0, l0);
+      a1 = ds2d(h1, l1);
     }
     __syncthreads();
     red[warp][lane] = a0;
@@ -1039,7 +1047,7 @@ __global__ void __launch_bounds__(256) k_tall_update(int n, int a_max, const int
 #pragma unroll
       for (int v = 0; v < CPT; ++v) {
         const int g = tx + TXC * v;
-        if (row < n && g < k) W[(size_t)row * k + g] += alpha * (double)acc[u][v];
+        if (row < n && g < k) W[(size_t)row * k + g] = fma(alpha, to_f64(acc[u][v]), W[(size_t)row * k + g]);
       }
     }
     return;
@@ -1074,7 +1082,7 @@ __global__ void __launch_bounds__(256) k_tall_update(int n, int a_max, const int
       v1 += __ldcg(part + (size_t)(sp + 1) * n * k + o);
     }
     if (sp < splits) v0 += __ldcg(part + (size_t)sp * n * k + o);
-    W[o] += alpha * (double)(v0 + v1);
+    W[o] = fma(alpha, to_f64(v0 + v1), W[o]);
   }
 }
 
@@ -1178,7 +1186,7 @@ __global__ void __launch_bounds__(256, 2) k_tall_update_w32(int n, int a_max, co
 __global__ void k_coef_to_f32(int a_max, const int* __restrict__ d_a, int k, const double* __restrict__ C,
                               float* __restrict__ Cf) {
   const int a = d_a ? min(*d_a, a_max) : a_max;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a * k; i += gridDim.x * blockDim.x) Cf[i] = (float)C[i];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a * k; i += gridDim.x * blockDim.x) Cf[i] = d2f_rn(C[i]);
 }
 
 void tall_update_init() {

@@ -20,6 +20,7 @@
 // expired wait sets *A.err and the CTA returns, so a failure ends the launch instead of hanging it.
 #include <mutex>
 
+#include "ds.cuh"
 #include "ops.cuh"
 #include "normalise_warp.cuh"
 
@@ -94,7 +95,8 @@ __device__ __forceinline__ double qraw(const PersistArgs& A, int row, int g) {
   for (int e = 0; e < 2; ++e) {
     const int sg = A.L.row_sign[2 * row + e];
     if (sg == 0) continue;
-    acc += (double)sg * (double)Z[A.row_z[2 * row + e] + (long long)g * A.row_zld[2 * row + e]];
+    const double z = neg_if(to_f64(Z[A.row_z[2 * row + e] + (long long)g * A.row_zld[2 * row + e]]), sg < 0);
+    acc = e == 0 ? z : acc + z;
   }
   return acc;
 }
@@ -149,7 +151,7 @@ __device__ void gtv_item(const PersistArgs& A, int it, unsigned char* smem) {
         if (sg == 0) continue;
         const int row = L.ell_row[(size_t)slot * L.ell_w + e];
         const double v = from_split ? split_val(A, row, g) : qraw<TL>(A, row, g);
-        y = fma((double)sg, v, y);
+        y += neg_if(v, sg < 0);
       }
 #pragma unroll
       for (int m = 0; m < P_MAXKD; ++m)
@@ -206,9 +208,7 @@ __device__ void gram_item(const PersistArgs& A, int a, int it, unsigned char* sm
     const double v = A.grp_w[e0 + tid] * A.r[row];
     srow[tid] = row;
     sw[tid] = v;
-    const float vh = (float)v;
-    swh[tid] = vh;
-    swl[tid] = (float)(v - (double)vh);
+    d2ds(v, swh[tid], swl[tid]);
   }
   __syncthreads();
   bool ok[4];
@@ -238,7 +238,7 @@ __device__ void gram_item(const PersistArgs& A, int a, int it, unsigned char* sm
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) res[u] = (double)h[u] + (double)l[u];
+    for (int u = 0; u < 4; ++u) res[u] = ds2d(h[u], l[u]);
   } else {
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll 4
@@ -357,7 +357,7 @@ __device__ void phase_tall(const PersistArgs& A, int a, unsigned char* smem) {
 #pragma unroll
       for (int i = 0; i < LC; ++i) {
         const int idx = tid + PT * i, cc = idx / KP, gg = idx % KP;
-        pc[i] = (idx < P_TU_CH * KP && c0 + cc < c_end && gg < k) ? (TH)A.C[(size_t)(c0 + cc) * k + gg] : TH(0);
+        pc[i] = (idx < P_TU_CH * KP && c0 + cc < c_end && gg < k) ? from_f64<TH>(A.C[(size_t)(c0 + cc) * k + gg]) : TH(0);
       }
     };
     if (c_begin < c_end) load(c_begin);
@@ -397,7 +397,7 @@ __device__ void phase_tall(const PersistArgs& A, int a, unsigned char* smem) {
           const int g = tx + TXC * v;
           if (row < n && g < k) {
             const size_t o = (size_t)row * k + g;
-            A.Zr[o] = A.Zr[o] - gapply(A, row, g) - (double)acc[u][v];
+            A.Zr[o] = A.Zr[o] - gapply(A, row, g) - to_f64(acc[u][v]);
           }
         }
       }
@@ -436,7 +436,7 @@ __device__ void phase_tall(const PersistArgs& A, int a, unsigned char* smem) {
       }
       for (; q < splits; ++q) v0 += part[(size_t)q * n * k + o];
       const int row = r0 + idx / k, g = idx % k;
-      A.Zr[o] = A.Zr[o] - gapply(A, row, g) - (double)((v0 + v1) + (v2 + v3));
+      A.Zr[o] = A.Zr[o] - gapply(A, row, g) - to_f64((v0 + v1) + (v2 + v3));
     }
   }
 }
@@ -487,9 +487,9 @@ __device__ void phase_local(const PersistArgs& A, unsigned char* smem) {
           for (int e = 0; e < L.ell_w; ++e) {
             const int sg = L.ell_sign[(size_t)slot * L.ell_w + e];
             if (sg == 0) continue;
-            y = fma((double)sg, A.Zr[(size_t)L.ell_row[(size_t)slot * L.ell_w + e] * k + g], y);
+            y += neg_if(A.Zr[(size_t)L.ell_row[(size_t)slot * L.ell_w + e] * k + g], sg < 0);
           }
-          yv = (TL)y;
+          yv = from_f64<TL>(y);
         }
         sb[kk][r] = yv;
       }
@@ -637,7 +637,7 @@ __device__ void phase_update(const PersistArgs& A, int a, unsigned char* smem) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   TH* Wn = (TH*)A.Wh + hist_col(a, A.n, A.k);   // the new block (a is a multiple of k)
   TH* Qn = (TH*)A.Qh + hist_col(a, A.n, A.k);
-  for (int idx = tid; idx < k * k; idx += PT) sT[idx / k][idx % k] = (TH)A.T[idx];
+  for (int idx = tid; idx < k * k; idx += PT) sT[idx / k][idx % k] = from_f64<TH>(A.T[idx]);
   if (tid < k) {
     double v = 0.0;
     for (int c = 0; c < k; ++c) v = fma(A.T[(size_t)tid * k + c], A.alpha[c], v);
@@ -655,7 +655,7 @@ __device__ void phase_update(const PersistArgs& A, int a, unsigned char* smem) {
     const long long row = base + sub;
     const bool ok = row < n && c0 < k;
     const double w0 = ok ? A.Zr[row * k + c0] : 0.0, q0 = ok ? A.Q[row * k + c0] : 0.0;
-    const TH w0h = (TH)w0, q0h = (TH)q0;
+    const TH w0h = from_f64<TH>(w0), q0h = from_f64<TH>(q0);
     TH wn = TH(0), qn = TH(0);
     const int ca = c0 < k ? c0 : 0;
     for (int j = 0; j < k; ++j) {

@@ -1,5 +1,5 @@
 // Tensor-core local products Z_p = S_p^+ Y_p on sm_103a: tcgen05.mma (kind::tf32, or kind::f16 with bf16
-// operands) with the accumulator in TMEM, operands staged by TMA (128-byte swizzle) through a 2-stage mbarrier
+// operands) with the accumulators in TMEM, operands staged by TMA (64-byte swizzle) through a 3-stage mbarrier
 // pipeline.
 //
 // Precision: both operands are split into pairs, x = hi + lo with hi = round(x) to the operand type and
@@ -8,10 +8,13 @@
 // local products); bf16 pairs carry 16 (near 2^-16, at twice the tensor rate of tf32).  The FP64 outer
 // refinement of the solver removes either error.
 //
-// One CTA computes a 128 (rows of S^+) x 256 (right-hand sides) tile of one pattern.  Warp roles: warp 0
-// lane 0 issues TMA loads, warp 1 lane 0 issues the MMAs, all four warps drain TMEM in the epilogue.  Every
-// wait on an mbarrier is bounded: on expiry the CTA records an error code, stops issuing work, waits (again
-// bounded) for its own MMAs to retire, frees TMEM and returns.
+// One CTA computes a 256 (rows of S^+) x 256 (right-hand sides) tile of one pattern as two 128 x 256 halves,
+// each an MMA of M = 128, N = 256 into its own TMEM accumulator (the two fill the 512 TMEM columns): both halves
+// use the same staged right-hand-side tile, so a K step loads 64 KB for 12 MMAs instead of 96 KB for 12 with one
+// 128-row half (operand bytes per flop from L2 are what limits this kernel).  Warp roles: warp 0 lane 0 issues
+// TMA loads, warp 1 lane 0 issues the MMAs, all eight warps drain TMEM in the epilogue (warps w and w + 4 the
+// same 32 TMEM lanes of the two halves).  Every wait on an mbarrier is bounded: on expiry the CTA records an
+// error code, stops issuing work, waits (again bounded) for its own MMAs to retire, frees TMEM and returns.
 #include <cuda.h>
 
 #include <algorithm>
@@ -25,15 +28,17 @@ namespace fetirp {
 
 namespace {
 
-// 128 x 256 output tile per CTA (one MMA of M = 128, N = 256): a wider tile loads 25 % fewer operand bytes per
-// flop from L2 than a square 128 x 128 one, which the three-product split makes the limiter
-constexpr int BM = 128, BN = 256;
-constexpr int ROW_BYTES = 128;                    // one K step of a tile row = one 128-byte swizzle row
-constexpr int STAGES = 2;
-constexpr int TILE_A_BYTES = BM * ROW_BYTES;      // 16 KB
-constexpr int TILE_B_BYTES = BN * ROW_BYTES;      // 32 KB
-constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + 2 * TILE_B_BYTES;   // A_hi, A_lo, B_hi, B_lo
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+// 256 x 256 output tile per CTA (two 128 x 256 halves)
+constexpr int BM = 256, BMH = 128, BN = 256;
+constexpr int ROW_BYTES = 64;                     // one K step of a tile row = one 64-byte swizzle row
+constexpr int STAGES = 3;
+constexpr int TILE_A_BYTES = BM * ROW_BYTES;      // 16 KB (both halves; the second starts 8 KB in)
+constexpr int TILE_B_BYTES = BN * ROW_BYTES;      // 16 KB
+constexpr int STAGE_BYTES = 2 * TILE_A_BYTES + 2 * TILE_B_BYTES;   // A_hi, A_lo, B_hi, B_lo: 64 KB
+constexpr int TMEM_COLS = 2 * BN;                 // two FP32 accumulators of 256 columns
+constexpr int THREADS = 256;
+// stages, 1024 bytes of alignment slack, barriers and flags, and 4 KB of margin past the last stage
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + 4096;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // a bounded wait gives up after 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -83,15 +88,15 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* ba
       : "memory");
 }
 
-// Shared-memory matrix descriptor (tcgen05): K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+// Shared-memory matrix descriptor (tcgen05): K-major, 64-byte swizzle, 8-row groups 512 bytes apart.
 __device__ __forceinline__ uint64_t smem_desc(const void* p) {
   const uint64_t addr = smem_u32(p);
   uint64_t d = 0;
   d |= (addr >> 4) & 0x3FFFull;                 // start address
   d |= (uint64_t)(16 >> 4) << 16;               // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset: next 8-row group
+  d |= (uint64_t)((8 * ROW_BYTES) >> 4) << 32;  // stride byte offset: next 8-row group
   d |= (uint64_t)1 << 46;                       // descriptor version (sm_100 family)
-  d |= (uint64_t)2 << 61;                       // layout: SWIZZLE_128B
+  d |= (uint64_t)4 << 61;                       // layout: SWIZZLE_64B
   return d;
 }
 
@@ -102,8 +107,8 @@ __device__ __forceinline__ uint32_t instr_desc() {
   d |= 1u << 4;                          // D format f32
   d |= (BF16 ? 1u : 2u) << 7;            // A format: bf16 (kind::f16) or tf32
   d |= (BF16 ? 1u : 2u) << 10;           // B format
-  d |= (uint32_t)(BN >> 3) << 17;  // N / 8
-  d |= (uint32_t)(BM >> 4) << 24;  // M / 16
+  d |= (uint32_t)(BN >> 3) << 17;   // N / 8
+  d |= (uint32_t)(BMH >> 4) << 24;  // M / 16 (one half)
   return d;
 }
 
@@ -143,10 +148,10 @@ struct TcParams {
 
 }  // namespace
 
-// BF16: operands are bf16 pairs (kind::f16, K = 16 per MMA, 64 per 128-byte row), else tf32 pairs
-// (kind::tf32, K = 8 per MMA, 32 per row); either way four MMAs of 32 bytes of K cover one row.
+// BF16: operands are bf16 pairs (kind::f16, K = 16 per MMA, 32 per 64-byte row), else tf32 pairs
+// (kind::tf32, K = 8 per MMA, 16 per row); either way two MMAs of 32 bytes of K cover one row.
 template <bool BF16>
-__global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcParams P) {
+__global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ TcParams P) {
   constexpr int BK = ROW_BYTES / (BF16 ? 2 : 4);   // K elements per stage
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -167,6 +172,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcPa
   const int tiles_n = (P.n_rhs[p] + BN - 1) / BN;
   const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
   const int nk = (P.n_b[p] + BK - 1) / BK;
+  const bool two = m0 + BMH < P.n_b[p];   // the second 128-row half has rows of S (else its MMAs are skipped)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -179,9 +185,9 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcPa
     *n_consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {   // TMEM allocation: BN fp32 columns, by one full warp
+  if (warp == 0) {   // TMEM allocation: two accumulators of BN fp32 columns, by one full warp
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(BN));
+                 "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -225,19 +231,26 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcPa
       if (*abort_flag) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       uint8_t* st = smem + s * STAGE_BYTES;
-      const uint64_t ahi = smem_desc(st), alo = smem_desc(st + TILE_A_BYTES);
       const uint64_t bhi = smem_desc(st + 2 * TILE_A_BYTES), blo = smem_desc(st + 2 * TILE_A_BYTES + TILE_B_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint64_t koff = (uint64_t)((kk * 32) >> 4);   // 32 bytes per MMA: 8 tf32 or 16 bf16 of K
-        if (BF16) {
-          mma_f16(tmem, ahi + koff, bhi + koff, idesc, (kb | kk) ? 1u : 0u);
-          mma_f16(tmem, ahi + koff, blo + koff, idesc, 1u);
-          mma_f16(tmem, alo + koff, bhi + koff, idesc, 1u);
-        } else {
-          mma_tf32(tmem, ahi + koff, bhi + koff, idesc, (kb | kk) ? 1u : 0u);
-          mma_tf32(tmem, ahi + koff, blo + koff, idesc, 1u);
-          mma_tf32(tmem, alo + koff, bhi + koff, idesc, 1u);
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !two) break;
+        // half h: rows h * 128 .. of the A tiles (8 KB in), accumulator at TMEM column h * BN
+        const uint64_t ahi = smem_desc(st + h * (BMH * ROW_BYTES));
+        const uint64_t alo = smem_desc(st + TILE_A_BYTES + h * (BMH * ROW_BYTES));
+        const uint32_t acc = tmem + (uint32_t)(h * BN);
+#pragma unroll
+        for (int kk = 0; kk < ROW_BYTES / 32; ++kk) {
+          const uint64_t koff = (uint64_t)((kk * 32) >> 4);   // 32 bytes per MMA: 8 tf32 or 16 bf16 of K
+          if (BF16) {
+            mma_f16(acc, ahi + koff, bhi + koff, idesc, (kb | kk) ? 1u : 0u);
+            mma_f16(acc, ahi + koff, blo + koff, idesc, 1u);
+            mma_f16(acc, alo + koff, bhi + koff, idesc, 1u);
+          } else {
+            mma_tf32(acc, ahi + koff, bhi + koff, idesc, (kb | kk) ? 1u : 0u);
+            mma_tf32(acc, ahi + koff, blo + koff, idesc, 1u);
+            mma_tf32(acc, alo + koff, bhi + koff, idesc, 1u);
+          }
         }
       }
       mma_commit(&empty[s]);   // frees the stage once these MMAs have read it
@@ -247,21 +260,23 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcPa
   }
   __syncwarp();
 
-  // epilogue: every warp waits for the accumulator, then drains its 32 TMEM lanes
+  // epilogue: every warp waits for the accumulators, then drains its 32 TMEM lanes of half warp / 4 (a warp
+  // reaches the TMEM lanes 32 (warp % 4) .. + 31 only)
   const bool ok = mbar_wait(done, 0);
   if (!ok) atomicCAS(P.error, 0, 3);
   // the TMEM loads below are warp-collective: take the decision for the whole CTA
   const bool drain = __syncthreads_and(ok && !*abort_flag) != 0;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (drain) {
-    const int row = m0 + warp * 32 + lane;
+  const int half = warp >> 2, quad = warp & 3;
+  if (drain && (half == 0 || two)) {
+    const int row = m0 + half * BMH + quad * 32 + lane;
     float* Z = P.Z[p];
     const long long ldz = P.ldz[p];
     const int nr = P.n_rhs[p];
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 32) {
       uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * BN + c0);
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
           "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -289,7 +304,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcPa
   }
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
 __global__ void k_split_tf32(const double* __restrict__ x, long long rows, long long cols, long long ld_in,
@@ -331,7 +346,7 @@ EncodeTiledFn encode_fn() {
 }
 
 // 2D map over a row-major (rows x cols, leading dimension ld) array of fp32 (esize 4) or bf16 (esize 2); box of
-// one 128-byte row of K (32 or 64 elements) x box_rows rows.
+// one 64-byte row of K (16 or 32 elements) x box_rows rows, 64-byte swizzle.
 void make_map(CUtensorMap* m, const void* base, long long rows, long long cols, long long ld, int box_rows,
               int esize) {
   if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * esize) % 16)
@@ -342,7 +357,7 @@ void make_map(CUtensorMap* m, const void* base, long long rows, long long cols, 
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode_fn()(m, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                            const_cast<void*>(base), dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Error(5, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
 }
@@ -403,8 +418,8 @@ void tc_gemm_split(const TcProblem& T, bool bf16, int* d_error, cudaStream_t s) 
     }
     P.tile_off[P.n_pat] = total;
     if (total == 0) continue;
-    if (bf16) k_tc_gemm<true><<<total, 128, SMEM_BYTES, s>>>(P);
-    else k_tc_gemm<false><<<total, 128, SMEM_BYTES, s>>>(P);
+    if (bf16) k_tc_gemm<true><<<total, THREADS, SMEM_BYTES, s>>>(P);
+    else k_tc_gemm<false><<<total, THREADS, SMEM_BYTES, s>>>(P);
     FETIRP_LAUNCH_CHECK();
   }
 }
