@@ -44,7 +44,7 @@ WORKLOADS = {
           "6 resident patterns (2D heat 16^2/32^2/64^2, 3D elastic 8^3/12^3/16^3), admitted by device memory",
 }
 DEFAULTS = {  # per workload: local-product precision, multivector width, direction-history cap (GB; 0 = library)
-    "c3": ("bf16x3", 32, 32.0), "c2": ("fp32", 8, 0.0), "c1": ("fp64", 4, 0.0), "c5": ("auto", 8, 0.0),
+    "c3": ("bf16x3", 16, 32.0), "c2": ("fp32", 8, 0.0), "c1": ("fp64", 4, 0.0), "c5": ("auto", 8, 0.0),
     "c4": ("auto", 0, 32.0),   # k = 0: autotuned
 }
 # Block iterations of the default workload (C3, k = 32, tol 1e-8): the count the library's FP64 solve needs
@@ -57,7 +57,7 @@ PHASE_KERNELS = {  # the kernels each phase launches
     "project": "k_gt_v, k_small_gemm, k_g_apply (FP64); k_split_pairs, k_gt_v_ds, k_small_gemm_ds, k_g_apply_ds "
                "(mixed forms)",
     "gram": "k_group_wr, k_gram_split + k_reduce_chunks_dyn, k_eta_partial(_ds) + k_eta_group_sums",
-    "reorth": "k_tall_update / k_tall_update_w32", "update": "k_split / k_perm_split, k_update",
+    "reorth": "k_tall_update / k_tall_update_w<16|32>", "update": "k_split / k_perm_split, k_update",
     "recover": "k_tri_*, k_unpermute_rotate", "normalise": "k_normalise",
     "iterate": "k_persist (whole block iterations in one cooperative launch)",
     "outer": "FP64 residual: k_gather_tile, k_local_gemm<double>, k_scatter, projection",
@@ -280,6 +280,17 @@ def run_ours(args, rank, world, local):
     roof["phases_ms_per_step"] = {F.PHASES[i]: round(float(ph_ms[i]) / args.steps, 3) for i in range(len(F.PHASES))}
     roof["phases_ms_per_step_untimed_probe"] = {F.PHASES[i]: round(float(probe_ms[i]), 3)
                                                 for i in range(len(F.PHASES))}
+    # the pattern set-up (tile Cholesky, L_S^{-1}, S^+): FP64 flops counted by the library from the tile plans
+    fi = F.PHASES.index("factor")
+    setup_roof = None
+    if ph_fl[fi] > 0 and ph_ms[fi] > 0:
+        ach = float(ph_fl[fi]) / (float(ph_ms[fi]) / 1e3) / 1e12
+        setup_roof = {"phase": "factor", "kernels": PHASE_KERNELS["factor"], "bound": "fp64",
+                      "achieved": round(ach, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                      "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                      "share_of_step": round(float(ph_ms[fi]) / total_ms, 4) if world == 1 else None,
+                      "peak_source": "nominal FP64 rate (no measured FP64 peak on this pool)",
+                      "work": "FP64 flops of the tile Cholesky (tile pairs with fill), L_S^{-1} and S^+ per step"}
     # the direction-history work (Gram products incl. eta, and the reorthogonalisation), its own key
     hg = [F.PHASES.index("gram"), F.PHASES.index("reorth")]
     hist_ms = float(sum(ph_ms[i] for i in hg))
@@ -373,6 +384,7 @@ def run_ours(args, rank, world, local):
                 "d2h_bytes_per_step": (prob.n_lambda + nu) * 8},
         "roofline": roof,
         "history_gram": history,
+        "setup_roofline": setup_roof,
         "clocks": clk.summary(local),
         "wall_s": round(wall, 4),
     }
@@ -629,7 +641,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "tf32x3", "bf16x3", "auto"],
                     help="local-product arithmetic (default per workload: c3 bf16x3, c2 fp32, c4/c5 auto)")
-    ap.add_argument("--k", type=int, default=None, help="multivector width (default per workload: c3 32, c2 8)")
+    ap.add_argument("--k", type=int, default=None, help="multivector width (default per workload: c3 16, c2 8, c4 autotuned)")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="relative tolerance of the inner solves; 0 = the library's per-precision default")
     ap.add_argument("--workload", default="c3", choices=list(WORKLOADS))
@@ -638,7 +650,7 @@ def main():
     ap.add_argument("--no-fp64-reference", action="store_true")
     ap.add_argument("--history-gb", type=float, default=None,
                     help="cap on the direction history (GB); 0 = the library default (half of free memory); "
-                         "default per workload: c3 32, others 0")
+                         "default per workload: c3 32, c4 32, others 0")
     ap.add_argument("--requests", type=int, default=1000, help="serving workload: number of structures")
     ap.add_argument("--rate", type=float, default=50.0, help="serving workload: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=4, help="serving workload: concurrent structures")

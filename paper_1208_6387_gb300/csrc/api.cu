@@ -560,8 +560,26 @@ void join_patterns(fetirp_ctx ctx, size_t np) {
   }
 }
 
+// FP64 flops of one pattern's set-up, counted from its tile plans (64^3 FMAs per tile product): the tile
+// Cholesky (diagonal factorisations, panel solves, trailing updates of every tile pair with fill), the kernel
+// solves, L_S^{-1} (a forward solve on the identity with the zero upper tiles skipped) and S^+ = L_S^{-T} L_S^{-1}
+// (lower triangle).  The Moore-Penrose correction (rank 2 kd) and the splits are not counted.
+double factor_flops(const PatternData& P) {
+  const double t3 = (double)TILE * TILE * TILE;
+  const double nt = P.plan.nt;
+  double f = 2.0 * t3 * (double)P.plan.pairs.size()          // trailing updates
+             + (2.0 / 3.0) * t3 * nt                          // diagonal tiles
+             + t3 * (double)P.plan.col_rows.size();           // panel solves
+  f += 2.0 * 2.0 * (double)P.kdim * TILE * TILE * (double)(P.plan.col_rows.size() + P.plan.nt);   // kernel N
+  const double nb = P.n_b;
+  f += 2.0 * (nb * nb * nb / 6.0) * 2.0;                       // L_S^{-1} and the lower-triangular product
+  return f;
+}
+
 void factorize_patterns(fetirp_ctx ctx, const std::vector<PatternData*>& pats) {
-  PhaseScope ph(ctx, FETIRP_PHASE_FACTOR, 0.0, 0.0);
+  double flops = 0.0;
+  for (const PatternData* P : pats) flops += factor_flops(*P);
+  PhaseScope ph(ctx, FETIRP_PHASE_FACTOR, flops, 0.0);
   const size_t np = pats.size();
   fork_patterns(ctx, np);
   for (size_t i = 0; i < np; ++i) factor_stage_a(*pats[i], ctx->opt.pivot_tol, ctx->fstreams[i]);

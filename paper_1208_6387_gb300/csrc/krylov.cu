@@ -1086,13 +1086,13 @@ __global__ void __launch_bounds__(256) k_tall_update(int n, int a_max, const int
   }
 }
 
-// The FP32-history update for k = 32 on a tall block (one split): 256-row tiles, each thread 8 rows (ty + 32 u)
-// x 4 columns (4 tx ..), with 16-byte shared loads along the history index (3 loads per 32 FMAs, so the FP32
-// pipe rather than the shared-memory port bounds it).  The 32-column history block of a tile is one contiguous
-// 32 KB range in the block layout (width 32); it is copied to shared memory with 16-byte asynchronous copies
+// The FP32-history update for k = 32 or 16 on a tall block (one split): 256-row tiles, each thread RPT rows
+// (ty + TY u) x 4 columns (4 tx ..), with 16-byte shared loads along the history index (about 1 load per 8 FMAs,
+// so the FP32 pipe rather than the shared-memory port bounds it).  A tile of 32 history columns is 32 / K blocks of
+// the block layout (width K), 256 rows each; it is copied to shared memory with 16-byte asynchronous copies
 // (cp.async) into two stages, the next tile in flight while the current one is used.  Rows >= n and history
-// columns >= a (a is a multiple of 32 here) are zero-filled by the copy.  Per output the history columns are
-// added in increasing order, one FMA each, as in k_tall_update.
+// columns >= a are zero-filled by the copy.  Per output the history columns are added in increasing order, one
+// FMA each, as in k_tall_update.
 constexpr int TW_ROWS = 256, TW_LD = 36;
 constexpr int TW_STAGE_FLOATS = TW_ROWS * TW_LD + 32 * 32;
 constexpr int TW_SMEM = 2 * TW_STAGE_FLOATS * 4;
@@ -1101,34 +1101,41 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
   const int n = valid ? 16 : 0;   // source bytes; the rest of the 16 is zero-filled
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
-__global__ void __launch_bounds__(256, 2) k_tall_update_w32(int n, int a_max, const int* __restrict__ d_a,
-                                                           const float* __restrict__ Wh,
-                                                           const float* __restrict__ Cf, double alpha,
-                                                           double* __restrict__ W) {
+template <int K>
+__global__ void __launch_bounds__(256, 2) k_tall_update_w(int n, int a_max, const int* __restrict__ d_a,
+                                                         const float* __restrict__ Wh,
+                                                         const float* __restrict__ Cf, double alpha,
+                                                         double* __restrict__ W) {
+  static_assert(K == 16 || K == 32, "history block width 16 or 32");
+  constexpr int TXN = K / 4;          // column groups of 4
+  constexpr int TY = 256 / TXN;       // row threads
+  constexpr int RPT = TW_ROWS / TY;   // rows per thread
   extern __shared__ __align__(16) float tw_smem[];
   const int a = d_a ? min(*d_a, a_max) : a_max;
   if (a <= 0) return;
   const int r0 = blockIdx.x * TW_ROWS;
-  const int tid = threadIdx.x, tx = tid >> 5, ty = tid & 31;
-  float acc[8][4];
+  const int tid = threadIdx.x, tx = tid / TY, ty = tid % TY;
+  float acc[RPT][4];
 #pragma unroll
-  for (int u = 0; u < 8; ++u)
+  for (int u = 0; u < RPT; ++u)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[u][j] = 0.f;
   auto issue = [&](int c0, int st) {   // tile of history columns c0 .. c0 + 31 into stage st
     float* sa = tw_smem + st * TW_STAGE_FLOATS;
     float* sc = sa + TW_ROWS * TW_LD;
-    const float* blk = Wh + (size_t)(c0 >> 5) * n * 32;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int q = tid + 256 * i, row = q >> 3, part = q & 7;
-      const int rr = r0 + row;
-      const bool ok = c0 + part * 4 + 4 <= a && rr < n;
-      cp_async16(sa + row * TW_LD + part * 4, blk + (size_t)(ok ? rr : 0) * 32 + part * 4, ok);
+      const int q = tid + 256 * i, row = q >> 3, part = q & 7;   // part: 4 history columns
+      const int rr = r0 + row, c = c0 + part * 4;
+      const bool ok = c + 4 <= a && rr < n;
+      const float* blk = Wh + (size_t)(c / K) * n * K + (c % K);
+      cp_async16(sa + row * TW_LD + part * 4, blk + (size_t)(ok ? rr : 0) * K, ok);
     }
-    const int cc = tid >> 3, gp = tid & 7;
-    const bool okc = c0 + cc < a;
-    cp_async16(sc + cc * 32 + gp * 4, Cf + (size_t)(okc ? c0 + cc : 0) * 32 + gp * 4, okc);
+    if (tid < 8 * K) {   // 32 x K coefficients, 4 per copy
+      const int cc = tid / (K / 4), gp = tid % (K / 4);
+      const bool okc = c0 + cc < a;
+      cp_async16(sc + cc * K + gp * 4, Cf + (size_t)(okc ? c0 + cc : 0) * K + gp * 4, okc);
+    }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
   const int ntile = (a + 31) / 32;
@@ -1147,10 +1154,10 @@ __global__ void __launch_bounds__(256, 2) k_tall_update_w32(int n, int a_max, co
     for (int cq = 0; cq < 8; ++cq) {
       float4 bv[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = *reinterpret_cast<const float4*>(sc + (cq * 4 + j) * 32 + tx * 4);
+      for (int j = 0; j < 4; ++j) bv[j] = *reinterpret_cast<const float4*>(sc + (cq * 4 + j) * K + tx * 4);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float4 av = *reinterpret_cast<const float4*>(sa + (ty + 32 * u) * TW_LD + cq * 4);
+      for (int u = 0; u < RPT; ++u) {
+        const float4 av = *reinterpret_cast<const float4*>(sa + (ty + TY * u) * TW_LD + cq * 4);
         acc[u][0] = fmaf(av.x, bv[0].x, acc[u][0]);
         acc[u][1] = fmaf(av.x, bv[0].y, acc[u][1]);
         acc[u][2] = fmaf(av.x, bv[0].z, acc[u][2]);
@@ -1172,10 +1179,10 @@ __global__ void __launch_bounds__(256, 2) k_tall_update_w32(int n, int a_max, co
     __syncthreads();   // every thread is done with stage t & 1 before tile t + 2 is copied into it
   }
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const int row = r0 + ty + 32 * u;
+  for (int u = 0; u < RPT; ++u) {
+    const int row = r0 + ty + TY * u;
     if (row >= n) continue;
-    double* w = W + (size_t)row * 32 + tx * 4;
+    double* w = W + (size_t)row * K + tx * 4;
 #pragma unroll
     for (int j = 0; j < 4; ++j) w[j] += alpha * (double)acc[u][j];
   }
@@ -1197,7 +1204,8 @@ void tall_update_init() {
   FETIRP_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) throw Error(1, "device ordinal out of range");
   if (!attr_set[dev]) {
-    FETIRP_CUDA(cudaFuncSetAttribute(k_tall_update_w32, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM));
+    FETIRP_CUDA(cudaFuncSetAttribute(k_tall_update_w<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM));
+    FETIRP_CUDA(cudaFuncSetAttribute(k_tall_update_w<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM));
     attr_set[dev] = true;
   }
 }
@@ -1235,10 +1243,14 @@ void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, int hk, 
     FETIRP_LAUNCH_CHECK();
     Ct = reinterpret_cast<const TH*>(Cf);
   }
-  if (sizeof(TH) == 4 && splits == 1 && k == 32 && hk == 32 && a_max % 32 == 0) {
+  if (sizeof(TH) == 4 && splits == 1 && (k == 32 || k == 16) && hk == k) {
     tall_update_init();
-    k_tall_update_w32<<<ceil_div(n, TW_ROWS), 256, TW_SMEM, s>>>(n, a_max, d_a, reinterpret_cast<const float*>(Wh),
-                                                                 reinterpret_cast<const float*>(Ct), alpha, W);
+    if (k == 32)
+      k_tall_update_w<32><<<ceil_div(n, TW_ROWS), 256, TW_SMEM, s>>>(n, a_max, d_a, reinterpret_cast<const float*>(Wh),
+                                                                     reinterpret_cast<const float*>(Ct), alpha, W);
+    else
+      k_tall_update_w<16><<<ceil_div(n, TW_ROWS), 256, TW_SMEM, s>>>(n, a_max, d_a, reinterpret_cast<const float*>(Wh),
+                                                                     reinterpret_cast<const float*>(Ct), alpha, W);
     FETIRP_LAUNCH_CHECK();
     return;
   }

@@ -71,3 +71,21 @@ def test_medium_operator_matches_the_oracle(medium, prec, tol):
     Qo = orc.PtFP(V)
     assert rel(Q, Qo) < tol, rel(Q, Qo)
     assert np.abs(Q - Qo).max() < 10 * tol * np.abs(Qo).max()
+
+
+@pytest.mark.parametrize("k", [16, 32])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_medium_solve_with_other_widths(medium, prec, k):
+    """The same structure with k = 16 and k = 32 contiguous occurrence groups (the specialised FP32 history
+    updates for those widths) against the stored direct solve."""
+    prob, lam_ref, u_ref = medium
+    ctx = F.fetirp_create(F.fetirp_default_options(precision=prec, tol=1e-10))
+    try:
+        F.load_problem(ctx, prob, groups=False)
+        F.fetirp_set_groups(ctx, k, (np.arange(prob.n_occ) * k // prob.n_occ).astype(np.int32))
+        lam, u, st = F.fetirp_solve(ctx, prob.n_lambda, prob.c, F.n_u(prob))
+    finally:
+        F.fetirp_destroy(ctx)
+    assert st["rel_residual"] <= 1e-10
+    assert rel(lam, lam_ref) < 1e-8, (rel(lam, lam_ref), st)
+    assert rel(u, u_ref) < 1e-8
