@@ -44,12 +44,13 @@ WORKLOADS = {
           "6 resident patterns (2D heat 16^2/32^2/64^2, 3D elastic 8^3/12^3/16^3), admitted by device memory",
 }
 DEFAULTS = {  # per workload: local-product precision, multivector width, direction-history cap (GB; 0 = library)
-    "c3": ("bf16x3", 16, 32.0), "c2": ("fp32", 8, 0.0), "c1": ("fp64", 4, 0.0), "c5": ("auto", 8, 0.0),
+    "c3": ("bf16x3", 4, 32.0), "c2": ("fp32", 8, 0.0), "c1": ("fp64", 4, 0.0), "c5": ("auto", 8, 0.0),
     "c4": ("auto", 0, 32.0),   # k = 0: autotuned
 }
-# Block iterations of the default workload (C3, k = 32, tol 1e-8): the count the library's FP64 solve needs
-# on this structure, used to scale the oracle's sampled per-iteration cost to a whole solve.
-C3_ITERATIONS = 120
+# Block iterations of the default workload (C3, k = 4, tol 1e-8): the count the library's solve needs on this
+# structure, used to scale the oracle's sampled per-iteration cost to a whole solve.  k = 4 is the width the
+# library's autotuner picks on C3 from {4, 8, 16, 32} (the direction-history work grows with k).
+C3_ITERATIONS = 132
 PHASE_KERNELS = {  # the kernels each phase launches
     "factor": "k_potrf_tile, k_trsm_tiles, k_update_pairs, k_tile_inverse, k_tri_*, k_lauum, k_split_tf32/bf16",
     "coarse": "k_gtg, k_gemm_f64",
@@ -416,8 +417,13 @@ def roofline(args, prob, F, peaks, src, ph_ms, ph_fl, ph_ln, stats):
                 "ms_per_launch": round(per_launch_ms, 4),
                 "peak_source": "hbm_gbs of " + src,
                 "work": "F-apply bytes (operators once + 2 n_lambda k 8 + 2 n_G k 8) x block iterations per launch"}
-    per_launch_ms = ph_ms[loc] / max(ph_ln[loc], 1)
-    flops_per_launch = ph_fl[loc] / max(ph_ln[loc], 1)
+    # one local product = 2 sum_p n_b^2 R_p useful flops; with a split reduction dimension (small blocks) it is
+    # the product kernel plus the in-order sum of its partials, both inside the phase's events
+    fl_one = sum(2.0 * p.n_b ** 2 * sum(1 for o in prob.occs if o.pattern == i) * prob.k
+                 for i, p in enumerate(prob.patterns))
+    n_prod = max(int(round(float(ph_fl[loc]) / fl_one)), 1) if fl_one > 0 else max(int(ph_ln[loc]), 1)
+    per_launch_ms = ph_ms[loc] / n_prod
+    flops_per_launch = ph_fl[loc] / n_prod
     achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12
     if args.fprec == "tf32x3":
         kern, bound = "k_tc_gemm (tcgen05 kind::tf32, 3 products)", "tensor"
@@ -435,8 +441,10 @@ def roofline(args, prob, F, peaks, src, ph_ms, ph_fl, ph_ln, stats):
         note = "FP64 nominal 1.25 TFLOP/s (152 SMs x 2070 MHz)"
     out = {"kernel": kern, "phase": "local", "bound": bound, "achieved": round(achieved, 3), "peak": round(peak, 2),
            "unit": "TFLOP/s", "frac": round(achieved / peak, 5), "traffic": None,
-           "flops_per_launch": flops_per_launch, "launches": int(ph_ln[loc]), "ms_per_launch": round(per_launch_ms, 4),
-           "peak_source": note, "work": "2 sum_p n_b^2 R_p per launch (R_p = occurrences of p x k)"}
+           "flops_per_launch": flops_per_launch, "launches": int(ph_ln[loc]), "products": n_prod,
+           "ms_per_launch": round(per_launch_ms, 4),
+           "peak_source": note, "work": "2 sum_p n_b^2 R_p per local product (R_p = occurrences of p x k); a product is one "
+                   "k_tc_gemm launch, plus k_tc_reduce when small blocks split the reduction dimension"}
     if args.fprec in ("tf32x3", "bf16x3"):
         out["issued_frac"] = round(3 * achieved / peak, 4)
     return out
@@ -641,7 +649,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "tf32x3", "bf16x3", "auto"],
                     help="local-product arithmetic (default per workload: c3 bf16x3, c2 fp32, c4/c5 auto)")
-    ap.add_argument("--k", type=int, default=None, help="multivector width (default per workload: c3 16, c2 8, c4 autotuned)")
+    ap.add_argument("--k", type=int, default=None, help="multivector width (default per workload: c3 4, c2 8, c4 autotuned)")
     ap.add_argument("--inner-tol", type=float, default=0.0,
                     help="relative tolerance of the inner solves; 0 = the library's per-precision default")
     ap.add_argument("--workload", default="c3", choices=list(WORKLOADS))

@@ -243,6 +243,7 @@ struct fetirp_ctx_s {
   DBuf<int> n_kept;
   DBuf<double> Y64, Z64;
   DBuf<float> Y32, Z32, Ylo32;
+  DBuf<float> tc_part;            // K-split partials of the tensor-core product (small blocks only)
   DBuf<int> tc_error;
   long long hist_cap = 0;
   int rr_blocks = 0;
@@ -645,6 +646,14 @@ void ensure_apply_buffers(fetirp_ctx ctx, int k) {
   total = std::max(total, total8);   // the bf16 products use the FP32 buffers with leading dimension ld_y8
   ctx->Y64.ensure(total); ctx->Z64.ensure(total);
   ctx->Y32.ensure(total); ctx->Z32.ensure(total); ctx->Ylo32.ensure(total);
+  TcProblem T;   // would the tensor-core product split its reduction dimension?
+  T.n_pat = (int)ctx->pats.size();
+  for (int p = 0; p < T.n_pat; ++p) {
+    T.n_b[p] = ctx->pats[p]->n_b;
+    T.n_rhs[p] = (int)ctx->use[p].occs.size() * k;
+  }
+  const int sp = tc_ksplits(T);
+  if (sp > 1) ctx->tc_part.ensure((size_t)sp * total);
 }
 
 void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, const double* c_dev) {
@@ -1210,6 +1219,8 @@ void apply_F(fetirp_ctx ctx, const double* in, double* out, int k, int prec, boo
     PatView<float> Yh{}, Yl{}, Zv{};
     TcProblem T;
     T.n_pat = n_pat;
+    T.part = ctx->tc_part.p;
+    T.part_elems = (long long)ctx->tc_part.n;
     double flops = 0, bytes = 0, rhs_elems = 0;
     for (int p = 0; p < n_pat; ++p) {
       PatternData& P = *ctx->pats[p];
@@ -1253,6 +1264,8 @@ void apply_F(fetirp_ctx ctx, const double* in, double* out, int k, int prec, boo
     PatView<float> Zv{};
     TcProblem T;
     T.n_pat = n_pat;
+    T.part = ctx->tc_part.p;
+    T.part_elems = (long long)ctx->tc_part.n;
     double flops = 0, bytes = 0, rhs_elems = 0;
     for (int p = 0; p < n_pat; ++p) {
       PatternData& P = *ctx->pats[p];
@@ -1493,7 +1506,8 @@ void reproject_lambda(fetirp_ctx ctx) {
 }
 
 struct Hist {
-  long long cols = 0;   // columns stored
+  long long cols = 0;    // columns stored
+  bool stalled = false;  // the last inner solve stopped making progress (see block_orthodir)
 };
 
 template <typename TH> TH* hist_w(fetirp_ctx ctx);
@@ -1899,7 +1913,14 @@ double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, His
       it_budget -= done;
       if (done < A.max_iters) break;   // the device found ||r|| <= target (or no direction kept)
     }
-  } else
+  } else {
+  // An inner solve of a mixed form whose residual has not dropped below 0.99 of its best for STALL iterations has
+  // reached what its low-precision operator (or, with the periodic shortcut, the rounded commutation of F with
+  // Pi) allows: it stops, and the outer FP64 step continues from the true residual with a fresh history.
+  const bool watch = prec != FETIRP_PREC_FP64;
+  const int STALL = std::max(200, 8 * G);
+  double best = rnorm;
+  int it_here = 0, best_it = 0;
   while (rnorm > target && it_budget > 0 && kept > 0) {
     const int g = std::min(G, it_budget);
     run_iterations<TH>(ctx, prec, g, g == G && ctx->opt.use_graphs, Wh, Qh);
@@ -1924,6 +1945,15 @@ double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, His
     kept = ctx->h_state[4];
     st.iterations += g;
     it_budget -= g;
+    it_here += g;
+    if (rnorm < 0.99 * best) {
+      best = rnorm;
+      best_it = it_here;
+    } else if (watch && it_here - best_it >= STALL) {
+      H.stalled = true;
+      break;
+    }
+  }
   }
   FETIRP_CUDA(cudaMemcpyAsync(ctx->h_state, ctx->d_state.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
   FETIRP_CUDA(cudaStreamSynchronize(s));
@@ -2107,6 +2137,10 @@ fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_st
         const double inner_target = std::max(inner_tol * rn, 0.5 * target);
         if (hist_fp64(ctx)) block_orthodir<double>(ctx, prec, inner_target, rn, H, st, budget);
         else block_orthodir<float>(ctx, prec, inner_target, rn, H, st, budget);
+        if (H.stalled) {   // the stored directions no longer serve the next inner solve
+          H.cols = 0;
+          H.stalled = false;
+        }
         reproject_lambda(ctx);
         residual(ctx);
         rn = norm2(ctx, ctx->r.p, nl);
@@ -2263,6 +2297,8 @@ void apply_noalloc(fetirp_ctx ctx, const double* V, double* Q, int k, int prec, 
     PatView<float> Yh{}, Yl{}, Zv{};
     TcProblem T;
     T.n_pat = n_pat;
+    T.part = ctx->tc_part.p;
+    T.part_elems = (long long)ctx->tc_part.n;
     for (int p = 0; p < n_pat; ++p) {
       PatternData& P = *ctx->pats[p];
       Yh.base[p] = (float*)(Yb + pbase[p] * es);

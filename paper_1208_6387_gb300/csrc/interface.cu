@@ -146,27 +146,34 @@ __global__ void k_split_pairs(long long n, const double* __restrict__ x, float* 
   if (i < n) dsplit(x[i], h[i], l[i]);
 }
 
-template <bool WIDE>
+// KL lanes per link (k <= KL <= 32, a power of two; WIDE: k <= 64 with two columns per lane and KL = 32): a warp
+// works on 32 / KL links at once, so that small blocks (k = 4, 8, 16) keep every lane busy.  Lane (sub, g):
+// column g of links sub, sub + 32 / KL, ...; the lanes of a column are added in FP64 by shuffles at the end.
+template <int KL, bool WIDE>
 __global__ void __launch_bounds__(GTV_THREADS, WIDE ? 2 : 3) k_gt_v_ds(Layout L, const double* __restrict__ V, int k,
                                                             double* __restrict__ X, int chunk) {
+  static_assert(!WIDE || KL == 32, "two columns per lane only with 32 lanes per link");
+  constexpr int SUB = 32 / KL;            // links a warp works on at once
+  constexpr int WORKERS = (GTV_THREADS / 32) * SUB;
   __shared__ double red[GTV_THREADS / 32][MAX_KDIM][64];
   __shared__ int s_last;
   const int s = blockIdx.x, c = blockIdx.y, nch = gridDim.y;
   const int kd = L.kdim[L.occ_pat[s]];
   const int l0 = L.slot_ptr[L.occ_obase[s]], nl = L.slot_ptr[L.occ_obase[s + 1]] - l0;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const bool c0 = lane < k, c1 = WIDE && lane + 32 < k;
+  const int g = lane % KL, sub = lane / KL, wid = w * SUB + sub;
+  const bool c0 = g < k, c1 = WIDE && g + 32 < k;
   const int i_end = min(nl, (c + 1) * chunk);
   float h0[MAX_KDIM] = {}, e0[MAX_KDIM] = {}, h1[MAX_KDIM] = {}, e1[MAX_KDIM] = {};
   if (kd > 0) {
-    for (int i = c * chunk + w; i < i_end; i += 32) {   // four links per step: their loads are in flight together
+    for (int i = c * chunk + wid; i < i_end; i += 4 * WORKERS) {   // four links per step: loads in flight together
       int code[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) code[u] = i + 8 * u < i_end ? L.slot_code[l0 + i + 8 * u] : -1;
+      for (int u = 0; u < 4; ++u) code[u] = i + WORKERS * u < i_end ? L.slot_code[l0 + i + WORKERS * u] : -1;
       double v0[4], v1[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const double* vr = V + (size_t)(max(code[u], 0) >> 1) * k + lane;
+        const double* vr = V + (size_t)(max(code[u], 0) >> 1) * k + g;
         v0[u] = (c0 && code[u] >= 0) ? vr[0] : 0.0;
         v1[u] = (WIDE && c1 && code[u] >= 0) ? vr[32] : 0.0;
       }
@@ -190,21 +197,29 @@ __global__ void __launch_bounds__(GTV_THREADS, WIDE ? 2 : 3) k_gt_v_ds(Layout L,
   }
 #pragma unroll
   for (int m = 0; m < MAX_KDIM; ++m) {
-    red[w][m][lane] = ds2d(h0[m], e0[m]);
-    red[w][m][lane + 32] = ds2d(h1[m], e1[m]);
+    double d0 = ds2d(h0[m], e0[m]), d1 = ds2d(h1[m], e1[m]);
+#pragma unroll
+    for (int off = KL; off < 32; off <<= 1) {   // the warp's links of column g, in a fixed order
+      d0 += __shfl_xor_sync(0xffffffffu, d0, off);
+      if (WIDE) d1 += __shfl_xor_sync(0xffffffffu, d1, off);
+    }
+    if (sub == 0) {
+      red[w][m][g] = d0;
+      if (WIDE) red[w][m][g + 32] = d1;
+    }
   }
   __syncthreads();
   const int t = threadIdx.x;
   double* part = L.gtv_part + (size_t)s * nch * MAX_KDIM * 64;
   for (int i = t; i < kd * k; i += blockDim.x) {
-    const int m = i / k, g = i % k;
+    const int m = i / k, gg = i % k;
     double v = 0.0;
 #pragma unroll
-    for (int q = 0; q < GTV_THREADS / 32; ++q) v += red[q][m][g];
+    for (int q = 0; q < GTV_THREADS / 32; ++q) v += red[q][m][gg];
     if (nch == 1)
-      X[(size_t)(L.occ_gofs[s] + m) * k + g] = v;
+      X[(size_t)(L.occ_gofs[s] + m) * k + gg] = v;
     else
-      part[((size_t)c * MAX_KDIM + m) * 64 + g] = v;
+      part[((size_t)c * MAX_KDIM + m) * 64 + gg] = v;
   }
   if (nch == 1) return;
   __threadfence();
@@ -214,10 +229,10 @@ __global__ void __launch_bounds__(GTV_THREADS, WIDE ? 2 : 3) k_gt_v_ds(Layout L,
   if (!s_last) return;
   __threadfence();
   for (int i = t; i < kd * k; i += blockDim.x) {
-    const int m = i / k, g = i % k;
+    const int m = i / k, gg = i % k;
     double v = 0.0;
-    for (int q = 0; q < nch; ++q) v += __ldcg(part + ((size_t)q * MAX_KDIM + m) * 64 + g);
-    X[(size_t)(L.occ_gofs[s] + m) * k + g] = v;
+    for (int q = 0; q < nch; ++q) v += __ldcg(part + ((size_t)q * MAX_KDIM + m) * 64 + gg);
+    X[(size_t)(L.occ_gofs[s] + m) * k + gg] = v;
   }
   if (t == 0) L.gtv_ticket[s] = 0u;
 }
@@ -298,10 +313,13 @@ constexpr int GT_SLOTS = 64, GT_LINKS = 512;
 // hi -> Y, lo -> Y2.  The links are summed in FP64: the first link's signed value by a sign-bit flip, each further
 // one (a minority of the slots have more than one) by an FP64 add; FP32 and narrower outputs are then rounded to
 // FP32 by integer operations (d2f_rn), so that the narrow FP64 pipe does no per-element conversion.
-template <typename TO, int SPLIT>
+// KL lanes per slot (k <= KL for KL < 32; KL = 32 also takes k <= 64 with a second column per lane): a warp
+// works on 32 / KL slots at once, so that small blocks keep every lane busy.
+template <typename TO, int SPLIT, int KL>
 __global__ void __launch_bounds__(256) k_gather_tile(Layout L, const double* __restrict__ V, int k, PatView<TO> Y,
                                                      PatView<TO> Y2, double alpha, double beta) {
   using ACC = std::conditional_t<std::is_same<TO, double>::value, double, float>;
+  constexpr int SUB = 32 / KL, UPW = 8 / SUB;   // slots a warp works on at once; slots per lane
   __shared__ int sptr[GT_SLOTS + 1];
   __shared__ int srow[GT_LINKS];
   __shared__ int8_t ssg[GT_LINKS];
@@ -325,35 +343,36 @@ __global__ void __launch_bounds__(256) k_gather_tile(Layout L, const double* __r
   __syncthreads();
   const int* lr = fits ? srow : L.slot_row + e0;
   const int8_t* ls = fits ? ssg : L.slot_sign + e0;
-  const bool c0 = lane < k, c1 = lane + 32 < k;
-  double y0[8], y1[8];
-  int ea[8], eb[8];
+  const int g = lane % KL, wid = w * SUB + lane / KL;   // column, slot worker (8 SUB workers)
+  const bool c0 = g < k, c1 = KL == 32 && g + 32 < k;
+  double y0[UPW], y1[UPW];
+  int ea[UPW], eb[UPW];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const int jl = w + 8 * u;
+  for (int u = 0; u < UPW; ++u) {
+    const int jl = wid + 8 * SUB * u;
     ea[u] = jl < ns ? sptr[jl] - e0 : 0;
     eb[u] = jl < ns ? sptr[jl + 1] - e0 : 0;
     y0[u] = 0.0;
     y1[u] = 0.0;
     if (ea[u] < eb[u]) {
       const bool neg = ls[ea[u]] < 0;
-      const double* vr = V + (size_t)lr[ea[u]] * k + lane;
+      const double* vr = V + (size_t)lr[ea[u]] * k + g;
       if (c0) y0[u] = neg_if(vr[0], neg);
       if (c1) y1[u] = neg_if(vr[32], neg);
     }
   }
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
+  for (int u = 0; u < UPW; ++u) {
     for (int e = ea[u] + 1; e < eb[u]; ++e) {
       const bool neg = ls[e] < 0;
-      const double* vr = V + (size_t)lr[e] * k + lane;
+      const double* vr = V + (size_t)lr[e] * k + g;
       if (c0) y0[u] += neg_if(vr[0], neg);
       if (c1) y1[u] += neg_if(vr[32], neg);
     }
-    const int jl = w + 8 * u;
+    const int jl = wid + 8 * SUB * u;
     if (jl < ns) {
-      tile[jl][lane] = from_f64<ACC>(y0[u]);
-      tile[jl][lane + 32] = from_f64<ACC>(y1[u]);
+      tile[jl][g] = from_f64<ACC>(y0[u]);
+      if (KL == 32) tile[jl][g + 32] = from_f64<ACC>(y1[u]);
     }
   }
   __syncthreads();
@@ -577,10 +596,12 @@ void gt_v_ds(const Layout& L, const double* V, int k, double* X, cudaStream_t s)
   if (L.n_occ == 0) return;
   if (k > 64) throw Error(1, "k > 64");
   if (!L.rowg_coef_hi) throw Error(1, "double-single coefficients of G not built");
-  if (k > 32)
-    k_gt_v_ds<true><<<dim3(L.n_occ, L.gtv_chunks), GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
-  else
-    k_gt_v_ds<false><<<dim3(L.n_occ, L.gtv_chunks), GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
+  const dim3 grid(L.n_occ, L.gtv_chunks);
+  if (k > 32) k_gt_v_ds<32, true><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
+  else if (k > 16) k_gt_v_ds<32, false><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
+  else if (k > 8) k_gt_v_ds<16, false><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
+  else if (k > 4) k_gt_v_ds<8, false><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
+  else k_gt_v_ds<4, false><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
   FETIRP_LAUNCH_CHECK();
 }
 
@@ -619,14 +640,24 @@ static int max_slots(const Layout& L) {
   for (int p = 0; p < L.n_pat; ++p) m = std::max(m, L.n_b[p]);
   return m;
 }
+// launch k_gather_tile with the lanes per slot that fit k
+template <typename TO, int SPLIT>
+void launch_gather_tile(const Layout& L, const double* V, int k, const PatView<TO>& Y, const PatView<TO>& Y2,
+                        double alpha, double beta, cudaStream_t s) {
+  const dim3 grid(L.n_occ, ceil_div(max_slots(L), GT_SLOTS));
+  if (k > 16) k_gather_tile<TO, SPLIT, 32><<<grid, 256, 0, s>>>(L, V, k, Y, Y2, alpha, beta);
+  else if (k > 8) k_gather_tile<TO, SPLIT, 16><<<grid, 256, 0, s>>>(L, V, k, Y, Y2, alpha, beta);
+  else if (k > 4) k_gather_tile<TO, SPLIT, 8><<<grid, 256, 0, s>>>(L, V, k, Y, Y2, alpha, beta);
+  else k_gather_tile<TO, SPLIT, 4><<<grid, 256, 0, s>>>(L, V, k, Y, Y2, alpha, beta);
+  FETIRP_LAUNCH_CHECK();
+}
+
 template <typename TO>
 void gather(const Layout& L, const double* V, int k, const PatView<TO>& Y, cudaStream_t s, double alpha,
             double beta) {
   if (L.n_occ == 0) return;
   if (k > 64) throw Error(1, "k > 64");
-  k_gather_tile<TO, 0><<<dim3(L.n_occ, ceil_div(max_slots(L), GT_SLOTS)), 256, 0, s>>>(L, V, k, Y, Y, alpha,
-                                                                                            beta);
-  FETIRP_LAUNCH_CHECK();
+  launch_gather_tile<TO, 0>(L, V, k, Y, Y, alpha, beta, s);
 }
 
 template <typename TI>
@@ -641,9 +672,7 @@ void gather_split(const Layout& L, const double* V, int k, const PatView<float>&
                   cudaStream_t s) {
   if (L.n_occ == 0) return;
   if (k > 64) throw Error(1, "k > 64");
-  k_gather_tile<float, 1><<<dim3(L.n_occ, ceil_div(max_slots(L), GT_SLOTS)), 256, 0, s>>>(L, V, k, Yh, Yl, 1.0,
-                                                                                             0.0);
-  FETIRP_LAUNCH_CHECK();
+  launch_gather_tile<float, 1>(L, V, k, Yh, Yl, 1.0, 0.0, s);
 }
 
 __global__ void k_perm_split(int n, int k, int pw, const int* __restrict__ src, const double* __restrict__ w,
@@ -694,9 +723,7 @@ void gather_split_bf16(const Layout& L, const double* V, int k, const PatView<__
                        const PatView<__nv_bfloat16>& Yl, cudaStream_t s) {
   if (L.n_occ == 0) return;
   if (k > 64) throw Error(1, "k > 64");
-  k_gather_tile<__nv_bfloat16, 2><<<dim3(L.n_occ, ceil_div(max_slots(L), GT_SLOTS)), 256, 0, s>>>(L, V, k, Yh, Yl,
-                                                                                                   1.0, 0.0);
-  FETIRP_LAUNCH_CHECK();
+  launch_gather_tile<__nv_bfloat16, 2>(L, V, k, Yh, Yl, 1.0, 0.0, s);
 }
 
 void split(const Layout& L, const double* r, int k, double* Z, cudaStream_t s) {

@@ -1086,7 +1086,7 @@ __global__ void __launch_bounds__(256) k_tall_update(int n, int a_max, const int
   }
 }
 
-// The FP32-history update for k = 32 or 16 on a tall block (one split): 256-row tiles, each thread RPT rows
+// The FP32-history update for k = 4, 8, 16 or 32 on a tall block (one split): 256-row tiles, each thread RPT rows
 // (ty + TY u) x 4 columns (4 tx ..), with 16-byte shared loads along the history index (about 1 load per 8 FMAs,
 // so the FP32 pipe rather than the shared-memory port bounds it).  A tile of 32 history columns is 32 / K blocks of
 // the block layout (width K), 256 rows each; it is copied to shared memory with 16-byte asynchronous copies
@@ -1106,7 +1106,7 @@ __global__ void __launch_bounds__(256, 2) k_tall_update_w(int n, int a_max, cons
                                                          const float* __restrict__ Wh,
                                                          const float* __restrict__ Cf, double alpha,
                                                          double* __restrict__ W) {
-  static_assert(K == 16 || K == 32, "history block width 16 or 32");
+  static_assert(K == 4 || K == 8 || K == 16 || K == 32, "history block width 4, 8, 16 or 32");
   constexpr int TXN = K / 4;          // column groups of 4
   constexpr int TY = 256 / TXN;       // row threads
   constexpr int RPT = TW_ROWS / TY;   // rows per thread
@@ -1206,6 +1206,8 @@ void tall_update_init() {
   if (!attr_set[dev]) {
     FETIRP_CUDA(cudaFuncSetAttribute(k_tall_update_w<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM));
     FETIRP_CUDA(cudaFuncSetAttribute(k_tall_update_w<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM));
+    FETIRP_CUDA(cudaFuncSetAttribute(k_tall_update_w<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM));
+    FETIRP_CUDA(cudaFuncSetAttribute(k_tall_update_w<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TW_SMEM));
     attr_set[dev] = true;
   }
 }
@@ -1243,14 +1245,15 @@ void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, int hk, 
     FETIRP_LAUNCH_CHECK();
     Ct = reinterpret_cast<const TH*>(Cf);
   }
-  if (sizeof(TH) == 4 && splits == 1 && (k == 32 || k == 16) && hk == k) {
+  if (sizeof(TH) == 4 && splits == 1 && (k == 32 || k == 16 || k == 8 || k == 4) && hk == k) {
     tall_update_init();
-    if (k == 32)
-      k_tall_update_w<32><<<ceil_div(n, TW_ROWS), 256, TW_SMEM, s>>>(n, a_max, d_a, reinterpret_cast<const float*>(Wh),
-                                                                     reinterpret_cast<const float*>(Ct), alpha, W);
-    else
-      k_tall_update_w<16><<<ceil_div(n, TW_ROWS), 256, TW_SMEM, s>>>(n, a_max, d_a, reinterpret_cast<const float*>(Wh),
-                                                                     reinterpret_cast<const float*>(Ct), alpha, W);
+    const float* wh = reinterpret_cast<const float*>(Wh);
+    const float* cf = reinterpret_cast<const float*>(Ct);
+    const int grid = ceil_div(n, TW_ROWS);
+    if (k == 32) k_tall_update_w<32><<<grid, 256, TW_SMEM, s>>>(n, a_max, d_a, wh, cf, alpha, W);
+    else if (k == 16) k_tall_update_w<16><<<grid, 256, TW_SMEM, s>>>(n, a_max, d_a, wh, cf, alpha, W);
+    else if (k == 8) k_tall_update_w<8><<<grid, 256, TW_SMEM, s>>>(n, a_max, d_a, wh, cf, alpha, W);
+    else k_tall_update_w<4><<<grid, 256, TW_SMEM, s>>>(n, a_max, d_a, wh, cf, alpha, W);
     FETIRP_LAUNCH_CHECK();
     return;
   }

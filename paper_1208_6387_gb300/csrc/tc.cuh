@@ -20,7 +20,16 @@ struct TcProblem {
   long long ldy[16];
   int n_b[16];
   int n_rhs[16];
+  // K-split scratch: when the output tiles alone would leave SMs idle, the reduction dimension is split over
+  // tc_ksplits(*this) CTAs per tile whose FP32 partials (layout of Z, one copy per split) are added in split order;
+  // part_elems must then be at least tc_ksplits(*this) * sum_p n_rhs[p] * ldy[p] (else no split is made)
+  float* part = nullptr;
+  long long part_elems = 0;
 };
+
+// K-split factor of the tensor-core product of T (1 or 2): 2 when at most half an SM's worth of 256 x 256 output
+// tiles exist and the reduction dimension is long enough to share.
+int tc_ksplits(const TcProblem& T);
 
 // Z = (S_hi + S_lo)(Y_hi + Y_lo) without the lo*lo term, FP32 accumulation in TMEM.  d_error: device int
 // that receives a nonzero code if a bounded wait inside the kernel expired (0 otherwise).

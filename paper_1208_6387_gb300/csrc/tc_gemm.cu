@@ -137,6 +137,8 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 struct TcParams {
   CUtensorMap a_hi[TC_MAXP], a_lo[TC_MAXP], b_hi[TC_MAXP], b_lo[TC_MAXP];
   float* Z[TC_MAXP];
+  float* part[TC_MAXP];   // K-split partials of pattern p (splits copies of the Z layout), when splits > 1
+  int splits;
   long long ldz[TC_MAXP];
   int n_b[TC_MAXP];
   int n_rhs[TC_MAXP];
@@ -164,14 +166,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
   volatile int* n_consumed = abort_flag + 2;   // stages whose full barrier the MMA thread observed
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = (int)blockIdx.x / P.splits, sp = (int)blockIdx.x % P.splits;
   int p = 0;
-  while (p + 1 < P.n_pat && (int)blockIdx.x >= P.tile_off[p + 1]) ++p;
+  while (p + 1 < P.n_pat && tile >= P.tile_off[p + 1]) ++p;
   // right-hand-side tiles inner: the CTAs of a wave share few 128-row tiles of S (read from DRAM once, then
   // served from L2 to the other CTAs of the row), and Y (a few tens of MB per pattern) stays in L2
-  const int t = blockIdx.x - P.tile_off[p];
+  const int t = tile - P.tile_off[p];
   const int tiles_n = (P.n_rhs[p] + BN - 1) / BN;
   const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
-  const int nk = (P.n_b[p] + BK - 1) / BK;
+  const int nk_all = (P.n_b[p] + BK - 1) / BK;
+  const int kb0 = (int)((long long)sp * nk_all / P.splits), kb1 = (int)((long long)(sp + 1) * nk_all / P.splits);
+  const int nk = kb1 - kb0;   // K steps of this CTA
   const bool two = m0 + BMH < P.n_b[p];   // the second 128-row half has rows of S (else its MMAs are skipped)
 
   if (threadIdx.x == 0) {
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
       if (*abort_flag) break;
       uint8_t* st = smem + s * STAGE_BYTES;
       mbar_expect_tx(&full[s], STAGE_BYTES);
-      const int kx = kb * BK;
+      const int kx = (kb0 + kb) * BK;
       tma_load_2d(&P.a_hi[p], &full[s], st, kx, m0);
       tma_load_2d(&P.a_lo[p], &full[s], st + TILE_A_BYTES, kx, m0);
       tma_load_2d(&P.b_hi[p], &full[s], st + 2 * TILE_A_BYTES, kx, n0);
@@ -270,7 +275,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
   const int half = warp >> 2, quad = warp & 3;
   if (drain && (half == 0 || two)) {
     const int row = m0 + half * BMH + quad * 32 + lane;
-    float* Z = P.Z[p];
+    // one split: the result; several: this split's partial (added by k_tc_reduce)
+    float* Z = P.splits > 1 ? P.part[p] + (size_t)sp * P.n_rhs[p] * P.ldz[p] : P.Z[p];
     const long long ldz = P.ldz[p];
     const int nr = P.n_rhs[p];
 #pragma unroll 1
@@ -305,6 +311,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_gemm(const __grid_constant__ 
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// Z = sum of the K-split partials in split order (the first n_b rows of every column), one thread per element
+__global__ void k_tc_reduce(const float* __restrict__ part, int splits, long long count, int n_b, long long ld,
+                            float* __restrict__ Z) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count || (int)(i % ld) >= n_b) return;
+  float acc = part[i];
+  for (int q = 1; q < splits; ++q) acc += part[(size_t)q * count + i];
+  Z[i] = acc;
 }
 
 __global__ void k_split_tf32(const double* __restrict__ x, long long rows, long long cols, long long ld_in,
@@ -387,6 +403,18 @@ void tc_init() {
   encode_fn();   // resolve the driver entry point outside any stream capture
 }
 
+int tc_ksplits(const TcProblem& T) {
+  long long tiles = 0;
+  int min_nb = 1 << 30;
+  for (int p = 0; p < T.n_pat; ++p)
+    if (T.n_rhs[p] > 0 && T.n_b[p] > 0) {
+      tiles += (long long)ceil_div(T.n_b[p], BM) * ceil_div(T.n_rhs[p], BN);
+      min_nb = std::min(min_nb, T.n_b[p]);
+    }
+  // two splits fill at most one wave of 152 SMs, and every split keeps >= 16 K steps of 16 elements
+  return (tiles > 0 && tiles <= 76 && min_nb >= 2 * 16 * 16) ? 2 : 1;
+}
+
 namespace {
 void tc_gemm_split(const TcProblem& T, bool bf16, int* d_error, cudaStream_t s) {
   tc_init();
@@ -394,8 +422,13 @@ void tc_gemm_split(const TcProblem& T, bool bf16, int* d_error, cudaStream_t s) 
   // patterns with work only: a structure need not use every pattern of the context (a tensor map of an empty
   // right-hand-side block would be invalid)
   std::vector<int> busy;
-  for (int p = 0; p < T.n_pat; ++p)
+  std::vector<long long> zoff(T.n_pat + 1, 0);   // offset of pattern p in the Z layout (the caller's order)
+  for (int p = 0; p < T.n_pat; ++p) {
     if (T.n_rhs[p] > 0 && T.n_b[p] > 0) busy.push_back(p);
+    zoff[p + 1] = zoff[p] + (long long)T.n_rhs[p] * T.ldy[p];
+  }
+  int splits = tc_ksplits(T);
+  if (splits > 1 && (!T.part || T.part_elems < splits * zoff[T.n_pat])) splits = 1;
   for (int base = 0; base < (int)busy.size(); base += TC_MAXP) {
     TcParams P;
     std::memset(&P, 0, sizeof(P));
@@ -409,6 +442,7 @@ void tc_gemm_split(const TcProblem& T, bool bf16, int* d_error, cudaStream_t s) 
       make_map(&P.b_hi[i], T.Y_hi[p], T.n_rhs[p], T.n_b[p], T.ldy[p], BN, es);
       make_map(&P.b_lo[i], T.Y_lo[p], T.n_rhs[p], T.n_b[p], T.ldy[p], BN, es);
       P.Z[i] = T.Z[p];
+      P.part[i] = T.part ? T.part + splits * zoff[p] : nullptr;
       P.ldz[i] = T.ldy[p];
       P.n_b[i] = T.n_b[p];
       P.n_rhs[i] = T.n_rhs[p];
@@ -417,10 +451,18 @@ void tc_gemm_split(const TcProblem& T, bool bf16, int* d_error, cudaStream_t s) 
       total += P.tiles_m[i] * ceil_div(T.n_rhs[p], BN);
     }
     P.tile_off[P.n_pat] = total;
+    P.splits = splits;
     if (total == 0) continue;
-    if (bf16) k_tc_gemm<true><<<total, THREADS, SMEM_BYTES, s>>>(P);
-    else k_tc_gemm<false><<<total, THREADS, SMEM_BYTES, s>>>(P);
+    if (bf16) k_tc_gemm<true><<<total * splits, THREADS, SMEM_BYTES, s>>>(P);
+    else k_tc_gemm<false><<<total * splits, THREADS, SMEM_BYTES, s>>>(P);
     FETIRP_LAUNCH_CHECK();
+    if (splits > 1)
+      for (int i = 0; i < P.n_pat; ++i) {
+        const long long count = (long long)P.n_rhs[i] * P.ldz[i];
+        k_tc_reduce<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(P.part[i], splits, count, P.n_b[i], P.ldz[i],
+                                                                    P.Z[i]);
+        FETIRP_LAUNCH_CHECK();
+      }
   }
 }
 }  // namespace

@@ -73,11 +73,12 @@ def test_medium_operator_matches_the_oracle(medium, prec, tol):
     assert np.abs(Q - Qo).max() < 10 * tol * np.abs(Qo).max()
 
 
-@pytest.mark.parametrize("k", [16, 32])
+@pytest.mark.parametrize("k", [4, 8, 16, 32])
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
 def test_medium_solve_with_other_widths(medium, prec, k):
-    """The same structure with k = 16 and k = 32 contiguous occurrence groups (the specialised FP32 history
-    updates for those widths) against the stored direct solve."""
+    """The same structure with k = 4, 8, 16 and 32 contiguous occurrence groups (the specialised FP32 history
+    updates and the lanes-per-link forms of the gather and G^T V for those widths) against the stored direct
+    solve."""
     prob, lam_ref, u_ref = medium
     ctx = F.fetirp_create(F.fetirp_default_options(precision=prec, tol=1e-10))
     try:
