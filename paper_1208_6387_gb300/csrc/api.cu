@@ -1558,14 +1558,15 @@ void enqueue_iteration_pc(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
   project_q(ctx, ctx->Zr.p, k, false);
   apply_F(ctx, ctx->Zr.p, ctx->Q.p, k, prec, false, false);
   project_q(ctx, ctx->Q.p, k, true);   // P~ = Q^T F W
-  int eta_off = 0;
+  int eta_off = 0, eta_n = 1;
   {
     PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 0.0, 0.0);
-    eta_off = eta_partials(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta_part, s, prec != FETIRP_PREC_FP64);
+    eta_off = eta_partials(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta_part, s, prec != FETIRP_PREC_FP64,
+                           &eta_n);
   }
   {
     PhaseScope ph(ctx, FETIRP_PHASE_NORMALISE, 0.0, 0.0);
-    normalise(k, ctx->eta_part.p + (size_t)eta_off * k * (k + 1), eta_off ? ETA_GROUPS : eta_chunks(nl),
+    normalise(k, ctx->eta_part.p + (size_t)eta_off * k * (k + 1), eta_n,
               prec == FETIRP_PREC_FP64 ? ctx->opt.eig_trunc : ctx->opt.eig_trunc_inner, ctx->T.p, ctx->alpha.p,
               ctx->n_kept.p, s);
   }
@@ -1583,7 +1584,7 @@ void enqueue_iteration_pc(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
 template <typename TH>
 void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
   if (ctx->pc.kind != 0) { enqueue_iteration_pc<TH>(ctx, prec, Wh, Qh); return; }
-  int eta_off = 0;
+  int eta_off = 0, eta_n = 1;
   cudaStream_t s = ctx->stream;
   const int nl = ctx->L.n_lambda, k = ctx->k;
   struct DsScope {   // double-single projections while the inner iteration of a mixed form is enqueued
@@ -1631,11 +1632,12 @@ void enqueue_iteration(fetirp_ctx ctx, int prec, TH* Wh, TH* Qh) {
   }
   {
     PhaseScope ph(ctx, FETIRP_PHASE_GRAM, 0.0, 0.0);
-    eta_off = eta_partials(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta_part, s, prec != FETIRP_PREC_FP64);
+    eta_off = eta_partials(nl, k, ctx->Zr.p, ctx->Q.p, ctx->r.p, ctx->eta_part, s, prec != FETIRP_PREC_FP64,
+                           &eta_n);
   }
   {
     PhaseScope ph(ctx, FETIRP_PHASE_NORMALISE, 0.0, 0.0);
-    normalise(k, ctx->eta_part.p + (size_t)eta_off * k * (k + 1), eta_off ? ETA_GROUPS : eta_chunks(nl),
+    normalise(k, ctx->eta_part.p + (size_t)eta_off * k * (k + 1), eta_n,
               prec == FETIRP_PREC_FP64 ? ctx->opt.eig_trunc : ctx->opt.eig_trunc_inner, ctx->T.p, ctx->alpha.p,
               ctx->n_kept.p, s);
   }

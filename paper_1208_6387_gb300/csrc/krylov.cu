@@ -538,6 +538,60 @@ __global__ void k_reduce_chunks_warp(int count, int chunks, const double* __rest
 // up to four chunks per SM (the sums are FP64-pipe bound: more resident warps keep the pipe busy)
 int eta_chunks(int n) { return std::max(1, std::min(608, ceil_div(n, 256))); }
 
+// (h, l) += (bh, bl) for unevaluated FP32 pairs: Knuth's TwoSum of the high parts, the low parts and the error
+// added, then renormalised (Dekker's Fast2Sum)
+__device__ __forceinline__ void ds_add(float& h, float& l, float bh, float bl) {
+  const float s = __fadd_rn(h, bh), bb = __fsub_rn(s, h);
+  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  const float t = __fadd_rn(__fadd_rn(l, bl), e);
+  h = __fadd_rn(s, t);
+  l = __fsub_rn(t, __fsub_rn(h, s));
+}
+
+// eta and W^T r for a narrow block (k = K <= 4): one thread per row, every thread holding all K (K + 1) sums as
+// FP32 pairs (the same products and sums as k_eta_partial_ds), added over the warp by shuffles in a fixed tree,
+// over the CTA's warps in warp order in FP64; one partial per CTA in the layout of k_eta_partial_ds.
+template <int K>
+__global__ void __launch_bounds__(256) k_eta_small_ds(int n, const double* __restrict__ W, const double* __restrict__ Q,
+                                                      const double* __restrict__ r, int rows_per_chunk,
+                                                      double* __restrict__ partial) {
+  constexpr int NO = K * (K + 1);
+  __shared__ double red[8][NO];
+  const int r0 = blockIdx.x * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+  float h[NO], l[NO];
+#pragma unroll
+  for (int o = 0; o < NO; ++o) { h[o] = 0.f; l[o] = 0.f; }
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+    float wh[K], wl[K], qh[K + 1], ql[K + 1];
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      ds_split(W[(size_t)row * K + c], wh[c], wl[c]);
+      ds_split(Q[(size_t)row * K + c], qh[c], ql[c]);
+    }
+    ds_split(r[row], qh[K], ql[K]);
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+      for (int j = 0; j <= K; ++j) ds_madd(wh[i], wl[i], qh[j], ql[j], h[i * (K + 1) + j], l[i * (K + 1) + j]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 0; o < NO; ++o) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float bh = __shfl_xor_sync(0xffffffffu, h[o], off), bl = __shfl_xor_sync(0xffffffffu, l[o], off);
+      ds_add(h[o], l[o], bh, bl);
+    }
+    if (lane == 0) red[warp][o] = ds2d(h[o], l[o]);
+  }
+  __syncthreads();
+  if (threadIdx.x < NO) {
+    double acc = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w][threadIdx.x];
+    partial[(size_t)blockIdx.x * NO + threadIdx.x] = acc;
+  }
+}
+
 // out[g][o] = sum of the chunk partials c = g, g + G, g + 2G, ... of output o (G = gridDim.y groups), four
 // independent running sums added in a fixed order: the first level of the eta reduction, spread over many SMs
 // (the FP64 adds of all chunks on the one normalising SM would take longer than the product itself)
@@ -558,14 +612,19 @@ __global__ void k_eta_group_sums(int nout, int chunks, const double* __restrict_
 }
 
 int eta_partials(int n, int k, const double* W, const double* Q, const double* r, DBuf<double>& partial,
-                 cudaStream_t s, bool ds) {
-  const int chunks = eta_chunks(n);
+                 cudaStream_t s, bool ds, int* n_read) {
+  const bool small = ds && k == 4;
+  // narrow blocks: one CTA per SM, a few thousand rows each (every thread sums several rows before the
+  // per-CTA reduction); otherwise up to 608 chunks of >= 256 rows
+  const int chunks = small ? std::max(1, std::min(152, ceil_div(n, 1024))) : eta_chunks(n);
   const int rows = ceil_div(n, chunks);
   const int nout = k * (k + 1);
   partial.ensure((size_t)(chunks + ETA_GROUPS) * nout);
-  if (ds) k_eta_partial_ds<<<chunks, 256, 0, s>>>(n, k, W, Q, r, rows, partial.p);
+  if (small) k_eta_small_ds<4><<<chunks, 256, 0, s>>>(n, W, Q, r, rows, partial.p);
+  else if (ds) k_eta_partial_ds<<<chunks, 256, 0, s>>>(n, k, W, Q, r, rows, partial.p);
   else k_eta_partial<<<chunks, 256, 0, s>>>(n, k, W, Q, r, rows, partial.p);
   FETIRP_LAUNCH_CHECK();
+  *n_read = std::min(chunks, ETA_GROUPS);
   if (chunks <= ETA_GROUPS) return 0;
   k_eta_group_sums<<<dim3(ceil_div(nout, 256), ETA_GROUPS), 256, 0, s>>>(nout, chunks, partial.p,
                                                                          partial.p + (size_t)chunks * nout);
@@ -909,15 +968,19 @@ __global__ void __launch_bounds__(256) k_hist_dot(int n, int a, const TH* __rest
   }
 }
 
+// C[i] = sum over the chunk partials of output i: one warp per output, lane j adds chunks j, j + 32, ... and the
+// lanes are added by a fixed shuffle tree (deterministic; the chunks of one output are read in parallel)
 __global__ void k_reduce_chunks_dyn(int a_max, const int* __restrict__ d_a, int k, int chunks,
                                     const double* __restrict__ partial, double* __restrict__ C) {
   const int a = d_a ? min(*d_a, a_max) : a_max;
   const int count = a * k;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= count) return;
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (i >= count) return;   // whole warps leave together (i is the same for the 32 lanes)
   double acc = 0.0;
-  for (int c = 0; c < chunks; ++c) acc += partial[(size_t)c * count + i];
-  C[i] = acc;
+  for (int c = lane; c < chunks; c += 32) acc += partial[(size_t)c * count + i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) C[i] = acc;
 }
 
 template <typename TH>
@@ -939,7 +1002,8 @@ void gram_split(int a_max, const int* d_a, int k, const TH* Qh, int n, int hk, c
   k_gram_split<TH><<<std::min(items, GS_GRID), 256, 0, s>>>(a_max, d_a, k, Qh, n, hk, grp_ptr, grp_row, wd, wh, wl,
                                                              chunks, partial.p);
   FETIRP_LAUNCH_CHECK();
-  k_reduce_chunks_dyn<<<ceil_div(a_max * k, 256), 256, 0, s>>>(a_max, d_a, k, chunks, partial.p, C);
+  k_reduce_chunks_dyn<<<(unsigned)ceil_div((long long)a_max * k * 32, 256), 256, 0, s>>>(a_max, d_a, k, chunks,
+                                                                                    partial.p, C);
   FETIRP_LAUNCH_CHECK();
 }
 template void gram_split<double>(int, const int*, int, const double*, int, int, const double*, const int*,

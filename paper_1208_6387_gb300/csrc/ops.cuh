@@ -293,16 +293,16 @@ void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, int hk, 
                  double* W, DBuf<double>& scratch, DBuf<unsigned>& tickets, cudaStream_t s);
 // history count += k with restart, dropped and iteration counters (one thread)
 void advance(int* cols, int k, long long cap, const int* n_kept, int* dropped, int* iters, cudaStream_t s);
-// Row-chunk partials (eta_chunks(n) of them) of [eta | wr] = W^T [Q | r], a k x (k+1) block, FP64 sums.  With
-// more than ETA_GROUPS chunks they are first added into ETA_GROUPS group sums (fixed order) stored after the
-// chunks; the return value is the offset, in blocks of k (k+1), of what normalise() must add (0: the chunks
-// themselves, eta_chunks(n) of them; else the ETA_GROUPS group sums).
+// Row-chunk partials of [eta | wr] = W^T [Q | r], a k x (k+1) block, FP64 sums: at most eta_chunks(n) of them
+// (k = 4 with ds: one per SM).  With more than ETA_GROUPS chunks they are first added into ETA_GROUPS group sums
+// (fixed order) stored after the chunks.  The return value is the offset, in blocks of k (k+1), of what
+// normalise() must add, and *n_read their number (the chunks themselves, or the ETA_GROUPS group sums).
 constexpr int ETA_GROUPS = 16;
 int eta_chunks(int n);
 // ds: the products and sums in double-single FP32 arithmetic (~2^-46 relative; the inner solves of the mixed
 // forms), else FP64.
 int eta_partials(int n, int k, const double* W, const double* Q, const double* r, DBuf<double>& partial,
-                 cudaStream_t s, bool ds = false);
+                 cudaStream_t s, bool ds, int* n_read);
 // C (m x k) = A (m x m) B (m x k), row-major, FP64, one warp per row (small coarse products).
 // part (optional, small_gemm_parts(m) * m * k doubles): the inner dimension is split over that many CTA rows
 // and the slices added in order (deterministic)
