@@ -42,8 +42,32 @@ def test_c3_operator_matches_oracle_on_sampled_columns(c3):
         F.fetirp_destroy(ctx)
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
-def test_c3_solve_satisfies_the_equations(c3, prec):
+def test_c3_operator_at_the_bench_width(c3):
+    """The block operator in the benchmark's launch configuration (k = 4: R_p = 256 right-hand sides per
+    pattern, one 256-column tile, the reduction dimension of the tensor-core product split over two CTAs),
+    compared element by element with the oracle on all four columns."""
+    prob = config("c3", k=4)
+    orc = FetiOracle(prob, use_schur=False)
+    ctx = F.fetirp_create(F.fetirp_default_options())
+    try:
+        F.load_problem(ctx, prob)
+        F.fetirp_prepare(ctx, prob.n_lambda, prob.c)
+        V = np.random.default_rng(22).standard_normal((prob.n_lambda, 4))
+        Qo = orc.PtFP(V)
+        for prec, tol in (("fp64", 1e-9), ("tf32x3", 5e-4), ("bf16x3", 1e-3)):
+            Q = F.fetirp_apply_block(ctx, V, F.PRECISIONS[prec])
+            rel = np.linalg.norm(Q - Qo) / np.linalg.norm(Qo)
+            assert rel < tol, (prec, rel)
+            assert np.abs(Q - Qo).max() < 10 * tol * np.abs(Qo).max(), prec
+    finally:
+        F.fetirp_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,k", [("tf32x3", 32), ("bf16x3", 32), ("bf16x3", 4)])
+def test_c3_solve_satisfies_the_equations(c3, prec, k):
+    """k = 4 with bf16x3 is the benchmark's configuration."""
+    if k != 32:
+        c3 = config("c3", k=k)
     ctx = F.fetirp_create(F.fetirp_default_options(precision=prec, tol=1e-8, max_iter=3000))
     try:
         F.load_problem(ctx, c3)
