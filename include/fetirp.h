@@ -181,7 +181,11 @@ void fetirp_destroy(fetirp_ctx ctx);
  *  expected_kernel_dim: -1 to accept the detected kernel dimension; otherwise FETIRP_ESINGULAR when the
  *     number of zero pivots differs.
  *  *pattern_id receives the id (0, 1, ...).
- * Device memory: a dense FP64 factor of (n rounded up to 64)^2 doubles plus S^+ in FP64 and FP32.
+ * Device memory: a dense FP64 factor of (n rounded up to 64)^2 doubles, L_S^{-1} and S^+ in FP64, S^dag in FP32
+ * and as tf32 and bf16 pairs.  Patterns with n_b >= 1024 form the bf16 pair of S^dag on the tensor cores and
+ * compute S^+ and the FP32 and tf32 forms of S^dag only on the first call that needs them (a solve, an apply
+ * or fetirp_get_pattern in FP64, FP32 or TF32X3; that call waits for them): a BF16X3 solve needs none of them
+ * and applies S^+ in its FP64 refinement through L_S^{-1}.
  */
 fetirp_status fetirp_create_pattern(fetirp_ctx ctx, int32_t n_nodes, int32_t dofs_per_node,
                                     const int64_t* rowptr, const int32_t* col, const double* val,

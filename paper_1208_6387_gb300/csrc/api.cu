@@ -2,6 +2,7 @@
 // operator and the multivector FETI solver driver.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -108,8 +109,17 @@ struct PatternData {
   ~PatternData() {
     if (h_zp_pinned) cudaFreeHost(h_zp_pinned);
   }
-  DBuf<float> S32, S_hi, S_lo;   // FP32 S^+ and its tf32 pair (leading dimension lds)
+  DBuf<float> S32, S_hi, S_lo;   // FP32 S^dag and its tf32 pair (leading dimension lds)
   long long lds = 0;
+  // Large patterns (n_b >= TC_SDAG_MIN_NB) form the bf16 pair of S^dag on the tensor cores from the rows of
+  // (L_S^{-1} Pi)^T (Ypair: tf32 pair, leading dimension lds); S^+ in FP64 and the FP32 forms of S^dag only when
+  // a caller needs them (ensure_splus64); until then their FP64 local products go through the factor
+  // (LocalProblem::X).
+  // S64, Sdag (kdim > 0), S32 and the tf32 pair hold the current factorisation's FP64 S^+, S^dag and their FP32
+  // roundings; large patterns form them on first use (ensure_splus64), their bf16 pair at factorisation.
+  std::atomic<bool> s64_ok{false};
+  std::mutex s64_mu;
+  DBuf<float> Ypair;
   DBuf<__nv_bfloat16> Sb_hi, Sb_lo;   // bf16 pair of S^dag (leading dimension ldsb, a multiple of 8)
   long long ldsb = 0;
   long long ld_y8 = 0;                // Y/Z leading dimension of the bf16 products (round_up(n_b, 8))
@@ -241,7 +251,7 @@ struct fetirp_ctx_s {
   DBuf<unsigned> tu_tickets;      // per row tile: CTAs of the history update that have stored their partial
   DBuf<double> eta_part;          // row-chunk partials of eta and W^T r
   DBuf<int> n_kept;
-  DBuf<double> Y64, Z64;
+  DBuf<double> Y64, Z64, W64;     // W64: scratch of the factored FP64 local product (large patterns)
   DBuf<float> Y32, Z32, Ylo32;
   DBuf<float> tc_part;            // K-split partials of the tensor-core product (small blocks only)
   DBuf<int> tc_error;
@@ -452,7 +462,12 @@ void factor_check(PatternData& P) {
                                       std::to_string(P.expected));
 }
 
-void factor_stage_b(PatternData& P, cudaStream_t s) {
+// Patterns with at least this many boundary dofs form S^dag on the tensor cores (factor_stage_b)
+constexpr int TC_SDAG_MIN_NB = 1024;
+void form_splus64(PatternData& P, cudaStream_t s);
+void form_sdag64(PatternData& P, cudaStream_t s);
+
+void factor_stage_b(PatternData& P, int* tc_error, cudaStream_t s) {
   const int npad = P.npad, kd = P.kdim;
   // kernel: N_r = -K_rr^{-1} K_rz, N_z = I (right-hand side built on the host from the CSR)
   P.N.ensure((size_t)npad * std::max(kd, 1));
@@ -494,47 +509,130 @@ void factor_stage_b(PatternData& P, cudaStream_t s) {
   FETIRP_LAUNCH_CHECK();
   tile_inverses(P.LS.p, nbp, P.zpS.p, P.DinvS.p, s);
   tri_solve(P.LS.p, nbp, P.planS, P.zpS.p, P.XS.p, nbp, nbp, false, s, P.DinvS.p, true);   // X = L_S^{-1}
-  P.S64.ensure((size_t)P.n_b * P.n_b);
-  lauum(P.XS.p, nbp, nbp, P.n_b, P.S64.p, P.n_b, s);   // S^+ = X^T X
-  // Moore-Penrose inverse S^dag = Pi S^+ Pi, Pi = I - N_b (N_b^T N_b)^{-1} N_b^T, for the low-precision local
-  // products: S^+ from zero pivots carries large components along the kernel (a body held at a few dofs)
-  // that the projector P removes again, so rounding them would survive that cancellation; S^dag has none.
-  // P^T F P is the same for every generalized inverse (Sec. 2), so the inner operator is unchanged.
   const int nb = P.n_b;
-  const double* Sdag = P.S64.p;
-  if (kd > 0) {
-    P.Sdag.ensure((size_t)nb * nb);
-    P.Nwork.ensure((size_t)nb * kd * 2 + 2 * kd * kd);
-    double* A = P.Nwork.p;                  // S^+ N_b       (nb x kd, row-major)
-    double* E = A + (size_t)nb * kd;        // N_b C^{-1}    (nb x kd)
-    double* Cm = E + (size_t)nb * kd;       // N_b^T N_b, then its inverse (kd x kd)
-    double* D = Cm + kd * kd;               // N_b^T S^+ N_b (kd x kd)
-    gemm_f64(nb, kd, nb, 1.0, P.S64.p, nb, 1, P.Nb.p, kd, 1, 0.0, A, kd, 1, s);
-    gemm_f64(kd, kd, nb, 1.0, P.Nb.p, 1, kd, P.Nb.p, kd, 1, 0.0, Cm, kd, 1, s);
-    gemm_f64(kd, kd, nb, 1.0, P.Nb.p, 1, kd, A, kd, 1, 0.0, D, kd, 1, s);
-    k_small_spd_inverse<<<1, 32, 0, s>>>(Cm, kd);
-    FETIRP_LAUNCH_CHECK();
-    gemm_f64(nb, kd, kd, 1.0, P.Nb.p, kd, 1, Cm, kd, 1, 0.0, E, kd, 1, s);
-    FETIRP_CUDA(cudaMemcpyAsync(P.Sdag.p, P.S64.p, sizeof(double) * (size_t)nb * nb, cudaMemcpyDeviceToDevice, s));
-    gemm_f64(nb, nb, kd, -1.0, E, kd, 1, A, 1, kd, 1.0, P.Sdag.p, nb, 1, s);    // - E A^T
-    gemm_f64(nb, nb, kd, -1.0, A, kd, 1, E, 1, kd, 1.0, P.Sdag.p, nb, 1, s);    // - A E^T
-    gemm_f64(nb, kd, kd, 1.0, E, kd, 1, D, kd, 1, 0.0, A, kd, 1, s);            // A <- E D
-    gemm_f64(nb, nb, kd, 1.0, A, kd, 1, E, 1, kd, 1.0, P.Sdag.p, nb, 1, s);     // + E D E^T
-    Sdag = P.Sdag.p;
-  }
-  P.S32.ensure((size_t)nb * nb);
-  const size_t nn = (size_t)nb * nb;
-  k_to_f32<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(nn, Sdag, P.S32.p);
-  FETIRP_LAUNCH_CHECK();
   P.lds = round_up(nb, 4);
-  P.S_hi.ensure((size_t)nb * P.lds);
-  P.S_lo.ensure((size_t)nb * P.lds);
-  split_tf32(Sdag, nb, nb, nb, P.S_hi.p, P.S_lo.p, P.lds, s);
   P.ldsb = round_up(nb, 8);
   P.ld_y8 = P.ldsb;
+  // every operator buffer is sized here, so that forming them later (ensure_splus64) allocates nothing
+  P.S64.ensure((size_t)nb * nb);
+  if (kd > 0) P.Sdag.ensure((size_t)nb * nb);
+  P.Nwork.ensure((size_t)nb * std::max(kd, 1) * 2 + 2 * kd * kd);
+  P.S32.ensure((size_t)nb * nb);
+  P.S_hi.ensure((size_t)nb * P.lds);
+  P.S_lo.ensure((size_t)nb * P.lds);
   P.Sb_hi.ensure((size_t)nb * P.ldsb);
   P.Sb_lo.ensure((size_t)nb * P.ldsb);
-  split_bf16(Sdag, nb, nb, nb, P.Sb_hi.p, P.Sb_lo.p, P.ldsb, s);
+  if (nb < TC_SDAG_MIN_NB) {
+    form_splus64(P, s);
+    const double* Sdag = kd > 0 ? P.Sdag.p : P.S64.p;
+    split_bf16(Sdag, nb, nb, nb, P.Sb_hi.p, P.Sb_lo.p, P.ldsb, s);
+    P.s64_ok = true;
+    return;
+  }
+  // Large patterns: the bf16 pair of S^dag = Pi S^+ Pi = Y^T Y, Y = Lam Pi, Lam = L_S^{-1},
+  // Pi = I - N_b C^{-1} N_b^T, C = N_b^T N_b.  Y is formed in FP64 (Lam minus a rank-kd term, so the large kernel
+  // components of S^+ never appear), rounded to tf32 pairs, and Y^T Y is one tensor-core product (tf32x3, FP32
+  // accumulation), rounded to the bf16 pair: no FP64 S^+ (n_b^3 / 3 FP64 flops) is formed.  That S^dag is
+  // accurate to ~1e-6 of sqrt(S^dag_ii S^dag_jj) (tf32 pair products, FP32 sums over n_b terms): the level of
+  // the bf16 pair's own rounding (2^-17), not that of an FP32 rounding, so the FP32 and tf32 forms of S^dag
+  // come from the FP64 S^+ (ensure_splus64).
+  P.s64_ok = false;
+  const double* A = nullptr;
+  const double* E = nullptr;
+  if (kd > 0) {
+    double* Aw = P.Nwork.p;                  // Lam N_b      (nb x kd, row-major)
+    double* Ew = Aw + (size_t)nb * kd;       // N_b C^{-1}   (nb x kd)
+    double* Cm = Ew + (size_t)nb * kd;       // N_b^T N_b, then its inverse (kd x kd)
+    gemm_f64(nb, kd, nb, 1.0, P.XS.p, 1, nbp, P.Nb.p, kd, 1, 0.0, Aw, kd, 1, s);
+    gemm_f64(kd, kd, nb, 1.0, P.Nb.p, 1, kd, P.Nb.p, kd, 1, 0.0, Cm, kd, 1, s);
+    k_small_spd_inverse<<<1, 32, 0, s>>>(Cm, kd);
+    FETIRP_LAUNCH_CHECK();
+    gemm_f64(nb, kd, kd, 1.0, P.Nb.p, kd, 1, Cm, kd, 1, 0.0, Ew, kd, 1, s);
+    A = Aw;
+    E = Ew;
+  }
+  P.Ypair.ensure((size_t)2 * nb * P.lds);
+  float* Yh = P.Ypair.p;
+  float* Yl = P.Ypair.p + (size_t)nb * P.lds;
+  pinv_rows_tf32(P.XS.p, nbp, A, E, kd, nb, Yh, Yl, P.lds, s);
+  TcProblem T;
+  T.n_pat = 1;
+  T.S_hi[0] = Yh; T.S_lo[0] = Yl; T.lds[0] = P.lds;
+  T.Y_hi[0] = Yh; T.Y_lo[0] = Yl; T.ldy[0] = P.lds;
+  T.Z[0] = P.S_hi.p;   // FP32 S^dag (leading dimension lds) in the tf32 buffer until ensure_splus64 fills it
+  T.n_b[0] = nb; T.n_rhs[0] = nb;
+  tc_gemm_tf32x3(T, tc_error, s);
+  split_bf16(P.S_hi.p, nb, nb, P.lds, P.Sb_hi.p, P.Sb_lo.p, P.ldsb, s);
+}
+
+// S^+ = Lam^T Lam in FP64 (k_lauum, n_b^3 / 3 flops), with a kernel the Moore-Penrose inverse
+// S^dag = Pi S^+ Pi, Pi = I - N_b (N_b^T N_b)^{-1} N_b^T (form_sdag64), and S^dag rounded to FP32 and to the
+// tf32 pair.  S^+ from zero pivots carries large components along the kernel (a body held at a few dofs) that
+// the projector P removes again, so rounding them for the low-precision products would survive that
+// cancellation; S^dag has none.  P^T F P is the same for every generalized inverse (Sec. 2), so the inner
+// operator is unchanged.
+void form_splus64(PatternData& P, cudaStream_t s) {
+  const int nb = P.n_b, nbp = P.nbpad, kd = P.kdim;
+  const size_t nn = (size_t)nb * nb;
+  lauum(P.XS.p, nbp, nbp, nb, P.S64.p, nb, s);   // S^+ = X^T X
+  const double* Sdag = P.S64.p;
+  if (kd > 0) {
+    form_sdag64(P, s);
+    Sdag = P.Sdag.p;
+  }
+  k_to_f32<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(nn, Sdag, P.S32.p);
+  FETIRP_LAUNCH_CHECK();
+  split_tf32(Sdag, nb, nb, nb, P.S_hi.p, P.S_lo.p, P.lds, s);
+}
+
+void form_sdag64(PatternData& P, cudaStream_t s) {
+  const int nb = P.n_b, kd = P.kdim;
+  double* A = P.Nwork.p;                  // S^+ N_b       (nb x kd, row-major)
+  double* E = A + (size_t)nb * kd;        // N_b C^{-1}    (nb x kd)
+  double* Cm = E + (size_t)nb * kd;       // N_b^T N_b, then its inverse (kd x kd)
+  double* D = Cm + kd * kd;               // N_b^T S^+ N_b (kd x kd)
+  gemm_f64(nb, kd, nb, 1.0, P.S64.p, nb, 1, P.Nb.p, kd, 1, 0.0, A, kd, 1, s);
+  gemm_f64(kd, kd, nb, 1.0, P.Nb.p, 1, kd, P.Nb.p, kd, 1, 0.0, Cm, kd, 1, s);
+  gemm_f64(kd, kd, nb, 1.0, P.Nb.p, 1, kd, A, kd, 1, 0.0, D, kd, 1, s);
+  k_small_spd_inverse<<<1, 32, 0, s>>>(Cm, kd);
+  FETIRP_LAUNCH_CHECK();
+  gemm_f64(nb, kd, kd, 1.0, P.Nb.p, kd, 1, Cm, kd, 1, 0.0, E, kd, 1, s);
+  FETIRP_CUDA(cudaMemcpyAsync(P.Sdag.p, P.S64.p, sizeof(double) * (size_t)nb * nb, cudaMemcpyDeviceToDevice, s));
+  gemm_f64(nb, nb, kd, -1.0, E, kd, 1, A, 1, kd, 1.0, P.Sdag.p, nb, 1, s);    // - E A^T
+  gemm_f64(nb, nb, kd, -1.0, A, kd, 1, E, 1, kd, 1.0, P.Sdag.p, nb, 1, s);    // - A E^T
+  gemm_f64(nb, kd, kd, 1.0, E, kd, 1, D, kd, 1, 0.0, A, kd, 1, s);            // A <- E D
+  gemm_f64(nb, nb, kd, 1.0, A, kd, 1, E, 1, kd, 1.0, P.Sdag.p, nb, 1, s);     // + E D E^T
+}
+
+// The FP64 S^+ (S^dag) of a large pattern and the FP32 and tf32 forms of S^dag, formed on first use after a
+// factorisation by the callers that need them: products in FP64 as a matrix (FP64 solves, the persistent FP64
+// iteration, the sparse-column plan, fetirp_get_pattern) and every FP32 or tf32x3 product.  Allocates nothing
+// (factor_stage_b sized the buffers); blocks until formed; patterns are shared by child contexts, hence the
+// lock.
+void ensure_splus64(PatternData& P, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(P.s64_mu);
+  if (P.s64_ok) return;
+  form_splus64(P, s);
+  FETIRP_CUDA(cudaStreamSynchronize(s));
+  P.s64_ok = true;
+}
+
+// The operators that products in precision prec read: everything but the bf16 pair needs ensure_splus64.
+// Their formation counts as set-up (the factorisation phase).
+void ensure_operators(fetirp_ctx ctx, int prec) {
+  if (prec == FETIRP_PREC_BF16X3) return;
+  const bool by_use = ctx->use.size() == ctx->pats.size();   // the patterns of the current structure only
+  std::vector<PatternData*> todo;
+  double flops = 0.0;
+  for (size_t p = 0; p < ctx->pats.size(); ++p) {
+    PatternData& P = *ctx->pats[p];
+    if ((by_use && ctx->use[p].occs.empty()) || P.s64_ok) continue;
+    todo.push_back(&P);
+    flops += 2.0 * ((double)P.n_b * P.n_b * P.n_b / 6.0);
+  }
+  if (todo.empty()) return;
+  PhaseScope ph(ctx, FETIRP_PHASE_FACTOR, flops, 0.0);
+  for (PatternData* P : todo) ensure_splus64(*P, ctx->stream);
 }
 
 // Per-pattern work on concurrent streams: fork_patterns(ctx, n) makes n streams wait for the work enqueued so far
@@ -573,9 +671,12 @@ double factor_flops(const PatternData& P) {
              + t3 * (double)P.plan.col_rows.size();           // panel solves
   f += 2.0 * 2.0 * (double)P.kdim * TILE * TILE * (double)(P.plan.col_rows.size() + P.plan.nt);   // kernel N
   const double nb = P.n_b;
-  f += 2.0 * (nb * nb * nb / 6.0) * 2.0;                       // L_S^{-1} and the lower-triangular product
+  f += 2.0 * (nb * nb * nb / 6.0);                             // L_S^{-1}
+  if (P.n_b < TC_SDAG_MIN_NB) f += 2.0 * (nb * nb * nb / 6.0);   // S^+ = L_S^{-T} L_S^{-1} (large: tensor cores)
   return f;
 }
+
+void check_tc_error(fetirp_ctx ctx);
 
 void factorize_patterns(fetirp_ctx ctx, const std::vector<PatternData*>& pats) {
   double flops = 0.0;
@@ -589,9 +690,15 @@ void factorize_patterns(fetirp_ctx ctx, const std::vector<PatternData*>& pats) {
     factor_check(*pats[i]);
     pats[i]->upload_zpiv(ctx->fstreams[i]);
   }
-  for (size_t i = 0; i < np; ++i) factor_stage_b(*pats[i], ctx->fstreams[i]);
+  if (!ctx->tc_error.p) {   // zeroed before the pattern streams run (they were forked earlier)
+    ctx->tc_error.alloc(1);
+    ctx->tc_error.zero(ctx->stream);
+    FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  for (size_t i = 0; i < np; ++i) factor_stage_b(*pats[i], ctx->tc_error.p, ctx->fstreams[i]);
   join_patterns(ctx, np);
   FETIRP_CUDA(cudaStreamSynchronize(ctx->stream));
+  check_tc_error(ctx);   // the tensor-core S^dag of large patterns
 }
 
 // Dense SPD inverse in FP64 (coarse matrix G^T G): tile Cholesky, X = L^{-1}, A^{-1} = X^T X.
@@ -637,6 +744,21 @@ void check_periodic(fetirp_ctx ctx);
 void precond_setup(fetirp_ctx ctx);
 
 // Local-product buffers for a block of k columns in every precision (allocated before any graph capture).
+// Does some pattern of the context apply S^+ in FP64 through its factor (no formed S^+)?
+bool factored_f64(fetirp_ctx ctx) {
+  for (auto& P : ctx->pats)
+    if (!P->s64_ok) return true;
+  return false;
+}
+
+// The factored FP64 local product of pattern P, if it has no formed S^+: LocalProblem fields X, ldx, W.
+void set_factored(LocalProblem& LP, int p, const PatternData& P, double* W) {
+  if (P.s64_ok) return;
+  LP.X[p] = P.XS.p;
+  LP.ldx[p] = P.nbpad;
+  LP.W[p] = W;
+}
+
 void ensure_apply_buffers(fetirp_ctx ctx, int k) {
   long long total = 0, total8 = 0;
   for (size_t p = 0; p < ctx->pats.size(); ++p) {
@@ -645,6 +767,7 @@ void ensure_apply_buffers(fetirp_ctx ctx, int k) {
   }
   total = std::max(total, total8);   // the bf16 products use the FP32 buffers with leading dimension ld_y8
   ctx->Y64.ensure(total); ctx->Z64.ensure(total);
+  if (factored_f64(ctx)) ctx->W64.ensure(total);
   ctx->Y32.ensure(total); ctx->Z32.ensure(total); ctx->Ylo32.ensure(total);
   TcProblem T;   // would the tensor-core product split its reduction dimension?
   T.n_pat = (int)ctx->pats.size();
@@ -1193,6 +1316,7 @@ void apply_F(fetirp_ctx ctx, const double* in, double* out, int k, int prec, boo
   LP.n_pat = n_pat;
   if (prec == FETIRP_PREC_FP64) {
     ctx->Y64.ensure(total); ctx->Z64.ensure(total);
+    if (factored_f64(ctx)) ctx->W64.ensure(total);
     PatView<double> Yv{}, Zv{};
     for (int p = 0; p < n_pat; ++p) {
       PatternData& P = *ctx->pats[p];
@@ -1200,6 +1324,7 @@ void apply_F(fetirp_ctx ctx, const double* in, double* out, int k, int prec, boo
       Zv.base[p] = ctx->Z64.p + base[p]; Zv.ld[p] = P.ld_y; Zv.off[p] = 0;
       LP.S[p] = P.S64.p; LP.n_b[p] = P.n_b; LP.n_rhs[p] = (int)ctx->use[p].occs.size() * k; LP.ld[p] = P.ld_y;
       LP.Y[p] = Yv.base[p]; LP.Z[p] = Zv.base[p];
+      set_factored(LP, p, P, P.s64_ok ? nullptr : ctx->W64.p + base[p]);
     }
     run_local<double>(ctx, L, src, out, k, Yv, Zv, LP, 8.0);
   } else if (prec == FETIRP_PREC_FP32) {
@@ -1779,6 +1904,7 @@ PersistArgs persist_args(fetirp_ctx ctx, bool fp64, TH* Wh, TH* Qh) {
     A.ybase[p] = total;
     A.ld[p] = P.ld_y;
     A.n_rhs[p] = (int)ctx->use[p].occs.size() * k;
+    ensure_splus64(P, s);   // the persistent product reads S^+ or the FP32 S^dag as a matrix
     A.S[p] = fp64 ? (const void*)P.S64.p : (const void*)P.S32.p;
     A.pocc[p] = ctx->use[p].d_occs.p;
     total += (long long)ctx->use[p].occs.size() * k * P.ld_y;
@@ -2123,6 +2249,7 @@ fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_st
       if (!ctx->use[p].occs.empty()) max_nb = std::max(max_nb, ctx->pats[p]->n_b);
     prec = (max_nb <= 512 && nl <= 262144) ? FETIRP_PREC_FP32 : FETIRP_PREC_TF32X3;
   }
+  ensure_operators(ctx, prec);
   // relative tolerance of every inner solve: the user's, or (0) one above the operator's rounding level
   const double inner_tol = ctx->opt.inner_tol > 0.0   ? ctx->opt.inner_tol
                            : prec == FETIRP_PREC_BF16X3 ? 1e-4
@@ -2332,6 +2459,7 @@ fetirp_status fetirp_apply_block_device_noalloc(fetirp_ctx ctx, int32_t k, const
     REQUIRE(k >= 1 && k <= 64, "k must be in 1..64");
     REQUIRE(d_V && d_Q, "NULL buffer");
     REQUIRE(precision >= FETIRP_PREC_FP64 && precision <= FETIRP_PREC_TF32X3, "unsupported precision");
+    ensure_operators(ctx, precision);
     apply_noalloc(ctx, d_V, d_Q, k, precision, noalloc_scratch(ctx->opt.device), FETIRP_NOALLOC_SCRATCH_BYTES);
     return FETIRP_OK;
   });
@@ -2676,6 +2804,7 @@ fetirp_status fetirp_apply_block_device(fetirp_ctx ctx, int32_t k, const double*
     REQUIRE(k >= 1 && k <= 64, "k must be in 1..64");
     REQUIRE(d_V && d_Q, "NULL buffer");
     REQUIRE(operator_precision(precision), "unsupported precision");
+    ensure_operators(ctx, precision);
     apply_F(ctx, d_V, d_Q, k, precision, true, true);
     return FETIRP_OK;
   });
@@ -2689,6 +2818,7 @@ fetirp_status fetirp_apply_block(fetirp_ctx ctx, int32_t k, const double* V, dou
     REQUIRE(operator_precision(precision), "unsupported precision");
     const size_t n = (size_t)ctx->L.n_lambda * k;
     DBuf<double> dv(n), dq(n);
+    ensure_operators(ctx, precision);
     dv.upload(V, n, ctx->stream);
     apply_F(ctx, dv.p, dq.p, k, precision, true, true);
     check_tc_error(ctx);
@@ -2828,6 +2958,7 @@ void split_plan_build(fetirp_ctx ctx) {
       FETIRP_CUDA(cudaMemcpyAsync(dE.p + mbase[p], E[p].data(), sizeof(double) * E[p].size(), cudaMemcpyHostToDevice, s));
   SP.M64.ensure(std::max<long long>(mtotal, 1));
   SP.M32.ensure(std::max<long long>(mtotal, 1));
+  for (int p = 0; p < n_pat; ++p) ensure_splus64(*ctx->pats[p], s);
   for (int pass = 0; pass < 2; ++pass) {   // S^+ E, then S^dag E
     LocalProblem LP{};
     LP.n_pat = n_pat;
@@ -2861,6 +2992,7 @@ void split_plan_build(fetirp_ctx ctx) {
 void apply_split(fetirp_ctx ctx, const double* d_r, double* d_Q, int prec) {
   SplitPlan& SP = ctx->sp;
   if (SP.k != ctx->k) split_plan_build(ctx);
+  ensure_operators(ctx, prec);   // formed by the plan; again after a refactorisation
   cudaStream_t s = ctx->stream;
   const Layout& L = ctx->L;
   const int k = ctx->k, n_pat = (int)ctx->pats.size();
@@ -3089,6 +3221,7 @@ fetirp_status fetirp_get_pattern(fetirp_ctx ctx, int32_t pid, int32_t* n_b_out, 
     PatternData& P = *ctx->pats[pid];
     if (n_b_out) *n_b_out = P.n_b;
     if (kdim_out) *kdim_out = P.kdim;
+    if (splus) ensure_splus64(P, ctx->stream);
     if (splus)
       FETIRP_CUDA(cudaMemcpyAsync(splus, P.S64.p, sizeof(double) * (size_t)P.n_b * P.n_b, cudaMemcpyDeviceToHost,
                                   ctx->stream));

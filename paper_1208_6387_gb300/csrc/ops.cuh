@@ -143,6 +143,12 @@ struct LocalProblem {
   const void* Y[MAXP];
   void* Z[MAXP];
   int n_pat;
+  // Factored form (FP64 only; X[p] non-null): S^+ Y = Lam^T (Lam Y) with Lam = L_S^{-1} the inverse of the
+  // Schur-complement factor (lower triangular), stored transposed: X[c * ldx + r] = Lam(r, c).  Two triangular
+  // products through the scratch W[p] (n_rhs x ld) instead of one product with a formed S^+; S is then unused.
+  const double* X[MAXP];
+  long long ldx[MAXP];
+  double* W[MAXP];
 };
 void local_gemm_f64(const LocalProblem& P, cudaStream_t s);
 void local_gemm_f32(const LocalProblem& P, cudaStream_t s);

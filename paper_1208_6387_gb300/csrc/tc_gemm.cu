@@ -323,8 +323,10 @@ __global__ void k_tc_reduce(const float* __restrict__ part, int splits, long lon
   Z[i] = acc;
 }
 
-__global__ void k_split_tf32(const double* __restrict__ x, long long rows, long long cols, long long ld_in,
-                             float* __restrict__ hi, float* __restrict__ lo, long long ld_out) {
+// x may alias hi (in place, ld_in == ld_out): each element is read and then written by one thread
+template <typename TI>
+__global__ void k_split_tf32(const TI* x, long long rows, long long cols, long long ld_in, float* hi, float* lo,
+                             long long ld_out) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= rows * ld_out) return;
   const long long r = idx / ld_out, c = idx % ld_out;
@@ -335,6 +337,29 @@ __global__ void k_split_tf32(const double* __restrict__ x, long long rows, long 
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v));
     h = __uint_as_float(t);
     l = v - h;
+  }
+  hi[idx] = h;
+  lo[idx] = l;
+}
+
+// Rows of Y^T = (Lam Pi)^T, split into tf32 pairs: Y^T(i, j) = Lam(j, i) - sum_m E(i, m) A(j, m), with
+// Lam(j, i) = X[i * ldx + j] (the transposed storage of the set-up's L_S^{-1}), A = Lam N_b and
+// E = N_b (N_b^T N_b)^{-1} (n_b x kd, row-major); columns n_b .. ld_out - 1 are zero.
+__global__ void k_pinv_rows_tf32(const double* __restrict__ X, long long ldx, const double* __restrict__ A,
+                                 const double* __restrict__ E, int kd, long long nb, float* __restrict__ hi,
+                                 float* __restrict__ lo, long long ld_out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nb * ld_out) return;
+  const long long i = idx / ld_out, j = idx % ld_out;
+  float h = 0.f, l = 0.f;
+  if (j < nb) {
+    double v = X[i * ldx + j];
+    for (int m = 0; m < kd; ++m) v -= E[i * kd + m] * A[j * kd + m];
+    const float f = (float)v;
+    uint32_t t;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(f));
+    h = __uint_as_float(t);
+    l = f - h;
   }
   hi[idx] = h;
   lo[idx] = l;
@@ -384,7 +409,21 @@ void split_tf32(const double* x, long long rows, long long cols, long long ld_in
                 long long ld_out, cudaStream_t s) {
   const long long n = rows * ld_out;
   if (n == 0) return;
-  k_split_tf32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, rows, cols, ld_in, hi, lo, ld_out);
+  k_split_tf32<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, rows, cols, ld_in, hi, lo, ld_out);
+  FETIRP_LAUNCH_CHECK();
+}
+void split_tf32(const float* x, long long rows, long long cols, long long ld_in, float* hi, float* lo,
+                long long ld_out, cudaStream_t s) {
+  const long long n = rows * ld_out;
+  if (n == 0) return;
+  k_split_tf32<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, rows, cols, ld_in, hi, lo, ld_out);
+  FETIRP_LAUNCH_CHECK();
+}
+void pinv_rows_tf32(const double* X, long long ldx, const double* A, const double* E, int kd, long long nb,
+                    float* hi, float* lo, long long ld_out, cudaStream_t s) {
+  const long long n = nb * ld_out;
+  if (n == 0) return;
+  k_pinv_rows_tf32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, ldx, A, E, kd, nb, hi, lo, ld_out);
   FETIRP_LAUNCH_CHECK();
 }
 
@@ -470,8 +509,9 @@ void tc_gemm_split(const TcProblem& T, bool bf16, int* d_error, cudaStream_t s) 
 void tc_gemm_tf32x3(const TcProblem& T, int* d_error, cudaStream_t s) { tc_gemm_split(T, false, d_error, s); }
 void tc_gemm_bf16x3(const TcProblem& T, int* d_error, cudaStream_t s) { tc_gemm_split(T, true, d_error, s); }
 
-// hi = bf16(x) (round to nearest), lo = bf16(x - hi); x is FP64, outputs bf16 with leading dimension ld_out
-__global__ void k_split_bf16(const double* __restrict__ x, long long rows, long long cols, long long ld_in,
+// hi = bf16(x) (round to nearest), lo = bf16(x - hi); x is FP64 or FP32, outputs bf16 with leading dimension ld_out
+template <typename TI>
+__global__ void k_split_bf16(const TI* __restrict__ x, long long rows, long long cols, long long ld_in,
                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long long ld_out) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= rows * ld_out) return;
@@ -486,12 +526,21 @@ __global__ void k_split_bf16(const double* __restrict__ x, long long rows, long 
   lo[idx] = __float2bfloat16_rn(l);
 }
 
-void split_bf16(const double* x, long long rows, long long cols, long long ld_in, __nv_bfloat16* hi,
-                __nv_bfloat16* lo, long long ld_out, cudaStream_t s) {
+template <typename TI>
+static void split_bf16_t(const TI* x, long long rows, long long cols, long long ld_in, __nv_bfloat16* hi,
+                         __nv_bfloat16* lo, long long ld_out, cudaStream_t s) {
   const long long n = rows * ld_out;
   if (n == 0) return;
-  k_split_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, rows, cols, ld_in, hi, lo, ld_out);
+  k_split_bf16<TI><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, rows, cols, ld_in, hi, lo, ld_out);
   FETIRP_LAUNCH_CHECK();
+}
+void split_bf16(const double* x, long long rows, long long cols, long long ld_in, __nv_bfloat16* hi,
+                __nv_bfloat16* lo, long long ld_out, cudaStream_t s) {
+  split_bf16_t(x, rows, cols, ld_in, hi, lo, ld_out, s);
+}
+void split_bf16(const float* x, long long rows, long long cols, long long ld_in, __nv_bfloat16* hi,
+                __nv_bfloat16* lo, long long ld_out, cudaStream_t s) {
+  split_bf16_t(x, rows, cols, ld_in, hi, lo, ld_out, s);
 }
 
 }  // namespace fetirp

@@ -32,7 +32,16 @@ CASES = {
     "heat_rot_ragged": lambda: heat_grid(5, (3, 2), kappas=(1.0, 30.0), checker=True, rotate=True, k=4, seed=7),
     "elastic_2x2x1": lambda: elastic_grid(3, (2, 2, 1), n_patterns=2, k=4, seed=1),
     "c3r": lambda: config("c3r"),
+    # n_b = 1158 >= 1024: S^dag formed on the tensor cores, FP64 products through the factor, S^+ on demand
+    "elastic8_2x2x1": lambda: elastic_grid(8, (2, 2, 1), n_patterns=2, k=4, seed=3),
 }
+# Solve tolerance per case: 1e-12, except where FP64 rounding alone stops the plain FP64 iteration above it (the
+# 8^3 elastic patterns stagnate at 5e-12); the method's target is 1e-8.
+SOLVE_TOL = {"elastic8_2x2x1": 1e-10}
+# Sparse-column against dense FP64 apply: the same products in another order, 1e-11, except on the 8^3 elastic
+# patterns (n_b = 1158), where the projection's cancellation leaves 8.7e-11 between the two: there the bound is
+# the oracle's, 1e-10.
+SPLIT_SELF_TOL = {"elastic8_2x2x1": 1e-10}
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -81,12 +90,13 @@ def test_apply_block_matches_oracle(name, prec, tol):
 def test_solve_matches_direct(name, prec):
     prob = config("c2") if name == "c2" else CASES[name]()
     us_ref, lam_ref, _, _ = direct(prob)
-    ctx = make_ctx(prob, precision=prec, tol=1e-12)   # inner tolerance: the library's per-precision default
+    tol = SOLVE_TOL.get(name, 1e-12)
+    ctx = make_ctx(prob, precision=prec, tol=tol)   # inner tolerance: the library's per-precision default
     try:
         lam, u, st = F.fetirp_solve(ctx, prob.n_lambda, prob.c, F.n_u(prob))
     finally:
         F.fetirp_destroy(ctx)
-    assert st["rel_residual"] <= 1e-12
+    assert st["rel_residual"] <= tol
     assert rel(lam, lam_ref) < 1e-8, st
     for a, b in zip(F.split_u(prob, u), us_ref):
         assert rel(a, b) < 1e-8
@@ -94,7 +104,7 @@ def test_solve_matches_direct(name, prec):
         assert st["outer_steps"] >= 1
 
 
-@pytest.mark.parametrize("name", ["c1", "heat_rot_ragged", "elastic_2x2x1", "c2"])
+@pytest.mark.parametrize("name", ["c1", "heat_rot_ragged", "elastic_2x2x1", "c2", "elastic8_2x2x1"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_persistent_and_graph_paths_agree(name, prec):
     """The persistent cooperative iteration (the default at these sizes) and the per-phase CUDA-graph path both
@@ -103,7 +113,8 @@ def test_persistent_and_graph_paths_agree(name, prec):
     us_ref, lam_ref, _, _ = direct(prob)
     its = {}
     for pers in (0, 1):
-        ctx = make_ctx(prob, precision=prec, tol=1e-12, inner_tol=1e-5, persistent=pers, timing=1)
+        ctx = make_ctx(prob, precision=prec, tol=SOLVE_TOL.get(name, 1e-12), inner_tol=1e-5, persistent=pers,
+                       timing=1)
         try:
             lam, u, st = F.fetirp_solve(ctx, prob.n_lambda, prob.c, F.n_u(prob))
         finally:
@@ -152,7 +163,7 @@ def test_sparse_column_apply_matches_dense_and_oracle(name, prec, tol):
     finally:
         F.fetirp_destroy(ctx)
     assert rel(Qs, ref) < tol, (rel(Qs, ref), rel(Qd, ref))
-    assert rel(Qs, Qd) < (1e-11 if prec == "fp64" else tol)
+    assert rel(Qs, Qd) < (SPLIT_SELF_TOL.get(name, 1e-11) if prec == "fp64" else tol)
 
 
 def test_classical_k1_and_block_agree():
