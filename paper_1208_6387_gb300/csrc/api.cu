@@ -133,6 +133,7 @@ struct PatternUse {
   DBuf<int> d_occs;
   DBuf<double> F;              // npad x n_occ loads (pattern frame, new ordering)
   DBuf<double> U;              // npad x n_occ work (local solves)
+  DBuf<double> Yf;             // npad x n_occ: L^{-1} F, the forward sweep of the loads (from d, for the recovery)
 };
 
 struct OccData {
@@ -1204,8 +1205,11 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
     const int no = (int)Us.occs.size();
     cudaStream_t ps = ctx->fstreams[p];
     if (no > 0) {
-      FETIRP_CUDA(cudaMemcpyAsync(Us.U.p, Us.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, ps));
+      const size_t bytes = sizeof(double) * (size_t)P.npad * no;
+      FETIRP_CUDA(cudaMemcpyAsync(Us.U.p, Us.F.p, bytes, cudaMemcpyDeviceToDevice, ps));
       tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, ps, P.Dinv.p);
+      Us.Yf.ensure((size_t)P.npad * no);
+      FETIRP_CUDA(cudaMemcpyAsync(Us.Yf.p, Us.U.p, bytes, cudaMemcpyDeviceToDevice, ps));
       tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, ps, P.Dinv.p, false, P.n_i / TILE);
     }
     V.base[p] = Us.U.p; V.ld[p] = P.npad; V.off[p] = P.n_i;
@@ -2089,7 +2093,8 @@ double block_orthodir(fetirp_ctx ctx, int prec, double target, double rnorm, His
   return rnorm;
 }
 
-void recover(fetirp_ctx ctx, double* d_u_out) {
+// res: d - F lambda for the current lambda when the caller has it (the solve's last FP64 residual), else null.
+void recover(fetirp_ctx ctx, double* d_u_out, const double* res) {
   cudaStream_t s = ctx->stream;
   PhaseOverride ov(ctx, FETIRP_PHASE_RECOVER);
   PhaseScope ph(ctx, FETIRP_PHASE_RECOVER, 0.0, 0.0);
@@ -2098,24 +2103,28 @@ void recover(fetirp_ctx ctx, double* d_u_out) {
   const int n_pat = (int)ctx->pats.size();
   // alpha = (G^T G)^{-1} G^T (d - F lambda)   (first row of Eq. 3)
   if (ctx->n_G > 0) {
-    apply_F(ctx, ctx->lam.p, ctx->t1.p, 1, FETIRP_PREC_FP64, false, false);
-    ctx->V1.ensure(nl);
-    FETIRP_CUDA(cudaMemcpyAsync(ctx->V1.p, ctx->d.p, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
-    axpy_f64(nl, -1.0, ctx->t1.p, ctx->V1.p, s);
-    gt_v(L, ctx->V1.p, 1, ctx->Xc.p, s);
+    if (!res) {
+      apply_F(ctx, ctx->lam.p, ctx->t1.p, 1, FETIRP_PREC_FP64, false, false);
+      ctx->V1.ensure(nl);
+      FETIRP_CUDA(cudaMemcpyAsync(ctx->V1.p, ctx->d.p, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
+      axpy_f64(nl, -1.0, ctx->t1.p, ctx->V1.p, s);
+      res = ctx->V1.p;
+    }
+    gt_v(L, res, 1, ctx->Xc.p, s);
     gemm_f64(ctx->n_G, 1, ctx->n_G, 1.0, ctx->Ginv.p, ctx->n_G, 1, ctx->Xc.p, 1, 1, 0.0, ctx->Ac.p, 1, 1, s);
   }
-  // u(s) = K^+ (f(s) - B(s)^T lambda) - N(s) alpha(s)
+  // u(s) = K^+ (f(s) - B(s)^T lambda) - N(s) alpha(s), with K^+ = L^{-T} L^{-1} and, by linearity,
+  // L^{-1} (f - B^T lambda) = L^{-1} f - L^{-1} B^T lambda: the first term is the forward sweep kept from d, the
+  // second lives on the boundary block rows only (the boundary is ordered last), so its sweep starts there.
   PatView<double> V{};
   for (int p = 0; p < n_pat; ++p) {
     PatternData& P = *ctx->pats[p];
     PatternUse& Us = ctx->use[p];
     const int no = (int)Us.occs.size();
-    if (no > 0)
-      FETIRP_CUDA(cudaMemcpyAsync(Us.U.p, Us.F.p, sizeof(double) * (size_t)P.npad * no, cudaMemcpyDeviceToDevice, s));
+    if (no > 0) FETIRP_CUDA(cudaMemsetAsync(Us.U.p, 0, sizeof(double) * (size_t)P.npad * no, s));
     V.base[p] = Us.U.p; V.ld[p] = P.npad; V.off[p] = P.n_i;
   }
-  rotate_traces<double>(L, V, 1, false, s);   // general rotations: f(s) to the global frame, add -B^T lambda,
+  rotate_traces<double>(L, V, 1, false, s);   // general rotations: to the global frame, add -B^T lambda,
   gather<double>(L, ctx->lam.p, 1, V, s, -1.0, 1.0);
   rotate_traces<double>(L, V, 1, true, s);    // and back to the pattern frame
   fork_patterns(ctx, n_pat);   // patterns on concurrent streams
@@ -2126,7 +2135,8 @@ void recover(fetirp_ctx ctx, double* d_u_out) {
     if (no == 0) continue;
     cudaStream_t ps = ctx->fstreams[p];
     double* Usol = Us.U.p;
-    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, ps, P.Dinv.p);
+    tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, false, ps, P.Dinv.p, false, 0, P.n_i / TILE);
+    axpy_f64((int)((long long)P.npad * no), 1.0, Us.Yf.p, Us.U.p, ps);
     tri_solve(P.L.p, P.npad, P.plan, P.zp.p, Us.U.p, P.npad, no, true, ps, P.Dinv.p);
     if (P.kdim > 0 && ctx->n_G > 0)
       gemm_f64(P.npad, no, P.kdim, -1.0, P.N.p, 1, P.npad, ctx->Ac.p + ctx->pofs[p], 1, P.kdim, 1.0, Usol, 1,
@@ -2294,7 +2304,7 @@ fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_st
   check_tc_error(ctx);
   if (d_lambda)
     FETIRP_CUDA(cudaMemcpyAsync(d_lambda, ctx->lam.p, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
-  if (d_u) recover(ctx, d_u);
+  if (d_u) recover(ctx, d_u, ctx->t1.p);   // t1 = d - F lambda from the last residual() above
   FETIRP_CUDA(cudaEventRecord(e1, s));
   FETIRP_CUDA(cudaEventSynchronize(e1));
   float ms = 0.f;

@@ -39,9 +39,11 @@ void chol_tiles(double* A, int npad, const TilePlan& plan, const double* diag0, 
 // stop_tile (backward solves only): only the block rows J >= stop_tile of the solution are wanted; each of them
 // depends on later block rows only, so the sweep stops there and updates no earlier block row (X above
 // stop_tile is left partly updated).
+// start_tile (forward solves only): the block rows J < start_tile of X are zero on entry (a right-hand side that
+// lives on the trailing block rows), so they stay zero and the sweep starts at start_tile.
 void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, double* X, int ldx, int nrhs,
                bool trans, cudaStream_t s, const double* Dinv = nullptr, bool identity_rhs = false,
-               int stop_tile = 0);
+               int stop_tile = 0, int start_tile = 0);
 // C (n_out x n_out, ld ldc) = X^T X for a lower-triangular X (column-major, ld, krows rows summed).
 void lauum(const double* X, int ld, int krows, int n_out, double* C, int ldc, cudaStream_t s);
 // Dinv (npad/64 tiles of 64 x 64, column-major) = inverses of the diagonal tiles of L (zero pivots -> 0).

@@ -347,17 +347,21 @@ __global__ void __launch_bounds__(256) k_tri_update(const double* L, int npad, i
 }
 
 // Generic strided GEMM, 32x32 output tile per CTA, 2x2 per thread (small FP64 products: more CTAs).
+// 32 x 32 output tile per CTA.  With part != nullptr the reduction dimension is split: CTA z sums k in
+// [z * kc, min(K, (z + 1) * kc)) and stores its raw sum in part[z][m][n] (k_gemm_f64_sum_parts finishes).
 __global__ void __launch_bounds__(256) k_gemm_f64_32(int M, int N, int K, double alpha, const double* __restrict__ A,
                                                      long long sAm, long long sAk, const double* __restrict__ B,
                                                      long long sBk, long long sBn, double beta, double* C,
-                                                     long long sCm, long long sCn) {
+                                                     long long sCm, long long sCn, double* part, int kc) {
   __shared__ double sa[32][33];
   __shared__ double sb[32][33];
   const int tid = threadIdx.x;
   const int m0 = blockIdx.x * 32, n0 = blockIdx.y * 32;
   const int tx = tid % 16, ty = tid / 16;
+  const int kbeg = part ? (int)blockIdx.z * kc : 0;
+  if (part) K = min(K, kbeg + kc);
   double acc[2][2] = {};
-  for (int k0 = 0; k0 < K; k0 += 32) {
+  for (int k0 = kbeg; k0 < K; k0 += 32) {
     for (int idx = tid; idx < 32 * 32; idx += 256) {
       int r, kk;
       if (sAk == 1) { kk = idx % 32; r = idx / 32; } else { r = idx % 32; kk = idx / 32; }
@@ -388,10 +392,27 @@ __global__ void __launch_bounds__(256) k_gemm_f64_32(int M, int N, int K, double
     for (int q = 0; q < 2; ++q) {
       const int n = n0 + tx * 2 + q;
       if (n >= N) continue;
+      if (part) {
+        part[((size_t)blockIdx.z * M + m) * N + n] = acc[p][q];
+        continue;
+      }
       double* c = C + m * sCm + n * sCn;
       *c = alpha * acc[p][q] + (beta == 0.0 ? 0.0 : beta * *c);
     }
   }
+}
+
+// C = alpha * (sum of the split partials, in split order) + beta * C
+__global__ void k_gemm_f64_sum_parts(int M, int N, int splits, const double* __restrict__ part, double alpha,
+                                     double beta, double* C, long long sCm, long long sCn) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long mn = (long long)M * N;
+  if (i >= mn) return;
+  double acc = 0.0;
+  for (int z = 0; z < splits; ++z) acc += part[z * mn + i];
+  const long long m = i / N, n = i % N;
+  double* c = C + m * sCm + n * sCn;
+  *c = alpha * acc + (beta == 0.0 ? 0.0 : beta * *c);
 }
 
 // Generic strided GEMM, 64x64 output tile per CTA, 4x4 per thread, FP64.
@@ -538,7 +559,7 @@ void tile_inverses(const double* L, int npad, const int* zp, double* Dinv, cudaS
 }
 
 void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, double* X, int ldx, int nrhs_all,
-               bool trans, cudaStream_t s, const double* Dinv, bool identity_rhs, int stop_tile) {
+               bool trans, cudaStream_t s, const double* Dinv, bool identity_rhs, int stop_tile, int start_tile) {
   if (nrhs_all <= 0) return;
   int nrhs = nrhs_all;
   int chunks = ceil_div(nrhs, TILE);
@@ -548,7 +569,7 @@ void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, d
     else k_tri_diag<<<chunks, 256, 0, s>>>(L, npad, J, zp, X, ldx, nrhs, tr);
   };
   if (!trans) {
-    for (int J = 0; J < plan.nt; ++J) {
+    for (int J = std::max(0, start_tile); J < plan.nt; ++J) {
       if (identity_rhs) {   // columns c >= 64 (J + 1) of L^{-1} are still zero in block rows <= J
         nrhs = std::min(nrhs_all, (J + 1) * TILE);
         chunks = ceil_div(nrhs, TILE);
@@ -589,7 +610,31 @@ void gemm_f64(int M, int N, int K, double alpha, const double* A, long long sAm,
   dim3 grid(ceil_div(M, TILE), ceil_div(N, TILE));
   if ((long long)grid.x * grid.y < 2 * 152) {   // too few 64x64 tiles to occupy the SMs' FP64 units
     dim3 g32(ceil_div(M, 32), ceil_div(N, 32));
-    k_gemm_f64_32<<<g32, 256, 0, s>>>(M, N, K, alpha, A, sAm, sAk, B, sBk, sBn, beta, C, sCm, sCn);
+    const long long tiles = (long long)g32.x * g32.y;
+    // fewer 32x32 tiles than SMs and a long reduction (the skinny products N^T f, Lam N_b): split the reduction
+    // over up to eight CTAs per SM (17 KB of shared memory each), >= 256 terms each, partials added in a fixed
+    // order (stream-ordered scratch; not inside a stream capture)
+    int splits = 1;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FETIRP_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (tiles < 152 && K >= 1024 && cap == cudaStreamCaptureStatusNone)
+      splits = (int)std::min<long long>(ceil_div(K, 256), std::max<long long>(1, 8 * 152 / tiles));
+    if (splits > 1) {
+      const int kc = ceil_div(ceil_div(K, splits), 32) * 32;
+      splits = ceil_div(K, kc);
+      double* part = nullptr;
+      FETIRP_CUDA(cudaMallocAsync(&part, sizeof(double) * (size_t)splits * M * N, s));
+      g32.z = splits;
+      k_gemm_f64_32<<<g32, 256, 0, s>>>(M, N, K, alpha, A, sAm, sAk, B, sBk, sBn, beta, C, sCm, sCn, part, kc);
+      FETIRP_LAUNCH_CHECK();
+      const long long mn = (long long)M * N;
+      k_gemm_f64_sum_parts<<<(unsigned)((mn + 255) / 256), 256, 0, s>>>(M, N, splits, part, alpha, beta, C, sCm,
+                                                                         sCn);
+      FETIRP_LAUNCH_CHECK();
+      FETIRP_CUDA(cudaFreeAsync(part, s));
+      return;
+    }
+    k_gemm_f64_32<<<g32, 256, 0, s>>>(M, N, K, alpha, A, sAm, sAk, B, sBk, sBn, beta, C, sCm, sCn, nullptr, 0);
   } else {
     k_gemm_f64<<<grid, 256, 0, s>>>(M, N, K, alpha, A, sAm, sAk, B, sBk, sBn, beta, C, sCm, sCn);
   }

@@ -264,6 +264,49 @@ __global__ void k_g_apply_ds(Layout L, const float* __restrict__ Ah, const float
   else *o = is_zero(beta) ? alpha * x : fma(alpha, x, beta * *o);
 }
 
+// The same for k = K (4 or 8) with one thread per row: the row's links and coefficients are read once for all K
+// columns, the coarse pairs as float4; per element the same products in the same order as k_g_apply_ds.
+template <int K>
+__global__ void k_g_apply_ds_rows(Layout L, const float* __restrict__ Ah, const float* __restrict__ Al,
+                                  double alpha, double beta, double* __restrict__ out) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= L.n_lambda) return;
+  float h[K], l[K];
+#pragma unroll
+  for (int g = 0; g < K; ++g) h[g] = l[g] = 0.f;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int g0 = L.rowg_gofs[2 * row + e];
+    if (g0 < 0) continue;
+    const int kd = L.rowg_kd[2 * row + e];
+    const float* ch = L.rowg_coef_hi + (size_t)(2 * row + e) * MAX_KDIM;
+    const float* cl = L.rowg_coef_lo + (size_t)(2 * row + e) * MAX_KDIM;
+#pragma unroll
+    for (int m = 0; m < MAX_KDIM; ++m)
+      if (m < kd) {
+        const float a = ch[m], b = cl[m];
+        const float4* ph = reinterpret_cast<const float4*>(Ah + (size_t)(g0 + m) * K);
+        const float4* pl = reinterpret_cast<const float4*>(Al + (size_t)(g0 + m) * K);
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q) {
+          const float4 vh = ph[q], vl = pl[q];
+          dsm(a, b, vh.x, vl.x, h[4 * q], l[4 * q]);
+          dsm(a, b, vh.y, vl.y, h[4 * q + 1], l[4 * q + 1]);
+          dsm(a, b, vh.z, vl.z, h[4 * q + 2], l[4 * q + 2]);
+          dsm(a, b, vh.w, vl.w, h[4 * q + 3], l[4 * q + 3]);
+        }
+      }
+  }
+  double* o = out + (size_t)row * K;
+  const bool minus = bits64(alpha) == bits64(-1.0), keep = bits64(beta) == bits64(1.0);
+#pragma unroll
+  for (int g = 0; g < K; ++g) {
+    const double x = ds2d(h[g], l[g]);
+    if (keep && minus) o[g] = o[g] - x;
+    else o[g] = is_zero(beta) ? alpha * x : fma(alpha, x, beta * o[g]);
+  }
+}
+
 // Block (s, t) of G^T G for one neighbour pair: sum over rows linking s and t.  Threads split the boundary
 // dofs of s; per-thread partials are reduced in a fixed order.
 __global__ void __launch_bounds__(128) k_gtg(Layout L, const int* __restrict__ pair_s, const int* __restrict__ pair_t,
@@ -596,12 +639,21 @@ void gt_v_ds(const Layout& L, const double* V, int k, double* X, cudaStream_t s)
   if (L.n_occ == 0) return;
   if (k > 64) throw Error(1, "k > 64");
   if (!L.rowg_coef_hi) throw Error(1, "double-single coefficients of G not built");
-  const dim3 grid(L.n_occ, L.gtv_chunks);
-  if (k > 32) k_gt_v_ds<32, true><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
-  else if (k > 16) k_gt_v_ds<32, false><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
-  else if (k > 8) k_gt_v_ds<16, false><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
-  else if (k > 4) k_gt_v_ds<8, false><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
-  else k_gt_v_ds<4, false><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, L.gtv_chunk);
+  // Chunk of links per CTA: the layout's (sized for 32 lanes per link), or, when a warp works on several links at
+  // once (k <= 16), long enough for about eight rounds of four links per worker, so that the loads in flight
+  // rather than the per-CTA reduction and its ticket set the time; never more chunks than the layout's partials.
+  const int kl = k > 16 ? 32 : k > 8 ? 16 : k > 4 ? 8 : 4;
+  const int workers = (GTV_THREADS / 32) * (32 / kl);
+  const int max_links = L.gtv_chunk * L.gtv_chunks;   // >= the links of the largest occurrence
+  int nch = L.gtv_chunks;
+  if (8 * 4 * workers > L.gtv_chunk) nch = std::max(1, std::min(nch, ceil_div(max_links, 8 * 4 * workers)));
+  const int chunk = (int)round_up(ceil_div(max_links, nch), 32);
+  const dim3 grid(L.n_occ, ceil_div(max_links, chunk));
+  if (k > 32) k_gt_v_ds<32, true><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, chunk);
+  else if (k > 16) k_gt_v_ds<32, false><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, chunk);
+  else if (k > 8) k_gt_v_ds<16, false><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, chunk);
+  else if (k > 4) k_gt_v_ds<8, false><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, chunk);
+  else k_gt_v_ds<4, false><<<grid, GTV_THREADS, 0, s>>>(L, V, k, X, chunk);
   FETIRP_LAUNCH_CHECK();
 }
 
@@ -615,7 +667,13 @@ void g_apply_ds(const Layout& L, const float* Ah, const float* Al, int k, double
                 cudaStream_t s) {
   long long n = (long long)L.n_lambda * k;
   if (n == 0) return;
-  k_g_apply_ds<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, Ah, Al, k, alpha, beta, out);
+  const bool vec = (reinterpret_cast<uintptr_t>(Ah) | reinterpret_cast<uintptr_t>(Al)) % 16 == 0;
+  if (k == 4 && vec)
+    k_g_apply_ds_rows<4><<<ceil_div(L.n_lambda, 256), 256, 0, s>>>(L, Ah, Al, alpha, beta, out);
+  else if (k == 8 && vec)
+    k_g_apply_ds_rows<8><<<ceil_div(L.n_lambda, 256), 256, 0, s>>>(L, Ah, Al, alpha, beta, out);
+  else
+    k_g_apply_ds<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, Ah, Al, k, alpha, beta, out);
   FETIRP_LAUNCH_CHECK();
 }
 
