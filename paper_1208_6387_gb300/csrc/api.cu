@@ -198,6 +198,12 @@ struct fetirp_ctx_s {
   DBuf<int> d_slot_ptr, d_slot_row, d_row_slot, d_slot_occ, d_occ_obase, d_occ_pat, d_occ_q, d_occ_gofs,
       d_occ_group, d_pair_s, d_pair_t, d_grp_ptr, d_grp_row, d_ell_row, d_gen_occ;
   DBuf<double> d_rot, d_gen_R, d_slot_nb;   // rotation of every occurrence; general rotations and their slot kernels
+  DBuf<int8_t> d_occ_general;               // per occurrence: 1 = a general rotation
+  // the structure tables above are kept between builds while no call changed the structure (topo_valid) and the
+  // patterns' sizes and kernel dimensions are those they were built for (topo_sig)
+  bool topo_valid = false;
+  int topo_nl = 0;
+  std::vector<long long> topo_sig;
   DBuf<int8_t> d_ell_sign;
   DBuf<double> d_grp_w;
   // tables of the persistent iteration: multivector columns of the row's slots, 1 / slot count, offsets of the
@@ -256,6 +262,7 @@ struct fetirp_ctx_s {
   DBuf<float> Y32, Z32, Ylo32;
   DBuf<float> tc_part;            // K-split partials of the tensor-core product (small blocks only)
   DBuf<int> tc_error;
+  DBuf<double> spd_A, spd_X, spd_diag;   // work of the coarse matrix inverse
   long long hist_cap = 0;
   int rr_blocks = 0;
   fetirp_stats last{};
@@ -706,16 +713,19 @@ void factorize_patterns(fetirp_ctx ctx, const std::vector<PatternData*>& pats) {
 void spd_inverse(fetirp_ctx ctx, const double* A_rowmajor, int n, int npad, TilePlan& plan, DBuf<int>& zp,
                  double* out_rowmajor) {
   cudaStream_t s = ctx->stream;
-  DBuf<double> A((size_t)npad * npad), X((size_t)npad * npad), diag(npad);
-  A.zero(s);
-  X.zero(s);
+  ctx->spd_A.ensure((size_t)npad * npad);
+  ctx->spd_X.ensure((size_t)npad * npad);
+  ctx->spd_diag.ensure(npad);
+  DBuf<double>&A = ctx->spd_A, &X = ctx->spd_X, &diag = ctx->spd_diag;
+  FETIRP_CUDA(cudaMemsetAsync(A.p, 0, sizeof(double) * (size_t)npad * npad, s));
+  FETIRP_CUDA(cudaMemsetAsync(X.p, 0, sizeof(double) * (size_t)npad * npad, s));
   FETIRP_CUDA(cudaMemcpy2DAsync(A.p, sizeof(double) * npad, A_rowmajor, sizeof(double) * n, sizeof(double) * n, n,
                                 cudaMemcpyDeviceToDevice, s));   // symmetric: row-major == column-major
   if (npad > n) {
     k_set_diag<<<ceil_div(npad - n, 128), 128, 0, s>>>(A.p, npad, n, npad, 1.0);
     FETIRP_LAUNCH_CHECK();
   }
-  zp.alloc(npad);
+  zp.ensure(npad);
   copy_diag(A.p, npad, diag.p, s);
   chol_tiles(A.p, npad, plan, diag.p, zp.p, 1e-13, s);
   std::vector<int> h(npad);
@@ -740,7 +750,11 @@ TilePlan dense_plan(int nt) {
 }
 
 // ----------------------------------------------------------------------------------------- structure
-void invalidate(fetirp_ctx ctx) { ctx->prepared = false; }
+// A call that changed the structure (occurrences, groups, permutation, preconditioner, row blocks, patterns)
+void invalidate(fetirp_ctx ctx) {
+  ctx->prepared = false;
+  ctx->topo_valid = false;
+}
 void check_periodic(fetirp_ctx ctx);
 void precond_setup(fetirp_ctx ctx);
 
@@ -789,383 +803,366 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
   REQUIRE(ctx->row_blocks.empty() || ctx->row_blocks.back() == n_lambda, "row blocks do not cover n_lambda rows");
   const int n_pat = (int)ctx->pats.size();
   if (n_pat > MAXP) throw Error(FETIRP_EINVAL, "more than 16 patterns in one structure");
-  // occurrence tables
-  std::vector<int> obase(n_occ + 1, 0), occ_pat(n_occ), occ_q(n_occ), occ_gofs(n_occ), group(n_occ);
-  ctx->use.resize(n_pat);
-  for (auto& u : ctx->use) u.occs.clear();
-  for (int o = 0; o < n_occ; ++o) {
-    PatternData& P = *ctx->pats[ctx->occs[o].pattern];
-    PatternUse& Us = ctx->use[ctx->occs[o].pattern];
-    occ_pat[o] = ctx->occs[o].pattern;
-    occ_q[o] = (int)Us.occs.size();
-    Us.occs.push_back(o);
-    obase[o + 1] = obase[o] + P.n_b;
+  // structure tables (host work and uploads): rebuilt only when the structure or the patterns' shapes changed
+  std::vector<long long> sig;
+  for (auto& P : ctx->pats) {
+    sig.push_back(P->n); sig.push_back(P->n_b); sig.push_back(P->kdim); sig.push_back(P->npad);
+    sig.push_back(P->ld_y); sig.push_back(P->dpn);
   }
-  ctx->pofs.assign(n_pat + 1, 0);
-  for (int p = 0; p < n_pat; ++p) ctx->pofs[p + 1] = ctx->pofs[p] + ctx->pats[p]->kdim * (int)ctx->use[p].occs.size();
-  for (int o = 0; o < n_occ; ++o) occ_gofs[o] = ctx->pofs[occ_pat[o]] + occ_q[o] * ctx->pats[occ_pat[o]]->kdim;
-  ctx->n_G = ctx->pofs[n_pat];
-  // multivector groups
-  int k;
-  if (ctx->perm.on) {   // the block is [z, Pi z, ...]; occurrence groups only serve the tables below
-    if (ctx->perm.n != n_lambda) throw Error(FETIRP_EINVAL, "the permutation's size differs from n_lambda");
-    k = ctx->perm.k;
-    for (int o = 0; o < n_occ; ++o) group[o] = (int)((long long)o * std::min(k, n_occ) / n_occ);
-  } else if (ctx->k_user > 0) {
-    k = ctx->k_user;
-    group = ctx->groups_user;
-  } else {
-    k = std::max(1, std::min(ctx->opt.block_k, n_occ));
-    for (int o = 0; o < n_occ; ++o) group[o] = (int)((long long)o * k / n_occ);
-  }
-  REQUIRE((int)group.size() == n_occ, "groups do not match the number of occurrences");
-  if (k > 64) throw Error(FETIRP_EINVAL, "block width k > 64 is not supported");
-  ctx->k = k;
-  ctx->h_group = group;
-  ctx->sp.k = -1;   // the sparse-column plan belongs to the previous structure
-  // links -> gather CSR by slot, scatter lists by row
-  const int n_slots = obase[n_occ];
-  std::vector<int> cnt_slot(n_slots, 0);
-  std::vector<int> row_cnt(nl, 0), row_slot(2 * (size_t)nl, 0);
-  std::vector<int8_t> row_sign(2 * (size_t)nl, 0);
-  for (int o = 0; o < n_occ; ++o) {
-    const OccData& O = ctx->occs[o];
-    for (size_t i = 0; i < O.link_row.size(); ++i) {
-      const int row = O.link_row[i];
-      if (row >= nl) throw Error(FETIRP_EINVAL, "lambda_row >= n_lambda");
-      const int slot = obase[o] + O.link_j[i];
-      cnt_slot[slot]++;
-      if (row_cnt[row] >= 2) throw Error(FETIRP_EINVAL, "multiplier row " + std::to_string(row) + " has more than two entries");
-      row_slot[2 * (size_t)row + row_cnt[row]] = slot;
-      row_sign[2 * (size_t)row + row_cnt[row]] = O.link_sign[i];
-      row_cnt[row]++;
+  if (!(ctx->topo_valid && ctx->topo_nl == nl && ctx->topo_sig == sig)) {
+    ctx->topo_valid = false;
+    // occurrence tables
+    std::vector<int> obase(n_occ + 1, 0), occ_pat(n_occ), occ_q(n_occ), occ_gofs(n_occ), group(n_occ);
+    ctx->use.resize(n_pat);
+    for (auto& u : ctx->use) u.occs.clear();
+    for (int o = 0; o < n_occ; ++o) {
+      PatternData& P = *ctx->pats[ctx->occs[o].pattern];
+      PatternUse& Us = ctx->use[ctx->occs[o].pattern];
+      occ_pat[o] = ctx->occs[o].pattern;
+      occ_q[o] = (int)Us.occs.size();
+      Us.occs.push_back(o);
+      obase[o + 1] = obase[o] + P.n_b;
     }
-  }
-  for (int r = 0; r < nl; ++r) {
-    if (row_cnt[r] == 0) throw Error(FETIRP_EINVAL, "multiplier row " + std::to_string(r) + " has no entry");
-    if (row_cnt[r] == 2 && row_slot[2 * (size_t)r] > row_slot[2 * (size_t)r + 1]) {
-      std::swap(row_slot[2 * (size_t)r], row_slot[2 * (size_t)r + 1]);
-      std::swap(row_sign[2 * (size_t)r], row_sign[2 * (size_t)r + 1]);
+    ctx->pofs.assign(n_pat + 1, 0);
+    for (int p = 0; p < n_pat; ++p) ctx->pofs[p + 1] = ctx->pofs[p] + ctx->pats[p]->kdim * (int)ctx->use[p].occs.size();
+    for (int o = 0; o < n_occ; ++o) occ_gofs[o] = ctx->pofs[occ_pat[o]] + occ_q[o] * ctx->pats[occ_pat[o]]->kdim;
+    ctx->n_G = ctx->pofs[n_pat];
+    // multivector groups
+    int k;
+    if (ctx->perm.on) {   // the block is [z, Pi z, ...]; occurrence groups only serve the tables below
+      if (ctx->perm.n != n_lambda) throw Error(FETIRP_EINVAL, "the permutation's size differs from n_lambda");
+      k = ctx->perm.k;
+      for (int o = 0; o < n_occ; ++o) group[o] = (int)((long long)o * std::min(k, n_occ) / n_occ);
+    } else if (ctx->k_user > 0) {
+      k = ctx->k_user;
+      group = ctx->groups_user;
+    } else {
+      k = std::max(1, std::min(ctx->opt.block_k, n_occ));
+      for (int o = 0; o < n_occ; ++o) group[o] = (int)((long long)o * k / n_occ);
     }
-  }
-  std::vector<int> slot_ptr(n_slots + 1, 0);
-  for (int i = 0; i < n_slots; ++i) slot_ptr[i + 1] = slot_ptr[i] + cnt_slot[i];
-  std::vector<int> slot_row(slot_ptr[n_slots]), fill(slot_ptr.begin(), slot_ptr.end() - 1);
-  std::vector<int8_t> slot_sign(slot_ptr[n_slots]);
-  std::vector<int> slot_code(slot_ptr[n_slots]);   // 2 row + e: the link's entry in the per-row tables
-  for (int r = 0; r < nl; ++r)   // rows in increasing order inside every slot
-    for (int e = 0; e < row_cnt[r]; ++e) {
-      const int slot = row_slot[2 * (size_t)r + e];
-      slot_row[fill[slot]] = r;
-      slot_sign[fill[slot]] = row_sign[2 * (size_t)r + e];
-      slot_code[fill[slot]] = 2 * r + e;
-      fill[slot]++;
-    }
-  int max_links = 1;   // links of the largest occurrence
-  for (int o = 0; o < n_occ; ++o) max_links = std::max(max_links, slot_ptr[obase[o + 1]] - slot_ptr[obase[o]]);
-  std::vector<int> slot_occ(n_slots);
-  for (int o = 0; o < n_occ; ++o)
-    for (int j = obase[o]; j < obase[o + 1]; ++j) slot_occ[j] = o;
-  int ell_w = 1;
-  for (int i = 0; i < n_slots; ++i) ell_w = std::max(ell_w, slot_ptr[i + 1] - slot_ptr[i]);
-  std::vector<int> ell_row((size_t)n_slots * ell_w, 0);
-  std::vector<int8_t> ell_sign((size_t)n_slots * ell_w, 0);
-  for (int i = 0; i < n_slots; ++i)
-    for (int e = slot_ptr[i]; e < slot_ptr[i + 1]; ++e) {
-      ell_row[(size_t)i * ell_w + (e - slot_ptr[i])] = slot_row[e];
-      ell_sign[(size_t)i * ell_w + (e - slot_ptr[i])] = slot_sign[e];
-    }
-  // rows of every multivector group with the multiplicity weight 1/(occurrences in the row): the split
-  // S(r)[row][g] = sum over the row's occurrences in group g of r[row] / count
-  std::vector<std::vector<std::pair<int, double>>> grp(k);
-  for (int r = 0; r < nl; ++r) {
-    const double w = 1.0 / row_cnt[r];
-    int g1 = group[slot_occ[row_slot[2 * (size_t)r]]];
-    if (row_cnt[r] == 2) {
-      int g2 = group[slot_occ[row_slot[2 * (size_t)r + 1]]];
-      if (g1 == g2) { grp[g1].push_back({r, 2.0 * w}); continue; }
-      grp[g2].push_back({r, w});
-    }
-    grp[g1].push_back({r, w});
-  }
-  std::vector<int> grp_ptr(k + 1, 0), grp_row, grp_src;
-  std::vector<double> grp_w;
-  if (ctx->perm.on) {   // column g of S(r) = Pi^g r: entries (row, source row, weight) of Pi^g, row by row
-    const int pw = ctx->perm.pw;
-    for (int g = 0; g < k; ++g) {
-      for (int r = 0; r < nl; ++r)
-        for (int e = 0; e < pw; ++e) {
-          const size_t i = ((size_t)r * k + g) * pw + e;
-          if (ctx->perm.w[i] == 0.0) continue;
-          grp_row.push_back(r);
-          grp_src.push_back(ctx->perm.src[i]);
-          grp_w.push_back(ctx->perm.w[i]);
-        }
-      grp_ptr[g + 1] = (int)grp_row.size();
-    }
-  } else {
-    for (int g = 0; g < k; ++g) {
-      std::sort(grp[g].begin(), grp[g].end());
-      for (auto& e : grp[g]) { grp_row.push_back(e.first); grp_w.push_back(e.second); }
-      grp_ptr[g + 1] = (int)grp_row.size();
-    }
-  }
-  // neighbour pairs (s, t) sharing a row, plus (s, s)
-  std::vector<std::vector<int>> nbr(n_occ);
-  for (int o = 0; o < n_occ; ++o) nbr[o].push_back(o);
-  for (int r = 0; r < nl; ++r)
-    if (row_cnt[r] == 2) {
-      const int a = slot_occ[row_slot[2 * (size_t)r]], b = slot_occ[row_slot[2 * (size_t)r + 1]];
-      nbr[a].push_back(b);
-      nbr[b].push_back(a);
-    }
-  std::vector<int> pair_s, pair_t;
-  for (int o = 0; o < n_occ; ++o) {
-    std::sort(nbr[o].begin(), nbr[o].end());
-    nbr[o].erase(std::unique(nbr[o].begin(), nbr[o].end()), nbr[o].end());
-    for (int t : nbr[o]) { pair_s.push_back(o); pair_t.push_back(t); }
-  }
-  // upload
-  ctx->d_slot_ptr.upload(slot_ptr, s);
-  ctx->d_slot_row.upload(slot_row, s);
-  ctx->d_slot_sign.upload(slot_sign, s);
-  ctx->d_slot_code.upload(slot_code, s);
-  ctx->d_row_slot.upload(row_slot, s);
-  ctx->d_row_sign.upload(row_sign, s);
-  ctx->d_slot_occ.upload(slot_occ, s);
-  ctx->d_occ_obase.upload(obase, s);
-  ctx->d_occ_pat.upload(occ_pat, s);
-  ctx->d_occ_q.upload(occ_q, s);
-  ctx->d_occ_gofs.upload(occ_gofs, s);
-  ctx->d_occ_group.upload(group, s);
-  ctx->max_group_rows = 0;
-  for (int g = 0; g < k; ++g) ctx->max_group_rows = std::max(ctx->max_group_rows, grp_ptr[g + 1] - grp_ptr[g]);
-  ctx->n_grp_entries = grp_ptr[k];
-  ctx->grp_wr.ensure(2 * (size_t)std::max(ctx->n_grp_entries, 1));
-  ctx->d_ell_row.upload(ell_row, s);
-  ctx->d_ell_sign.upload(ell_sign, s);
-  ctx->d_grp_ptr.upload(grp_ptr, s);
-  ctx->d_grp_row.upload(grp_row, s);
-  ctx->d_grp_w.upload(grp_w, s);
-  if (ctx->pc.kind != 0) {
-    // scaling Delta(s) of every row entry (Eqs. 4-5, sum over the row's entries = 1): multiplicity 1 / count, or
-    // stiffness: the other side's share of the diagonal stiffness at the link's dof (global frame); 1 on
-    // Dirichlet rows
-    auto kdiag = [&](int slot) -> double {   // diagonal of R-hat K R-hat^T at the slot's global dof
-      const int o = slot_occ[slot];
-      const PatternData& P = *ctx->pats[occ_pat[o]];
-      const int j = slot - obase[o];
-      const int b = j / P.dpn, c = j % P.dpn, node = P.bnd_nodes[b];
-      auto entry = [&](int i, int jj) {
-        for (int64_t e = P.rowptr[i]; e < P.rowptr[i + 1]; ++e)
-          if (P.col[e] == jj) return P.val[e];
-        return 0.0;
-      };
-      if (!ctx->occs[o].general) return entry(node * P.dpn + c, node * P.dpn + c);
-      const double* R = ctx->occs[o].Rd;
-      double v = 0.0;
-      for (int c2 = 0; c2 < P.dpn; ++c2)
-        for (int c3 = 0; c3 < P.dpn; ++c3)
-          v += R[3 * c + c2] * R[3 * c + c3] * entry(node * P.dpn + c2, node * P.dpn + c3);
-      return v;
-    };
-    std::vector<double> delta(2 * (size_t)nl, 0.0), row_w(2 * (size_t)nl, 0.0);
-    for (int r = 0; r < nl; ++r) {
-      if (row_cnt[r] == 1) { delta[2 * (size_t)r] = 1.0; continue; }
-      if (ctx->pc.scaling == 0) { delta[2 * (size_t)r] = delta[2 * (size_t)r + 1] = 0.5; continue; }
-      const double k0 = kdiag(row_slot[2 * (size_t)r]), k1 = kdiag(row_slot[2 * (size_t)r + 1]);
-      if (!(k0 > 0.0 && k1 > 0.0)) throw Error(FETIRP_EINVAL, "stiffness scaling needs a positive diagonal");
-      delta[2 * (size_t)r] = k1 / (k0 + k1);
-      delta[2 * (size_t)r + 1] = k0 / (k0 + k1);
-    }
-    for (size_t i = 0; i < delta.size(); ++i) row_w[i] = row_sign[i] * delta[i];
-    std::vector<double> link_w(slot_row.size());
-    for (size_t e = 0; e < slot_row.size(); ++e) link_w[e] = slot_sign[e] * delta[(size_t)slot_code[e]];
-    // group lists with the Delta weights (same rows as grp_row): the split of the preconditioned residual
-    std::vector<double> grp_wd(grp_row.size(), 0.0);
-    if (!ctx->perm.on)
-      for (int g = 0; g < k; ++g)
-        for (int i = grp_ptr[g]; i < grp_ptr[g + 1]; ++i) {
-          const int r = grp_row[i];
-          for (int e = 0; e < row_cnt[r]; ++e)
-            if (group[slot_occ[row_slot[2 * (size_t)r + e]]] == g) grp_wd[i] += delta[2 * (size_t)r + e];
-        }
-    else
-      grp_wd = grp_w;
-    ctx->pc.row_d.upload(delta, s);
-    ctx->pc.row_w.upload(row_w, s);
-    ctx->pc.link_w.upload(link_w, s);
-    ctx->pc.grp_wd.upload(grp_wd, s);
-    FETIRP_CUDA(cudaStreamSynchronize(s));
-  }
-  if (ctx->perm.on) {
-    ctx->perm.d_grp_src.upload(grp_src, s);
-    ctx->perm.d_src.upload(ctx->perm.src, s);
-    ctx->perm.d_w.upload(ctx->perm.w, s);
-  }
-  {
-    std::vector<long long> pbase(n_pat + 1, 0);
-    for (int p = 0; p < n_pat; ++p)
-      pbase[p + 1] = pbase[p] + (long long)ctx->use[p].occs.size() * k * ctx->pats[p]->ld_y;
-    std::vector<int> row_grp(2 * (size_t)nl, -1), row_zld(2 * (size_t)nl, 0);
-    std::vector<double> row_wt(nl);
-    std::vector<long long> row_z(2 * (size_t)nl, 0);
-    for (int r = 0; r < nl; ++r) {
-      row_wt[r] = 1.0 / row_cnt[r];
-      for (int e = 0; e < row_cnt[r]; ++e) {
-        const int slot = row_slot[2 * (size_t)r + e];
-        const int o = slot_occ[slot];
-        const int p = occ_pat[o];
-        const long long ld = ctx->pats[p]->ld_y;
-        row_grp[2 * (size_t)r + e] = group[o];
-        row_z[2 * (size_t)r + e] = pbase[p] + (long long)occ_q[o] * k * ld + (slot - obase[o]);
-        row_zld[2 * (size_t)r + e] = (int)ld;
+    REQUIRE((int)group.size() == n_occ, "groups do not match the number of occurrences");
+    if (k > 64) throw Error(FETIRP_EINVAL, "block width k > 64 is not supported");
+    ctx->k = k;
+    ctx->h_group = group;
+    // links -> gather CSR by slot, scatter lists by row
+    const int n_slots = obase[n_occ];
+    std::vector<int> cnt_slot(n_slots, 0);
+    std::vector<int> row_cnt(nl, 0), row_slot(2 * (size_t)nl, 0);
+    std::vector<int8_t> row_sign(2 * (size_t)nl, 0);
+    for (int o = 0; o < n_occ; ++o) {
+      const OccData& O = ctx->occs[o];
+      for (size_t i = 0; i < O.link_row.size(); ++i) {
+        const int row = O.link_row[i];
+        if (row >= nl) throw Error(FETIRP_EINVAL, "lambda_row >= n_lambda");
+        const int slot = obase[o] + O.link_j[i];
+        cnt_slot[slot]++;
+        if (row_cnt[row] >= 2) throw Error(FETIRP_EINVAL, "multiplier row " + std::to_string(row) + " has more than two entries");
+        row_slot[2 * (size_t)row + row_cnt[row]] = slot;
+        row_sign[2 * (size_t)row + row_cnt[row]] = O.link_sign[i];
+        row_cnt[row]++;
       }
     }
-    ctx->d_row_grp.upload(row_grp, s);
-    ctx->d_row_zld.upload(row_zld, s);
-    ctx->d_row_wt.upload(row_wt, s);
-    ctx->d_row_z.upload(row_z, s);
-    // G restricted to the row: coarse column of each slot's occurrence and sign * Nb[j][m] (m < 6)
-    std::vector<int> rowg_gofs(2 * (size_t)nl, -1), rowg_kd(2 * (size_t)nl, 0);
-    std::vector<double> rowg_coef(12 * (size_t)nl, 0.0);
-    std::vector<std::vector<double>> hNb(n_pat);   // (pattern data is shared between contexts: copy locally)
-    for (int p = 0; p < n_pat; ++p) {
-      const PatternData& P = *ctx->pats[p];
-      if (P.kdim > 6) continue;   // such structures do not use the persistent iteration
-      hNb[p].resize((size_t)P.n_b * P.kdim);
-      if (P.kdim > 0)
-        FETIRP_CUDA(cudaMemcpyAsync(hNb[p].data(), P.Nb.p, sizeof(double) * hNb[p].size(), cudaMemcpyDeviceToHost, s));
+    for (int r = 0; r < nl; ++r) {
+      if (row_cnt[r] == 0) throw Error(FETIRP_EINVAL, "multiplier row " + std::to_string(r) + " has no entry");
+      if (row_cnt[r] == 2 && row_slot[2 * (size_t)r] > row_slot[2 * (size_t)r + 1]) {
+        std::swap(row_slot[2 * (size_t)r], row_slot[2 * (size_t)r + 1]);
+        std::swap(row_sign[2 * (size_t)r], row_sign[2 * (size_t)r + 1]);
+      }
     }
-    FETIRP_CUDA(cudaStreamSynchronize(s));
-    // the kernel restricted to a slot, in the global frame: N_b[j] for folded rotations; for a general
-    // rotation the slot (node b, global component c) takes sum_c2 R[c][c2] N_b[b dpn + c2]
-    auto nb_of = [&](int slot, int m) -> double {
-      const int o = slot_occ[slot];
-      const PatternData& P = *ctx->pats[occ_pat[o]];
-      const int j = slot - obase[o];
-      const std::vector<double>& nb = hNb[occ_pat[o]];
-      if (!ctx->occs[o].general) return nb[(size_t)j * P.kdim + m];
-      const int b = j / P.dpn, c = j % P.dpn;
-      double v = 0.0;
-      for (int c2 = 0; c2 < P.dpn; ++c2) v += ctx->occs[o].Rd[3 * c + c2] * nb[(size_t)(b * P.dpn + c2) * P.kdim + m];
-      return v;
-    };
-    for (int r = 0; r < nl; ++r)
+    std::vector<int> slot_ptr(n_slots + 1, 0);
+    for (int i = 0; i < n_slots; ++i) slot_ptr[i + 1] = slot_ptr[i] + cnt_slot[i];
+    std::vector<int> slot_row(slot_ptr[n_slots]), fill(slot_ptr.begin(), slot_ptr.end() - 1);
+    std::vector<int8_t> slot_sign(slot_ptr[n_slots]);
+    std::vector<int> slot_code(slot_ptr[n_slots]);   // 2 row + e: the link's entry in the per-row tables
+    for (int r = 0; r < nl; ++r)   // rows in increasing order inside every slot
       for (int e = 0; e < row_cnt[r]; ++e) {
         const int slot = row_slot[2 * (size_t)r + e];
+        slot_row[fill[slot]] = r;
+        slot_sign[fill[slot]] = row_sign[2 * (size_t)r + e];
+        slot_code[fill[slot]] = 2 * r + e;
+        fill[slot]++;
+      }
+    int max_links = 1;   // links of the largest occurrence
+    for (int o = 0; o < n_occ; ++o) max_links = std::max(max_links, slot_ptr[obase[o + 1]] - slot_ptr[obase[o]]);
+    std::vector<int> slot_occ(n_slots);
+    for (int o = 0; o < n_occ; ++o)
+      for (int j = obase[o]; j < obase[o + 1]; ++j) slot_occ[j] = o;
+    int ell_w = 1;
+    for (int i = 0; i < n_slots; ++i) ell_w = std::max(ell_w, slot_ptr[i + 1] - slot_ptr[i]);
+    std::vector<int> ell_row((size_t)n_slots * ell_w, 0);
+    std::vector<int8_t> ell_sign((size_t)n_slots * ell_w, 0);
+    for (int i = 0; i < n_slots; ++i)
+      for (int e = slot_ptr[i]; e < slot_ptr[i + 1]; ++e) {
+        ell_row[(size_t)i * ell_w + (e - slot_ptr[i])] = slot_row[e];
+        ell_sign[(size_t)i * ell_w + (e - slot_ptr[i])] = slot_sign[e];
+      }
+    // rows of every multivector group with the multiplicity weight 1/(occurrences in the row): the split
+    // S(r)[row][g] = sum over the row's occurrences in group g of r[row] / count
+    std::vector<std::vector<std::pair<int, double>>> grp(k);
+    for (int r = 0; r < nl; ++r) {
+      const double w = 1.0 / row_cnt[r];
+      int g1 = group[slot_occ[row_slot[2 * (size_t)r]]];
+      if (row_cnt[r] == 2) {
+        int g2 = group[slot_occ[row_slot[2 * (size_t)r + 1]]];
+        if (g1 == g2) { grp[g1].push_back({r, 2.0 * w}); continue; }
+        grp[g2].push_back({r, w});
+      }
+      grp[g1].push_back({r, w});
+    }
+    std::vector<int> grp_ptr(k + 1, 0), grp_row, grp_src;
+    std::vector<double> grp_w;
+    if (ctx->perm.on) {   // column g of S(r) = Pi^g r: entries (row, source row, weight) of Pi^g, row by row
+      const int pw = ctx->perm.pw;
+      for (int g = 0; g < k; ++g) {
+        for (int r = 0; r < nl; ++r)
+          for (int e = 0; e < pw; ++e) {
+            const size_t i = ((size_t)r * k + g) * pw + e;
+            if (ctx->perm.w[i] == 0.0) continue;
+            grp_row.push_back(r);
+            grp_src.push_back(ctx->perm.src[i]);
+            grp_w.push_back(ctx->perm.w[i]);
+          }
+        grp_ptr[g + 1] = (int)grp_row.size();
+      }
+    } else {
+      for (int g = 0; g < k; ++g) {
+        std::sort(grp[g].begin(), grp[g].end());
+        for (auto& e : grp[g]) { grp_row.push_back(e.first); grp_w.push_back(e.second); }
+        grp_ptr[g + 1] = (int)grp_row.size();
+      }
+    }
+    // neighbour pairs (s, t) sharing a row, plus (s, s)
+    std::vector<std::vector<int>> nbr(n_occ);
+    for (int o = 0; o < n_occ; ++o) nbr[o].push_back(o);
+    for (int r = 0; r < nl; ++r)
+      if (row_cnt[r] == 2) {
+        const int a = slot_occ[row_slot[2 * (size_t)r]], b = slot_occ[row_slot[2 * (size_t)r + 1]];
+        nbr[a].push_back(b);
+        nbr[b].push_back(a);
+      }
+    std::vector<int> pair_s, pair_t;
+    for (int o = 0; o < n_occ; ++o) {
+      std::sort(nbr[o].begin(), nbr[o].end());
+      nbr[o].erase(std::unique(nbr[o].begin(), nbr[o].end()), nbr[o].end());
+      for (int t : nbr[o]) { pair_s.push_back(o); pair_t.push_back(t); }
+    }
+    // upload
+    ctx->d_slot_ptr.upload(slot_ptr, s);
+    ctx->d_slot_row.upload(slot_row, s);
+    ctx->d_slot_sign.upload(slot_sign, s);
+    ctx->d_slot_code.upload(slot_code, s);
+    ctx->d_row_slot.upload(row_slot, s);
+    ctx->d_row_sign.upload(row_sign, s);
+    ctx->d_slot_occ.upload(slot_occ, s);
+    ctx->d_occ_obase.upload(obase, s);
+    ctx->d_occ_pat.upload(occ_pat, s);
+    ctx->d_occ_q.upload(occ_q, s);
+    ctx->d_occ_gofs.upload(occ_gofs, s);
+    ctx->d_occ_group.upload(group, s);
+    ctx->max_group_rows = 0;
+    for (int g = 0; g < k; ++g) ctx->max_group_rows = std::max(ctx->max_group_rows, grp_ptr[g + 1] - grp_ptr[g]);
+    ctx->n_grp_entries = grp_ptr[k];
+    ctx->grp_wr.ensure(2 * (size_t)std::max(ctx->n_grp_entries, 1));
+    ctx->d_ell_row.upload(ell_row, s);
+    ctx->d_ell_sign.upload(ell_sign, s);
+    ctx->d_grp_ptr.upload(grp_ptr, s);
+    ctx->d_grp_row.upload(grp_row, s);
+    ctx->d_grp_w.upload(grp_w, s);
+    if (ctx->pc.kind != 0) {
+      // scaling Delta(s) of every row entry (Eqs. 4-5, sum over the row's entries = 1): multiplicity 1 / count, or
+      // stiffness: the other side's share of the diagonal stiffness at the link's dof (global frame); 1 on
+      // Dirichlet rows
+      auto kdiag = [&](int slot) -> double {   // diagonal of R-hat K R-hat^T at the slot's global dof
         const int o = slot_occ[slot];
         const PatternData& P = *ctx->pats[occ_pat[o]];
-        if (P.kdim > 6 || P.kdim == 0) continue;
-        rowg_gofs[2 * (size_t)r + e] = occ_gofs[o];
-        rowg_kd[2 * (size_t)r + e] = P.kdim;
-        for (int m = 0; m < P.kdim; ++m) rowg_coef[(2 * (size_t)r + e) * 6 + m] = row_sign[2 * (size_t)r + e] * nb_of(slot, m);
+        const int j = slot - obase[o];
+        const int b = j / P.dpn, c = j % P.dpn, node = P.bnd_nodes[b];
+        auto entry = [&](int i, int jj) {
+          for (int64_t e = P.rowptr[i]; e < P.rowptr[i + 1]; ++e)
+            if (P.col[e] == jj) return P.val[e];
+          return 0.0;
+        };
+        if (!ctx->occs[o].general) return entry(node * P.dpn + c, node * P.dpn + c);
+        const double* R = ctx->occs[o].Rd;
+        double v = 0.0;
+        for (int c2 = 0; c2 < P.dpn; ++c2)
+          for (int c3 = 0; c3 < P.dpn; ++c3)
+            v += R[3 * c + c2] * R[3 * c + c3] * entry(node * P.dpn + c2, node * P.dpn + c3);
+        return v;
+      };
+      std::vector<double> delta(2 * (size_t)nl, 0.0), row_w(2 * (size_t)nl, 0.0);
+      for (int r = 0; r < nl; ++r) {
+        if (row_cnt[r] == 1) { delta[2 * (size_t)r] = 1.0; continue; }
+        if (ctx->pc.scaling == 0) { delta[2 * (size_t)r] = delta[2 * (size_t)r + 1] = 0.5; continue; }
+        const double k0 = kdiag(row_slot[2 * (size_t)r]), k1 = kdiag(row_slot[2 * (size_t)r + 1]);
+        if (!(k0 > 0.0 && k1 > 0.0)) throw Error(FETIRP_EINVAL, "stiffness scaling needs a positive diagonal");
+        delta[2 * (size_t)r] = k1 / (k0 + k1);
+        delta[2 * (size_t)r + 1] = k0 / (k0 + k1);
       }
-    std::vector<int> gen_occ;
-    std::vector<double> gen_R;
-    for (int o = 0; o < n_occ; ++o)
-      if (ctx->occs[o].general) {
-        gen_occ.push_back(o);
-        gen_R.insert(gen_R.end(), ctx->occs[o].Rd, ctx->occs[o].Rd + 9);
-      }
-    ctx->n_gen = (int)gen_occ.size();
-    if (ctx->n_gen > 0) {
-      for (int p = 0; p < n_pat; ++p)
-        if (ctx->pats[p]->kdim > 6) throw Error(FETIRP_EINVAL, "general rotations need kernel dimensions <= 6");
-      std::vector<double> snb((size_t)n_slots * 6, 0.0);
-      for (int slot = 0; slot < n_slots; ++slot)
-        for (int m = 0; m < ctx->pats[occ_pat[slot_occ[slot]]]->kdim; ++m) snb[(size_t)slot * 6 + m] = nb_of(slot, m);
-      ctx->d_gen_occ.upload(gen_occ, s);
-      ctx->d_gen_R.upload(gen_R, s);
-      ctx->d_slot_nb.upload(snb, s);
+      for (size_t i = 0; i < delta.size(); ++i) row_w[i] = row_sign[i] * delta[i];
+      std::vector<double> link_w(slot_row.size());
+      for (size_t e = 0; e < slot_row.size(); ++e) link_w[e] = slot_sign[e] * delta[(size_t)slot_code[e]];
+      // group lists with the Delta weights (same rows as grp_row): the split of the preconditioned residual
+      std::vector<double> grp_wd(grp_row.size(), 0.0);
+      if (!ctx->perm.on)
+        for (int g = 0; g < k; ++g)
+          for (int i = grp_ptr[g]; i < grp_ptr[g + 1]; ++i) {
+            const int r = grp_row[i];
+            for (int e = 0; e < row_cnt[r]; ++e)
+              if (group[slot_occ[row_slot[2 * (size_t)r + e]]] == g) grp_wd[i] += delta[2 * (size_t)r + e];
+          }
+      else
+        grp_wd = grp_w;
+      ctx->pc.row_d.upload(delta, s);
+      ctx->pc.row_w.upload(row_w, s);
+      ctx->pc.link_w.upload(link_w, s);
+      ctx->pc.grp_wd.upload(grp_wd, s);
+      FETIRP_CUDA(cudaStreamSynchronize(s));
     }
-    ctx->n_gcoef = 0;
-    for (int kd : rowg_kd) ctx->n_gcoef += kd;
-    ctx->d_rowg_gofs.upload(rowg_gofs, s);
-    ctx->d_rowg_kd.upload(rowg_kd, s);
-    ctx->d_rowg_coef.upload(rowg_coef, s);
+    if (ctx->perm.on) {
+      ctx->perm.d_grp_src.upload(grp_src, s);
+      ctx->perm.d_src.upload(ctx->perm.src, s);
+      ctx->perm.d_w.upload(ctx->perm.w, s);
+    }
     {
-      std::vector<float> ch(rowg_coef.size()), cl(rowg_coef.size());
-      for (size_t i = 0; i < rowg_coef.size(); ++i) {
-        ch[i] = (float)rowg_coef[i];
-        cl[i] = (float)(rowg_coef[i] - (double)ch[i]);
+      std::vector<long long> pbase(n_pat + 1, 0);
+      for (int p = 0; p < n_pat; ++p)
+        pbase[p + 1] = pbase[p] + (long long)ctx->use[p].occs.size() * k * ctx->pats[p]->ld_y;
+      std::vector<int> row_grp(2 * (size_t)nl, -1), row_zld(2 * (size_t)nl, 0);
+      std::vector<double> row_wt(nl);
+      std::vector<long long> row_z(2 * (size_t)nl, 0);
+      for (int r = 0; r < nl; ++r) {
+        row_wt[r] = 1.0 / row_cnt[r];
+        for (int e = 0; e < row_cnt[r]; ++e) {
+          const int slot = row_slot[2 * (size_t)r + e];
+          const int o = slot_occ[slot];
+          const int p = occ_pat[o];
+          const long long ld = ctx->pats[p]->ld_y;
+          row_grp[2 * (size_t)r + e] = group[o];
+          row_z[2 * (size_t)r + e] = pbase[p] + (long long)occ_q[o] * k * ld + (slot - obase[o]);
+          row_zld[2 * (size_t)r + e] = (int)ld;
+        }
       }
-      ctx->ds_coef.ensure(2 * rowg_coef.size());
-      FETIRP_CUDA(cudaMemcpyAsync(ctx->ds_coef.p, ch.data(), sizeof(float) * ch.size(), cudaMemcpyHostToDevice, s));
-      FETIRP_CUDA(cudaMemcpyAsync(ctx->ds_coef.p + ch.size(), cl.data(), sizeof(float) * cl.size(),
-                                  cudaMemcpyHostToDevice, s));
-      FETIRP_CUDA(cudaStreamSynchronize(s));   // the host vectors go out of scope
+      ctx->d_row_grp.upload(row_grp, s);
+      ctx->d_row_zld.upload(row_zld, s);
+      ctx->d_row_wt.upload(row_wt, s);
+      ctx->d_row_z.upload(row_z, s);
+      // G restricted to the row: coarse column of each slot's occurrence and its kernel dimension; the values
+      // sign * N_b[j][m] follow every factorisation and are formed on the device (row_coefs, below)
+      std::vector<int> rowg_gofs(2 * (size_t)nl, -1), rowg_kd(2 * (size_t)nl, 0);
+      for (int r = 0; r < nl; ++r)
+        for (int e = 0; e < row_cnt[r]; ++e) {
+          const int o = slot_occ[row_slot[2 * (size_t)r + e]];
+          const PatternData& P = *ctx->pats[occ_pat[o]];
+          if (P.kdim > 6 || P.kdim == 0) continue;   // such structures do not use the persistent iteration
+          rowg_gofs[2 * (size_t)r + e] = occ_gofs[o];
+          rowg_kd[2 * (size_t)r + e] = P.kdim;
+        }
+      std::vector<int> gen_occ;
+      std::vector<double> gen_R;
+      std::vector<int8_t> occ_general(n_occ, 0);
+      for (int o = 0; o < n_occ; ++o)
+        if (ctx->occs[o].general) {
+          gen_occ.push_back(o);
+          gen_R.insert(gen_R.end(), ctx->occs[o].Rd, ctx->occs[o].Rd + 9);
+          occ_general[o] = 1;
+        }
+      ctx->n_gen = (int)gen_occ.size();
+      if (ctx->n_gen > 0) {
+        for (int p = 0; p < n_pat; ++p)
+          if (ctx->pats[p]->kdim > 6) throw Error(FETIRP_EINVAL, "general rotations need kernel dimensions <= 6");
+        ctx->d_gen_occ.upload(gen_occ, s);
+        ctx->d_gen_R.upload(gen_R, s);
+        ctx->d_slot_nb.ensure((size_t)n_slots * 6);
+      }
+      ctx->d_occ_general.upload(occ_general, s);
+      ctx->n_gcoef = 0;
+      for (int kd : rowg_kd) ctx->n_gcoef += kd;
+      ctx->d_rowg_gofs.upload(rowg_gofs, s);
+      ctx->d_rowg_kd.upload(rowg_kd, s);
+      ctx->d_rowg_coef.ensure(12 * (size_t)nl);
+      ctx->ds_coef.ensure(2 * 12 * (size_t)nl);
     }
-  }
-  ctx->d_pair_s.upload(pair_s, s);
-  ctx->d_pair_t.upload(pair_t, s);
-  ctx->n_pairs = (int)pair_s.size();
-  std::vector<double> rot(9 * (size_t)n_occ);
-  for (int o = 0; o < n_occ; ++o) std::memcpy(&rot[9 * (size_t)o], ctx->occs[o].Rd, sizeof(double) * 9);
-  ctx->d_rot.upload(rot, s);
-  ctx->uoff.assign(n_occ + 1, 0);
-  for (int o = 0; o < n_occ; ++o) ctx->uoff[o + 1] = ctx->uoff[o] + ctx->pats[occ_pat[o]]->n;
-  ctx->n_u = ctx->uoff[n_occ];
-  ctx->d_uoff.upload(ctx->uoff, s);
+    ctx->d_pair_s.upload(pair_s, s);
+    ctx->d_pair_t.upload(pair_t, s);
+    ctx->n_pairs = (int)pair_s.size();
+    std::vector<double> rot(9 * (size_t)n_occ);
+    for (int o = 0; o < n_occ; ++o) std::memcpy(&rot[9 * (size_t)o], ctx->occs[o].Rd, sizeof(double) * 9);
+    ctx->d_rot.upload(rot, s);
+    ctx->uoff.assign(n_occ + 1, 0);
+    for (int o = 0; o < n_occ; ++o) ctx->uoff[o + 1] = ctx->uoff[o] + ctx->pats[occ_pat[o]]->n;
+    ctx->n_u = ctx->uoff[n_occ];
+    ctx->d_uoff.upload(ctx->uoff, s);
 
-  Layout& L = ctx->L;
-  L = Layout{};
-  L.n_lambda = nl; L.n_occ = n_occ; L.n_slots = n_slots; L.n_G = ctx->n_G; L.n_pat = n_pat; L.k = k;
-  L.slot_ptr = ctx->d_slot_ptr.p; L.slot_row = ctx->d_slot_row.p; L.slot_sign = ctx->d_slot_sign.p;
-  L.row_slot = ctx->d_row_slot.p; L.row_sign = ctx->d_row_sign.p; L.slot_occ = ctx->d_slot_occ.p;
-  L.ell_w = ell_w; L.ell_row = ctx->d_ell_row.p; L.ell_sign = ctx->d_ell_sign.p;
-  L.occ_obase = ctx->d_occ_obase.p; L.occ_pat = ctx->d_occ_pat.p; L.occ_q = ctx->d_occ_q.p;
-  L.occ_gofs = ctx->d_occ_gofs.p; L.occ_group = ctx->d_occ_group.p;
-  int max_nb = 1;
-  for (int p = 0; p < n_pat; ++p) {
-    L.Nb[p] = ctx->pats[p]->Nb.p;
-    L.n_b[p] = ctx->pats[p]->n_b;
-    L.kdim[p] = ctx->pats[p]->kdim;
-    max_nb = std::max(max_nb, ctx->pats[p]->n_b);
-  }
-  L.row_grp = ctx->d_row_grp.p; L.row_wt = ctx->d_row_wt.p;
-  L.rowg_gofs = ctx->d_rowg_gofs.p; L.rowg_kd = ctx->d_rowg_kd.p; L.rowg_coef = ctx->d_rowg_coef.p;
-  L.rowg_coef_hi = ctx->ds_coef.p;
-  L.rowg_coef_lo = ctx->ds_coef.p + 12 * (size_t)nl;
-  L.slot_code = ctx->d_slot_code.p;
-  for (int p = 0; p < n_pat; ++p) L.dpn[p] = ctx->pats[p]->dpn;
-  L.n_gen = ctx->n_gen;
-  L.gen_occ = ctx->n_gen ? ctx->d_gen_occ.p : nullptr;
-  L.gen_R = ctx->n_gen ? ctx->d_gen_R.p : nullptr;
-  L.slot_nb = ctx->n_gen ? ctx->d_slot_nb.p : nullptr;
-  {  // G^T V chunks: at most 512 links per CTA, and at least two CTAs per SM while chunks keep >= 64 links
-    int chunks =
-        std::max(ceil_div(max_links, 512), std::min(ceil_div(max_links, 64), ceil_div(2 * 152, std::max(n_occ, 1))));
-    L.gtv_chunk = (int)round_up(ceil_div(max_links, chunks), 32);
-    L.gtv_chunks = ceil_div(max_links, L.gtv_chunk);
-    ctx->d_gtv_part.ensure((size_t)std::max(n_occ, 1) * L.gtv_chunks * 6 * 64);
-    ctx->d_gtv_ticket.ensure((size_t)std::max(n_occ, 1));
-    ctx->d_gtv_ticket.zero(s);
-    L.gtv_part = ctx->d_gtv_part.p; L.gtv_ticket = ctx->d_gtv_ticket.p;
-  }
-  // per-pattern loads (pattern frame, new ordering) and work
-  for (int p = 0; p < n_pat; ++p) {
-    PatternData& P = *ctx->pats[p];
-    PatternUse& Us = ctx->use[p];
-    const int no = (int)Us.occs.size();
-    std::vector<double> F((size_t)P.npad * std::max(no, 1), 0.0);
-    for (int q = 0; q < no; ++q) {
-      const OccData& O = ctx->occs[Us.occs[q]];
-      for (int d = 0; d < P.n; ++d) F[(size_t)q * P.npad + P.newidx[d]] = O.f_local[d];
+    Layout& L = ctx->L;
+    L = Layout{};
+    L.n_lambda = nl; L.n_occ = n_occ; L.n_slots = n_slots; L.n_G = ctx->n_G; L.n_pat = n_pat; L.k = k;
+    L.slot_ptr = ctx->d_slot_ptr.p; L.slot_row = ctx->d_slot_row.p; L.slot_sign = ctx->d_slot_sign.p;
+    L.row_slot = ctx->d_row_slot.p; L.row_sign = ctx->d_row_sign.p; L.slot_occ = ctx->d_slot_occ.p;
+    L.ell_w = ell_w; L.ell_row = ctx->d_ell_row.p; L.ell_sign = ctx->d_ell_sign.p;
+    L.occ_obase = ctx->d_occ_obase.p; L.occ_pat = ctx->d_occ_pat.p; L.occ_q = ctx->d_occ_q.p;
+    L.occ_gofs = ctx->d_occ_gofs.p; L.occ_group = ctx->d_occ_group.p;
+    int max_nb = 1;
+    for (int p = 0; p < n_pat; ++p) {
+      L.Nb[p] = ctx->pats[p]->Nb.p;
+      L.n_b[p] = ctx->pats[p]->n_b;
+      L.kdim[p] = ctx->pats[p]->kdim;
+      max_nb = std::max(max_nb, ctx->pats[p]->n_b);
     }
-    Us.F.upload(F, s);
-    Us.U.ensure((size_t)P.npad * std::max(no, 1));
-    Us.d_occs.upload(Us.occs, s);
+    L.row_grp = ctx->d_row_grp.p; L.row_wt = ctx->d_row_wt.p;
+    L.rowg_gofs = ctx->d_rowg_gofs.p; L.rowg_kd = ctx->d_rowg_kd.p; L.rowg_coef = ctx->d_rowg_coef.p;
+    L.rowg_coef_hi = ctx->ds_coef.p;
+    L.rowg_coef_lo = ctx->ds_coef.p + 12 * (size_t)nl;
+    L.slot_code = ctx->d_slot_code.p;
+    for (int p = 0; p < n_pat; ++p) L.dpn[p] = ctx->pats[p]->dpn;
+    L.n_gen = ctx->n_gen;
+    L.gen_occ = ctx->n_gen ? ctx->d_gen_occ.p : nullptr;
+    L.gen_R = ctx->n_gen ? ctx->d_gen_R.p : nullptr;
+    L.slot_nb = ctx->n_gen ? ctx->d_slot_nb.p : nullptr;
+    {  // G^T V chunks: at most 512 links per CTA, and at least two CTAs per SM while chunks keep >= 64 links
+      int chunks =
+          std::max(ceil_div(max_links, 512), std::min(ceil_div(max_links, 64), ceil_div(2 * 152, std::max(n_occ, 1))));
+      L.gtv_chunk = (int)round_up(ceil_div(max_links, chunks), 32);
+      L.gtv_chunks = ceil_div(max_links, L.gtv_chunk);
+      ctx->d_gtv_part.ensure((size_t)std::max(n_occ, 1) * L.gtv_chunks * 6 * 64);
+      ctx->d_gtv_ticket.ensure((size_t)std::max(n_occ, 1));
+      ctx->d_gtv_ticket.zero(s);
+      L.gtv_part = ctx->d_gtv_part.p; L.gtv_ticket = ctx->d_gtv_ticket.p;
+    }
+    // per-pattern loads (pattern frame, new ordering) and work
+    for (int p = 0; p < n_pat; ++p) {
+      PatternData& P = *ctx->pats[p];
+      PatternUse& Us = ctx->use[p];
+      const int no = (int)Us.occs.size();
+      std::vector<double> F((size_t)P.npad * std::max(no, 1), 0.0);
+      for (int q = 0; q < no; ++q) {
+        const OccData& O = ctx->occs[Us.occs[q]];
+        for (int d = 0; d < P.n; ++d) F[(size_t)q * P.npad + P.newidx[d]] = O.f_local[d];
+      }
+      Us.F.upload(F, s);
+      Us.U.ensure((size_t)P.npad * std::max(no, 1));
+      Us.d_occs.upload(Us.occs, s);
+    }
+    ctx->topo_valid = true;
+    ctx->topo_nl = nl;
+    ctx->topo_sig = sig;
   }
+  const int k = ctx->k;
+  Layout& L = ctx->L;
+  for (int p = 0; p < n_pat; ++p) L.Nb[p] = ctx->pats[p]->Nb.p;
+  ctx->sp.k = -1;   // the sparse-column plan belongs to the previous structure or factorisation
+  // G by row from the current kernels
+  row_coefs(L, ctx->d_rot.p, ctx->d_occ_general.p, ctx->d_rowg_coef.p, ctx->ds_coef.p, ctx->ds_coef.p + 12 * (size_t)nl,
+            ctx->n_gen ? ctx->d_slot_nb.p : nullptr, s);
   // coarse problem: G^T G (FP64), its inverse, e, lambda_0 (projector paragraph)
   PhaseScope ph(ctx, FETIRP_PHASE_COARSE, 0.0, 0.0);
   ctx->n_Gpad = (int)round_up(std::max(ctx->n_G, 1), TILE);
-  ctx->GtG.alloc((size_t)std::max(ctx->n_G, 1) * std::max(ctx->n_G, 1));
-  ctx->Ginv.alloc((size_t)std::max(ctx->n_G, 1) * std::max(ctx->n_G, 1));
-  ctx->e.alloc(std::max(ctx->n_G, 1));
-  ctx->d.alloc(nl);
-  ctx->lambda0.alloc(nl);
-  ctx->c.alloc(nl);
+  ctx->GtG.ensure((size_t)std::max(ctx->n_G, 1) * std::max(ctx->n_G, 1));
+  ctx->Ginv.ensure((size_t)std::max(ctx->n_G, 1) * std::max(ctx->n_G, 1));
+  ctx->e.ensure(std::max(ctx->n_G, 1));
+  ctx->d.ensure(nl);
+  ctx->lambda0.ensure(nl);
+  ctx->c.ensure(nl);
   if (c_host) ctx->c.upload(c_host, nl, s);
   else if (c_dev) FETIRP_CUDA(cudaMemcpyAsync(ctx->c.p, c_dev, sizeof(double) * nl, cudaMemcpyDeviceToDevice, s));
   else ctx->c.zero(s);
@@ -3219,7 +3216,7 @@ fetirp_status fetirp_factorize(fetirp_ctx ctx) {
     factorize_patterns(ctx, all);
     ctx->phases_pending = true;
     ctx->pending_launches = (long long)(g_launch_count - l0);
-    invalidate(ctx);
+    ctx->prepared = false;   // d, the coarse problem and G's values follow the new factors; the structure stands
     return FETIRP_OK;
   });
 }

@@ -657,6 +657,64 @@ void gt_v_ds(const Layout& L, const double* V, int k, double* X, cudaStream_t s)
   FETIRP_LAUNCH_CHECK();
 }
 
+// G restricted to the rows (Layout.rowg_*): entry (row, e) of row r is sign * N_b of the e-th slot's occurrence at
+// the slot's dof, in the global frame; for a general rotation R of the occurrence (node b, global component c)
+// sum_c2 R[c][c2] N_b[b dpn + c2].  rowg_gofs / rowg_kd (the structure) are given; the values come from the
+// patterns' current kernels, so they follow every refactorisation.  Also their FP32 pairs (hi = fl32(v),
+// lo = fl32(v - hi)) and, with general rotations, slot_nb.
+__device__ __forceinline__ double slot_kernel(const Layout& L, const double* __restrict__ rot,
+                                              const int8_t* __restrict__ general, int slot, int m) {
+  const int o = L.slot_occ[slot];
+  const int p = L.occ_pat[o];
+  const int j = slot - L.occ_obase[o], kd = L.kdim[p];
+  const double* nb = L.Nb[p];
+  if (!general[o]) return nb[(size_t)j * kd + m];
+  const int dpn = L.dpn[p], b = j / dpn, c = j % dpn;
+  const double* R = rot + (size_t)9 * o;
+  double v = 0.0;
+  for (int c2 = 0; c2 < dpn; ++c2) v += R[3 * c + c2] * nb[(size_t)(b * dpn + c2) * kd + m];
+  return v;
+}
+
+__global__ void k_row_coefs(Layout L, const double* __restrict__ rot, const int8_t* __restrict__ general,
+                            double* __restrict__ coef, float* __restrict__ hi, float* __restrict__ lo) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // 2 row + e
+  if (i >= 2 * (long long)L.n_lambda) return;
+  const int kd = L.rowg_kd[i];
+  const int slot = L.row_slot[i];
+  const double sg = (double)L.row_sign[i];
+#pragma unroll
+  for (int m = 0; m < MAX_KDIM; ++m) {
+    const double v = m < kd ? sg * slot_kernel(L, rot, general, slot, m) : 0.0;
+    const float h = __double2float_rn(v);
+    coef[i * MAX_KDIM + m] = v;
+    hi[i * MAX_KDIM + m] = h;
+    lo[i * MAX_KDIM + m] = __double2float_rn(v - (double)h);
+  }
+}
+
+__global__ void k_slot_kernels(Layout L, const double* __restrict__ rot, const int8_t* __restrict__ general,
+                               double* __restrict__ snb) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= L.n_slots) return;
+  const int kd = L.kdim[L.occ_pat[L.slot_occ[slot]]];
+#pragma unroll
+  for (int m = 0; m < MAX_KDIM; ++m) snb[(size_t)slot * MAX_KDIM + m] = m < kd ? slot_kernel(L, rot, general, slot, m) : 0.0;
+}
+
+void row_coefs(const Layout& L, const double* rot, const int8_t* general, double* coef, float* hi, float* lo,
+               double* slot_nb, cudaStream_t s) {
+  const long long n = 2 * (long long)L.n_lambda;
+  if (n > 0) {
+    k_row_coefs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, rot, general, coef, hi, lo);
+    FETIRP_LAUNCH_CHECK();
+  }
+  if (slot_nb && L.n_slots > 0) {
+    k_slot_kernels<<<ceil_div(L.n_slots, 256), 256, 0, s>>>(L, rot, general, slot_nb);
+    FETIRP_LAUNCH_CHECK();
+  }
+}
+
 void split_pairs(long long n, const double* x, float* h, float* l, cudaStream_t s) {
   if (n <= 0) return;
   k_split_pairs<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(n, x, h, l);

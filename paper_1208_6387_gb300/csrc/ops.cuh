@@ -88,6 +88,11 @@ void split_pairs(long long n, const double* x, float* h, float* l, cudaStream_t 
 void small_gemm_ds(int m, int k, const float* Ah, const float* Al, const float* Bh, const float* Bl, double* C,
                    cudaStream_t s, double* part = nullptr);
 // dense G^T G (n_G x n_G, row-major), nb_ptr/nb_list: neighbour occurrences of every occurrence
+// Layout.rowg_coef and its FP32 pairs (hi, lo; 12 n_lambda entries each) from the patterns' kernels N_b, with
+// rot (9 per occurrence) and general (1 = a general rotation); slot_nb (n_slots x 6, may be NULL) likewise.
+// Reads Layout's row, slot, occurrence tables, Nb, kdim, dpn and rowg_kd.
+void row_coefs(const Layout& L, const double* rot, const int8_t* general, double* coef, float* hi, float* lo,
+               double* slot_nb, cudaStream_t s);
 void gtg_dense(const Layout& L, const int* nb_ptr, const int* nb_list, int n_pairs, const int* pair_s,
                const int* pair_t, double* GtG, cudaStream_t s);
 
