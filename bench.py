@@ -52,16 +52,18 @@ DEFAULTS = {  # per workload: local-product precision, multivector width, direct
 # library's autotuner picks on C3 from {4, 8, 16, 32} (the direction-history work grows with k).
 C3_ITERATIONS = 132
 PHASE_KERNELS = {  # the kernels each phase launches
-    "factor": "k_potrf_tile, k_trsm_tiles, k_update_pairs, k_tile_inverse, k_tri_*, k_lauum, k_split_tf32/bf16",
-    "coarse": "k_gtg, k_gemm_f64",
+    "factor": "k_potrf_tile, k_trsm_tiles, k_update_pairs, k_tile_inverse, k_tri_*; n_b >= 1024: k_pinv_rows_tf32, "
+              "k_tc_gemm<0> (S^dag = Y^T Y), k_split_bf16; else k_lauum, k_split_tf32/bf16",
+    "coarse": "k_row_coefs, k_gtg, k_gemm_f64, d: k_tri_*",
     "local": "k_local_gemm / k_tc_gemm", "gather": "k_gather_tile, k_rotate_traces", "scatter": "k_scatter",
-    "project": "k_gt_v, k_small_gemm, k_g_apply (FP64); k_split_pairs, k_gt_v_ds, k_small_gemm_ds, k_g_apply_ds "
-               "(mixed forms)",
+    "project": "k_gt_v, k_small_gemm, k_g_apply (FP64); k_split_pairs, k_gt_v_ds, k_small_gemm_ds, "
+               "k_g_apply_ds(_rows) (mixed forms)",
     "gram": "k_group_wr, k_gram_split + k_reduce_chunks_dyn, k_eta_partial(_ds) + k_eta_group_sums",
-    "reorth": "k_tall_update / k_tall_update_w<16|32>", "update": "k_split / k_perm_split, k_update",
+    "reorth": "k_tall_update / k_tall_update_w<4|8|16|32>", "update": "k_split / k_perm_split, k_update",
     "recover": "k_tri_*, k_unpermute_rotate", "normalise": "k_normalise",
     "iterate": "k_persist (whole block iterations in one cooperative launch)",
-    "outer": "FP64 residual: k_gather_tile, k_local_gemm<double>, k_scatter, projection",
+    "outer": "FP64 residual: k_gather_tile, k_local_gemm<double> (n_b >= 1024: two triangular products with "
+             "L_S^{-1}), k_scatter, projection",
 }
 PHASE_BOUND = {  # roofline resource of each phase's kernels
     "factor": "alu", "coarse": "alu", "local": "alu", "gather": "hbm", "scatter": "hbm", "project": "alu",
@@ -296,7 +298,8 @@ def run_ours(args, rank, world, local):
                       "frac": round(ach / FP64_PEAK_TFLOPS, 4),
                       "share_of_step": round(float(ph_ms[fi]) / total_ms, 4) if world == 1 else None,
                       "peak_source": "nominal FP64 rate (no measured FP64 peak on this pool)",
-                      "work": "FP64 flops of the tile Cholesky (tile pairs with fill), L_S^{-1} and S^+ per step"}
+                      "work": "FP64 flops of the tile Cholesky (tile pairs with fill), L_S^{-1}, and S^+ for n_b < 1024 (larger "
+                              "patterns form S^dag on the tensor cores), per step"}
     # the direction-history work (Gram products incl. eta, and the reorthogonalisation), its own key
     hg = [F.PHASES.index("gram"), F.PHASES.index("reorth")]
     hist_ms = float(sum(ph_ms[i] for i in hg))
