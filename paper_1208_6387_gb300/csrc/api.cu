@@ -120,6 +120,7 @@ struct PatternData {
   std::atomic<bool> s64_ok{false};
   std::mutex s64_mu;
   DBuf<float> Ypair;
+  DBuf<double> gemm_scratch;   // split partials of the skinny products with N_b (gemm_f64)
   DBuf<__nv_bfloat16> Sb_hi, Sb_lo;   // bf16 pair of S^dag (leading dimension ldsb, a multiple of 8)
   long long ldsb = 0;
   long long ld_y8 = 0;                // Y/Z leading dimension of the bf16 products (round_up(n_b, 8))
@@ -263,6 +264,7 @@ struct fetirp_ctx_s {
   DBuf<float> tc_part;            // K-split partials of the tensor-core product (small blocks only)
   DBuf<int> tc_error;
   DBuf<double> spd_A, spd_X, spd_diag;   // work of the coarse matrix inverse
+  DBuf<double> gemm_scratch;             // split partials of the skinny coarse products (gemm_f64)
   long long hist_cap = 0;
   int rr_blocks = 0;
   fetirp_stats last{};
@@ -525,6 +527,7 @@ void factor_stage_b(PatternData& P, int* tc_error, cudaStream_t s) {
   P.S64.ensure((size_t)nb * nb);
   if (kd > 0) P.Sdag.ensure((size_t)nb * nb);
   P.Nwork.ensure((size_t)nb * std::max(kd, 1) * 2 + 2 * kd * kd);
+  P.gemm_scratch.ensure(std::max<size_t>({gemm_f64_scratch(nb, kd, nb), gemm_f64_scratch(kd, kd, nb), 1}));
   P.S32.ensure((size_t)nb * nb);
   P.S_hi.ensure((size_t)nb * P.lds);
   P.S_lo.ensure((size_t)nb * P.lds);
@@ -551,8 +554,8 @@ void factor_stage_b(PatternData& P, int* tc_error, cudaStream_t s) {
     double* Aw = P.Nwork.p;                  // Lam N_b      (nb x kd, row-major)
     double* Ew = Aw + (size_t)nb * kd;       // N_b C^{-1}   (nb x kd)
     double* Cm = Ew + (size_t)nb * kd;       // N_b^T N_b, then its inverse (kd x kd)
-    gemm_f64(nb, kd, nb, 1.0, P.XS.p, 1, nbp, P.Nb.p, kd, 1, 0.0, Aw, kd, 1, s);
-    gemm_f64(kd, kd, nb, 1.0, P.Nb.p, 1, kd, P.Nb.p, kd, 1, 0.0, Cm, kd, 1, s);
+    gemm_f64(nb, kd, nb, 1.0, P.XS.p, 1, nbp, P.Nb.p, kd, 1, 0.0, Aw, kd, 1, s, P.gemm_scratch.p, P.gemm_scratch.n);
+    gemm_f64(kd, kd, nb, 1.0, P.Nb.p, 1, kd, P.Nb.p, kd, 1, 0.0, Cm, kd, 1, s, P.gemm_scratch.p, P.gemm_scratch.n);
     k_small_spd_inverse<<<1, 32, 0, s>>>(Cm, kd);
     FETIRP_LAUNCH_CHECK();
     gemm_f64(nb, kd, kd, 1.0, P.Nb.p, kd, 1, Cm, kd, 1, 0.0, Ew, kd, 1, s);
@@ -599,9 +602,9 @@ void form_sdag64(PatternData& P, cudaStream_t s) {
   double* E = A + (size_t)nb * kd;        // N_b C^{-1}    (nb x kd)
   double* Cm = E + (size_t)nb * kd;       // N_b^T N_b, then its inverse (kd x kd)
   double* D = Cm + kd * kd;               // N_b^T S^+ N_b (kd x kd)
-  gemm_f64(nb, kd, nb, 1.0, P.S64.p, nb, 1, P.Nb.p, kd, 1, 0.0, A, kd, 1, s);
-  gemm_f64(kd, kd, nb, 1.0, P.Nb.p, 1, kd, P.Nb.p, kd, 1, 0.0, Cm, kd, 1, s);
-  gemm_f64(kd, kd, nb, 1.0, P.Nb.p, 1, kd, A, kd, 1, 0.0, D, kd, 1, s);
+  gemm_f64(nb, kd, nb, 1.0, P.S64.p, nb, 1, P.Nb.p, kd, 1, 0.0, A, kd, 1, s, P.gemm_scratch.p, P.gemm_scratch.n);
+  gemm_f64(kd, kd, nb, 1.0, P.Nb.p, 1, kd, P.Nb.p, kd, 1, 0.0, Cm, kd, 1, s, P.gemm_scratch.p, P.gemm_scratch.n);
+  gemm_f64(kd, kd, nb, 1.0, P.Nb.p, 1, kd, A, kd, 1, 0.0, D, kd, 1, s, P.gemm_scratch.p, P.gemm_scratch.n);
   k_small_spd_inverse<<<1, 32, 0, s>>>(Cm, kd);
   FETIRP_LAUNCH_CHECK();
   gemm_f64(nb, kd, kd, 1.0, P.Nb.p, kd, 1, Cm, kd, 1, 0.0, E, kd, 1, s);
@@ -1179,15 +1182,20 @@ void build_structure(fetirp_ctx ctx, int64_t n_lambda, const double* c_host, con
     split_pairs(ng2, ctx->Ginv.p, ctx->ds_ginv.p, ctx->ds_ginv.p + ng2, s);
     ctx->ds_xa.ensure(4 * (size_t)ctx->n_G * 64);
     // e_s = N^T f_s
+    size_t scr = gemm_f64_scratch(ctx->n_G, 1, ctx->n_G);
+    for (int p = 0; p < n_pat; ++p)
+      scr = std::max(scr, gemm_f64_scratch(ctx->pats[p]->kdim, (int)ctx->use[p].occs.size(), ctx->pats[p]->npad));
+    ctx->gemm_scratch.ensure(std::max<size_t>(scr, 1));
     for (int p = 0; p < n_pat; ++p) {
       PatternData& P = *ctx->pats[p];
       PatternUse& Us = ctx->use[p];
       const int no = (int)Us.occs.size();
       if (no == 0 || P.kdim == 0) continue;
       gemm_f64(P.kdim, no, P.npad, 1.0, P.N.p, P.npad, 1, Us.F.p, 1, P.npad, 0.0, ctx->e.p + ctx->pofs[p], 1, P.kdim,
-               s);
+               s, ctx->gemm_scratch.p, ctx->gemm_scratch.n);
     }
-    gemm_f64(ctx->n_G, 1, ctx->n_G, 1.0, ctx->Ginv.p, ctx->n_G, 1, ctx->e.p, 1, 1, 0.0, ctx->Ac.p, 1, 1, s);
+    gemm_f64(ctx->n_G, 1, ctx->n_G, 1.0, ctx->Ginv.p, ctx->n_G, 1, ctx->e.p, 1, 1, 0.0, ctx->Ac.p, 1, 1, s,
+             ctx->gemm_scratch.p, ctx->gemm_scratch.n);
     g_apply(L, ctx->Ac.p, 1, 1.0, 0.0, ctx->lambda0.p, s);
   } else {
     ctx->lambda0.zero(s);
@@ -2108,7 +2116,8 @@ void recover(fetirp_ctx ctx, double* d_u_out, const double* res) {
       res = ctx->V1.p;
     }
     gt_v(L, res, 1, ctx->Xc.p, s);
-    gemm_f64(ctx->n_G, 1, ctx->n_G, 1.0, ctx->Ginv.p, ctx->n_G, 1, ctx->Xc.p, 1, 1, 0.0, ctx->Ac.p, 1, 1, s);
+    gemm_f64(ctx->n_G, 1, ctx->n_G, 1.0, ctx->Ginv.p, ctx->n_G, 1, ctx->Xc.p, 1, 1, 0.0, ctx->Ac.p, 1, 1, s,
+             ctx->gemm_scratch.p, ctx->gemm_scratch.n);
   }
   // u(s) = K^+ (f(s) - B(s)^T lambda) - N(s) alpha(s), with K^+ = L^{-T} L^{-1} and, by linearity,
   // L^{-1} (f - B^T lambda) = L^{-1} f - L^{-1} B^T lambda: the first term is the forward sweep kept from d, the

@@ -51,10 +51,14 @@ void tile_inverses(const double* L, int npad, const int* zp, double* Dinv, cudaS
 
 // C(m, n) = alpha * sum_k A(m, k) B(k, n) + beta * C(m, n) with arbitrary element strides:
 // A(m, k) = A[m * sAm + k * sAk], B(k, n) = B[k * sBk + n * sBn], C(m, n) = C[m * sCm + n * sCn].
-// FP64 arithmetic.  Generic (set-up and small coarse products).
+// FP64 arithmetic.  Generic (set-up and small coarse products).  A skinny product (fewer 32 x 32 output tiles
+// than SMs, a long reduction) splits its reduction dimension over more CTAs when the caller passes scratch of at
+// least gemm_f64_scratch(M, N, K) doubles (stream-ordered: reusable by the next call on the same stream), and
+// not inside a stream capture; the partials are added in a fixed order.
+size_t gemm_f64_scratch(int M, int N, int K);
 void gemm_f64(int M, int N, int K, double alpha, const double* A, long long sAm, long long sAk,
               const double* B, long long sBk, long long sBn, double beta, double* C, long long sCm,
-              long long sCn, cudaStream_t s);
+              long long sCn, cudaStream_t s, double* scratch = nullptr, size_t scratch_elems = 0);
 
 void copy_diag(const double* A, int npad, double* diag, cudaStream_t s);
 void zero_zp_rows(double* A, int npad, const int* zp, cudaStream_t s);

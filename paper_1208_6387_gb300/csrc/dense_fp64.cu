@@ -603,35 +603,44 @@ void tri_solve(const double* L, int npad, const TilePlan& plan, const int* zp, d
   }
 }
 
+// Reduction-dimension split of a skinny product: up to eight CTAs per SM (17 KB of shared memory each), >= 256
+// terms each; 1 = no split
+static int gemm_f64_splits(int M, int N, int K, int* kc_out) {
+  const long long t64 = (long long)ceil_div(M, TILE) * ceil_div(N, TILE);
+  const long long tiles = (long long)ceil_div(M, 32) * ceil_div(N, 32);
+  if (t64 >= 2 * 152 || tiles >= 152 || K < 1024) return 1;
+  int splits = (int)std::min<long long>(ceil_div(K, 256), std::max<long long>(1, 8 * 152 / tiles));
+  if (splits <= 1) return 1;
+  const int kc = ceil_div(ceil_div(K, splits), 32) * 32;
+  if (kc_out) *kc_out = kc;
+  return ceil_div(K, kc);
+}
+
+size_t gemm_f64_scratch(int M, int N, int K) {
+  if (M <= 0 || N <= 0) return 0;
+  const int splits = gemm_f64_splits(M, N, K, nullptr);
+  return splits > 1 ? (size_t)splits * M * N : 0;
+}
+
 void gemm_f64(int M, int N, int K, double alpha, const double* A, long long sAm, long long sAk, const double* B,
               long long sBk, long long sBn, double beta, double* C, long long sCm, long long sCn,
-              cudaStream_t s) {
+              cudaStream_t s, double* scratch, size_t scratch_elems) {
   if (M <= 0 || N <= 0) return;
   dim3 grid(ceil_div(M, TILE), ceil_div(N, TILE));
   if ((long long)grid.x * grid.y < 2 * 152) {   // too few 64x64 tiles to occupy the SMs' FP64 units
     dim3 g32(ceil_div(M, 32), ceil_div(N, 32));
-    const long long tiles = (long long)g32.x * g32.y;
-    // fewer 32x32 tiles than SMs and a long reduction (the skinny products N^T f, Lam N_b): split the reduction
-    // over up to eight CTAs per SM (17 KB of shared memory each), >= 256 terms each, partials added in a fixed
-    // order (stream-ordered scratch; not inside a stream capture)
-    int splits = 1;
+    int kc = 0;
+    const int splits = gemm_f64_splits(M, N, K, &kc);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    FETIRP_CUDA(cudaStreamIsCapturing(s, &cap));
-    if (tiles < 152 && K >= 1024 && cap == cudaStreamCaptureStatusNone)
-      splits = (int)std::min<long long>(ceil_div(K, 256), std::max<long long>(1, 8 * 152 / tiles));
-    if (splits > 1) {
-      const int kc = ceil_div(ceil_div(K, splits), 32) * 32;
-      splits = ceil_div(K, kc);
-      double* part = nullptr;
-      FETIRP_CUDA(cudaMallocAsync(&part, sizeof(double) * (size_t)splits * M * N, s));
+    if (splits > 1) FETIRP_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (splits > 1 && scratch && scratch_elems >= (size_t)splits * M * N && cap == cudaStreamCaptureStatusNone) {
       g32.z = splits;
-      k_gemm_f64_32<<<g32, 256, 0, s>>>(M, N, K, alpha, A, sAm, sAk, B, sBk, sBn, beta, C, sCm, sCn, part, kc);
+      k_gemm_f64_32<<<g32, 256, 0, s>>>(M, N, K, alpha, A, sAm, sAk, B, sBk, sBn, beta, C, sCm, sCn, scratch, kc);
       FETIRP_LAUNCH_CHECK();
       const long long mn = (long long)M * N;
-      k_gemm_f64_sum_parts<<<(unsigned)((mn + 255) / 256), 256, 0, s>>>(M, N, splits, part, alpha, beta, C, sCm,
+      k_gemm_f64_sum_parts<<<(unsigned)((mn + 255) / 256), 256, 0, s>>>(M, N, splits, scratch, alpha, beta, C, sCm,
                                                                          sCn);
       FETIRP_LAUNCH_CHECK();
-      FETIRP_CUDA(cudaFreeAsync(part, s));
       return;
     }
     k_gemm_f64_32<<<g32, 256, 0, s>>>(M, N, K, alpha, A, sAm, sAk, B, sBk, sBn, beta, C, sCm, sCn, nullptr, 0);
