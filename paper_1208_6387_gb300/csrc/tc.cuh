@@ -46,12 +46,9 @@ void split_bf16(const double* x, long long rows, long long cols, long long ld_in
                 __nv_bfloat16* lo, long long ld_out, cudaStream_t s);
 void split_bf16(const float* x, long long rows, long long cols, long long ld_in, __nv_bfloat16* hi,
                 __nv_bfloat16* lo, long long ld_out, cudaStream_t s);
-// hi = tf32(x) (round to nearest), lo = x - hi of x rounded to FP32; x is FP64 or FP32, outputs FP32 with
-// leading dimension ld_out.  The FP32 form may work in place (x == hi, ld_in == ld_out): each element is read
-// by the thread that writes it.
+// hi = tf32(x) (round to nearest), lo = x - hi of x rounded to FP32; x is FP64, outputs FP32 with leading
+// dimension ld_out.
 void split_tf32(const double* x, long long rows, long long cols, long long ld_in, float* hi, float* lo,
-                long long ld_out, cudaStream_t s);
-void split_tf32(const float* x, long long rows, long long cols, long long ld_in, float* hi, float* lo,
                 long long ld_out, cudaStream_t s);
 // The nb rows of Y^T = (Lam Pi)^T in tf32 pairs, where Lam = L_S^{-1} is stored transposed (X[i * ldx + j] =
 // Lam(j, i)), Pi = I - N_b (N_b^T N_b)^{-1} N_b^T the orthogonal projector off the kernel traces, A = Lam N_b and

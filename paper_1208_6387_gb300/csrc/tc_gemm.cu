@@ -323,10 +323,8 @@ __global__ void k_tc_reduce(const float* __restrict__ part, int splits, long lon
   Z[i] = acc;
 }
 
-// x may alias hi (in place, ld_in == ld_out): each element is read and then written by one thread
-template <typename TI>
-__global__ void k_split_tf32(const TI* x, long long rows, long long cols, long long ld_in, float* hi, float* lo,
-                             long long ld_out) {
+__global__ void k_split_tf32(const double* __restrict__ x, long long rows, long long cols, long long ld_in,
+                             float* __restrict__ hi, float* __restrict__ lo, long long ld_out) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= rows * ld_out) return;
   const long long r = idx / ld_out, c = idx % ld_out;
@@ -409,14 +407,7 @@ void split_tf32(const double* x, long long rows, long long cols, long long ld_in
                 long long ld_out, cudaStream_t s) {
   const long long n = rows * ld_out;
   if (n == 0) return;
-  k_split_tf32<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, rows, cols, ld_in, hi, lo, ld_out);
-  FETIRP_LAUNCH_CHECK();
-}
-void split_tf32(const float* x, long long rows, long long cols, long long ld_in, float* hi, float* lo,
-                long long ld_out, cudaStream_t s) {
-  const long long n = rows * ld_out;
-  if (n == 0) return;
-  k_split_tf32<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, rows, cols, ld_in, hi, lo, ld_out);
+  k_split_tf32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, rows, cols, ld_in, hi, lo, ld_out);
   FETIRP_LAUNCH_CHECK();
 }
 void pinv_rows_tf32(const double* X, long long ldx, const double* A, const double* E, int kd, long long nb,
