@@ -111,12 +111,11 @@ struct PatternData {
   }
   DBuf<float> S32, S_hi, S_lo;   // FP32 S^dag and its tf32 pair (leading dimension lds)
   long long lds = 0;
-  // Large patterns (n_b >= TC_SDAG_MIN_NB) form the bf16 pair of S^dag on the tensor cores from the rows of
-  // (L_S^{-1} Pi)^T (Ypair: tf32 pair, leading dimension lds); S^+ in FP64 and the FP32 forms of S^dag only when
-  // a caller needs them (ensure_splus64); until then their FP64 local products go through the factor
+  // s64_ok: S64, Sdag (kdim > 0), S32 and the tf32 pair hold the current factorisation's FP64 S^+, S^dag and
+  // their FP32 roundings.  Large patterns (n_b >= TC_SDAG_MIN_NB) form those only on first use (ensure_splus64)
+  // and cut the bf16 pair of S^dag at factorisation from a tensor-core Gram of the rows of (L_S^{-1} Pi)^T
+  // (Ypair: tf32 pair, leading dimension lds); until then their FP64 local products go through the factor
   // (LocalProblem::X).
-  // S64, Sdag (kdim > 0), S32 and the tf32 pair hold the current factorisation's FP64 S^+, S^dag and their FP32
-  // roundings; large patterns form them on first use (ensure_splus64), their bf16 pair at factorisation.
   std::atomic<bool> s64_ok{false};
   std::mutex s64_mu;
   DBuf<float> Ypair;
