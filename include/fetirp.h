@@ -330,9 +330,12 @@ fetirp_status fetirp_solve_device(fetirp_ctx ctx, int64_t n_lambda, const double
  */
 fetirp_status fetirp_apply_block(fetirp_ctx ctx, int32_t k, const double* V, double* Q, int32_t precision);
 
-/* As fetirp_apply_block on DEVICE buffers; enqueued on the context's stream, returns without waiting.  A
- * bounded wait of the tensor-core pipeline (FETIRP_PREC_TF32X3) that expired is reported only through
- * fetirp_device_status, since the call returns before the kernel has run. */
+/* As fetirp_apply_block on DEVICE buffers; enqueued on the context's stream, returns without waiting, except
+ * that the first call after a factorisation in FP64, FP32 or TF32X3 on a structure with a pattern of
+ * n_b >= 1024 first forms that pattern's S^+ and FP32 / tf32 forms of S^dag (see fetirp_create_pattern) and
+ * waits for them: make that call before any stream capture.  A bounded wait of the tensor-core pipeline
+ * (FETIRP_PREC_TF32X3) that expired is reported only through fetirp_device_status, since the call returns
+ * before the kernel has run. */
 fetirp_status fetirp_apply_block_device(fetirp_ctx ctx, int32_t k, const double* d_V, double* d_Q,
                                         int32_t precision);
 
@@ -374,7 +377,9 @@ fetirp_status fetirp_apply_split_device(fetirp_ctx ctx, const double* d_r, doubl
  *    2 x sum over occurrences of the boundary dof count) in FP64) returns FETIRP_EINVAL with the sizes in
  *    fetirp_last_error; nothing is written.
  *  - Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress, with that
- *    device current) and caches it; make that first call before any stream capture.
+ *    device current) and caches it, and the first call after a factorisation forms the operators of large
+ *    patterns as fetirp_apply_block_device does (into buffers sized at factorisation: no allocation); make
+ *    those first calls before any stream capture.
  *  - Sharing: every call on a device uses the same array and it keeps the previous call's contents; the
  *    call overwrites every scratch entry it reads, so nothing has to start at zero.  Calls that overlap on the
  *    GPU (other streams, other host threads, other contexts on the same device) race on the array and must
