@@ -514,27 +514,6 @@ template void gram<float, double>(int, int, int, const float*, int, const double
 template void gram<double, double>(int, int, int, const double*, int, const double*, int, double*,
                                    DBuf<double>&, cudaStream_t);
 
-__global__ void k_split_eta(int k, const double* __restrict__ ext, double* __restrict__ eta, double* __restrict__ wr) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= k * (k + 1)) return;
-  const int i = idx / (k + 1), j = idx % (k + 1);
-  if (j == k) wr[i] = ext[idx];
-  else eta[i * k + j] = ext[idx];
-}
-
-// Sum of chunk partials, one warp per output: lanes take chunks lane, lane+32, ... and a fixed shuffle tree
-// combines them (deterministic).
-__global__ void k_reduce_chunks_warp(int count, int chunks, const double* __restrict__ partial,
-                                     double* __restrict__ C) {
-  const int o = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (o >= count) return;
-  double v = 0.0;
-  for (int c = lane; c < chunks; c += 32) v += partial[(size_t)c * count + o];
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  if (lane == 0) C[o] = v;
-}
-
 // up to four chunks per SM (the sums are FP64-pipe bound: more resident warps keep the pipe busy)
 int eta_chunks(int n) { return std::max(1, std::min(608, ceil_div(n, 256))); }
 
