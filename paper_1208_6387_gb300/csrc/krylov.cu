@@ -505,10 +505,6 @@ void gram(int n, int a, int b, const TA* A, int lda, const TB* B, int ldb, doubl
   FETIRP_LAUNCH_CHECK();
 }
 
-void gram_f64(int n, int a, int b, const double* A, int lda, const double* B, int ldb, double* C,
-              DBuf<double>& partial, cudaStream_t s) {
-  gram<double, double>(n, a, b, A, lda, B, ldb, C, partial, s);
-}
 template void gram<float, double>(int, int, int, const float*, int, const double*, int, double*, DBuf<double>&,
                                   cudaStream_t);
 template void gram<double, double>(int, int, int, const double*, int, const double*, int, double*,
@@ -1315,21 +1311,6 @@ template void tall_update<double>(int, int, const int*, int, const double*, int,
                                   DBuf<double>&, DBuf<unsigned>&, cudaStream_t);
 template void tall_update<float>(int, int, const int*, int, const float*, int, const double*, double, double*,
                                  DBuf<double>&, DBuf<unsigned>&, cudaStream_t);
-
-// End of a block iteration: history count += k (restart when the next block would not fit), dropped
-// directions and iterations counted on the device.
-__global__ void k_advance(int* cols, int k, long long cap, const int* n_kept, int* dropped, int* iters) {
-  int c = *cols + k;
-  if ((long long)c + k > cap) c = 0;
-  *cols = c;
-  *dropped += k - *n_kept;
-  *iters += 1;
-}
-
-void advance(int* cols, int k, long long cap, const int* n_kept, int* dropped, int* iters, cudaStream_t s) {
-  k_advance<<<1, 1, 0, s>>>(cols, k, cap, n_kept, dropped, iters);
-  FETIRP_LAUNCH_CHECK();
-}
 
 void sum_sq(int n, const double* x, double* out_partial, int blocks, cudaStream_t s) {
   k_sum_sq<<<blocks, 256, 0, s>>>(n, x, out_partial);

@@ -267,8 +267,6 @@ int persist_ctas(bool fp64, int k);   // co-resident CTAs of the launch (0 if th
 // ---- block Gram products and the F-normalised update (numerical-issues subsection) -----------------
 // C (a x b, row-major) = A^T B, A n x a (ld lda), B n x b (ld ldb), FP64 accumulation over n in a fixed
 // order (two passes: per-chunk partials, then an ordered sum).
-void gram_f64(int n, int a, int b, const double* A, int lda, const double* B, int ldb, double* C,
-              DBuf<double>& partial, cudaStream_t s);
 template <typename TA, typename TB>
 void gram(int n, int a, int b, const TA* A, int lda, const TB* B, int ldb, double* C, DBuf<double>& partial,
           cudaStream_t s);
@@ -302,8 +300,6 @@ void tall_update_init();
 template <typename TH>
 void tall_update(int n, int a_max, const int* d_a, int k, const TH* Wh, int hk, const double* C, double alpha,
                  double* W, DBuf<double>& scratch, DBuf<unsigned>& tickets, cudaStream_t s);
-// history count += k with restart, dropped and iteration counters (one thread)
-void advance(int* cols, int k, long long cap, const int* n_kept, int* dropped, int* iters, cudaStream_t s);
 // Row-chunk partials of [eta | wr] = W^T [Q | r], a k x (k+1) block, FP64 sums: at most eta_chunks(n) of them
 // (k = 4 with ds: one per SM).  With more than ETA_GROUPS chunks they are first added into ETA_GROUPS group sums
 // (fixed order) stored after the chunks.  The return value is the offset, in blocks of k (k+1), of what
